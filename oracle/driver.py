@@ -1,0 +1,157 @@
+"""MLMC sample-size formulas and the adaptive MLMC driver (oracle side).
+
+TEST INFRASTRUCTURE ONLY (tests/, __graft_entry__.smoke(), bench.py's
+CPU-baseline / reference arm).
+
+Sec. 2.1: with per-level variance V_l and cost C_l, minimising
+sum N_l C_l subject to sum V_l / N_l = eps^2 gives N_l = lambda sqrt(V_l / C_l)
+with lambda = eps^-2 sum_k sqrt(V_k C_k), and total cost
+eps^-2 (sum_l sqrt(V_l C_l))^2 (eq. total_cost_MLMC).
+Sec. 2.2: the nested estimator has two terms per level (the approximate
+level difference and the exact-minus-approximate correction) and the same
+formula applies over all 2(L+1) terms with one multiplier lambda_M.
+
+The adaptive loop is the one of Giles (2008), which Sec. 6 says the on-line
+phase follows, with these stated constants (the paper gives none): variance
+target (1 - theta) eps^2 with theta = 1/2, bias target sqrt(theta) eps,
+weak order alpha = 1 (Euler-Maruyama), extrapolated variance decay beta
+(1 for Euler-Maruyama, 2 for Milstein) for a newly added level, L_min = 2,
+N_init = 10^4, L_max = 10.  Costs follow the model C = 2^l c_kind, so the
+sample counts are deterministic functions of the sums.
+"""
+import math
+
+from . import core
+
+
+def optimal_n(V, C, var_target):
+    """Real-valued optimal sample counts N_k = lambda sqrt(V_k / C_k)."""
+    lam = sum(math.sqrt(v * c) for v, c in zip(V, C)) / var_target
+    return [lam * math.sqrt(v / c) if v > 0 else 0.0 for v, c in zip(V, C)]
+
+
+def total_cost(V, C, eps2):
+    """eps^-2 (sum sqrt(V C))^2, eq. total_cost_MLMC (and its nested analogue)."""
+    return (sum(math.sqrt(v * c) for v, c in zip(V, C))) ** 2 / eps2
+
+
+def bias_estimate(means, alpha=1.0):
+    """Giles (2008) remaining-bias estimate from the last two level means."""
+    L = len(means) - 1
+    r = abs(means[L]) / (2.0 ** alpha - 1.0)
+    if L >= 1:
+        r = max(r, abs(means[L - 1]) / 2.0 ** alpha / (2.0 ** alpha - 1.0))
+    return r
+
+
+PLAIN_FP64, PLAIN_FP32, NESTED_FIXED, NESTED_FP16, NESTED_BF16 = range(5)
+
+
+def estimator_plan(mode):
+    """Per-level estimator variants for a driver mode."""
+    return {
+        PLAIN_FP64: [core.FP64_EXACT],
+        PLAIN_FP32: [core.FP32_EXACT],
+        NESTED_FIXED: [core.FIXED_APPROX, core.CORR_FIXED],
+        NESTED_FP16: [core.FP16_APPROX, core.CORR_FP16],
+        NESTED_BF16: [core.BF16_APPROX, core.CORR_BF16],
+    }[mode]
+
+
+def mlmc(eps, p, seed, mode=PLAIN_FP64, cost=None, fmt_of_level=None, d=10, method=1,
+         request=0, L_min=2, L_max=10, N_init=10_000, theta=0.5):
+    """Adaptive (nested) MLMC; returns dict(price, var, L, N=[[N per estimator] per level])."""
+    plan = estimator_plan(mode)
+    ne = len(plan)
+    if cost is None:
+        cost = {v: 1.0 for v in plan}
+    beta = 2.0 if p["scheme"] == core.MILSTEIN else 1.0
+    disc = math.exp(-p["r"] * p["T"])
+    L = L_min
+    N = [[0] * ne for _ in range(L + 1)]
+    S1 = [[0.0] * ne for _ in range(L + 1)]
+    S2 = [[0.0] * ne for _ in range(L + 1)]
+    dN = [[N_init] * ne for _ in range(L + 1)]
+    extrap = [[None] * ne for _ in range(L + 1)]
+
+    def run(lev, k, count):
+        v = plan[k]
+        fmt = fmt_of_level(lev) if fmt_of_level else None
+        s, _ = core.level(p, lev, N[lev][k], count, v, seed, request=request, d=d,
+                          method=method, fmt=fmt)
+        S1[lev][k] += disc * s["sum"]
+        S2[lev][k] += disc * disc * s["sum2"]
+        N[lev][k] += count
+
+    while True:
+        while any(x > 0 for row in dN for x in row):
+            for lev in range(L + 1):
+                for k in range(ne):
+                    if dN[lev][k] > 0:
+                        run(lev, k, dN[lev][k])
+            V, C = [], []
+            for lev in range(L + 1):
+                for k in range(ne):
+                    if N[lev][k] > 0:
+                        m = S1[lev][k] / N[lev][k]
+                        var = max(S2[lev][k] / N[lev][k] - m * m, 0.0)
+                    else:
+                        var = extrap[lev][k]
+                    V.append(max(var, 1e-300))
+                    C.append(cost[plan[k]] * 2.0 ** lev)
+            Nopt = optimal_n(V, C, (1.0 - theta) * eps * eps)
+            for lev in range(L + 1):
+                for k in range(ne):
+                    want = int(math.ceil(Nopt[lev * ne + k]))
+                    dN[lev][k] = max(0, want - N[lev][k])
+        means = [sum(S1[lev][k] / N[lev][k] for k in range(ne)) for lev in range(L + 1)]
+        if bias_estimate(means) <= math.sqrt(theta) * eps or L >= L_max:
+            break
+        # add a level with extrapolated variances
+        L += 1
+        N.append([0] * ne)
+        S1.append([0.0] * ne)
+        S2.append([0.0] * ne)
+        prev_var = []
+        for k in range(ne):
+            m = S1[L - 1][k] / N[L - 1][k]
+            prev_var.append(max(S2[L - 1][k] / N[L - 1][k] - m * m, 1e-300) / 2.0 ** beta)
+        extrap.append(prev_var)
+        V, C = [], []
+        for lev in range(L + 1):
+            for k in range(ne):
+                if N[lev][k] > 0:
+                    m = S1[lev][k] / N[lev][k]
+                    V.append(max(S2[lev][k] / N[lev][k] - m * m, 1e-300))
+                else:
+                    V.append(extrap[lev][k])
+                C.append(cost[plan[k]] * 2.0 ** lev)
+        Nopt = optimal_n(V, C, (1.0 - theta) * eps * eps)
+        dN = [[max(0, int(math.ceil(Nopt[lev * ne + k])) - N[lev][k]) for k in range(ne)]
+              for lev in range(L + 1)]
+    price = sum(S1[lev][k] / N[lev][k] for lev in range(L + 1) for k in range(ne))
+    var = 0.0
+    for lev in range(L + 1):
+        for k in range(ne):
+            m = S1[lev][k] / N[lev][k]
+            var += max(S2[lev][k] / N[lev][k] - m * m, 0.0) / N[lev][k]
+    return dict(price=price, var=var, L=L, N=N)
+
+
+def price_on_schedule(p, seed, mode, N, fmt_of_level=None, d=10, method=1, request=0):
+    """Price from fixed per-(level, estimator) sample counts N[l][k] (samples [0, N))."""
+    plan = estimator_plan(mode)
+    disc = math.exp(-p["r"] * p["T"])
+    price, var = 0.0, 0.0
+    sums = []
+    for lev, row in enumerate(N):
+        srow = []
+        for k, n in enumerate(row):
+            fmt = fmt_of_level(lev) if fmt_of_level else None
+            s, _ = core.level(p, lev, 0, n, plan[k], seed, request=request, d=d, method=method, fmt=fmt)
+            m = disc * s["sum"] / n
+            price += m
+            var += max(disc * disc * s["sum2"] / n - m * m, 0.0) / n
+            srow.append(s)
+        sums.append(srow)
+    return dict(price=price, var=var, sums=sums)
