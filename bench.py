@@ -1,0 +1,301 @@
+"""Benchmark of the nested-MLMC level path on GB300.
+
+One step = one launch of the whole level work list of the nested workload:
+European and digital call on GBM (S0 = K = 100, r = 0.05, sigma = 0.2, T = 1),
+Euler-Maruyama, levels 0..8, approximate estimator (Method-1 table, d = 10,
+fixed point with the default per-level formats) with N~_l = max(10^4, 10^7
+2^-1.5l) samples and correction estimator (FP32 exact minus fixed point on
+shared uniforms) with 10^4 samples per level.  Inputs (the work list and
+tables) are resident in device memory when the timed region starts; L2 is
+flushed between steps (256 MiB write) outside the per-step events.
+
+Prints one JSON line.  `--impl reference` times the CPU oracle instead (the
+reference arm).  Under torchrun each rank simulates a disjoint sample range
+(first_sample offset by rank), the step time is the max over ranks and the
+value is the path-steps of all ranks per second (weak scaling).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2502_07123_gb300 import workloads as W  # noqa: E402
+
+METRIC = "time-to-ε price & path-steps/s: nested approx-RV vs plain MLMC; p50/p99 latency"
+UNIT = "path-steps/s"
+WORKLOAD = "nested MLMC step: euro+digital call GBM, EM, levels 0-8, N~ 1e7..1e4 fixed-point approx + 1e4 FP32-fixed corrections"
+
+# Algorithmic 32-bit lane operations per fine path-step (roofline section):
+#   Philox4x32-10: 10 rounds x (2 wide multiplies + 2 three-input XORs) / 4 words = 10
+#   table index, lookup and sign: 5
+#   fixed-point Algorithm-1 fine step (2 products, 2 sums, 4 roundings): 10
+#   coarse step every other fine step: (1 + 10) / 2 = 5.5
+OPS_APPROX_FIXED_EM = 30.5
+# SM issue peak: 152 SMs x 4 schedulers x 32 lanes x 2070 MHz (one warp instruction per scheduler per clock)
+ALU_PEAK_TOPS = 152 * 4 * 32 * 2.070e9 / 1e12
+
+
+def build_items(m, rank=0):
+    cfg = W.nested_config()
+    items, meta = [], []
+    cache = {}
+    for it in cfg["items"]:
+        p = it["params"]
+        key = p["payoff"]
+        if key not in cache:
+            cache[key] = m.make_params(p, d=cfg["d"], method=cfg["method"],
+                                       formats=[W.default_format(p, lev) for lev in range(9)],
+                                       request=it["request"])
+        items.append(dict(params=cache[key], level=it["level"], variant=it["variant"],
+                          first_sample=rank * it["N"], N=it["N"]))
+        meta.append(it)
+    return items, meta, cfg
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def oracle_step_sample(meta, cfg, fraction, rank=0):
+    """Time the CPU oracle on the first `fraction` of every work item; returns (path_steps, seconds)."""
+    from oracle import core
+    steps = 0
+    t0 = time.perf_counter()
+    for it in meta:
+        n = max(1, int(it["N"] * fraction))
+        p = it["params"]
+        fmt = W.default_format(p, it["level"]) if it["variant"] in (W.FIXED_APPROX, W.CORR_FIXED) else None
+        core.level(p, it["level"], rank * it["N"], n, it["variant"], cfg["seed"], request=it["request"],
+                   d=cfg["d"], method=cfg["method"], fmt=fmt)
+        steps += n << it["level"]
+    return steps, time.perf_counter() - t0
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle on the host cores, same workload, bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import build as ob
+    ob.build()
+    items_meta = W.nested_config()
+    meta = items_meta["items"]
+    frac = args.ref_fraction
+    for _ in range(args.warmup):
+        oracle_step_sample(meta, items_meta, frac * 0.1)
+    tot_steps, tot_s = 0, 0.0
+    for _ in range(args.steps):
+        s, dt = oracle_step_sample(meta, items_meta, frac)
+        tot_steps += s
+        tot_s += dt
+    v = tot_steps / tot_s
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "first %.3g of every work item" % frac},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "first %.3g of every work item per step" % frac},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--steps-per-thread", type=int, default=0)
+    ap.add_argument("--cpu-fraction", type=float, default=0.25)
+    ap.add_argument("--ref-fraction", type=float, default=0.1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tte", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2502_07123_gb300 import mlmc as m
+
+    items, meta, cfg = build_items(m, rank)
+    tuning = None
+    if args.threads or args.steps_per_thread:
+        tuning = dict(threads=args.threads, steps_per_thread=args.steps_per_thread)
+    plan = m.Plan(items, cfg["seed"], tuning)
+    info = plan.info()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    for _ in range(max(3, args.warmup)):
+        plan.launch(stream)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kern_ms = {}
+    with ClockSampler(local) as clocks:
+        barrier()
+        t_wall = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            plan.launch(stream)
+            ends[k].record(stream)
+            for j in range(info["kernels"]):
+                fam, ms = plan.kernel_time(j)
+                kern_ms.setdefault(fam, []).append(ms)
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    local_ms = sum(step_ms) / len(step_ms)
+    ms = local_ms
+    if world > 1:
+        t = torch.tensor([local_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    steps_per_launch = info["path_steps"] * world
+    value = steps_per_launch / (ms * 1e-3)
+
+    # results of the last launch, merged over ranks on the host (no data-path collective)
+    res = plan.results()
+
+    # end-to-end: the same work through the host-buffer C-ABI call (plan build, H2D, launch, D2H)
+    e2e_ms = []
+    for _ in range(max(2, min(5, args.steps))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m.mlmc_run(items, cfg["seed"], tuning)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_value = info["path_steps"] / (statistics.median(e2e_ms) * 1e-3)
+
+    # roofline of the dominant kernel (approximate estimator, fixed point, family 2)
+    dom = max(kern_ms, key=lambda f: sum(kern_ms[f]))
+    dom_ms = sum(kern_ms[dom]) / len(kern_ms[dom])
+    approx_steps = sum(it["N"] << it["level"] for it in items if it["variant"] == m.FIXED_APPROX)
+    roofline = None
+    if dom == 2:
+        achieved = OPS_APPROX_FIXED_EM * approx_steps / (dom_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Top/s",
+                    "frac": achieved / ALU_PEAK_TOPS, "traffic": None,
+                    "kernel": "level_kernel<APPROX,fixed,EM,terminal>", "ms_per_launch": dom_ms,
+                    "ops_per_path_step": OPS_APPROX_FIXED_EM}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "i64+f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "path_steps_per_step": steps_per_launch,
+                   "work_items": len(items), "kernels_per_step": info["kernels"] + 1,
+                   "ctas_per_step": info["ctas"], "l2": "flushed between steps (256 MiB write)",
+                   "wall_s": t_wall},
+        "gpu_launches": (info["kernels"] + 1) * args.steps,
+        "kernel_ms": {str(f): sum(v) / len(v) for f, v in kern_ms.items()},
+        "clocks": clocks.summary(),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": info["h2d_bytes"],
+                "d2h_bytes_per_step": info["d2h_bytes"], "ms": statistics.median(e2e_ms)},
+        "roofline": roofline,
+    }
+    if rank == 0 and not args.no_tte:
+        out["time_to_eps"] = time_to_eps(m, torch)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import build as ob
+        ob.build()
+        steps_c, secs = oracle_step_sample(meta, cfg, args.cpu_fraction)
+        out["cpu_baseline"] = {"value": steps_c / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": "first %.3g of every work item of one step (%d path-steps, %.1f s)"
+                                         % (args.cpu_fraction, steps_c, secs)}
+    if rank == 0:
+        print(json.dumps(out))
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def time_to_eps(m, torch, eps=1e-3, seeds=(1, 2, 3)):
+    """Wall time of mlmc_estimate at RMS error eps: nested fixed point vs plain FP32 (European call)."""
+    p = W.params()
+    P = m.make_params(p, d=10, method=1, formats=[W.default_format(p, lev) for lev in range(11)])
+    out = {"eps": eps}
+    for name, mode in (("plain_fp32", m.MODE_PLAIN_FP32), ("nested_fixed", m.MODE_NESTED_FIXED)):
+        m.mlmc_estimate(1e-2, P, mode, 99, 10)   # warm tables and contexts
+        ts, prices = [], []
+        for s in seeds:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = m.mlmc_estimate(eps, P, mode, s, 10)
+            ts.append(time.perf_counter() - t0)
+            prices.append(r["price"])
+        out[name] = {"s_median": statistics.median(ts), "prices": prices, "L": r["L"], "N": r["N"]}
+    out["speedup_nested_vs_plain"] = out["plain_fp32"]["s_median"] / out["nested_fixed"]["s_median"]
+    return out
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,242 @@
+/*
+ * mlmc.h -- C ABI of the GB300 nested-MLMC level library (libmlmc_gb300.so).
+ *
+ * The library simulates, on one CUDA GPU, the per-sample coupled fine/coarse
+ * Geometric Brownian Motion paths of one or more MLMC levels and reduces them
+ * to per-level sums of Y and Y^2, as described in Haas & Giles, "A nested MLMC
+ * framework for efficient simulations on FPGAs" (arXiv 2502.07123):
+ *   - Sec. 2.1, eq. classic_MLMC_iden: level differences Y = P_l - P_{l-1}
+ *     with fine and coarse paths driven by the same Normal increments;
+ *   - Sec. 2.2, eq. chap:nested_exp: the nested split into an approximate
+ *     level difference dP~_l and the correction dP_l - dP~_l;
+ *   - Sec. 3: exact Normals Z = Phi^{-1}(U) and approximate Normals Z~ from a
+ *     table indexed by the top d bits of the same uniform integer J;
+ *   - Sec. 4.1, Algorithm 1: the low-precision path step in fixed point.
+ *
+ * Conventions for every entry point:
+ *   - Host pointers are caller-owned and only read or written during the call.
+ *     Pointers documented as "device" must point to CUDA device memory of the
+ *     current device that stays valid until the enqueued work has finished.
+ *   - Every call returns an mlmc_status; no call aborts the process.  On an
+ *     error the output arguments are left unspecified.
+ *   - Sums are of discounted sample values: the factor exp(-rT) is applied.
+ *   - A `void *stream` argument is a cudaStream_t (NULL = legacy default stream).
+ *   - The library allocates its own device memory (tables, work lists, scratch)
+ *     lazily on the current CUDA device and keeps it until process exit.
+ *   - Calls from several host threads must be serialised by the caller.
+ *   - There is no CPU fallback: without a usable CUDA device every compute
+ *     entry point returns MLMC_ECUDA.
+ */
+#ifndef MLMC_GB300_H
+#define MLMC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MLMC_OK = 0,
+  MLMC_EINVAL = 1,     /* an argument is out of range or inconsistent        */
+  MLMC_ENOMEM = 2,     /* a device or host allocation failed                 */
+  MLMC_ECUDA = 3,      /* a CUDA runtime call failed (or no device)          */
+  MLMC_ETIMEOUT = 4,   /* a bounded wait ran out                             */
+  MLMC_EOVERFLOW = 5,  /* a constant does not fit its fixed-point format     */
+  MLMC_ENOTREADY = 6   /* results requested before the work was launched     */
+} mlmc_status;
+
+typedef enum { MLMC_EULER = 0, MLMC_MILSTEIN = 1 } mlmc_scheme;
+
+/* Payoffs (undiscounted form; the library discounts the sums):
+ *   EURO     max(S_N - K, 0)
+ *   DIGITAL  1[S_N > K]
+ *   ASIAN    max(A - K, 0), A = trapezoidal time average on the path's own grid
+ *   LOOKBACK S_N - min_i S_i (floating-strike call, minimum over the path's grid) */
+typedef enum { MLMC_EURO = 0, MLMC_DIGITAL = 1, MLMC_ASIAN = 2, MLMC_LOOKBACK = 3 } mlmc_payoff;
+
+/* Estimator variants.  "EXACT" = plain level difference dP_l with exact Normals
+ * (Sec. 2.1); "APPROX" = dP~_l with approximate Normals and low-precision
+ * arithmetic (eq. GBM_sde_fi); "NESTED_CORR" = dP_l - dP~_l on shared uniforms
+ * (eq. chap:nested_exp), exact part in FP32. */
+typedef enum {
+  MLMC_FP64_EXACT = 0,
+  MLMC_FP32_EXACT = 1,
+  MLMC_FP16_APPROX = 2,
+  MLMC_BF16_APPROX = 3,
+  MLMC_FIXED_APPROX = 4,
+  MLMC_NESTED_CORR_FIXED = 5,
+  MLMC_NESTED_CORR_FP16 = 6,
+  MLMC_NESTED_CORR_BF16 = 7
+} mlmc_variant;
+
+/* Fixed-point format of the Algorithm-1 variables on one level (Sec. 4.1):
+ * value = n 2^-f[i], |n| <= 2^(e[i]+f[i]) - 1, i in the order
+ * {Z~, con1, con2, mul1, sum1, mul2, S}.  The GPU path requires
+ * e+f <= 31 for the first five and e+f <= 62 for mul2 and S, and that every
+ * exact product and alignment fits 62 bits (checked; MLMC_EINVAL otherwise). */
+typedef struct {
+  int8_t e[7];
+  int8_t f[7];
+} mlmc_format;
+
+typedef struct {
+  double S0, K, r, sigma, T;    /* GBM dS = r S dt + sigma S dW, maturity T      */
+  int32_t payoff;               /* mlmc_payoff                                   */
+  int32_t scheme;               /* mlmc_scheme                                   */
+  int32_t icdf_method;          /* 1: piecewise constant on uniform intervals (Sec. 3.1);
+                                   3: piecewise linear on dyadic intervals (Sec. 3.3) */
+  int32_t icdf_bits;            /* d in [2, 14]: bits of J used by the table      */
+  const mlmc_format *formats;   /* host array indexed by level, or NULL for the
+                                   library's default schedule (mlmc_default_format) */
+  int32_t n_formats;            /* entries in formats                            */
+  uint32_t request_id;          /* enters the Philox counter (independent streams) */
+} mlmc_params;
+
+/* Per-level result.  sum/sum2 are discounted FP64 sums of Y and Y^2.  When
+ * exact_int is 1 (approximate-only estimators, whose samples are integers)
+ * isum and isum2 hold the exact undiscounted integer sums in units 2^-unit
+ * and 2^-2unit; sum = exp(-rT) 2^-unit isum rounded once. */
+typedef struct {
+  double sum, sum2;
+  uint64_t n;
+  double seconds;               /* device time of the launch that produced it    */
+  uint64_t saturations;         /* samples on which a fixed-point value saturated */
+  int64_t isum;
+  uint64_t isum2_lo, isum2_hi;
+  int32_t unit, exact_int;
+} mlmc_sums;
+
+/* One simulated sample, written by mlmc_level_dump (for parity testing). */
+typedef struct {
+  double pf, pc;     /* exact-path payoffs (undiscounted); pc = 0 on level 0   */
+  double sf, sc;     /* exact-path terminal values                             */
+  double af, ac;     /* approximate-path terminal values                       */
+  int64_t qf, qc;    /* approximate-path payoffs, integers in units 2^-unit    */
+  double y;          /* the sample value accumulated into the sums (undiscounted) */
+  uint32_t sat, pad; /* sat = 1 if a fixed-point value saturated              */
+} mlmc_sample;
+
+/* Chunking of the level kernels.  threads: CTA size (32..1024, multiple of 32);
+ * steps_per_thread: target fine path-steps per thread (>= 1); zero = default. */
+typedef struct {
+  int32_t threads;
+  int32_t steps_per_thread;
+} mlmc_tuning;
+
+/* One unit of work: samples [first_sample, first_sample + N) of one level. */
+typedef struct {
+  const mlmc_params *params;    /* host pointer, copied at plan creation         */
+  int32_t level;                /* l in [0, 20]: 2^l fine steps of size T 2^-l   */
+  int32_t variant;              /* mlmc_variant                                  */
+  uint64_t first_sample;
+  uint64_t N;
+  int32_t stream;               /* Philox stream id 0..255, or -1 for the default
+                                   (1 for APPROX variants, 0 otherwise)          */
+  int32_t pad;
+} mlmc_work;
+
+typedef struct mlmc_plan mlmc_plan;
+
+/* ---- single level (Sec. 2.1 / 2.2 level estimator) ----------------------
+ * Simulates samples [first_sample, first_sample + N) of `level` with variant v
+ * and writes their sums to *out (host).  Blocks until the result is on the host.
+ * Sample s, fine step i draws J = word (w mod 4) of Philox4x32-10 with key
+ * (seed_lo, seed_hi) and counter (q_lo, q_hi, level | stream << 8, request_id),
+ * w = s 2^level + i, q = w div 4.  N = 0 gives zero sums.
+ * Errors: MLMC_EINVAL (bad level/variant/params/formats), MLMC_EOVERFLOW (a
+ * constant outside its format), MLMC_ECUDA, MLMC_ENOMEM. */
+mlmc_status mlmc_level(int level, uint64_t N, const mlmc_params *p, mlmc_variant v,
+                       uint64_t seed, uint64_t first_sample, mlmc_sums *out);
+
+/* As mlmc_level, with an explicit Philox stream (-1 = default), and also writes
+ * every sample to d_samples (device array of N mlmc_sample, caller-owned). */
+mlmc_status mlmc_level_dump(int level, uint64_t N, const mlmc_params *p, mlmc_variant v,
+                            uint64_t seed, uint64_t first_sample, int32_t stream,
+                            mlmc_sample *d_samples, mlmc_sums *out);
+
+/* ---- batched work lists ---------------------------------------------------
+ * A plan holds a device-resident work list; launching it enqueues one level
+ * kernel per kernel configuration (concurrently, on forked streams) and a
+ * finalize kernel, all on `stream`, with no host synchronisation and no host
+ * <-> device copy.  Results stay on the device until mlmc_plan_results.
+ * Work items are simulated in order of decreasing cost per CTA.
+ * Errors as mlmc_level; a plan with n_work = 0 is MLMC_EINVAL. */
+mlmc_status mlmc_plan_create(mlmc_plan **plan, const mlmc_work *work, int n_work,
+                             uint64_t seed, const mlmc_tuning *tuning);
+mlmc_status mlmc_plan_launch(mlmc_plan *plan, void *stream);
+/* Synchronises with the last launch and copies one mlmc_sums per work item
+ * (host array of n_work).  seconds = device time of the last launch.
+ * MLMC_ENOTREADY if the plan was never launched. */
+mlmc_status mlmc_plan_results(mlmc_plan *plan, mlmc_sums *out);
+/* Number of level-kernel launches and CTAs one launch of the plan issues, the
+ * fine path-steps it simulates (sum of N 2^level), and the bytes the plan
+ * copies host->device at creation and device->host per mlmc_plan_results.
+ * Any output pointer may be NULL. */
+mlmc_status mlmc_plan_info(const mlmc_plan *plan, int *kernels, uint64_t *ctas,
+                           uint64_t *path_steps, uint64_t *h2d_bytes, uint64_t *d2h_bytes);
+/* Device time (ms, CUDA events on the kernel's own stream) of level kernel k of
+ * the last launch, and its family (0 exact FP32, 1 exact FP64, 2 approximate
+ * fixed, 3 approximate binary16, 4 approximate bfloat16, 5/6/7 correction with
+ * fixed / binary16 / bfloat16).  Waits for that kernel.  MLMC_ENOTREADY before
+ * the first launch, MLMC_EINVAL for k out of range. */
+mlmc_status mlmc_plan_kernel_time(const mlmc_plan *plan, int k, int *family, double *ms);
+void mlmc_plan_destroy(mlmc_plan *plan);
+
+/* Host-buffer convenience: create, launch on `stream`, read results, destroy. */
+mlmc_status mlmc_run(const mlmc_work *work, int n_work, uint64_t seed,
+                     const mlmc_tuning *tuning, mlmc_sums *out, void *stream);
+
+/* ---- adaptive MLMC (Sec. 2.1-2.2 sample allocation, on-line phase of Sec. 6) ----
+ * Estimates E[P] to root-mean-square error eps with the adaptive algorithm of
+ * Giles (2008): variance target eps^2/2, bias target eps/sqrt(2), weak order 1,
+ * L from 2 up to max_level, 10^4 initial samples per level and estimator,
+ * sample counts N = ceil(lambda sqrt(V/C)) with lambda = (eps^2/2)^-1 sum sqrt(V C)
+ * over every (level, estimator) term.  mode: 0 plain FP64, 1 plain FP32,
+ * 2 nested fixed point, 3 nested binary16, 4 nested bfloat16.  The cost model
+ * is C = 2^l c_kind with c_kind from mlmc_cost_model (deterministic).
+ * Outputs (host): *price, *stderr_out, *L; N_l[l * 2 + k] = samples of
+ * estimator k on level l (k = 0: plain or approximate, k = 1: correction), for
+ * l <= *L (caller array of 2 * cap_levels).  Errors as mlmc_level, MLMC_EINVAL
+ * if cap_levels <= max_level. */
+mlmc_status mlmc_estimate(double eps, const mlmc_params *p, int mode, uint64_t seed,
+                          int max_level, double *price, double *stderr_out, int *L,
+                          uint64_t *N_l, int cap_levels);
+
+/* Cost per fine path-step of each estimator kind used by mlmc_estimate
+ * (relative units; defaults: exact FP32 1.0, exact FP64 8.0, approximate 0.5,
+ * correction 1.5).  kind: 0 exact FP64, 1 exact FP32, 2 approximate, 3 correction.
+ * Setting a value <= 0 restores the default.  Host only; no GPU needed. */
+mlmc_status mlmc_cost_model(int kind, double cost_per_step);
+
+/* ---- host helpers (no GPU needed) ---------------------------------------- */
+/* The default fixed-point schedule for a level (used when params->formats is NULL).
+ * Fractional bits f = {12, 16+l, 14+l, 12+l, 12+l, 12+l, 14+l} clamped to [10, 24]
+ * (one more bit per level, Sec. 6.3).  Integer bits e are the smallest with
+ * |x| < 2^e (and e + f >= 1) for these bounds, h = T 2^-l:
+ *   Z~ 8;  con1 max(|r| 2h, sigma^2 h / 2);  con2 sigma sqrt(h);
+ *   mul1 M = max(16 sigma sqrt(h), 128 sigma^2 h);  sum1 |r| 2h + M;
+ *   S max(S0 exp(|r| T + 6 sigma sqrt(T)), K);  mul2 e_S + e_sum1. */
+mlmc_status mlmc_default_format(const mlmc_params *p, int level, mlmc_format *out);
+
+/* Approximate-Normal table built on the GPU (for parity testing): writes the
+ * value of every index k < 2^(d-1) as doubles (host array of 2^(d-1)).
+ * rep: 0 fp64, 1 fp32, 2 fp16, 3 bf16, 4 fixed with fZ fractional bits.
+ * method 3 values are the a + b k evaluations the kernels use. */
+mlmc_status mlmc_icdf_table(int method, int d, int rep, int fZ, double *out);
+
+/* Philox4x32-10 words computed on the GPU for n counters (for parity testing):
+ * ctr is a host array of 4n words, out a host array of 4n words. */
+mlmc_status mlmc_philox(const uint32_t *ctr, uint64_t n, uint64_t seed, uint32_t *out);
+
+/* Human-readable message of a status (static string). */
+const char *mlmc_strerror(mlmc_status s);
+
+/* Library version string (static). */
+const char *mlmc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MLMC_GB300_H */

@@ -1,0 +1,972 @@
+// Host side of the C ABI declared in include/mlmc.h: device context and table
+// cache, work-item planning (chunking, per-level constants and fixed-point
+// formats), plan launch on forked streams, the deterministic finalize kernel,
+// and the adaptive MLMC driver (Sec. 2.1-2.2 sample allocation).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "item.h"
+#include "kernels.h"
+#include "mlmc.h"
+#include "tables.h"
+
+using namespace mlmc;
+
+// The Python binding mirrors these layouts.
+static_assert(sizeof(mlmc_params) == 72, "mlmc_params layout");
+static_assert(sizeof(mlmc_sums) == 72, "mlmc_sums layout");
+static_assert(sizeof(mlmc_work) == 40, "mlmc_work layout");
+static_assert(sizeof(mlmc_sample) == 80, "mlmc_sample layout");
+static_assert(sizeof(mlmc_format) == 14, "mlmc_format layout");
+
+// ---------------------------------------------------------------------------
+// plan object (opaque in the C ABI)
+// ---------------------------------------------------------------------------
+struct LaunchRec {
+  int family;               // 0..7, see launch_family_of
+  int scheme, pc;
+  uint32_t chunk0, n_chunks;
+  int item_off, n_items;
+  size_t smem;
+};
+
+struct mlmc_plan {
+  int n_work = 0;
+  int threads = 128;
+  std::vector<ItemDesc> items;       // launch sub-arrays first, zero-chunk items last
+  std::vector<LaunchRec> launches;
+  std::vector<double> disc;          // per work item
+  std::vector<int> unit, exact_int;
+  std::vector<uint64_t> N;
+  uint32_t total_chunks = 0;
+  uint64_t path_steps = 0;
+  RoundKeys rk{};
+  ItemDesc *d_items = nullptr;
+  Partial *d_partials = nullptr;
+  DevSums *d_out = nullptr;
+  std::vector<cudaStream_t> aux;
+  std::vector<cudaEvent_t> join;
+  std::vector<cudaEvent_t> kstart, kstop;   // around each level kernel, on its stream
+  cudaEvent_t fork = nullptr, t0 = nullptr, t1 = nullptr;
+  cudaStream_t last_stream = nullptr;
+  bool launched = false;
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// device context and table cache
+// ---------------------------------------------------------------------------
+struct Ctx {
+  bool inited = false;
+  int device = -1;
+  int num_sms = 0;
+  cudaStream_t st = nullptr;
+  std::map<int, std::vector<double>> m1_host;               // d -> Method-1 table (FP64)
+  std::map<int, double *> m1_dev;                           // d -> device FP64 table
+  std::map<std::tuple<int, int, int, int>, void *> tables;  // (method, d, rep, fZ) -> device table
+};
+Ctx g;
+
+double g_cost[4] = {8.0, 1.0, 0.5, 1.5};
+const double g_cost_default[4] = {8.0, 1.0, 0.5, 1.5};
+
+#define CK(call)                                      \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return MLMC_ECUDA;         \
+  } while (0)
+
+mlmc_status ensure_ctx() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MLMC_ECUDA;
+  if (g.inited && g.device == dev) return MLMC_OK;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) return MLMC_ECUDA;
+  if (g.inited && g.device != dev) {
+    // a different device became current: start a fresh cache for it
+    g.m1_host.clear();
+    g.m1_dev.clear();
+    g.tables.clear();
+  }
+  CK(cudaDeviceGetAttribute(&g.num_sms, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaStreamCreateWithFlags(&g.st, cudaStreamNonBlocking));
+  g.device = dev;
+  g.inited = true;
+  return MLMC_OK;
+}
+
+mlmc_status m1_table(int d, double **dev, const std::vector<double> **host) {
+  auto it = g.m1_dev.find(d);
+  if (it == g.m1_dev.end()) {
+    const int n = 1 << (d - 1);
+    double *p = nullptr;
+    CK(cudaMalloc(&p, sizeof(double) * n));
+    CK(launch_m1_table(d, p, g.st));
+    std::vector<double> h(n);
+    CK(cudaMemcpyAsync(h.data(), p, sizeof(double) * n, cudaMemcpyDeviceToHost, g.st));
+    CK(cudaStreamSynchronize(g.st));
+    g.m1_dev[d] = p;
+    g.m1_host[d] = std::move(h);
+    it = g.m1_dev.find(d);
+  }
+  *dev = it->second;
+  *host = &g.m1_host[d];
+  return MLMC_OK;
+}
+
+// Method 3 (Sec. 3.3): least-squares line a + b k through (k, Z_k) on each
+// dyadic index class {0,1}, {2,3}, {4..7}, ..., {2^(d-2) .. 2^(d-1)-1}.
+void m3_fit(const std::vector<double> &Z, int d, M3Coef &c) {
+  std::memset(&c, 0, sizeof c);
+  for (int cls = 0; cls < d - 1; ++cls) {
+    const int lo = cls == 0 ? 0 : (1 << cls);
+    const int hi = cls == 0 ? 1 : (1 << (cls + 1)) - 1;
+    const int n = hi - lo + 1;
+    double kbar = 0.0, zbar = 0.0;
+    for (int k = lo; k <= hi; ++k) { kbar += k; zbar += Z[k]; }
+    kbar /= n;
+    zbar /= n;
+    double sxx = 0.0, sxy = 0.0;
+    for (int k = lo; k <= hi; ++k) {
+      sxx += (k - kbar) * (k - kbar);
+      sxy += (k - kbar) * (Z[k] - zbar);
+    }
+    const double b = sxy / sxx;
+    const double a = zbar - b * kbar;
+    c.a[cls] = (float)a;
+    c.b[cls] = (float)b;
+    c.A[cls] = (int64_t)std::floor(std::ldexp(a, M3_FRAC) + 0.5);
+    c.B[cls] = (int64_t)std::floor(std::ldexp(b, M3_FRAC) + 0.5);
+  }
+}
+
+mlmc_status get_table(int method, int d, int rep, int fZ, const void **out) {
+  if (rep != REP_FIXED) fZ = 0;
+  auto key = std::make_tuple(method, d, rep, fZ);
+  auto it = g.tables.find(key);
+  if (it != g.tables.end()) { *out = it->second; return MLMC_OK; }
+  double *z64 = nullptr;
+  const std::vector<double> *zh = nullptr;
+  mlmc_status s = m1_table(d, &z64, &zh);
+  if (s != MLMC_OK) return s;
+  void *p = nullptr;
+  const int n = 1 << (d - 1);
+  if (method == 1) {
+    if (rep == REP_FP64) {
+      p = z64;
+    } else {
+      const size_t es = (rep == REP_FP16 || rep == REP_BF16) ? 2 : 4;
+      CK(cudaMalloc(&p, es * n));
+      CK(launch_m1_convert(z64, n, rep, fZ, p, g.st));
+      CK(cudaStreamSynchronize(g.st));
+    }
+  } else {
+    M3Coef c;
+    m3_fit(*zh, d, c);
+    CK(cudaMalloc(&p, sizeof(M3Coef)));
+    CK(cudaMemcpy(p, &c, sizeof(M3Coef), cudaMemcpyHostToDevice));
+  }
+  g.tables[key] = p;
+  *out = p;
+  return MLMC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// parameters, formats and constants
+// ---------------------------------------------------------------------------
+enum { F_Z = 0, F_CON1 = 1, F_CON2 = 2, F_MUL1 = 3, F_SUM1 = 4, F_MUL2 = 5, F_S = 6 };
+
+bool params_ok(const mlmc_params *p) {
+  if (!p) return false;
+  if (!(std::isfinite(p->S0) && std::isfinite(p->K) && std::isfinite(p->r) && std::isfinite(p->sigma) &&
+        std::isfinite(p->T)))
+    return false;
+  if (!(p->S0 > 0.0) || p->K < 0.0 || p->sigma < 0.0 || !(p->T > 0.0)) return false;
+  if (p->payoff < 0 || p->payoff > 3 || p->scheme < 0 || p->scheme > 1) return false;
+  if (p->icdf_method != 1 && p->icdf_method != 3) return false;
+  if (p->icdf_bits < 2 || p->icdf_bits > 14) return false;
+  if (p->formats && p->n_formats < 0) return false;
+  return true;
+}
+
+int bitlen(double x, int f) {
+  if (x <= 0.0) return 1 - f;
+  return std::max((int)std::floor(std::log2(x)) + 1, 1 - f);
+}
+
+void default_format(const mlmc_params *p, int level, mlmc_format *out) {
+  const double r = p->r, sig = p->sigma, T = p->T, S0 = p->S0, K = p->K;
+  const double h = T / (double)(1LL << level);
+  int f[7] = {12, 16 + level, 14 + level, 12 + level, 12 + level, 12 + level, 14 + level};
+  for (int i = 0; i < 7; ++i) f[i] = std::min(24, std::max(10, f[i]));
+  const double mul1_bound = std::max(16.0 * sig * std::sqrt(h), 128.0 * sig * sig * h);
+  int e[7];
+  e[F_Z] = 3;
+  e[F_CON1] = bitlen(std::max(std::fabs(r) * 2.0 * h, 0.5 * sig * sig * h), f[F_CON1]);
+  e[F_CON2] = bitlen(sig * std::sqrt(h), f[F_CON2]);
+  e[F_MUL1] = bitlen(mul1_bound, f[F_MUL1]);
+  e[F_SUM1] = bitlen(std::fabs(r) * 2.0 * h + mul1_bound, f[F_SUM1]);
+  e[F_S] = bitlen(std::max(S0 * std::exp(std::fabs(r) * T + 6.0 * sig * std::sqrt(T)), K), f[F_S]);
+  e[F_MUL2] = e[F_S] + e[F_SUM1];
+  for (int i = 0; i < 7; ++i) { out->e[i] = (int8_t)e[i]; out->f[i] = (int8_t)f[i]; }
+}
+
+Requant make_rq(int from, int to) {
+  Requant q;
+  if (to >= from) { q.ls = to - from; q.rs = 0; q.radd = 0; }
+  else { q.ls = 0; q.rs = from - to; q.radd = (int64_t)1 << (q.rs - 1); }
+  return q;
+}
+
+// rd of a real constant to f fractional bits, within e integer bits.
+mlmc_status const_fixed(double x, int e, int f, int64_t *out) {
+  const double s = std::ldexp(x, f);
+  if (!(std::fabs(s) < 4503599627370496.0)) return MLMC_EOVERFLOW;
+  const double n = std::floor(s + 0.5);
+  if (std::fabs(n) > std::ldexp(1.0, e + f) - 1.0) return MLMC_EOVERFLOW;
+  *out = (int64_t)n;
+  return MLMC_OK;
+}
+
+// Ranges the int32 / int64 datapath of the level kernel can hold exactly.
+bool format_ok_gpu(const mlmc_format &F, bool milstein, int d) {
+  int e[7], f[7];
+  for (int i = 0; i < 7; ++i) { e[i] = F.e[i]; f[i] = F.f[i]; }
+  for (int i = 0; i < 7; ++i) {
+    if (f[i] < 0 || f[i] > 40) return false;
+    const int w = e[i] + f[i];
+    if (w < 1) return false;
+    if (i < F_MUL2 && w > 31) return false;
+    if (w > 62) return false;
+  }
+  if (f[F_Z] > 28) return false;  // Method-3 evaluation shifts by M3_FRAC - f_Z >= 2; 2 f_Z < 63
+  (void)d;
+  const int F1 = std::max(f[F_CON1], f[F_MUL1]);
+  const int F2 = std::max(f[F_S], f[F_MUL2]);
+  const int zc = e[F_Z] + 1 + f[F_Z];                       // coarse z: one more integer bit
+  if ((e[F_CON2] + f[F_CON2]) + zc > 62) return false;      // con2 * z
+  if (e[F_CON2] + e[F_Z] + 1 + f[F_MUL1] > 62) return false; // left re-quantisation of that product
+  if (e[F_CON1] + 1 + F1 > 60 || e[F_MUL1] + F1 > 60) return false;  // aligned sum1 terms (3 of them)
+  if (std::max(e[F_CON1] + 1, e[F_MUL1]) + 2 + f[F_SUM1] > 62) return false;
+  if (milstein && (e[F_CON1] + f[F_CON1]) + 2 * zc > 62) return false;  // con3 * (z^2 - m)
+  if ((e[F_S] + f[F_S]) + (e[F_SUM1] + f[F_SUM1]) > 62) return false;   // S * sum1
+  if (e[F_S] + e[F_SUM1] + f[F_MUL2] > 62) return false;
+  if (e[F_S] + F2 > 61 || e[F_MUL2] + F2 > 61) return false;           // aligned S + mul2
+  return true;
+}
+
+int family_of(int variant) {
+  // 0 exact f32, 1 exact f64, 2 approx fixed, 3 approx f16, 4 approx bf16, 5 corr fixed, 6 corr f16, 7 corr bf16
+  switch (variant) {
+    case MLMC_FP32_EXACT: return 0;
+    case MLMC_FP64_EXACT: return 1;
+    case MLMC_FIXED_APPROX: return 2;
+    case MLMC_FP16_APPROX: return 3;
+    case MLMC_BF16_APPROX: return 4;
+    case MLMC_NESTED_CORR_FIXED: return 5;
+    case MLMC_NESTED_CORR_FP16: return 6;
+    default: return 7;
+  }
+}
+int cost_kind_of(int variant) {
+  if (variant == MLMC_FP64_EXACT) return 0;
+  if (variant == MLMC_FP32_EXACT) return 1;
+  if (variant == MLMC_FIXED_APPROX || variant == MLMC_FP16_APPROX || variant == MLMC_BF16_APPROX) return 2;
+  return 3;
+}
+
+cudaError_t launch_by_family(int fam, int scheme, int pc, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                             const LaunchArgs &a) {
+  switch (fam) {
+    case 0: return launch_exact_f32(scheme, pc, grid, block, smem, st, a);
+    case 1: return launch_exact_f64(scheme, pc, grid, block, smem, st, a);
+    case 2: return launch_approx_fixed(scheme, pc, grid, block, smem, st, a);
+    case 3: return launch_approx_f16(scheme, pc, grid, block, smem, st, a);
+    case 4: return launch_approx_bf16(scheme, pc, grid, block, smem, st, a);
+    case 5: return launch_corr_fixed(scheme, pc, grid, block, smem, st, a);
+    case 6: return launch_corr_f16(scheme, pc, grid, block, smem, st, a);
+    default: return launch_corr_bf16(scheme, pc, grid, block, smem, st, a);
+  }
+}
+
+uint16_t half_bits(double x) { return __half_as_ushort(__double2half(x)); }
+uint16_t bf16_bits(double x) { return __bfloat16_as_ushort(__double2bfloat16(x)); }
+
+struct BuiltItem {
+  ItemDesc it;
+  int family, scheme, pc;
+  size_t smem;
+  double chunk_cost;
+};
+
+mlmc_status build_item(const mlmc_work &w, int out_index, int threads, int steps_per_thread, void *dump,
+                       BuiltItem &b, double &disc, int &unit, int &exact_int) {
+  const mlmc_params *p = w.params;
+  if (!params_ok(p)) return MLMC_EINVAL;
+  if (w.level < 0 || w.level > 20 || w.variant < 0 || w.variant > 7) return MLMC_EINVAL;
+  if (w.stream < -1 || w.stream > 255) return MLMC_EINVAL;
+  const int lev = w.level;
+  // word index s 2^l + i and the group index must stay below 2^62
+  if (w.N > (1ULL << 58) || w.first_sample > (1ULL << (60 - lev)) - w.N) return MLMC_EINVAL;
+  ItemDesc &it = b.it;
+  std::memset(&it, 0, sizeof it);
+  const int v = w.variant;
+  const bool approx = !(v == MLMC_FP32_EXACT || v == MLMC_FP64_EXACT);
+  const int stream = w.stream >= 0 ? w.stream
+                     : (v == MLMC_FIXED_APPROX || v == MLMC_FP16_APPROX || v == MLMC_BF16_APPROX ? 1 : 0);
+  it.first = w.first_sample;
+  it.N = w.N;
+  it.level = lev;
+  it.nlog = lev;
+  it.payoff = p->payoff;
+  it.scheme = p->scheme;
+  it.method = p->icdf_method;
+  it.d = p->icdf_bits;
+  it.ctr2 = (uint32_t)lev | ((uint32_t)stream << 8);
+  it.ctr3 = p->request_id;
+  it.out_index = (uint32_t)out_index;
+  it.dump = dump;
+  // chunking
+  const uint64_t spc = lev >= 2 ? 1 : (lev == 1 ? 2 : 4);
+  const uint64_t steps_per_group = std::max<uint64_t>(4, 1ULL << lev);
+  it.g0 = w.first_sample / spc;
+  it.g1 = w.N == 0 ? it.g0 : (w.first_sample + w.N + spc - 1) / spc;
+  const uint64_t groups = it.g1 - it.g0;
+  uint64_t G = std::max<uint64_t>(1, (uint64_t)steps_per_thread / steps_per_group);
+  const uint64_t min_ctas = 4ULL * (uint64_t)std::max(1, g.num_sms);
+  const uint64_t cap = std::max<uint64_t>(1, (groups + (uint64_t)threads * min_ctas - 1) / ((uint64_t)threads * min_ctas));
+  G = std::min(G, cap);
+  it.groups_per_thread = (uint32_t)G;
+  const uint64_t per_chunk = G * (uint64_t)threads;
+  const uint64_t nch = (groups + per_chunk - 1) / per_chunk;
+  if (nch > 0x7fffffffULL) return MLMC_EINVAL;
+  it.n_chunks = (uint32_t)nch;
+  b.chunk_cost = (double)per_chunk * (double)steps_per_group * g_cost[cost_kind_of(v)];
+  // exact-path constants (the same FP64 expressions as the fixed-point ones)
+  const double h = std::ldexp(p->T, -lev);
+  const double rh = p->r * h, rh2 = p->r * (2.0 * h), sqh = std::sqrt(h);
+  const double c2 = p->sigma * sqh, c3 = 0.5 * p->sigma * p->sigma * h;
+  it.c1d = rh; it.c2d = c2; it.c1cd = rh2; it.c3d = c3; it.S0d = p->S0; it.Kd = p->K;
+  it.c1f = (float)rh; it.c2f = (float)c2; it.c1cf = (float)rh2; it.c3f = (float)c3;
+  it.S0f = (float)p->S0; it.Kf = (float)p->K;
+  disc = std::exp(-p->r * p->T);
+  unit = 0;
+  exact_int = 0;
+  b.smem = 0;
+  if (approx) {
+    const bool fixed = (v == MLMC_FIXED_APPROX || v == MLMC_NESTED_CORR_FIXED);
+    const bool bf = (v == MLMC_BF16_APPROX || v == MLMC_NESTED_CORR_BF16);
+    const int rep = fixed ? REP_FIXED : (bf ? REP_BF16 : REP_FP16);
+    int fZ = 0;
+    if (fixed) {
+      mlmc_format F;
+      if (p->formats && lev < p->n_formats) F = p->formats[lev];
+      else if (p->formats) return MLMC_EINVAL;
+      else default_format(p, lev, &F);
+      if (!format_ok_gpu(F, p->scheme == MLMC_MILSTEIN, p->icdf_bits)) return MLMC_EINVAL;
+      int e[7], f[7];
+      for (int i = 0; i < 7; ++i) { e[i] = F.e[i]; f[i] = F.f[i]; }
+      fZ = f[F_Z];
+      FixedConsts &fx = it.fx;
+      int64_t con1, con1c, con2, con3, S0q, Kq;
+      mlmc_status s = MLMC_OK;
+      if ((s = const_fixed(rh, e[F_CON1], f[F_CON1], &con1)) != MLMC_OK) return s;
+      if ((s = const_fixed(rh2, e[F_CON1] + 1, f[F_CON1], &con1c)) != MLMC_OK) return s;
+      if ((s = const_fixed(c2, e[F_CON2], f[F_CON2], &con2)) != MLMC_OK) return s;
+      if ((s = const_fixed(c3, e[F_CON1], f[F_CON1], &con3)) != MLMC_OK) return s;
+      if ((s = const_fixed(p->S0, e[F_S], f[F_S], &S0q)) != MLMC_OK) return s;
+      if ((s = const_fixed(p->K, e[F_S], f[F_S], &Kq)) != MLMC_OK) return s;
+      const int F1 = std::max(f[F_CON1], f[F_MUL1]);
+      const int F2 = std::max(f[F_S], f[F_MUL2]);
+      fx.con1A = con1 * ((int64_t)1 << (F1 - f[F_CON1]));
+      fx.con1cA = con1c * ((int64_t)1 << (F1 - f[F_CON1]));
+      fx.con2 = (int32_t)con2;
+      fx.con3 = (int32_t)con3;
+      fx.S0 = S0q;
+      fx.K = Kq;
+      for (int i = 0; i < 7; ++i) fx.lim[i] = ((int64_t)1 << (e[i] + f[i])) - 1;
+      fx.q_mul1 = make_rq(f[F_CON2] + f[F_Z], f[F_MUL1]);
+      fx.q_mul3 = make_rq(f[F_CON1] + 2 * f[F_Z], f[F_MUL1]);
+      fx.sh_mul1_F1 = F1 - f[F_MUL1];
+      fx.q_sum1 = make_rq(F1, f[F_SUM1]);
+      fx.q_mul2 = make_rq(f[F_S] + f[F_SUM1], f[F_MUL2]);
+      fx.sh_S_F2 = F2 - f[F_S];
+      fx.sh_mul2_F2 = F2 - f[F_MUL2];
+      fx.q_S = make_rq(F2, f[F_S]);
+      fx.fZ2 = 2 * f[F_Z];
+      fx.fS = f[F_S];
+      // the table must fit Z's format
+      double *z64;
+      const std::vector<double> *zh;
+      if ((s = m1_table(p->icdf_bits, &z64, &zh)) != MLMC_OK) return s;
+      const double zmax = std::fabs((*zh)[0]);
+      if (std::floor(std::ldexp(zmax, fZ) + 0.5) > std::ldexp(1.0, e[F_Z] + fZ) - 1.0) return MLMC_EOVERFLOW;
+      unit = f[F_S] + (p->payoff == MLMC_ASIAN ? lev + 1 : 0);
+    } else {
+      uint16_t (*cv)(double) = bf ? bf16_bits : half_bits;
+      it.h_c1 = cv(rh);
+      it.h_c1c = cv(rh2);
+      it.h_c2 = cv(c2);
+      it.h_c3 = cv(c3);
+      it.h_S0 = cv(p->S0);
+      unit = 24;
+    }
+    const void *tab = nullptr;
+    mlmc_status s = get_table(p->icdf_method, p->icdf_bits, rep, fZ, &tab);
+    if (s != MLMC_OK) return s;
+    it.ztab = tab;
+    b.smem = p->icdf_method == 1 ? (size_t)(1 << (p->icdf_bits - 1)) * (fixed ? 4 : 2) : sizeof(M3Coef);
+    exact_int = (v == MLMC_FIXED_APPROX || v == MLMC_FP16_APPROX || v == MLMC_BF16_APPROX) ? 1 : 0;
+  }
+  it.unit = unit;
+  it.unit_scale = std::ldexp(1.0f, -unit);
+  b.family = family_of(v);
+  b.scheme = p->scheme;
+  b.pc = p->payoff == MLMC_ASIAN ? PC_ASIAN : (p->payoff == MLMC_LOOKBACK ? PC_LOOKBACK : PC_TERMINAL);
+  return MLMC_OK;
+}
+
+void make_round_keys(uint64_t seed, RoundKeys &rk) {
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    rk.k[2 * r] = k0;
+    rk.k[2 * r + 1] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+// Deterministic sum of each item's chunk partials (fixed lane assignment and
+// tree order, so repeated launches give bit-identical results).
+__global__ void finalize_kernel(const ItemDesc *items, int n_items, const Partial *partials, DevSums *out) {
+  const int i = blockIdx.x;
+  if (i >= n_items) return;
+  const ItemDesc &it = items[i];
+  int64_t isum = 0;
+  uint64_t lo = 0, hi = 0, ns = 0;
+  double ds = 0.0, dq = 0.0;
+  for (uint32_t c = threadIdx.x; c < it.n_chunks; c += 32) {
+    const Partial &p = partials[it.chunk_begin + c];
+    isum += p.isum;
+    const uint64_t nlo = lo + p.isum2_lo;
+    hi += p.isum2_hi + (uint64_t)(nlo < lo);
+    lo = nlo;
+    ds += p.dsum;
+    dq += p.dsum2;
+    ns += p.nsat;
+  }
+  for (int m = 16; m >= 1; m >>= 1) {
+    isum += __shfl_xor_sync(0xffffffffu, (long long)isum, m);
+    const uint64_t olo = __shfl_xor_sync(0xffffffffu, (unsigned long long)lo, m);
+    const uint64_t ohi = __shfl_xor_sync(0xffffffffu, (unsigned long long)hi, m);
+    const uint64_t nlo = lo + olo;
+    hi += ohi + (uint64_t)(nlo < lo);
+    lo = nlo;
+    ds += __shfl_xor_sync(0xffffffffu, ds, m);
+    dq += __shfl_xor_sync(0xffffffffu, dq, m);
+    ns += __shfl_xor_sync(0xffffffffu, (unsigned long long)ns, m);
+  }
+  if (threadIdx.x == 0) {
+    DevSums r;
+    r.dsum = ds; r.dsum2 = dq; r.isum = isum; r.isum2_lo = lo; r.isum2_hi = hi; r.nsat = ns;
+    out[it.out_index] = r;
+  }
+}
+
+void free_plan_device(mlmc_plan *pl) {
+  if (pl->d_items) cudaFree(pl->d_items);
+  if (pl->d_partials) cudaFree(pl->d_partials);
+  if (pl->d_out) cudaFree(pl->d_out);
+  for (auto s : pl->aux) cudaStreamDestroy(s);
+  for (auto e : pl->join) cudaEventDestroy(e);
+  for (auto e : pl->kstart) cudaEventDestroy(e);
+  for (auto e : pl->kstop) cudaEventDestroy(e);
+  pl->kstart.clear(); pl->kstop.clear();
+  if (pl->fork) cudaEventDestroy(pl->fork);
+  if (pl->t0) cudaEventDestroy(pl->t0);
+  if (pl->t1) cudaEventDestroy(pl->t1);
+  pl->d_items = nullptr; pl->d_partials = nullptr; pl->d_out = nullptr;
+  pl->aux.clear(); pl->join.clear();
+  pl->fork = pl->t0 = pl->t1 = nullptr;
+}
+
+mlmc_status plan_create_impl(mlmc_plan **out, const mlmc_work *work, int n_work, uint64_t seed,
+                             const mlmc_tuning *tuning, void *const *dumps) {
+  if (!out || !work || n_work <= 0) return MLMC_EINVAL;
+  mlmc_status s = ensure_ctx();
+  if (s != MLMC_OK) return s;
+  int threads = 128, spt = 256;
+  if (tuning) {
+    if (tuning->threads) threads = tuning->threads;
+    if (tuning->steps_per_thread) spt = tuning->steps_per_thread;
+  }
+  if (threads < 32 || threads > 256 || threads % 32 || spt < 1) return MLMC_EINVAL;
+  mlmc_plan *pl = new (std::nothrow) mlmc_plan;
+  if (!pl) return MLMC_ENOMEM;
+  pl->n_work = n_work;
+  pl->threads = threads;
+  pl->disc.resize(n_work);
+  pl->unit.resize(n_work);
+  pl->exact_int.resize(n_work);
+  pl->N.resize(n_work);
+  std::vector<BuiltItem> built(n_work);
+  for (int i = 0; i < n_work; ++i) {
+    s = build_item(work[i], i, threads, spt, dumps ? dumps[i] : nullptr, built[i], pl->disc[i], pl->unit[i],
+                   pl->exact_int[i]);
+    if (s != MLMC_OK) { delete pl; return s; }
+    pl->N[i] = work[i].N;
+    pl->path_steps += work[i].N << work[i].level;
+  }
+  // group by kernel configuration; within a launch, most expensive chunks first
+  std::map<std::tuple<int, int, int>, std::vector<int>> groups;
+  std::vector<int> empty;
+  for (int i = 0; i < n_work; ++i) {
+    if (built[i].it.n_chunks == 0) { empty.push_back(i); continue; }
+    groups[std::make_tuple(built[i].family, built[i].scheme, built[i].pc)].push_back(i);
+  }
+  std::vector<std::pair<double, std::vector<int>>> order;
+  for (auto &kv : groups) {
+    auto &v = kv.second;
+    std::stable_sort(v.begin(), v.end(), [&](int a, int b) { return built[a].chunk_cost > built[b].chunk_cost; });
+    double tot = 0.0;
+    for (int i : v) tot += built[i].chunk_cost * built[i].it.n_chunks;
+    order.push_back({tot, v});
+  }
+  std::stable_sort(order.begin(), order.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+  uint32_t chunk = 0;
+  for (auto &o : order) {
+    LaunchRec L;
+    const BuiltItem &b0 = built[o.second[0]];
+    L.family = b0.family; L.scheme = b0.scheme; L.pc = b0.pc;
+    L.chunk0 = chunk;
+    L.item_off = (int)pl->items.size();
+    L.n_items = (int)o.second.size();
+    L.smem = 0;
+    for (int i : o.second) {
+      ItemDesc it = built[i].it;
+      it.chunk_begin = chunk;
+      chunk += it.n_chunks;
+      L.smem = std::max(L.smem, built[i].smem);
+      pl->items.push_back(it);
+    }
+    L.n_chunks = chunk - L.chunk0;
+    pl->launches.push_back(L);
+  }
+  for (int i : empty) {
+    ItemDesc it = built[i].it;
+    it.chunk_begin = chunk;
+    pl->items.push_back(it);
+  }
+  pl->total_chunks = chunk;
+  make_round_keys(seed, pl->rk);
+  const size_t ni = pl->items.size();
+  if (cudaMalloc(&pl->d_items, sizeof(ItemDesc) * ni) != cudaSuccess ||
+      cudaMalloc(&pl->d_partials, sizeof(Partial) * std::max<uint32_t>(1, chunk)) != cudaSuccess ||
+      cudaMalloc(&pl->d_out, sizeof(DevSums) * n_work) != cudaSuccess) {
+    free_plan_device(pl);
+    delete pl;
+    return MLMC_ENOMEM;
+  }
+  if (cudaMemcpy(pl->d_items, pl->items.data(), sizeof(ItemDesc) * ni, cudaMemcpyHostToDevice) != cudaSuccess) {
+    free_plan_device(pl);
+    delete pl;
+    return MLMC_ECUDA;
+  }
+  bool ok = cudaEventCreate(&pl->t0) == cudaSuccess && cudaEventCreate(&pl->t1) == cudaSuccess &&
+            cudaEventCreateWithFlags(&pl->fork, cudaEventDisableTiming) == cudaSuccess;
+  if (ok && pl->launches.size() > 1) {
+    for (size_t i = 0; i < pl->launches.size() && ok; ++i) {
+      cudaStream_t st;
+      cudaEvent_t ev;
+      ok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+      if (ok) { pl->aux.push_back(st); pl->join.push_back(ev); }
+    }
+  }
+  for (size_t i = 0; i < pl->launches.size() && ok; ++i) {
+    cudaEvent_t a, b;
+    ok = cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess;
+    if (ok) { pl->kstart.push_back(a); pl->kstop.push_back(b); }
+  }
+  if (!ok) { free_plan_device(pl); delete pl; return MLMC_ECUDA; }
+  *out = pl;
+  return MLMC_OK;
+}
+
+mlmc_status plan_launch_impl(mlmc_plan *pl, cudaStream_t st) {
+  CK(cudaEventRecord(pl->t0, st));
+  const bool fork = pl->launches.size() > 1;
+  if (fork) CK(cudaEventRecord(pl->fork, st));
+  for (size_t i = 0; i < pl->launches.size(); ++i) {
+    const LaunchRec &L = pl->launches[i];
+    cudaStream_t ls = st;
+    if (fork) {
+      ls = pl->aux[i];
+      CK(cudaStreamWaitEvent(ls, pl->fork, 0));
+    }
+    LaunchArgs a;
+    a.items = pl->d_items + L.item_off;
+    a.n_items = L.n_items;
+    a.chunk0 = L.chunk0;
+    a.partials = pl->d_partials;
+    a.rk = pl->rk;
+    CK(cudaEventRecord(pl->kstart[i], ls));
+    CK(launch_by_family(L.family, L.scheme, L.pc, dim3(L.n_chunks), dim3(pl->threads), L.smem, ls, a));
+    CK(cudaEventRecord(pl->kstop[i], ls));
+    if (fork) {
+      CK(cudaEventRecord(pl->join[i], ls));
+      CK(cudaStreamWaitEvent(st, pl->join[i], 0));
+    }
+  }
+  finalize_kernel<<<(unsigned)pl->items.size(), 32, 0, st>>>(pl->d_items, (int)pl->items.size(), pl->d_partials,
+                                                              pl->d_out);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(pl->t1, st));
+  pl->last_stream = st;
+  pl->launched = true;
+  return MLMC_OK;
+}
+
+double u128_to_double(uint64_t lo, uint64_t hi) {
+  const unsigned __int128 v = ((unsigned __int128)hi << 64) | lo;
+  return (double)v;
+}
+
+mlmc_status plan_results_impl(mlmc_plan *pl, mlmc_sums *out) {
+  if (!pl->launched) return MLMC_ENOTREADY;
+  CK(cudaEventSynchronize(pl->t1));
+  float ms = 0.0f;
+  CK(cudaEventElapsedTime(&ms, pl->t0, pl->t1));
+  std::vector<DevSums> h(pl->n_work);
+  CK(cudaMemcpy(h.data(), pl->d_out, sizeof(DevSums) * pl->n_work, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < pl->n_work; ++i) {
+    mlmc_sums &o = out[i];
+    std::memset(&o, 0, sizeof o);
+    const double disc = pl->disc[i];
+    o.n = pl->N[i];
+    o.seconds = ms * 1e-3;
+    o.saturations = h[i].nsat;
+    o.unit = pl->unit[i];
+    o.exact_int = pl->exact_int[i];
+    if (o.exact_int) {
+      o.isum = h[i].isum;
+      o.isum2_lo = h[i].isum2_lo;
+      o.isum2_hi = h[i].isum2_hi;
+      o.sum = disc * std::ldexp((double)h[i].isum, -o.unit);
+      o.sum2 = disc * disc * std::ldexp(u128_to_double(h[i].isum2_lo, h[i].isum2_hi), -2 * o.unit);
+    } else {
+      o.sum = disc * h[i].dsum;
+      o.sum2 = disc * disc * h[i].dsum2;
+    }
+  }
+  return MLMC_OK;
+}
+
+mlmc_status run_sync(const mlmc_work *work, int n_work, uint64_t seed, const mlmc_tuning *tuning,
+                     void *const *dumps, mlmc_sums *out, cudaStream_t st) {
+  mlmc_plan *pl = nullptr;
+  mlmc_status s = plan_create_impl(&pl, work, n_work, seed, tuning, dumps);
+  if (s != MLMC_OK) return s;
+  s = plan_launch_impl(pl, st);
+  if (s == MLMC_OK) s = plan_results_impl(pl, out);
+  free_plan_device(pl);
+  delete pl;
+  return s;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+mlmc_status mlmc_level(int level, uint64_t N, const mlmc_params *p, mlmc_variant v, uint64_t seed,
+                       uint64_t first_sample, mlmc_sums *out) {
+  if (!out) return MLMC_EINVAL;
+  mlmc_work w;
+  std::memset(&w, 0, sizeof w);
+  w.params = p; w.level = level; w.variant = (int32_t)v; w.first_sample = first_sample; w.N = N; w.stream = -1;
+  mlmc_status s = ensure_ctx();
+  if (s != MLMC_OK) return s;
+  return run_sync(&w, 1, seed, nullptr, nullptr, out, g.st);
+}
+
+mlmc_status mlmc_level_dump(int level, uint64_t N, const mlmc_params *p, mlmc_variant v, uint64_t seed,
+                            uint64_t first_sample, int32_t stream, mlmc_sample *d_samples, mlmc_sums *out) {
+  if (!out || (N > 0 && !d_samples)) return MLMC_EINVAL;
+  mlmc_work w;
+  std::memset(&w, 0, sizeof w);
+  w.params = p; w.level = level; w.variant = (int32_t)v; w.first_sample = first_sample; w.N = N;
+  w.stream = stream;
+  mlmc_status s = ensure_ctx();
+  if (s != MLMC_OK) return s;
+  void *dumps[1] = {d_samples};
+  return run_sync(&w, 1, seed, nullptr, dumps, out, g.st);
+}
+
+mlmc_status mlmc_plan_create(mlmc_plan **plan, const mlmc_work *work, int n_work, uint64_t seed,
+                             const mlmc_tuning *tuning) {
+  return plan_create_impl(plan, work, n_work, seed, tuning, nullptr);
+}
+
+mlmc_status mlmc_plan_launch(mlmc_plan *plan, void *stream) {
+  if (!plan) return MLMC_EINVAL;
+  return plan_launch_impl(plan, (cudaStream_t)stream);
+}
+
+mlmc_status mlmc_plan_results(mlmc_plan *plan, mlmc_sums *out) {
+  if (!plan || !out) return MLMC_EINVAL;
+  return plan_results_impl(plan, out);
+}
+
+mlmc_status mlmc_plan_info(const mlmc_plan *plan, int *kernels, uint64_t *ctas, uint64_t *path_steps,
+                           uint64_t *h2d_bytes, uint64_t *d2h_bytes) {
+  if (!plan) return MLMC_EINVAL;
+  if (kernels) *kernels = (int)plan->launches.size();
+  if (ctas) *ctas = plan->total_chunks;
+  if (path_steps) *path_steps = plan->path_steps;
+  if (h2d_bytes) *h2d_bytes = sizeof(ItemDesc) * plan->items.size();
+  if (d2h_bytes) *d2h_bytes = sizeof(DevSums) * (uint64_t)plan->n_work;
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_plan_kernel_time(const mlmc_plan *plan, int k, int *family, double *ms) {
+  if (!plan || k < 0 || k >= (int)plan->launches.size()) return MLMC_EINVAL;
+  if (!plan->launched) return MLMC_ENOTREADY;
+  if (family) *family = plan->launches[k].family;
+  if (ms) {
+    CK(cudaEventSynchronize(plan->kstop[k]));
+    float t = 0.0f;
+    CK(cudaEventElapsedTime(&t, plan->kstart[k], plan->kstop[k]));
+    *ms = t;
+  }
+  return MLMC_OK;
+}
+
+void mlmc_plan_destroy(mlmc_plan *plan) {
+  if (!plan) return;
+  if (plan->launched) cudaEventSynchronize(plan->t1);
+  free_plan_device(plan);
+  delete plan;
+}
+
+mlmc_status mlmc_run(const mlmc_work *work, int n_work, uint64_t seed, const mlmc_tuning *tuning,
+                     mlmc_sums *out, void *stream) {
+  if (!out) return MLMC_EINVAL;
+  return run_sync(work, n_work, seed, tuning, nullptr, out, (cudaStream_t)stream);
+}
+
+mlmc_status mlmc_cost_model(int kind, double cost_per_step) {
+  if (kind < 0 || kind > 3 || !std::isfinite(cost_per_step)) return MLMC_EINVAL;
+  g_cost[kind] = cost_per_step > 0.0 ? cost_per_step : g_cost_default[kind];
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_default_format(const mlmc_params *p, int level, mlmc_format *out) {
+  if (!params_ok(p) || !out || level < 0 || level > 20) return MLMC_EINVAL;
+  default_format(p, level, out);
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_icdf_table(int method, int d, int rep, int fZ, double *out) {
+  if ((method != 1 && method != 3) || d < 2 || d > 14 || rep < 0 || rep > 4 || !out) return MLMC_EINVAL;
+  if (rep == REP_FIXED && (fZ < 0 || fZ > 28)) return MLMC_EINVAL;
+  if (method == 3 && rep == REP_FP64) return MLMC_EINVAL;
+  mlmc_status s = ensure_ctx();
+  if (s != MLMC_OK) return s;
+  const void *tab = nullptr;
+  if ((s = get_table(method, d, rep, fZ, &tab)) != MLMC_OK) return s;
+  const int n = 1 << (d - 1);
+  double *dv = nullptr;
+  CK(cudaMalloc(&dv, sizeof(double) * n));
+  cudaError_t e = launch_table_values(method, d, rep, fZ, tab, dv, g.st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, dv, sizeof(double) * n, cudaMemcpyDeviceToHost, g.st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g.st);
+  cudaFree(dv);
+  return e == cudaSuccess ? MLMC_OK : MLMC_ECUDA;
+}
+
+mlmc_status mlmc_philox(const uint32_t *ctr, uint64_t n, uint64_t seed, uint32_t *out) {
+  if ((!ctr || !out) && n) return MLMC_EINVAL;
+  if (n == 0) return MLMC_OK;
+  mlmc_status s = ensure_ctx();
+  if (s != MLMC_OK) return s;
+  RoundKeys rk;
+  make_round_keys(seed, rk);
+  uint4 *dc = nullptr, *dout = nullptr;
+  if (cudaMalloc(&dc, 16 * n) != cudaSuccess) return MLMC_ENOMEM;
+  if (cudaMalloc(&dout, 16 * n) != cudaSuccess) { cudaFree(dc); return MLMC_ENOMEM; }
+  cudaError_t e = cudaMemcpyAsync(dc, ctr, 16 * n, cudaMemcpyHostToDevice, g.st);
+  if (e == cudaSuccess) e = launch_philox(dc, n, rk, dout, g.st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, 16 * n, cudaMemcpyDeviceToHost, g.st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g.st);
+  cudaFree(dc);
+  cudaFree(dout);
+  return e == cudaSuccess ? MLMC_OK : MLMC_ECUDA;
+}
+
+const char *mlmc_strerror(mlmc_status s) {
+  switch (s) {
+    case MLMC_OK: return "ok";
+    case MLMC_EINVAL: return "invalid argument";
+    case MLMC_ENOMEM: return "out of memory";
+    case MLMC_ECUDA: return "CUDA runtime error or no CUDA device";
+    case MLMC_ETIMEOUT: return "timed out";
+    case MLMC_EOVERFLOW: return "constant outside its fixed-point format";
+    case MLMC_ENOTREADY: return "results requested before launch";
+    default: return "unknown status";
+  }
+}
+
+const char *mlmc_version(void) { return "mlmc-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// adaptive MLMC (Giles 2008 loop; nested variant of Sec. 2.2)
+// ---------------------------------------------------------------------------
+namespace {
+
+struct EstPlan {
+  int n;          // estimators per level
+  int variant[2];
+};
+
+bool est_plan(int mode, EstPlan &e) {
+  switch (mode) {
+    case 0: e = {1, {MLMC_FP64_EXACT, 0}}; return true;
+    case 1: e = {1, {MLMC_FP32_EXACT, 0}}; return true;
+    case 2: e = {2, {MLMC_FIXED_APPROX, MLMC_NESTED_CORR_FIXED}}; return true;
+    case 3: e = {2, {MLMC_FP16_APPROX, MLMC_NESTED_CORR_FP16}}; return true;
+    case 4: e = {2, {MLMC_BF16_APPROX, MLMC_NESTED_CORR_BF16}}; return true;
+    default: return false;
+  }
+}
+
+// N_k = ceil(lambda sqrt(V_k / C_k)), lambda = sum_j sqrt(V_j C_j) / var_target (Sec. 2.1 / 2.2).
+void optimal_counts(const std::vector<double> &V, const std::vector<double> &C, double var_target,
+                    std::vector<uint64_t> &Nopt) {
+  double lam = 0.0;
+  for (size_t k = 0; k < V.size(); ++k) lam += std::sqrt(V[k] * C[k]);
+  lam /= var_target;
+  Nopt.resize(V.size());
+  for (size_t k = 0; k < V.size(); ++k) {
+    const double x = V[k] > 0.0 ? lam * std::sqrt(V[k] / C[k]) : 0.0;
+    Nopt[k] = (uint64_t)std::ceil(std::min(x, 1e18));
+  }
+}
+
+}  // namespace
+
+extern "C" mlmc_status mlmc_estimate(double eps, const mlmc_params *p, int mode, uint64_t seed, int max_level,
+                                     double *price, double *stderr_out, int *Lout, uint64_t *N_l,
+                                     int cap_levels) {
+  EstPlan ep;
+  if (!(eps > 0.0) || !std::isfinite(eps) || !params_ok(p) || !est_plan(mode, ep)) return MLMC_EINVAL;
+  if (max_level < 2 || max_level > 20 || cap_levels <= max_level || !price || !stderr_out || !Lout || !N_l)
+    return MLMC_EINVAL;
+  mlmc_status s = ensure_ctx();
+  if (s != MLMC_OK) return s;
+  const int ne = ep.n;
+  const double theta = 0.5, alpha = 1.0;
+  const double beta = p->scheme == MLMC_MILSTEIN ? 2.0 : 1.0;
+  const uint64_t N_init = 10000;
+  int L = 2;
+  std::vector<std::vector<uint64_t>> N(L + 1, std::vector<uint64_t>(ne, 0)), dN(L + 1, std::vector<uint64_t>(ne, N_init));
+  std::vector<std::vector<double>> S1(L + 1, std::vector<double>(ne, 0.0)), S2 = S1;
+  std::vector<std::vector<double>> Vext(L + 1, std::vector<double>(ne, 0.0));
+  std::vector<mlmc_work> work;
+  std::vector<mlmc_sums> res;
+  std::vector<std::pair<int, int>> idx;
+  auto level_var = [&](int l, int k) {
+    if (N[l][k] == 0) return Vext[l][k];
+    const double m = S1[l][k] / (double)N[l][k];
+    return std::max(S2[l][k] / (double)N[l][k] - m * m, 0.0);
+  };
+  auto update_dn = [&]() {
+    std::vector<double> V, C;
+    for (int l = 0; l <= L; ++l)
+      for (int k = 0; k < ne; ++k) {
+        V.push_back(std::max(level_var(l, k), 1e-300));
+        C.push_back(std::ldexp(g_cost[cost_kind_of(ep.variant[k])], l));
+      }
+    std::vector<uint64_t> Nopt;
+    optimal_counts(V, C, (1.0 - theta) * eps * eps, Nopt);
+    for (int l = 0; l <= L; ++l)
+      for (int k = 0; k < ne; ++k) {
+        const uint64_t want = Nopt[(size_t)l * ne + k];
+        dN[l][k] = want > N[l][k] ? want - N[l][k] : 0;
+      }
+  };
+  for (int iter = 0; iter < 1000; ++iter) {
+    bool any = true;
+    while (any) {
+      work.clear();
+      idx.clear();
+      for (int l = 0; l <= L; ++l)
+        for (int k = 0; k < ne; ++k)
+          if (dN[l][k] > 0) {
+            mlmc_work w;
+            std::memset(&w, 0, sizeof w);
+            w.params = p; w.level = l; w.variant = ep.variant[k]; w.first_sample = N[l][k]; w.N = dN[l][k];
+            w.stream = -1;
+            work.push_back(w);
+            idx.push_back({l, k});
+          }
+      if (work.empty()) break;
+      res.resize(work.size());
+      s = run_sync(work.data(), (int)work.size(), seed, nullptr, nullptr, res.data(), g.st);
+      if (s != MLMC_OK) return s;
+      for (size_t j = 0; j < work.size(); ++j) {
+        const int l = idx[j].first, k = idx[j].second;
+        S1[l][k] += res[j].sum;
+        S2[l][k] += res[j].sum2;
+        N[l][k] += work[j].N;
+      }
+      update_dn();
+      any = false;
+      for (int l = 0; l <= L; ++l)
+        for (int k = 0; k < ne; ++k) any |= dN[l][k] > 0;
+    }
+    // bias test on the last two levels (weak order alpha)
+    std::vector<double> means(L + 1, 0.0);
+    for (int l = 0; l <= L; ++l)
+      for (int k = 0; k < ne; ++k) means[l] += S1[l][k] / (double)N[l][k];
+    double rem = std::fabs(means[L]) / (std::pow(2.0, alpha) - 1.0);
+    rem = std::max(rem, std::fabs(means[L - 1]) / std::pow(2.0, alpha) / (std::pow(2.0, alpha) - 1.0));
+    if (rem <= std::sqrt(theta) * eps || L >= max_level) break;
+    L += 1;
+    N.push_back(std::vector<uint64_t>(ne, 0));
+    dN.push_back(std::vector<uint64_t>(ne, 0));
+    S1.push_back(std::vector<double>(ne, 0.0));
+    S2.push_back(std::vector<double>(ne, 0.0));
+    std::vector<double> ve(ne);
+    for (int k = 0; k < ne; ++k) ve[k] = std::max(level_var(L - 1, k), 1e-300) / std::pow(2.0, beta);
+    Vext.push_back(ve);
+    update_dn();
+  }
+  double pr = 0.0, var = 0.0;
+  for (int l = 0; l <= L; ++l)
+    for (int k = 0; k < ne; ++k) {
+      pr += S1[l][k] / (double)N[l][k];
+      var += level_var(l, k) / (double)N[l][k];
+    }
+  *price = pr;
+  *stderr_out = std::sqrt(var);
+  *Lout = L;
+  for (int l = 0; l < cap_levels; ++l)
+    for (int k = 0; k < 2; ++k) N_l[2 * l + k] = (l <= L && k < ne) ? N[l][k] : 0;
+  return MLMC_OK;
+}

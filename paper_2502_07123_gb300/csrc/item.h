@@ -1,0 +1,103 @@
+// Device work-item descriptor and reduction records of the level kernels.
+// Built on the host (api.cu) from the public mlmc_work / mlmc_params and
+// copied to device memory once per plan.
+#pragma once
+#include <stdint.h>
+
+namespace mlmc {
+
+// estimator kinds (template parameter EST of the level kernel)
+enum Est : int { EST_EXACT = 0, EST_APPROX = 1, EST_CORR = 2 };
+// exact-path precision
+enum Xp : int { XP_NONE = 0, XP_F32 = 1, XP_F64 = 2 };
+// approximate-path arithmetic
+enum Ap : int { AP_NONE = 0, AP_FIXED = 1, AP_F16 = 2, AP_BF16 = 3 };
+// payoff classes that need different path functionals
+enum PayClass : int { PC_TERMINAL = 0, PC_ASIAN = 1, PC_LOOKBACK = 2 };
+
+// ((x << ls) + radd) >> rs with at most one of ls, rs non-zero: the exact
+// re-expression of n 2^-from in 2^-to, rounded to nearest with ties toward +inf.
+struct Requant {
+  int32_t ls, rs;
+  int64_t radd;
+};
+
+struct FixedConsts {
+  int64_t con1A, con1cA;   // con1, con1_c aligned to the sum1 accumulation grid F1
+  int32_t con2, con3;      // con2 (f_con2), con3 (f_con1)
+  int64_t S0, K;           // in S's format
+  int64_t lim[7];          // saturation limits 2^(e+f) - 1
+  Requant q_mul1;          // con2 * z          : f_con2 + f_Z      -> f_mul1
+  Requant q_mul3;          // con3 * (z^2 - m)  : f_con1 + 2 f_Z    -> f_mul1
+  int32_t sh_mul1_F1;      // mul1 -> F1 (left shift)
+  Requant q_sum1;          // F1 -> f_sum1
+  Requant q_mul2;          // S * sum1          : f_S + f_sum1      -> f_mul2
+  int32_t sh_S_F2, sh_mul2_F2;  // S, mul2 -> F2 (left shifts)
+  Requant q_S;             // F2 -> f_S
+  int32_t fZ2;             // 2 f_Z (Milstein: the constant m is m 2^(2 f_Z))
+  int32_t fS;
+};
+
+struct ItemDesc {
+  // sample range and chunking
+  uint64_t first, N;       // samples [first, first + N)
+  uint64_t g0, g1;         // groups [g0, g1) covering the range
+  uint32_t groups_per_thread;
+  uint32_t chunk_begin;    // first chunk (CTA) of this item within its launch
+  uint32_t n_chunks;
+  uint32_t out_index;      // index of this item's result record
+  // method
+  int32_t level, nlog;     // nlog = level (2^level fine steps)
+  int32_t payoff, scheme, method, d;
+  uint32_t ctr2, ctr3;     // Philox counter words 2 and 3: level | stream << 8, request
+  int32_t unit;            // approximate payoff unit exponent
+  float unit_scale;        // 2^-unit (FP32, correction estimators)
+  // exact path constants
+  float c1f, c2f, c1cf, c3f, S0f, Kf;
+  double c1d, c2d, c1cd, c3d, S0d, Kd;
+  // approximate path
+  FixedConsts fx;
+  uint16_t h_c1, h_c1c, h_c2, h_c3, h_S0, h_pad;  // binary16 / bfloat16 bit patterns
+  const void *ztab;        // device table for method 1 (int32 / half bits), or method-3 coefficients
+  // optional per-sample dump (device), indexed by sample - first
+  void *dump;
+};
+
+// Per-CTA partial sums, written by the level kernel and summed in chunk order.
+struct Partial {
+  int64_t isum;
+  uint64_t isum2_lo, isum2_hi;
+  double dsum, dsum2;
+  uint64_t nsat;
+};
+
+// Per-item result on the device (undiscounted).
+struct DevSums {
+  double dsum, dsum2;
+  int64_t isum;
+  uint64_t isum2_lo, isum2_hi;
+  uint64_t nsat;
+};
+
+// Philox4x32-10 round keys (k0 + r W0, k1 + r W1), r = 0..9, precomputed on the host.
+struct RoundKeys {
+  uint32_t k[20];
+};
+
+// Launch-wide arguments of a level kernel (passed as a __grid_constant__ parameter).
+struct LaunchArgs {
+  const ItemDesc *items;   // the items of this launch, ordered by chunk_begin
+  int n_items;
+  uint32_t chunk0;         // global chunk index of blockIdx.x == 0
+  Partial *partials;       // indexed by global chunk index
+  RoundKeys rk;
+};
+
+// Method-3 coefficient tables (Sec. 3.3): d-1 classes.
+struct M3Coef {
+  int64_t A[16], B[16];    // fixed point with M3_FRAC bits
+  float a[16], b[16];
+};
+constexpr int M3_FRAC = 30;
+
+}  // namespace mlmc

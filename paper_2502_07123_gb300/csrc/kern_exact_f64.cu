@@ -1,0 +1,10 @@
+// Level-kernel family: estimator EST_EXACT, exact precision XP_F64, approximate arithmetic AP_NONE.
+#include "kernels.h"
+#include "level_kernel.cuh"
+
+namespace mlmc {
+cudaError_t launch_exact_f64(int scheme, int pc, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                      const LaunchArgs &a) {
+  return launch_family<EST_EXACT, XP_F64, AP_NONE>(scheme, pc, grid, block, smem, st, a);
+}
+}  // namespace mlmc

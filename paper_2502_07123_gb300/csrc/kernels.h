@@ -1,0 +1,18 @@
+// Launch entry points of the level-kernel families (one translation unit each).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace mlmc {
+struct LaunchArgs;
+#define MLMC_FAMILY(name) \
+  cudaError_t name(int scheme, int pc, dim3 grid, dim3 block, size_t smem, cudaStream_t st, const LaunchArgs &a);
+MLMC_FAMILY(launch_exact_f32)
+MLMC_FAMILY(launch_exact_f64)
+MLMC_FAMILY(launch_approx_fixed)
+MLMC_FAMILY(launch_approx_f16)
+MLMC_FAMILY(launch_approx_bf16)
+MLMC_FAMILY(launch_corr_fixed)
+MLMC_FAMILY(launch_corr_f16)
+MLMC_FAMILY(launch_corr_bf16)
+#undef MLMC_FAMILY
+}  // namespace mlmc

@@ -1,0 +1,515 @@
+// The MLMC level kernel: per-sample coupled fine/coarse GBM paths of one
+// level (Sec. 2.1), exact Normals and/or table-based approximate Normals from
+// the same uniform J (Sec. 3), the low-precision path in fixed point
+// (Algorithm 1) or binary16/bfloat16, payoffs, the level difference / nested
+// correction (eq. chap:nested_exp) and per-CTA sums of Y and Y^2.
+//
+// Layout: one CTA processes one chunk of one work item; each thread simulates
+// groups of samples whose uniforms come from one Philox call per group (4
+// samples per call on level 0, 2 on level 1, one sample with 2^l / 4 calls
+// above), entirely in registers.  The approximate-Normal table of the item
+// lives in shared memory.  The only global-memory traffic is the work-item
+// descriptor, the table, one Partial record per CTA and the optional dump.
+#pragma once
+#include "device_common.cuh"
+#include "mlmc.h"
+
+namespace mlmc {
+
+using mlmc_sample_rec = ::mlmc_sample;
+
+template <int XP> struct XType { using T = float; };
+template <> struct XType<XP_F64> { using T = double; };
+template <int AP> struct HType { using T = __half; };
+template <> struct HType<AP_BF16> { using T = __nv_bfloat16; };
+
+constexpr int MAX_THREADS = 256;
+
+template <int EST, int XP, int AP, int SCHEME, int PC>
+struct LevelSim {
+  static constexpr bool HAS_EXACT = (EST != EST_APPROX);
+  static constexpr bool HAS_APPROX = (EST != EST_EXACT);
+  static constexpr bool MIL = (SCHEME == 1);
+  using X = typename XType<XP>::T;
+  using H = typename HType<AP>::T;
+  using HO = HalfOps<H>;
+
+  // ---- per-item constants (registers) ----
+  int level, nsteps, payoff, d, method;
+  X c1, c2, c1c, c3, S0, K;
+  // fixed point
+  FixedConsts fx;
+  // half
+  H hc1, hc1c, hc2, hc3, hS0;
+  float K32;
+  float unit_scale;
+  const void *smem_tab;
+
+  // ---- per-sample state ----
+  X S, Sc, zprev, accF, accC, minF, minC;
+  int64_t aS, aSc, aaccF, aaccC, aminF, aminC;
+  int32_t azprev;
+  H hS, hSc, hzprev, hminF, hminC;
+  float haccF, haccC;
+  uint32_t sat;
+
+  __device__ __forceinline__ void load(const ItemDesc &it, const void *tab) {
+    level = it.level;
+    nsteps = 1 << it.level;
+    payoff = it.payoff;
+    d = it.d;
+    method = it.method;
+    if constexpr (XP == XP_F64) {
+      c1 = it.c1d; c2 = it.c2d; c1c = it.c1cd; c3 = it.c3d; S0 = it.S0d; K = it.Kd;
+    } else {
+      c1 = it.c1f; c2 = it.c2f; c1c = it.c1cf; c3 = it.c3f; S0 = it.S0f; K = it.Kf;
+    }
+    if constexpr (AP == AP_FIXED) fx = it.fx;
+    if constexpr (AP == AP_F16 || AP == AP_BF16) {
+      hc1 = HO::from_bits(it.h_c1); hc1c = HO::from_bits(it.h_c1c);
+      hc2 = HO::from_bits(it.h_c2); hc3 = HO::from_bits(it.h_c3);
+      hS0 = HO::from_bits(it.h_S0);
+      K32 = it.Kf;
+    }
+    unit_scale = it.unit_scale;
+    smem_tab = tab;
+  }
+
+  __device__ __forceinline__ void begin() {
+    if constexpr (HAS_EXACT) {
+      S = S0; Sc = S0; zprev = X(0);
+      accF = X(0.5) * S0; accC = accF; minF = S0; minC = S0;
+    }
+    if constexpr (AP == AP_FIXED) {
+      aS = fx.S0; aSc = fx.S0; aaccF = 0; aaccC = 0; aminF = fx.S0; aminC = fx.S0; azprev = 0;
+    }
+    if constexpr (AP == AP_F16 || AP == AP_BF16) {
+      hS = hS0; hSc = hS0; hzprev = HO::from_f(0.0f); hminF = hS0; hminC = hS0;
+      haccF = __fmul_rn(0.5f, HO::to_f(hS0)); haccC = haccF;
+    }
+    sat = 0;
+  }
+
+  // ---- exact path (FP32 / FP64) ----
+  __device__ __forceinline__ X exact_inc(X z, X cc1, X mm) const {
+    if constexpr (MIL) return fma(c3, fma(z, z, -mm), fma(c2, z, cc1));
+    else return fma(c2, z, cc1);
+  }
+
+  // ---- fixed-point Algorithm-1 step ----
+  __device__ __forceinline__ int64_t fx_step(int64_t s, int32_t z, int64_t con1A, int m) {
+    const int64_t mul1 = saturate(requant((int64_t)fx.con2 * z, fx.q_mul1), fx.lim[3], sat);
+    int64_t acc = con1A + (int64_t)((uint64_t)mul1 << fx.sh_mul1_F1);
+    if constexpr (MIL) {
+      const int64_t zz = (int64_t)z * z - ((int64_t)m << fx.fZ2);
+      const int64_t mul3 = saturate(requant((int64_t)fx.con3 * zz, fx.q_mul3), fx.lim[3], sat);
+      acc += (int64_t)((uint64_t)mul3 << fx.sh_mul1_F1);
+    }
+    const int64_t sum1 = saturate(requant(acc, fx.q_sum1), fx.lim[4], sat);
+    const int64_t mul2 = saturate(requant(s * sum1, fx.q_mul2), fx.lim[5], sat);
+    const int64_t s2 = (int64_t)((uint64_t)s << fx.sh_S_F2) + (int64_t)((uint64_t)mul2 << fx.sh_mul2_F2);
+    return saturate(requant(s2, fx.q_S), fx.lim[6], sat);
+  }
+
+  // ---- half-precision step (one rounding per operation) ----
+  __device__ __forceinline__ H h_step(H s, H z, H cc1, H mh) const {
+    const H mul1 = HO::mul(hc2, z);
+    H sum1 = HO::add(cc1, mul1);
+    if constexpr (MIL) {
+      const H sq = HO::mul(z, z);
+      const H sqm = HO::sub(sq, mh);
+      const H mul3 = HO::mul(hc3, sqm);
+      sum1 = HO::add(sum1, mul3);
+    }
+    const H mul2 = HO::mul(s, sum1);
+    return HO::add(s, mul2);
+  }
+
+  __device__ __forceinline__ int32_t fixed_z(ApproxIndex ai) const {
+    int32_t v;
+    if (method == 1) {
+      v = ((const int32_t *)smem_tab)[ai.idx];
+    } else {
+      const M3Coef *m3 = (const M3Coef *)smem_tab;
+      const int c = m3_class(ai.idx);
+      const int64_t t = m3->A[c] + m3->B[c] * (int64_t)ai.idx;
+      const int sh = M3_FRAC - fx.fZ2 / 2;
+      v = (int32_t)((t + ((int64_t)1 << (sh - 1))) >> sh);
+    }
+    return ai.neg ? -v : v;
+  }
+
+  __device__ __forceinline__ H half_z(ApproxIndex ai) const {
+    H v;
+    if (method == 1) {
+      v = HO::from_bits(((const uint16_t *)smem_tab)[ai.idx]);
+    } else {
+      const M3Coef *m3 = (const M3Coef *)smem_tab;
+      const int c = m3_class(ai.idx);
+      v = HO::from_f(fmaf(m3->b[c], (float)ai.idx, m3->a[c]));
+    }
+    return ai.neg ? HO::neg(v) : v;
+  }
+
+  // One fine step i driven by J (and the coarse step when i is odd).
+  __device__ __forceinline__ void step(uint32_t J, int i) {
+    if constexpr (HAS_EXACT) {
+      X z;
+      if constexpr (XP == XP_F64) z = exact_normal_f64(J);
+      else z = exact_normal_f32(J);
+      if constexpr (PC == PC_ASIAN) { if (i > 0) accF = accF + S; }
+      S = fma(S, exact_inc(z, c1, X(1)), S);
+      if constexpr (PC == PC_LOOKBACK) minF = fmin(minF, S);
+      if (level > 0) {
+        if (i & 1) {
+          const X zc = zprev + z;
+          if constexpr (PC == PC_ASIAN) { if (i > 1) accC = accC + Sc; }
+          Sc = fma(Sc, exact_inc(zc, c1c, X(2)), Sc);
+          if constexpr (PC == PC_LOOKBACK) minC = fmin(minC, Sc);
+        } else {
+          zprev = z;
+        }
+      }
+    }
+    if constexpr (HAS_APPROX) {
+      const ApproxIndex ai = approx_index(J, d);
+      if constexpr (AP == AP_FIXED) {
+        const int32_t z = fixed_z(ai);
+        if constexpr (PC == PC_ASIAN) { if (i > 0) aaccF += aS; }
+        aS = fx_step(aS, z, fx.con1A, 1);
+        if constexpr (PC == PC_LOOKBACK) aminF = aS < aminF ? aS : aminF;
+        if (level > 0) {
+          if (i & 1) {
+            if constexpr (PC == PC_ASIAN) { if (i > 1) aaccC += aSc; }
+            aSc = fx_step(aSc, azprev + z, fx.con1cA, 2);
+            if constexpr (PC == PC_LOOKBACK) aminC = aSc < aminC ? aSc : aminC;
+          } else {
+            azprev = z;
+          }
+        }
+      } else {
+        const H z = half_z(ai);
+        if constexpr (PC == PC_ASIAN) { if (i > 0) haccF = __fadd_rn(haccF, HO::to_f(hS)); }
+        hS = h_step(hS, z, hc1, HO::from_f(1.0f));
+        if constexpr (PC == PC_LOOKBACK) hminF = HO::to_f(hS) < HO::to_f(hminF) ? hS : hminF;
+        if (level > 0) {
+          if (i & 1) {
+            const H zc = HO::add(hzprev, z);
+            if constexpr (PC == PC_ASIAN) { if (i > 1) haccC = __fadd_rn(haccC, HO::to_f(hSc)); }
+            hSc = h_step(hSc, zc, hc1c, HO::from_f(2.0f));
+            if constexpr (PC == PC_LOOKBACK) hminC = HO::to_f(hSc) < HO::to_f(hminC) ? hSc : hminC;
+          } else {
+            hzprev = z;
+          }
+        }
+      }
+    }
+  }
+
+  // ---- payoffs ----
+  __device__ __forceinline__ X exact_payoff(X x, X acc, X mn, int steps) const {
+    if constexpr (PC == PC_TERMINAL) {
+      if (payoff == 1) return x > K ? X(1) : X(0);
+      const X dd = x - K;
+      return dd > X(0) ? dd : X(0);
+    } else if constexpr (PC == PC_ASIAN) {
+      const X avg = (acc + X(0.5) * x) * (X(1) / X(steps));
+      const X dd = avg - K;
+      return dd > X(0) ? dd : X(0);
+    } else {
+      return x - mn;
+    }
+  }
+  __device__ __forceinline__ int64_t fixed_payoff(int64_t x, int64_t inner, int64_t mn, int steps, bool coarse) const {
+    if constexpr (PC == PC_TERMINAL) {
+      if (payoff == 1) return x > fx.K ? ((int64_t)1 << fx.fS) : 0;
+      return x > fx.K ? x - fx.K : 0;
+    } else if constexpr (PC == PC_ASIAN) {
+      const int64_t twice = fx.S0 + 2 * inner + x;
+      const int64_t twoNK = 2 * (int64_t)steps * fx.K;
+      const int64_t v = twice > twoNK ? twice - twoNK : 0;
+      return coarse ? 2 * v : v;
+    } else {
+      return x - mn;
+    }
+  }
+  __device__ __forceinline__ int64_t half_payoff(H x, float acc, H mn, int steps) const {
+    float P;
+    const float xf = HO::to_f(x);
+    if constexpr (PC == PC_TERMINAL) {
+      if (payoff == 1) {
+        P = xf > K32 ? 1.0f : 0.0f;
+      } else {
+        const float dd = __fsub_rn(xf, K32);
+        P = dd > 0.0f ? dd : 0.0f;
+      }
+    } else if constexpr (PC == PC_ASIAN) {
+      const float tot = __fadd_rn(acc, __fmul_rn(0.5f, xf));
+      const float avg = __fmul_rn(tot, 1.0f / (float)steps);
+      const float dd = __fsub_rn(avg, K32);
+      P = dd > 0.0f ? dd : 0.0f;
+    } else {
+      P = __fsub_rn(xf, HO::to_f(mn));
+    }
+    return __float2ll_rn(__fmul_rn(P, 16777216.0f));
+  }
+
+  // Finish the sample: payoffs, sample value, accumulation and optional dump.
+  template <class Acc>
+  __device__ __forceinline__ void finish(Acc &acc, bool valid, mlmc_sample_rec *dump) {
+    X pf = X(0), pc = X(0);
+    int64_t qf = 0, qc = 0;
+    if constexpr (HAS_EXACT) {
+      pf = exact_payoff(S, accF, minF, nsteps);
+      if (level > 0) pc = exact_payoff(Sc, accC, minC, nsteps >> 1);
+    }
+    if constexpr (AP == AP_FIXED) {
+      qf = fixed_payoff(aS, aaccF, aminF, nsteps, false);
+      if (level > 0) qc = fixed_payoff(aSc, aaccC, aminC, nsteps >> 1, true);
+    }
+    if constexpr (AP == AP_F16 || AP == AP_BF16) {
+      if constexpr (HAS_APPROX) {
+        qf = half_payoff(hS, haccF, hminF, nsteps);
+        if (level > 0) qc = half_payoff(hSc, haccC, hminC, nsteps >> 1);
+      }
+    }
+    if (!valid) return;
+    double ydump;
+    if constexpr (EST == EST_EXACT) {
+      const X y = pf - pc;
+      acc.add_real(y);
+      ydump = (double)y;
+    } else if constexpr (EST == EST_APPROX) {
+      const int64_t yi = qf - qc;
+      acc.add_int(yi);
+      ydump = (double)yi * (double)unit_scale;
+    } else {
+      const float yx = (float)(pf - pc);
+      const float ya = __fmul_rn(__ll2float_rn(qf - qc), unit_scale);
+      const float y = __fsub_rn(yx, ya);
+      acc.add_real(y);
+      ydump = (double)y;
+    }
+    acc.nsat += sat;
+    if (dump) {
+      mlmc_sample_rec r;
+      r.pf = (double)pf; r.pc = (double)pc;
+      r.sf = HAS_EXACT ? (double)S : 0.0;
+      r.sc = (HAS_EXACT && level > 0) ? (double)Sc : 0.0;
+      if constexpr (AP == AP_FIXED) {
+        r.af = ldexp((double)aS, -fx.fS);
+        r.ac = level > 0 ? ldexp((double)aSc, -fx.fS) : 0.0;
+      } else if constexpr (AP == AP_F16 || AP == AP_BF16) {
+        r.af = HAS_APPROX ? (double)HO::to_f(hS) : 0.0;
+        r.ac = (HAS_APPROX && level > 0) ? (double)HO::to_f(hSc) : 0.0;
+      } else {
+        r.af = 0.0; r.ac = 0.0;
+      }
+      r.qf = qf; r.qc = qc; r.y = ydump; r.sat = sat; r.pad = 0;
+      *dump = r;
+    }
+  }
+};
+
+// Per-thread accumulator
+template <int EST, int XP>
+struct ThreadAcc {
+  // integer estimators
+  int64_t isum;
+  uint64_t q_lo, q_hi;
+  // FP32 estimators (Kahan), FP64 estimators
+  KahanF ks, kq;
+  double ds, dq;
+  uint32_t nsat;
+  __device__ __forceinline__ void init() {
+    isum = 0; q_lo = 0; q_hi = 0; ks.init(); kq.init(); ds = 0.0; dq = 0.0; nsat = 0;
+  }
+  __device__ __forceinline__ void add_int(int64_t y) {
+    isum += y;
+    add_square(q_lo, q_hi, y);
+  }
+  template <class T>
+  __device__ __forceinline__ void add_real(T y) {
+    if constexpr (XP == XP_F64 && EST == EST_EXACT) {
+      ds += (double)y;
+      dq = fma((double)y, (double)y, dq);
+    } else {
+      ks.add((float)y);
+      kq.add(__fmul_rn((float)y, (float)y));
+    }
+  }
+};
+
+template <class T>
+__device__ __forceinline__ T shfl_xor(T v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+
+// Reduce the CTA's thread accumulators into one Partial (thread 0 writes it).
+template <int EST, int XP>
+__device__ __forceinline__ void block_reduce_write(ThreadAcc<EST, XP> &a, Partial *out) {
+  int64_t isum = a.isum;
+  uint64_t lo = a.q_lo, hi = a.q_hi;
+  double ds, dq;
+  if constexpr (XP == XP_F64 && EST == EST_EXACT) { ds = a.ds; dq = a.dq; }
+  else { ds = a.ks.value(); dq = a.kq.value(); }
+  uint64_t ns = a.nsat;
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) {
+    isum += shfl_xor((long long)isum, m);
+    const uint64_t olo = (uint64_t)shfl_xor((unsigned long long)lo, m);
+    const uint64_t ohi = (uint64_t)shfl_xor((unsigned long long)hi, m);
+    add_u128(lo, hi, olo, ohi);
+    ds += shfl_xor(ds, m);
+    dq += shfl_xor(dq, m);
+    ns += (uint64_t)shfl_xor((unsigned long long)ns, m);
+  }
+  __shared__ Partial wp[MAX_THREADS / 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    Partial p;
+    p.isum = isum; p.isum2_lo = lo; p.isum2_hi = hi; p.dsum = ds; p.dsum2 = dq; p.nsat = ns;
+    wp[warp] = p;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Partial t = wp[0];
+    const int nw = blockDim.x >> 5;
+    for (int w = 1; w < nw; ++w) {
+      t.isum += wp[w].isum;
+      add_u128(t.isum2_lo, t.isum2_hi, wp[w].isum2_lo, wp[w].isum2_hi);
+      t.dsum += wp[w].dsum;
+      t.dsum2 += wp[w].dsum2;
+      t.nsat += wp[w].nsat;
+    }
+    *out = t;
+  }
+}
+
+template <int EST, int XP, int AP, int SCHEME, int PC>
+__global__ void __launch_bounds__(MAX_THREADS)
+level_kernel(const __grid_constant__ LaunchArgs args) {
+  using Sim = LevelSim<EST, XP, AP, SCHEME, PC>;
+  extern __shared__ __align__(16) unsigned char smem_tab[];
+  __shared__ int s_item;
+  const uint32_t gc = args.chunk0 + blockIdx.x;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = args.n_items - 1;
+    while (lo < hi) {  // last item with chunk_begin <= gc
+      const int mid = (lo + hi + 1) >> 1;
+      if (args.items[mid].chunk_begin <= gc) lo = mid; else hi = mid - 1;
+    }
+    s_item = lo;
+  }
+  __syncthreads();
+  const ItemDesc &it = args.items[s_item];
+  // stage the approximate-Normal table in shared memory
+  if constexpr (AP != AP_NONE) {
+    if (it.method == 1) {
+      const int n = 1 << (it.d - 1);
+      if constexpr (AP == AP_FIXED) {
+        const int32_t *src = (const int32_t *)it.ztab;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) ((int32_t *)smem_tab)[k] = src[k];
+      } else {
+        const uint16_t *src = (const uint16_t *)it.ztab;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) ((uint16_t *)smem_tab)[k] = src[k];
+      }
+    } else {
+      const uint32_t *src = (const uint32_t *)it.ztab;
+      for (int k = threadIdx.x; k < (int)(sizeof(M3Coef) / 4); k += blockDim.x)
+        ((uint32_t *)smem_tab)[k] = src[k];
+    }
+    __syncthreads();
+  }
+  Sim sim;
+  sim.load(it, smem_tab);
+  ThreadAcc<EST, XP> acc;
+  acc.init();
+
+  const uint32_t chunk = gc - it.chunk_begin;
+  const uint64_t per_chunk = (uint64_t)it.groups_per_thread * blockDim.x;
+  const uint64_t gbeg = it.g0 + (uint64_t)chunk * per_chunk;
+  const uint64_t gend = min(it.g1, gbeg + per_chunk);
+  const uint64_t first = it.first, last = it.first + it.N;
+  const int lev = it.level;
+  const uint4 ctr_hi = make_uint4(0, 0, it.ctr2, it.ctr3);
+  mlmc_sample_rec *dump = (mlmc_sample_rec *)it.dump;
+
+  for (uint64_t g = gbeg + threadIdx.x; g < gend; g += blockDim.x) {
+    if (lev >= 2) {
+      // one sample per group, 2^l / 4 Philox calls
+      const uint64_t s = g;
+      const uint32_t calls = 1u << (lev - 2);
+      sim.begin();
+      for (uint32_t c = 0; c < calls; ++c) {
+        const uint64_t q = s * calls + c;
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), ctr_hi.z, ctr_hi.w), args.rk);
+        const int i0 = (int)(c << 2);
+        sim.step(w.x, i0);
+        sim.step(w.y, i0 + 1);
+        sim.step(w.z, i0 + 2);
+        sim.step(w.w, i0 + 3);
+      }
+      const bool valid = s >= first && s < last;
+      sim.finish(acc, valid, dump && valid ? dump + (s - first) : nullptr);
+    } else if (lev == 1) {
+      const uint4 w = philox4x32_10(make_uint4((uint32_t)g, (uint32_t)(g >> 32), ctr_hi.z, ctr_hi.w), args.rk);
+      const uint64_t s0 = 2 * g;
+      sim.begin();
+      sim.step(w.x, 0);
+      sim.step(w.y, 1);
+      {
+        const bool valid = s0 >= first && s0 < last;
+        sim.finish(acc, valid, dump && valid ? dump + (s0 - first) : nullptr);
+      }
+      sim.begin();
+      sim.step(w.z, 0);
+      sim.step(w.w, 1);
+      {
+        const bool valid = s0 + 1 >= first && s0 + 1 < last;
+        sim.finish(acc, valid, dump && valid ? dump + (s0 + 1 - first) : nullptr);
+      }
+    } else {
+      const uint4 w = philox4x32_10(make_uint4((uint32_t)g, (uint32_t)(g >> 32), ctr_hi.z, ctr_hi.w), args.rk);
+      const uint64_t s0 = 4 * g;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        sim.begin();
+        sim.step(word_of(w, k), 0);
+        const bool valid = s0 + k >= first && s0 + k < last;
+        sim.finish(acc, valid, dump && valid ? dump + (s0 + k - first) : nullptr);
+      }
+    }
+  }
+  block_reduce_write<EST, XP>(acc, args.partials + gc);
+}
+
+}  // namespace mlmc
+
+namespace mlmc {
+
+template <int EST, int XP, int AP, int SCHEME, int PC>
+cudaError_t launch_one(dim3 grid, dim3 block, size_t smem, cudaStream_t st, const LaunchArgs &a) {
+  auto k = level_kernel<EST, XP, AP, SCHEME, PC>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k<<<grid, block, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+// All (scheme, payoff class) instantiations of one (estimator, precision) family.
+template <int EST, int XP, int AP>
+cudaError_t launch_family(int scheme, int pc, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                          const LaunchArgs &a) {
+  switch (scheme * 3 + pc) {
+    case 0: return launch_one<EST, XP, AP, 0, PC_TERMINAL>(grid, block, smem, st, a);
+    case 1: return launch_one<EST, XP, AP, 0, PC_ASIAN>(grid, block, smem, st, a);
+    case 2: return launch_one<EST, XP, AP, 0, PC_LOOKBACK>(grid, block, smem, st, a);
+    case 3: return launch_one<EST, XP, AP, 1, PC_TERMINAL>(grid, block, smem, st, a);
+    case 4: return launch_one<EST, XP, AP, 1, PC_ASIAN>(grid, block, smem, st, a);
+    case 5: return launch_one<EST, XP, AP, 1, PC_LOOKBACK>(grid, block, smem, st, a);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace mlmc

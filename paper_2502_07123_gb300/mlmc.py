@@ -1,0 +1,298 @@
+"""Python binding of libmlmc_gb300.so (the C ABI of include/mlmc.h).
+
+Argument marshalling only: every step of the level simulation runs in the
+CUDA library.  PyTorch is used for device memory (per-sample dumps) and for
+the current CUDA stream.  There is no fallback: if the library has not been
+built, or no CUDA device is usable, the calls raise MLMCError.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libmlmc_gb300.so")
+
+# enums (include/mlmc.h)
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW, ENOTREADY = range(7)
+EULER, MILSTEIN = 0, 1
+EURO, DIGITAL, ASIAN, LOOKBACK = 0, 1, 2, 3
+FP64_EXACT, FP32_EXACT, FP16_APPROX, BF16_APPROX, FIXED_APPROX, NESTED_CORR_FIXED, NESTED_CORR_FP16, \
+    NESTED_CORR_BF16 = range(8)
+MODE_PLAIN_FP64, MODE_PLAIN_FP32, MODE_NESTED_FIXED, MODE_NESTED_FP16, MODE_NESTED_BF16 = range(5)
+REP_FP64, REP_FP32, REP_FP16, REP_BF16, REP_FIXED = range(5)
+
+
+class MLMCError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = _lib.mlmc_strerror(status).decode() if _lib is not None else str(status)
+        super().__init__("%s: %s (status %d)" % (where, msg, status))
+
+
+class Format(ctypes.Structure):
+    _fields_ = [("e", ctypes.c_int8 * 7), ("f", ctypes.c_int8 * 7)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("S0", ctypes.c_double), ("K", ctypes.c_double), ("r", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("T", ctypes.c_double),
+                ("payoff", ctypes.c_int32), ("scheme", ctypes.c_int32),
+                ("icdf_method", ctypes.c_int32), ("icdf_bits", ctypes.c_int32),
+                ("formats", ctypes.POINTER(Format)), ("n_formats", ctypes.c_int32),
+                ("request_id", ctypes.c_uint32)]
+
+
+class Sums(ctypes.Structure):
+    _fields_ = [("sum", ctypes.c_double), ("sum2", ctypes.c_double), ("n", ctypes.c_uint64),
+                ("seconds", ctypes.c_double), ("saturations", ctypes.c_uint64),
+                ("isum", ctypes.c_int64), ("isum2_lo", ctypes.c_uint64), ("isum2_hi", ctypes.c_uint64),
+                ("unit", ctypes.c_int32), ("exact_int", ctypes.c_int32)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("steps_per_thread", ctypes.c_int32)]
+
+
+class Work(ctypes.Structure):
+    _fields_ = [("params", ctypes.POINTER(Params)), ("level", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("first_sample", ctypes.c_uint64), ("N", ctypes.c_uint64),
+                ("stream", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+SAMPLE_DTYPE = np.dtype([("pf", "<f8"), ("pc", "<f8"), ("sf", "<f8"), ("sc", "<f8"),
+                         ("af", "<f8"), ("ac", "<f8"), ("qf", "<i8"), ("qc", "<i8"),
+                         ("y", "<f8"), ("sat", "<u4"), ("pad", "<u4")])
+SAMPLE_BYTES = SAMPLE_DTYPE.itemsize
+
+_lib = None
+
+
+def load():
+    """Load the CUDA library; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libmlmc_gb300.so is not built (run paper_2502_07123_gb300/build.py or "
+                          "__graft_entry__.build()); there is no CPU fallback")
+    L = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    st = ctypes.c_int
+    sig = {
+        "mlmc_level": (st, [ctypes.c_int, ctypes.c_uint64, P(Params), ctypes.c_int, ctypes.c_uint64,
+                            ctypes.c_uint64, P(Sums)]),
+        "mlmc_level_dump": (st, [ctypes.c_int, ctypes.c_uint64, P(Params), ctypes.c_int, ctypes.c_uint64,
+                                 ctypes.c_uint64, ctypes.c_int32, ctypes.c_void_p, P(Sums)]),
+        "mlmc_plan_create": (st, [P(ctypes.c_void_p), P(Work), ctypes.c_int, ctypes.c_uint64, P(Tuning)]),
+        "mlmc_plan_launch": (st, [ctypes.c_void_p, ctypes.c_void_p]),
+        "mlmc_plan_results": (st, [ctypes.c_void_p, P(Sums)]),
+        "mlmc_plan_info": (st, [ctypes.c_void_p, P(ctypes.c_int), P(ctypes.c_uint64), P(ctypes.c_uint64),
+                                P(ctypes.c_uint64), P(ctypes.c_uint64)]),
+        "mlmc_plan_kernel_time": (st, [ctypes.c_void_p, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_double)]),
+        "mlmc_plan_destroy": (None, [ctypes.c_void_p]),
+        "mlmc_run": (st, [P(Work), ctypes.c_int, ctypes.c_uint64, P(Tuning), P(Sums), ctypes.c_void_p]),
+        "mlmc_estimate": (st, [ctypes.c_double, P(Params), ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+                               P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_int), P(ctypes.c_uint64),
+                               ctypes.c_int]),
+        "mlmc_cost_model": (st, [ctypes.c_int, ctypes.c_double]),
+        "mlmc_default_format": (st, [P(Params), ctypes.c_int, P(Format)]),
+        "mlmc_icdf_table": (st, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_double)]),
+        "mlmc_philox": (st, [P(ctypes.c_uint32), ctypes.c_uint64, ctypes.c_uint64, P(ctypes.c_uint32)]),
+        "mlmc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "mlmc_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status, where):
+    if status != OK:
+        raise MLMCError(status, where)
+
+
+def _sums_dict(s):
+    d = {k: getattr(s, k) for k, _ in Sums._fields_}
+    d["isum2"] = (int(s.isum2_hi) << 64) | int(s.isum2_lo)
+    return d
+
+
+def make_params(p, d=10, method=1, formats=None, request=0):
+    """Build an mlmc_params from a dict (S0, K, r, sigma, T, payoff, scheme).
+
+    formats: None (library default schedule) or a list, indexed by level, of
+    {'e': [7], 'f': [7]}.  Returns the ctypes struct; the format array is kept
+    alive as an attribute of the struct."""
+    P = Params()
+    P.S0, P.K, P.r, P.sigma, P.T = (float(p[k]) for k in ("S0", "K", "r", "sigma", "T"))
+    P.payoff, P.scheme = int(p["payoff"]), int(p["scheme"])
+    P.icdf_method, P.icdf_bits = int(method), int(d)
+    P.request_id = int(request)
+    if formats is not None:
+        arr = (Format * len(formats))()
+        for i, fm in enumerate(formats):
+            for j in range(7):
+                arr[i].e[j] = int(fm["e"][j])
+                arr[i].f[j] = int(fm["f"][j])
+        P.formats = ctypes.cast(arr, ctypes.POINTER(Format))
+        P.n_formats = len(formats)
+        P._keep = arr
+    else:
+        P.formats = None
+        P.n_formats = 0
+    return P
+
+
+def mlmc_level(level, N, params, variant, seed, first_sample=0):
+    L = load()
+    s = Sums()
+    _check(L.mlmc_level(level, N, ctypes.byref(params), variant, seed, first_sample, ctypes.byref(s)),
+           "mlmc_level")
+    return _sums_dict(s)
+
+
+def mlmc_level_dump(level, N, params, variant, seed, first_sample=0, stream=-1):
+    """Returns (sums dict, numpy structured array of the N samples)."""
+    import torch
+    L = load()
+    buf = torch.empty(max(1, N) * SAMPLE_BYTES, dtype=torch.uint8, device="cuda")
+    s = Sums()
+    torch.cuda.synchronize()
+    _check(L.mlmc_level_dump(level, N, ctypes.byref(params), variant, seed, first_sample, stream,
+                             ctypes.c_void_p(buf.data_ptr()), ctypes.byref(s)), "mlmc_level_dump")
+    host = buf[: N * SAMPLE_BYTES].cpu().numpy()
+    return _sums_dict(s), host.view(SAMPLE_DTYPE)
+
+
+def _works(items):
+    """items: list of dict(params=Params, level, variant, first_sample=0, N, stream=-1)."""
+    arr = (Work * len(items))()
+    keep = []
+    for i, it in enumerate(items):
+        keep.append(it["params"])
+        arr[i].params = ctypes.pointer(it["params"])
+        arr[i].level = int(it["level"])
+        arr[i].variant = int(it["variant"])
+        arr[i].first_sample = int(it.get("first_sample", 0))
+        arr[i].N = int(it["N"])
+        arr[i].stream = int(it.get("stream", -1))
+    return arr, keep
+
+
+def _tuning(tuning):
+    if tuning is None:
+        return None
+    t = Tuning()
+    t.threads, t.steps_per_thread = int(tuning.get("threads", 0)), int(tuning.get("steps_per_thread", 0))
+    return ctypes.byref(t)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """A device-resident work list (mlmc_plan_create / _launch / _results)."""
+
+    def __init__(self, items, seed, tuning=None):
+        L = load()
+        self._arr, self._keep = _works(items)
+        self.n = len(items)
+        self._h = ctypes.c_void_p()
+        _check(L.mlmc_plan_create(ctypes.byref(self._h), self._arr, self.n, seed, _tuning(tuning)),
+               "mlmc_plan_create")
+
+    def launch(self, stream=None):
+        _check(load().mlmc_plan_launch(self._h, _stream_handle(stream)), "mlmc_plan_launch")
+
+    def results(self):
+        out = (Sums * self.n)()
+        _check(load().mlmc_plan_results(self._h, out), "mlmc_plan_results")
+        return [_sums_dict(out[i]) for i in range(self.n)]
+
+    def info(self):
+        k = ctypes.c_int()
+        c, ps, hb, db = (ctypes.c_uint64() for _ in range(4))
+        _check(load().mlmc_plan_info(self._h, ctypes.byref(k), ctypes.byref(c), ctypes.byref(ps),
+                                     ctypes.byref(hb), ctypes.byref(db)), "mlmc_plan_info")
+        return dict(kernels=k.value, ctas=c.value, path_steps=ps.value, h2d_bytes=hb.value, d2h_bytes=db.value)
+
+    def kernel_time(self, k):
+        """(family, ms) of level kernel k of the last launch (CUDA events on its stream)."""
+        fam = ctypes.c_int()
+        ms = ctypes.c_double()
+        _check(load().mlmc_plan_kernel_time(self._h, k, ctypes.byref(fam), ctypes.byref(ms)),
+               "mlmc_plan_kernel_time")
+        return fam.value, ms.value
+
+    def close(self):
+        if self._h:
+            load().mlmc_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mlmc_run(items, seed, tuning=None, stream=None):
+    L = load()
+    arr, keep = _works(items)
+    out = (Sums * len(items))()
+    _check(L.mlmc_run(arr, len(items), seed, _tuning(tuning), out, _stream_handle(stream)), "mlmc_run")
+    return [_sums_dict(out[i]) for i in range(len(items))]
+
+
+def mlmc_estimate(eps, params, mode, seed, max_level=10):
+    L = load()
+    cap = max_level + 1
+    price, se = ctypes.c_double(), ctypes.c_double()
+    lev = ctypes.c_int()
+    Nl = (ctypes.c_uint64 * (2 * cap))()
+    _check(L.mlmc_estimate(eps, ctypes.byref(params), mode, seed, max_level, ctypes.byref(price),
+                           ctypes.byref(se), ctypes.byref(lev), Nl, cap), "mlmc_estimate")
+    N = [[int(Nl[2 * l]), int(Nl[2 * l + 1])] for l in range(lev.value + 1)]
+    return dict(price=price.value, stderr=se.value, L=lev.value, N=N)
+
+
+def mlmc_cost_model(kind, cost_per_step):
+    _check(load().mlmc_cost_model(kind, cost_per_step), "mlmc_cost_model")
+
+
+def mlmc_default_format(params, level):
+    F = Format()
+    _check(load().mlmc_default_format(ctypes.byref(params), level, ctypes.byref(F)), "mlmc_default_format")
+    return {"e": [F.e[i] for i in range(7)], "f": [F.f[i] for i in range(7)]}
+
+
+def mlmc_icdf_table(method, d, rep, fZ=0):
+    out = (ctypes.c_double * (1 << (d - 1)))()
+    _check(load().mlmc_icdf_table(method, d, rep, fZ, out), "mlmc_icdf_table")
+    return np.frombuffer(out, dtype=np.float64).copy()
+
+
+def mlmc_philox(ctr, seed):
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    out = np.empty_like(ctr)
+    P = ctypes.POINTER(ctypes.c_uint32)
+    _check(load().mlmc_philox(ctr.ctypes.data_as(P), ctr.shape[0], seed, out.ctypes.data_as(P)), "mlmc_philox")
+    return out
+
+
+def mlmc_strerror(status):
+    return load().mlmc_strerror(status).decode()
+
+
+def mlmc_version():
+    return load().mlmc_version().decode()

@@ -1,0 +1,54 @@
+"""Shared helpers of the GPU parity tests (comparison rules and tolerances)."""
+import numpy as np
+
+from oracle import core
+
+# FP32 exact path: 1e-5 relative per path (terminal value and path functionals)
+RTOL_F32 = 1e-5
+# FP64 exact path: GPU normcdfinv / fused multiply-adds against the oracle's Newton inverse
+RTOL_F64 = 1e-12
+
+APPROX_ONLY = (core.FIXED_APPROX, core.FP16_APPROX, core.BF16_APPROX)
+CORR = (core.CORR_FIXED, core.CORR_FP16, core.CORR_BF16)
+
+
+def exact_rtol(variant):
+    return RTOL_F64 if variant == core.FP64_EXACT else RTOL_F32
+
+
+def compare_samples(variant, p, g, o):
+    """Element-wise parity of one dump against the oracle's dump of the same samples."""
+    assert g.shape == o.shape
+    if core.has_approx(variant):
+        # integer / IEEE-emulated work: bit-exact
+        for f in ("qf", "qc", "af", "ac", "sat"):
+            bad = np.nonzero(g[f] != o[f])[0]
+            assert bad.size == 0, (f, bad[:5], g[f][bad[:5]], o[f][bad[:5]])
+    if core.has_exact(variant):
+        rt = exact_rtol(variant)
+        for f in ("sf", "sc"):
+            err = np.abs(g[f] - o[f])
+            assert np.all(err <= rt * np.abs(o[f]) + 1e-300), (f, float(np.max(err / np.maximum(np.abs(o[f]), 1e-300))))
+        scale = np.maximum(np.abs(o["sf"]), p["K"]) + np.abs(o["sc"])
+        for f in ("pf", "pc"):
+            err = np.abs(g[f] - o[f])
+            if p["payoff"] == core.DIGITAL:
+                s = o["sf"] if f == "pf" else o["sc"]
+                near = np.abs(s - p["K"]) <= 4 * rt * np.abs(s)
+                assert np.all((err == 0) | near), f
+            else:
+                assert np.all(err <= 4 * rt * scale), (f, float(np.max(err / scale)))
+    # the sample value
+    if variant in APPROX_ONLY:
+        assert np.array_equal(g["y"], o["y"])
+    else:
+        rt = exact_rtol(variant)
+        scale = np.maximum(np.abs(o["sf"]), p["K"]) + np.abs(o["sc"])
+        tol = 8 * rt * scale
+        if p["payoff"] == core.DIGITAL:
+            near = (np.abs(o["sf"] - p["K"]) <= 4 * rt * o["sf"]) | (np.abs(o["sc"] - p["K"]) <= 4 * rt * np.abs(o["sc"]))
+            tol = np.where(near, 1.0 + 1e-9, tol)
+        if variant in CORR:
+            tol = tol + 2.0**-22 * np.abs(o["y"] - (o["pf"] - o["pc"])) + 1e-30
+        err = np.abs(g["y"] - o["y"])
+        assert np.all(err <= tol), float(np.max(err - tol))

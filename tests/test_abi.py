@@ -1,0 +1,86 @@
+"""The C ABI library builds for sm_103a, loads without a GPU and exports every
+function include/mlmc.h declares; host-only helpers agree with their stated rules."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mlmc.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(mlmc_[a-z0-9_]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if shutil.which("nvcc") is None and not os.path.exists(
+            os.path.join(ROOT, "paper_2502_07123_gb300", "_build", "libmlmc_gb300.so")):
+        pytest.skip("nvcc not available")
+    from paper_2502_07123_gb300 import build
+    build.build()
+    from paper_2502_07123_gb300 import mlmc
+    return mlmc
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("mlmc_level", "mlmc_estimate", "mlmc_level_dump", "mlmc_plan_create", "mlmc_plan_launch",
+                     "mlmc_plan_results", "mlmc_run", "mlmc_strerror"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    L = ctypes.CDLL(lib.LIB_PATH)
+    missing = [n for n in _declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_struct_layouts(lib):
+    assert ctypes.sizeof(lib.Params) == 72
+    assert ctypes.sizeof(lib.Sums) == 72
+    assert ctypes.sizeof(lib.Work) == 40
+    assert lib.SAMPLE_BYTES == 80
+
+
+def test_default_format_matches_input_schedule(lib):
+    from paper_2502_07123_gb300 import workloads as W
+    for over in ({}, {"sigma": 0.4}, {"sigma": 0.1, "r": 0.0}, {"S0": 80.0, "K": 120.0, "T": 2.0},
+                 {"scheme": W.MILSTEIN, "sigma": 0.5, "T": 0.25}):
+        p = W.params(**over)
+        P = lib.make_params(p)
+        for lev in range(0, 21):
+            assert lib.mlmc_default_format(P, lev) == W.default_format(p, lev), (over, lev)
+
+
+def test_strerror_and_version(lib):
+    assert lib.mlmc_strerror(lib.EINVAL) == "invalid argument"
+    assert "sm_103a" in lib.mlmc_version()
+
+
+def test_host_argument_checks(lib):
+    from paper_2502_07123_gb300 import workloads as W
+    P = lib.make_params(W.params())
+    with pytest.raises(lib.MLMCError) as e:
+        lib.mlmc_default_format(P, 21)
+    assert e.value.status == lib.EINVAL
+    with pytest.raises(lib.MLMCError):
+        lib.mlmc_cost_model(7, 1.0)
+    lib.mlmc_cost_model(2, 0.0)  # restores the default
+
+
+def test_no_cpu_fallback(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2502_07123_gb300 import workloads as W
+    P = lib.make_params(W.params())
+    with pytest.raises(lib.MLMCError) as e:
+        lib.mlmc_level(2, 100, P, lib.FP32_EXACT, 1)
+    assert e.value.status == lib.ECUDA
