@@ -235,17 +235,22 @@ def main():
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_value = info["path_steps"] / (statistics.median(e2e_ms) * 1e-3)
 
-    # roofline of the dominant kernel (approximate estimator, fixed point, family 2)
+    # roofline of the dominant kernel: the approximate fixed-point estimator with a
+    # 32-bit S (family 8: levels 0-7 of the workload; level 8 needs a 64-bit S, family 9)
     dom = max(kern_ms, key=lambda f: sum(kern_ms[f]))
     dom_ms = sum(kern_ms[dom]) / len(kern_ms[dom])
-    approx_steps = sum(it["N"] << it["level"] for it in items if it["variant"] == m.FIXED_APPROX)
+    fam_steps = {8: sum(it["N"] << it["level"] for it in items
+                        if it["variant"] == m.FIXED_APPROX and it["level"] <= 7),
+                 2: sum(it["N"] << it["level"] for it in items if it["variant"] == m.FIXED_APPROX)}
     roofline = None
-    if dom == 2:
-        achieved = OPS_APPROX_FIXED_EM * approx_steps / (dom_ms * 1e-3) / 1e12
+    if dom in fam_steps:
+        achieved = OPS_APPROX_FIXED_EM * fam_steps[dom] / (dom_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Top/s",
                     "frac": achieved / ALU_PEAK_TOPS, "traffic": None,
-                    "kernel": "level_kernel<APPROX,fixed,EM,terminal>", "ms_per_launch": dom_ms,
-                    "ops_per_path_step": OPS_APPROX_FIXED_EM}
+                    "kernel": "level_kernel<APPROX,F32,FX32,EM,terminal>" if dom == 8
+                    else "level_kernel<APPROX,F32,FIXED,EM,terminal>",
+                    "ms_per_launch": dom_ms, "ops_per_path_step": OPS_APPROX_FIXED_EM,
+                    "path_steps_per_launch": fam_steps[dom]}
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

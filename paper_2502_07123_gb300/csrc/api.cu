@@ -60,6 +60,7 @@ struct mlmc_plan {
   cudaEvent_t fork = nullptr, t0 = nullptr, t1 = nullptr;
   cudaStream_t last_stream = nullptr;
   bool launched = false;
+  bool borrowed = false;   // device buffers, streams and events belong to the context arena
 };
 
 namespace {
@@ -67,14 +68,29 @@ namespace {
 // ---------------------------------------------------------------------------
 // device context and table cache
 // ---------------------------------------------------------------------------
+// Reusable device buffers, streams and events of the synchronous calls
+// (mlmc_level, mlmc_run, mlmc_estimate), grown on demand.
+struct Arena {
+  ItemDesc *items = nullptr;
+  size_t cap_items = 0;
+  Partial *partials = nullptr;
+  size_t cap_chunks = 0;
+  DevSums *out = nullptr;
+  size_t cap_out = 0;
+  std::vector<cudaStream_t> aux;
+  std::vector<cudaEvent_t> join, kstart, kstop;
+  cudaEvent_t fork = nullptr, t0 = nullptr, t1 = nullptr;
+};
+
 struct Ctx {
   bool inited = false;
+  Arena arena;
   int device = -1;
   int num_sms = 0;
   cudaStream_t st = nullptr;
   std::map<int, std::vector<double>> m1_host;               // d -> Method-1 table (FP64)
   std::map<int, double *> m1_dev;                           // d -> device FP64 table
-  std::map<std::tuple<int, int, int, int>, void *> tables;  // (method, d, rep, fZ) -> device table
+  std::map<std::tuple<int, int, int, int, int>, void *> tables;  // (method, d, rep, fZ, signed) -> table
 };
 Ctx g;
 
@@ -151,9 +167,13 @@ void m3_fit(const std::vector<double> &Z, int d, M3Coef &c) {
   }
 }
 
-mlmc_status get_table(int method, int d, int rep, int fZ, const void **out) {
+// Device table of one representation.  full_signed (method 1 only): all 2^d
+// entries indexed directly by j, as the level kernels use it; otherwise the
+// 2^(d-1) entries of the lower half (parity checks).
+mlmc_status get_table(int method, int d, int rep, int fZ, const void **out, bool full_signed = false) {
   if (rep != REP_FIXED) fZ = 0;
-  auto key = std::make_tuple(method, d, rep, fZ);
+  if (method != 1) full_signed = false;
+  auto key = std::make_tuple(method, d, rep, fZ, full_signed ? 1 : 0);
   auto it = g.tables.find(key);
   if (it != g.tables.end()) { *out = it->second; return MLMC_OK; }
   double *z64 = nullptr;
@@ -162,7 +182,12 @@ mlmc_status get_table(int method, int d, int rep, int fZ, const void **out) {
   if (s != MLMC_OK) return s;
   void *p = nullptr;
   const int n = 1 << (d - 1);
-  if (method == 1) {
+  if (method == 1 && full_signed) {
+    const size_t es = (rep == REP_FP16 || rep == REP_BF16) ? 2 : 4;
+    CK(cudaMalloc(&p, es * 2 * n));
+    CK(launch_m1_signed(z64, d, rep, fZ, p, g.st));
+    CK(cudaStreamSynchronize(g.st));
+  } else if (method == 1) {
     if (rep == REP_FP64) {
       p = z64;
     } else {
@@ -289,6 +314,10 @@ int cost_kind_of(int variant) {
 cudaError_t launch_by_family(int fam, int scheme, int pc, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                              const LaunchArgs &a) {
   switch (fam) {
+    case 8: return launch_approx_fx32(scheme, pc, grid, block, smem, st, a);
+    case 9: return launch_approx_fx64(scheme, pc, grid, block, smem, st, a);
+    case 10: return launch_corr_fx32(scheme, pc, grid, block, smem, st, a);
+    case 11: return launch_corr_fx64(scheme, pc, grid, block, smem, st, a);
     case 0: return launch_exact_f32(scheme, pc, grid, block, smem, st, a);
     case 1: return launch_exact_f64(scheme, pc, grid, block, smem, st, a);
     case 2: return launch_approx_fixed(scheme, pc, grid, block, smem, st, a);
@@ -298,6 +327,89 @@ cudaError_t launch_by_family(int fam, int scheme, int pc, dim3 grid, dim3 block,
     case 6: return launch_corr_f16(scheme, pc, grid, block, smem, st, a);
     default: return launch_corr_bf16(scheme, pc, grid, block, smem, st, a);
   }
+}
+
+int64_t radd_of(int k) { return k > 0 ? (int64_t)1 << (k - 1) : 0; }
+
+// floor(v / 2^k) for a 128-bit value (k >= 0)
+__int128 floor_shift(__int128 v, int k) { return v >> k; }
+
+// Decide whether the fast fixed-point datapath computes exactly the values of
+// the general one for this format: every rounding is a right shift, and the
+// magnitudes of mul1, mul3, sum1 (from the table bound) and of mul2 (given
+// |S| <= lim_S) can never reach their saturation limits, so that only S needs
+// a run-time range check.  Fills ff and tells whether S needs 64 bits.
+bool fast_fixed(const int e[7], const int f[7], int64_t con1, int64_t con1c, int64_t con2, int64_t con3,
+                int64_t zmax, bool milstein, FastFixed &ff, bool &s64) {
+  typedef __int128 I;
+  const int fZ = f[F_Z];
+  if (f[F_CON1] < f[F_MUL1] || f[F_CON1] < f[F_SUM1] || f[F_S] < f[F_MUL2]) return false;
+  const int rs1 = f[F_CON2] + fZ - f[F_MUL1];
+  const int rs3 = f[F_CON1] + 2 * fZ - f[F_MUL1];
+  const int rs_sum1 = f[F_CON1] - f[F_SUM1];
+  const int rs2 = f[F_S] + f[F_SUM1] - f[F_MUL2];
+  if (rs1 < 0 || rs3 < 0 || rs2 < 0 || rs1 > 62 || rs3 > 62 || rs2 > 62 || rs_sum1 > 30) return false;
+  const int shF1 = f[F_CON1] - f[F_MUL1];
+  const int shS = f[F_S] - f[F_MUL2];
+  if (shF1 > 30 || shS > 30) return false;
+  auto lim = [&](int v) { return ((I)1 << (e[v] + f[v])) - 1; };
+  const I zc = 2 * (I)zmax;  // coarse increments are sums of two table values
+  const I r1 = radd_of(rs1), r3 = radd_of(rs3), rsum = radd_of(rs_sum1), r2 = radd_of(rs2);
+  if ((I)con2 * zc + r1 >= ((I)1 << 62)) return false;
+  const I m1a = floor_shift((I)con2 * zc + r1, rs1), m1b = floor_shift(-(I)con2 * zc + r1, rs1);
+  const I mul1_abs = std::max(m1a, -m1b);
+  if (mul1_abs > lim(F_MUL1)) return false;
+  I mul3_abs = 0;
+  if (milstein) {
+    const I one = (I)1 << (2 * fZ);
+    const I zz_max = zc * zc - one, zz_min = -2 * one;
+    if ((I)con3 * zz_max + r3 >= ((I)1 << 62) || zc * zc >= ((I)1 << 62)) return false;
+    const I a = floor_shift((I)con3 * zz_max + r3, rs3), b = floor_shift((I)con3 * zz_min + r3, rs3);
+    mul3_abs = std::max(a < 0 ? -a : a, b < 0 ? -b : b);
+    if (mul3_abs > lim(F_MUL1)) return false;
+  }
+  const I c1max = std::max((I)(con1 < 0 ? -con1 : con1), (I)(con1c < 0 ? -con1c : con1c));
+  const I acc_abs = c1max + rsum + (mul1_abs + mul3_abs) * ((I)1 << shF1);
+  if (acc_abs >= ((I)1 << 31) - 1) return false;
+  const I sum1_abs = floor_shift(acc_abs, rs_sum1) + 1;
+  if (sum1_abs > lim(F_SUM1)) return false;
+  const I limS = lim(F_S);
+  if (limS * sum1_abs + r2 >= ((I)1 << 62)) return false;
+  const I mul2_abs = floor_shift(limS * sum1_abs + r2, rs2) + 1;
+  if (mul2_abs > lim(F_MUL2) || mul2_abs >= ((I)1 << 31)) return false;
+  const I snew = limS + mul2_abs * ((I)1 << shS);
+  if (snew >= ((I)1 << 62)) return false;
+  s64 = !(snew < ((I)1 << 31) - 1);
+  ff.con2 = (int32_t)con2;
+  ff.con3 = (int32_t)con3;
+  ff.con1r = (int32_t)(con1 + (int64_t)rsum);
+  ff.con1cr = (int32_t)(con1c + (int64_t)rsum);
+  ff.mulF1 = 1 << shF1;
+  ff.rs1 = rs1; ff.rs3 = rs3; ff.rs_sum1 = rs_sum1; ff.rs2 = rs2;
+  ff.mulS = 1 << shS;
+  ff.radd1 = (int64_t)r1; ff.radd3 = (int64_t)r3; ff.radd2 = (int64_t)r2;
+  ff.mfine = (int64_t)1 << (2 * fZ);
+  ff.mcoarse = (int64_t)2 << (2 * fZ);
+  ff.limS = (int64_t)limS;
+  return true;
+}
+
+// Largest |table value| in Z's fixed-point format, as the kernels evaluate it.
+int64_t table_zmax_fixed(const std::vector<double> &Z, int d, int method, int fZ) {
+  int64_t zmax = 0;
+  if (method == 1) {
+    for (double v : Z) zmax = std::max<int64_t>(zmax, std::llabs((int64_t)std::floor(std::ldexp(v, fZ) + 0.5)));
+    return zmax;
+  }
+  M3Coef c;
+  m3_fit(Z, d, c);
+  const int sh = M3_FRAC - fZ;
+  for (int k = 0; k < (1 << (d - 1)); ++k) {
+    const int cls = k < 2 ? 0 : 31 - __builtin_clz((unsigned)k);
+    const int64_t t = c.A[cls] + c.B[cls] * (int64_t)k;
+    zmax = std::max<int64_t>(zmax, std::llabs((t + ((int64_t)1 << (sh - 1))) >> sh));
+  }
+  return zmax;
 }
 
 uint16_t half_bits(double x) { return __half_as_ushort(__double2half(x)); }
@@ -364,6 +476,7 @@ mlmc_status build_item(const mlmc_work &w, int out_index, int threads, int steps
   unit = 0;
   exact_int = 0;
   b.smem = 0;
+  bool fast = false, fast64 = false;
   if (approx) {
     const bool fixed = (v == MLMC_FIXED_APPROX || v == MLMC_NESTED_CORR_FIXED);
     const bool bf = (v == MLMC_BF16_APPROX || v == MLMC_NESTED_CORR_BF16);
@@ -410,9 +523,12 @@ mlmc_status build_item(const mlmc_work &w, int out_index, int threads, int steps
       double *z64;
       const std::vector<double> *zh;
       if ((s = m1_table(p->icdf_bits, &z64, &zh)) != MLMC_OK) return s;
-      const double zmax = std::fabs((*zh)[0]);
-      if (std::floor(std::ldexp(zmax, fZ) + 0.5) > std::ldexp(1.0, e[F_Z] + fZ) - 1.0) return MLMC_EOVERFLOW;
+      const int64_t zmax = table_zmax_fixed(*zh, p->icdf_bits, p->icdf_method, fZ);
+      if ((double)zmax > std::ldexp(1.0, e[F_Z] + fZ) - 1.0) return MLMC_EOVERFLOW;
       unit = f[F_S] + (p->payoff == MLMC_ASIAN ? lev + 1 : 0);
+      bool s64 = false;
+      fast = fast_fixed(e, f, con1, con1c, con2, con3, zmax, p->scheme == MLMC_MILSTEIN, it.ff, s64);
+      fast64 = s64;
     } else {
       uint16_t (*cv)(double) = bf ? bf16_bits : half_bits;
       it.h_c1 = cv(rh);
@@ -423,15 +539,19 @@ mlmc_status build_item(const mlmc_work &w, int out_index, int threads, int steps
       unit = 24;
     }
     const void *tab = nullptr;
-    mlmc_status s = get_table(p->icdf_method, p->icdf_bits, rep, fZ, &tab);
+    mlmc_status s = get_table(p->icdf_method, p->icdf_bits, rep, fZ, &tab, true);
     if (s != MLMC_OK) return s;
     it.ztab = tab;
-    b.smem = p->icdf_method == 1 ? (size_t)(1 << (p->icdf_bits - 1)) * (fixed ? 4 : 2) : sizeof(M3Coef);
+    b.smem = p->icdf_method == 1 ? (size_t)(1 << p->icdf_bits) * (fixed ? 4 : 2) : sizeof(M3Coef);
     exact_int = (v == MLMC_FIXED_APPROX || v == MLMC_FP16_APPROX || v == MLMC_BF16_APPROX) ? 1 : 0;
   }
   it.unit = unit;
   it.unit_scale = std::ldexp(1.0f, -unit);
   b.family = family_of(v);
+  if (fast) {
+    if (b.family == 2) b.family = fast64 ? 9 : 8;
+    else if (b.family == 5) b.family = fast64 ? 11 : 10;
+  }
   b.scheme = p->scheme;
   b.pc = p->payoff == MLMC_ASIAN ? PC_ASIAN : (p->payoff == MLMC_LOOKBACK ? PC_LOOKBACK : PC_TERMINAL);
   return MLMC_OK;
@@ -485,6 +605,12 @@ __global__ void finalize_kernel(const ItemDesc *items, int n_items, const Partia
 }
 
 void free_plan_device(mlmc_plan *pl) {
+  if (pl->borrowed) {
+    pl->d_items = nullptr; pl->d_partials = nullptr; pl->d_out = nullptr;
+    pl->aux.clear(); pl->join.clear(); pl->kstart.clear(); pl->kstop.clear();
+    pl->fork = pl->t0 = pl->t1 = nullptr;
+    return;
+  }
   if (pl->d_items) cudaFree(pl->d_items);
   if (pl->d_partials) cudaFree(pl->d_partials);
   if (pl->d_out) cudaFree(pl->d_out);
@@ -501,8 +627,38 @@ void free_plan_device(mlmc_plan *pl) {
   pl->fork = pl->t0 = pl->t1 = nullptr;
 }
 
+template <class T>
+bool grow(T *&p, size_t &cap, size_t need) {
+  if (need <= cap) return true;
+  if (p) cudaFree(p);
+  p = nullptr;
+  cap = 0;
+  const size_t n = std::max(need, cap * 2);
+  if (cudaMalloc(&p, sizeof(T) * n) != cudaSuccess) return false;
+  cap = n;
+  return true;
+}
+
+bool arena_events(Arena &A, size_t launches) {
+  if (!A.t0) {
+    if (cudaEventCreate(&A.t0) != cudaSuccess || cudaEventCreate(&A.t1) != cudaSuccess ||
+        cudaEventCreateWithFlags(&A.fork, cudaEventDisableTiming) != cudaSuccess)
+      return false;
+  }
+  while (A.aux.size() < launches) {
+    cudaStream_t st;
+    cudaEvent_t j, a, b;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&j, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+      return false;
+    A.aux.push_back(st); A.join.push_back(j); A.kstart.push_back(a); A.kstop.push_back(b);
+  }
+  return true;
+}
+
 mlmc_status plan_create_impl(mlmc_plan **out, const mlmc_work *work, int n_work, uint64_t seed,
-                             const mlmc_tuning *tuning, void *const *dumps) {
+                             const mlmc_tuning *tuning, void *const *dumps, Arena *arena = nullptr) {
   if (!out || !work || n_work <= 0) return MLMC_EINVAL;
   mlmc_status s = ensure_ctx();
   if (s != MLMC_OK) return s;
@@ -535,13 +691,13 @@ mlmc_status plan_create_impl(mlmc_plan **out, const mlmc_work *work, int n_work,
     if (built[i].it.n_chunks == 0) { empty.push_back(i); continue; }
     groups[std::make_tuple(built[i].family, built[i].scheme, built[i].pc)].push_back(i);
   }
+  // launches are ordered by their most expensive CTA, so that the longest
+  // chains (deep levels, exact paths) start first and the rest fill in
   std::vector<std::pair<double, std::vector<int>>> order;
   for (auto &kv : groups) {
     auto &v = kv.second;
     std::stable_sort(v.begin(), v.end(), [&](int a, int b) { return built[a].chunk_cost > built[b].chunk_cost; });
-    double tot = 0.0;
-    for (int i : v) tot += built[i].chunk_cost * built[i].it.n_chunks;
-    order.push_back({tot, v});
+    order.push_back({built[v[0]].chunk_cost, v});
   }
   std::stable_sort(order.begin(), order.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
   uint32_t chunk = 0;
@@ -571,6 +727,31 @@ mlmc_status plan_create_impl(mlmc_plan **out, const mlmc_work *work, int n_work,
   pl->total_chunks = chunk;
   make_round_keys(seed, pl->rk);
   const size_t ni = pl->items.size();
+  if (arena) {
+    Arena &A = *arena;
+    const size_t nl = pl->launches.size();
+    if (!grow(A.items, A.cap_items, ni) || !grow(A.partials, A.cap_chunks, std::max<size_t>(1, chunk)) ||
+        !grow(A.out, A.cap_out, (size_t)n_work) || !arena_events(A, nl)) {
+      delete pl;
+      return MLMC_ENOMEM;
+    }
+    pl->borrowed = true;
+    pl->d_items = A.items; pl->d_partials = A.partials; pl->d_out = A.out;
+    pl->fork = A.fork; pl->t0 = A.t0; pl->t1 = A.t1;
+    if (nl > 1) {
+      pl->aux.assign(A.aux.begin(), A.aux.begin() + nl);
+      pl->join.assign(A.join.begin(), A.join.begin() + nl);
+    }
+    pl->kstart.assign(A.kstart.begin(), A.kstart.begin() + nl);
+    pl->kstop.assign(A.kstop.begin(), A.kstop.begin() + nl);
+    if (cudaMemcpyAsync(pl->d_items, pl->items.data(), sizeof(ItemDesc) * ni, cudaMemcpyHostToDevice, g.st) !=
+        cudaSuccess) {
+      delete pl;
+      return MLMC_ECUDA;
+    }
+    *out = pl;
+    return MLMC_OK;
+  }
   if (cudaMalloc(&pl->d_items, sizeof(ItemDesc) * ni) != cudaSuccess ||
       cudaMalloc(&pl->d_partials, sizeof(Partial) * std::max<uint32_t>(1, chunk)) != cudaSuccess ||
       cudaMalloc(&pl->d_out, sizeof(DevSums) * n_work) != cudaSuccess) {
@@ -676,8 +857,15 @@ mlmc_status plan_results_impl(mlmc_plan *pl, mlmc_sums *out) {
 mlmc_status run_sync(const mlmc_work *work, int n_work, uint64_t seed, const mlmc_tuning *tuning,
                      void *const *dumps, mlmc_sums *out, cudaStream_t st) {
   mlmc_plan *pl = nullptr;
-  mlmc_status s = plan_create_impl(&pl, work, n_work, seed, tuning, dumps);
+  mlmc_status s = plan_create_impl(&pl, work, n_work, seed, tuning, dumps, &g.arena);
   if (s != MLMC_OK) return s;
+  // the work list was copied on the context stream: order the launch after it
+  if (st != g.st) {
+    if (cudaEventRecord(g.arena.fork, g.st) != cudaSuccess || cudaStreamWaitEvent(st, g.arena.fork, 0) != cudaSuccess) {
+      delete pl;
+      return MLMC_ECUDA;
+    }
+  }
   s = plan_launch_impl(pl, st);
   if (s == MLMC_OK) s = plan_results_impl(pl, out);
   free_plan_device(pl);

@@ -11,7 +11,10 @@ enum Est : int { EST_EXACT = 0, EST_APPROX = 1, EST_CORR = 2 };
 // exact-path precision
 enum Xp : int { XP_NONE = 0, XP_F32 = 1, XP_F64 = 2 };
 // approximate-path arithmetic
-enum Ap : int { AP_NONE = 0, AP_FIXED = 1, AP_F16 = 2, AP_BF16 = 3 };
+// AP_FIXED is the general fixed-point datapath (64-bit, saturating every
+// variable); AP_FX32 / AP_FX64 are the fast datapath for formats whose bounds
+// the host has proven (32-bit values, S in 32 or 64 bits, only S range-checked).
+enum Ap : int { AP_NONE = 0, AP_FIXED = 1, AP_F16 = 2, AP_BF16 = 3, AP_FX32 = 4, AP_FX64 = 5 };
 // payoff classes that need different path functionals
 enum PayClass : int { PC_TERMINAL = 0, PC_ASIAN = 1, PC_LOOKBACK = 2 };
 
@@ -38,6 +41,20 @@ struct FixedConsts {
   int32_t fS;
 };
 
+// Constants of the fast fixed-point step (host-proven: no variable but S can
+// leave its format; S is checked every step).  Every rounding adds its half
+// unit before an arithmetic right shift; left alignments are multiplications.
+struct FastFixed {
+  int32_t con2, con3;
+  int32_t con1r, con1cr;     // con1, con1_c plus the rounding half unit of sum1
+  int32_t mulF1;             // 2^(f_con1 - f_mul1): mul1, mul3 onto the sum1 accumulation grid
+  int32_t rs1, rs3, rs_sum1, rs2;
+  int32_t mulS;              // 2^(f_S - f_mul2)
+  int64_t radd1, radd3, radd2;
+  int64_t mfine, mcoarse;    // 1 and 2 in units 2^-2fZ (Milstein)
+  int64_t limS;
+};
+
 struct ItemDesc {
   // sample range and chunking
   uint64_t first, N;       // samples [first, first + N)
@@ -57,6 +74,7 @@ struct ItemDesc {
   double c1d, c2d, c1cd, c3d, S0d, Kd;
   // approximate path
   FixedConsts fx;
+  FastFixed ff;
   uint16_t h_c1, h_c1c, h_c2, h_c3, h_S0, h_pad;  // binary16 / bfloat16 bit patterns
   const void *ztab;        // device table for method 1 (int32 / half bits), or method-3 coefficients
   // optional per-sample dump (device), indexed by sample - first

@@ -1,0 +1,10 @@
+// Level-kernel family: estimator EST_CORR, exact precision XP_F32, approximate arithmetic AP_FX32.
+#include "kernels.h"
+#include "level_kernel.cuh"
+
+namespace mlmc {
+cudaError_t launch_corr_fx32(int scheme, int pc, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                      const LaunchArgs &a) {
+  return launch_family<EST_CORR, XP_F32, AP_FX32>(scheme, pc, grid, block, smem, st, a);
+}
+}  // namespace mlmc

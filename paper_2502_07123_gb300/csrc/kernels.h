@@ -14,5 +14,9 @@ MLMC_FAMILY(launch_approx_bf16)
 MLMC_FAMILY(launch_corr_fixed)
 MLMC_FAMILY(launch_corr_f16)
 MLMC_FAMILY(launch_corr_bf16)
+MLMC_FAMILY(launch_approx_fx32)
+MLMC_FAMILY(launch_approx_fx64)
+MLMC_FAMILY(launch_corr_fx32)
+MLMC_FAMILY(launch_corr_fx64)
 #undef MLMC_FAMILY
 }  // namespace mlmc

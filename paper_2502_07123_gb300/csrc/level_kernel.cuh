@@ -11,6 +11,8 @@
 // lives in shared memory.  The only global-memory traffic is the work-item
 // descriptor, the table, one Partial record per CTA and the optional dump.
 #pragma once
+#include <type_traits>
+
 #include "device_common.cuh"
 #include "mlmc.h"
 
@@ -30,15 +32,20 @@ struct LevelSim {
   static constexpr bool HAS_EXACT = (EST != EST_APPROX);
   static constexpr bool HAS_APPROX = (EST != EST_EXACT);
   static constexpr bool MIL = (SCHEME == 1);
+  static constexpr bool FAST = (AP == AP_FX32 || AP == AP_FX64);
+  static constexpr bool FIXED = (AP == AP_FIXED || FAST);
+  static constexpr bool HALF = (AP == AP_F16 || AP == AP_BF16);
+  using AS = typename std::conditional<AP == AP_FX32, int32_t, int64_t>::type;  // fixed-point S
   using X = typename XType<XP>::T;
   using H = typename HType<AP>::T;
   using HO = HalfOps<H>;
 
   // ---- per-item constants (registers) ----
-  int level, nsteps, payoff, d, method;
+  int level, nsteps, payoff, d, dshift, method;
   X c1, c2, c1c, c3, S0, K;
   // fixed point
   FixedConsts fx;
+  FastFixed ff;
   // half
   H hc1, hc1c, hc2, hc3, hS0;
   float K32;
@@ -47,7 +54,9 @@ struct LevelSim {
 
   // ---- per-sample state ----
   X S, Sc, zprev, accF, accC, minF, minC;
-  int64_t aS, aSc, aaccF, aaccC, aminF, aminC;
+  AS aS, aSc, aminF, aminC;
+  bool satb;
+  int64_t aaccF, aaccC;
   int32_t azprev;
   H hS, hSc, hzprev, hminF, hminC;
   float haccF, haccC;
@@ -58,14 +67,16 @@ struct LevelSim {
     nsteps = 1 << it.level;
     payoff = it.payoff;
     d = it.d;
+    dshift = 32 - it.d;
     method = it.method;
     if constexpr (XP == XP_F64) {
       c1 = it.c1d; c2 = it.c2d; c1c = it.c1cd; c3 = it.c3d; S0 = it.S0d; K = it.Kd;
     } else {
       c1 = it.c1f; c2 = it.c2f; c1c = it.c1cf; c3 = it.c3f; S0 = it.S0f; K = it.Kf;
     }
-    if constexpr (AP == AP_FIXED) fx = it.fx;
-    if constexpr (AP == AP_F16 || AP == AP_BF16) {
+    if constexpr (FIXED) fx = it.fx;
+    if constexpr (FAST) ff = it.ff;
+    if constexpr (HALF) {
       hc1 = HO::from_bits(it.h_c1); hc1c = HO::from_bits(it.h_c1c);
       hc2 = HO::from_bits(it.h_c2); hc3 = HO::from_bits(it.h_c3);
       hS0 = HO::from_bits(it.h_S0);
@@ -80,10 +91,11 @@ struct LevelSim {
       S = S0; Sc = S0; zprev = X(0);
       accF = X(0.5) * S0; accC = accF; minF = S0; minC = S0;
     }
-    if constexpr (AP == AP_FIXED) {
-      aS = fx.S0; aSc = fx.S0; aaccF = 0; aaccC = 0; aminF = fx.S0; aminC = fx.S0; azprev = 0;
+    if constexpr (FIXED) {
+      aS = (AS)fx.S0; aSc = (AS)fx.S0; aaccF = 0; aaccC = 0; aminF = aS; aminC = aS; azprev = 0;
+      satb = false;
     }
-    if constexpr (AP == AP_F16 || AP == AP_BF16) {
+    if constexpr (HALF) {
       hS = hS0; hSc = hS0; hzprev = HO::from_f(0.0f); hminF = hS0; hminC = hS0;
       haccF = __fmul_rn(0.5f, HO::to_f(hS0)); haccC = haccF;
     }
@@ -111,6 +123,30 @@ struct LevelSim {
     return saturate(requant(s2, fx.q_S), fx.lim[6], sat);
   }
 
+  // ---- fast fixed-point Algorithm-1 step (same values as fx_step while S stays in range) ----
+  __device__ __forceinline__ AS ff_step(AS s, int32_t z, int32_t c1r, int64_t m) {
+    const int32_t mul1 = (int32_t)(((int64_t)ff.con2 * z + ff.radd1) >> ff.rs1);
+    int32_t acc = c1r + mul1 * ff.mulF1;
+    if constexpr (MIL) {
+      const int64_t zz = (int64_t)z * z - m;
+      const int32_t mul3 = (int32_t)((ff.con3 * zz + ff.radd3) >> ff.rs3);
+      acc += mul3 * ff.mulF1;
+    }
+    const int32_t sum1 = acc >> ff.rs_sum1;
+    if constexpr (AP == AP_FX32) {
+      const int32_t mul2 = (int32_t)(((int64_t)s * sum1 + ff.radd2) >> ff.rs2);
+      s = (int32_t)((uint32_t)s + (uint32_t)mul2 * (uint32_t)ff.mulS);
+    } else {
+      const int32_t mul2 = (int32_t)((int64_t)((uint64_t)s * (uint64_t)(int64_t)sum1 + (uint64_t)ff.radd2) >> ff.rs2);
+      s = (int64_t)((uint64_t)s + (uint64_t)((int64_t)mul2 * ff.mulS));
+    }
+    // saturation of S (the only variable the host could not bound)
+    const AS lim = (AS)ff.limS;
+    const AS c = s > lim ? lim : (s < -lim ? -lim : s);
+    satb = satb || (c != s);
+    return c;
+  }
+
   // ---- half-precision step (one rounding per operation) ----
   __device__ __forceinline__ H h_step(H s, H z, H cc1, H mh) const {
     const H mul1 = HO::mul(hc2, z);
@@ -125,11 +161,13 @@ struct LevelSim {
     return HO::add(s, mul2);
   }
 
-  __device__ __forceinline__ int32_t fixed_z(ApproxIndex ai) const {
+  // Approximate Normal of J in Z's fixed-point format: Method 1 reads the
+  // signed table at j = top d bits of J; Method 3 evaluates the class line.
+  __device__ __forceinline__ int32_t fixed_z(uint32_t J) const {
+    if (method == 1) return ((const int32_t *)smem_tab)[J >> dshift];
+    const ApproxIndex ai = approx_index(J, d);
     int32_t v;
-    if (method == 1) {
-      v = ((const int32_t *)smem_tab)[ai.idx];
-    } else {
+    {
       const M3Coef *m3 = (const M3Coef *)smem_tab;
       const int c = m3_class(ai.idx);
       const int64_t t = m3->A[c] + m3->B[c] * (int64_t)ai.idx;
@@ -139,11 +177,11 @@ struct LevelSim {
     return ai.neg ? -v : v;
   }
 
-  __device__ __forceinline__ H half_z(ApproxIndex ai) const {
+  __device__ __forceinline__ H half_z(uint32_t J) const {
+    if (method == 1) return HO::from_bits(((const uint16_t *)smem_tab)[J >> dshift]);
+    const ApproxIndex ai = approx_index(J, d);
     H v;
-    if (method == 1) {
-      v = HO::from_bits(((const uint16_t *)smem_tab)[ai.idx]);
-    } else {
+    {
       const M3Coef *m3 = (const M3Coef *)smem_tab;
       const int c = m3_class(ai.idx);
       v = HO::from_f(fmaf(m3->b[c], (float)ai.idx, m3->a[c]));
@@ -151,7 +189,8 @@ struct LevelSim {
     return ai.neg ? HO::neg(v) : v;
   }
 
-  // One fine step i driven by J (and the coarse step when i is odd).
+  // One fine step i driven by J, and the coarse step after odd i (levels >= 1).
+  template <bool COARSE>
   __device__ __forceinline__ void step(uint32_t J, int i) {
     if constexpr (HAS_EXACT) {
       X z;
@@ -160,7 +199,7 @@ struct LevelSim {
       if constexpr (PC == PC_ASIAN) { if (i > 0) accF = accF + S; }
       S = fma(S, exact_inc(z, c1, X(1)), S);
       if constexpr (PC == PC_LOOKBACK) minF = fmin(minF, S);
-      if (level > 0) {
+      if constexpr (COARSE) {
         if (i & 1) {
           const X zc = zprev + z;
           if constexpr (PC == PC_ASIAN) { if (i > 1) accC = accC + Sc; }
@@ -172,27 +211,28 @@ struct LevelSim {
       }
     }
     if constexpr (HAS_APPROX) {
-      const ApproxIndex ai = approx_index(J, d);
-      if constexpr (AP == AP_FIXED) {
-        const int32_t z = fixed_z(ai);
+      if constexpr (FIXED) {
+        const int32_t z = fixed_z(J);
         if constexpr (PC == PC_ASIAN) { if (i > 0) aaccF += aS; }
-        aS = fx_step(aS, z, fx.con1A, 1);
+        if constexpr (FAST) aS = ff_step(aS, z, ff.con1r, ff.mfine);
+        else aS = fx_step(aS, z, fx.con1A, 1);
         if constexpr (PC == PC_LOOKBACK) aminF = aS < aminF ? aS : aminF;
-        if (level > 0) {
+        if constexpr (COARSE) {
           if (i & 1) {
             if constexpr (PC == PC_ASIAN) { if (i > 1) aaccC += aSc; }
-            aSc = fx_step(aSc, azprev + z, fx.con1cA, 2);
+            if constexpr (FAST) aSc = ff_step(aSc, azprev + z, ff.con1cr, ff.mcoarse);
+            else aSc = fx_step(aSc, azprev + z, fx.con1cA, 2);
             if constexpr (PC == PC_LOOKBACK) aminC = aSc < aminC ? aSc : aminC;
           } else {
             azprev = z;
           }
         }
       } else {
-        const H z = half_z(ai);
+        const H z = half_z(J);
         if constexpr (PC == PC_ASIAN) { if (i > 0) haccF = __fadd_rn(haccF, HO::to_f(hS)); }
         hS = h_step(hS, z, hc1, HO::from_f(1.0f));
         if constexpr (PC == PC_LOOKBACK) hminF = HO::to_f(hS) < HO::to_f(hminF) ? hS : hminF;
-        if (level > 0) {
+        if constexpr (COARSE) {
           if (i & 1) {
             const H zc = HO::add(hzprev, z);
             if constexpr (PC == PC_ASIAN) { if (i > 1) haccC = __fadd_rn(haccC, HO::to_f(hSc)); }
@@ -258,7 +298,7 @@ struct LevelSim {
   template <class Acc>
   __device__ __forceinline__ void finish(Acc &acc, bool valid, mlmc_sample_rec *dump) {
     X pf = X(0), pc = X(0);
-    int64_t qf = 0, qc = 0;
+    int64_t qf = 0, qc = 0, afS = 0, acS = 0;
     if constexpr (HAS_EXACT) {
       pf = exact_payoff(S, accF, minF, nsteps);
       if (level > 0) pc = exact_payoff(Sc, accC, minC, nsteps >> 1);
@@ -266,6 +306,15 @@ struct LevelSim {
     if constexpr (AP == AP_FIXED) {
       qf = fixed_payoff(aS, aaccF, aminF, nsteps, false);
       if (level > 0) qc = fixed_payoff(aSc, aaccC, aminC, nsteps >> 1, true);
+      afS = aS;
+      acS = aSc;
+    }
+    if constexpr (FAST) {
+      qf = fixed_payoff(aS, aaccF, aminF, nsteps, false);
+      if (level > 0) qc = fixed_payoff(aSc, aaccC, aminC, nsteps >> 1, true);
+      afS = aS;
+      acS = aSc;
+      sat = satb ? 1u : 0u;
     }
     if constexpr (AP == AP_F16 || AP == AP_BF16) {
       if constexpr (HAS_APPROX) {
@@ -281,7 +330,8 @@ struct LevelSim {
       ydump = (double)y;
     } else if constexpr (EST == EST_APPROX) {
       const int64_t yi = qf - qc;
-      acc.add_int(yi);
+      if constexpr (AP == AP_FX32 && PC == PC_TERMINAL) acc.add_int32((int32_t)yi);  // |Y| < 2^31 here
+      else acc.add_int(yi);
       ydump = (double)yi * (double)unit_scale;
     } else {
       const float yx = (float)(pf - pc);
@@ -296,10 +346,10 @@ struct LevelSim {
       r.pf = (double)pf; r.pc = (double)pc;
       r.sf = HAS_EXACT ? (double)S : 0.0;
       r.sc = (HAS_EXACT && level > 0) ? (double)Sc : 0.0;
-      if constexpr (AP == AP_FIXED) {
-        r.af = ldexp((double)aS, -fx.fS);
-        r.ac = level > 0 ? ldexp((double)aSc, -fx.fS) : 0.0;
-      } else if constexpr (AP == AP_F16 || AP == AP_BF16) {
+      if constexpr (FIXED) {
+        r.af = ldexp((double)afS, -fx.fS);
+        r.ac = level > 0 ? ldexp((double)acS, -fx.fS) : 0.0;
+      } else if constexpr (HALF) {
         r.af = HAS_APPROX ? (double)HO::to_f(hS) : 0.0;
         r.ac = (HAS_APPROX && level > 0) ? (double)HO::to_f(hSc) : 0.0;
       } else {
@@ -327,6 +377,10 @@ struct ThreadAcc {
   __device__ __forceinline__ void add_int(int64_t y) {
     isum += y;
     add_square(q_lo, q_hi, y);
+  }
+  __device__ __forceinline__ void add_int32(int32_t y) {
+    isum += y;
+    add_u128(q_lo, q_hi, (uint64_t)((int64_t)y * y), 0);
   }
   template <class T>
   __device__ __forceinline__ void add_real(T y) {
@@ -404,8 +458,8 @@ level_kernel(const __grid_constant__ LaunchArgs args) {
   // stage the approximate-Normal table in shared memory
   if constexpr (AP != AP_NONE) {
     if (it.method == 1) {
-      const int n = 1 << (it.d - 1);
-      if constexpr (AP == AP_FIXED) {
+      const int n = 1 << it.d;
+      if constexpr (AP == AP_FIXED || AP == AP_FX32 || AP == AP_FX64) {
         const int32_t *src = (const int32_t *)it.ztab;
         for (int k = threadIdx.x; k < n; k += blockDim.x) ((int32_t *)smem_tab)[k] = src[k];
       } else {
@@ -443,38 +497,43 @@ level_kernel(const __grid_constant__ LaunchArgs args) {
         const uint64_t q = s * calls + c;
         const uint4 w = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), ctr_hi.z, ctr_hi.w), args.rk);
         const int i0 = (int)(c << 2);
-        sim.step(w.x, i0);
-        sim.step(w.y, i0 + 1);
-        sim.step(w.z, i0 + 2);
-        sim.step(w.w, i0 + 3);
+        sim.template step<true>(w.x, i0);
+        sim.template step<true>(w.y, i0 + 1);
+        sim.template step<true>(w.z, i0 + 2);
+        sim.template step<true>(w.w, i0 + 3);
       }
       const bool valid = s >= first && s < last;
       sim.finish(acc, valid, dump && valid ? dump + (s - first) : nullptr);
     } else if (lev == 1) {
       const uint4 w = philox4x32_10(make_uint4((uint32_t)g, (uint32_t)(g >> 32), ctr_hi.z, ctr_hi.w), args.rk);
       const uint64_t s0 = 2 * g;
+      // samples s0 + k are valid for k in [klo, khi)
+      const int klo = s0 >= first ? 0 : (int)min(first - s0, (uint64_t)2);
+      const int khi = last <= s0 ? 0 : (int)min(last - s0, (uint64_t)2);
       sim.begin();
-      sim.step(w.x, 0);
-      sim.step(w.y, 1);
+      sim.template step<true>(w.x, 0);
+      sim.template step<true>(w.y, 1);
       {
-        const bool valid = s0 >= first && s0 < last;
+        const bool valid = 0 >= klo && 0 < khi;
         sim.finish(acc, valid, dump && valid ? dump + (s0 - first) : nullptr);
       }
       sim.begin();
-      sim.step(w.z, 0);
-      sim.step(w.w, 1);
+      sim.template step<true>(w.z, 0);
+      sim.template step<true>(w.w, 1);
       {
-        const bool valid = s0 + 1 >= first && s0 + 1 < last;
+        const bool valid = 1 >= klo && 1 < khi;
         sim.finish(acc, valid, dump && valid ? dump + (s0 + 1 - first) : nullptr);
       }
     } else {
       const uint4 w = philox4x32_10(make_uint4((uint32_t)g, (uint32_t)(g >> 32), ctr_hi.z, ctr_hi.w), args.rk);
       const uint64_t s0 = 4 * g;
+      const int klo = s0 >= first ? 0 : (int)min(first - s0, (uint64_t)4);
+      const int khi = last <= s0 ? 0 : (int)min(last - s0, (uint64_t)4);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         sim.begin();
-        sim.step(word_of(w, k), 0);
-        const bool valid = s0 + k >= first && s0 + k < last;
+        sim.template step<false>(word_of(w, k), 0);
+        const bool valid = k >= klo && k < khi;
         sim.finish(acc, valid, dump && valid ? dump + (s0 + k - first) : nullptr);
       }
     }

@@ -45,6 +45,39 @@ __global__ void m1_convert_kernel(const double *z, int n, int rep, int fZ, void 
   }
 }
 
+// Method-1 table over all 2^d values of j (the top d bits of J), as the level
+// kernels index it: entry j < 2^(d-1) is the rounded Z_j, entry j >= 2^(d-1)
+// the negated rounded Z_{2^d-1-j} (the mirrored interval, Sec. 3.1).
+__global__ void m1_signed_kernel(const double *z, int d, int rep, int fZ, void *out) {
+  const int half = 1 << (d - 1);
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= 2 * half) return;
+  const bool neg = j >= half;
+  const double v = z[neg ? 2 * half - 1 - j : j];
+  switch (rep) {
+    case REP_FP16: {
+      const __half h = __double2half(v);
+      ((uint16_t *)out)[j] = __half_as_ushort(neg ? __hneg(h) : h);
+      break;
+    }
+    case REP_BF16: {
+      const __nv_bfloat16 h = __double2bfloat16(v);
+      ((uint16_t *)out)[j] = __bfloat16_as_ushort(neg ? __hneg(h) : h);
+      break;
+    }
+    case REP_FIXED: {
+      const int32_t q = (int32_t)floor(ldexp(v, fZ) + 0.5);
+      ((int32_t *)out)[j] = neg ? -q : q;
+      break;
+    }
+    default: {
+      const float f = (float)v;
+      ((float *)out)[j] = neg ? -f : f;
+      break;
+    }
+  }
+}
+
 // Values of every table index as the level kernels see them (for parity tests).
 __global__ void table_values_kernel(int method, int d, int rep, int fZ, const void *tab, double *out) {
   const int n = 1 << (d - 1);
@@ -86,6 +119,11 @@ cudaError_t launch_m1_table(int d, double *out, cudaStream_t st) {
 }
 cudaError_t launch_m1_convert(const double *z, int n, int rep, int fZ, void *out, cudaStream_t st) {
   m1_convert_kernel<<<(n + 127) / 128, 128, 0, st>>>(z, n, rep, fZ, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_m1_signed(const double *z, int d, int rep, int fZ, void *out, cudaStream_t st) {
+  const int n = 1 << d;
+  m1_signed_kernel<<<(n + 127) / 128, 128, 0, st>>>(z, d, rep, fZ, out);
   return cudaGetLastError();
 }
 cudaError_t launch_table_values(int method, int d, int rep, int fZ, const void *tab, double *out,

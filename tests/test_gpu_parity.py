@@ -46,11 +46,12 @@ def test_icdf_tables_bit_exact(m, d, method):
             bad = np.nonzero(g != o)[0]
             assert bad.size == 0, (name, fZ, bad[:4], g[bad[:4]], o[bad[:4]])
     if method == 1:
-        # FP64 values: GPU normcdfinv / expm1 against the 40-digit closed form
+        # FP64 values: GPU normcdfinv / expm1 against the 40-digit closed form.  The
+        # difference of adjacent quantiles loses about d bits, so the bound scales with 2^d.
         g = m.mlmc_icdf_table(1, d, m.REP_FP64)
         o = tables.m1_fp64(d)
         rel = np.abs(g - o) / np.abs(o)
-        assert np.max(rel) <= 1e-13, float(np.max(rel))
+        assert np.max(rel) <= 2.0**d * 1e-15, float(np.max(rel))
 
 
 VARIANTS = [core.FP64_EXACT, core.FP32_EXACT, core.FP16_APPROX, core.BF16_APPROX, core.FIXED_APPROX,
