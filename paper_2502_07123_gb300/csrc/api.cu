@@ -455,6 +455,10 @@ mlmc_status build_item(const mlmc_work &w, int out_index, int threads, int steps
   it.g0 = w.first_sample / spc;
   it.g1 = w.N == 0 ? it.g0 : (w.first_sample + w.N + spc - 1) / spc;
   const uint64_t groups = it.g1 - it.g0;
+  // groups whose samples all lie in [first, first + N)
+  it.gf0 = (w.first_sample + spc - 1) / spc;
+  it.gf1 = (w.first_sample + w.N) / spc;
+  if (it.gf1 < it.gf0) it.gf1 = it.gf0;
   uint64_t G = std::max<uint64_t>(1, (uint64_t)steps_per_thread / steps_per_group);
   const uint64_t min_ctas = 4ULL * (uint64_t)std::max(1, g.num_sms);
   const uint64_t cap = std::max<uint64_t>(1, (groups + (uint64_t)threads * min_ctas - 1) / ((uint64_t)threads * min_ctas));
@@ -529,6 +533,13 @@ mlmc_status build_item(const mlmc_work &w, int out_index, int threads, int steps
       bool s64 = false;
       fast = fast_fixed(e, f, con1, con1c, con2, con3, zmax, p->scheme == MLMC_MILSTEIN, it.ff, s64);
       fast64 = s64;
+      if (fast && !s64) {
+        // terminal payoffs are below max(lim_S, 2^f_S) in magnitude: one thread's sum of
+        // squares stays below 2^64 if samples_per_thread * ymax^2 < 2^64
+        const double ymax = std::max(std::ldexp(1.0, e[F_S] + f[F_S]), std::ldexp(1.0, f[F_S]));
+        const double per_thread = (double)it.groups_per_thread * (double)spc;
+        it.ff.narrow_sq = per_thread * ymax * ymax < 0x1p63 ? 1 : 0;
+      }
     } else {
       uint16_t (*cv)(double) = bf ? bf16_bits : half_bits;
       it.h_c1 = cv(rh);

@@ -53,12 +53,15 @@ struct FastFixed {
   int64_t radd1, radd3, radd2;
   int64_t mfine, mcoarse;    // 1 and 2 in units 2^-2fZ (Milstein)
   int64_t limS;
+  int32_t narrow_sq;         // 1: sum of squared samples of one thread fits 64 bits (host-checked)
+  int32_t pad;
 };
 
 struct ItemDesc {
   // sample range and chunking
   uint64_t first, N;       // samples [first, first + N)
   uint64_t g0, g1;         // groups [g0, g1) covering the range
+  uint64_t gf0, gf1;       // groups [gf0, gf1) lie entirely inside the sample range
   uint32_t groups_per_thread;
   uint32_t chunk_begin;    // first chunk (CTA) of this item within its launch
   uint32_t n_chunks;

@@ -142,8 +142,8 @@ struct LevelSim {
     }
     // saturation of S (the only variable the host could not bound)
     const AS lim = (AS)ff.limS;
-    const AS c = s > lim ? lim : (s < -lim ? -lim : s);
-    satb = satb || (c != s);
+    const AS c = min(max(s, -lim), lim);
+    satb |= (c != s);
     return c;
   }
 
@@ -261,7 +261,12 @@ struct LevelSim {
     }
   }
   __device__ __forceinline__ int64_t fixed_payoff(int64_t x, int64_t inner, int64_t mn, int steps, bool coarse) const {
-    if constexpr (PC == PC_TERMINAL) {
+    if constexpr (PC == PC_TERMINAL && AP == AP_FX32) {
+      // S, K < 2^31 on this datapath: 32-bit arithmetic
+      const int32_t x32 = (int32_t)x, K32v = (int32_t)fx.K;
+      const int32_t v = payoff == 1 ? (int32_t)1 << fx.fS : x32 - K32v;
+      return x32 > K32v ? v : 0;
+    } else if constexpr (PC == PC_TERMINAL) {
       if (payoff == 1) return x > fx.K ? ((int64_t)1 << fx.fS) : 0;
       return x > fx.K ? x - fx.K : 0;
     } else if constexpr (PC == PC_ASIAN) {
@@ -330,8 +335,13 @@ struct LevelSim {
       ydump = (double)y;
     } else if constexpr (EST == EST_APPROX) {
       const int64_t yi = qf - qc;
-      if constexpr (AP == AP_FX32 && PC == PC_TERMINAL) acc.add_int32((int32_t)yi);  // |Y| < 2^31 here
-      else acc.add_int(yi);
+      if constexpr (AP == AP_FX32 && PC == PC_TERMINAL) {
+        // |Y| < 2^31 here; the host bounds the thread's sum of squares below 2^64
+        if (ff.narrow_sq) acc.add_int32_narrow((int32_t)yi);
+        else acc.add_int32((int32_t)yi);
+      } else {
+        acc.add_int(yi);
+      }
       ydump = (double)yi * (double)unit_scale;
     } else {
       const float yx = (float)(pf - pc);
@@ -381,6 +391,10 @@ struct ThreadAcc {
   __device__ __forceinline__ void add_int32(int32_t y) {
     isum += y;
     add_u128(q_lo, q_hi, (uint64_t)((int64_t)y * y), 0);
+  }
+  __device__ __forceinline__ void add_int32_narrow(int32_t y) {
+    isum += y;
+    q_lo += (uint64_t)((int64_t)y * y);
   }
   template <class T>
   __device__ __forceinline__ void add_real(T y) {
@@ -487,14 +501,18 @@ level_kernel(const __grid_constant__ LaunchArgs args) {
   const uint4 ctr_hi = make_uint4(0, 0, it.ctr2, it.ctr3);
   mlmc_sample_rec *dump = (mlmc_sample_rec *)it.dump;
 
-  for (uint64_t g = gbeg + threadIdx.x; g < gend; g += blockDim.x) {
+  const uint64_t gf0 = it.gf0, gf1 = it.gf1;
+  const uint32_t ng = gend > gbeg ? (uint32_t)(gend - gbeg) : 0u;
+  for (uint32_t r = threadIdx.x; r < ng; r += blockDim.x) {
+    const uint64_t g = gbeg + r;
     if (lev >= 2) {
       // one sample per group, 2^l / 4 Philox calls
       const uint64_t s = g;
       const uint32_t calls = 1u << (lev - 2);
+      const uint64_t qbase = s * calls;
       sim.begin();
       for (uint32_t c = 0; c < calls; ++c) {
-        const uint64_t q = s * calls + c;
+        const uint64_t q = qbase + c;
         const uint4 w = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), ctr_hi.z, ctr_hi.w), args.rk);
         const int i0 = (int)(c << 2);
         sim.template step<true>(w.x, i0);
@@ -502,39 +520,41 @@ level_kernel(const __grid_constant__ LaunchArgs args) {
         sim.template step<true>(w.z, i0 + 2);
         sim.template step<true>(w.w, i0 + 3);
       }
-      const bool valid = s >= first && s < last;
+      const bool valid = (g >= gf0 && g < gf1) || (s >= first && s < last);
       sim.finish(acc, valid, dump && valid ? dump + (s - first) : nullptr);
-    } else if (lev == 1) {
-      const uint4 w = philox4x32_10(make_uint4((uint32_t)g, (uint32_t)(g >> 32), ctr_hi.z, ctr_hi.w), args.rk);
-      const uint64_t s0 = 2 * g;
-      // samples s0 + k are valid for k in [klo, khi)
-      const int klo = s0 >= first ? 0 : (int)min(first - s0, (uint64_t)2);
-      const int khi = last <= s0 ? 0 : (int)min(last - s0, (uint64_t)2);
-      sim.begin();
-      sim.template step<true>(w.x, 0);
-      sim.template step<true>(w.y, 1);
-      {
-        const bool valid = 0 >= klo && 0 < khi;
-        sim.finish(acc, valid, dump && valid ? dump + (s0 - first) : nullptr);
-      }
-      sim.begin();
-      sim.template step<true>(w.z, 0);
-      sim.template step<true>(w.w, 1);
-      {
-        const bool valid = 1 >= klo && 1 < khi;
-        sim.finish(acc, valid, dump && valid ? dump + (s0 + 1 - first) : nullptr);
-      }
     } else {
       const uint4 w = philox4x32_10(make_uint4((uint32_t)g, (uint32_t)(g >> 32), ctr_hi.z, ctr_hi.w), args.rk);
-      const uint64_t s0 = 4 * g;
-      const int klo = s0 >= first ? 0 : (int)min(first - s0, (uint64_t)4);
-      const int khi = last <= s0 ? 0 : (int)min(last - s0, (uint64_t)4);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      const int spc = lev == 1 ? 2 : 4;
+      const uint64_t s0 = (uint64_t)spc * g;
+      // samples s0 + k are valid for k in [klo, khi)
+      int klo = 0, khi = spc;
+      if (!(g >= gf0 && g < gf1)) {
+        klo = s0 >= first ? 0 : (int)min(first - s0, (uint64_t)spc);
+        khi = last <= s0 ? 0 : (int)min(last - s0, (uint64_t)spc);
+      }
+      if (lev == 1) {
         sim.begin();
-        sim.template step<false>(word_of(w, k), 0);
-        const bool valid = k >= klo && k < khi;
-        sim.finish(acc, valid, dump && valid ? dump + (s0 + k - first) : nullptr);
+        sim.template step<true>(w.x, 0);
+        sim.template step<true>(w.y, 1);
+        {
+          const bool valid = 0 >= klo && 0 < khi;
+          sim.finish(acc, valid, dump && valid ? dump + (s0 - first) : nullptr);
+        }
+        sim.begin();
+        sim.template step<true>(w.z, 0);
+        sim.template step<true>(w.w, 1);
+        {
+          const bool valid = 1 >= klo && 1 < khi;
+          sim.finish(acc, valid, dump && valid ? dump + (s0 + 1 - first) : nullptr);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          sim.begin();
+          sim.template step<false>(word_of(w, k), 0);
+          const bool valid = k >= klo && k < khi;
+          sim.finish(acc, valid, dump && valid ? dump + (s0 + k - first) : nullptr);
+        }
       }
     }
   }
