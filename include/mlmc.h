@@ -156,6 +156,28 @@ mlmc_status mlmc_level_dump(int level, uint64_t N, const mlmc_params *p, mlmc_va
                             uint64_t seed, uint64_t first_sample, int32_t stream,
                             mlmc_sample *d_samples, mlmc_sums *out);
 
+/* ---- single level without device allocation -------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * must not allocate device memory while they run: a process whose device
+ * memory is owned by another allocator (a framework's caching pool, or memory
+ * reserved up front), a latency-critical loop in which a cudaMalloc would
+ * synchronise the device, or code whose memory budget has been fixed ahead.
+ * It computes exactly what mlmc_level computes (same kernels, same chunking)
+ * and calls no cudaMalloc, cudaFree or other allocating routine, on the host
+ * side of CUDA or the device.  Its scratch (per-CTA partial sums, the work
+ * item, the tables and the result record) is one file-scope device array of
+ * about 0.9 MiB that every GPU which loads the library keeps until exit.
+ * Limits: at most 16384 CTAs (128 threads each) per call -- larger sample
+ * counts return MLMC_EINVAL; icdf_bits <= 14.  All work is enqueued on `stream`
+ * (a cudaStream_t, NULL = legacy default stream) and the call returns after
+ * synchronising it; seconds = 0.  The first call on a device looks up the
+ * array's device address, so make that first call before any stream capture.
+ * Every call overwrites the whole array; calls that overlap on the GPU (from
+ * several host threads, or enqueued on different streams) race and must be
+ * serialised by the caller.  Errors as mlmc_level. */
+mlmc_status mlmc_level_noalloc(int level, uint64_t N, const mlmc_params *p, mlmc_variant v,
+                               uint64_t seed, uint64_t first_sample, mlmc_sums *out, void *stream);
+
 /* ---- batched work lists ---------------------------------------------------
  * A plan holds a device-resident work list; launching it enqueues one level
  * kernel per kernel configuration (concurrently, on forked streams) and a

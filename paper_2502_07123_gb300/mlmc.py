@@ -84,6 +84,8 @@ def load():
                             ctypes.c_uint64, P(Sums)]),
         "mlmc_level_dump": (st, [ctypes.c_int, ctypes.c_uint64, P(Params), ctypes.c_int, ctypes.c_uint64,
                                  ctypes.c_uint64, ctypes.c_int32, ctypes.c_void_p, P(Sums)]),
+        "mlmc_level_noalloc": (st, [ctypes.c_int, ctypes.c_uint64, P(Params), ctypes.c_int, ctypes.c_uint64,
+                                    ctypes.c_uint64, P(Sums), ctypes.c_void_p]),
         "mlmc_plan_create": (st, [P(ctypes.c_void_p), P(Work), ctypes.c_int, ctypes.c_uint64, P(Tuning)]),
         "mlmc_plan_launch": (st, [ctypes.c_void_p, ctypes.c_void_p]),
         "mlmc_plan_results": (st, [ctypes.c_void_p, P(Sums)]),
@@ -166,6 +168,18 @@ def mlmc_level_dump(level, N, params, variant, seed, first_sample=0, stream=-1):
                              ctypes.c_void_p(buf.data_ptr()), ctypes.byref(s)), "mlmc_level_dump")
     host = buf[: N * SAMPLE_BYTES].cpu().numpy()
     return _sums_dict(s), host.view(SAMPLE_DTYPE)
+
+
+def mlmc_level_noalloc(level, N, params, variant, seed, first_sample=0, stream=None):
+    """mlmc_level without device allocation (scratch in a fixed device array of the
+    library); `stream` is a cudaStream_t handle as int, a torch stream, or None for
+    the legacy default stream."""
+    L = load()
+    s = Sums()
+    h = ctypes.c_void_p(None) if stream is None else _stream_handle(stream)
+    _check(L.mlmc_level_noalloc(level, N, ctypes.byref(params), variant, seed, first_sample, ctypes.byref(s), h),
+           "mlmc_level_noalloc")
+    return _sums_dict(s)
 
 
 def _works(items):
