@@ -31,7 +31,8 @@ from paper_2502_07123_gb300 import workloads as W  # noqa: E402
 
 METRIC = "time-to-ε price & path-steps/s: nested approx-RV vs plain MLMC; p50/p99 latency"
 UNIT = "path-steps/s"
-WORKLOAD = "nested MLMC step: euro+digital call GBM, EM, levels 0-8, N~ 1e7..1e4 fixed-point approx + 1e4 FP32-fixed corrections"
+WORKLOAD = ("nested MLMC step: euro+digital call GBM, EM, levels 0-8, N~ 1e7..1e4 fixed-point approx "
+            "(packed draws) + 1e4 FP32-fixed corrections")
 
 # Algorithmic 32-bit lane operations per fine path-step (roofline section):
 #   Philox4x32-10: 10 rounds x (2 wide multiplies + 2 three-input XORs) / 4 words = 10
@@ -53,7 +54,7 @@ def build_items(m, rank=0):
         if key not in cache:
             cache[key] = m.make_params(p, d=cfg["d"], method=cfg["method"],
                                        formats=[W.default_format(p, lev) for lev in range(9)],
-                                       request=it["request"])
+                                       request=it["request"], rng_pack=cfg["rng_pack"])
         items.append(dict(params=cache[key], level=it["level"], variant=it["variant"],
                           first_sample=rank * it["N"], N=it["N"]))
         meta.append(it)
@@ -117,7 +118,8 @@ def oracle_step_sample(meta, cfg, fraction, rank=0):
         p = it["params"]
         fmt = W.default_format(p, it["level"]) if it["variant"] in (W.FIXED_APPROX, W.CORR_FIXED) else None
         core.level(p, it["level"], rank * it["N"], n, it["variant"], cfg["seed"], request=it["request"],
-                   d=cfg["d"], method=cfg["method"], fmt=fmt)
+                   d=cfg["d"], method=cfg["method"], fmt=fmt,
+                   pack=cfg["rng_pack"] if it["variant"] == W.FIXED_APPROX else 0)
         steps += n << it["level"]
     return steps, time.perf_counter() - t0
 
@@ -286,7 +288,7 @@ def main():
 def time_to_eps(m, torch, eps=1e-3, seeds=(1, 2, 3)):
     """Wall time of mlmc_estimate at RMS error eps: nested fixed point vs plain FP32 (European call)."""
     p = W.params()
-    P = m.make_params(p, d=10, method=1, formats=[W.default_format(p, lev) for lev in range(11)])
+    P = m.make_params(p, d=10, method=1, formats=[W.default_format(p, lev) for lev in range(11)], rng_pack=1)
     out = {"eps": eps}
     for name, mode in (("plain_fp32", m.MODE_PLAIN_FP32), ("nested_fixed", m.MODE_NESTED_FIXED)):
         m.mlmc_estimate(1e-2, P, mode, 99, 10)   # warm tables and contexts

@@ -92,6 +92,13 @@ typedef struct {
                                    library's default schedule (mlmc_default_format) */
   int32_t n_formats;            /* entries in formats                            */
   uint32_t request_id;          /* enters the Philox counter (independent streams) */
+  int32_t rng_pack;             /* 1: approximate-only estimators read 3 table indices
+                                   from each 32-bit Philox word (d = 9 or 10 only):
+                                   sample s = 3P + L takes bits [32-d(L+1), 32-dL) of
+                                   the word its pack P reads at each step; 0: one word
+                                   per step.  Ignored by exact and correction estimators,
+                                   which need all 32 bits of J (Sec. 3.1 coupling). */
+  int32_t reserved;             /* must be 0 */
 } mlmc_params;
 
 /* Per-level result.  sum/sum2 are discounted FP64 sums of Y and Y^2.  When
@@ -118,7 +125,7 @@ typedef struct {
   uint32_t sat, pad; /* sat = 1 if a fixed-point value saturated              */
 } mlmc_sample;
 
-/* Chunking of the level kernels.  threads: CTA size (32..1024, multiple of 32);
+/* Chunking of the level kernels.  threads: CTA size (32..128, multiple of 32);
  * steps_per_thread: target fine path-steps per thread (>= 1); zero = default. */
 typedef struct {
   int32_t threads;

@@ -86,6 +86,8 @@ def lib():
         L.or_philox_array.argtypes = [u32p, u32p, ctypes.c_uint64, u32p]
         L.or_draw_array.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                     u64p, u32p, ctypes.c_uint64, u32p]
+        L.or_draw_packed_array.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                           u64p, u32p, ctypes.c_uint64, ctypes.c_int, u32p]
         L.or_exact_normal_array.argtypes = [u32p, ctypes.c_uint64, f64p]
         L.or_round_fp16_array.argtypes = [f64p, ctypes.c_uint64, f64p]
         L.or_round_bf16_array.argtypes = [f64p, ctypes.c_uint64, f64p]
@@ -94,7 +96,7 @@ def lib():
         L.or_norminv_lower.restype = ctypes.c_double
         L.or_level.argtypes = [ctypes.POINTER(Params), ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
                                ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
-                               ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(Format),
+                               ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(Format), ctypes.c_int,
                                ctypes.POINTER(Sums), ctypes.c_void_p]
         L.or_level.restype = ctypes.c_int
         _lib = L
@@ -114,6 +116,14 @@ def draws(seed, request, level, stream, samples, steps) -> np.ndarray:
     t = np.ascontiguousarray(steps, dtype=np.uint32)
     out = np.empty(s.shape[0], dtype=np.uint32)
     lib().or_draw_array(seed, request, level, stream, s, t, s.shape[0], out)
+    return out
+
+
+def draws_packed(seed, request, level, stream, samples, steps, d) -> np.ndarray:
+    s = np.ascontiguousarray(samples, dtype=np.uint64)
+    t = np.ascontiguousarray(steps, dtype=np.uint32)
+    out = np.empty(s.shape[0], dtype=np.uint32)
+    lib().or_draw_packed_array(seed, request, level, stream, s, t, s.shape[0], int(d), out)
     return out
 
 
@@ -160,7 +170,7 @@ class OracleError(RuntimeError):
 
 
 def level(p, lev, first, N, variant, seed, request=0, stream=None, d=10, method=1,
-          fmt=None, dump=False):
+          fmt=None, dump=False, pack=0):
     """Simulate samples [first, first+N) of one level; return (sums dict, dump array or None).
 
     p: dict with S0, K, r, sigma, T, payoff, scheme.
@@ -182,7 +192,7 @@ def level(p, lev, first, N, variant, seed, request=0, stream=None, d=10, method=
     st = lib().or_level(ctypes.byref(P), int(lev), int(first), int(N), int(variant), int(seed),
                         int(request), int(stream), int(d),
                         ztab.ctypes.data if ztab is not None else None,
-                        ctypes.byref(F) if F is not None else None,
+                        ctypes.byref(F) if F is not None else None, int(pack),
                         ctypes.byref(S), out.ctypes.data if dump else None)
     if st != 0:
         raise OracleError("or_level returned %d" % st)

@@ -109,6 +109,27 @@ uint32_t or_draw(uint64_t seed, uint32_t request, uint32_t level, uint32_t strea
   return out[w & 3u];
 }
 
+/* Packed draws of approximate-only estimators (a reading, see below): with
+ * k = floor(32 / d) >= 2 fields per 32-bit word, sample s belongs to pack
+ * P = s div k and lane L = s mod k; its fine step i reads word
+ * w = P 2^level + i (call w div 4, output word w mod 4, same counter layout as
+ * or_draw) and uses field L, i.e. bits [32 - d (L+1), 32 - d L).  The result is
+ * returned shifted to the top of a 32-bit value, so that the usual "top d bits"
+ * rule of the approximate Normal applies unchanged. */
+uint32_t or_draw_packed(uint64_t seed, uint32_t request, uint32_t level, uint32_t stream,
+                        uint64_t sample, uint32_t step, int d) {
+  const uint64_t k = (uint64_t)(32 / d);
+  const uint64_t pack = sample / k, lane = sample % k;
+  uint64_t w = (pack << level) + (uint64_t)step;
+  uint64_t q = w >> 2;
+  uint32_t ctr[4] = {(uint32_t)q, (uint32_t)(q >> 32), level | (stream << 8), request};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t out[4];
+  or_philox4x32_10(ctr, key, out);
+  uint32_t J = out[w & 3u];
+  return J << (uint32_t)(d * (int)lane);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Exact inverse Normal CDF in FP64 (Sec. 3: "computing Z is trivial").     */
 /* Newton's method on Phi(z) = u, started from the Abramowitz & Stegun      */
@@ -262,7 +283,7 @@ static double payoff_fp64(const or_params *p, const path_acc *a) {
 /* ------------------------------------------------------------------------ */
 typedef struct {
   const or_params *p;
-  int level, n, variant, d;
+  int level, n, variant, d, pack;
   uint64_t seed; uint32_t request, stream;
   double h;
   /* approximate-path tables and constants */
@@ -382,6 +403,11 @@ static int64_t fx_payoff(const level_cfg *c, const fx_acc *a, int coarse) {
   }
 }
 
+static uint32_t approx_draw(const level_cfg *c, uint64_t s, int i) {
+  if (c->pack) return or_draw_packed(c->seed, c->request, c->level, c->stream, s, i, c->d);
+  return or_draw(c->seed, c->request, c->level, c->stream, s, i);
+}
+
 static void fixed_sample(const level_cfg *c, uint64_t s, or_sample *out) {
   int milstein = c->p->scheme == OR_MILSTEIN;
   uint32_t sat = 0;
@@ -390,7 +416,7 @@ static void fixed_sample(const level_cfg *c, uint64_t s, or_sample *out) {
   fx_start(&af, c->S0q);
   fx_start(&ac, c->S0q);
   for (int i = 0; i < c->n; ++i) {
-    uint32_t J = or_draw(c->seed, c->request, c->level, c->stream, s, i);
+    uint32_t J = approx_draw(c, s, i);
     uint32_t idx; int neg;
     approx_index(J, c->d, &idx, &neg);
     int64_t z = neg ? -c->zq[idx] : c->zq[idx];
@@ -468,7 +494,7 @@ static int half_sample(const level_cfg *c, uint64_t s, or_sample *out) {
   h_start(&af, (float)c->hS0);
   h_start(&ac, (float)c->hS0);
   for (int i = 0; i < c->n; ++i) {
-    uint32_t J = or_draw(c->seed, c->request, c->level, c->stream, s, i);
+    uint32_t J = approx_draw(c, s, i);
     uint32_t idx; int neg;
     approx_index(J, c->d, &idx, &neg);
     double z = neg ? -c->ztab[idx] : c->ztab[idx];
@@ -511,13 +537,15 @@ static int validate_format(const or_format *F, int milstein) {
 
 int or_level(const or_params *p, int level, uint64_t first, uint64_t N, int variant,
              uint64_t seed, uint32_t request, uint32_t stream,
-             int d, const double *ztab, const or_format *fmt,
+             int d, const double *ztab, const or_format *fmt, int pack,
              or_sums *sums, or_sample *dump) {
   if (level < 0 || level > 20 || variant < 0 || variant > 7) return OR_EINVAL;
+  /* packed draws only feed approximate-only estimators (their uniforms need d bits, not 32) */
+  if (pack && (has_exact(variant) || d < 2 || 32 / d < 2)) return OR_EINVAL;
   if (p->payoff < 0 || p->payoff > 3 || p->scheme < 0 || p->scheme > 1) return OR_EINVAL;
   level_cfg c;
   memset(&c, 0, sizeof c);
-  c.p = p; c.level = level; c.n = 1 << level; c.variant = variant; c.d = d;
+  c.p = p; c.level = level; c.n = 1 << level; c.variant = variant; c.d = d; c.pack = pack;
   c.seed = seed; c.request = request; c.stream = stream;
   c.h = ldexp(p->T, -level);
   c.ztab = ztab;
@@ -637,4 +665,8 @@ void or_approx_normal_array(const uint32_t *J, uint64_t n, int d, const double *
     approx_index(J[i], d, &idx, &neg);
     out[i] = neg ? -ztab[idx] : ztab[idx];
   }
+}
+void or_draw_packed_array(uint64_t seed, uint32_t request, uint32_t level, uint32_t stream,
+                          const uint64_t *sample, const uint32_t *step, uint64_t n, int d, uint32_t *J) {
+  for (uint64_t i = 0; i < n; ++i) J[i] = or_draw_packed(seed, request, level, stream, sample[i], step[i], d);
 }

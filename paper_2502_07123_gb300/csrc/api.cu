@@ -23,7 +23,7 @@
 using namespace mlmc;
 
 // The Python binding mirrors these layouts.
-static_assert(sizeof(mlmc_params) == 72, "mlmc_params layout");
+static_assert(sizeof(mlmc_params) == 80, "mlmc_params layout");
 static_assert(sizeof(mlmc_sums) == 72, "mlmc_sums layout");
 static_assert(sizeof(mlmc_work) == 40, "mlmc_work layout");
 static_assert(sizeof(mlmc_sample) == 80, "mlmc_sample layout");
@@ -222,7 +222,16 @@ bool params_ok(const mlmc_params *p) {
   if (p->icdf_method != 1 && p->icdf_method != 3) return false;
   if (p->icdf_bits < 2 || p->icdf_bits > 14) return false;
   if (p->formats && p->n_formats < 0) return false;
+  if (p->rng_pack != 0 && p->rng_pack != 1) return false;
+  if (p->reserved != 0) return false;
   return true;
+}
+
+// Lanes per pack of an approximate-only estimator (packed draws need 3 fields of d bits).
+int pack_lanes(const mlmc_params *p, int variant) {
+  const bool approx_only = variant == MLMC_FIXED_APPROX || variant == MLMC_FP16_APPROX || variant == MLMC_BF16_APPROX;
+  if (!approx_only || !p->rng_pack) return 1;
+  return 32 / p->icdf_bits == 3 ? 3 : 0;  // 0: packing requested but unsupported for this d
 }
 
 int bitlen(double x, int f) {
@@ -314,6 +323,11 @@ int cost_kind_of(int variant) {
 cudaError_t launch_by_family(int fam, int scheme, int pc, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                              const LaunchArgs &a) {
   switch (fam) {
+    case 12: return launch_approx_fixed_p3(scheme, pc, grid, block, smem, st, a);
+    case 13: return launch_approx_f16_p3(scheme, pc, grid, block, smem, st, a);
+    case 14: return launch_approx_bf16_p3(scheme, pc, grid, block, smem, st, a);
+    case 15: return launch_approx_fx32_p3(scheme, pc, grid, block, smem, st, a);
+    case 16: return launch_approx_fx64_p3(scheme, pc, grid, block, smem, st, a);
     case 8: return launch_approx_fx32(scheme, pc, grid, block, smem, st, a);
     case 9: return launch_approx_fx64(scheme, pc, grid, block, smem, st, a);
     case 10: return launch_corr_fx32(scheme, pc, grid, block, smem, st, a);
@@ -449,8 +463,10 @@ mlmc_status build_item(const mlmc_work &w, int out_index, int threads, int steps
   it.ctr3 = p->request_id;
   it.out_index = (uint32_t)out_index;
   it.dump = dump;
-  // chunking
-  const uint64_t spc = lev >= 2 ? 1 : (lev == 1 ? 2 : 4);
+  const int KP = pack_lanes(p, v);
+  if (KP == 0) return MLMC_EINVAL;
+  // chunking: a group is one Philox call's worth of packs of KP samples
+  const uint64_t spc = (uint64_t)KP * (lev >= 2 ? 1 : (lev == 1 ? 2 : 4));
   const uint64_t steps_per_group = std::max<uint64_t>(4, 1ULL << lev);
   it.g0 = w.first_sample / spc;
   it.g1 = w.N == 0 ? it.g0 : (w.first_sample + w.N + spc - 1) / spc;
@@ -459,7 +475,7 @@ mlmc_status build_item(const mlmc_work &w, int out_index, int threads, int steps
   it.gf0 = (w.first_sample + spc - 1) / spc;
   it.gf1 = (w.first_sample + w.N) / spc;
   if (it.gf1 < it.gf0) it.gf1 = it.gf0;
-  uint64_t G = std::max<uint64_t>(1, (uint64_t)steps_per_thread / steps_per_group);
+  uint64_t G = std::max<uint64_t>(1, (uint64_t)steps_per_thread / (steps_per_group * KP));
   const uint64_t min_ctas = 4ULL * (uint64_t)std::max(1, g.num_sms);
   const uint64_t cap = std::max<uint64_t>(1, (groups + (uint64_t)threads * min_ctas - 1) / ((uint64_t)threads * min_ctas));
   G = std::min(G, cap);
@@ -468,7 +484,7 @@ mlmc_status build_item(const mlmc_work &w, int out_index, int threads, int steps
   const uint64_t nch = (groups + per_chunk - 1) / per_chunk;
   if (nch > 0x7fffffffULL) return MLMC_EINVAL;
   it.n_chunks = (uint32_t)nch;
-  b.chunk_cost = (double)per_chunk * (double)steps_per_group * g_cost[cost_kind_of(v)];
+  b.chunk_cost = (double)per_chunk * (double)steps_per_group * KP * g_cost[cost_kind_of(v)];
   // exact-path constants (the same FP64 expressions as the fixed-point ones)
   const double h = std::ldexp(p->T, -lev);
   const double rh = p->r * h, rh2 = p->r * (2.0 * h), sqh = std::sqrt(h);
@@ -534,11 +550,10 @@ mlmc_status build_item(const mlmc_work &w, int out_index, int threads, int steps
       fast = fast_fixed(e, f, con1, con1c, con2, con3, zmax, p->scheme == MLMC_MILSTEIN, it.ff, s64);
       fast64 = s64;
       if (fast && !s64) {
-        // terminal payoffs are below max(lim_S, 2^f_S) in magnitude: one thread's sum of
-        // squares stays below 2^64 if samples_per_thread * ymax^2 < 2^64
+        // the 32-bit datapath sums a group's squared terminal payoff differences in
+        // 64 bits: |Y| <= max(lim_S, 2^f_S), so spc samples need spc ymax^2 < 2^64
         const double ymax = std::max(std::ldexp(1.0, e[F_S] + f[F_S]), std::ldexp(1.0, f[F_S]));
-        const double per_thread = (double)it.groups_per_thread * (double)spc;
-        it.ff.narrow_sq = per_thread * ymax * ymax < 0x1p63 ? 1 : 0;
+        if (!((double)spc * ymax * ymax < 0x1p64)) fast64 = true;
       }
     } else {
       uint16_t (*cv)(double) = bf ? bf16_bits : half_bits;
@@ -562,6 +577,17 @@ mlmc_status build_item(const mlmc_work &w, int out_index, int threads, int steps
   if (fast) {
     if (b.family == 2) b.family = fast64 ? 9 : 8;
     else if (b.family == 5) b.family = fast64 ? 11 : 10;
+  }
+  if (KP == 3) {
+    // packed families: 12 fixed (general), 13 binary16, 14 bfloat16, 15 fixed 32-bit S, 16 fixed 64-bit S
+    switch (b.family) {
+      case 2: b.family = 12; break;
+      case 3: b.family = 13; break;
+      case 4: b.family = 14; break;
+      case 8: b.family = 15; break;
+      case 9: b.family = 16; break;
+      default: return MLMC_EINVAL;
+    }
   }
   b.scheme = p->scheme;
   b.pc = p->payoff == MLMC_ASIAN ? PC_ASIAN : (p->payoff == MLMC_LOOKBACK ? PC_LOOKBACK : PC_TERMINAL);
@@ -678,7 +704,7 @@ mlmc_status plan_create_impl(mlmc_plan **out, const mlmc_work *work, int n_work,
     if (tuning->threads) threads = tuning->threads;
     if (tuning->steps_per_thread) spt = tuning->steps_per_thread;
   }
-  if (threads < 32 || threads > 256 || threads % 32 || spt < 1) return MLMC_EINVAL;
+  if (threads < 32 || threads > 128 || threads % 32 || spt < 1) return MLMC_EINVAL;
   mlmc_plan *pl = new (std::nothrow) mlmc_plan;
   if (!pl) return MLMC_ENOMEM;
   pl->n_work = n_work;
@@ -1291,7 +1317,9 @@ extern "C" mlmc_status mlmc_level_noalloc(int level, uint64_t N, const mlmc_para
   it.ctr3 = p->request_id;
   it.out_index = 0;
   it.dump = nullptr;
-  const uint64_t spc = level >= 2 ? 1 : (level == 1 ? 2 : 4);
+  const int KP = pack_lanes(p, vi);
+  if (KP == 0) return MLMC_EINVAL;
+  const uint64_t spc = (uint64_t)KP * (level >= 2 ? 1 : (level == 1 ? 2 : 4));
   const uint64_t steps_per_group = std::max<uint64_t>(4, 1ULL << level);
   it.g0 = first_sample / spc;
   it.g1 = N == 0 ? it.g0 : (first_sample + N + spc - 1) / spc;
@@ -1299,7 +1327,7 @@ extern "C" mlmc_status mlmc_level_noalloc(int level, uint64_t N, const mlmc_para
   it.gf0 = (first_sample + spc - 1) / spc;
   it.gf1 = (first_sample + N) / spc;
   if (it.gf1 < it.gf0) it.gf1 = it.gf0;
-  uint64_t G = std::max<uint64_t>(1, (uint64_t)spt / steps_per_group);
+  uint64_t G = std::max<uint64_t>(1, (uint64_t)spt / (steps_per_group * KP));
   const uint64_t min_ctas = 4ULL * (uint64_t)std::max(1, nsm);
   G = std::min(G, std::max<uint64_t>(1, (groups + (uint64_t)threads * min_ctas - 1) / ((uint64_t)threads * min_ctas)));
   it.groups_per_thread = (uint32_t)G;
@@ -1372,7 +1400,7 @@ extern "C" mlmc_status mlmc_level_noalloc(int level, uint64_t N, const mlmc_para
       fast = fast_fixed(e, f, con1, con1c, con2, con3, zmax, p->scheme == MLMC_MILSTEIN, it.ff, fast64);
       if (fast && !fast64) {
         const double ymax = std::max(std::ldexp(1.0, e[F_S] + f[F_S]), std::ldexp(1.0, f[F_S]));
-        it.ff.narrow_sq = (double)G * (double)spc * ymax * ymax < 0x1p63 ? 1 : 0;
+        if (!((double)spc * ymax * ymax < 0x1p64)) fast64 = true;
       }
     } else {
       uint16_t (*cv)(double) = bf ? bf16_bits : half_bits;
@@ -1396,6 +1424,16 @@ extern "C" mlmc_status mlmc_level_noalloc(int level, uint64_t N, const mlmc_para
     if (fast) {
       if (family == 2) family = fast64 ? 9 : 8;
       else if (family == 5) family = fast64 ? 11 : 10;
+    }
+    if (KP == 3) {
+      switch (family) {
+        case 2: family = 12; break;
+        case 3: family = 13; break;
+        case 4: family = 14; break;
+        case 8: family = 15; break;
+        case 9: family = 16; break;
+        default: return MLMC_EINVAL;
+      }
     }
   }
   it.unit = unit;

@@ -53,8 +53,7 @@ struct FastFixed {
   int64_t radd1, radd3, radd2;
   int64_t mfine, mcoarse;    // 1 and 2 in units 2^-2fZ (Milstein)
   int64_t limS;
-  int32_t narrow_sq;         // 1: sum of squared samples of one thread fits 64 bits (host-checked)
-  int32_t pad;
+  int32_t pad0, pad1;
 };
 
 struct ItemDesc {

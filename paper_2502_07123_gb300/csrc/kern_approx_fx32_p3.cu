@@ -1,0 +1,11 @@
+// Level-kernel family: estimator EST_APPROX, approximate arithmetic AP_FX32, packed draws
+// (three lockstep samples per Philox word).
+#include "kernels.h"
+#include "level_kernel.cuh"
+
+namespace mlmc {
+cudaError_t launch_approx_fx32_p3(int scheme, int pc, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                      const LaunchArgs &a) {
+  return launch_family<EST_APPROX, XP_F32, AP_FX32, 3>(scheme, pc, grid, block, smem, st, a);
+}
+}  // namespace mlmc

@@ -18,5 +18,10 @@ MLMC_FAMILY(launch_approx_fx32)
 MLMC_FAMILY(launch_approx_fx64)
 MLMC_FAMILY(launch_corr_fx32)
 MLMC_FAMILY(launch_corr_fx64)
+MLMC_FAMILY(launch_approx_fixed_p3)
+MLMC_FAMILY(launch_approx_f16_p3)
+MLMC_FAMILY(launch_approx_bf16_p3)
+MLMC_FAMILY(launch_approx_fx32_p3)
+MLMC_FAMILY(launch_approx_fx64_p3)
 #undef MLMC_FAMILY
 }  // namespace mlmc

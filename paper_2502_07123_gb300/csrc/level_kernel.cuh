@@ -26,9 +26,20 @@ template <int AP> struct HType { using T = __half; };
 template <> struct HType<AP_BF16> { using T = __nv_bfloat16; };
 
 constexpr int MAX_THREADS = 256;
+// Register budget: the approximate fixed-point Euler kernel with terminal payoffs
+// (the bulk of the nested estimator) runs with 6 resident 128-thread CTAs per SM
+// (<= 85 registers per thread), measured faster than its natural ~100 registers;
+// every other instantiation keeps its natural allocation (a cap there spills).
+constexpr int LAUNCH_THREADS = 128;
+template <int EST, int AP, int SCHEME, int PC> struct MinCtas {
+  static constexpr int value = (EST == EST_APPROX && AP == AP_FX32 && SCHEME == 0 && PC == PC_TERMINAL) ? 6 : 1;
+};
 
-template <int EST, int XP, int AP, int SCHEME, int PC>
+// KP > 1 (approximate-only estimators): KP samples advance in lockstep, lane L
+// reading bits [32 - d(L+1), 32 - dL) of the shared word (packed draws).
+template <int EST, int XP, int AP, int SCHEME, int PC, int KP = 1>
 struct LevelSim {
+  static_assert(KP == 1 || EST == EST_APPROX, "packed draws feed approximate-only estimators");
   static constexpr bool HAS_EXACT = (EST != EST_APPROX);
   static constexpr bool HAS_APPROX = (EST != EST_EXACT);
   static constexpr bool MIL = (SCHEME == 1);
@@ -52,15 +63,15 @@ struct LevelSim {
   float unit_scale;
   const void *smem_tab;
 
-  // ---- per-sample state ----
+  // ---- per-sample state (approximate state per lane) ----
   X S, Sc, zprev, accF, accC, minF, minC;
-  AS aS, aSc, aminF, aminC;
-  bool satb;
-  int64_t aaccF, aaccC;
-  int32_t azprev;
-  H hS, hSc, hzprev, hminF, hminC;
-  float haccF, haccC;
-  uint32_t sat;
+  AS aS[KP], aSc[KP], aminF[KP], aminC[KP];
+  bool satb[KP];
+  int64_t aaccF[KP], aaccC[KP];
+  int32_t azprev[KP];
+  H hS[KP], hSc[KP], hzprev[KP], hminF[KP], hminC[KP];
+  float haccF[KP], haccC[KP];
+  uint32_t sat[KP];
 
   __device__ __forceinline__ void load(const ItemDesc &it, const void *tab) {
     level = it.level;
@@ -91,15 +102,19 @@ struct LevelSim {
       S = S0; Sc = S0; zprev = X(0);
       accF = X(0.5) * S0; accC = accF; minF = S0; minC = S0;
     }
-    if constexpr (FIXED) {
-      aS = (AS)fx.S0; aSc = (AS)fx.S0; aaccF = 0; aaccC = 0; aminF = aS; aminC = aS; azprev = 0;
-      satb = false;
+#pragma unroll
+    for (int l = 0; l < KP; ++l) {
+      if constexpr (FIXED) {
+        aS[l] = (AS)fx.S0; aSc[l] = (AS)fx.S0; aaccF[l] = 0; aaccC[l] = 0; aminF[l] = aS[l]; aminC[l] = aS[l];
+        azprev[l] = 0;
+        satb[l] = false;
+      }
+      if constexpr (HALF) {
+        hS[l] = hS0; hSc[l] = hS0; hzprev[l] = HO::from_f(0.0f); hminF[l] = hS0; hminC[l] = hS0;
+        haccF[l] = __fmul_rn(0.5f, HO::to_f(hS0)); haccC[l] = haccF[l];
+      }
+      sat[l] = 0;
     }
-    if constexpr (HALF) {
-      hS = hS0; hSc = hS0; hzprev = HO::from_f(0.0f); hminF = hS0; hminC = hS0;
-      haccF = __fmul_rn(0.5f, HO::to_f(hS0)); haccC = haccF;
-    }
-    sat = 0;
   }
 
   // ---- exact path (FP32 / FP64) ----
@@ -109,7 +124,7 @@ struct LevelSim {
   }
 
   // ---- fixed-point Algorithm-1 step ----
-  __device__ __forceinline__ int64_t fx_step(int64_t s, int32_t z, int64_t con1A, int m) {
+  __device__ __forceinline__ int64_t fx_step(int64_t s, int32_t z, int64_t con1A, int m, uint32_t &sat) {
     const int64_t mul1 = saturate(requant((int64_t)fx.con2 * z, fx.q_mul1), fx.lim[3], sat);
     int64_t acc = con1A + (int64_t)((uint64_t)mul1 << fx.sh_mul1_F1);
     if constexpr (MIL) {
@@ -124,7 +139,7 @@ struct LevelSim {
   }
 
   // ---- fast fixed-point Algorithm-1 step (same values as fx_step while S stays in range) ----
-  __device__ __forceinline__ AS ff_step(AS s, int32_t z, int32_t c1r, int64_t m) {
+  __device__ __forceinline__ AS ff_step(AS s, int32_t z, int32_t c1r, int64_t m, bool &satb) {
     const int32_t mul1 = (int32_t)(((int64_t)ff.con2 * z + ff.radd1) >> ff.rs1);
     int32_t acc = c1r + mul1 * ff.mulF1;
     if constexpr (MIL) {
@@ -211,35 +226,39 @@ struct LevelSim {
       }
     }
     if constexpr (HAS_APPROX) {
-      if constexpr (FIXED) {
-        const int32_t z = fixed_z(J);
-        if constexpr (PC == PC_ASIAN) { if (i > 0) aaccF += aS; }
-        if constexpr (FAST) aS = ff_step(aS, z, ff.con1r, ff.mfine);
-        else aS = fx_step(aS, z, fx.con1A, 1);
-        if constexpr (PC == PC_LOOKBACK) aminF = aS < aminF ? aS : aminF;
-        if constexpr (COARSE) {
-          if (i & 1) {
-            if constexpr (PC == PC_ASIAN) { if (i > 1) aaccC += aSc; }
-            if constexpr (FAST) aSc = ff_step(aSc, azprev + z, ff.con1cr, ff.mcoarse);
-            else aSc = fx_step(aSc, azprev + z, fx.con1cA, 2);
-            if constexpr (PC == PC_LOOKBACK) aminC = aSc < aminC ? aSc : aminC;
-          } else {
-            azprev = z;
+#pragma unroll
+      for (int l = 0; l < KP; ++l) {
+        const uint32_t Jl = l == 0 ? J : (J << (d * l));  // this lane's field at the top
+        if constexpr (FIXED) {
+          const int32_t z = fixed_z(Jl);
+          if constexpr (PC == PC_ASIAN) { if (i > 0) aaccF[l] += aS[l]; }
+          if constexpr (FAST) aS[l] = ff_step(aS[l], z, ff.con1r, ff.mfine, satb[l]);
+          else aS[l] = fx_step(aS[l], z, fx.con1A, 1, sat[l]);
+          if constexpr (PC == PC_LOOKBACK) aminF[l] = aS[l] < aminF[l] ? aS[l] : aminF[l];
+          if constexpr (COARSE) {
+            if (i & 1) {
+              if constexpr (PC == PC_ASIAN) { if (i > 1) aaccC[l] += aSc[l]; }
+              if constexpr (FAST) aSc[l] = ff_step(aSc[l], azprev[l] + z, ff.con1cr, ff.mcoarse, satb[l]);
+              else aSc[l] = fx_step(aSc[l], azprev[l] + z, fx.con1cA, 2, sat[l]);
+              if constexpr (PC == PC_LOOKBACK) aminC[l] = aSc[l] < aminC[l] ? aSc[l] : aminC[l];
+            } else {
+              azprev[l] = z;
+            }
           }
-        }
-      } else {
-        const H z = half_z(J);
-        if constexpr (PC == PC_ASIAN) { if (i > 0) haccF = __fadd_rn(haccF, HO::to_f(hS)); }
-        hS = h_step(hS, z, hc1, HO::from_f(1.0f));
-        if constexpr (PC == PC_LOOKBACK) hminF = HO::to_f(hS) < HO::to_f(hminF) ? hS : hminF;
-        if constexpr (COARSE) {
-          if (i & 1) {
-            const H zc = HO::add(hzprev, z);
-            if constexpr (PC == PC_ASIAN) { if (i > 1) haccC = __fadd_rn(haccC, HO::to_f(hSc)); }
-            hSc = h_step(hSc, zc, hc1c, HO::from_f(2.0f));
-            if constexpr (PC == PC_LOOKBACK) hminC = HO::to_f(hSc) < HO::to_f(hminC) ? hSc : hminC;
-          } else {
-            hzprev = z;
+        } else {
+          const H z = half_z(Jl);
+          if constexpr (PC == PC_ASIAN) { if (i > 0) haccF[l] = __fadd_rn(haccF[l], HO::to_f(hS[l])); }
+          hS[l] = h_step(hS[l], z, hc1, HO::from_f(1.0f));
+          if constexpr (PC == PC_LOOKBACK) hminF[l] = HO::to_f(hS[l]) < HO::to_f(hminF[l]) ? hS[l] : hminF[l];
+          if constexpr (COARSE) {
+            if (i & 1) {
+              const H zc = HO::add(hzprev[l], z);
+              if constexpr (PC == PC_ASIAN) { if (i > 1) haccC[l] = __fadd_rn(haccC[l], HO::to_f(hSc[l])); }
+              hSc[l] = h_step(hSc[l], zc, hc1c, HO::from_f(2.0f));
+              if constexpr (PC == PC_LOOKBACK) hminC[l] = HO::to_f(hSc[l]) < HO::to_f(hminC[l]) ? hSc[l] : hminC[l];
+            } else {
+              hzprev[l] = z;
+            }
           }
         }
       }
@@ -301,30 +320,26 @@ struct LevelSim {
 
   // Finish the sample: payoffs, sample value, accumulation and optional dump.
   template <class Acc>
-  __device__ __forceinline__ void finish(Acc &acc, bool valid, mlmc_sample_rec *dump) {
+  __device__ __forceinline__ void finish(Acc &acc, int l, bool valid, mlmc_sample_rec *dump) {
     X pf = X(0), pc = X(0);
     int64_t qf = 0, qc = 0, afS = 0, acS = 0;
+    uint32_t lsat = 0;
     if constexpr (HAS_EXACT) {
       pf = exact_payoff(S, accF, minF, nsteps);
       if (level > 0) pc = exact_payoff(Sc, accC, minC, nsteps >> 1);
     }
-    if constexpr (AP == AP_FIXED) {
-      qf = fixed_payoff(aS, aaccF, aminF, nsteps, false);
-      if (level > 0) qc = fixed_payoff(aSc, aaccC, aminC, nsteps >> 1, true);
-      afS = aS;
-      acS = aSc;
+    if constexpr (FIXED) {
+      qf = fixed_payoff(aS[l], aaccF[l], aminF[l], nsteps, false);
+      if (level > 0) qc = fixed_payoff(aSc[l], aaccC[l], aminC[l], nsteps >> 1, true);
+      afS = aS[l];
+      acS = aSc[l];
+      if constexpr (FAST) lsat = satb[l] ? 1u : 0u;
+      else lsat = sat[l];
     }
-    if constexpr (FAST) {
-      qf = fixed_payoff(aS, aaccF, aminF, nsteps, false);
-      if (level > 0) qc = fixed_payoff(aSc, aaccC, aminC, nsteps >> 1, true);
-      afS = aS;
-      acS = aSc;
-      sat = satb ? 1u : 0u;
-    }
-    if constexpr (AP == AP_F16 || AP == AP_BF16) {
+    if constexpr (HALF) {
       if constexpr (HAS_APPROX) {
-        qf = half_payoff(hS, haccF, hminF, nsteps);
-        if (level > 0) qc = half_payoff(hSc, haccC, hminC, nsteps >> 1);
+        qf = half_payoff(hS[l], haccF[l], hminF[l], nsteps);
+        if (level > 0) qc = half_payoff(hSc[l], haccC[l], hminC[l], nsteps >> 1);
       }
     }
     if (!valid) return;
@@ -336,9 +351,8 @@ struct LevelSim {
     } else if constexpr (EST == EST_APPROX) {
       const int64_t yi = qf - qc;
       if constexpr (AP == AP_FX32 && PC == PC_TERMINAL) {
-        // |Y| < 2^31 here; the host bounds the thread's sum of squares below 2^64
-        if (ff.narrow_sq) acc.add_int32_narrow((int32_t)yi);
-        else acc.add_int32((int32_t)yi);
+        // |Y| < 2^31 here and the host bounds a group's sum of squares below 2^64
+        acc.add_group((int32_t)yi);
       } else {
         acc.add_int(yi);
       }
@@ -350,7 +364,7 @@ struct LevelSim {
       acc.add_real(y);
       ydump = (double)y;
     }
-    acc.nsat += sat;
+    acc.nsat += lsat;
     if (dump) {
       mlmc_sample_rec r;
       r.pf = (double)pf; r.pc = (double)pc;
@@ -360,12 +374,12 @@ struct LevelSim {
         r.af = ldexp((double)afS, -fx.fS);
         r.ac = level > 0 ? ldexp((double)acS, -fx.fS) : 0.0;
       } else if constexpr (HALF) {
-        r.af = HAS_APPROX ? (double)HO::to_f(hS) : 0.0;
-        r.ac = (HAS_APPROX && level > 0) ? (double)HO::to_f(hSc) : 0.0;
+        r.af = HAS_APPROX ? (double)HO::to_f(hS[l]) : 0.0;
+        r.ac = (HAS_APPROX && level > 0) ? (double)HO::to_f(hSc[l]) : 0.0;
       } else {
         r.af = 0.0; r.ac = 0.0;
       }
-      r.qf = qf; r.qc = qc; r.y = ydump; r.sat = sat; r.pad = 0;
+      r.qf = qf; r.qc = qc; r.y = ydump; r.sat = lsat; r.pad = 0;
       *dump = r;
     }
   }
@@ -382,19 +396,22 @@ struct ThreadAcc {
   double ds, dq;
   uint32_t nsat;
   __device__ __forceinline__ void init() {
-    isum = 0; q_lo = 0; q_hi = 0; ks.init(); kq.init(); ds = 0.0; dq = 0.0; nsat = 0;
+    isum = 0; q_lo = 0; q_hi = 0; gq = 0; ks.init(); kq.init(); ds = 0.0; dq = 0.0; nsat = 0;
   }
   __device__ __forceinline__ void add_int(int64_t y) {
     isum += y;
     add_square(q_lo, q_hi, y);
   }
-  __device__ __forceinline__ void add_int32(int32_t y) {
-    isum += y;
-    add_u128(q_lo, q_hi, (uint64_t)((int64_t)y * y), 0);
+  // Two wide multiply-adds per sample (FMA pipe): sum y and the group's sum of
+  // y^2 in 64 bits; flush_group() adds the latter into the 128-bit total.
+  uint64_t gq;
+  __device__ __forceinline__ void add_group(int32_t y) {
+    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(isum) : "r"(y), "r"(1));
+    asm("mad.wide.s32 %0, %1, %1, %0;" : "+l"(gq) : "r"(y));
   }
-  __device__ __forceinline__ void add_int32_narrow(int32_t y) {
-    isum += y;
-    q_lo += (uint64_t)((int64_t)y * y);
+  __device__ __forceinline__ void flush_group() {
+    add_u128(q_lo, q_hi, gq, 0);
+    gq = 0;
   }
   template <class T>
   __device__ __forceinline__ void add_real(T y) {
@@ -430,7 +447,7 @@ __device__ __forceinline__ void block_reduce_write(ThreadAcc<EST, XP> &a, Partia
     dq += shfl_xor(dq, m);
     ns += (uint64_t)shfl_xor((unsigned long long)ns, m);
   }
-  __shared__ Partial wp[MAX_THREADS / 32];
+  __shared__ Partial wp[LAUNCH_THREADS / 32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) {
     Partial p;
@@ -452,10 +469,10 @@ __device__ __forceinline__ void block_reduce_write(ThreadAcc<EST, XP> &a, Partia
   }
 }
 
-template <int EST, int XP, int AP, int SCHEME, int PC>
-__global__ void __launch_bounds__(MAX_THREADS)
+template <int EST, int XP, int AP, int SCHEME, int PC, int KP>
+__global__ void __launch_bounds__(LAUNCH_THREADS, MinCtas<EST, AP, SCHEME, PC>::value)
 level_kernel(const __grid_constant__ LaunchArgs args) {
-  using Sim = LevelSim<EST, XP, AP, SCHEME, PC>;
+  using Sim = LevelSim<EST, XP, AP, SCHEME, PC, KP>;
   extern __shared__ __align__(16) unsigned char smem_tab[];
   __shared__ int s_item;
   const uint32_t gc = args.chunk0 + blockIdx.x;
@@ -503,13 +520,15 @@ level_kernel(const __grid_constant__ LaunchArgs args) {
 
   const uint64_t gf0 = it.gf0, gf1 = it.gf1;
   const uint32_t ng = gend > gbeg ? (uint32_t)(gend - gbeg) : 0u;
+  // A group is one Philox call's worth of packs (4 on level 0, 2 on level 1) or,
+  // from level 2, one pack over 2^l / 4 calls; a pack holds KP samples.
   for (uint32_t r = threadIdx.x; r < ng; r += blockDim.x) {
     const uint64_t g = gbeg + r;
+    const bool full = g >= gf0 && g < gf1;
     if (lev >= 2) {
-      // one sample per group, 2^l / 4 Philox calls
-      const uint64_t s = g;
+      const uint64_t P = g;
       const uint32_t calls = 1u << (lev - 2);
-      const uint64_t qbase = s * calls;
+      const uint64_t qbase = P * calls;
       sim.begin();
       for (uint32_t c = 0; c < calls; ++c) {
         const uint64_t q = qbase + c;
@@ -520,43 +539,50 @@ level_kernel(const __grid_constant__ LaunchArgs args) {
         sim.template step<true>(w.z, i0 + 2);
         sim.template step<true>(w.w, i0 + 3);
       }
-      const bool valid = (g >= gf0 && g < gf1) || (s >= first && s < last);
-      sim.finish(acc, valid, dump && valid ? dump + (s - first) : nullptr);
+#pragma unroll
+      for (int l = 0; l < KP; ++l) {
+        const uint64_t s = P * KP + l;
+        const bool valid = full || (s >= first && s < last);
+        sim.finish(acc, l, valid, dump && valid ? dump + (s - first) : nullptr);
+      }
     } else {
       const uint4 w = philox4x32_10(make_uint4((uint32_t)g, (uint32_t)(g >> 32), ctr_hi.z, ctr_hi.w), args.rk);
-      const int spc = lev == 1 ? 2 : 4;
-      const uint64_t s0 = (uint64_t)spc * g;
+      const int ppg = lev == 1 ? 2 : 4;  // packs per group
+      const uint64_t s0 = (uint64_t)(ppg * KP) * g;
       // samples s0 + k are valid for k in [klo, khi)
-      int klo = 0, khi = spc;
-      if (!(g >= gf0 && g < gf1)) {
-        klo = s0 >= first ? 0 : (int)min(first - s0, (uint64_t)spc);
-        khi = last <= s0 ? 0 : (int)min(last - s0, (uint64_t)spc);
+      int klo = 0, khi = ppg * KP;
+      if (!full) {
+        klo = s0 >= first ? 0 : (int)min(first - s0, (uint64_t)(ppg * KP));
+        khi = last <= s0 ? 0 : (int)min(last - s0, (uint64_t)(ppg * KP));
       }
       if (lev == 1) {
-        sim.begin();
-        sim.template step<true>(w.x, 0);
-        sim.template step<true>(w.y, 1);
-        {
-          const bool valid = 0 >= klo && 0 < khi;
-          sim.finish(acc, valid, dump && valid ? dump + (s0 - first) : nullptr);
-        }
-        sim.begin();
-        sim.template step<true>(w.z, 0);
-        sim.template step<true>(w.w, 1);
-        {
-          const bool valid = 1 >= klo && 1 < khi;
-          sim.finish(acc, valid, dump && valid ? dump + (s0 + 1 - first) : nullptr);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          sim.begin();
+          sim.template step<true>(u == 0 ? w.x : w.z, 0);
+          sim.template step<true>(u == 0 ? w.y : w.w, 1);
+#pragma unroll
+          for (int l = 0; l < KP; ++l) {
+            const int k = u * KP + l;
+            const bool valid = k >= klo && k < khi;
+            sim.finish(acc, l, valid, dump && valid ? dump + (s0 + k - first) : nullptr);
+          }
         }
       } else {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int u = 0; u < 4; ++u) {
           sim.begin();
-          sim.template step<false>(word_of(w, k), 0);
-          const bool valid = k >= klo && k < khi;
-          sim.finish(acc, valid, dump && valid ? dump + (s0 + k - first) : nullptr);
+          sim.template step<false>(word_of(w, u), 0);
+#pragma unroll
+          for (int l = 0; l < KP; ++l) {
+            const int k = u * KP + l;
+            const bool valid = k >= klo && k < khi;
+            sim.finish(acc, l, valid, dump && valid ? dump + (s0 + k - first) : nullptr);
+          }
         }
       }
     }
+    if constexpr (EST == EST_APPROX && AP == AP_FX32 && PC == PC_TERMINAL) acc.flush_group();
   }
   block_reduce_write<EST, XP>(acc, args.partials + gc);
 }
@@ -565,9 +591,9 @@ level_kernel(const __grid_constant__ LaunchArgs args) {
 
 namespace mlmc {
 
-template <int EST, int XP, int AP, int SCHEME, int PC>
+template <int EST, int XP, int AP, int SCHEME, int PC, int KP>
 cudaError_t launch_one(dim3 grid, dim3 block, size_t smem, cudaStream_t st, const LaunchArgs &a) {
-  auto k = level_kernel<EST, XP, AP, SCHEME, PC>;
+  auto k = level_kernel<EST, XP, AP, SCHEME, PC, KP>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -577,16 +603,16 @@ cudaError_t launch_one(dim3 grid, dim3 block, size_t smem, cudaStream_t st, cons
 }
 
 // All (scheme, payoff class) instantiations of one (estimator, precision) family.
-template <int EST, int XP, int AP>
+template <int EST, int XP, int AP, int KP = 1>
 cudaError_t launch_family(int scheme, int pc, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                           const LaunchArgs &a) {
   switch (scheme * 3 + pc) {
-    case 0: return launch_one<EST, XP, AP, 0, PC_TERMINAL>(grid, block, smem, st, a);
-    case 1: return launch_one<EST, XP, AP, 0, PC_ASIAN>(grid, block, smem, st, a);
-    case 2: return launch_one<EST, XP, AP, 0, PC_LOOKBACK>(grid, block, smem, st, a);
-    case 3: return launch_one<EST, XP, AP, 1, PC_TERMINAL>(grid, block, smem, st, a);
-    case 4: return launch_one<EST, XP, AP, 1, PC_ASIAN>(grid, block, smem, st, a);
-    case 5: return launch_one<EST, XP, AP, 1, PC_LOOKBACK>(grid, block, smem, st, a);
+    case 0: return launch_one<EST, XP, AP, 0, PC_TERMINAL, KP>(grid, block, smem, st, a);
+    case 1: return launch_one<EST, XP, AP, 0, PC_ASIAN, KP>(grid, block, smem, st, a);
+    case 2: return launch_one<EST, XP, AP, 0, PC_LOOKBACK, KP>(grid, block, smem, st, a);
+    case 3: return launch_one<EST, XP, AP, 1, PC_TERMINAL, KP>(grid, block, smem, st, a);
+    case 4: return launch_one<EST, XP, AP, 1, PC_ASIAN, KP>(grid, block, smem, st, a);
+    case 5: return launch_one<EST, XP, AP, 1, PC_LOOKBACK, KP>(grid, block, smem, st, a);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -40,7 +40,7 @@ class Params(ctypes.Structure):
                 ("payoff", ctypes.c_int32), ("scheme", ctypes.c_int32),
                 ("icdf_method", ctypes.c_int32), ("icdf_bits", ctypes.c_int32),
                 ("formats", ctypes.POINTER(Format)), ("n_formats", ctypes.c_int32),
-                ("request_id", ctypes.c_uint32)]
+                ("request_id", ctypes.c_uint32), ("rng_pack", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Sums(ctypes.Structure):
@@ -123,7 +123,7 @@ def _sums_dict(s):
     return d
 
 
-def make_params(p, d=10, method=1, formats=None, request=0):
+def make_params(p, d=10, method=1, formats=None, request=0, rng_pack=0):
     """Build an mlmc_params from a dict (S0, K, r, sigma, T, payoff, scheme).
 
     formats: None (library default schedule) or a list, indexed by level, of
@@ -134,6 +134,8 @@ def make_params(p, d=10, method=1, formats=None, request=0):
     P.payoff, P.scheme = int(p["payoff"]), int(p["scheme"])
     P.icdf_method, P.icdf_bits = int(method), int(d)
     P.request_id = int(request)
+    P.rng_pack = int(rng_pack)
+    P.reserved = 0
     if formats is not None:
         arr = (Format * len(formats))()
         for i, fm in enumerate(formats):

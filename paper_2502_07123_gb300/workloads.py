@@ -106,7 +106,8 @@ def nested_counts(level: int) -> tuple:
 
 def nested_config():
     """Nested MLMC: European and digital call, EM, levels 0..8, Method-1 table with d = 10,
-    approximate paths in fixed point (default_format), correction = FP32 exact - fixed."""
+    approximate paths in fixed point (default_format) with packed draws (three table
+    indices per 32-bit word), correction = FP32 exact - fixed (one word per step)."""
     items = []
     for payoff in (EURO, DIGITAL):
         p = params(payoff=payoff)
@@ -115,7 +116,7 @@ def nested_config():
             items.append(dict(params=p, level=lev, N=n_a, variant=FIXED_APPROX, request=payoff))
             items.append(dict(params=p, level=lev, N=n_c, variant=CORR_FIXED, request=payoff))
     return dict(name="nested-fixed-em-euro+digital-l0-8", items=items, d=10, method=1,
-                seed=SEED_NESTED)
+                seed=SEED_NESTED, rng_pack=1)
 
 
 def sweep_points():

@@ -43,7 +43,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_struct_layouts(lib):
-    assert ctypes.sizeof(lib.Params) == 72
+    assert ctypes.sizeof(lib.Params) == 80
     assert ctypes.sizeof(lib.Sums) == 72
     assert ctypes.sizeof(lib.Work) == 40
     assert lib.SAMPLE_BYTES == 80

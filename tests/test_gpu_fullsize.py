@@ -41,7 +41,7 @@ def test_nested_workload_full_size(m):
         assert r["n"] == it["N"]
         if it["variant"] == W.FIXED_APPROX:
             o, _ = core.level(p, it["level"], 0, it["N"], it["variant"], cfg["seed"], request=it["request"],
-                              d=cfg["d"], method=cfg["method"], fmt=fmt)
+                              d=cfg["d"], method=cfg["method"], fmt=fmt, pack=cfg["rng_pack"])
             assert r["isum"] == o["isum"] and r["isum2"] == o["isum2"], it
             assert r["saturations"] == o["saturations"]
         else:
@@ -66,10 +66,12 @@ def test_nested_workload_sampled_samples(m):
             continue
         p = it["params"]
         fmts = [W.default_format(p, lev) for lev in range(9)]
-        P = m.make_params(p, d=cfg["d"], method=cfg["method"], formats=fmts, request=it["request"])
+        P = m.make_params(p, d=cfg["d"], method=cfg["method"], formats=fmts, request=it["request"],
+                          rng_pack=cfg["rng_pack"])
+        pack = cfg["rng_pack"] if it["variant"] == W.FIXED_APPROX else 0
         _, gd = m.mlmc_level_dump(it["level"], it["N"], P, it["variant"], cfg["seed"], 0)
         idx = np.sort(rng.choice(it["N"], size=64, replace=False))
         for s in idx:
             _, od = core.level(p, it["level"], int(s), 1, it["variant"], cfg["seed"], request=it["request"],
-                               d=cfg["d"], method=cfg["method"], fmt=fmts[it["level"]], dump=True)
+                               d=cfg["d"], method=cfg["method"], fmt=fmts[it["level"]], dump=True, pack=pack)
             compare_samples(it["variant"], p, gd[s:s + 1], od)

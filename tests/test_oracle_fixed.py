@@ -105,20 +105,24 @@ for lev in (0, 1, 2):
             CASES.append((lev, payoff, scheme, int(rng.integers(6, 21)), int(rng.integers(0, 1000))))
 
 
+@pytest.mark.parametrize("pack", [0, 1])
 @pytest.mark.parametrize("lev,payoff,scheme,fbits,seed", CASES)
-def test_fixed_point_matches_rationals(lev, payoff, scheme, fbits, seed):
+def test_fixed_point_matches_rationals(lev, payoff, scheme, fbits, seed, pack):
     p = W.params(payoff=payoff, scheme=scheme, sigma=0.3)
     fmt = W.default_format(p, lev)
     r = np.random.default_rng(seed)
     fmt["f"] = [int(x) for x in r.integers(max(4, fbits - 4), fbits + 5, 7)]
     d = 8
     N = 64
-    sums, dump = core.level(p, lev, 1000, N, core.FIXED_APPROX, seed, d=d, fmt=fmt, dump=True)
+    sums, dump = core.level(p, lev, 1000, N, core.FIXED_APPROX, seed, d=d, fmt=fmt, dump=True, pack=pack)
     ztab = tables.table(d, 1, "fixed", fmt["f"][V_Z])
     n = 1 << lev
     s_idx = np.repeat(np.arange(1000, 1000 + N, dtype=np.uint64), n)
     steps = np.tile(np.arange(n, dtype=np.uint32), N)
-    J = core.draws(seed, 0, lev, 1, s_idx, steps).reshape(N, n)
+    if pack:
+        J = core.draws_packed(seed, 0, lev, 1, s_idx, steps, d).reshape(N, n)
+    else:
+        J = core.draws(seed, 0, lev, 1, s_idx, steps).reshape(N, n)
     unit = sums["unit"]
     tot = 0
     for t in range(N):
