@@ -164,6 +164,8 @@ def main():
     ap.add_argument("--ref-fraction", type=float, default=0.1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tte", action="store_true")
+    ap.add_argument("--serving", action="store_true",
+                    help="also run the batched (256 options) and serving (Poisson arrivals) workloads")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -244,13 +246,15 @@ def main():
     fam_steps = {8: sum(it["N"] << it["level"] for it in items
                         if it["variant"] == m.FIXED_APPROX and it["level"] <= 7),
                  2: sum(it["N"] << it["level"] for it in items if it["variant"] == m.FIXED_APPROX)}
+    fam_steps[15] = fam_steps[8]
+    fam_names = {8: "level_kernel<APPROX,F32,FX32,EM,terminal>", 2: "level_kernel<APPROX,F32,FIXED,EM,terminal>",
+                 15: "level_kernel<APPROX,F32,FX32,EM,terminal,packed x3>"}
     roofline = None
     if dom in fam_steps:
         achieved = OPS_APPROX_FIXED_EM * fam_steps[dom] / (dom_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Top/s",
                     "frac": achieved / ALU_PEAK_TOPS, "traffic": None,
-                    "kernel": "level_kernel<APPROX,F32,FX32,EM,terminal>" if dom == 8
-                    else "level_kernel<APPROX,F32,FIXED,EM,terminal>",
+                    "kernel": fam_names[dom],
                     "ms_per_launch": dom_ms, "ops_per_path_step": OPS_APPROX_FIXED_EM,
                     "path_steps_per_launch": fam_steps[dom]}
 
@@ -271,6 +275,9 @@ def main():
     }
     if rank == 0 and not args.no_tte:
         out["time_to_eps"] = time_to_eps(m, torch)
+    if rank == 0 and world == 1 and args.serving:
+        out["batched"] = batched_run(m)
+        out["serving"] = [serving_run(m, rate) for rate in (100, 1000, 10000)]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import build as ob
         ob.build()
@@ -283,6 +290,85 @@ def main():
     plan.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def _bs_price(o):
+    """Black-Scholes value of a European or digital call (None for other payoffs)."""
+    from scipy.stats import norm
+    S0, K, r, sig, T = o["S0"], o["K"], o["r"], o["sigma"], o["T"]
+    d1 = (math.log(S0 / K) + (r + 0.5 * sig * sig) * T) / (sig * math.sqrt(T))
+    d2 = d1 - sig * math.sqrt(T)
+    if o["payoff"] == W.EURO:
+        return S0 * norm.cdf(d1) - K * math.exp(-r * T) * norm.cdf(d2)
+    if o["payoff"] == W.DIGITAL:
+        return math.exp(-r * T) * norm.cdf(d2)
+    return None
+
+
+def _engine_params(m, o, request):
+    return m.make_params(o, d=10, method=1, formats=[W.default_format(o, lev) for lev in range(11)],
+                         request=request, rng_pack=1)
+
+
+def batched_run(m, n=256, seed=7, mode=2):
+    """All n options of the batched workload submitted at once to the engine."""
+    opts = W.batched_options(n, seed)
+    eng = m.Engine(max_slots=n, max_level=10)
+    t0 = time.perf_counter()
+    rids = [eng.submit(_engine_params(m, o, i), o["eps"], mode, 1) for i, o in enumerate(opts)]
+    done = {}
+    while len(done) < n:
+        eng.step()
+        for i, r in enumerate(rids):
+            if i not in done:
+                res = eng.poll(r)
+                if res is not None:
+                    done[i] = res
+    wall = time.perf_counter() - t0
+    st = eng.stats()
+    eng.close()
+    errs = [(done[i]["price"] - _bs_price(o)) / o["eps"] for i, o in enumerate(opts) if _bs_price(o) is not None]
+    lat = sorted(done[i]["latency_s"] for i in range(n))
+    return {"requests": n, "wall_s": wall, "requests_per_s": n / wall, "engine_steps": st["steps"],
+            "launches": st["launches"], "path_steps": st["path_steps"], "path_steps_per_s": st["path_steps"] / wall,
+            "rms_err_over_eps_vs_black_scholes": math.sqrt(sum(e * e for e in errs) / len(errs)),
+            "checked_against_black_scholes": len(errs), "p50_latency_s": lat[n // 2],
+            "p99_latency_s": lat[min(n - 1, int(0.99 * n))]}
+
+
+def serving_run(m, rate, n=400, seed=11, mode=2):
+    """Poisson arrivals at `rate` req/s, options drawn as the batched workload;
+    requests are admitted while others run (continuous batching)."""
+    arrivals = W.poisson_arrivals(rate, n, seed)
+    opts = W.batched_options(n, seed)
+    eng = m.Engine(max_slots=256, max_level=10)
+    rids = [None] * n
+    done = {}
+    nxt = 0
+    t0 = time.perf_counter()
+    while len(done) < n:
+        t = time.perf_counter() - t0
+        while nxt < n and arrivals[nxt] <= t:
+            rids[nxt] = eng.submit(_engine_params(m, opts[nxt], nxt), opts[nxt]["eps"], mode, 1)
+            nxt += 1
+        if nxt == len(done) and nxt < n:
+            time.sleep(max(0.0, min(arrivals[nxt] - t, 0.01)))
+            continue
+        eng.step()
+        for i in range(nxt):
+            if i not in done:
+                res = eng.poll(rids[i])
+                if res is not None:
+                    done[i] = res
+    wall = time.perf_counter() - t0
+    st = eng.stats()
+    eng.close()
+    lat = sorted(done[i]["latency_s"] for i in range(n))
+    errs = [(done[i]["price"] - _bs_price(o)) / o["eps"] for i, o in enumerate(opts) if _bs_price(o) is not None]
+    return {"arrival_rate": rate, "requests": n, "wall_s": wall, "requests_per_s": n / wall,
+            "p50_latency_s": lat[n // 2], "p99_latency_s": lat[min(n - 1, int(0.99 * n))],
+            "engine_steps": st["steps"], "launches": st["launches"],
+            "rms_err_over_eps_vs_black_scholes": math.sqrt(sum(e * e for e in errs) / len(errs))}
 
 
 def time_to_eps(m, torch, eps=1e-3, seeds=(1, 2, 3)):

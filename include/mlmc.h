@@ -233,6 +233,42 @@ mlmc_status mlmc_estimate(double eps, const mlmc_params *p, int mode, uint64_t s
                           int max_level, double *price, double *stderr_out, int *L,
                           uint64_t *N_l, int cap_levels);
 
+/* ---- continuous-batching engine (many adaptive requests per launch) --------
+ * Requests (params, eps, mode, seed) queue on submit and are admitted into free
+ * slots; each slot keeps its adaptive state (sums of Y and Y^2, sample counts,
+ * pending counts per level and estimator) in FP64 in device memory.  One
+ * mlmc_engine_step admits waiting requests, runs the pending work of every
+ * active request in one batched plan launch per distinct seed, and updates
+ * every slot on the device: level variances, N = ceil(lambda sqrt(V/C))
+ * (Sec. 2.1 / 2.2), the bias test, a new level or completion -- the same
+ * algorithm and arithmetic as mlmc_estimate, so a request's result is the same
+ * whatever else runs beside it.  Slots are limited by max_slots and by
+ * device_bytes_budget (0 = no budget).  Requests that share a seed must have
+ * distinct request_id values in their params.
+ * Errors: MLMC_EINVAL for bad arguments (params->formats, when given, must
+ * cover levels 0..max_level), MLMC_ENOMEM, MLMC_ECUDA. */
+typedef struct {
+  int32_t max_slots;             /* concurrent requests (0 = 256)           */
+  int32_t max_level;             /* L_max of every request, 2..20           */
+  uint64_t device_bytes_budget;  /* bytes of slot state allowed, 0 = any    */
+} mlmc_engine_config;
+typedef struct mlmc_engine mlmc_engine;
+mlmc_status mlmc_engine_create(mlmc_engine **e, const mlmc_engine_config *cfg);
+/* Copies *p (and its format table); mode as mlmc_estimate. */
+mlmc_status mlmc_engine_submit(mlmc_engine *e, const mlmc_params *p, double eps, int mode, uint64_t seed,
+                               uint64_t *req_id);
+/* One engine iteration on `stream` (synchronous).  *active = requests holding a
+ * slot after the step, *queued = requests waiting for one (either may be NULL). */
+mlmc_status mlmc_engine_step(mlmc_engine *e, void *stream, int *active, int *queued);
+/* *done = 1 once the request has completed; then price, standard error, final
+ * level and latency (seconds from submit to completion) are filled in. */
+mlmc_status mlmc_engine_poll(mlmc_engine *e, uint64_t req_id, double *price, double *stderr_out, int *L,
+                             int *done, double *latency_s);
+/* Engine counters: steps taken, plan launches, fine path-steps simulated, slots. */
+mlmc_status mlmc_engine_stats(const mlmc_engine *e, uint64_t *steps, uint64_t *launches,
+                              uint64_t *path_steps, int *slots);
+void mlmc_engine_destroy(mlmc_engine *e);
+
 /* Cost per fine path-step of each estimator kind used by mlmc_estimate
  * (relative units; defaults: exact FP32 1.0, exact FP64 8.0, approximate 0.5,
  * correction 1.5).  kind: 0 exact FP64, 1 exact FP32, 2 approximate, 3 correction.
@@ -243,7 +279,8 @@ mlmc_status mlmc_cost_model(int kind, double cost_per_step);
 /* The default fixed-point schedule for a level (used when params->formats is NULL).
  * Fractional bits f = {12, 16+l, 14+l, 12+l, 12+l, 12+l, 14+l} clamped to [10, 24]
  * (one more bit per level, Sec. 6.3).  Integer bits e are the smallest with
- * |x| < 2^e (and e + f >= 1) for these bounds, h = T 2^-l:
+ * |x| < 2^e (and e + f >= 1) for these bounds, h = T 2^-l (for con1, con2 and
+ * S, whose bounds include rounded constants: x + 2^-(f+1) < 2^e):
  *   Z~ 8;  con1 max(|r| 2h, sigma^2 h / 2);  con2 sigma sqrt(h);
  *   mul1 M = max(16 sigma sqrt(h), 128 sigma^2 h);  sum1 |r| 2h + M;
  *   S max(S0 exp(|r| T + 6 sigma sqrt(T)), K);  mul2 e_S + e_sum1. */

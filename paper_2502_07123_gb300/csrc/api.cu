@@ -19,6 +19,7 @@
 #include "kernels.h"
 #include "mlmc.h"
 #include "tables.h"
+#include "host_api.h"
 
 using namespace mlmc;
 
@@ -63,7 +64,7 @@ struct mlmc_plan {
   bool borrowed = false;   // device buffers, streams and events belong to the context arena
 };
 
-namespace {
+namespace mlmc_host {
 
 // ---------------------------------------------------------------------------
 // device context and table cache
@@ -238,6 +239,8 @@ int bitlen(double x, int f) {
   if (x <= 0.0) return 1 - f;
   return std::max((int)std::floor(std::log2(x)) + 1, 1 - f);
 }
+// e such that x rounded to f fractional bits stays below 2^e: x + 2^-(f+1) < 2^e
+int bitlen_rounded(double x, int f) { return bitlen(x + std::ldexp(1.0, -(f + 1)), f); }
 
 void default_format(const mlmc_params *p, int level, mlmc_format *out) {
   const double r = p->r, sig = p->sigma, T = p->T, S0 = p->S0, K = p->K;
@@ -247,11 +250,11 @@ void default_format(const mlmc_params *p, int level, mlmc_format *out) {
   const double mul1_bound = std::max(16.0 * sig * std::sqrt(h), 128.0 * sig * sig * h);
   int e[7];
   e[F_Z] = 3;
-  e[F_CON1] = bitlen(std::max(std::fabs(r) * 2.0 * h, 0.5 * sig * sig * h), f[F_CON1]);
-  e[F_CON2] = bitlen(sig * std::sqrt(h), f[F_CON2]);
+  e[F_CON1] = bitlen_rounded(std::max(std::fabs(r) * 2.0 * h, 0.5 * sig * sig * h), f[F_CON1]);
+  e[F_CON2] = bitlen_rounded(sig * std::sqrt(h), f[F_CON2]);
   e[F_MUL1] = bitlen(mul1_bound, f[F_MUL1]);
   e[F_SUM1] = bitlen(std::fabs(r) * 2.0 * h + mul1_bound, f[F_SUM1]);
-  e[F_S] = bitlen(std::max(S0 * std::exp(std::fabs(r) * T + 6.0 * sig * std::sqrt(T)), K), f[F_S]);
+  e[F_S] = bitlen_rounded(std::max(S0 * std::exp(std::fabs(r) * T + 6.0 * sig * std::sqrt(T)), K), f[F_S]);
   e[F_MUL2] = e[F_S] + e[F_SUM1];
   for (int i = 0; i < 7; ++i) { out->e[i] = (int8_t)e[i]; out->f[i] = (int8_t)f[i]; }
 }
@@ -910,7 +913,34 @@ mlmc_status run_sync(const mlmc_work *work, int n_work, uint64_t seed, const mlm
   return s;
 }
 
-}  // namespace
+cudaStream_t ctx_stream() { return g.st; }
+double cost_of_variant(int variant) { return g_cost[cost_kind_of(variant)]; }
+mlmc_status plan_create_transient(mlmc_plan **out, const mlmc_work *work, int n_work, uint64_t seed,
+                                  const mlmc_tuning *tuning) {
+  return plan_create_impl(out, work, n_work, seed, tuning, nullptr, &g.arena);
+}
+mlmc_status plan_launch_on(mlmc_plan *pl, cudaStream_t st) {
+  if (st != g.st) {
+    // a transient plan's work list was copied on the context stream: order after it
+    MLMC_CK(cudaEventRecord(g.arena.fork, g.st));
+    MLMC_CK(cudaStreamWaitEvent(st, g.arena.fork, 0));
+  }
+  return plan_launch_impl(pl, st);
+}
+const mlmc::DevSums *plan_out_device(const mlmc_plan *pl) { return pl->d_out; }
+void plan_item_scale(const mlmc_plan *pl, int i, double *disc, int *unit, int *exact_int) {
+  *disc = pl->disc[i];
+  *unit = pl->unit[i];
+  *exact_int = pl->exact_int[i];
+}
+void plan_release(mlmc_plan *pl) {
+  free_plan_device(pl);
+  delete pl;
+}
+
+}  // namespace mlmc_host
+
+using namespace mlmc_host;
 
 // ---------------------------------------------------------------------------
 // C ABI

@@ -54,6 +54,11 @@ class Tuning(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("steps_per_thread", ctypes.c_int32)]
 
 
+class EngineConfig(ctypes.Structure):
+    _fields_ = [("max_slots", ctypes.c_int32), ("max_level", ctypes.c_int32),
+                ("device_bytes_budget", ctypes.c_uint64)]
+
+
 class Work(ctypes.Structure):
     _fields_ = [("params", ctypes.POINTER(Params)), ("level", ctypes.c_int32), ("variant", ctypes.c_int32),
                 ("first_sample", ctypes.c_uint64), ("N", ctypes.c_uint64),
@@ -98,6 +103,15 @@ def load():
                                P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_int), P(ctypes.c_uint64),
                                ctypes.c_int]),
         "mlmc_cost_model": (st, [ctypes.c_int, ctypes.c_double]),
+        "mlmc_engine_create": (st, [P(ctypes.c_void_p), P(EngineConfig)]),
+        "mlmc_engine_submit": (st, [ctypes.c_void_p, P(Params), ctypes.c_double, ctypes.c_int, ctypes.c_uint64,
+                                    P(ctypes.c_uint64)]),
+        "mlmc_engine_step": (st, [ctypes.c_void_p, ctypes.c_void_p, P(ctypes.c_int), P(ctypes.c_int)]),
+        "mlmc_engine_poll": (st, [ctypes.c_void_p, ctypes.c_uint64, P(ctypes.c_double), P(ctypes.c_double),
+                                  P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_double)]),
+        "mlmc_engine_stats": (st, [ctypes.c_void_p, P(ctypes.c_uint64), P(ctypes.c_uint64), P(ctypes.c_uint64),
+                                   P(ctypes.c_int)]),
+        "mlmc_engine_destroy": (None, [ctypes.c_void_p]),
         "mlmc_default_format": (st, [P(Params), ctypes.c_int, P(Format)]),
         "mlmc_icdf_table": (st, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_double)]),
         "mlmc_philox": (st, [P(ctypes.c_uint32), ctypes.c_uint64, ctypes.c_uint64, P(ctypes.c_uint32)]),
@@ -280,6 +294,56 @@ def mlmc_estimate(eps, params, mode, seed, max_level=10):
                            ctypes.byref(se), ctypes.byref(lev), Nl, cap), "mlmc_estimate")
     N = [[int(Nl[2 * l]), int(Nl[2 * l + 1])] for l in range(lev.value + 1)]
     return dict(price=price.value, stderr=se.value, L=lev.value, N=N)
+
+
+class Engine:
+    """Continuous-batching engine (mlmc_engine_*): submit requests, step, poll."""
+
+    def __init__(self, max_slots=256, max_level=10, device_bytes_budget=0):
+        L = load()
+        cfg = EngineConfig(max_slots, max_level, device_bytes_budget)
+        self._h = ctypes.c_void_p()
+        _check(L.mlmc_engine_create(ctypes.byref(self._h), ctypes.byref(cfg)), "mlmc_engine_create")
+        self._keep = {}
+
+    def submit(self, params, eps, mode, seed):
+        rid = ctypes.c_uint64()
+        _check(load().mlmc_engine_submit(self._h, ctypes.byref(params), eps, mode, seed, ctypes.byref(rid)),
+               "mlmc_engine_submit")
+        return rid.value
+
+    def step(self, stream=None):
+        a, q = ctypes.c_int(), ctypes.c_int()
+        h = ctypes.c_void_p(None) if stream is None else _stream_handle(stream)
+        _check(load().mlmc_engine_step(self._h, h, ctypes.byref(a), ctypes.byref(q)), "mlmc_engine_step")
+        return a.value, q.value
+
+    def poll(self, rid):
+        pr, se, lat = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        lev, done = ctypes.c_int(), ctypes.c_int()
+        _check(load().mlmc_engine_poll(self._h, rid, ctypes.byref(pr), ctypes.byref(se), ctypes.byref(lev),
+                                       ctypes.byref(done), ctypes.byref(lat)), "mlmc_engine_poll")
+        if not done.value:
+            return None
+        return dict(price=pr.value, stderr=se.value, L=lev.value, latency_s=lat.value)
+
+    def stats(self):
+        a, b, c = (ctypes.c_uint64() for _ in range(3))
+        sl = ctypes.c_int()
+        _check(load().mlmc_engine_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                        ctypes.byref(sl)), "mlmc_engine_stats")
+        return dict(steps=a.value, launches=b.value, path_steps=c.value, slots=sl.value)
+
+    def close(self):
+        if self._h:
+            load().mlmc_engine_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def mlmc_cost_model(kind, cost_per_step):

@@ -41,6 +41,12 @@ def _bitlen(x: float, f: int) -> int:
     return max(int(math.floor(math.log2(x))) + 1, 1 - f)
 
 
+def _bitlen_rounded(x: float, f: int) -> int:
+    """Integer bits e such that x rounded to f fractional bits stays below 2^e:
+    x + 2^-(f+1) < 2^e."""
+    return _bitlen(x + math.ldexp(1.0, -(f + 1)), f)
+
+
 def default_format(p: dict, level: int) -> dict:
     """Per-level fixed-point formats (e_i, f_i) for the Algorithm-1 variables.
 
@@ -48,7 +54,8 @@ def default_format(p: dict, level: int) -> dict:
     this is a stated schedule: fractional bits grow by one per level (the
     d_S,l+1 = d_S,l + 1 trend of Sec. 6.3) and follow the size ordering of
     Sec. 6.3 (con1 ~ h, con2/mul1/sum1/mul2 ~ sqrt(h), S ~ 1), clamped to
-    [10, 24].  Integer bits bound each variable's magnitude:
+    [10, 24].  Integer bits bound each variable's magnitude (for the rounded
+    constants con1, con2, S0 and K: their values rounded to f bits):
       Z     : |Z~| < 8 for every table size d <= 16 (coarse sums are exact),
       con1  : max(|r| 2h, sigma^2 h / 2) (the Milstein constant shares it),
       con2  : sigma sqrt(h),
@@ -72,11 +79,11 @@ def default_format(p: dict, level: int) -> dict:
     mul1_bound = max(16.0 * sig * math.sqrt(h), 128.0 * sig * sig * h)
     e = {
         "Z": 3,
-        "con1": _bitlen(max(abs(r) * 2.0 * h, 0.5 * sig * sig * h), f["con1"]),
-        "con2": _bitlen(sig * math.sqrt(h), f["con2"]),
+        "con1": _bitlen_rounded(max(abs(r) * 2.0 * h, 0.5 * sig * sig * h), f["con1"]),
+        "con2": _bitlen_rounded(sig * math.sqrt(h), f["con2"]),
         "mul1": _bitlen(mul1_bound, f["mul1"]),
         "sum1": _bitlen(abs(r) * 2.0 * h + mul1_bound, f["sum1"]),
-        "S": _bitlen(max(S0 * math.exp(abs(r) * T + 6.0 * sig * math.sqrt(T)), K), f["S"]),
+        "S": _bitlen_rounded(max(S0 * math.exp(abs(r) * T + 6.0 * sig * math.sqrt(T)), K), f["S"]),
     }
     e["mul2"] = e["S"] + e["sum1"]
     return {"e": [e[v] for v in FORMAT_VARS], "f": [f[v] for v in FORMAT_VARS]}

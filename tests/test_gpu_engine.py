@@ -1,0 +1,114 @@
+"""Continuous-batching engine: each request's result is the same alone, in a
+mix of other requests, and through mlmc_estimate (same algorithm and
+arithmetic, work of other requests only shares the launches); prices agree
+with Black-Scholes within their error bars; admission respects slots and the
+memory budget."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2502_07123_gb300 import workloads as W
+from tests.test_oracle_paths import black_scholes_call, black_scholes_digital
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def m():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2502_07123_gb300 import mlmc
+    return mlmc
+
+
+def _P(m, p, request, pack=1):
+    return m.make_params(p, d=10, method=1, formats=[W.default_format(p, lev) for lev in range(11)],
+                         request=request, rng_pack=pack)
+
+
+def _run(eng, rids):
+    out = {}
+    for _ in range(10_000):
+        active, queued = eng.step()
+        for r in rids:
+            if r not in out:
+                res = eng.poll(r)
+                if res is not None:
+                    out[r] = res
+        if len(out) == len(rids):
+            return out
+    raise AssertionError("engine did not finish")
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_engine_equals_estimate_and_is_mix_independent(m, mode):
+    pA = W.params(payoff=W.EURO)
+    eps = 0.02
+    ref = m.mlmc_estimate(eps, _P(m, pA, 17), mode, 5, 10)
+    # alone
+    eng = m.Engine(max_slots=8, max_level=10)
+    rid = eng.submit(_P(m, pA, 17), eps, mode, 5)
+    alone = _run(eng, [rid])[rid]
+    eng.close()
+    assert alone["price"] == ref["price"] and alone["stderr"] == ref["stderr"] and alone["L"] == ref["L"]
+    # in a mix of 40 other requests (different options, accuracies, payoffs), admitted over time
+    opts = W.batched_options(40, seed=3)
+    eng = m.Engine(max_slots=16, max_level=10)
+    others = []
+    for i, o in enumerate(opts[:20]):
+        others.append(eng.submit(_P(m, o, 100 + i), max(o["eps"], 5e-3) * 4, mode, 5))
+    eng.step()
+    eng.step()
+    ridA = eng.submit(_P(m, pA, 17), eps, mode, 5)
+    for i, o in enumerate(opts[20:]):
+        others.append(eng.submit(_P(m, o, 200 + i), max(o["eps"], 5e-3) * 4, mode, 5))
+    res = _run(eng, [ridA] + others)
+    st = eng.stats()
+    eng.close()
+    mixed = res[ridA]
+    assert mixed["price"] == alone["price"] and mixed["stderr"] == alone["stderr"] and mixed["L"] == alone["L"]
+    assert st["launches"] < st["steps"] * 2   # many requests per launch
+
+
+def test_engine_prices_match_black_scholes(m):
+    eng = m.Engine(max_slots=32, max_level=10)
+    cases = []
+    rng = np.random.default_rng(4)
+    for i in range(24):
+        p = W.params(S0=float(rng.uniform(80, 120)), K=float(rng.uniform(80, 120)),
+                     sigma=float(rng.uniform(0.1, 0.4)), T=float(rng.uniform(0.25, 2.0)),
+                     payoff=int(rng.integers(0, 2)))
+        eps = float(np.exp(rng.uniform(np.log(0.01), np.log(0.05))))
+        rid = eng.submit(_P(m, p, i), eps, 2, 11)
+        cases.append((rid, p, eps))
+    res = _run(eng, [c[0] for c in cases])
+    eng.close()
+    z = []
+    for rid, p, eps in cases:
+        f = black_scholes_call if p["payoff"] == W.EURO else black_scholes_digital
+        ref = f(p["S0"], p["K"], p["r"], p["sigma"], p["T"])
+        r = res[rid]
+        assert abs(r["price"] - ref) < 4 * r["stderr"] + eps / math.sqrt(2), (p, r, ref)
+        z.append((r["price"] - ref) / eps)
+    assert math.sqrt(np.mean(np.square(z))) < 1.5   # RMS error about eps
+
+
+def test_engine_admission_by_slots_and_memory(m):
+    eng = m.Engine(max_slots=3, max_level=8)
+    assert eng.stats()["slots"] == 3
+    rids = [eng.submit(_P(m, W.params(), i), 0.05, 1, 9) for i in range(7)]
+    a, q = eng.step()
+    assert a <= 3 and q == 4
+    res = _run(eng, rids)
+    assert len(res) == 7
+    eng.close()
+    with pytest.raises(m.MLMCError) as e:
+        m.Engine(max_slots=4, max_level=8, device_bytes_budget=64)
+    assert e.value.status == m.ENOMEM
+    small = m.Engine(max_slots=100, max_level=8, device_bytes_budget=2 * 3000)
+    assert small.stats()["slots"] < 100
+    small.close()
