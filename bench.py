@@ -376,7 +376,9 @@ def time_to_eps(m, torch, eps=1e-3, seeds=(1, 2, 3)):
     p = W.params()
     P = m.make_params(p, d=10, method=1, formats=[W.default_format(p, lev) for lev in range(11)], rng_pack=1)
     out = {"eps": eps}
-    for name, mode in (("plain_fp32", m.MODE_PLAIN_FP32), ("nested_fixed", m.MODE_NESTED_FIXED)):
+    for name, mode in (("plain_fp32", m.MODE_PLAIN_FP32), ("nested_fixed", m.MODE_NESTED_FIXED),
+                       ("nested_fixed_exact_low", m.MODE_NESTED_FIXED_EXACT_LOW),
+                       ("nested_fp16_exact_low", m.MODE_NESTED_FP16_EXACT_LOW)):
         m.mlmc_estimate(1e-2, P, mode, 99, 10)   # warm tables and contexts
         ts, prices = [], []
         for s in seeds:
@@ -386,7 +388,8 @@ def time_to_eps(m, torch, eps=1e-3, seeds=(1, 2, 3)):
             ts.append(time.perf_counter() - t0)
             prices.append(r["price"])
         out[name] = {"s_median": statistics.median(ts), "prices": prices, "L": r["L"], "N": r["N"]}
-    out["speedup_nested_vs_plain"] = out["plain_fp32"]["s_median"] / out["nested_fixed"]["s_median"]
+    for name in ("nested_fixed", "nested_fixed_exact_low", "nested_fp16_exact_low"):
+        out["speedup_%s_vs_plain_fp32" % name] = out["plain_fp32"]["s_median"] / out[name]["s_median"]
     return out
 
 

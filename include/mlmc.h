@@ -141,8 +141,16 @@ typedef struct {
   uint64_t N;
   int32_t stream;               /* Philox stream id 0..255, or -1 for the default
                                    (1 for APPROX variants, 0 otherwise)          */
-  int32_t pad;
+  int32_t flags;                /* bit 0 (MLMC_WORK_ENUMERATE): instead of random
+                                   draws, sample s of an approximate-only estimator
+                                   on level 0 or 1 takes table index
+                                   j_i = (s >> (d i)) mod 2^d at fine step i, so
+                                   samples [0, 2^(d 2^l)) cover every combination of
+                                   table cells once and their mean is E[dP~_l]
+                                   exactly; needs first_sample = 0 and
+                                   N = 2^(d 2^l) <= 2^24 */
 } mlmc_work;
+#define MLMC_WORK_ENUMERATE 1
 
 typedef struct mlmc_plan mlmc_plan;
 
@@ -223,7 +231,12 @@ mlmc_status mlmc_run(const mlmc_work *work, int n_work, uint64_t seed,
  * L from 2 up to max_level, 10^4 initial samples per level and estimator,
  * sample counts N = ceil(lambda sqrt(V/C)) with lambda = (eps^2/2)^-1 sum sqrt(V C)
  * over every (level, estimator) term.  mode: 0 plain FP64, 1 plain FP32,
- * 2 nested fixed point, 3 nested binary16, 4 nested bfloat16.  The cost model
+ * 2 nested fixed point, 3 nested binary16, 4 nested bfloat16, 5 and 6 nested
+ * fixed point / binary16 whose approximate terms on levels 0 and 1 (when
+ * d 2^l <= 20) are computed exactly, by enumerating the 2^(d 2^l) combinations
+ * of table cells (MLMC_WORK_ENUMERATE), and then carry no variance and take no
+ * further samples (the approximate Normal has finitely many values; the
+ * corrections stay Monte Carlo).  The cost model
  * is C = 2^l c_kind with c_kind from mlmc_cost_model (deterministic).
  * Outputs (host): *price, *stderr_out, *L; N_l[l * 2 + k] = samples of
  * estimator k on level l (k = 0: plain or approximate, k = 1: correction), for

@@ -97,7 +97,7 @@ def lib():
         L.or_level.argtypes = [ctypes.POINTER(Params), ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
                                ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(Format), ctypes.c_int,
-                               ctypes.POINTER(Sums), ctypes.c_void_p]
+                               ctypes.c_int, ctypes.POINTER(Sums), ctypes.c_void_p]
         L.or_level.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -170,7 +170,7 @@ class OracleError(RuntimeError):
 
 
 def level(p, lev, first, N, variant, seed, request=0, stream=None, d=10, method=1,
-          fmt=None, dump=False, pack=0):
+          fmt=None, dump=False, pack=0, enumerate=0):
     """Simulate samples [first, first+N) of one level; return (sums dict, dump array or None).
 
     p: dict with S0, K, r, sigma, T, payoff, scheme.
@@ -192,7 +192,7 @@ def level(p, lev, first, N, variant, seed, request=0, stream=None, d=10, method=
     st = lib().or_level(ctypes.byref(P), int(lev), int(first), int(N), int(variant), int(seed),
                         int(request), int(stream), int(d),
                         ztab.ctypes.data if ztab is not None else None,
-                        ctypes.byref(F) if F is not None else None, int(pack),
+                        ctypes.byref(F) if F is not None else None, int(pack), int(enumerate),
                         ctypes.byref(S), out.ctypes.data if dump else None)
     if st != 0:
         raise OracleError("or_level returned %d" % st)

@@ -35,16 +35,36 @@ def total_cost(V, C, eps2):
     return (sum(math.sqrt(v * c) for v, c in zip(V, C))) ** 2 / eps2
 
 
+def floor_levels(values, factor):
+    """Giles' safeguard against levels whose few samples show almost nothing:
+    from level 2 on, x_l >= x_{l-1} / (2 factor), applied in level order."""
+    out = list(values)
+    for l in range(2, len(out)):
+        out[l] = max(out[l], 0.5 * out[l - 1] / factor)
+    return out
+
+
 def bias_estimate(means, alpha=1.0):
-    """Giles (2008) remaining-bias estimate from the last two level means."""
-    L = len(means) - 1
-    r = abs(means[L]) / (2.0 ** alpha - 1.0)
+    """Giles (2008) remaining-bias estimate from the last two (floored) level means."""
+    m = floor_levels([abs(x) for x in means], 2.0 ** alpha)
+    L = len(m) - 1
+    r = m[L] / (2.0 ** alpha - 1.0)
     if L >= 1:
-        r = max(r, abs(means[L - 1]) / 2.0 ** alpha / (2.0 ** alpha - 1.0))
+        r = max(r, m[L - 1] / 2.0 ** alpha / (2.0 ** alpha - 1.0))
     return r
 
 
-PLAIN_FP64, PLAIN_FP32, NESTED_FIXED, NESTED_FP16, NESTED_BF16 = range(5)
+PLAIN_FP64, PLAIN_FP32, NESTED_FIXED, NESTED_FP16, NESTED_BF16, NESTED_FIXED_EXACT_LOW, NESTED_FP16_EXACT_LOW = range(7)
+
+# Levels whose approximate level difference is computed exactly, by enumerating
+# the 2^(d 2^l) combinations of table cells (d 2^l <= EXACT_MAX_BITS).
+EXACT_MAX_BITS = 20
+
+
+def exact_levels(mode, d):
+    if mode not in (NESTED_FIXED_EXACT_LOW, NESTED_FP16_EXACT_LOW):
+        return set()
+    return {lev for lev in (0, 1) if (d << lev) <= EXACT_MAX_BITS}
 
 
 def estimator_plan(mode):
@@ -55,6 +75,8 @@ def estimator_plan(mode):
         NESTED_FIXED: [core.FIXED_APPROX, core.CORR_FIXED],
         NESTED_FP16: [core.FP16_APPROX, core.CORR_FP16],
         NESTED_BF16: [core.BF16_APPROX, core.CORR_BF16],
+        NESTED_FIXED_EXACT_LOW: [core.FIXED_APPROX, core.CORR_FIXED],
+        NESTED_FP16_EXACT_LOW: [core.FP16_APPROX, core.CORR_FP16],
     }[mode]
 
 
@@ -73,12 +95,36 @@ def mlmc(eps, p, seed, mode=PLAIN_FP64, cost=None, fmt_of_level=None, d=10, meth
     S2 = [[0.0] * ne for _ in range(L + 1)]
     dN = [[N_init] * ne for _ in range(L + 1)]
     extrap = [[None] * ne for _ in range(L + 1)]
+    exact = exact_levels(mode, d)
+    for lev in exact:
+        dN[lev][0] = 1 << (d << lev)   # every combination of table cells once
+
+    def is_exact(lev, k):
+        return k == 0 and lev in exact
+
+    def _vc():
+        """Floored level variances and costs of every (level, estimator), level-major."""
+        cols = []
+        for k in range(ne):
+            col = []
+            for lev in range(L + 1):
+                if is_exact(lev, k):
+                    col.append(0.0)          # an exact mean has no variance
+                elif N[lev][k] > 0:
+                    m = S1[lev][k] / N[lev][k]
+                    col.append(max(S2[lev][k] / N[lev][k] - m * m, 0.0))
+                else:
+                    col.append(extrap[lev][k])
+            cols.append(floor_levels(col, 2.0 ** beta))
+        V = [max(cols[k][lev], 1e-300) for lev in range(L + 1) for k in range(ne)]
+        C = [cost[plan[k]] * 2.0 ** lev for lev in range(L + 1) for k in range(ne)]
+        return V, C
 
     def run(lev, k, count):
         v = plan[k]
         fmt = fmt_of_level(lev) if fmt_of_level else None
         s, _ = core.level(p, lev, N[lev][k], count, v, seed, request=request, d=d,
-                          method=method, fmt=fmt)
+                          method=method, fmt=fmt, enumerate=1 if is_exact(lev, k) else 0)
         S1[lev][k] += disc * s["sum"]
         S2[lev][k] += disc * disc * s["sum2"]
         N[lev][k] += count
@@ -89,17 +135,7 @@ def mlmc(eps, p, seed, mode=PLAIN_FP64, cost=None, fmt_of_level=None, d=10, meth
                 for k in range(ne):
                     if dN[lev][k] > 0:
                         run(lev, k, dN[lev][k])
-            V, C = [], []
-            for lev in range(L + 1):
-                for k in range(ne):
-                    if N[lev][k] > 0:
-                        m = S1[lev][k] / N[lev][k]
-                        var = max(S2[lev][k] / N[lev][k] - m * m, 0.0)
-                    else:
-                        var = extrap[lev][k]
-                    V.append(max(var, 1e-300))
-                    C.append(cost[plan[k]] * 2.0 ** lev)
-            Nopt = optimal_n(V, C, (1.0 - theta) * eps * eps)
+            Nopt = optimal_n(*_vc(), (1.0 - theta) * eps * eps)
             for lev in range(L + 1):
                 for k in range(ne):
                     want = int(math.ceil(Nopt[lev * ne + k]))
@@ -117,22 +153,15 @@ def mlmc(eps, p, seed, mode=PLAIN_FP64, cost=None, fmt_of_level=None, d=10, meth
             m = S1[L - 1][k] / N[L - 1][k]
             prev_var.append(max(S2[L - 1][k] / N[L - 1][k] - m * m, 1e-300) / 2.0 ** beta)
         extrap.append(prev_var)
-        V, C = [], []
-        for lev in range(L + 1):
-            for k in range(ne):
-                if N[lev][k] > 0:
-                    m = S1[lev][k] / N[lev][k]
-                    V.append(max(S2[lev][k] / N[lev][k] - m * m, 1e-300))
-                else:
-                    V.append(extrap[lev][k])
-                C.append(cost[plan[k]] * 2.0 ** lev)
-        Nopt = optimal_n(V, C, (1.0 - theta) * eps * eps)
+        Nopt = optimal_n(*_vc(), (1.0 - theta) * eps * eps)
         dN = [[max(0, int(math.ceil(Nopt[lev * ne + k])) - N[lev][k]) for k in range(ne)]
               for lev in range(L + 1)]
     price = sum(S1[lev][k] / N[lev][k] for lev in range(L + 1) for k in range(ne))
     var = 0.0
     for lev in range(L + 1):
         for k in range(ne):
+            if is_exact(lev, k):
+                continue
             m = S1[lev][k] / N[lev][k]
             var += max(S2[lev][k] / N[lev][k] - m * m, 0.0) / N[lev][k]
     return dict(price=price, var=var, L=L, N=N)

@@ -283,7 +283,7 @@ static double payoff_fp64(const or_params *p, const path_acc *a) {
 /* ------------------------------------------------------------------------ */
 typedef struct {
   const or_params *p;
-  int level, n, variant, d, pack;
+  int level, n, variant, d, pack, enumerate;
   uint64_t seed; uint32_t request, stream;
   double h;
   /* approximate-path tables and constants */
@@ -404,6 +404,8 @@ static int64_t fx_payoff(const level_cfg *c, const fx_acc *a, int coarse) {
 }
 
 static uint32_t approx_draw(const level_cfg *c, uint64_t s, int i) {
+  /* enumeration of the table cells (levels 0-1): j_i = (s >> (d i)) mod 2^d, in the top d bits */
+  if (c->enumerate) return (uint32_t)((s >> (c->d * i)) & ((1ULL << c->d) - 1ULL)) << (32 - c->d);
   if (c->pack) return or_draw_packed(c->seed, c->request, c->level, c->stream, s, i, c->d);
   return or_draw(c->seed, c->request, c->level, c->stream, s, i);
 }
@@ -537,15 +539,17 @@ static int validate_format(const or_format *F, int milstein) {
 
 int or_level(const or_params *p, int level, uint64_t first, uint64_t N, int variant,
              uint64_t seed, uint32_t request, uint32_t stream,
-             int d, const double *ztab, const or_format *fmt, int pack,
+             int d, const double *ztab, const or_format *fmt, int pack, int enumerate,
              or_sums *sums, or_sample *dump) {
   if (level < 0 || level > 20 || variant < 0 || variant > 7) return OR_EINVAL;
+  if (enumerate && (has_exact(variant) || level > 1 || (d << level) > 24)) return OR_EINVAL;
   /* packed draws only feed approximate-only estimators (their uniforms need d bits, not 32) */
   if (pack && (has_exact(variant) || d < 2 || 32 / d < 2)) return OR_EINVAL;
   if (p->payoff < 0 || p->payoff > 3 || p->scheme < 0 || p->scheme > 1) return OR_EINVAL;
   level_cfg c;
   memset(&c, 0, sizeof c);
   c.p = p; c.level = level; c.n = 1 << level; c.variant = variant; c.d = d; c.pack = pack;
+  c.enumerate = enumerate;
   c.seed = seed; c.request = request; c.stream = stream;
   c.h = ldexp(p->T, -level);
   c.ztab = ztab;

@@ -466,7 +466,17 @@ mlmc_status build_item(const mlmc_work &w, int out_index, int threads, int steps
   it.ctr3 = p->request_id;
   it.out_index = (uint32_t)out_index;
   it.dump = dump;
-  const int KP = pack_lanes(p, v);
+  if (w.flags & ~MLMC_WORK_ENUMERATE) return MLMC_EINVAL;
+  const bool enumerate = (w.flags & MLMC_WORK_ENUMERATE) != 0;
+  int KP = pack_lanes(p, v);
+  if (enumerate) {
+    // every combination of table cells once: approximate-only, levels 0-1, samples [0, 2^(d 2^l))
+    const bool approx_only = v == MLMC_FIXED_APPROX || v == MLMC_FP16_APPROX || v == MLMC_BF16_APPROX;
+    const int bits = p->icdf_bits << lev;
+    if (!approx_only || lev > 1 || bits > 24 || w.first_sample != 0 || w.N != (1ULL << bits)) return MLMC_EINVAL;
+    KP = 1;
+    it.enumerate = 1;
+  }
   if (KP == 0) return MLMC_EINVAL;
   // chunking: a group is one Philox call's worth of packs of KP samples
   const uint64_t spc = (uint64_t)KP * (lev >= 2 ? 1 : (lev == 1 ? 2 : 4));
@@ -1097,15 +1107,21 @@ namespace {
 struct EstPlan {
   int n;          // estimators per level
   int variant[2];
+  bool exact_low; // approximate terms of levels 0-1 computed exactly by enumeration
 };
+
+// Levels whose approximate level difference is a finite sum over 2^(d 2^l) <= 2^20 cells.
+constexpr int EXACT_MAX_BITS = 20;
 
 bool est_plan(int mode, EstPlan &e) {
   switch (mode) {
-    case 0: e = {1, {MLMC_FP64_EXACT, 0}}; return true;
-    case 1: e = {1, {MLMC_FP32_EXACT, 0}}; return true;
-    case 2: e = {2, {MLMC_FIXED_APPROX, MLMC_NESTED_CORR_FIXED}}; return true;
-    case 3: e = {2, {MLMC_FP16_APPROX, MLMC_NESTED_CORR_FP16}}; return true;
-    case 4: e = {2, {MLMC_BF16_APPROX, MLMC_NESTED_CORR_BF16}}; return true;
+    case 0: e = {1, {MLMC_FP64_EXACT, 0}, false}; return true;
+    case 1: e = {1, {MLMC_FP32_EXACT, 0}, false}; return true;
+    case 2: e = {2, {MLMC_FIXED_APPROX, MLMC_NESTED_CORR_FIXED}, false}; return true;
+    case 3: e = {2, {MLMC_FP16_APPROX, MLMC_NESTED_CORR_FP16}, false}; return true;
+    case 4: e = {2, {MLMC_BF16_APPROX, MLMC_NESTED_CORR_BF16}, false}; return true;
+    case 5: e = {2, {MLMC_FIXED_APPROX, MLMC_NESTED_CORR_FIXED}, true}; return true;
+    case 6: e = {2, {MLMC_FP16_APPROX, MLMC_NESTED_CORR_FP16}, true}; return true;
     default: return false;
   }
 }
@@ -1142,19 +1158,30 @@ extern "C" mlmc_status mlmc_estimate(double eps, const mlmc_params *p, int mode,
   std::vector<std::vector<uint64_t>> N(L + 1, std::vector<uint64_t>(ne, 0)), dN(L + 1, std::vector<uint64_t>(ne, N_init));
   std::vector<std::vector<double>> S1(L + 1, std::vector<double>(ne, 0.0)), S2 = S1;
   std::vector<std::vector<double>> Vext(L + 1, std::vector<double>(ne, 0.0));
+  auto is_exact = [&](int l, int k) { return ep.exact_low && k == 0 && l <= 1 && (p->icdf_bits << l) <= EXACT_MAX_BITS; };
+  for (int l = 0; l <= 1; ++l)
+    if (is_exact(l, 0)) dN[l][0] = 1ULL << (p->icdf_bits << l);  // every combination of table cells once
   std::vector<mlmc_work> work;
   std::vector<mlmc_sums> res;
   std::vector<std::pair<int, int>> idx;
   auto level_var = [&](int l, int k) {
+    if (is_exact(l, k)) return 0.0;  // an exact mean has no variance
     if (N[l][k] == 0) return Vext[l][k];
     const double m = S1[l][k] / (double)N[l][k];
     return std::max(S2[l][k] / (double)N[l][k] - m * m, 0.0);
   };
+  const double beta_factor = std::pow(2.0, beta);
   auto update_dn = [&]() {
     std::vector<double> V, C;
+    double vprev[2] = {0.0, 0.0};
     for (int l = 0; l <= L; ++l)
       for (int k = 0; k < ne; ++k) {
-        V.push_back(std::max(level_var(l, k), 1e-300));
+        // variance floor V_l >= V_{l-1} / (2 * 2^beta) from level 2 on, so that a level
+        // whose few samples show (almost) no variance still receives samples
+        double v = level_var(l, k);
+        if (l >= 2) v = std::max(v, 0.5 * vprev[k] / beta_factor);
+        vprev[k] = v;
+        V.push_back(std::max(v, 1e-300));
         C.push_back(std::ldexp(g_cost[cost_kind_of(ep.variant[k])], l));
       }
     std::vector<uint64_t> Nopt;
@@ -1177,6 +1204,7 @@ extern "C" mlmc_status mlmc_estimate(double eps, const mlmc_params *p, int mode,
             std::memset(&w, 0, sizeof w);
             w.params = p; w.level = l; w.variant = ep.variant[k]; w.first_sample = N[l][k]; w.N = dN[l][k];
             w.stream = -1;
+            w.flags = is_exact(l, k) ? MLMC_WORK_ENUMERATE : 0;
             work.push_back(w);
             idx.push_back({l, k});
           }
@@ -1197,8 +1225,12 @@ extern "C" mlmc_status mlmc_estimate(double eps, const mlmc_params *p, int mode,
     }
     // bias test on the last two levels (weak order alpha)
     std::vector<double> means(L + 1, 0.0);
-    for (int l = 0; l <= L; ++l)
+    for (int l = 0; l <= L; ++l) {
       for (int k = 0; k < ne; ++k) means[l] += S1[l][k] / (double)N[l][k];
+      means[l] = std::fabs(means[l]);
+      // the same floor on the level means: |m_l| >= |m_{l-1}| / (2 * 2^alpha)
+      if (l >= 2) means[l] = std::max(means[l], 0.5 * means[l - 1] / std::pow(2.0, alpha));
+    }
     double rem = std::fabs(means[L]) / (std::pow(2.0, alpha) - 1.0);
     rem = std::max(rem, std::fabs(means[L - 1]) / std::pow(2.0, alpha) / (std::pow(2.0, alpha) - 1.0));
     if (rem <= std::sqrt(theta) * eps || L >= max_level) break;

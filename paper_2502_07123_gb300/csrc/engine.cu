@@ -4,8 +4,8 @@
 // Each admitted request owns a slot of FP64 state in device memory (sums of Y
 // and Y^2, sample counts, pending counts per level and estimator).  One engine
 // step gathers the pending (request, level, estimator, count) work of every
-// active slot into one batched plan launch, then update_kernel adds the new
-// sums into each slot and, on the device, recomputes the level variances, the
+// active slot into one batched plan launch; accumulate_kernel then adds the new
+// sums into each slot and decide_kernel, on the device, recomputes the level variances, the
 // optimal sample counts N = ceil(lambda sqrt(V / C)) (Sec. 2.1 / 2.2) and the
 // bias test of the adaptive loop.  The host only moves the pending counts back
 // to build the next work list.  The arithmetic, and its order, is that of
@@ -35,7 +35,7 @@ constexpr int MAXL = 21;
 
 struct SlotState {
   int32_t active, done, L, ne;
-  int32_t max_level, pad0;
+  int32_t max_level, exact_mask;       // bit l: the approximate term of level l is exact
   double eps, sqrt_theta_eps, var_target, beta_factor;
   double cost[2];                      // cost per fine path-step of each estimator
   double S1[MAXL][2], S2[MAXL][2];     // discounted sums
@@ -66,6 +66,7 @@ __device__ double u128_to_double_rn(unsigned long long lo, unsigned long long hi
 }
 
 __device__ double level_var(const SlotState &s, int l, int k) {
+  if (k == 0 && ((s.exact_mask >> l) & 1)) return 0.0;  // an exact mean has no variance
   if (s.N[l][k] == 0) return s.Vext[l][k];
   const double n = __ull2double_rn(s.N[l][k]);
   const double m = __ddiv_rn(s.S1[l][k], n);
@@ -74,18 +75,28 @@ __device__ double level_var(const SlotState &s, int l, int k) {
 }
 
 // dN = ceil(lambda sqrt(V/C)) - N over all levels <= L and estimators (mlmc_estimate's update).
+// Level variance with the floor V_l >= V_{l-1} / (2 * 2^beta) from level 2 on.
+__device__ double floored_var(const SlotState &s, int l, int k, double &vprev) {
+  double v = level_var(s, l, k);
+  if (l >= 2) v = fmax(v, __ddiv_rn(__dmul_rn(0.5, vprev), s.beta_factor));
+  vprev = v;
+  return fmax(v, 1e-300);
+}
+
 __device__ void update_dn(SlotState &s) {
   double lam = 0.0;
+  double vp[2] = {0.0, 0.0};
   for (int l = 0; l <= s.L; ++l)
     for (int k = 0; k < s.ne; ++k) {
-      const double V = fmax(level_var(s, l, k), 1e-300);
+      const double V = floored_var(s, l, k, vp[k]);
       const double C = ldexp(s.cost[k], l);
       lam = __dadd_rn(lam, __dsqrt_rn(__dmul_rn(V, C)));
     }
   lam = __ddiv_rn(lam, s.var_target);
+  vp[0] = vp[1] = 0.0;
   for (int l = 0; l <= s.L; ++l)
     for (int k = 0; k < s.ne; ++k) {
-      const double V = fmax(level_var(s, l, k), 1e-300);
+      const double V = floored_var(s, l, k, vp[k]);
       const double C = ldexp(s.cost[k], l);
       const double x = V > 0.0 ? __dmul_rn(lam, __dsqrt_rn(__ddiv_rn(V, C))) : 0.0;
       const unsigned long long want = (unsigned long long)ceil(fmin(x, 1e18));
@@ -125,11 +136,17 @@ __global__ void decide_kernel(SlotState *slots, SlotReport *rep, int n_slots) {
     for (int l = 0; l <= s.L; ++l)
       for (int k = 0; k < s.ne; ++k) any |= s.dN[l][k] > 0;
     if (!any) {
-      // bias estimate from the last two level means (weak order 1)
-      double mL = 0.0, mL1 = 0.0;
-      for (int k = 0; k < s.ne; ++k) {
-        mL = __dadd_rn(mL, __ddiv_rn(s.S1[s.L][k], __ull2double_rn(s.N[s.L][k])));
-        mL1 = __dadd_rn(mL1, __ddiv_rn(s.S1[s.L - 1][k], __ull2double_rn(s.N[s.L - 1][k])));
+      // bias estimate from the last two level means (weak order 1), with the
+      // floor |m_l| >= |m_{l-1}| / (2 * 2^alpha) from level 2 on
+      double mprev = 0.0, mL = 0.0, mL1 = 0.0;
+      for (int l = 0; l <= s.L; ++l) {
+        double ml = 0.0;
+        for (int k = 0; k < s.ne; ++k) ml = __dadd_rn(ml, __ddiv_rn(s.S1[l][k], __ull2double_rn(s.N[l][k])));
+        ml = fabs(ml);
+        if (l >= 2) ml = fmax(ml, __ddiv_rn(__dmul_rn(0.5, mprev), 2.0));
+        if (l == s.L - 1) mL1 = ml;
+        if (l == s.L) mL = ml;
+        mprev = ml;
       }
       double rem = __ddiv_rn(fabs(mL), 1.0);
       rem = fmax(rem, __ddiv_rn(__ddiv_rn(fabs(mL1), 2.0), 1.0));
@@ -175,7 +192,16 @@ struct Request {
   double price, se;
   int L;
   unsigned long long N[MAXL][2];      // samples taken so far (host mirror of the slot's counts)
+  int exact_mask;                     // bit l: approximate term of level l computed by enumeration
 };
+
+int exact_mask_of(int mode, int d) {
+  if (mode != 5 && mode != 6) return 0;
+  int m = 0;
+  for (int l = 0; l <= 1; ++l)
+    if ((d << l) <= 20) m |= 1 << l;
+  return m;
+}
 
 double now_s() {
   using namespace std::chrono;
@@ -189,6 +215,8 @@ bool mode_variants(int mode, int &ne, int v[2]) {
     case 2: ne = 2; v[0] = MLMC_FIXED_APPROX; v[1] = MLMC_NESTED_CORR_FIXED; return true;
     case 3: ne = 2; v[0] = MLMC_FP16_APPROX; v[1] = MLMC_NESTED_CORR_FP16; return true;
     case 4: ne = 2; v[0] = MLMC_BF16_APPROX; v[1] = MLMC_NESTED_CORR_BF16; return true;
+    case 5: ne = 2; v[0] = MLMC_FIXED_APPROX; v[1] = MLMC_NESTED_CORR_FIXED; return true;
+    case 6: ne = 2; v[0] = MLMC_FP16_APPROX; v[1] = MLMC_NESTED_CORR_FP16; return true;
     default: return false;
   }
 }
@@ -264,6 +292,7 @@ mlmc_status mlmc_engine_submit(mlmc_engine *e, const mlmc_params *p, double eps,
   r.price = r.se = 0.0;
   r.L = 0;
   std::memset(r.N, 0, sizeof r.N);
+  r.exact_mask = exact_mask_of(mode, p->icdf_bits);
   e->reqs.push_back(std::move(r));
   const size_t idx = e->reqs.size() - 1;
   e->by_id[e->reqs[idx].id] = idx;
@@ -295,15 +324,17 @@ mlmc_status mlmc_engine_step(mlmc_engine *e, void *stream, int *active_out, int 
     h.var_target = (1.0 - 0.5) * r.eps * r.eps;
     h.beta_factor = std::pow(2.0, r.p.scheme == MLMC_MILSTEIN ? 2.0 : 1.0);
     for (int k = 0; k < ne; ++k) h.cost[k] = cost_of_variant(v[k]);
+    h.exact_mask = r.exact_mask;
     for (int l = 0; l <= 2; ++l)
-      for (int k = 0; k < ne; ++k) h.dN[l][k] = 10000;
+      for (int k = 0; k < ne; ++k)
+        h.dN[l][k] = (k == 0 && ((r.exact_mask >> l) & 1)) ? (1ULL << (r.p.icdf_bits << l)) : 10000;
     MLMC_CK(cudaMemcpyAsync(e->d_slots + sl, &h, sizeof h, cudaMemcpyHostToDevice, st));
     SlotReport &hr = e->h_rep[sl];
     std::memset(&hr, 0, sizeof hr);
     hr.active = 1;
     hr.L = 2;
     for (int l = 0; l <= 2; ++l)
-      for (int k = 0; k < ne; ++k) hr.dN[l][k] = 10000;
+      for (int k = 0; k < ne; ++k) hr.dN[l][k] = h.dN[l][k];
     e->slot_req[sl] = (int)idx;
     r.slot = sl;
     r.t_admit = now_s();
@@ -333,6 +364,7 @@ mlmc_status mlmc_engine_step(mlmc_engine *e, void *stream, int *active_out, int 
           w.N = hr.dN[l][k];
           w.first_sample = r.N[l][k];
           w.stream = -1;
+          w.flags = (k == 0 && ((r.exact_mask >> l) & 1)) ? MLMC_WORK_ENUMERATE : 0;
           work.push_back(w);
           ItemMap m;
           std::memset(&m, 0, sizeof m);

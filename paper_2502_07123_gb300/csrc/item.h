@@ -70,6 +70,7 @@ struct ItemDesc {
   int32_t payoff, scheme, method, d;
   uint32_t ctr2, ctr3;     // Philox counter words 2 and 3: level | stream << 8, request
   int32_t unit;            // approximate payoff unit exponent
+  int32_t enumerate;       // 1: table indices enumerate samples instead of Philox draws
   float unit_scale;        // 2^-unit (FP32, correction estimators)
   // exact path constants
   float c1f, c2f, c1cf, c3f, S0f, Kf;

@@ -20,6 +20,19 @@ namespace mlmc {
 
 using mlmc_sample_rec = ::mlmc_sample;
 
+// Words of "call" q when the table indices enumerate the samples (levels 0 and
+// 1): sample s takes j_i = (s >> (d i)) mod 2^d at step i, placed in the top d
+// bits; the word layout per call is the one of the Philox draws.
+__device__ __forceinline__ uint4 enum_words(uint64_t q, int lev, int d) {
+  const uint32_t mask = (1u << d) - 1u, sh = 32u - (uint32_t)d;
+  if (lev == 0) {
+    const uint32_t s = 4u * (uint32_t)q;
+    return make_uint4((s & mask) << sh, ((s + 1u) & mask) << sh, ((s + 2u) & mask) << sh, ((s + 3u) & mask) << sh);
+  }
+  const uint32_t s0 = 2u * (uint32_t)q, s1 = s0 + 1u;
+  return make_uint4((s0 & mask) << sh, ((s0 >> d) & mask) << sh, (s1 & mask) << sh, ((s1 >> d) & mask) << sh);
+}
+
 template <int XP> struct XType { using T = float; };
 template <> struct XType<XP_F64> { using T = double; };
 template <int AP> struct HType { using T = __half; };
@@ -546,7 +559,9 @@ level_kernel(const __grid_constant__ LaunchArgs args) {
         sim.finish(acc, l, valid, dump && valid ? dump + (s - first) : nullptr);
       }
     } else {
-      const uint4 w = philox4x32_10(make_uint4((uint32_t)g, (uint32_t)(g >> 32), ctr_hi.z, ctr_hi.w), args.rk);
+      const uint4 w = it.enumerate ? enum_words(g, lev, it.d)
+                                   : philox4x32_10(make_uint4((uint32_t)g, (uint32_t)(g >> 32), ctr_hi.z, ctr_hi.w),
+                                                   args.rk);
       const int ppg = lev == 1 ? 2 : 4;  // packs per group
       const uint64_t s0 = (uint64_t)(ppg * KP) * g;
       // samples s0 + k are valid for k in [klo, khi)

@@ -19,7 +19,9 @@ EULER, MILSTEIN = 0, 1
 EURO, DIGITAL, ASIAN, LOOKBACK = 0, 1, 2, 3
 FP64_EXACT, FP32_EXACT, FP16_APPROX, BF16_APPROX, FIXED_APPROX, NESTED_CORR_FIXED, NESTED_CORR_FP16, \
     NESTED_CORR_BF16 = range(8)
-MODE_PLAIN_FP64, MODE_PLAIN_FP32, MODE_NESTED_FIXED, MODE_NESTED_FP16, MODE_NESTED_BF16 = range(5)
+MODE_PLAIN_FP64, MODE_PLAIN_FP32, MODE_NESTED_FIXED, MODE_NESTED_FP16, MODE_NESTED_BF16, \
+    MODE_NESTED_FIXED_EXACT_LOW, MODE_NESTED_FP16_EXACT_LOW = range(7)
+WORK_ENUMERATE = 1
 REP_FP64, REP_FP32, REP_FP16, REP_BF16, REP_FIXED = range(5)
 
 
@@ -62,7 +64,7 @@ class EngineConfig(ctypes.Structure):
 class Work(ctypes.Structure):
     _fields_ = [("params", ctypes.POINTER(Params)), ("level", ctypes.c_int32), ("variant", ctypes.c_int32),
                 ("first_sample", ctypes.c_uint64), ("N", ctypes.c_uint64),
-                ("stream", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("stream", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 SAMPLE_DTYPE = np.dtype([("pf", "<f8"), ("pc", "<f8"), ("sf", "<f8"), ("sc", "<f8"),
@@ -210,6 +212,7 @@ def _works(items):
         arr[i].first_sample = int(it.get("first_sample", 0))
         arr[i].N = int(it["N"])
         arr[i].stream = int(it.get("stream", -1))
+        arr[i].flags = int(it.get("flags", 0))
     return arr, keep
 
 

@@ -139,3 +139,15 @@ def test_adaptive_nested_mlmc_black_scholes():
     assert abs(res["price"] - ref) < 3 * math.sqrt(res["var"]) + eps / math.sqrt(2)
     # far more approximate than correction samples on the coarse levels (Sec. 2.2)
     assert res["N"][0][0] > 5 * res["N"][0][1]
+
+
+def test_adaptive_nested_exact_low_levels_black_scholes():
+    """Mode with the approximate terms of levels 0-1 computed by enumeration."""
+    p = W.params()
+    eps = 0.05
+    res = driver.mlmc(eps, p, 77, mode=driver.NESTED_FIXED_EXACT_LOW, N_init=2000,
+                      cost={core.FIXED_APPROX: 0.9, core.CORR_FIXED: 1.9},
+                      fmt_of_level=lambda lev: W.default_format(p, lev))
+    ref = black_scholes_call(p["S0"], p["K"], p["r"], p["sigma"], p["T"])
+    assert abs(res["price"] - ref) < 3 * math.sqrt(res["var"]) + eps / math.sqrt(2)
+    assert res["N"][0][0] == 1 << 10 and res["N"][1][0] == 1 << 20
