@@ -164,6 +164,8 @@ def main():
     ap.add_argument("--ref-fraction", type=float, default=0.1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tte", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shape (128 threads, 256 path-steps per thread)")
     ap.add_argument("--serving", action="store_true",
                     help="also run the batched (256 options) and serving (Poisson arrivals) workloads")
     args = ap.parse_args()
@@ -185,8 +187,14 @@ def main():
 
     items, meta, cfg = build_items(m, rank)
     tuning = None
+    shape = "default 128 threads x 256 path-steps per thread"
     if args.threads or args.steps_per_thread:
         tuning = dict(threads=args.threads, steps_per_thread=args.steps_per_thread)
+        shape = "fixed %d threads x %d path-steps per thread" % (args.threads, args.steps_per_thread)
+    elif not args.no_autotune:
+        # launch shape per kernel class, timed on this GPU (outside the timed region)
+        shapes = m.mlmc_autotune(items, cfg["seed"], reps=3)
+        shape = "autotuned per kernel class: " + ", ".join("%dx%d" % t for t in sorted(set(shapes)))
     plan = m.Plan(items, cfg["seed"], tuning)
     info = plan.info()
     stream = torch.cuda.current_stream()
@@ -265,6 +273,7 @@ def main():
         "config": {"workload": WORKLOAD, "path_steps_per_step": steps_per_launch,
                    "work_items": len(items), "kernels_per_step": info["kernels"] + 1,
                    "ctas_per_step": info["ctas"], "l2": "flushed between steps (256 MiB write)",
+                   "launch_shape": shape,
                    "wall_s": t_wall},
         "gpu_launches": (info["kernels"] + 1) * args.steps,
         "kernel_ms": {str(f): sum(v) / len(v) for f, v in kern_ms.items()},
@@ -310,33 +319,24 @@ def _engine_params(m, o, request):
                          request=request, rng_pack=1)
 
 
-def batched_run(m, n=256, seed=7, mode=2):
-    """All n options of the batched workload submitted at once to the engine."""
+def batched_run(m, n=256, seed=7, mode=5, iters_per_launch=2):
+    """The batched workload through mlmc_batch_estimate: all n options in one
+    engine, every graph launch running iters_per_launch iterations of all of them."""
     opts = W.batched_options(n, seed)
-    eng = m.Engine(max_slots=n, max_level=10)
+    plist = [_engine_params(m, o, i) for i, o in enumerate(opts)]
+    eps = [o["eps"] for o in opts]
+    m.mlmc_batch_estimate(plist[:4], [1e-2] * 4, mode, 1, max_level=10)   # warm tables and kernels
     t0 = time.perf_counter()
-    rids = [eng.submit(_engine_params(m, o, i), o["eps"], mode, 1) for i, o in enumerate(opts)]
-    done = {}
-    while len(done) < n:
-        eng.step()
-        for i, r in enumerate(rids):
-            if i not in done:
-                res = eng.poll(r)
-                if res is not None:
-                    done[i] = res
+    r = m.mlmc_batch_estimate(plist, eps, mode, 1, max_level=10, iters_per_launch=iters_per_launch)
     wall = time.perf_counter() - t0
-    st = eng.stats()
-    eng.close()
-    errs = [(done[i]["price"] - _bs_price(o)) / o["eps"] for i, o in enumerate(opts) if _bs_price(o) is not None]
-    lat = sorted(done[i]["latency_s"] for i in range(n))
-    return {"requests": n, "wall_s": wall, "requests_per_s": n / wall, "engine_steps": st["steps"],
-            "launches": st["launches"], "path_steps": st["path_steps"], "path_steps_per_s": st["path_steps"] / wall,
+    errs = [(r["price"][i] - _bs_price(o)) / o["eps"] for i, o in enumerate(opts) if _bs_price(o) is not None]
+    return {"requests": n, "mode": mode, "wall_s": wall, "requests_per_s": n / wall,
+            "graph_launches": r["launches"], "iters_per_launch": iters_per_launch,
             "rms_err_over_eps_vs_black_scholes": math.sqrt(sum(e * e for e in errs) / len(errs)),
-            "checked_against_black_scholes": len(errs), "p50_latency_s": lat[n // 2],
-            "p99_latency_s": lat[min(n - 1, int(0.99 * n))]}
+            "checked_against_black_scholes": len(errs)}
 
 
-def serving_run(m, rate, n=400, seed=11, mode=2):
+def serving_run(m, rate, n=400, seed=11, mode=5):
     """Poisson arrivals at `rate` req/s, options drawn as the batched workload;
     requests are admitted while others run (continuous batching)."""
     arrivals = W.poisson_arrivals(rate, n, seed)
@@ -362,13 +362,23 @@ def serving_run(m, rate, n=400, seed=11, mode=2):
                     done[i] = res
     wall = time.perf_counter() - t0
     st = eng.stats()
+    gi = eng.graph_info()
     eng.close()
     lat = sorted(done[i]["latency_s"] for i in range(n))
     errs = [(done[i]["price"] - _bs_price(o)) / o["eps"] for i, o in enumerate(opts) if _bs_price(o) is not None]
-    return {"arrival_rate": rate, "requests": n, "wall_s": wall, "requests_per_s": n / wall,
+    return {"arrival_rate": rate, "requests": n, "mode": mode, "wall_s": wall, "requests_per_s": n / wall,
             "p50_latency_s": lat[n // 2], "p99_latency_s": lat[min(n - 1, int(0.99 * n))],
-            "engine_steps": st["steps"], "launches": st["launches"],
+            "engine_steps": st["steps"], "graph_launches": st["launches"], "graph_captures": gi["captures"],
             "rms_err_over_eps_vs_black_scholes": math.sqrt(sum(e * e for e in errs) / len(errs))}
+
+
+def _engine_solve(eng, P, eps, mode, seed):
+    rid = eng.submit(P, eps, mode, seed)
+    while True:
+        eng.step()
+        r = eng.poll(rid)
+        if r is not None:
+            return r
 
 
 def time_to_eps(m, torch, eps=1e-3, seeds=(1, 2, 3)):
@@ -388,8 +398,27 @@ def time_to_eps(m, torch, eps=1e-3, seeds=(1, 2, 3)):
             ts.append(time.perf_counter() - t0)
             prices.append(r["price"])
         out[name] = {"s_median": statistics.median(ts), "prices": prices, "L": r["L"], "N": r["N"]}
-    for name in ("nested_fixed", "nested_fixed_exact_low", "nested_fp16_exact_low"):
+    # the same adaptive algorithm driven on the device: one request through a
+    # (created and warmed) engine's graph iteration instead of host-driven plans
+    for name, mode in (("plain_fp32_graph", m.MODE_PLAIN_FP32),
+                       ("nested_fixed_exact_low_graph", m.MODE_NESTED_FIXED_EXACT_LOW)):
+        eng = m.Engine(max_slots=1, max_level=10)
+        _engine_solve(eng, P, 1e-2, mode, 99)
+        ts, prices = [], []
+        for s in seeds:
+            torch.cuda.synchronize()
+            l0 = eng.stats()["launches"]
+            t0 = time.perf_counter()
+            r = _engine_solve(eng, P, eps, mode, s)
+            ts.append(time.perf_counter() - t0)
+            prices.append(r["price"])
+        out[name] = {"s_median": statistics.median(ts), "prices": prices, "L": r["L"],
+                     "graph_launches": eng.stats()["launches"] - l0}
+        eng.close()
+    for name in ("nested_fixed", "nested_fixed_exact_low", "nested_fp16_exact_low", "nested_fixed_exact_low_graph"):
         out["speedup_%s_vs_plain_fp32" % name] = out["plain_fp32"]["s_median"] / out[name]["s_median"]
+    out["speedup_nested_fixed_exact_low_graph_vs_plain_fp32_graph"] = (
+        out["plain_fp32_graph"]["s_median"] / out["nested_fixed_exact_low_graph"]["s_median"])
     return out
 
 

@@ -126,7 +126,8 @@ typedef struct {
 } mlmc_sample;
 
 /* Chunking of the level kernels.  threads: CTA size (32..128, multiple of 32);
- * steps_per_thread: target fine path-steps per thread (>= 1); zero = default. */
+ * steps_per_thread: target fine path-steps per thread (>= 1); zero = the
+ * library's launch-shape table (128 / 256 unless mlmc_autotune changed it). */
 typedef struct {
   int32_t threads;
   int32_t steps_per_thread;
@@ -225,6 +226,25 @@ void mlmc_plan_destroy(mlmc_plan *plan);
 mlmc_status mlmc_run(const mlmc_work *work, int n_work, uint64_t seed,
                      const mlmc_tuning *tuning, mlmc_sums *out, void *stream);
 
+/* ---- launch-shape autotuner ----------------------------------------------
+ * The level kernels' launch shape (CTA threads; fine path-steps, hence paths,
+ * per thread) is chosen per kernel class: (kernel family, scheme, payoff class,
+ * level class {0}, {1}, {2..4}, {5..7}, {>= 8}).  mlmc_autotune times the work
+ * items of each class present in `work` on this GPU with every distinct
+ * chunking from threads {128, 96, 64} x steps_per_thread {256, 64, 128, 512,
+ * 1024, 2048} (median of `reps` launches by CUDA events, after one untimed
+ * launch; a candidate must beat the best so far by 2%), and installs the
+ * fastest in the process-wide table that every later call without an
+ * mlmc_tuning uses (plans, mlmc_run, mlmc_level, mlmc_level_noalloc,
+ * mlmc_estimate, engine admissions).  chosen (host, n_work entries, or NULL)
+ * receives each item's shape.  The shape changes the chunking only: integer
+ * sums are unchanged, FP32 sums may change in their last bits.  Synchronous;
+ * runs the work (1 + reps) times per candidate.  Errors as mlmc_plan_create,
+ * MLMC_EINVAL for reps outside [1, 1000]. */
+mlmc_status mlmc_autotune(const mlmc_work *work, int n_work, uint64_t seed, int reps, mlmc_tuning *chosen);
+/* Restore the default shape (128 threads, 256 path-steps per thread) for every class. */
+void mlmc_tuning_reset(void);
+
 /* ---- adaptive MLMC (Sec. 2.1-2.2 sample allocation, on-line phase of Sec. 6) ----
  * Estimates E[P] to root-mean-square error eps with the adaptive algorithm of
  * Giles (2008): variance target eps^2/2, bias target eps/sqrt(2), weak order 1,
@@ -249,38 +269,70 @@ mlmc_status mlmc_estimate(double eps, const mlmc_params *p, int mode, uint64_t s
 /* ---- continuous-batching engine (many adaptive requests per launch) --------
  * Requests (params, eps, mode, seed) queue on submit and are admitted into free
  * slots; each slot keeps its adaptive state (sums of Y and Y^2, sample counts,
- * pending counts per level and estimator) in FP64 in device memory.  One
- * mlmc_engine_step admits waiting requests, runs the pending work of every
- * active request in one batched plan launch per distinct seed, and updates
- * every slot on the device: level variances, N = ceil(lambda sqrt(V/C))
- * (Sec. 2.1 / 2.2), the bias test, a new level or completion -- the same
- * algorithm and arithmetic as mlmc_estimate, so a request's result is the same
- * whatever else runs beside it.  Slots are limited by max_slots and by
- * device_bytes_budget (0 = no budget).  Requests that share a seed must have
- * distinct request_id values in their params.
- * Errors: MLMC_EINVAL for bad arguments (params->formats, when given, must
- * cover levels 0..max_level), MLMC_ENOMEM, MLMC_ECUDA. */
+ * pending counts per level and estimator) in FP64 in device memory, with one
+ * work-item template per (level, estimator) built at admission.  One engine
+ * iteration is device work only: a scheduler kernel chunks every active
+ * slot's pending (level, estimator) work and groups it by launch class, one
+ * persistent level-kernel launch per class runs it (fixed grid of resident
+ * CTAs, chunks taken in turn), an accumulate kernel adds each item's sums to
+ * its slot in chunk order, and a decide kernel recomputes level variances,
+ * N = ceil(lambda sqrt(V/C)) (Sec. 2.1 / 2.2), the bias test, a new level or
+ * completion -- the same algorithm and arithmetic as mlmc_estimate, so a
+ * request's result is the same whatever else runs beside it.  The iteration
+ * is captured once as a CUDA graph (again when a new launch class appears)
+ * and replayed; mlmc_engine_step admits waiting requests (host), launches the
+ * graph once (iters_per_launch iterations), waits for it and retires
+ * completed requests.  Slots are limited by max_slots and by
+ * device_bytes_budget (0 = no budget): a slot needs its state, templates and
+ * work-list space, about 30 KB at max_level 10.  The per-chunk partial array
+ * (48 bytes a chunk) starts at max(4 chunks per template, 65536) and grows
+ * when an iteration needs more.
+ * Requests that share a seed must have distinct request_id values in their
+ * params.  Errors: MLMC_EINVAL for bad arguments (params->formats, when
+ * given, must cover levels 0..max_level), MLMC_ENOMEM, MLMC_ECUDA; a request
+ * that cannot be admitted (for instance a format its constants do not fit,
+ * or more than 32 launch classes) completes with that status from
+ * mlmc_engine_poll and a NaN price. */
 typedef struct {
-  int32_t max_slots;             /* concurrent requests (0 = 256)           */
-  int32_t max_level;             /* L_max of every request, 2..20           */
-  uint64_t device_bytes_budget;  /* bytes of slot state allowed, 0 = any    */
+  int32_t max_slots;             /* concurrent requests (0 = 256)                 */
+  int32_t max_level;             /* L_max of every request, 2..20                 */
+  uint64_t device_bytes_budget;  /* bytes of per-slot device memory, 0 = any      */
+  int32_t iters_per_launch;      /* engine iterations per graph launch, 0..64 (0 = 1) */
+  int32_t reserved;              /* must be 0 */
 } mlmc_engine_config;
 typedef struct mlmc_engine mlmc_engine;
 mlmc_status mlmc_engine_create(mlmc_engine **e, const mlmc_engine_config *cfg);
 /* Copies *p (and its format table); mode as mlmc_estimate. */
 mlmc_status mlmc_engine_submit(mlmc_engine *e, const mlmc_params *p, double eps, int mode, uint64_t seed,
                                uint64_t *req_id);
-/* One engine iteration on `stream` (synchronous).  *active = requests holding a
- * slot after the step, *queued = requests waiting for one (either may be NULL). */
+/* One graph launch on `stream` (synchronous; NULL = the default stream).
+ * *active = requests holding a slot after the step, *queued = requests
+ * waiting for one (either may be NULL). */
 mlmc_status mlmc_engine_step(mlmc_engine *e, void *stream, int *active, int *queued);
 /* *done = 1 once the request has completed; then price, standard error, final
- * level and latency (seconds from submit to completion) are filled in. */
+ * level and latency (seconds from submit to completion) are filled in.
+ * Returns the request's status (MLMC_OK unless its admission failed). */
 mlmc_status mlmc_engine_poll(mlmc_engine *e, uint64_t req_id, double *price, double *stderr_out, int *L,
                              int *done, double *latency_s);
-/* Engine counters: steps taken, plan launches, fine path-steps simulated, slots. */
+/* Engine counters: steps taken, graph launches, fine path-steps simulated, slots. */
 mlmc_status mlmc_engine_stats(const mlmc_engine *e, uint64_t *steps, uint64_t *launches,
                               uint64_t *path_steps, int *slots);
+/* Captured iteration: launch classes in the graph, captures so far,
+ * iterations per launch, partial-array capacity in chunks (any may be NULL). */
+mlmc_status mlmc_engine_graph_info(const mlmc_engine *e, int *groups, int *captures, int *iters_per_launch,
+                                   uint64_t *partial_capacity);
 void mlmc_engine_destroy(mlmc_engine *e);
+
+/* Batched adaptive MLMC: n independent requests (params[i], eps[i]), all in
+ * `mode` with `seed` (distinct params[i].request_id), run to completion in one
+ * engine of n slots: every graph launch covers iters_per_launch iterations of
+ * all requests.  Outputs (host arrays of n; stderr_out and L may be NULL):
+ * price, standard error, final level; *launches = graph launches (may be
+ * NULL).  Each result equals what mlmc_estimate returns for that request.
+ * Errors as the engine functions; MLMC_ETIMEOUT after 100000 launches. */
+mlmc_status mlmc_batch_estimate(const mlmc_params *params, const double *eps, int n, int mode, uint64_t seed,
+                                int max_level, int iters_per_launch, double *price, double *stderr_out, int *L,
+                                int *launches, void *stream);
 
 /* Cost per fine path-step of each estimator kind used by mlmc_estimate
  * (relative units; defaults: exact FP32 1.0, exact FP64 8.0, approximate 0.5,

@@ -17,6 +17,7 @@
 
 #include "item.h"
 #include "kernels.h"
+#include "reduce.cuh"
 #include "mlmc.h"
 #include "tables.h"
 #include "host_api.h"
@@ -34,8 +35,9 @@ static_assert(sizeof(mlmc_format) == 14, "mlmc_format layout");
 // plan object (opaque in the C ABI)
 // ---------------------------------------------------------------------------
 struct LaunchRec {
-  int family;               // 0..7, see launch_family_of
+  int family;               // kernel family, see launch_by_family
   int scheme, pc;
+  int threads;              // CTA size
   uint32_t chunk0, n_chunks;
   int item_off, n_items;
   size_t smem;
@@ -97,6 +99,20 @@ Ctx g;
 
 double g_cost[4] = {8.0, 1.0, 0.5, 1.5};
 const double g_cost_default[4] = {8.0, 1.0, 0.5, 1.5};
+
+// Launch shape per (kernel family, scheme, payoff class, level class): CTA
+// threads and fine path-steps per thread.  Defaults 128 / 256 until
+// mlmc_autotune installs measured choices.
+constexpr int TUNE_THREADS = 128, TUNE_SPT = 256;
+std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune;
+
+int level_class(int level) { return level <= 1 ? level : (level <= 4 ? 2 : (level <= 7 ? 3 : 4)); }
+
+void tuning_for(int family, int scheme, int pc, int level, int *threads, int *spt) {
+  auto f = g_tune.find(std::make_tuple(family, scheme, pc, level_class(level)));
+  *threads = f == g_tune.end() ? TUNE_THREADS : f->second.first;
+  *spt = f == g_tune.end() ? TUNE_SPT : f->second.second;
+}
 
 #define CK(call)                                      \
   do {                                                \
@@ -324,25 +340,25 @@ int cost_kind_of(int variant) {
 }
 
 cudaError_t launch_by_family(int fam, int scheme, int pc, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
-                             const LaunchArgs &a) {
+                             const LaunchArgs &a, int *occ) {
   switch (fam) {
-    case 12: return launch_approx_fixed_p3(scheme, pc, grid, block, smem, st, a);
-    case 13: return launch_approx_f16_p3(scheme, pc, grid, block, smem, st, a);
-    case 14: return launch_approx_bf16_p3(scheme, pc, grid, block, smem, st, a);
-    case 15: return launch_approx_fx32_p3(scheme, pc, grid, block, smem, st, a);
-    case 16: return launch_approx_fx64_p3(scheme, pc, grid, block, smem, st, a);
-    case 8: return launch_approx_fx32(scheme, pc, grid, block, smem, st, a);
-    case 9: return launch_approx_fx64(scheme, pc, grid, block, smem, st, a);
-    case 10: return launch_corr_fx32(scheme, pc, grid, block, smem, st, a);
-    case 11: return launch_corr_fx64(scheme, pc, grid, block, smem, st, a);
-    case 0: return launch_exact_f32(scheme, pc, grid, block, smem, st, a);
-    case 1: return launch_exact_f64(scheme, pc, grid, block, smem, st, a);
-    case 2: return launch_approx_fixed(scheme, pc, grid, block, smem, st, a);
-    case 3: return launch_approx_f16(scheme, pc, grid, block, smem, st, a);
-    case 4: return launch_approx_bf16(scheme, pc, grid, block, smem, st, a);
-    case 5: return launch_corr_fixed(scheme, pc, grid, block, smem, st, a);
-    case 6: return launch_corr_f16(scheme, pc, grid, block, smem, st, a);
-    default: return launch_corr_bf16(scheme, pc, grid, block, smem, st, a);
+    case 12: return launch_approx_fixed_p3(scheme, pc, grid, block, smem, st, a, occ);
+    case 13: return launch_approx_f16_p3(scheme, pc, grid, block, smem, st, a, occ);
+    case 14: return launch_approx_bf16_p3(scheme, pc, grid, block, smem, st, a, occ);
+    case 15: return launch_approx_fx32_p3(scheme, pc, grid, block, smem, st, a, occ);
+    case 16: return launch_approx_fx64_p3(scheme, pc, grid, block, smem, st, a, occ);
+    case 8: return launch_approx_fx32(scheme, pc, grid, block, smem, st, a, occ);
+    case 9: return launch_approx_fx64(scheme, pc, grid, block, smem, st, a, occ);
+    case 10: return launch_corr_fx32(scheme, pc, grid, block, smem, st, a, occ);
+    case 11: return launch_corr_fx64(scheme, pc, grid, block, smem, st, a, occ);
+    case 0: return launch_exact_f32(scheme, pc, grid, block, smem, st, a, occ);
+    case 1: return launch_exact_f64(scheme, pc, grid, block, smem, st, a, occ);
+    case 2: return launch_approx_fixed(scheme, pc, grid, block, smem, st, a, occ);
+    case 3: return launch_approx_f16(scheme, pc, grid, block, smem, st, a, occ);
+    case 4: return launch_approx_bf16(scheme, pc, grid, block, smem, st, a, occ);
+    case 5: return launch_corr_fixed(scheme, pc, grid, block, smem, st, a, occ);
+    case 6: return launch_corr_f16(scheme, pc, grid, block, smem, st, a, occ);
+    default: return launch_corr_bf16(scheme, pc, grid, block, smem, st, a, occ);
   }
 }
 
@@ -432,15 +448,22 @@ int64_t table_zmax_fixed(const std::vector<double> &Z, int d, int method, int fZ
 uint16_t half_bits(double x) { return __half_as_ushort(__double2half(x)); }
 uint16_t bf16_bits(double x) { return __bfloat16_as_ushort(__double2bfloat16(x)); }
 
-struct BuiltItem {
-  ItemDesc it;
-  int family, scheme, pc;
-  size_t smem;
-  double chunk_cost;
-};
 
-mlmc_status build_item(const mlmc_work &w, int out_index, int threads, int steps_per_thread, void *dump,
-                       BuiltItem &b, double &disc, int &unit, int &exact_int) {
+// Split an item's sample groups into chunks of `threads` x groups_per_thread.
+mlmc_status chunk_built(BuiltItem &b, int threads, int spt) {
+  ItemDesc &it = b.it;
+  uint32_t gpt = 1;
+  const uint64_t spg = steps_per_group(it.level);
+  const uint64_t nch = chunk_count(it.g1 - it.g0, spg, b.kp, threads, spt, g.num_sms, &gpt);
+  if (nch > 0x7fffffffULL) return MLMC_EINVAL;
+  it.groups_per_thread = gpt;
+  it.n_chunks = (uint32_t)nch;
+  b.chunk_cost = (double)gpt * (double)threads * (double)spg * b.kp * b.cost_step;
+  return MLMC_OK;
+}
+
+mlmc_status build_item(const mlmc_work &w, int out_index, void *dump, BuiltItem &b, double &disc, int &unit,
+                       int &exact_int) {
   const mlmc_params *p = w.params;
   if (!params_ok(p)) return MLMC_EINVAL;
   if (w.level < 0 || w.level > 20 || w.variant < 0 || w.variant > 7) return MLMC_EINVAL;
@@ -478,26 +501,16 @@ mlmc_status build_item(const mlmc_work &w, int out_index, int threads, int steps
     it.enumerate = 1;
   }
   if (KP == 0) return MLMC_EINVAL;
-  // chunking: a group is one Philox call's worth of packs of KP samples
-  const uint64_t spc = (uint64_t)KP * (lev >= 2 ? 1 : (lev == 1 ? 2 : 4));
-  const uint64_t steps_per_group = std::max<uint64_t>(4, 1ULL << lev);
+  // sample groups (chunking into CTAs: chunk_built)
+  const uint64_t spc = samples_per_group(lev, KP);
   it.g0 = w.first_sample / spc;
   it.g1 = w.N == 0 ? it.g0 : (w.first_sample + w.N + spc - 1) / spc;
-  const uint64_t groups = it.g1 - it.g0;
   // groups whose samples all lie in [first, first + N)
   it.gf0 = (w.first_sample + spc - 1) / spc;
   it.gf1 = (w.first_sample + w.N) / spc;
   if (it.gf1 < it.gf0) it.gf1 = it.gf0;
-  uint64_t G = std::max<uint64_t>(1, (uint64_t)steps_per_thread / (steps_per_group * KP));
-  const uint64_t min_ctas = 4ULL * (uint64_t)std::max(1, g.num_sms);
-  const uint64_t cap = std::max<uint64_t>(1, (groups + (uint64_t)threads * min_ctas - 1) / ((uint64_t)threads * min_ctas));
-  G = std::min(G, cap);
-  it.groups_per_thread = (uint32_t)G;
-  const uint64_t per_chunk = G * (uint64_t)threads;
-  const uint64_t nch = (groups + per_chunk - 1) / per_chunk;
-  if (nch > 0x7fffffffULL) return MLMC_EINVAL;
-  it.n_chunks = (uint32_t)nch;
-  b.chunk_cost = (double)per_chunk * (double)steps_per_group * KP * g_cost[cost_kind_of(v)];
+  b.kp = KP;
+  b.cost_step = g_cost[cost_kind_of(v)];
   // exact-path constants (the same FP64 expressions as the fixed-point ones)
   const double h = std::ldexp(p->T, -lev);
   const double rh = p->r * h, rh2 = p->r * (2.0 * h), sqh = std::sqrt(h);
@@ -623,35 +636,8 @@ __global__ void finalize_kernel(const ItemDesc *items, int n_items, const Partia
   const int i = blockIdx.x;
   if (i >= n_items) return;
   const ItemDesc &it = items[i];
-  int64_t isum = 0;
-  uint64_t lo = 0, hi = 0, ns = 0;
-  double ds = 0.0, dq = 0.0;
-  for (uint32_t c = threadIdx.x; c < it.n_chunks; c += 32) {
-    const Partial &p = partials[it.chunk_begin + c];
-    isum += p.isum;
-    const uint64_t nlo = lo + p.isum2_lo;
-    hi += p.isum2_hi + (uint64_t)(nlo < lo);
-    lo = nlo;
-    ds += p.dsum;
-    dq += p.dsum2;
-    ns += p.nsat;
-  }
-  for (int m = 16; m >= 1; m >>= 1) {
-    isum += __shfl_xor_sync(0xffffffffu, (long long)isum, m);
-    const uint64_t olo = __shfl_xor_sync(0xffffffffu, (unsigned long long)lo, m);
-    const uint64_t ohi = __shfl_xor_sync(0xffffffffu, (unsigned long long)hi, m);
-    const uint64_t nlo = lo + olo;
-    hi += ohi + (uint64_t)(nlo < lo);
-    lo = nlo;
-    ds += __shfl_xor_sync(0xffffffffu, ds, m);
-    dq += __shfl_xor_sync(0xffffffffu, dq, m);
-    ns += __shfl_xor_sync(0xffffffffu, (unsigned long long)ns, m);
-  }
-  if (threadIdx.x == 0) {
-    DevSums r;
-    r.dsum = ds; r.dsum2 = dq; r.isum = isum; r.isum2_lo = lo; r.isum2_hi = hi; r.nsat = ns;
-    out[it.out_index] = r;
-  }
+  const DevSums r = warp_sum_partials(partials + it.chunk_begin, it.n_chunks);
+  if (threadIdx.x == 0) out[it.out_index] = r;
 }
 
 void free_plan_device(mlmc_plan *pl) {
@@ -712,34 +698,41 @@ mlmc_status plan_create_impl(mlmc_plan **out, const mlmc_work *work, int n_work,
   if (!out || !work || n_work <= 0) return MLMC_EINVAL;
   mlmc_status s = ensure_ctx();
   if (s != MLMC_OK) return s;
-  int threads = 128, spt = 256;
+  int o_threads = 0, o_spt = 0;  // 0: the tuning table's choice per item
   if (tuning) {
-    if (tuning->threads) threads = tuning->threads;
-    if (tuning->steps_per_thread) spt = tuning->steps_per_thread;
+    o_threads = tuning->threads;
+    o_spt = tuning->steps_per_thread;
+    if (o_threads && (o_threads < 32 || o_threads > 128 || o_threads % 32)) return MLMC_EINVAL;
+    if (o_spt < 0) return MLMC_EINVAL;
   }
-  if (threads < 32 || threads > 128 || threads % 32 || spt < 1) return MLMC_EINVAL;
   mlmc_plan *pl = new (std::nothrow) mlmc_plan;
   if (!pl) return MLMC_ENOMEM;
   pl->n_work = n_work;
-  pl->threads = threads;
   pl->disc.resize(n_work);
   pl->unit.resize(n_work);
   pl->exact_int.resize(n_work);
   pl->N.resize(n_work);
   std::vector<BuiltItem> built(n_work);
+  std::vector<int> item_threads(n_work);
   for (int i = 0; i < n_work; ++i) {
-    s = build_item(work[i], i, threads, spt, dumps ? dumps[i] : nullptr, built[i], pl->disc[i], pl->unit[i],
-                   pl->exact_int[i]);
+    s = build_item(work[i], i, dumps ? dumps[i] : nullptr, built[i], pl->disc[i], pl->unit[i], pl->exact_int[i]);
+    if (s != MLMC_OK) { delete pl; return s; }
+    int th, sp;
+    tuning_for(built[i].family, built[i].scheme, built[i].pc, work[i].level, &th, &sp);
+    if (o_threads) th = o_threads;
+    if (o_spt) sp = o_spt;
+    item_threads[i] = th;
+    s = chunk_built(built[i], th, sp);
     if (s != MLMC_OK) { delete pl; return s; }
     pl->N[i] = work[i].N;
     pl->path_steps += work[i].N << work[i].level;
   }
   // group by kernel configuration; within a launch, most expensive chunks first
-  std::map<std::tuple<int, int, int>, std::vector<int>> groups;
+  std::map<std::tuple<int, int, int, int>, std::vector<int>> groups;
   std::vector<int> empty;
   for (int i = 0; i < n_work; ++i) {
     if (built[i].it.n_chunks == 0) { empty.push_back(i); continue; }
-    groups[std::make_tuple(built[i].family, built[i].scheme, built[i].pc)].push_back(i);
+    groups[std::make_tuple(built[i].family, built[i].scheme, built[i].pc, item_threads[i])].push_back(i);
   }
   // launches are ordered by their most expensive CTA, so that the longest
   // chains (deep levels, exact paths) start first and the rest fill in
@@ -755,6 +748,7 @@ mlmc_status plan_create_impl(mlmc_plan **out, const mlmc_work *work, int n_work,
     LaunchRec L;
     const BuiltItem &b0 = built[o.second[0]];
     L.family = b0.family; L.scheme = b0.scheme; L.pc = b0.pc;
+    L.threads = item_threads[o.second[0]];
     L.chunk0 = chunk;
     L.item_off = (int)pl->items.size();
     L.n_items = (int)o.second.size();
@@ -850,10 +844,11 @@ mlmc_status plan_launch_impl(mlmc_plan *pl, cudaStream_t st) {
     a.items = pl->d_items + L.item_off;
     a.n_items = L.n_items;
     a.chunk0 = L.chunk0;
+    a.dyn = nullptr;
     a.partials = pl->d_partials;
     a.rk = pl->rk;
     CK(cudaEventRecord(pl->kstart[i], ls));
-    CK(launch_by_family(L.family, L.scheme, L.pc, dim3(L.n_chunks), dim3(pl->threads), L.smem, ls, a));
+    CK(launch_by_family(L.family, L.scheme, L.pc, dim3(L.n_chunks), dim3(L.threads), L.smem, ls, a, nullptr));
     CK(cudaEventRecord(pl->kstop[i], ls));
     if (fork) {
       CK(cudaEventRecord(pl->join[i], ls));
@@ -924,6 +919,7 @@ mlmc_status run_sync(const mlmc_work *work, int n_work, uint64_t seed, const mlm
 }
 
 cudaStream_t ctx_stream() { return g.st; }
+int ctx_num_sms() { return g.num_sms; }
 double cost_of_variant(int variant) { return g_cost[cost_kind_of(variant)]; }
 mlmc_status plan_create_transient(mlmc_plan **out, const mlmc_work *work, int n_work, uint64_t seed,
                                   const mlmc_tuning *tuning) {
@@ -946,6 +942,33 @@ void plan_item_scale(const mlmc_plan *pl, int i, double *disc, int *unit, int *e
 void plan_release(mlmc_plan *pl) {
   free_plan_device(pl);
   delete pl;
+}
+
+// Median device time (ms) of `reps` launches of a plan of `work` with one
+// launch shape, after one untimed launch.
+mlmc_status time_shape(const std::vector<mlmc_work> &work, uint64_t seed, int threads, int spt, int reps,
+                       double *ms) {
+  mlmc_tuning t;
+  t.threads = threads;
+  t.steps_per_thread = spt;
+  mlmc_plan *pl = nullptr;
+  mlmc_status s = plan_create_impl(&pl, work.data(), (int)work.size(), seed, &t, nullptr);
+  if (s != MLMC_OK) return s;
+  std::vector<float> v;
+  for (int r = 0; r <= reps && s == MLMC_OK; ++r) {
+    s = plan_launch_impl(pl, g.st);
+    float x = 0.0f;
+    if (s == MLMC_OK && (cudaEventSynchronize(pl->t1) != cudaSuccess ||
+                         cudaEventElapsedTime(&x, pl->t0, pl->t1) != cudaSuccess))
+      s = MLMC_ECUDA;
+    if (r > 0) v.push_back(x);
+  }
+  free_plan_device(pl);
+  delete pl;
+  if (s != MLMC_OK) return s;
+  std::sort(v.begin(), v.end());
+  *ms = v[v.size() / 2];
+  return MLMC_OK;
 }
 
 }  // namespace mlmc_host
@@ -1026,6 +1049,61 @@ void mlmc_plan_destroy(mlmc_plan *plan) {
   free_plan_device(plan);
   delete plan;
 }
+
+mlmc_status mlmc_autotune(const mlmc_work *work, int n_work, uint64_t seed, int reps, mlmc_tuning *chosen) {
+  if (!work || n_work <= 0 || reps < 1 || reps > 1000) return MLMC_EINVAL;
+  mlmc_status s = ensure_ctx();
+  if (s != MLMC_OK) return s;
+  // kernel classes among the items
+  std::map<std::tuple<int, int, int, int>, std::vector<int>> cls;
+  std::vector<BuiltItem> built(n_work);
+  for (int i = 0; i < n_work; ++i) {
+    double disc;
+    int unit, ei;
+    if ((s = build_item(work[i], i, nullptr, built[i], disc, unit, ei)) != MLMC_OK) return s;
+    cls[std::make_tuple(built[i].family, built[i].scheme, built[i].pc, level_class(work[i].level))].push_back(i);
+  }
+  static const int cand_threads[] = {128, 96, 64};
+  static const int cand_spt[] = {256, 64, 128, 512, 1024, 2048};
+  for (auto &kv : cls) {
+    std::vector<mlmc_work> sub;
+    for (int i : kv.second) sub.push_back(work[i]);
+    int best_t = TUNE_THREADS, best_s = TUNE_SPT;
+    double best_ms = 0.0;
+    bool have = false;
+    std::vector<std::vector<uint32_t>> seen;   // chunkings already timed
+    for (int th : cand_threads)
+      for (int sp : cand_spt) {
+        std::vector<uint32_t> sig{(uint32_t)th};
+        for (int i : kv.second) {
+          BuiltItem b = built[i];
+          if ((s = chunk_built(b, th, sp)) != MLMC_OK) return s;
+          sig.push_back(b.it.groups_per_thread);
+        }
+        if (std::find(seen.begin(), seen.end(), sig) != seen.end()) continue;
+        seen.push_back(sig);
+        double ms = 0.0;
+        if ((s = time_shape(sub, seed, th, sp, reps, &ms)) != MLMC_OK) return s;
+        // the first candidate is the default shape; another must be 2% faster to replace it
+        if (!have || ms < 0.98 * best_ms) {
+          best_ms = ms;
+          best_t = th;
+          best_s = sp;
+          have = true;
+        }
+      }
+    const auto &k = kv.first;
+    g_tune[k] = std::make_pair(best_t, best_s);
+    if (chosen)
+      for (int i : kv.second) {
+        chosen[i].threads = best_t;
+        chosen[i].steps_per_thread = best_s;
+      }
+  }
+  return MLMC_OK;
+}
+
+void mlmc_tuning_reset(void) { g_tune.clear(); }
 
 mlmc_status mlmc_run(const mlmc_work *work, int n_work, uint64_t seed, const mlmc_tuning *tuning,
                      mlmc_sums *out, void *stream) {
@@ -1360,8 +1438,7 @@ extern "C" mlmc_status mlmc_level_noalloc(int level, uint64_t N, const mlmc_para
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
 
-  // work item, chunked exactly as mlmc_level chunks it (128 threads, 256 path-steps per thread)
-  const int threads = 128, spt = 256;
+  // the work item, chunked exactly as mlmc_level chunks it
   ItemDesc it;
   std::memset(&it, 0, sizeof it);
   const int vi = (int)v;
@@ -1381,23 +1458,13 @@ extern "C" mlmc_status mlmc_level_noalloc(int level, uint64_t N, const mlmc_para
   it.dump = nullptr;
   const int KP = pack_lanes(p, vi);
   if (KP == 0) return MLMC_EINVAL;
-  const uint64_t spc = (uint64_t)KP * (level >= 2 ? 1 : (level == 1 ? 2 : 4));
-  const uint64_t steps_per_group = std::max<uint64_t>(4, 1ULL << level);
+  const uint64_t spc = samples_per_group(level, KP);
   it.g0 = first_sample / spc;
   it.g1 = N == 0 ? it.g0 : (first_sample + N + spc - 1) / spc;
   const uint64_t groups = it.g1 - it.g0;
   it.gf0 = (first_sample + spc - 1) / spc;
   it.gf1 = (first_sample + N) / spc;
   if (it.gf1 < it.gf0) it.gf1 = it.gf0;
-  uint64_t G = std::max<uint64_t>(1, (uint64_t)spt / (steps_per_group * KP));
-  const uint64_t min_ctas = 4ULL * (uint64_t)std::max(1, nsm);
-  G = std::min(G, std::max<uint64_t>(1, (groups + (uint64_t)threads * min_ctas - 1) / ((uint64_t)threads * min_ctas)));
-  it.groups_per_thread = (uint32_t)G;
-  const uint64_t per_chunk = G * (uint64_t)threads;
-  const uint64_t nch = (groups + per_chunk - 1) / per_chunk;
-  if (nch > NOALLOC_MAX_CTAS) return MLMC_EINVAL;  // beyond the scratch array's CTA capacity
-  it.n_chunks = (uint32_t)nch;
-  it.chunk_begin = 0;
   const double h = std::ldexp(p->T, -level);
   const double rh = p->r * h, rh2 = p->r * (2.0 * h), sqh = std::sqrt(h);
   const double c2 = p->sigma * sqh, c3 = 0.5 * p->sigma * p->sigma * h;
@@ -1500,15 +1567,24 @@ extern "C" mlmc_status mlmc_level_noalloc(int level, uint64_t N, const mlmc_para
   }
   it.unit = unit;
   it.unit_scale = std::ldexp(1.0f, -unit);
+  const int pc = p->payoff == MLMC_ASIAN ? PC_ASIAN : (p->payoff == MLMC_LOOKBACK ? PC_LOOKBACK : PC_TERMINAL);
+  int threads, spt;
+  tuning_for(family, p->scheme, pc, level, &threads, &spt);
+  uint32_t gpt = 1;
+  const uint64_t nch = chunk_count(groups, steps_per_group(level), KP, threads, spt, nsm, &gpt);
+  if (nch > NOALLOC_MAX_CTAS) return MLMC_EINVAL;  // beyond the scratch array's CTA capacity
+  it.groups_per_thread = gpt;
+  it.n_chunks = (uint32_t)nch;
+  it.chunk_begin = 0;
   CK(cudaMemcpyAsync(&S->item, &it, sizeof(ItemDesc), cudaMemcpyHostToDevice, st));
   LaunchArgs a;
   a.items = &S->item;
   a.n_items = 1;
   a.chunk0 = 0;
+  a.dyn = nullptr;
   a.partials = S->partials;
   make_round_keys(seed, a.rk);
-  const int pc = p->payoff == MLMC_ASIAN ? PC_ASIAN : (p->payoff == MLMC_LOOKBACK ? PC_LOOKBACK : PC_TERMINAL);
-  if (it.n_chunks > 0) CK(launch_by_family(family, p->scheme, pc, dim3(it.n_chunks), dim3(threads), smem, st, a));
+  if (it.n_chunks > 0) CK(launch_by_family(family, p->scheme, pc, dim3(it.n_chunks), dim3(threads), smem, st, a, nullptr));
   finalize_kernel<<<1, 32, 0, st>>>(&S->item, 1, S->partials, &S->out);
   CK(cudaGetLastError());
   DevSums res;

@@ -1,16 +1,30 @@
 // Continuous-batching pricing engine: many adaptive (nested) MLMC requests
-// share every level-kernel launch.
+// share every level-kernel launch, and one engine iteration is one CUDA-graph
+// launch with no host work inside it.
 //
 // Each admitted request owns a slot of FP64 state in device memory (sums of Y
-// and Y^2, sample counts, pending counts per level and estimator).  One engine
-// step gathers the pending (request, level, estimator, count) work of every
-// active slot into one batched plan launch; accumulate_kernel then adds the new
-// sums into each slot and decide_kernel, on the device, recomputes the level variances, the
-// optimal sample counts N = ceil(lambda sqrt(V / C)) (Sec. 2.1 / 2.2) and the
-// bias test of the adaptive loop.  The host only moves the pending counts back
-// to build the next work list.  The arithmetic, and its order, is that of
-// mlmc_estimate, with every floating-point operation rounded separately, so a
-// request's result does not depend on which other requests share its launches.
+// and Y^2, sample counts, pending counts per level and estimator) and, built
+// on the host once at admission, one work-item template per (level,
+// estimator).  An iteration, captured once as a CUDA graph and replayed, is:
+//   sched_kernel   - reads every slot's pending counts, chunks each pending
+//                    (slot, level, estimator) item exactly as a plan would,
+//                    and lays the items out by launch group (kernel family,
+//                    scheme, payoff class, CTA size, seed) with chunk offsets;
+//   fill_kernel    - writes the iteration's work items from the templates;
+//   level kernels  - one device-scheduled launch per group, on forked streams,
+//                    each a fixed grid of resident CTAs looping over the
+//                    group's chunks (level_kernel_dyn);
+//   acc_kernel     - sums each item's chunk partials in chunk order and adds
+//                    them into its slot;
+//   decide_kernel  - per slot: level variances, N = ceil(lambda sqrt(V / C))
+//                    (Sec. 2.1 / 2.2), the bias test, a new level or
+//                    completion;
+// and a copy of the per-slot reports to pinned host memory.  The host admits
+// waiting requests between graph launches and reads completed results.  The
+// arithmetic, and its order, is that of mlmc_estimate, with every
+// floating-point operation rounded separately and every item chunked by its
+// own size only, so a request's result does not depend on which other
+// requests share its launches.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -20,11 +34,13 @@
 #include <deque>
 #include <map>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "host_api.h"
 #include "item.h"
 #include "mlmc.h"
+#include "reduce.cuh"
 
 using namespace mlmc;
 using namespace mlmc_host;
@@ -32,6 +48,8 @@ using namespace mlmc_host;
 namespace {
 
 constexpr int MAXL = 21;
+constexpr int GMAX = 32;                          // launch groups per engine
+constexpr unsigned long long NCAP = 1ULL << 34;   // samples of one item per iteration
 
 struct SlotState {
   int32_t active, done, L, ne;
@@ -44,26 +62,28 @@ struct SlotState {
   double price, se;
 };
 
-// What the host reads back after each step.
+// What the host reads back after each graph launch, per slot.
 struct SlotReport {
   int32_t active, done, L, pad;
-  unsigned long long dN[MAXL][2];
   double price, se;
 };
 
-struct ItemMap {
-  int32_t slot, level, est, exact_int, unit, pad;
+// Per (slot, level, estimator) template: what the scheduler needs beside the ItemDesc.
+struct TmplMeta {
+  int32_t group;          // launch group, -1: no template
+  int32_t kp, threads, spt;
+  int32_t unit, exact_int, level, est;
   double disc;
 };
 
-__device__ double u128_to_double_rn(unsigned long long lo, unsigned long long hi) {
-  if (hi == 0) return __ull2double_rn(lo);
-  const int z = __clzll((long long)hi);
-  unsigned long long m = z ? ((hi << z) | (lo >> (64 - z))) : hi;
-  const unsigned long long rest = z ? (lo << z) : lo;
-  m |= (rest != 0ULL) ? 1ULL : 0ULL;   // sticky bit below the 64 kept bits
-  return ldexp(__ull2double_rn(m), 64 - z);
-}
+// Iteration status (device; copied to pinned host memory with the reports).
+struct EngStatus {
+  uint32_t n_items;                  // work items of the last iteration
+  uint32_t overflow;                 // 1: it needed more chunks than the partial array holds
+  unsigned long long chunks;         // chunks it needed (all groups)
+  unsigned long long path_steps;     // fine path-steps simulated since creation
+  int32_t active, done;              // slots active / completed after it
+};
 
 __device__ double level_var(const SlotState &s, int l, int k) {
   if (k == 0 && ((s.exact_mask >> l) & 1)) return 0.0;  // an exact mean has no variance
@@ -104,30 +124,168 @@ __device__ void update_dn(SlotState &s) {
     }
 }
 
-// Add this step's results into the slots (each (slot, level, estimator) appears at most once).
-__global__ void accumulate_kernel(SlotState *slots, const ItemMap *map, const DevSums *res, int n) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const ItemMap &mp = map[i];
-  SlotState &s = slots[mp.slot];
-  const DevSums &r = res[i];
-  double sum, sum2;
-  if (mp.exact_int) {
-    sum = __dmul_rn(mp.disc, ldexp(__ll2double_rn(r.isum), -mp.unit));
-    sum2 = __dmul_rn(__dmul_rn(mp.disc, mp.disc), ldexp(u128_to_double_rn(r.isum2_lo, r.isum2_hi), -2 * mp.unit));
-  } else {
-    sum = __dmul_rn(mp.disc, r.dsum);
-    sum2 = __dmul_rn(__dmul_rn(mp.disc, mp.disc), r.dsum2);
+// Pending work of template t (slot t / il): samples [first, first + N).
+__device__ bool pending(const SlotState *slots, const TmplMeta *meta, int il, int t, unsigned long long &first,
+                        unsigned long long &N) {
+  const TmplMeta &m = meta[t];
+  if (m.group < 0) return false;
+  const SlotState &S = slots[t / il];
+  if (!S.active || S.done || m.level > S.L || m.est >= S.ne) return false;
+  const unsigned long long dn = S.dN[m.level][m.est];
+  if (dn == 0) return false;
+  N = dn < NCAP ? dn : NCAP;
+  first = S.N[m.level][m.est];
+  return true;
+}
+
+// Chunk count and groups per thread of template t's pending work (as a plan chunks it).
+__device__ uint64_t pending_chunks(const TmplMeta &m, unsigned long long first, unsigned long long N, int num_sms,
+                                   uint32_t *gpt, uint64_t *g0, uint64_t *g1) {
+  const uint64_t spc = samples_per_group(m.level, m.kp);
+  *g0 = first / spc;
+  *g1 = (first + N + spc - 1) / spc;
+  return chunk_count(*g1 - *g0, steps_per_group(m.level), m.kp, m.threads, m.spt, num_sms, gpt);
+}
+
+// One block of 1024 threads: the iteration's work list, grouped by launch group.
+__global__ void __launch_bounds__(1024) sched_kernel(const SlotState *slots, const TmplMeta *meta, int n_tmpl, int il,
+                                                     int n_groups, unsigned long long cap_chunks, int num_sms,
+                                                     uint32_t *t_nch, int *run_src, uint32_t *run_nch,
+                                                     uint32_t *run_cb, DynLaunch *dyn, EngStatus *status) {
+  __shared__ uint32_t s_cnt[GMAX], s_fill[GMAX], s_ioff[GMAX];
+  __shared__ unsigned long long s_chk[GMAX], s_coff[GMAX];
+  __shared__ int s_over;
+  const int tid = threadIdx.x;
+  if (tid < GMAX) { s_cnt[tid] = 0; s_fill[tid] = 0; s_chk[tid] = 0; }
+  __syncthreads();
+  for (int t = tid; t < n_tmpl; t += blockDim.x) {
+    unsigned long long first, N;
+    uint32_t nch = 0;
+    if (pending(slots, meta, il, t, first, N)) {
+      uint32_t gpt;
+      uint64_t g0, g1;
+      nch = (uint32_t)pending_chunks(meta[t], first, N, num_sms, &gpt, &g0, &g1);
+      const int g = meta[t].group;
+      atomicAdd(&s_cnt[g], 1u);
+      atomicAdd(&s_chk[g], (unsigned long long)nch);
+    }
+    t_nch[t] = nch;
   }
-  s.S1[mp.level][mp.est] = __dadd_rn(s.S1[mp.level][mp.est], sum);
-  s.S2[mp.level][mp.est] = __dadd_rn(s.S2[mp.level][mp.est], sum2);
-  s.N[mp.level][mp.est] += s.dN[mp.level][mp.est];
+  __syncthreads();
+  if (tid == 0) {
+    uint32_t ioff = 0;
+    unsigned long long coff = 0;
+    for (int g = 0; g < n_groups; ++g) {
+      s_ioff[g] = ioff;
+      s_coff[g] = coff;
+      ioff += s_cnt[g];
+      coff += s_chk[g];
+    }
+    const int over = coff > cap_chunks;
+    s_over = over;
+    for (int g = 0; g < n_groups; ++g) {
+      DynLaunch d;
+      d.item_off = s_ioff[g];
+      d.n_items = over ? 0u : s_cnt[g];
+      d.chunk0 = (uint32_t)s_coff[g];
+      d.n_chunks = over ? 0u : (uint32_t)s_chk[g];
+      dyn[g] = d;
+    }
+    status->n_items = over ? 0u : ioff;
+    status->overflow = (uint32_t)over;
+    status->chunks = coff;
+    status->active = 0;
+    status->done = 0;
+  }
+  __syncthreads();
+  if (s_over) return;
+  for (int t = tid; t < n_tmpl; t += blockDim.x) {
+    const uint32_t nch = t_nch[t];
+    if (nch == 0) continue;
+    const int g = meta[t].group;
+    const uint32_t pos = s_ioff[g] + atomicAdd(&s_fill[g], 1u);
+    run_src[pos] = t;
+    run_nch[pos] = nch;
+  }
+  __syncthreads();
+  // chunk offsets: warp g scans group g in list order
+  const int warp = tid >> 5, lane = tid & 31;
+  if (warp < n_groups) {
+    const uint32_t beg = s_ioff[warp], n = s_cnt[warp];
+    unsigned long long base = s_coff[warp];
+    for (uint32_t j0 = 0; j0 < n; j0 += 32) {
+      const uint32_t j = j0 + lane;
+      unsigned long long x = j < n ? run_nch[beg + j] : 0ULL;
+      unsigned long long inc = x;
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+      }
+      if (j < n) run_cb[beg + j] = (uint32_t)(base + inc - x);
+      base += __shfl_sync(0xffffffffu, inc, 31);
+    }
+  }
+}
+
+// The iteration's work items, from the templates (one thread per item).
+__global__ void fill_kernel(const SlotState *slots, const TmplMeta *meta, const ItemDesc *tmpl, int il,
+                            int num_sms, const int *run_src, const uint32_t *run_nch, const uint32_t *run_cb,
+                            const EngStatus *status, ItemDesc *run, unsigned long long *run_n) {
+  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (status->overflow || j >= status->n_items) return;
+  const int t = run_src[j];
+  unsigned long long first = 0, N = 0;
+  pending(slots, meta, il, t, first, N);
+  uint32_t gpt;
+  uint64_t g0, g1;
+  pending_chunks(meta[t], first, N, num_sms, &gpt, &g0, &g1);
+  const uint64_t spc = samples_per_group(meta[t].level, meta[t].kp);
+  ItemDesc it = tmpl[t];
+  it.first = first;
+  it.N = N;
+  it.g0 = g0;
+  it.g1 = g1;
+  it.gf0 = (first + spc - 1) / spc;
+  it.gf1 = (first + N) / spc;
+  if (it.gf1 < it.gf0) it.gf1 = it.gf0;
+  it.groups_per_thread = gpt;
+  it.n_chunks = run_nch[j];
+  it.chunk_begin = run_cb[j];
+  it.out_index = j;
+  run[j] = it;
+  run_n[j] = N;
+}
+
+// Sum each item's chunk partials (one warp per item, chunk order) and add the
+// result into its slot (each (slot, level, estimator) appears at most once).
+__global__ void acc_kernel(SlotState *slots, const TmplMeta *meta, int il, const int *run_src,
+                           const uint32_t *run_nch, const uint32_t *run_cb, const unsigned long long *run_n,
+                           const Partial *partials, EngStatus *status) {
+  const uint32_t j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (status->overflow || j >= status->n_items) return;
+  const DevSums r = warp_sum_partials(partials + run_cb[j], run_nch[j]);
+  if ((threadIdx.x & 31) != 0) return;
+  const int t = run_src[j];
+  const TmplMeta &m = meta[t];
+  SlotState &s = slots[t / il];
+  double sum, sum2;
+  if (m.exact_int) {
+    sum = __dmul_rn(m.disc, ldexp(__ll2double_rn(r.isum), -m.unit));
+    sum2 = __dmul_rn(__dmul_rn(m.disc, m.disc), ldexp(u128_to_double_rn(r.isum2_lo, r.isum2_hi), -2 * m.unit));
+  } else {
+    sum = __dmul_rn(m.disc, r.dsum);
+    sum2 = __dmul_rn(__dmul_rn(m.disc, m.disc), r.dsum2);
+  }
+  s.S1[m.level][m.est] = __dadd_rn(s.S1[m.level][m.est], sum);
+  s.S2[m.level][m.est] = __dadd_rn(s.S2[m.level][m.est], sum2);
+  s.N[m.level][m.est] += run_n[j];
+  atomicAdd(&status->path_steps, run_n[j] << m.level);
 }
 
 // Per slot: new sample counts, the bias test, a new level, or completion.
-__global__ void decide_kernel(SlotState *slots, SlotReport *rep, int n_slots) {
+__global__ void decide_kernel(SlotState *slots, SlotReport *rep, int n_slots, EngStatus *status) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_slots) return;
+  if (i >= n_slots || status->overflow) return;
   SlotState &s = slots[i];
   SlotReport &r = rep[i];
   if (s.active && !s.done) {
@@ -174,9 +332,10 @@ __global__ void decide_kernel(SlotState *slots, SlotReport *rep, int n_slots) {
   r.active = s.active;
   r.done = s.done;
   r.L = s.L;
-  for (int l = 0; l < MAXL; ++l) { r.dN[l][0] = s.dN[l][0]; r.dN[l][1] = s.dN[l][1]; }
   r.price = s.price;
   r.se = s.se;
+  if (s.active && !s.done) atomicAdd(&status->active, 1);
+  if (s.active && s.done) atomicAdd(&status->done, 1);
 }
 
 struct Request {
@@ -189,9 +348,9 @@ struct Request {
   double t_submit, t_admit, t_done;
   int slot;
   int done;
+  mlmc_status status;                 // MLMC_OK, or why admission failed
   double price, se;
   int L;
-  unsigned long long N[MAXL][2];      // samples taken so far (host mirror of the slot's counts)
   int exact_mask;                     // bit l: approximate term of level l computed by enumeration
 };
 
@@ -221,34 +380,267 @@ bool mode_variants(int mode, int &ne, int v[2]) {
   }
 }
 
+// A launch group: the items of one level-kernel launch per iteration.
+struct Group {
+  int family, scheme, pc, threads;
+  size_t smem;
+  uint64_t seed;
+  RoundKeys rk;
+  int refs = 0;           // templates of admitted requests in this group
+  int grid = 0;           // resident CTAs of the device-scheduled kernel
+  bool in_graph = false;
+};
+
+template <class T>
+bool dev_alloc(T **p, size_t n) {
+  return cudaMalloc((void **)p, sizeof(T) * std::max<size_t>(n, 1)) == cudaSuccess;
+}
+
 }  // namespace
 
 struct mlmc_engine {
-  int max_slots = 0, max_level = 10;
+  int max_slots = 0, max_level = 10, il = 0, iters = 1;
+  int num_sms = 0;
+  // device state
   SlotState *d_slots = nullptr;
   SlotReport *d_rep = nullptr;
-  ItemMap *d_map = nullptr;
-  size_t map_cap = 0;
-  std::vector<SlotReport> h_rep;
-  std::vector<int> slot_req;                 // slot -> index in reqs, -1 if free
-  std::deque<size_t> queue;                  // waiting requests (indices into reqs)
+  ItemDesc *d_tmpl = nullptr, *d_run = nullptr;
+  TmplMeta *d_meta = nullptr;
+  uint32_t *d_tnch = nullptr, *d_run_nch = nullptr, *d_run_cb = nullptr;
+  int *d_run_src = nullptr;
+  unsigned long long *d_run_n = nullptr;
+  DynLaunch *d_dyn = nullptr;
+  EngStatus *d_status = nullptr;
+  Partial *d_partials = nullptr;
+  unsigned long long cap_chunks = 0;
+  // pinned host copies of the reports
+  SlotReport *h_rep = nullptr;
+  EngStatus *h_status = nullptr;
+  // groups and the captured iteration
+  std::vector<Group> groups;
+  std::vector<std::vector<int>> slot_groups;   // per slot: group of each template (for refs)
+  bool dirty = true;
+  cudaStream_t cs = nullptr;                   // capture stream
+  std::vector<cudaStream_t> aux;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  // host queue
+  std::vector<int> slot_req;                   // slot -> index in reqs, -1 if free
+  std::deque<size_t> queue;                    // waiting requests (indices into reqs)
   std::vector<Request> reqs;
   std::map<uint64_t, size_t> by_id;
   uint64_t next_id = 1;
-  uint64_t steps = 0, launches = 0, path_steps = 0;
+  uint64_t steps = 0, launches = 0, path_steps = 0, captures = 0;
 };
+
+namespace {
+
+size_t slot_bytes(int il) {
+  return sizeof(SlotState) + sizeof(SlotReport) +
+         (size_t)il * (2 * sizeof(ItemDesc) + sizeof(TmplMeta) + 4 * sizeof(uint32_t) + sizeof(unsigned long long) +
+                       4 * sizeof(Partial));
+}
+
+void release(mlmc_engine *e) {
+  if (e->exec) cudaGraphExecDestroy(e->exec);
+  if (e->graph) cudaGraphDestroy(e->graph);
+  for (auto st : e->aux) cudaStreamDestroy(st);
+  for (auto ev : e->join) cudaEventDestroy(ev);
+  if (e->fork) cudaEventDestroy(e->fork);
+  if (e->cs) cudaStreamDestroy(e->cs);
+  cudaFree(e->d_slots); cudaFree(e->d_rep); cudaFree(e->d_tmpl); cudaFree(e->d_run); cudaFree(e->d_meta);
+  cudaFree(e->d_tnch); cudaFree(e->d_run_nch); cudaFree(e->d_run_cb); cudaFree(e->d_run_src); cudaFree(e->d_run_n);
+  cudaFree(e->d_dyn); cudaFree(e->d_status); cudaFree(e->d_partials);
+  if (e->h_rep) cudaFreeHost(e->h_rep);
+  if (e->h_status) cudaFreeHost(e->h_status);
+}
+
+// Capture `iters` iterations (and the report copies) as one CUDA graph.
+mlmc_status capture(mlmc_engine *e) {
+  if (e->exec) { cudaGraphExecDestroy(e->exec); e->exec = nullptr; }
+  if (e->graph) { cudaGraphDestroy(e->graph); e->graph = nullptr; }
+  std::vector<int> live;
+  for (int gi = 0; gi < (int)e->groups.size(); ++gi) {
+    Group &G = e->groups[gi];
+    G.in_graph = G.refs > 0;
+    if (!G.in_graph) continue;
+    live.push_back(gi);
+    if (G.grid == 0) {
+      int nb = 0;
+      LaunchArgs q;
+      std::memset(&q, 0, sizeof q);
+      MLMC_CK(launch_by_family(G.family, G.scheme, G.pc, dim3(1), dim3(G.threads), G.smem, e->cs, q, &nb));
+      if (nb < 1) return MLMC_EINVAL;
+      G.grid = nb * e->num_sms;
+    }
+  }
+  while (e->aux.size() < live.size()) {
+    cudaStream_t st;
+    cudaEvent_t ev;
+    MLMC_CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    e->aux.push_back(st);
+    MLMC_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    e->join.push_back(ev);
+  }
+  const int n_tmpl = e->max_slots * e->il;
+  MLMC_CK(cudaStreamBeginCapture(e->cs, cudaStreamCaptureModeThreadLocal));
+  cudaError_t err = cudaSuccess;
+  for (int k = 0; k < e->iters && err == cudaSuccess; ++k) {
+    sched_kernel<<<1, 1024, 0, e->cs>>>(e->d_slots, e->d_meta, n_tmpl, e->il, (int)e->groups.size(), e->cap_chunks,
+                                        e->num_sms, e->d_tnch, e->d_run_src, e->d_run_nch, e->d_run_cb, e->d_dyn,
+                                        e->d_status);
+    fill_kernel<<<(n_tmpl + 127) / 128, 128, 0, e->cs>>>(e->d_slots, e->d_meta, e->d_tmpl, e->il, e->num_sms,
+                                                         e->d_run_src, e->d_run_nch, e->d_run_cb, e->d_status,
+                                                         e->d_run, e->d_run_n);
+    err = cudaEventRecord(e->fork, e->cs);
+    for (size_t i = 0; i < live.size() && err == cudaSuccess; ++i) {
+      const Group &G = e->groups[live[i]];
+      cudaStream_t ls = e->aux[i];
+      LaunchArgs a;
+      a.items = e->d_run;
+      a.n_items = 0;
+      a.chunk0 = 0;
+      a.partials = e->d_partials;
+      a.rk = G.rk;
+      a.dyn = e->d_dyn + live[i];
+      if ((err = cudaStreamWaitEvent(ls, e->fork, 0)) != cudaSuccess) break;
+      if ((err = launch_by_family(G.family, G.scheme, G.pc, dim3(G.grid), dim3(G.threads), G.smem, ls, a,
+                                  nullptr)) != cudaSuccess)
+        break;
+      if ((err = cudaEventRecord(e->join[i], ls)) != cudaSuccess) break;
+      err = cudaStreamWaitEvent(e->cs, e->join[i], 0);
+    }
+    if (err != cudaSuccess) break;
+    acc_kernel<<<(n_tmpl + 3) / 4, 128, 0, e->cs>>>(e->d_slots, e->d_meta, e->il, e->d_run_src, e->d_run_nch,
+                                                    e->d_run_cb, e->d_run_n, e->d_partials, e->d_status);
+    decide_kernel<<<(e->max_slots + 127) / 128, 128, 0, e->cs>>>(e->d_slots, e->d_rep, e->max_slots, e->d_status);
+    err = cudaGetLastError();
+  }
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(e->h_rep, e->d_rep, sizeof(SlotReport) * e->max_slots, cudaMemcpyDeviceToHost, e->cs);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(e->h_status, e->d_status, sizeof(EngStatus), cudaMemcpyDeviceToHost, e->cs);
+  cudaGraph_t gr = nullptr;
+  const cudaError_t end = cudaStreamEndCapture(e->cs, &gr);
+  if (err != cudaSuccess || end != cudaSuccess) {
+    if (gr) cudaGraphDestroy(gr);
+    return MLMC_ECUDA;
+  }
+  e->graph = gr;
+  MLMC_CK(cudaGraphInstantiate(&e->exec, e->graph, 0));
+  e->dirty = false;
+  e->captures += 1;
+  return MLMC_OK;
+}
+
+// Group index of a launch class, added if new (MLMC_EINVAL beyond GMAX).
+mlmc_status group_of(mlmc_engine *e, const BuiltItem &b, int threads, uint64_t seed, int *gi) {
+  for (int i = 0; i < (int)e->groups.size(); ++i) {
+    const Group &G = e->groups[i];
+    if (G.family == b.family && G.scheme == b.scheme && G.pc == b.pc && G.threads == threads && G.smem == b.smem &&
+        G.seed == seed) {
+      *gi = i;
+      return MLMC_OK;
+    }
+  }
+  if ((int)e->groups.size() >= GMAX) return MLMC_EINVAL;
+  Group G;
+  G.family = b.family; G.scheme = b.scheme; G.pc = b.pc; G.threads = threads; G.smem = b.smem; G.seed = seed;
+  make_round_keys(seed, G.rk);
+  e->groups.push_back(G);
+  *gi = (int)e->groups.size() - 1;
+  return MLMC_OK;
+}
+
+// Admit request idx into free slot sl: templates, metadata and initial state.
+mlmc_status admit(mlmc_engine *e, int sl, size_t idx, cudaStream_t st) {
+  Request &r = e->reqs[idx];
+  int ne, v[2];
+  mode_variants(r.mode, ne, v);
+  r.p.formats = r.formats.empty() ? nullptr : r.formats.data();
+  const int il = e->il;
+  std::vector<ItemDesc> tm(il);
+  std::vector<TmplMeta> meta(il);
+  std::vector<int> gl;
+  std::memset(tm.data(), 0, sizeof(ItemDesc) * il);
+  for (int t = 0; t < il; ++t) meta[t].group = -1;
+  for (int l = 0; l <= e->max_level; ++l)
+    for (int k = 0; k < ne; ++k) {
+      const bool exact = k == 0 && ((r.exact_mask >> l) & 1);
+      mlmc_work w;
+      std::memset(&w, 0, sizeof w);
+      w.params = &r.p;
+      w.level = l;
+      w.variant = v[k];
+      w.first_sample = 0;
+      w.N = exact ? (1ULL << (r.p.icdf_bits << l)) : 0;
+      w.stream = -1;
+      w.flags = exact ? MLMC_WORK_ENUMERATE : 0;
+      BuiltItem b;
+      double disc;
+      int unit, ei;
+      mlmc_status s = build_item(w, 0, nullptr, b, disc, unit, ei);
+      if (s != MLMC_OK) return s;
+      int th, sp, gi;
+      tuning_for(b.family, b.scheme, b.pc, l, &th, &sp);
+      if ((s = group_of(e, b, th, r.seed, &gi)) != MLMC_OK) return s;
+      const int t = l * 2 + k;
+      tm[t] = b.it;
+      TmplMeta &m = meta[t];
+      m.group = gi; m.kp = b.kp; m.threads = th; m.spt = sp;
+      m.unit = unit; m.exact_int = ei; m.level = l; m.est = k; m.disc = disc;
+      gl.push_back(gi);
+    }
+  for (int gi : gl) {
+    Group &G = e->groups[gi];
+    if (G.refs++ == 0 && !G.in_graph) e->dirty = true;
+  }
+  e->slot_groups[sl] = gl;
+  SlotState h;
+  std::memset(&h, 0, sizeof h);
+  h.active = 1;
+  h.done = 0;
+  h.L = 2;
+  h.ne = ne;
+  h.max_level = e->max_level;
+  h.eps = r.eps;
+  h.sqrt_theta_eps = std::sqrt(0.5) * r.eps;
+  h.var_target = (1.0 - 0.5) * r.eps * r.eps;
+  h.beta_factor = std::pow(2.0, r.p.scheme == MLMC_MILSTEIN ? 2.0 : 1.0);
+  for (int k = 0; k < ne; ++k) h.cost[k] = cost_of_variant(v[k]);
+  h.exact_mask = r.exact_mask;
+  for (int l = 0; l <= 2; ++l)
+    for (int k = 0; k < ne; ++k)
+      h.dN[l][k] = (k == 0 && ((r.exact_mask >> l) & 1)) ? (1ULL << (r.p.icdf_bits << l)) : 10000;
+  MLMC_CK(cudaMemcpyAsync(e->d_tmpl + (size_t)sl * il, tm.data(), sizeof(ItemDesc) * il, cudaMemcpyHostToDevice, st));
+  MLMC_CK(cudaMemcpyAsync(e->d_meta + (size_t)sl * il, meta.data(), sizeof(TmplMeta) * il, cudaMemcpyHostToDevice,
+                          st));
+  MLMC_CK(cudaMemcpyAsync(e->d_slots + sl, &h, sizeof h, cudaMemcpyHostToDevice, st));
+  // pageable sources: tm, meta and h may go out of scope once cudaMemcpyAsync returns
+  return MLMC_OK;
+}
+
+void free_slot_groups(mlmc_engine *e, int sl) {
+  for (int gi : e->slot_groups[sl]) e->groups[gi].refs -= 1;
+  e->slot_groups[sl].clear();
+}
+
+}  // namespace
 
 extern "C" {
 
 mlmc_status mlmc_engine_create(mlmc_engine **out, const mlmc_engine_config *cfg) {
   if (!out || !cfg || cfg->max_level < 2 || cfg->max_level > MAXL - 1) return MLMC_EINVAL;
+  if (cfg->iters_per_launch < 0 || cfg->iters_per_launch > 64 || cfg->reserved != 0) return MLMC_EINVAL;
   mlmc_status s = ensure_ctx();
   if (s != MLMC_OK) return s;
+  const int il = (cfg->max_level + 1) * 2;
   int slots = cfg->max_slots > 0 ? cfg->max_slots : 256;
-  // admission by memory: the slot table must fit the budget
+  // admission by memory: per-slot state, templates and work-list space must fit the budget
   if (cfg->device_bytes_budget) {
-    const uint64_t per = sizeof(SlotState) + sizeof(SlotReport);
-    const uint64_t fit = cfg->device_bytes_budget / per;
+    const uint64_t fit = cfg->device_bytes_budget / slot_bytes(il);
     if (fit == 0) return MLMC_ENOMEM;
     slots = (int)std::min<uint64_t>((uint64_t)slots, fit);
   }
@@ -256,16 +648,36 @@ mlmc_status mlmc_engine_create(mlmc_engine **out, const mlmc_engine_config *cfg)
   if (!e) return MLMC_ENOMEM;
   e->max_slots = slots;
   e->max_level = cfg->max_level;
-  if (cudaMalloc(&e->d_slots, sizeof(SlotState) * slots) != cudaSuccess ||
-      cudaMalloc(&e->d_rep, sizeof(SlotReport) * slots) != cudaSuccess ||
-      cudaMemset(e->d_slots, 0, sizeof(SlotState) * slots) != cudaSuccess) {
-    cudaFree(e->d_slots);
-    cudaFree(e->d_rep);
+  e->il = il;
+  e->iters = cfg->iters_per_launch > 0 ? cfg->iters_per_launch : 1;
+  e->num_sms = ctx_num_sms();
+  const size_t nt = (size_t)slots * il;
+  e->cap_chunks = std::max<unsigned long long>(4ULL * nt, 1ULL << 16);
+  bool ok = dev_alloc(&e->d_slots, slots) && dev_alloc(&e->d_rep, slots) && dev_alloc(&e->d_tmpl, nt) &&
+            dev_alloc(&e->d_run, nt) && dev_alloc(&e->d_meta, nt) && dev_alloc(&e->d_tnch, nt) &&
+            dev_alloc(&e->d_run_nch, nt) && dev_alloc(&e->d_run_cb, nt) && dev_alloc(&e->d_run_src, nt) &&
+            dev_alloc(&e->d_run_n, nt) && dev_alloc(&e->d_dyn, GMAX) && dev_alloc(&e->d_status, 1) &&
+            dev_alloc(&e->d_partials, e->cap_chunks) &&
+            cudaHostAlloc((void **)&e->h_rep, sizeof(SlotReport) * slots, cudaHostAllocDefault) == cudaSuccess &&
+            cudaHostAlloc((void **)&e->h_status, sizeof(EngStatus), cudaHostAllocDefault) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&e->cs, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming) == cudaSuccess;
+  if (ok) {
+    std::vector<TmplMeta> none(nt);
+    for (auto &m : none) { std::memset(&m, 0, sizeof m); m.group = -1; }
+    ok = cudaMemset(e->d_slots, 0, sizeof(SlotState) * slots) == cudaSuccess &&
+         cudaMemset(e->d_status, 0, sizeof(EngStatus)) == cudaSuccess &&
+         cudaMemset(e->d_dyn, 0, sizeof(DynLaunch) * GMAX) == cudaSuccess &&
+         cudaMemcpy(e->d_meta, none.data(), sizeof(TmplMeta) * nt, cudaMemcpyHostToDevice) == cudaSuccess;
+  }
+  if (!ok) {
+    release(e);
     delete e;
     return MLMC_ENOMEM;
   }
-  e->h_rep.resize(slots);
+  std::memset(e->h_status, 0, sizeof(EngStatus));
   e->slot_req.assign(slots, -1);
+  e->slot_groups.assign(slots, {});
   *out = e;
   return MLMC_OK;
 }
@@ -289,9 +701,9 @@ mlmc_status mlmc_engine_submit(mlmc_engine *e, const mlmc_params *p, double eps,
   r.t_admit = r.t_done = 0.0;
   r.slot = -1;
   r.done = 0;
+  r.status = MLMC_OK;
   r.price = r.se = 0.0;
   r.L = 0;
-  std::memset(r.N, 0, sizeof r.N);
   r.exact_mask = exact_mask_of(mode, p->icdf_bits);
   e->reqs.push_back(std::move(r));
   const size_t idx = e->reqs.size() - 1;
@@ -310,135 +722,66 @@ mlmc_status mlmc_engine_step(mlmc_engine *e, void *stream, int *active_out, int 
     const size_t idx = e->queue.front();
     e->queue.pop_front();
     Request &r = e->reqs[idx];
-    int ne, v[2];
-    mode_variants(r.mode, ne, v);
-    SlotState h;
-    std::memset(&h, 0, sizeof h);
-    h.active = 1;
-    h.done = 0;
-    h.L = 2;
-    h.ne = ne;
-    h.max_level = e->max_level;
-    h.eps = r.eps;
-    h.sqrt_theta_eps = std::sqrt(0.5) * r.eps;
-    h.var_target = (1.0 - 0.5) * r.eps * r.eps;
-    h.beta_factor = std::pow(2.0, r.p.scheme == MLMC_MILSTEIN ? 2.0 : 1.0);
-    for (int k = 0; k < ne; ++k) h.cost[k] = cost_of_variant(v[k]);
-    h.exact_mask = r.exact_mask;
-    for (int l = 0; l <= 2; ++l)
-      for (int k = 0; k < ne; ++k)
-        h.dN[l][k] = (k == 0 && ((r.exact_mask >> l) & 1)) ? (1ULL << (r.p.icdf_bits << l)) : 10000;
-    MLMC_CK(cudaMemcpyAsync(e->d_slots + sl, &h, sizeof h, cudaMemcpyHostToDevice, st));
-    SlotReport &hr = e->h_rep[sl];
-    std::memset(&hr, 0, sizeof hr);
-    hr.active = 1;
-    hr.L = 2;
-    for (int l = 0; l <= 2; ++l)
-      for (int k = 0; k < ne; ++k) hr.dN[l][k] = h.dN[l][k];
+    const mlmc_status s = admit(e, sl, idx, st);
+    if (s != MLMC_OK) {
+      // the request cannot run (for instance a format its constants do not fit):
+      // it completes with this status and the slot stays free
+      r.done = 1;
+      r.status = s;
+      r.price = r.se = std::nan("");
+      r.t_done = now_s();
+      if (s == MLMC_ECUDA) return s;
+      --sl;
+      continue;
+    }
     e->slot_req[sl] = (int)idx;
     r.slot = sl;
     r.t_admit = now_s();
   }
-  // 2. one batched launch over the pending work of every active slot
-  std::vector<mlmc_work> work;
-  std::vector<ItemMap> map;
-  int active = 0;
-  for (int sl = 0; sl < e->max_slots; ++sl) {
-    const int idx = e->slot_req[sl];
-    if (idx < 0) continue;
-    Request &r = e->reqs[idx];
-    if (r.done) continue;
-    ++active;
-    int ne, v[2];
-    mode_variants(r.mode, ne, v);
-    r.p.formats = r.formats.empty() ? nullptr : r.formats.data();
-    const SlotReport &hr = e->h_rep[sl];
-    for (int l = 0; l <= hr.L; ++l)
-      for (int k = 0; k < ne; ++k)
-        if (hr.dN[l][k] > 0) {
-          mlmc_work w;
-          std::memset(&w, 0, sizeof w);
-          w.params = &r.p;
-          w.level = l;
-          w.variant = v[k];
-          w.N = hr.dN[l][k];
-          w.first_sample = r.N[l][k];
-          w.stream = -1;
-          w.flags = (k == 0 && ((r.exact_mask >> l) & 1)) ? MLMC_WORK_ENUMERATE : 0;
-          work.push_back(w);
-          ItemMap m;
-          std::memset(&m, 0, sizeof m);
-          m.slot = sl;
-          m.level = l;
-          m.est = k;
-          map.push_back(m);
-        }
-  }
-  (void)active;
-  if (!work.empty()) {
-    // one launch per distinct seed (the key of Philox); requests sharing a seed are
-    // told apart by the request id in their counters
-    std::map<uint64_t, std::vector<size_t>> by_seed;
-    for (size_t i = 0; i < work.size(); ++i) by_seed[e->reqs[e->slot_req[map[i].slot]].seed].push_back(i);
-    for (auto &kv : by_seed) {
-      const std::vector<size_t> &ix = kv.second;
-      std::vector<mlmc_work> w;
-      for (size_t i : ix) w.push_back(work[i]);
-      mlmc_plan *pl = nullptr;
-      mlmc_status s = plan_create_transient(&pl, w.data(), (int)w.size(), kv.first, nullptr);
-      if (s != MLMC_OK) return s;
-      s = plan_launch_on(pl, st);
-      if (s != MLMC_OK) { plan_release(pl); return s; }
-      std::vector<ItemMap> m(ix.size());
-      for (size_t j = 0; j < ix.size(); ++j) {
-        m[j] = map[ix[j]];
-        plan_item_scale(pl, (int)j, &m[j].disc, &m[j].unit, &m[j].exact_int);
+  int running = 0;
+  for (int sl = 0; sl < e->max_slots; ++sl) running += e->slot_req[sl] >= 0;
+  // 2. one graph launch: `iters` iterations of every active slot's pending work
+  if (running > 0) {
+    for (int attempt = 0;; ++attempt) {
+      if (e->dirty) {
+        const mlmc_status s = capture(e);
+        if (s != MLMC_OK) return s;
       }
-      if (m.size() > e->map_cap) {
-        cudaFree(e->d_map);
-        e->d_map = nullptr;
-        e->map_cap = std::max(m.size(), 2 * e->map_cap);
-        MLMC_CK(cudaMalloc(&e->d_map, sizeof(ItemMap) * e->map_cap));
-      }
-      MLMC_CK(cudaMemcpyAsync(e->d_map, m.data(), sizeof(ItemMap) * m.size(), cudaMemcpyHostToDevice, st));
-      accumulate_kernel<<<(unsigned)((m.size() + 127) / 128), 128, 0, st>>>(e->d_slots, e->d_map,
-                                                                            plan_out_device(pl), (int)m.size());
-      MLMC_CK(cudaGetLastError());
+      MLMC_CK(cudaGraphLaunch(e->exec, st));
       MLMC_CK(cudaStreamSynchronize(st));
-      plan_release(pl);
       e->launches += 1;
+      if (!e->h_status->overflow) break;
+      if (attempt >= 4) return MLMC_ENOMEM;
+      // more chunks than the partial array holds: grow it and run the iteration again
+      const unsigned long long need = std::max(2 * e->h_status->chunks, 2 * e->cap_chunks);
+      cudaFree(e->d_partials);
+      e->d_partials = nullptr;
+      if (!dev_alloc(&e->d_partials, need)) return MLMC_ENOMEM;
+      e->cap_chunks = need;
+      e->dirty = true;
     }
-    for (size_t i = 0; i < work.size(); ++i) {
-      e->path_steps += work[i].N << work[i].level;
-      e->reqs[e->slot_req[map[i].slot]].N[map[i].level][map[i].est] += work[i].N;
+    e->path_steps = e->h_status->path_steps;
+    // 3. completed requests leave their slots
+    const double t = now_s();
+    for (int sl = 0; sl < e->max_slots; ++sl) {
+      const int idx = e->slot_req[sl];
+      if (idx < 0) continue;
+      const SlotReport &hr = e->h_rep[sl];
+      Request &r = e->reqs[idx];
+      if (hr.done && !r.done) {
+        r.done = 1;
+        r.price = hr.price;
+        r.se = hr.se;
+        r.L = hr.L;
+        r.t_done = t;
+        SlotState z;
+        std::memset(&z, 0, sizeof z);
+        MLMC_CK(cudaMemcpyAsync(e->d_slots + sl, &z, sizeof z, cudaMemcpyHostToDevice, st));
+        free_slot_groups(e, sl);
+        e->slot_req[sl] = -1;
+      }
     }
   }
-  // 3. decisions on the device, pending counts back to the host
-  decide_kernel<<<(e->max_slots + 127) / 128, 128, 0, st>>>(e->d_slots, e->d_rep, e->max_slots);
-  MLMC_CK(cudaGetLastError());
-  MLMC_CK(cudaMemcpyAsync(e->h_rep.data(), e->d_rep, sizeof(SlotReport) * e->max_slots, cudaMemcpyDeviceToHost,
-                          st));
-  MLMC_CK(cudaStreamSynchronize(st));
-  const double t = now_s();
-  for (int sl = 0; sl < e->max_slots; ++sl) {
-    const int idx = e->slot_req[sl];
-    if (idx < 0) continue;
-    const SlotReport &hr = e->h_rep[sl];
-    Request &r = e->reqs[idx];
-    if (hr.done && !r.done) {
-      r.done = 1;
-      r.price = hr.price;
-      r.se = hr.se;
-      r.L = hr.L;
-      r.t_done = t;
-      // free the slot
-      SlotState z;
-      std::memset(&z, 0, sizeof z);
-      MLMC_CK(cudaMemcpyAsync(e->d_slots + sl, &z, sizeof z, cudaMemcpyHostToDevice, st));
-      e->slot_req[sl] = -1;
-    }
-  }
-  MLMC_CK(cudaStreamSynchronize(st));
   e->steps += 1;
   if (active_out) {
     int a = 0;
@@ -462,7 +805,7 @@ mlmc_status mlmc_engine_poll(mlmc_engine *e, uint64_t req_id, double *price, dou
     if (L) *L = r.L;
     if (latency_s) *latency_s = r.t_done - r.t_submit;
   }
-  return MLMC_OK;
+  return r.status;
 }
 
 mlmc_status mlmc_engine_stats(const mlmc_engine *e, uint64_t *steps, uint64_t *launches, uint64_t *path_steps,
@@ -475,12 +818,55 @@ mlmc_status mlmc_engine_stats(const mlmc_engine *e, uint64_t *steps, uint64_t *l
   return MLMC_OK;
 }
 
+mlmc_status mlmc_engine_graph_info(const mlmc_engine *e, int *groups, int *captures, int *iters_per_launch,
+                                   uint64_t *partial_capacity) {
+  if (!e) return MLMC_EINVAL;
+  if (groups) {
+    int n = 0;
+    for (const Group &G : e->groups) n += G.in_graph;
+    *groups = n;
+  }
+  if (captures) *captures = (int)e->captures;
+  if (iters_per_launch) *iters_per_launch = e->iters;
+  if (partial_capacity) *partial_capacity = e->cap_chunks;
+  return MLMC_OK;
+}
+
 void mlmc_engine_destroy(mlmc_engine *e) {
   if (!e) return;
-  cudaFree(e->d_slots);
-  cudaFree(e->d_rep);
-  cudaFree(e->d_map);
+  if (e->cs) cudaStreamSynchronize(e->cs);
+  release(e);
   delete e;
+}
+
+mlmc_status mlmc_batch_estimate(const mlmc_params *params, const double *eps, int n, int mode, uint64_t seed,
+                                int max_level, int iters_per_launch, double *price, double *stderr_out, int *L,
+                                int *launches, void *stream) {
+  if (!params || !eps || n <= 0 || !price) return MLMC_EINVAL;
+  mlmc_engine_config cfg;
+  std::memset(&cfg, 0, sizeof cfg);
+  cfg.max_slots = n;
+  cfg.max_level = max_level;
+  cfg.iters_per_launch = iters_per_launch;
+  mlmc_engine *e = nullptr;
+  mlmc_status s = mlmc_engine_create(&e, &cfg);
+  if (s != MLMC_OK) return s;
+  std::vector<uint64_t> ids(n);
+  for (int i = 0; i < n && s == MLMC_OK; ++i) s = mlmc_engine_submit(e, &params[i], eps[i], mode, seed, &ids[i]);
+  int active = 1, queued = 1;
+  for (int k = 0; s == MLMC_OK && (active > 0 || queued > 0); ++k) {
+    if (k >= 100000) { s = MLMC_ETIMEOUT; break; }
+    s = mlmc_engine_step(e, stream, &active, &queued);
+  }
+  for (int i = 0; i < n && s == MLMC_OK; ++i) {
+    int done = 0;
+    s = mlmc_engine_poll(e, ids[i], &price[i], stderr_out ? &stderr_out[i] : nullptr, L ? &L[i] : nullptr, &done,
+                         nullptr);
+    if (s == MLMC_OK && !done) s = MLMC_ETIMEOUT;
+  }
+  if (launches) *launches = (int)e->launches;
+  mlmc_engine_destroy(e);
+  return s;
 }
 
 }  // extern "C"

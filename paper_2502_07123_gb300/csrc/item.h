@@ -105,6 +105,16 @@ struct RoundKeys {
   uint32_t k[20];
 };
 
+// Item and chunk counts of a launch whose work is decided on the device (the
+// engine's scheduler writes them before the launch; a CTA takes chunks
+// blockIdx.x, blockIdx.x + gridDim.x, ...).
+struct DynLaunch {
+  uint32_t item_off;       // first item of the launch in LaunchArgs::items
+  uint32_t n_items;
+  uint32_t chunk0;         // global chunk index of the launch's first chunk
+  uint32_t n_chunks;
+};
+
 // Launch-wide arguments of a level kernel (passed as a __grid_constant__ parameter).
 struct LaunchArgs {
   const ItemDesc *items;   // the items of this launch, ordered by chunk_begin
@@ -112,7 +122,39 @@ struct LaunchArgs {
   uint32_t chunk0;         // global chunk index of blockIdx.x == 0
   Partial *partials;       // indexed by global chunk index
   RoundKeys rk;
+  const DynLaunch *dyn;    // nullptr: one chunk per CTA, gridDim.x chunks
 };
+
+#if defined(__CUDACC__)
+#define MLMC_HD __host__ __device__
+#else
+#define MLMC_HD
+#endif
+
+// Sample groups.  A group is one Philox call's worth of packs (4 packs on level
+// 0, 2 on level 1) or, from level 2, one pack over the 2^l / 4 calls of its
+// path; a pack holds kp lockstep samples (kp = 3 with packed draws, else 1).
+MLMC_HD inline uint64_t samples_per_group(int level, int kp) {
+  return (uint64_t)kp * (level >= 2 ? 1u : (level == 1 ? 2u : 4u));
+}
+MLMC_HD inline uint64_t steps_per_group(int level) { return level >= 2 ? (1ULL << level) : 4ULL; }
+
+// Chunking of an item of `groups` sample groups for CTAs of `threads` threads:
+// about spt fine path-steps per thread (at least one group), but no fewer than
+// four CTAs per SM while the item has that many groups.  Returns the number of
+// chunks (CTAs) and sets *gpt, the groups per thread.
+MLMC_HD inline uint64_t chunk_count(uint64_t groups, uint64_t spg, int kp, int threads, int spt, int num_sms,
+                                    uint32_t *gpt) {
+  uint64_t G = (uint64_t)spt / (spg * (uint64_t)kp);
+  if (G < 1) G = 1;
+  const uint64_t min_ctas = 4ULL * (uint64_t)(num_sms > 1 ? num_sms : 1);
+  uint64_t cap = (groups + (uint64_t)threads * min_ctas - 1) / ((uint64_t)threads * min_ctas);
+  if (cap < 1) cap = 1;
+  if (G > cap) G = cap;
+  *gpt = (uint32_t)G;
+  const uint64_t per_chunk = G * (uint64_t)threads;
+  return (groups + per_chunk - 1) / per_chunk;
+}
 
 // Method-3 coefficient tables (Sec. 3.3): d-1 classes.
 struct M3Coef {

@@ -5,7 +5,7 @@
 
 namespace mlmc {
 cudaError_t launch_approx_bf16_p3(int scheme, int pc, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
-                      const LaunchArgs &a) {
-  return launch_family<EST_APPROX, XP_F32, AP_BF16, 3>(scheme, pc, grid, block, smem, st, a);
+                      const LaunchArgs &a, int *occ) {
+  return launch_family<EST_APPROX, XP_F32, AP_BF16, 3>(scheme, pc, grid, block, smem, st, a, occ);
 }
 }  // namespace mlmc

@@ -4,8 +4,12 @@
 
 namespace mlmc {
 struct LaunchArgs;
-#define MLMC_FAMILY(name) \
-  cudaError_t name(int scheme, int pc, dim3 grid, dim3 block, size_t smem, cudaStream_t st, const LaunchArgs &a);
+// Launch one level kernel of the family for (scheme, payoff class).  With
+// occ != nullptr nothing is launched: *occ receives the resident CTAs per SM of
+// the device-scheduled kernel (level_kernel_dyn) for this block and smem size.
+#define MLMC_FAMILY(name)                                                                                      \
+  cudaError_t name(int scheme, int pc, dim3 grid, dim3 block, size_t smem, cudaStream_t st, const LaunchArgs &a, \
+                   int *occ);
 MLMC_FAMILY(launch_exact_f32)
 MLMC_FAMILY(launch_exact_f64)
 MLMC_FAMILY(launch_approx_fixed)

@@ -482,40 +482,48 @@ __device__ __forceinline__ void block_reduce_write(ThreadAcc<EST, XP> &a, Partia
   }
 }
 
+// One chunk (gc) of one launch: find its item, stage the item's table in shared
+// memory (unless *staged, when given, says that it is there already), simulate the chunk's sample groups
+// and write the CTA's Partial for the chunk.  Every thread has finished the
+// previous chunk before the table is overwritten (block_reduce_write ends with
+// a barrier).
 template <int EST, int XP, int AP, int SCHEME, int PC, int KP>
-__global__ void __launch_bounds__(LAUNCH_THREADS, MinCtas<EST, AP, SCHEME, PC>::value)
-level_kernel(const __grid_constant__ LaunchArgs args) {
+__device__ __forceinline__ void run_chunk(const LaunchArgs &args, const ItemDesc *items, int n_items, uint32_t gc,
+                                          const void **staged) {
   using Sim = LevelSim<EST, XP, AP, SCHEME, PC, KP>;
   extern __shared__ __align__(16) unsigned char smem_tab[];
   __shared__ int s_item;
-  const uint32_t gc = args.chunk0 + blockIdx.x;
   if (threadIdx.x == 0) {
-    int lo = 0, hi = args.n_items - 1;
+    int lo = 0, hi = n_items - 1;
     while (lo < hi) {  // last item with chunk_begin <= gc
       const int mid = (lo + hi + 1) >> 1;
-      if (args.items[mid].chunk_begin <= gc) lo = mid; else hi = mid - 1;
+      if (items[mid].chunk_begin <= gc) lo = mid; else hi = mid - 1;
     }
     s_item = lo;
   }
   __syncthreads();
-  const ItemDesc &it = args.items[s_item];
-  // stage the approximate-Normal table in shared memory
+  const ItemDesc &it = items[s_item];
+  // stage the approximate-Normal table in shared memory (every thread has
+  // finished the previous chunk: block_reduce_write ends with a barrier)
   if constexpr (AP != AP_NONE) {
-    if (it.method == 1) {
-      const int n = 1 << it.d;
-      if constexpr (AP == AP_FIXED || AP == AP_FX32 || AP == AP_FX64) {
-        const int32_t *src = (const int32_t *)it.ztab;
-        for (int k = threadIdx.x; k < n; k += blockDim.x) ((int32_t *)smem_tab)[k] = src[k];
+    if (!staged || it.ztab != *staged) {
+      if (staged) *staged = it.ztab;
+      if (it.method == 1) {
+        const int n = 1 << it.d;
+        if constexpr (AP == AP_FIXED || AP == AP_FX32 || AP == AP_FX64) {
+          const int32_t *src = (const int32_t *)it.ztab;
+          for (int k = threadIdx.x; k < n; k += blockDim.x) ((int32_t *)smem_tab)[k] = src[k];
+        } else {
+          const uint16_t *src = (const uint16_t *)it.ztab;
+          for (int k = threadIdx.x; k < n; k += blockDim.x) ((uint16_t *)smem_tab)[k] = src[k];
+        }
       } else {
-        const uint16_t *src = (const uint16_t *)it.ztab;
-        for (int k = threadIdx.x; k < n; k += blockDim.x) ((uint16_t *)smem_tab)[k] = src[k];
+        const uint32_t *src = (const uint32_t *)it.ztab;
+        for (int k = threadIdx.x; k < (int)(sizeof(M3Coef) / 4); k += blockDim.x)
+          ((uint32_t *)smem_tab)[k] = src[k];
       }
-    } else {
-      const uint32_t *src = (const uint32_t *)it.ztab;
-      for (int k = threadIdx.x; k < (int)(sizeof(M3Coef) / 4); k += blockDim.x)
-        ((uint32_t *)smem_tab)[k] = src[k];
+      __syncthreads();
     }
-    __syncthreads();
   }
   Sim sim;
   sim.load(it, smem_tab);
@@ -602,17 +610,37 @@ level_kernel(const __grid_constant__ LaunchArgs args) {
   block_reduce_write<EST, XP>(acc, args.partials + gc);
 }
 
+// Static launch: CTA b runs chunk chunk0 + b of the launch.
+template <int EST, int XP, int AP, int SCHEME, int PC, int KP>
+__global__ void __launch_bounds__(LAUNCH_THREADS, MinCtas<EST, AP, SCHEME, PC>::value)
+level_kernel(const __grid_constant__ LaunchArgs args) {
+  run_chunk<EST, XP, AP, SCHEME, PC, KP>(args, args.items, args.n_items, args.chunk0 + blockIdx.x, nullptr);
+}
+
+// Device-scheduled launch (fixed grid, captured once in a CUDA graph): the item
+// and chunk counts come from args.dyn, written on the device before the
+// launch; CTA b runs chunks b, b + gridDim.x, ...
+template <int EST, int XP, int AP, int SCHEME, int PC, int KP>
+__global__ void __launch_bounds__(LAUNCH_THREADS, MinCtas<EST, AP, SCHEME, PC>::value)
+level_kernel_dyn(const __grid_constant__ LaunchArgs args) {
+  const DynLaunch d = *args.dyn;
+  const void *staged = nullptr;
+  for (uint32_t rel = blockIdx.x; rel < d.n_chunks; rel += gridDim.x)
+    run_chunk<EST, XP, AP, SCHEME, PC, KP>(args, args.items + d.item_off, (int)d.n_items, d.chunk0 + rel, &staged);
+}
+
 }  // namespace mlmc
 
 namespace mlmc {
 
 template <int EST, int XP, int AP, int SCHEME, int PC, int KP>
-cudaError_t launch_one(dim3 grid, dim3 block, size_t smem, cudaStream_t st, const LaunchArgs &a) {
-  auto k = level_kernel<EST, XP, AP, SCHEME, PC, KP>;
+cudaError_t launch_one(dim3 grid, dim3 block, size_t smem, cudaStream_t st, const LaunchArgs &a, int *occ) {
+  auto k = (a.dyn || occ) ? level_kernel_dyn<EST, XP, AP, SCHEME, PC, KP> : level_kernel<EST, XP, AP, SCHEME, PC, KP>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
+  if (occ) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, (int)block.x, smem);
   k<<<grid, block, smem, st>>>(a);
   return cudaGetLastError();
 }
@@ -620,14 +648,14 @@ cudaError_t launch_one(dim3 grid, dim3 block, size_t smem, cudaStream_t st, cons
 // All (scheme, payoff class) instantiations of one (estimator, precision) family.
 template <int EST, int XP, int AP, int KP = 1>
 cudaError_t launch_family(int scheme, int pc, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
-                          const LaunchArgs &a) {
+                          const LaunchArgs &a, int *occ) {
   switch (scheme * 3 + pc) {
-    case 0: return launch_one<EST, XP, AP, 0, PC_TERMINAL, KP>(grid, block, smem, st, a);
-    case 1: return launch_one<EST, XP, AP, 0, PC_ASIAN, KP>(grid, block, smem, st, a);
-    case 2: return launch_one<EST, XP, AP, 0, PC_LOOKBACK, KP>(grid, block, smem, st, a);
-    case 3: return launch_one<EST, XP, AP, 1, PC_TERMINAL, KP>(grid, block, smem, st, a);
-    case 4: return launch_one<EST, XP, AP, 1, PC_ASIAN, KP>(grid, block, smem, st, a);
-    case 5: return launch_one<EST, XP, AP, 1, PC_LOOKBACK, KP>(grid, block, smem, st, a);
+    case 0: return launch_one<EST, XP, AP, 0, PC_TERMINAL, KP>(grid, block, smem, st, a, occ);
+    case 1: return launch_one<EST, XP, AP, 0, PC_ASIAN, KP>(grid, block, smem, st, a, occ);
+    case 2: return launch_one<EST, XP, AP, 0, PC_LOOKBACK, KP>(grid, block, smem, st, a, occ);
+    case 3: return launch_one<EST, XP, AP, 1, PC_TERMINAL, KP>(grid, block, smem, st, a, occ);
+    case 4: return launch_one<EST, XP, AP, 1, PC_ASIAN, KP>(grid, block, smem, st, a, occ);
+    case 5: return launch_one<EST, XP, AP, 1, PC_LOOKBACK, KP>(grid, block, smem, st, a, occ);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -58,7 +58,8 @@ class Tuning(ctypes.Structure):
 
 class EngineConfig(ctypes.Structure):
     _fields_ = [("max_slots", ctypes.c_int32), ("max_level", ctypes.c_int32),
-                ("device_bytes_budget", ctypes.c_uint64)]
+                ("device_bytes_budget", ctypes.c_uint64), ("iters_per_launch", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class Work(ctypes.Structure):
@@ -113,7 +114,14 @@ def load():
                                   P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_double)]),
         "mlmc_engine_stats": (st, [ctypes.c_void_p, P(ctypes.c_uint64), P(ctypes.c_uint64), P(ctypes.c_uint64),
                                    P(ctypes.c_int)]),
+        "mlmc_engine_graph_info": (st, [ctypes.c_void_p, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int),
+                                        P(ctypes.c_uint64)]),
         "mlmc_engine_destroy": (None, [ctypes.c_void_p]),
+        "mlmc_batch_estimate": (st, [P(Params), P(ctypes.c_double), ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                     ctypes.c_int, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_double),
+                                     P(ctypes.c_int), P(ctypes.c_int), ctypes.c_void_p]),
+        "mlmc_autotune": (st, [P(Work), ctypes.c_int, ctypes.c_uint64, ctypes.c_int, P(Tuning)]),
+        "mlmc_tuning_reset": (None, []),
         "mlmc_default_format": (st, [P(Params), ctypes.c_int, P(Format)]),
         "mlmc_icdf_table": (st, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_double)]),
         "mlmc_philox": (st, [P(ctypes.c_uint32), ctypes.c_uint64, ctypes.c_uint64, P(ctypes.c_uint32)]),
@@ -287,6 +295,36 @@ def mlmc_run(items, seed, tuning=None, stream=None):
     return [_sums_dict(out[i]) for i in range(len(items))]
 
 
+def mlmc_autotune(items, seed, reps=5):
+    """Time the launch shapes of each kernel class in `items` and install the fastest
+    (mlmc_autotune); returns the chosen (threads, steps_per_thread) per item."""
+    L = load()
+    arr, keep = _works(items)
+    out = (Tuning * len(items))()
+    _check(L.mlmc_autotune(arr, len(items), seed, reps, out), "mlmc_autotune")
+    return [(t.threads, t.steps_per_thread) for t in out]
+
+
+def mlmc_tuning_reset():
+    load().mlmc_tuning_reset()
+
+
+def mlmc_batch_estimate(params_list, eps, mode, seed, max_level=10, iters_per_launch=1, stream=None):
+    """Batched adaptive MLMC through one engine (mlmc_batch_estimate).  params_list: Params
+    structures (distinct request ids); eps: one accuracy per request."""
+    L = load()
+    n = len(params_list)
+    P = (Params * n)(*params_list)
+    E = (ctypes.c_double * n)(*[float(x) for x in eps])
+    pr, se = (ctypes.c_double * n)(), (ctypes.c_double * n)()
+    lv = (ctypes.c_int * n)()
+    launches = ctypes.c_int()
+    h = ctypes.c_void_p(None) if stream is None else _stream_handle(stream)
+    _check(L.mlmc_batch_estimate(P, E, n, mode, seed, max_level, iters_per_launch, pr, se, lv,
+                                 ctypes.byref(launches), h), "mlmc_batch_estimate")
+    return dict(price=list(pr), stderr=list(se), L=list(lv), launches=launches.value)
+
+
 def mlmc_estimate(eps, params, mode, seed, max_level=10):
     L = load()
     cap = max_level + 1
@@ -302,9 +340,9 @@ def mlmc_estimate(eps, params, mode, seed, max_level=10):
 class Engine:
     """Continuous-batching engine (mlmc_engine_*): submit requests, step, poll."""
 
-    def __init__(self, max_slots=256, max_level=10, device_bytes_budget=0):
+    def __init__(self, max_slots=256, max_level=10, device_bytes_budget=0, iters_per_launch=1):
         L = load()
-        cfg = EngineConfig(max_slots, max_level, device_bytes_budget)
+        cfg = EngineConfig(max_slots, max_level, device_bytes_budget, iters_per_launch, 0)
         self._h = ctypes.c_void_p()
         _check(L.mlmc_engine_create(ctypes.byref(self._h), ctypes.byref(cfg)), "mlmc_engine_create")
         self._keep = {}
@@ -336,6 +374,13 @@ class Engine:
         _check(load().mlmc_engine_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
                                         ctypes.byref(sl)), "mlmc_engine_stats")
         return dict(steps=a.value, launches=b.value, path_steps=c.value, slots=sl.value)
+
+    def graph_info(self):
+        g, c, it = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        cap = ctypes.c_uint64()
+        _check(load().mlmc_engine_graph_info(self._h, ctypes.byref(g), ctypes.byref(c), ctypes.byref(it),
+                                             ctypes.byref(cap)), "mlmc_engine_graph_info")
+        return dict(groups=g.value, captures=c.value, iters_per_launch=it.value, partial_capacity=cap.value)
 
     def close(self):
         if self._h:

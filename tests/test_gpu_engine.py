@@ -109,6 +109,64 @@ def test_engine_admission_by_slots_and_memory(m):
     with pytest.raises(m.MLMCError) as e:
         m.Engine(max_slots=4, max_level=8, device_bytes_budget=64)
     assert e.value.status == m.ENOMEM
-    small = m.Engine(max_slots=100, max_level=8, device_bytes_budget=2 * 3000)
-    assert small.stats()["slots"] < 100
+    small = m.Engine(max_slots=100, max_level=8, device_bytes_budget=1 << 20)
+    assert 1 <= small.stats()["slots"] < 100
     small.close()
+
+
+def test_engine_graph_iterations_and_partial_growth(m):
+    """One graph launch per step (captured once per new launch class); an
+    iteration that needs more chunks than the partial array holds grows the
+    array and reruns, with the same result as mlmc_estimate."""
+    pA = W.params(payoff=W.EURO)
+    eps = 0.004
+    ref = m.mlmc_estimate(eps, _P(m, pA, 3), 2, 21, 10)
+    eng = m.Engine(max_slots=1, max_level=10)
+    cap0 = eng.graph_info()["partial_capacity"]
+    rid = eng.submit(_P(m, pA, 3), eps, 2, 21)
+    res = _run(eng, [rid])[rid]
+    gi = eng.graph_info()
+    st = eng.stats()
+    eng.close()
+    assert res["price"] == ref["price"] and res["stderr"] == ref["stderr"] and res["L"] == ref["L"]
+    assert gi["partial_capacity"] > cap0
+    assert 2 <= gi["groups"] <= 4         # approximate (packed) and correction kernels, 32- or 64-bit S
+    assert gi["captures"] <= 1 + 5        # first capture plus one per growth of the partial array
+    assert st["launches"] >= st["steps"]
+
+
+@pytest.mark.parametrize("iters", [1, 4])
+def test_batch_estimate_equals_estimate(m, iters):
+    """mlmc_batch_estimate: a mixed batch (payoffs, accuracies, options) in one
+    engine; each result equals mlmc_estimate of that request alone."""
+    opts = W.batched_options(12, seed=5)
+    plist, eps = [], []
+    for i, o in enumerate(opts):
+        plist.append(_P(m, o, 300 + i))
+        eps.append(max(o["eps"], 4e-3) * 5)
+    out = m.mlmc_batch_estimate(plist, eps, 5, 13, max_level=10, iters_per_launch=iters)
+    for i in range(len(opts)):
+        ref = m.mlmc_estimate(eps[i], plist[i], 5, 13, 10)
+        assert out["price"][i] == ref["price"] and out["stderr"][i] == ref["stderr"], i
+        assert out["L"][i] == ref["L"]
+    assert out["launches"] >= 1
+    if iters > 1:
+        single = m.mlmc_batch_estimate(plist, eps, 5, 13, max_level=10, iters_per_launch=1)
+        assert out["launches"] < single["launches"]
+
+
+def test_engine_rejects_unfit_request_without_failing_others(m):
+    """A request whose fixed-point formats cannot hold its constants completes
+    with MLMC_EOVERFLOW; the others run."""
+    p = W.params()
+    bad = [dict(e=list(f["e"]), f=list(f["f"])) for f in (W.default_format(p, lev) for lev in range(11))]
+    bad[1]["e"][6] = 2        # S in 2 integer bits cannot hold S0 = 100
+    eng = m.Engine(max_slots=4, max_level=10)
+    r_bad = eng.submit(m.make_params(p, d=10, method=1, formats=bad, request=1), 0.05, 2, 3)
+    r_ok = eng.submit(_P(m, p, 2), 0.05, 2, 3)
+    with pytest.raises(m.MLMCError) as e:
+        _run(eng, [r_bad, r_ok])
+    assert e.value.status == m.EOVERFLOW
+    res = _run(eng, [r_ok])
+    eng.close()
+    assert math.isfinite(res[r_ok]["price"])
