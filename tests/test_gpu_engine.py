@@ -119,7 +119,7 @@ def test_engine_graph_iterations_and_partial_growth(m):
     iteration that needs more chunks than the partial array holds grows the
     array and reruns, with the same result as mlmc_estimate."""
     pA = W.params(payoff=W.EURO)
-    eps = 0.004
+    eps = 4e-4      # about 5e9 approximate samples on level 0: > 65536 chunks in one iteration
     ref = m.mlmc_estimate(eps, _P(m, pA, 3), 2, 21, 10)
     eng = m.Engine(max_slots=1, max_level=10)
     cap0 = eng.graph_info()["partial_capacity"]
