@@ -164,6 +164,7 @@ def main():
     ap.add_argument("--ref-fraction", type=float, default=0.1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tte", action="store_true")
+    ap.add_argument("--no-serving-sample", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shape (128 threads, 256 path-steps per thread)")
     ap.add_argument("--serving", action="store_true",
@@ -284,6 +285,11 @@ def main():
     }
     if rank == 0 and not args.no_tte:
         out["time_to_eps"] = time_to_eps(m, torch)
+    if rank == 0 and world == 1 and not args.no_serving_sample:
+        # bounded serving sample: 200 requests drawn as the serving workload at
+        # 1000 req/s, accuracies in the coarser half [1e-3, 1e-2] of its range
+        # (--serving runs the full range; its tail of eps ~ 1e-4 requests takes minutes)
+        out["serving_sample"] = serving_run(m, 1000, n=200, eps_range=(1e-3, 1e-2))
     if rank == 0 and world == 1 and args.serving:
         out["batched"] = batched_run(m)
         out["serving"] = [serving_run(m, rate) for rate in (100, 1000, 10000)]
@@ -314,34 +320,62 @@ def _bs_price(o):
     return None
 
 
-def _engine_params(m, o, request):
-    return m.make_params(o, d=10, method=1, formats=[W.default_format(o, lev) for lev in range(11)],
+def _engine_params(m, o, request, max_level=10):
+    return m.make_params(o, d=10, method=1, formats=[W.default_format(o, lev) for lev in range(max_level + 1)],
                          request=request, rng_pack=1)
 
 
-def batched_run(m, n=256, seed=7, mode=5, iters_per_launch=2):
-    """The batched workload through mlmc_batch_estimate: all n options in one
-    engine, every graph launch running iters_per_launch iterations of all of them."""
+def _accuracy(done, opts, max_level):
+    """RMS of (price - Black-Scholes) / eps over the European and digital requests,
+    and the number of requests that stopped at the maximum level."""
+    errs = [(done[i]["price"] - _bs_price(o)) / o["eps"] for i, o in enumerate(opts) if _bs_price(o) is not None]
+    at_max = sum(1 for i in range(len(opts)) if done[i]["L"] >= max_level)
+    return {"rms_err_over_eps_vs_black_scholes": math.sqrt(sum(e * e for e in errs) / len(errs)),
+            "checked_against_black_scholes": len(errs), "stopped_at_max_level": at_max,
+            "max_level": max_level}
+
+
+def batched_run(m, n=256, seed=7, mode=5, iters_per_launch=2, max_level=14):
+    """The batched workload: all n options submitted at once to one engine, every
+    graph launch running iters_per_launch iterations of all of them (what
+    mlmc_batch_estimate does, with the engine's counters kept)."""
     opts = W.batched_options(n, seed)
-    plist = [_engine_params(m, o, i) for i, o in enumerate(opts)]
-    eps = [o["eps"] for o in opts]
-    m.mlmc_batch_estimate(plist[:4], [1e-2] * 4, mode, 1, max_level=10)   # warm tables and kernels
+    eng = m.Engine(max_slots=n, max_level=max_level, iters_per_launch=iters_per_launch)
+    _engine_solve(eng, _engine_params(m, opts[0], 0, max_level), 1e-2, mode, 99)   # warm tables and kernels
+    s0 = eng.stats()
     t0 = time.perf_counter()
-    r = m.mlmc_batch_estimate(plist, eps, mode, 1, max_level=10, iters_per_launch=iters_per_launch)
+    rids = [eng.submit(_engine_params(m, o, i, max_level), o["eps"], mode, 1) for i, o in enumerate(opts)]
+    done = {}
+    while len(done) < n:
+        eng.step()
+        for i, r in enumerate(rids):
+            if i not in done:
+                res = eng.poll(r)
+                if res is not None:
+                    done[i] = res
     wall = time.perf_counter() - t0
-    errs = [(r["price"][i] - _bs_price(o)) / o["eps"] for i, o in enumerate(opts) if _bs_price(o) is not None]
-    return {"requests": n, "mode": mode, "wall_s": wall, "requests_per_s": n / wall,
-            "graph_launches": r["launches"], "iters_per_launch": iters_per_launch,
-            "rms_err_over_eps_vs_black_scholes": math.sqrt(sum(e * e for e in errs) / len(errs)),
-            "checked_against_black_scholes": len(errs)}
+    st = eng.stats()
+    gi = eng.graph_info()
+    eng.close()
+    lat = sorted(done[i]["latency_s"] for i in range(n))
+    out = {"requests": n, "mode": mode, "wall_s": wall, "requests_per_s": n / wall,
+           "graph_launches": st["launches"] - s0["launches"], "iters_per_launch": iters_per_launch,
+           "graph_captures": gi["captures"], "launch_classes": gi["groups"],
+           "path_steps": st["path_steps"] - s0["path_steps"],
+           "path_steps_per_s": (st["path_steps"] - s0["path_steps"]) / wall,
+           "p50_latency_s": lat[n // 2], "p99_latency_s": lat[min(n - 1, int(0.99 * n))]}
+    out.update(_accuracy(done, opts, max_level))
+    return out
 
 
-def serving_run(m, rate, n=400, seed=11, mode=5):
+def serving_run(m, rate, n=400, seed=11, mode=5, max_level=14, eps_range=(1e-4, 1e-2)):
     """Poisson arrivals at `rate` req/s, options drawn as the batched workload;
     requests are admitted while others run (continuous batching)."""
     arrivals = W.poisson_arrivals(rate, n, seed)
-    opts = W.batched_options(n, seed)
-    eng = m.Engine(max_slots=256, max_level=10)
+    opts = W.batched_options(n, seed, eps_range)
+    eng = m.Engine(max_slots=256, max_level=max_level)
+    _engine_solve(eng, _engine_params(m, opts[0], 0, max_level), 1e-2, mode, 99)   # warm tables and kernels
+    s0 = eng.stats()
     rids = [None] * n
     done = {}
     nxt = 0
@@ -349,7 +383,7 @@ def serving_run(m, rate, n=400, seed=11, mode=5):
     while len(done) < n:
         t = time.perf_counter() - t0
         while nxt < n and arrivals[nxt] <= t:
-            rids[nxt] = eng.submit(_engine_params(m, opts[nxt], nxt), opts[nxt]["eps"], mode, 1)
+            rids[nxt] = eng.submit(_engine_params(m, opts[nxt], nxt, max_level), opts[nxt]["eps"], mode, 1)
             nxt += 1
         if nxt == len(done) and nxt < n:
             time.sleep(max(0.0, min(arrivals[nxt] - t, 0.01)))
@@ -365,11 +399,14 @@ def serving_run(m, rate, n=400, seed=11, mode=5):
     gi = eng.graph_info()
     eng.close()
     lat = sorted(done[i]["latency_s"] for i in range(n))
-    errs = [(done[i]["price"] - _bs_price(o)) / o["eps"] for i, o in enumerate(opts) if _bs_price(o) is not None]
-    return {"arrival_rate": rate, "requests": n, "mode": mode, "wall_s": wall, "requests_per_s": n / wall,
-            "p50_latency_s": lat[n // 2], "p99_latency_s": lat[min(n - 1, int(0.99 * n))],
-            "engine_steps": st["steps"], "graph_launches": st["launches"], "graph_captures": gi["captures"],
-            "rms_err_over_eps_vs_black_scholes": math.sqrt(sum(e * e for e in errs) / len(errs))}
+    out = {"arrival_rate": rate, "requests": n, "eps_range": list(eps_range), "mode": mode, "wall_s": wall,
+           "requests_per_s": n / wall,
+           "p50_latency_s": lat[n // 2], "p99_latency_s": lat[min(n - 1, int(0.99 * n))],
+           "engine_steps": st["steps"] - s0["steps"], "graph_launches": st["launches"] - s0["launches"],
+           "graph_captures": gi["captures"], "path_steps": st["path_steps"] - s0["path_steps"],
+           "path_steps_per_s": (st["path_steps"] - s0["path_steps"]) / wall}
+    out.update(_accuracy(done, opts, max_level))
+    return out
 
 
 def _engine_solve(eng, P, eps, mode, seed):

@@ -135,15 +135,16 @@ def sweep_points():
     return pts
 
 
-def batched_options(n=256, seed=7):
-    """Batched workload: n independent options; payoff mix European / digital / Asian."""
+def batched_options(n=256, seed=7, eps_range=(1e-4, 1e-2)):
+    """Batched workload: n independent options; payoff mix European / digital / Asian;
+    accuracies log-uniform in eps_range."""
     rng = np.random.default_rng(seed)
     S0 = rng.uniform(80, 120, n)
     K = rng.uniform(80, 120, n)
     sig = rng.uniform(0.1, 0.5, n)
     T = rng.uniform(0.25, 2.0, n)
     pay = rng.integers(0, 3, n)
-    eps = np.exp(rng.uniform(math.log(1e-4), math.log(1e-2), n))
+    eps = np.exp(rng.uniform(math.log(eps_range[0]), math.log(eps_range[1]), n))
     return [dict(S0=float(S0[i]), K=float(K[i]), r=0.05, sigma=float(sig[i]), T=float(T[i]),
                  payoff=int(pay[i]), scheme=EULER, eps=float(eps[i])) for i in range(n)]
 
