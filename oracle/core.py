@@ -72,6 +72,11 @@ class Sums(ctypes.Structure):
                 ("unit", ctypes.c_int32), ("exact_int", ctypes.c_int32)]
 
 
+class Sens(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_double * 7), ("maxabs", ctypes.c_double * 7), ("sum_dp", ctypes.c_double),
+                ("sum_dp2", ctypes.c_double), ("n", ctypes.c_uint64)]
+
+
 _lib = None
 
 
@@ -99,6 +104,14 @@ def lib():
                                ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(Format), ctypes.c_int,
                                ctypes.c_int, ctypes.POINTER(Sums), ctypes.c_void_p]
         L.or_level.restype = ctypes.c_int
+        L.or_sens_instances.argtypes = [ctypes.c_int]
+        L.or_sens_instances.restype = ctypes.c_int
+        L.or_sensitivities.argtypes = [ctypes.POINTER(Params), ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
+                                       ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(Sens), ctypes.c_void_p]
+        L.or_sensitivities.restype = ctypes.c_int
+        L.or_sens_probe.argtypes = [ctypes.POINTER(Params), ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32,
+                                    ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_void_p]
+        L.or_sens_probe.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -199,3 +212,39 @@ def level(p, lev, first, N, variant, seed, request=0, stream=None, d=10, method=
     sums = {k: getattr(S, k) for k, _ in Sums._fields_}
     sums["isum2"] = (int(S.isum2_hi) << 64) | int(S.isum2_lo)
     return sums, out
+
+
+# ---------------------------------------------------------------------------
+# Error-model statistics (Sec. 4.2-4.3), European call, Euler-Maruyama
+# ---------------------------------------------------------------------------
+SENS_VARS = ("Z", "con1", "con2", "mul1", "sum1", "mul2", "S")
+
+
+def sens_instances(lev):
+    return int(lib().or_sens_instances(int(lev)))
+
+
+def sensitivities(p, lev, first, N, seed, request=0, per_instance=True):
+    """Sums over samples [first, first+N) of the per-type squared sensitivities
+    of DeltaP_l, maxima of |x| per type, sums of DeltaP and DeltaP^2, and (if
+    per_instance) the per-instance sums of squared sensitivities (7 x n_inst)."""
+    P = Params(p["S0"], p["K"], p["r"], p["sigma"], p["T"], int(p["payoff"]), int(p["scheme"]))
+    S = Sens()
+    ni = sens_instances(lev)
+    inst = np.zeros((7, ni), dtype=np.float64) if per_instance else None
+    st = lib().or_sensitivities(ctypes.byref(P), int(lev), int(first), int(N), int(seed), int(request),
+                                ctypes.byref(S), inst.ctypes.data if per_instance else None)
+    if st != 0:
+        raise OracleError("or_sensitivities returned %d" % st)
+    return {"A": np.array(S.A[:]), "maxabs": np.array(S.maxabs[:]), "sum_dp": S.sum_dp, "sum_dp2": S.sum_dp2,
+            "n": S.n, "inst": inst}
+
+
+def sens_probe(p, lev, seed, request, s, vtype, inst, delta, want_xbar=False):
+    """DeltaP of sample s with delta added to one instance; with want_xbar also the
+    adjoint sensitivities of every instance of the unperturbed sample (7 x n_inst)."""
+    P = Params(p["S0"], p["K"], p["r"], p["sigma"], p["T"], int(p["payoff"]), int(p["scheme"]))
+    xb = np.zeros((7, sens_instances(lev)), dtype=np.float64) if want_xbar else None
+    dp = lib().or_sens_probe(ctypes.byref(P), int(lev), int(seed), int(request), int(s), int(vtype), int(inst),
+                             float(delta), xb.ctypes.data if want_xbar else None)
+    return (dp, xb) if want_xbar else dp

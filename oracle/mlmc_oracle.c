@@ -674,3 +674,192 @@ void or_draw_packed_array(uint64_t seed, uint32_t request, uint32_t level, uint3
                           const uint64_t *sample, const uint32_t *step, uint64_t n, int d, uint32_t *J) {
   for (uint64_t i = 0; i < n; ++i) J[i] = or_draw_packed(seed, request, level, stream, sample[i], step[i], d);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Error-model statistics of one level (Sec. 4.2-4.3).                      */
+/*                                                                          */
+/* For the level difference DeltaP = P_f - P_c of the European call        */
+/* (discounted, Euler-Maruyama, exact FP64 Normals from stream 0 as the     */
+/* correction estimator draws them), every intermediate variable of          */
+/* Algorithm 1 -- con1 (and the coarse con1 for 2h), con2, Z_k, mul1_k,      */
+/* sum1_k, mul2_k, S_k on the fine and the coarse path, and S0 -- is an      */
+/* instance whose rounding error enters DeltaP.  Its sensitivity            */
+/* xbar = d DeltaP / d x comes from reverse-mode algorithmic                */
+/* differentiation: a forward sweep that records the tape, then a backward  */
+/* sweep through the four operations of each step in reverse order.  The    */
+/* coarse step uses con1c = r 2h, con2 and Zc_k = Z_2k + Z_2k+1, so Z_j and  */
+/* con2 are shared by both paths and S0 starts both.                        */
+/*                                                                          */
+/* Per sample the sums over instances of xbar^2 of each variable type feed  */
+/* V_indep (eq. optimistic); per-instance sums feed V_corr (eq.             */
+/* pessimistic); the maxima of |x| give the exponents (Sec. 4.1).           */
+/* Instance index within a type (n = 2^l fine steps, m = n/2 coarse):      */
+/*   mul1, sum1, mul2: fine k -> k, coarse k -> n + k;                      */
+/*   S: S_{k+1} fine -> k, coarse S^c_{k+1} -> n + k, S0 -> n + m;          */
+/*   Z: Z_j -> j;  con1: fine 0, coarse 1;  con2: 0.                         */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  double A[7];        /* sums over samples of sum_instances xbar^2 per type  */
+  double maxabs[7];   /* max |x| per type                                    */
+  double sum_dp, sum_dp2;
+  uint64_t n;
+} or_sens;
+
+/* One sample: forward sweep (tape), payoffs, backward sweep.  perturb_type /
+ * perturb_inst / delta add delta to one instance right after it is computed
+ * (finite-difference checks); xbar_out (7 x n_inst, may be 0) receives the
+ * sensitivities of every instance.  Returns DeltaP. */
+static double sens_sample(const or_params *p, int level, uint64_t seed, uint32_t request, uint64_t s,
+                          int perturb_type, int perturb_inst, double delta, double *tape, double *xbar_out,
+                          int n_inst, double *maxabs) {
+  const int n = 1 << level, m = level > 0 ? n / 2 : 0;
+  const double h = ldexp(p->T, -level);
+  const double disc = exp(-p->r * p->T);
+  double *Z = tape, *S = Z + n, *mul1 = S + n + 1, *sum1 = mul1 + n, *mul2 = sum1 + n;
+  double *Zc = mul2 + n, *Sc = Zc + m, *mul1c = Sc + m + 1, *sum1c = mul1c + m, *mul2c = sum1c + m;
+#define PERT(type, inst, x) ((perturb_type == (type) && perturb_inst == (inst)) ? (x) + delta : (x))
+  double con1 = PERT(V_CON1, 0, p->r * h);
+  double con1c = PERT(V_CON1, 1, p->r * (2.0 * h));
+  double con2 = PERT(V_CON2, 0, p->sigma * sqrt(h));
+  double S0 = PERT(V_S, n + m, p->S0);
+  /* forward sweep, fine path (Algorithm 1) */
+  S[0] = S0;
+  for (int k = 0; k < n; ++k) {
+    Z[k] = PERT(V_Z, k, or_exact_normal(or_draw(seed, request, (uint32_t)level, 0u, s, (uint32_t)k)));
+    mul1[k] = PERT(V_MUL1, k, con2 * Z[k]);
+    sum1[k] = PERT(V_SUM1, k, con1 + mul1[k]);
+    mul2[k] = PERT(V_MUL2, k, S[k] * sum1[k]);
+    S[k + 1] = PERT(V_S, k, S[k] + mul2[k]);
+  }
+  /* coarse path: one step of 2h per pair of fine increments */
+  if (level > 0) {
+    Sc[0] = S0;
+    for (int k = 0; k < m; ++k) {
+      Zc[k] = Z[2 * k] + Z[2 * k + 1];
+      mul1c[k] = PERT(V_MUL1, n + k, con2 * Zc[k]);
+      sum1c[k] = PERT(V_SUM1, n + k, con1c + mul1c[k]);
+      mul2c[k] = PERT(V_MUL2, n + k, Sc[k] * sum1c[k]);
+      Sc[k + 1] = PERT(V_S, n + k, Sc[k] + mul2c[k]);
+    }
+  }
+#undef PERT
+  const double Pf = disc * (S[n] > p->K ? S[n] - p->K : 0.0);
+  const double Pc = level > 0 ? disc * (Sc[m] > p->K ? Sc[m] - p->K : 0.0) : 0.0;
+  if (maxabs) {
+    double v[7] = {0, 0, 0, 0, 0, 0, 0};
+    v[V_CON1] = fmax(fabs(con1), level > 0 ? fabs(con1c) : 0.0);
+    v[V_CON2] = fabs(con2);
+    v[V_S] = fabs(S0);
+    for (int k = 0; k < n; ++k) {
+      v[V_Z] = fmax(v[V_Z], fabs(Z[k]));
+      v[V_MUL1] = fmax(v[V_MUL1], fabs(mul1[k]));
+      v[V_SUM1] = fmax(v[V_SUM1], fabs(sum1[k]));
+      v[V_MUL2] = fmax(v[V_MUL2], fabs(mul2[k]));
+      v[V_S] = fmax(v[V_S], fabs(S[k + 1]));
+    }
+    for (int k = 0; k < m; ++k) {
+      v[V_MUL1] = fmax(v[V_MUL1], fabs(mul1c[k]));
+      v[V_SUM1] = fmax(v[V_SUM1], fabs(sum1c[k]));
+      v[V_MUL2] = fmax(v[V_MUL2], fabs(mul2c[k]));
+      v[V_S] = fmax(v[V_S], fabs(Sc[k + 1]));
+    }
+    for (int t = 0; t < 7; ++t) maxabs[t] = fmax(maxabs[t], v[t]);
+  }
+  if (xbar_out) {
+    double *xb[7];
+    for (int t = 0; t < 7; ++t) {
+      xb[t] = xbar_out + (size_t)t * n_inst;
+      for (int i = 0; i < n_inst; ++i) xb[t][i] = 0.0;
+    }
+    /* backward sweep, fine path: seed dDeltaP/dS_n = disc 1[S_n > K] */
+    double Sbar = S[n] > p->K ? disc : 0.0;
+    double con1bar = 0.0, con2bar = 0.0;
+    for (int k = n - 1; k >= 0; --k) {
+      xb[V_S][k] = Sbar;                       /* S_{k+1} = S_k + mul2_k     */
+      const double mul2bar = Sbar;
+      xb[V_MUL2][k] = mul2bar;                 /* mul2_k = S_k * sum1_k      */
+      const double sum1bar = mul2bar * S[k];
+      Sbar = Sbar + mul2bar * sum1[k];
+      xb[V_SUM1][k] = sum1bar;                 /* sum1_k = con1 + mul1_k     */
+      const double mul1bar = sum1bar;
+      con1bar += sum1bar;
+      xb[V_MUL1][k] = mul1bar;                 /* mul1_k = con2 * Z_k        */
+      con2bar += mul1bar * Z[k];
+      xb[V_Z][k] += mul1bar * con2;
+    }
+    double S0bar = Sbar;
+    xb[V_CON1][0] = con1bar;
+    if (level > 0) {
+      /* backward sweep, coarse path: seed -disc 1[S^c_m > K] */
+      double Scbar = Sc[m] > p->K ? -disc : 0.0;
+      double con1cbar = 0.0;
+      for (int k = m - 1; k >= 0; --k) {
+        xb[V_S][n + k] = Scbar;
+        const double mul2bar = Scbar;
+        xb[V_MUL2][n + k] = mul2bar;
+        const double sum1bar = mul2bar * Sc[k];
+        Scbar = Scbar + mul2bar * sum1c[k];
+        xb[V_SUM1][n + k] = sum1bar;
+        const double mul1bar = sum1bar;
+        con1cbar += sum1bar;
+        xb[V_MUL1][n + k] = mul1bar;
+        con2bar += mul1bar * Zc[k];
+        xb[V_Z][2 * k] += mul1bar * con2;      /* Zc_k = Z_2k + Z_2k+1        */
+        xb[V_Z][2 * k + 1] += mul1bar * con2;
+      }
+      S0bar += Scbar;
+      xb[V_CON1][1] = con1cbar;
+    }
+    xb[V_CON2][0] = con2bar;
+    xb[V_S][n + m] = S0bar;
+  }
+  return Pf - Pc;
+}
+
+/* Number of instances per type at a level (the stride of per-instance arrays). */
+int or_sens_instances(int level) { return (1 << level) + (level > 0 ? (1 << level) / 2 : 0) + 1; }
+
+/* Statistics over samples [first, first + N): per-type sums of xbar^2, maxima,
+ * sums of DeltaP and DeltaP^2, and (if inst != 0) per-instance sums of xbar^2
+ * (7 x or_sens_instances(level), type-major).  European call, Euler only. */
+int or_sensitivities(const or_params *p, int level, uint64_t first, uint64_t N, uint64_t seed, uint32_t request,
+                     or_sens *out, double *inst) {
+  if (level < 0 || level > 12 || p->payoff != OR_EURO || p->scheme != OR_EULER) return OR_EINVAL;
+  const int n = 1 << level, m = level > 0 ? n / 2 : 0;
+  const int ni = or_sens_instances(level);
+  static double tape[5 * 4096 + 1 + 5 * 2048 + 1];
+  static double xbar[7 * (4096 + 2048 + 1)];
+  memset(out, 0, sizeof *out);
+  if (inst) for (int i = 0; i < 7 * ni; ++i) inst[i] = 0.0;
+  neumaier A[7], sdp = {0, 0}, sdp2 = {0, 0};
+  memset(A, 0, sizeof A);
+  (void)m;
+  for (uint64_t s = first; s < first + N; ++s) {
+    const double dp = sens_sample(p, level, seed, request, s, -1, -1, 0.0, tape, xbar, ni, out->maxabs);
+    nm_add(&sdp, dp);
+    nm_add(&sdp2, dp * dp);
+    for (int t = 0; t < 7; ++t) {
+      double a = 0.0;
+      for (int i = 0; i < ni; ++i) {
+        const double x = xbar[(size_t)t * ni + i];
+        a += x * x;
+        if (inst) inst[(size_t)t * ni + i] += x * x;
+      }
+      nm_add(&A[t], a);
+    }
+  }
+  for (int t = 0; t < 7; ++t) out->A[t] = A[t].s + A[t].c;
+  out->sum_dp = sdp.s + sdp.c;
+  out->sum_dp2 = sdp2.s + sdp2.c;
+  out->n = N;
+  return OR_OK;
+}
+
+/* DeltaP of one sample with delta added to one instance, and the adjoint
+ * sensitivities of all instances of the unperturbed sample (xbar: 7 x n_inst). */
+double or_sens_probe(const or_params *p, int level, uint64_t seed, uint32_t request, uint64_t s, int type,
+                     int inst, double delta, double *xbar) {
+  static double tape[5 * 4096 + 1 + 5 * 2048 + 1];
+  if (xbar) sens_sample(p, level, seed, request, s, -1, -1, 0.0, tape, xbar, or_sens_instances(level), 0);
+  return sens_sample(p, level, seed, request, s, type, inst, delta, tape, 0, 0, 0);
+}
