@@ -334,6 +334,71 @@ mlmc_status mlmc_batch_estimate(const mlmc_params *params, const double *eps, in
                                 int max_level, int iters_per_launch, double *price, double *stderr_out, int *L,
                                 int *launches, void *stream);
 
+/* ---- error model and bit-width optimisation (Sec. 4-6) ----------------------
+ * mlmc_sensitivities: statistics of the level difference DeltaP_l = P_f - P_c
+ * (discounted European call, Euler-Maruyama, exact FP64 Normals from the
+ * correction estimator's uniforms, stream 0) for samples [first_sample,
+ * first_sample + N), with every intermediate variable of Algorithm 1 -- con1
+ * (and the coarse constant r 2h), con2, Z_j, mul1_k, sum1_k, mul2_k, S_k on the
+ * fine and coarse path, and S0 -- as an instance whose sensitivity
+ * xbar = d DeltaP / d x is computed by adjoint (algorithmic) differentiation:
+ *   A[t]      = E[sum over the instances of type t of xbar^2]  (V_indep, eq. optimistic)
+ *   B[t]      = sum over the instances of sqrt(E[xbar^2])      (V_corr, eq. pessimistic)
+ *   maxabs[t] = max |x| over instances and samples            (exponents, Sec. 4.1)
+ *   mean, var = of DeltaP_l;  n_instances = 2^l + 2^(l-1) + 1 (l >= 1; 2 on level 0).
+ * Type order t: Z, con1, con2, mul1, sum1, mul2, S (the mlmc_format order).
+ * inst (host, 7 x n_instances doubles, type-major, or NULL) receives E[xbar^2]
+ * per instance: mul1 / sum1 / mul2: fine step k at k, coarse step k at
+ * 2^l + k; S: S_{k+1} fine at k, coarse at 2^l + k, S0 last; Z: Z_j at j;
+ * con1: fine 0, coarse 1; con2: 0.  level 0..10, European payoff and Euler
+ * scheme only (MLMC_EINVAL otherwise).  Synchronous; allocates scratch. */
+typedef struct {
+  double A[7];
+  double B[7];
+  double maxabs[7];
+  double mean, var;
+  uint64_t n;
+  int32_t n_instances;
+  int32_t reserved;
+} mlmc_sensitivity;
+mlmc_status mlmc_sensitivities(int level, uint64_t N, const mlmc_params *p, uint64_t seed,
+                               uint64_t first_sample, mlmc_sensitivity *out, double *inst);
+
+/* mlmc_optimise_level: optimal bit-widths of one level (host only, no GPU).
+ * Minimises the level cost sqrt(V C~(d)) + sqrt(V_indep(d) C) (eq.
+ * level_cost2) with V = s->var, C = 2^l c_rng, C~(d) = steps (1/2 sum M_t
+ * d_t^2 + sum M'_t d_t) (eq. cost_sq, steps = fine + coarse steps): for a
+ * Lagrange multiplier lambda every d_t solves (ln 4 / 12) A_t 4^(e_t - d_t) =
+ * lambda steps (M_t d_t + M'_t) (eq. Lagr), and a golden-section search over
+ * log(lambda) finds the optimum (Sec. 6.1); the real widths are then rounded
+ * down and bits added greedily by variance decrease per unit cost until
+ * V_indep is back at or below the real solution's (Sec. 6.2).  e_t is the
+ * smallest integer with maxabs_t < 2^e_t.  With cfg->lut_mse (MSE of the
+ * approximate Normal for table bits d, indexed by d) the smallest d_lut in
+ * [2, lut_max_bits] with A_Z MSE(d_lut) <= V_indep is chosen (Sec. 4.3). */
+typedef struct {
+  double c_rng;              /* cost of one full-precision path-step; <= 0: 1e4 (Sec. 6.1) */
+  double mul[7], add[7];     /* M_t, M'_t per time step; all zero: Algorithm 1's counts */
+  const double *lut_mse;     /* host array indexed by table bits, or NULL */
+  int32_t lut_max_bits;      /* 0: 16 */
+  int32_t reserved;
+} mlmc_opt_config;
+typedef struct {
+  int32_t e[7];              /* exponents */
+  int32_t d[7];              /* integer bit-widths */
+  double d_real[7];          /* real solution */
+  double lambda;
+  double v_indep, v_indep_real, v_corr;
+  double cost_lp, cost_exact;
+  double level_cost_ratio;   /* sqrt(C~/C) + sqrt(V_indep/V) (the paper's Fig. 5 quantity) */
+  double mse_term;           /* A_Z MSE(lut_bits) */
+  int32_t lut_bits;          /* 0: not chosen */
+  int32_t reserved;
+  mlmc_format format;        /* e and f = max(0, d - e), ready for mlmc_params.formats */
+} mlmc_opt_result;
+mlmc_status mlmc_optimise_level(int level, const mlmc_sensitivity *s, const mlmc_opt_config *cfg,
+                                mlmc_opt_result *out);
+
 /* Cost per fine path-step of each estimator kind used by mlmc_estimate
  * (relative units; defaults: exact FP32 1.0, exact FP64 8.0, approximate 0.5,
  * correction 1.5).  kind: 0 exact FP64, 1 exact FP32, 2 approximate, 3 correction.

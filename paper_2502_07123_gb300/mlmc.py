@@ -62,6 +62,26 @@ class EngineConfig(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class Sensitivity(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_double * 7), ("B", ctypes.c_double * 7), ("maxabs", ctypes.c_double * 7),
+                ("mean", ctypes.c_double), ("var", ctypes.c_double), ("n", ctypes.c_uint64),
+                ("n_instances", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class OptConfig(ctypes.Structure):
+    _fields_ = [("c_rng", ctypes.c_double), ("mul", ctypes.c_double * 7), ("add", ctypes.c_double * 7),
+                ("lut_mse", ctypes.POINTER(ctypes.c_double)), ("lut_max_bits", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class OptResult(ctypes.Structure):
+    _fields_ = [("e", ctypes.c_int32 * 7), ("d", ctypes.c_int32 * 7), ("d_real", ctypes.c_double * 7),
+                ("lambda_", ctypes.c_double), ("v_indep", ctypes.c_double), ("v_indep_real", ctypes.c_double),
+                ("v_corr", ctypes.c_double), ("cost_lp", ctypes.c_double), ("cost_exact", ctypes.c_double),
+                ("level_cost_ratio", ctypes.c_double), ("mse_term", ctypes.c_double),
+                ("lut_bits", ctypes.c_int32), ("reserved", ctypes.c_int32), ("format", Format)]
+
+
 class Work(ctypes.Structure):
     _fields_ = [("params", ctypes.POINTER(Params)), ("level", ctypes.c_int32), ("variant", ctypes.c_int32),
                 ("first_sample", ctypes.c_uint64), ("N", ctypes.c_uint64),
@@ -122,6 +142,9 @@ def load():
                                      P(ctypes.c_int), P(ctypes.c_int), ctypes.c_void_p]),
         "mlmc_autotune": (st, [P(Work), ctypes.c_int, ctypes.c_uint64, ctypes.c_int, P(Tuning)]),
         "mlmc_tuning_reset": (None, []),
+        "mlmc_sensitivities": (st, [ctypes.c_int, ctypes.c_uint64, P(Params), ctypes.c_uint64, ctypes.c_uint64,
+                                    P(Sensitivity), ctypes.c_void_p]),
+        "mlmc_optimise_level": (st, [ctypes.c_int, P(Sensitivity), P(OptConfig), P(OptResult)]),
         "mlmc_default_format": (st, [P(Params), ctypes.c_int, P(Format)]),
         "mlmc_icdf_table": (st, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_double)]),
         "mlmc_philox": (st, [P(ctypes.c_uint32), ctypes.c_uint64, ctypes.c_uint64, P(ctypes.c_uint32)]),
@@ -293,6 +316,51 @@ def mlmc_run(items, seed, tuning=None, stream=None):
     out = (Sums * len(items))()
     _check(L.mlmc_run(arr, len(items), seed, _tuning(tuning), out, _stream_handle(stream)), "mlmc_run")
     return [_sums_dict(out[i]) for i in range(len(items))]
+
+
+def mlmc_sensitivities(level, N, params, seed, first_sample=0, per_instance=False):
+    """Error-model statistics of DeltaP_l (mlmc_sensitivities): per-type A, B, maxima,
+    mean and variance; with per_instance the 7 x n_instances array of E[xbar^2]."""
+    L = load()
+    out = Sensitivity()
+    ni = (1 << level) + ((1 << level) // 2 if level > 0 else 0) + 1
+    inst = np.zeros((7, ni), dtype=np.float64) if per_instance else None
+    _check(L.mlmc_sensitivities(level, N, ctypes.byref(params), seed, first_sample, ctypes.byref(out),
+                                inst.ctypes.data if per_instance else None), "mlmc_sensitivities")
+    d = dict(A=list(out.A), B=list(out.B), maxabs=list(out.maxabs), mean=out.mean, var=out.var, n=out.n,
+             n_instances=out.n_instances, struct=out)
+    if per_instance:
+        d["inst"] = inst
+    return d
+
+
+def mlmc_optimise_level(level, sens, c_rng=0.0, lut_mse=None, lut_max_bits=0, mul=None, add=None):
+    """Optimal bit-widths of one level (mlmc_optimise_level, host only).  sens: a dict
+    with A, B, maxabs, var (for example from mlmc_sensitivities); lut_mse: sequence
+    indexed by table bits (MSE of the approximate Normal) or None."""
+    L = load()
+    S = Sensitivity()
+    for t in range(7):
+        S.A[t], S.B[t], S.maxabs[t] = sens["A"][t], sens["B"][t], sens["maxabs"][t]
+    S.var = sens["var"]
+    S.mean = sens.get("mean", 0.0)
+    cfg = OptConfig()
+    cfg.c_rng = c_rng
+    if mul is not None:
+        for t in range(7):
+            cfg.mul[t], cfg.add[t] = mul[t], add[t]
+    keep = None
+    if lut_mse is not None:
+        keep = (ctypes.c_double * len(lut_mse))(*[float(x) for x in lut_mse])
+        cfg.lut_mse = keep
+    cfg.lut_max_bits = lut_max_bits
+    out = OptResult()
+    _check(L.mlmc_optimise_level(level, ctypes.byref(S), ctypes.byref(cfg), ctypes.byref(out)),
+           "mlmc_optimise_level")
+    return dict(e=list(out.e), d=list(out.d), d_real=list(out.d_real), **{"lambda": out.lambda_},
+                v_indep=out.v_indep, v_indep_real=out.v_indep_real, v_corr=out.v_corr, cost_lp=out.cost_lp,
+                cost_exact=out.cost_exact, level_cost_ratio=out.level_cost_ratio, mse_term=out.mse_term,
+                lut_bits=out.lut_bits, format={"e": list(out.format.e), "f": list(out.format.f)})
 
 
 def mlmc_autotune(items, seed, reps=5):
