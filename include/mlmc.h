@@ -229,10 +229,12 @@ mlmc_status mlmc_run(const mlmc_work *work, int n_work, uint64_t seed,
 /* ---- launch-shape autotuner ----------------------------------------------
  * The level kernels' launch shape (CTA threads; fine path-steps, hence paths,
  * per thread) is chosen per kernel class: (kernel family, scheme, payoff class,
- * level class {0}, {1}, {2..4}, {5..7}, {>= 8}).  mlmc_autotune times the work
- * items of each class present in `work` on this GPU with every distinct
- * chunking from threads {128, 96, 64} x steps_per_thread {256, 64, 128, 512,
- * 1024, 2048} (median of `reps` launches by CUDA events, after one untimed
+ * level class {0}, {1}, {2..4}, {5..7}, {>= 8}).  mlmc_autotune runs one
+ * pass of coordinate descent over the classes present in `work` (largest
+ * model work first): each class in turn tries every distinct chunking from
+ * threads {128, 96, 64} x steps_per_thread {256, 64, 128, 512, 1024, 2048}
+ * while the other classes keep their shapes, timing the whole work list as
+ * one plan (median of `reps` launches by CUDA events, after one untimed
  * launch; a candidate must beat the best so far by 2%), and installs the
  * fastest in the process-wide table that every later call without an
  * mlmc_tuning uses (plans, mlmc_run, mlmc_level, mlmc_level_noalloc,

@@ -944,15 +944,11 @@ void plan_release(mlmc_plan *pl) {
   delete pl;
 }
 
-// Median device time (ms) of `reps` launches of a plan of `work` with one
-// launch shape, after one untimed launch.
-mlmc_status time_shape(const std::vector<mlmc_work> &work, uint64_t seed, int threads, int spt, int reps,
-                       double *ms) {
-  mlmc_tuning t;
-  t.threads = threads;
-  t.steps_per_thread = spt;
+// Median device time (ms) of `reps` launches of a plan of `work` (launch
+// shapes from the tuning table), after one untimed launch.
+mlmc_status time_plan(const mlmc_work *work, int n_work, uint64_t seed, int reps, double *ms) {
   mlmc_plan *pl = nullptr;
-  mlmc_status s = plan_create_impl(&pl, work.data(), (int)work.size(), seed, &t, nullptr);
+  mlmc_status s = plan_create_impl(&pl, work, n_work, seed, nullptr, nullptr);
   if (s != MLMC_OK) return s;
   std::vector<float> v;
   for (int r = 0; r <= reps && s == MLMC_OK; ++r) {
@@ -1054,48 +1050,60 @@ mlmc_status mlmc_autotune(const mlmc_work *work, int n_work, uint64_t seed, int 
   if (!work || n_work <= 0 || reps < 1 || reps > 1000) return MLMC_EINVAL;
   mlmc_status s = ensure_ctx();
   if (s != MLMC_OK) return s;
-  // kernel classes among the items
-  std::map<std::tuple<int, int, int, int>, std::vector<int>> cls;
+  // kernel classes among the items, with their model work
+  typedef std::tuple<int, int, int, int> Key;
+  std::map<Key, std::vector<int>> cls;
+  std::map<Key, double> work_of;
   std::vector<BuiltItem> built(n_work);
   for (int i = 0; i < n_work; ++i) {
     double disc;
     int unit, ei;
     if ((s = build_item(work[i], i, nullptr, built[i], disc, unit, ei)) != MLMC_OK) return s;
-    cls[std::make_tuple(built[i].family, built[i].scheme, built[i].pc, level_class(work[i].level))].push_back(i);
+    const Key k = std::make_tuple(built[i].family, built[i].scheme, built[i].pc, level_class(work[i].level));
+    cls[k].push_back(i);
+    work_of[k] += std::ldexp((double)work[i].N, work[i].level) * built[i].cost_step;
   }
+  std::vector<Key> order;
+  for (auto &kv : cls) order.push_back(kv.first);
+  std::stable_sort(order.begin(), order.end(), [&](const Key &a, const Key &b) { return work_of[a] > work_of[b]; });
   static const int cand_threads[] = {128, 96, 64};
   static const int cand_spt[] = {256, 64, 128, 512, 1024, 2048};
-  for (auto &kv : cls) {
-    std::vector<mlmc_work> sub;
-    for (int i : kv.second) sub.push_back(work[i]);
-    int best_t = TUNE_THREADS, best_s = TUNE_SPT;
+  // one pass of coordinate descent: each class in turn takes the shape that
+  // makes the whole work list fastest, the other classes keeping theirs
+  for (const Key &k : order) {
+    const std::vector<int> &ix = cls[k];
+    int cur_t, cur_s;
+    tuning_for(std::get<0>(k), std::get<1>(k), std::get<2>(k), work[ix[0]].level, &cur_t, &cur_s);
+    int best_t = cur_t, best_s = cur_s;
     double best_ms = 0.0;
-    bool have = false;
+    if ((s = time_plan(work, n_work, seed, reps, &best_ms)) != MLMC_OK) return s;
     std::vector<std::vector<uint32_t>> seen;   // chunkings already timed
-    for (int th : cand_threads)
-      for (int sp : cand_spt) {
-        std::vector<uint32_t> sig{(uint32_t)th};
-        for (int i : kv.second) {
-          BuiltItem b = built[i];
-          if ((s = chunk_built(b, th, sp)) != MLMC_OK) return s;
-          sig.push_back(b.it.groups_per_thread);
+    for (int pass = 0; pass < 2; ++pass)
+      for (int th : cand_threads)
+        for (int sp : cand_spt) {
+          if (pass == 0 && !(th == cur_t && sp == cur_s)) continue;   // the current shape first
+          std::vector<uint32_t> sig{(uint32_t)th};
+          for (int i : ix) {
+            BuiltItem b = built[i];
+            if ((s = chunk_built(b, th, sp)) != MLMC_OK) return s;
+            sig.push_back(b.it.groups_per_thread);
+          }
+          if (std::find(seen.begin(), seen.end(), sig) != seen.end()) continue;
+          seen.push_back(sig);
+          if (pass == 0) continue;
+          g_tune[k] = std::make_pair(th, sp);
+          double ms = 0.0;
+          if ((s = time_plan(work, n_work, seed, reps, &ms)) != MLMC_OK) return s;
+          // a candidate must make the work list 2% faster than the best so far
+          if (ms < 0.98 * best_ms) {
+            best_ms = ms;
+            best_t = th;
+            best_s = sp;
+          }
         }
-        if (std::find(seen.begin(), seen.end(), sig) != seen.end()) continue;
-        seen.push_back(sig);
-        double ms = 0.0;
-        if ((s = time_shape(sub, seed, th, sp, reps, &ms)) != MLMC_OK) return s;
-        // the first candidate is the default shape; another must be 2% faster to replace it
-        if (!have || ms < 0.98 * best_ms) {
-          best_ms = ms;
-          best_t = th;
-          best_s = sp;
-          have = true;
-        }
-      }
-    const auto &k = kv.first;
     g_tune[k] = std::make_pair(best_t, best_s);
     if (chosen)
-      for (int i : kv.second) {
+      for (int i : ix) {
         chosen[i].threads = best_t;
         chosen[i].steps_per_thread = best_s;
       }

@@ -478,6 +478,17 @@ def mlmc_icdf_table(method, d, rep, fZ=0):
     return np.frombuffer(out, dtype=np.float64).copy()
 
 
+def icdf_mse(d, method=1):
+    """Mean square error E[(Z - Z~)^2] of the approximate Normal with d table bits,
+    from the library's FP64 table: Z~ is the conditional mean of Z on each cell
+    (method 1), so E[(Z - Z~)^2] = 1 - E[Z~^2] = 1 - 2^(1-d) sum_k Z_k^2; for
+    method 3 the cross term does not vanish and this returns None."""
+    if method != 1:
+        return None
+    z = mlmc_icdf_table(1, d, 0)
+    return 1.0 - float(np.sum(z * z)) * 2.0 ** (1 - d)
+
+
 def mlmc_philox(ctr, seed):
     ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
     out = np.empty_like(ctr)

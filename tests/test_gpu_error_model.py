@@ -77,3 +77,8 @@ def test_optimised_widths_bound_the_gpu_corrections(m):
         assert 0.1 * v_indep_ext <= var <= 10.0 * v_indep_ext, (lev, var, v_indep_ext)
     slope = (slope_d[6] - slope_d[2]) / 4.0
     assert 0.6 <= slope <= 1.4
+
+
+def test_table_mse_matches_oracle(m):
+    for d in (4, 8, 10, 12, 14):
+        assert m.icdf_mse(d) == pytest.approx(MSE[d], rel=1e-9)
