@@ -102,7 +102,7 @@ def lib():
         L.or_level.argtypes = [ctypes.POINTER(Params), ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
                                ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(Format), ctypes.c_int,
-                               ctypes.c_int, ctypes.POINTER(Sums), ctypes.c_void_p]
+                               ctypes.c_int, ctypes.POINTER(Sums), ctypes.c_void_p, ctypes.c_void_p]
         L.or_level.restype = ctypes.c_int
         L.or_sens_instances.argtypes = [ctypes.c_int]
         L.or_sens_instances.restype = ctypes.c_int
@@ -202,11 +202,15 @@ def level(p, lev, first, N, variant, seed, request=0, stream=None, d=10, method=
         F = make_format(fmt)
     S = Sums()
     out = np.zeros(N, dtype=SAMPLE_DTYPE) if dump else None
+    perm = None
+    if method == 2 and variant in (CORR_FIXED, CORR_FP16, CORR_BF16):
+        perm = np.ascontiguousarray(tables.m2_optimise(d)["pi"], dtype=np.uint32)
     st = lib().or_level(ctypes.byref(P), int(lev), int(first), int(N), int(variant), int(seed),
                         int(request), int(stream), int(d),
                         ztab.ctypes.data if ztab is not None else None,
                         ctypes.byref(F) if F is not None else None, int(pack), int(enumerate),
-                        ctypes.byref(S), out.ctypes.data if dump else None)
+                        ctypes.byref(S), out.ctypes.data if dump else None,
+                        perm.ctypes.data if perm is not None else None)
     if st != 0:
         raise OracleError("or_level returned %d" % st)
     sums = {k: getattr(S, k) for k, _ in Sums._fields_}

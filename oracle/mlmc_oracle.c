@@ -295,7 +295,22 @@ typedef struct {
   double hc1, hc1c, hc2, hc3, hS0;
   float K32;
   int unit;
+  const uint32_t *perm;      /* Method 2: interval rank pi(j) of every d-bit j, or 0 */
 } level_cfg;
+
+/* J of the exact path at fine step i of sample s.  With Method 2 (Sec. 3.2) the
+ * correction estimator's exact path takes the uniform in the interval pi(j) the
+ * approximate value is ranked at, keeping J's low 32 - d bits:
+ * U = 2^-d pi(j) + 2^-32 ((J mod 2^(32-d)) + 1/2). */
+static uint32_t exact_J(const level_cfg *c, uint64_t s, int i) {
+  uint32_t J = or_draw(c->seed, c->request, (uint32_t)c->level, c->stream, s, (uint32_t)i);
+  if (c->perm) {
+    const int sh = 32 - c->d;
+    const uint32_t low = sh >= 32 ? J : (J & ((1u << sh) - 1u));
+    J = (c->perm[J >> sh] << sh) | low;
+  }
+  return J;
+}
 
 static int has_exact(int v) { return v == OR_FP64_EXACT || v == OR_FP32_EXACT || v >= OR_CORR_FIXED; }
 static int has_approx(int v) { return v != OR_FP64_EXACT && v != OR_FP32_EXACT; }
@@ -316,7 +331,7 @@ static void exact_sample(const level_cfg *c, uint64_t s, or_sample *out) {
   double Sc = p->S0, Sc_frozen = p->S0;
   double Zprev = 0.0;
   for (int i = 0; i < c->n; ++i) {
-    double Z = or_exact_normal(or_draw(c->seed, c->request, c->level, c->stream, s, i));
+    double Z = or_exact_normal(exact_J(c, s, i));
     /* fine: S_{i+1} = S_i + a(S_i) h + b(S_i) sqrt(h) Z_i, a = r S, b = sigma S */
     double Snew = S + p->r * S * h + p->sigma * S * sqh * Z;
     if (p->scheme == OR_MILSTEIN)  /* + 1/2 b b' h (Z^2 - 1), b b' = sigma^2 S */
@@ -540,7 +555,7 @@ static int validate_format(const or_format *F, int milstein) {
 int or_level(const or_params *p, int level, uint64_t first, uint64_t N, int variant,
              uint64_t seed, uint32_t request, uint32_t stream,
              int d, const double *ztab, const or_format *fmt, int pack, int enumerate,
-             or_sums *sums, or_sample *dump) {
+             or_sums *sums, or_sample *dump, const uint32_t *perm) {
   if (level < 0 || level > 20 || variant < 0 || variant > 7) return OR_EINVAL;
   if (enumerate && (has_exact(variant) || level > 1 || (d << level) > 24)) return OR_EINVAL;
   /* packed draws only feed approximate-only estimators (their uniforms need d bits, not 32) */
@@ -551,6 +566,7 @@ int or_level(const or_params *p, int level, uint64_t first, uint64_t N, int vari
   c.p = p; c.level = level; c.n = 1 << level; c.variant = variant; c.d = d; c.pack = pack;
   c.enumerate = enumerate;
   c.seed = seed; c.request = request; c.stream = stream;
+  c.perm = variant >= OR_CORR_FIXED ? perm : 0;   /* the correction's exact path */
   c.h = ldexp(p->T, -level);
   c.ztab = ztab;
   int approx = has_approx(variant), exact = has_exact(variant);

@@ -13,6 +13,17 @@ mean over each uniform interval [k 2^-d, (k+1) 2^-d], k < 2^(d-1):
 (the second line is the antiderivative of z phi(z) after u = Phi(z)).  It is
 evaluated here in mpmath at 40 significant digits and rounded once.
 
+Method 2 (Sec. 3.2): the d-bit index j is split into n fields of b = d/n bits
+(the first field is the top bits); each field gives X = +-x_k from a small
+table of 2^(b-1) values with the Method-1 sign rule, and the approximate
+Normal is the sum of the n values.  The small table starts as the b-bit
+Method-1 table divided by sqrt(n); then, repeatedly, the 2^d sums are sorted
+ascending (ties by j), which defines the permutation pi (pi(j) = rank of
+Z~_j), and the small table is refitted by least squares to the d-bit
+Method-1 values of the intervals the sums are ranked at, Z_{pi(j)}, until pi
+no longer changes.  The exact path uses the uniform in interval pi(j) with
+J's low bits: U = 2^-d pi(j) + 2^-32 ((J mod 2^(32-d)) + 1/2).
+
 Method 3 (Sec. 3.3): Z_k is replaced by a + b k on each dyadic index class.
 Reading of the classes: {0, 1}, {2, 3}, {4..7}, ..., {2^(d-2) .. 2^(d-1)-1},
 i.e. d-1 classes (the table size stated in Sec. 3.3), with index 0 merged into
@@ -114,6 +125,129 @@ def _round_bf16(x: np.ndarray) -> np.ndarray:
     return core.round_bf16(np.asarray(x, dtype=np.float64))
 
 
+def m1_full(d: int) -> np.ndarray:
+    """The d-bit Method-1 values of every interval j < 2^d in ascending order
+    (lower half Z_j, upper half -Z_{2^d - 1 - j})."""
+    half = m1_fp64(d)
+    return np.concatenate([half, -half[::-1]])
+
+
+def _m2_fields(d: int, n: int):
+    """Per field i: (index into the small table, sign) for every j < 2^d."""
+    b = d // n
+    full, half = 1 << b, 1 << (b - 1)
+    j = np.arange(1 << d)
+    out = []
+    for i in range(n):
+        f = (j >> (b * (n - 1 - i))) & (full - 1)
+        low = f < half
+        out.append((np.where(low, f, full - 1 - f), np.where(low, 1.0, -1.0)))
+    return out
+
+
+def m2_design(d: int, n: int) -> np.ndarray:
+    """Matrix A (2^d x 2^(b-1)) with Z~ = A x: field value f < 2^(b-1) adds +x_f,
+    otherwise -x_{2^b - 1 - f} (the Method-1 sign rule per field)."""
+    b = d // n
+    A = np.zeros((1 << d, 1 << (b - 1)))
+    rows = np.arange(1 << d)
+    for idx, sgn in _m2_fields(d, n):
+        np.add.at(A, (rows, idx), sgn)
+    return A
+
+
+def m2_sums(x: np.ndarray, d: int, n: int) -> np.ndarray:
+    """Z~_j = X^(1) + ... + X^(n) in FP64, added in field order."""
+    acc = None
+    for idx, sgn in _m2_fields(d, n):
+        v = sgn * x[idx]
+        acc = v if acc is None else acc + v
+    return acc
+
+
+def m2_rank(values: np.ndarray) -> np.ndarray:
+    """pi(j) = position of values[j] in the ascending order (ties by j)."""
+    order = np.argsort(values, kind="stable")
+    pi = np.empty(len(values), dtype=np.int64)
+    pi[order] = np.arange(len(values))
+    return pi
+
+
+def m2_mse(values: np.ndarray, pi: np.ndarray, d: int) -> float:
+    """E[(Phi^{-1}(U) - Z~)^2] with U in interval pi(j): the Method-1 MSE plus
+    2^-d sum_j (Z_{pi(j)} - Z~_j)^2 (the decomposition of eq. mse_dyadic)."""
+    _, mse1 = moments_m1(d)
+    return float(mse1) + float(np.sum((m1_full(d)[pi] - values) ** 2)) / (1 << d)
+
+
+@functools.lru_cache(maxsize=None)
+def m2_optimise(d: int, n: int = 2, max_iter: int = 1000):
+    """Method 2 small table after the iterative least-squares stage; returns
+    dict(x, values, pi, iterations, x0, mse0, mse).  The iteration stops when the
+    permutation no longer changes (or after max_iter least-squares solves)."""
+    if d % n or d // n < 2:
+        raise ValueError("n must divide d with at least 2 bits per field")
+    b = d // n
+    A = m2_design(d, n)
+    T = m1_full(d)
+    x0 = m1_fp64(b) / np.sqrt(n)
+    v0 = m2_sums(x0, d, n)
+    pi0 = m2_rank(v0)
+    x, pi, it = x0, pi0, 0
+    while it < max_iter:
+        x = np.linalg.lstsq(A, T[pi], rcond=None)[0]
+        it += 1
+        v = m2_sums(x, d, n)
+        new = m2_rank(v)
+        if np.array_equal(new, pi):
+            break
+        pi = new
+    v = m2_sums(x, d, n)
+    return {"x": x, "values": v, "pi": pi, "iterations": it, "x0": x0, "mse0": m2_mse(v0, pi0, d),
+            "mse": m2_mse(v, pi, d)}
+
+
+def m2_table(d: int, rep: str, fZ: int = 0, n: int = 2) -> np.ndarray:
+    """Method-2 values of every j < 2^d in a representation: each small-table value
+    rounded once (fixed: to fZ bits; fp16 / bf16; fp32), then the fields added in
+    order, exactly in fixed point and with one rounding per addition otherwise."""
+    import math
+    res = m2_optimise(d, n)
+    x = res["x"]
+    b = d // n
+    full, half = 1 << b, 1 << (b - 1)
+    if rep == "fp64":
+        return res["values"]
+    if rep == "fixed":
+        xq = [round_fixed(v, fZ) for v in x]
+    elif rep == "fp16":
+        xq = list(_round_fp16(x))
+    elif rep == "bf16":
+        xq = list(_round_bf16(x))
+    elif rep == "fp32":
+        xq = [float(np.float32(v)) for v in x]
+    else:
+        raise ValueError(rep)
+    out = np.empty(1 << d)
+    for j in range(1 << d):
+        acc = None
+        for i in range(n):
+            f = (j >> (b * (n - 1 - i))) & (full - 1)
+            v = xq[f] if f < half else -xq[full - 1 - f]
+            if acc is None:
+                acc = v
+            elif rep == "fixed":
+                acc = acc + v
+            elif rep == "fp16":
+                acc = float(_round_fp16(np.array([acc + v]))[0])
+            elif rep == "bf16":
+                acc = float(_round_bf16(np.array([acc + v]))[0])
+            else:
+                acc = float(np.float32(acc + v))
+        out[j] = math.ldexp(acc, -fZ) if rep == "fixed" else acc
+    return out
+
+
 def table(d: int, method: int, rep: str, fZ: int = 0) -> np.ndarray:
     """Approximate-Normal value for every table index k < 2^(d-1), as float64.
 
@@ -135,8 +269,10 @@ def table(d: int, method: int, rep: str, fZ: int = 0) -> np.ndarray:
             import math
             return np.array([math.ldexp(round_fixed(v, fZ), -fZ) for v in z64])
         raise ValueError(rep)
+    if method == 2:
+        return m2_table(d, rep, fZ)[:half]
     if method != 3:
-        raise ValueError("method must be 1 or 3")
+        raise ValueError("method must be 1, 2 or 3")
     coef = m3_coefficients_fp64(d)
     if rep == "fixed":
         import math
