@@ -86,6 +86,11 @@ typedef struct {
   int32_t payoff;               /* mlmc_payoff                                   */
   int32_t scheme;               /* mlmc_scheme                                   */
   int32_t icdf_method;          /* 1: piecewise constant on uniform intervals (Sec. 3.1);
+                                   2: sum of two table variables of d/2 bits with the
+                                      least-squares / permutation optimisation (Sec. 3.2;
+                                      d even, >= 4); the correction estimators' exact
+                                      path then uses the uniform in interval pi(j),
+                                      U = 2^-d pi(j) + 2^-32 ((J mod 2^(32-d)) + 1/2);
                                    3: piecewise linear on dyadic intervals (Sec. 3.3) */
   int32_t icdf_bits;            /* d in [2, 14]: bits of J used by the table      */
   const mlmc_format *formats;   /* host array indexed by level, or NULL for the
@@ -184,7 +189,9 @@ mlmc_status mlmc_level_dump(int level, uint64_t N, const mlmc_params *p, mlmc_va
  * item, the tables and the result record) is one file-scope device array of
  * about 0.9 MiB that every GPU which loads the library keeps until exit.
  * Limits: at most 16384 CTAs (128 threads each) per call -- larger sample
- * counts return MLMC_EINVAL; icdf_bits <= 14.  All work is enqueued on `stream`
+ * counts return MLMC_EINVAL; icdf_bits <= 14; icdf_method 1 or 3 (Method 2's
+ * tables are built on the host and need allocation: MLMC_EINVAL).  All work
+ * is enqueued on `stream`
  * (a cudaStream_t, NULL = legacy default stream) and the call returns after
  * synchronising it; seconds = 0.  The first call on a device looks up the
  * array's device address, so make that first call before any stream capture.
@@ -423,6 +430,17 @@ mlmc_status mlmc_default_format(const mlmc_params *p, int level, mlmc_format *ou
  * rep: 0 fp64, 1 fp32, 2 fp16, 3 bf16, 4 fixed with fZ fractional bits.
  * method 3 values are the a + b k evaluations the kernels use. */
 mlmc_status mlmc_icdf_table(int method, int d, int rep, int fZ, double *out);
+/* Method 2 (Sec. 3.2): the optimised small table x (host array of 2^(d/2-1)
+ * doubles, or NULL), the interval rank pi(j) of every j < 2^d (host array of
+ * 2^d, or NULL) and the number of least-squares fits until pi stopped
+ * changing (at most 1000).  The small table starts as the (d/2)-bit Method-1
+ * table / sqrt(2); each fit solves the normal equations for
+ * sum_j (Z_{pi(j)} - Z~_j)^2 with Z_k the d-bit Method-1 values, then the 2^d
+ * sums are ranked again (ascending, ties by j).  Table values of method 2 in
+ * every representation: each x rounded once, the two fields added exactly
+ * (fixed point) or with one rounding.  MLMC_EINVAL for odd d or d outside
+ * [4, 14]. */
+mlmc_status mlmc_icdf_method2(int d, double *x, uint32_t *perm, int *iterations);
 
 /* Philox4x32-10 words computed on the GPU for n counters (for parity testing):
  * ctr is a host array of 4n words, out a host array of 4n words. */

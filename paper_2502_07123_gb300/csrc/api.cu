@@ -94,6 +94,7 @@ struct Ctx {
   std::map<int, std::vector<double>> m1_host;               // d -> Method-1 table (FP64)
   std::map<int, double *> m1_dev;                           // d -> device FP64 table
   std::map<std::tuple<int, int, int, int, int>, void *> tables;  // (method, d, rep, fZ, signed) -> table
+  std::map<int, uint16_t *> m2_perm;                         // d -> device interval ranks (Method 2)
 };
 Ctx g;
 
@@ -187,9 +188,166 @@ void m3_fit(const std::vector<double> &Z, int d, M3Coef &c) {
 // Device table of one representation.  full_signed (method 1 only): all 2^d
 // entries indexed directly by j, as the level kernels use it; otherwise the
 // 2^(d-1) entries of the lower half (parity checks).
+uint16_t half_bits(double x) { return __half_as_ushort(__double2half(x)); }
+uint16_t bf16_bits(double x) { return __bfloat16_as_ushort(__double2bfloat16(x)); }
+
+// Method 2 (Sec. 3.2) with two fields: the d-bit index j splits into a high
+// and a low field of b = d/2 bits; each gives +-x_k from a small table of
+// 2^(b-1) values (Method-1 sign rule per field) and Z~_j is their sum.  The
+// small table starts as the b-bit Method-1 table / sqrt(2); then the 2^d sums
+// are ranked ascending (ties by j), pi(j) = rank, and x is refitted by least
+// squares (normal equations, Cholesky in long double) to the d-bit Method-1
+// values Z_{pi(j)}, until pi stops changing (at most 1000 fits).
+struct M2Table {
+  std::vector<double> x;         // small table
+  std::vector<double> values;    // Z~_j, j < 2^d, FP64 sums in field order
+  std::vector<uint32_t> pi;      // interval rank of every j
+  int iterations = 0;
+};
+std::map<int, M2Table> g_m2;
+
+struct M2Field { int idx; double sgn; };
+inline void m2_fields(int j, int b, M2Field &hi, M2Field &lo) {
+  const int full = 1 << b, half = 1 << (b - 1);
+  const int f1 = j >> b, f2 = j & (full - 1);
+  hi = f1 < half ? M2Field{f1, 1.0} : M2Field{full - 1 - f1, -1.0};
+  lo = f2 < half ? M2Field{f2, 1.0} : M2Field{full - 1 - f2, -1.0};
+}
+
+bool chol_solve(std::vector<long double> M, std::vector<long double> r, int k, std::vector<double> &y) {
+  for (int c = 0; c < k; ++c) {
+    long double dg = M[c * k + c];
+    for (int q = 0; q < c; ++q) dg -= M[c * k + q] * M[c * k + q];
+    if (!(dg > 0.0L)) return false;
+    dg = std::sqrt(dg);
+    M[c * k + c] = dg;
+    for (int rr = c + 1; rr < k; ++rr) {
+      long double v = M[rr * k + c];
+      for (int q = 0; q < c; ++q) v -= M[rr * k + q] * M[c * k + q];
+      M[rr * k + c] = v / dg;
+    }
+  }
+  for (int c = 0; c < k; ++c) {          // L z = r
+    long double v = r[c];
+    for (int q = 0; q < c; ++q) v -= M[c * k + q] * r[q];
+    r[c] = v / M[c * k + c];
+  }
+  for (int c = k - 1; c >= 0; --c) {     // L^T y = z
+    long double v = r[c];
+    for (int q = c + 1; q < k; ++q) v -= M[q * k + c] * r[q];
+    r[c] = v / M[c * k + c];
+  }
+  y.resize(k);
+  for (int c = 0; c < k; ++c) y[c] = (double)r[c];
+  return true;
+}
+
+mlmc_status m2_build(int d, const M2Table **out) {
+  auto it = g_m2.find(d);
+  if (it != g_m2.end()) { *out = &it->second; return MLMC_OK; }
+  if (d % 2 || d < 4) return MLMC_EINVAL;
+  const int b = d / 2, k = 1 << (b - 1), N = 1 << d;
+  double *dv;
+  const std::vector<double> *zb = nullptr, *zd = nullptr;
+  mlmc_status s;
+  if ((s = m1_table(b, &dv, &zb)) != MLMC_OK) return s;
+  if ((s = m1_table(d, &dv, &zd)) != MLMC_OK) return s;
+  std::vector<double> T(N);
+  for (int j = 0; j < N; ++j) T[j] = j < N / 2 ? (*zd)[j] : -(*zd)[N - 1 - j];
+  std::vector<M2Field> fh(N), fl(N);
+  for (int j = 0; j < N; ++j) m2_fields(j, b, fh[j], fl[j]);
+  // normal matrix A^T A (A has one +-1 per field in every row)
+  std::vector<long double> M((size_t)k * k, 0.0L);
+  for (int j = 0; j < N; ++j) {
+    const M2Field f[2] = {fh[j], fl[j]};
+    for (int a = 0; a < 2; ++a)
+      for (int c = 0; c < 2; ++c) M[(size_t)f[a].idx * k + f[c].idx] += (long double)(f[a].sgn * f[c].sgn);
+  }
+  M2Table t;
+  t.x.resize(k);
+  for (int q = 0; q < k; ++q) t.x[q] = (*zb)[q] / std::sqrt(2.0);
+  auto sums = [&](const std::vector<double> &x, std::vector<double> &v) {
+    v.resize(N);
+    for (int j = 0; j < N; ++j) v[j] = fh[j].sgn * x[fh[j].idx] + fl[j].sgn * x[fl[j].idx];
+  };
+  auto rank = [&](const std::vector<double> &v, std::vector<uint32_t> &pi) {
+    std::vector<int> order(N);
+    for (int j = 0; j < N; ++j) order[j] = j;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return v[a] < v[c]; });
+    pi.resize(N);
+    for (int r = 0; r < N; ++r) pi[order[r]] = (uint32_t)r;
+  };
+  sums(t.x, t.values);
+  rank(t.values, t.pi);
+  for (t.iterations = 0; t.iterations < 1000;) {
+    std::vector<long double> rhs(k, 0.0L);
+    for (int j = 0; j < N; ++j) {
+      const long double y = T[t.pi[j]];
+      rhs[fh[j].idx] += fh[j].sgn * y;
+      rhs[fl[j].idx] += fl[j].sgn * y;
+    }
+    if (!chol_solve(M, rhs, k, t.x)) return MLMC_EINVAL;
+    ++t.iterations;
+    sums(t.x, t.values);
+    std::vector<uint32_t> pn;
+    rank(t.values, pn);
+    if (pn == t.pi) break;
+    t.pi.swap(pn);
+  }
+  auto ins = g_m2.emplace(d, std::move(t));
+  *out = &ins.first->second;
+  return MLMC_OK;
+}
+
+// Method-2 value of index j in a representation: each small-table value rounded
+// once, the two fields added exactly (fixed point) or with one rounding.
+double m2_value(const M2Table &t, int d, int j, int rep, int fZ) {
+  const int b = d / 2;
+  M2Field h, l;
+  m2_fields(j, b, h, l);
+  const double a = t.x[h.idx], c = t.x[l.idx];
+  switch (rep) {
+    case REP_FIXED: {
+      const int64_t qa = (int64_t)std::floor(std::ldexp(a, fZ) + 0.5), qc = (int64_t)std::floor(std::ldexp(c, fZ) + 0.5);
+      return std::ldexp((double)((int64_t)h.sgn * qa + (int64_t)l.sgn * qc), -fZ);
+    }
+    case REP_FP16: {
+      const double ha = (double)__half2float(__double2half(a)), hc = (double)__half2float(__double2half(c));
+      return (double)__half2float(__double2half(h.sgn * ha + l.sgn * hc));
+    }
+    case REP_BF16: {
+      const double ba = (double)__bfloat162float(__double2bfloat16(a));
+      const double bc = (double)__bfloat162float(__double2bfloat16(c));
+      return (double)__bfloat162float(__double2bfloat16(h.sgn * ba + l.sgn * bc));
+    }
+    case REP_FP32: {
+      const double fa = (double)(float)a, fc = (double)(float)c;
+      return (double)(float)(h.sgn * fa + l.sgn * fc);
+    }
+    default: return t.values[j];
+  }
+}
+
+// Device copy of the Method-2 interval ranks of index width d.
+mlmc_status m2_perm_device(int d, const uint16_t **out) {
+  auto it = g.m2_perm.find(d);
+  if (it != g.m2_perm.end()) { *out = it->second; return MLMC_OK; }
+  const M2Table *t;
+  mlmc_status s = m2_build(d, &t);
+  if (s != MLMC_OK) return s;
+  std::vector<uint16_t> h(1 << d);
+  for (int j = 0; j < (1 << d); ++j) h[j] = (uint16_t)t->pi[j];
+  uint16_t *p = nullptr;
+  CK(cudaMalloc(&p, sizeof(uint16_t) * h.size()));
+  CK(cudaMemcpy(p, h.data(), sizeof(uint16_t) * h.size(), cudaMemcpyHostToDevice));
+  g.m2_perm[d] = p;
+  *out = p;
+  return MLMC_OK;
+}
+
 mlmc_status get_table(int method, int d, int rep, int fZ, const void **out, bool full_signed = false) {
   if (rep != REP_FIXED) fZ = 0;
-  if (method != 1) full_signed = false;
+  if (method == 3) full_signed = false;
   auto key = std::make_tuple(method, d, rep, fZ, full_signed ? 1 : 0);
   auto it = g.tables.find(key);
   if (it != g.tables.end()) { *out = it->second; return MLMC_OK; }
@@ -199,7 +357,28 @@ mlmc_status get_table(int method, int d, int rep, int fZ, const void **out, bool
   if (s != MLMC_OK) return s;
   void *p = nullptr;
   const int n = 1 << (d - 1);
-  if (method == 1 && full_signed) {
+  if (method == 2) {
+    // the signed table over all 2^d indices, built on the host
+    if (!full_signed) return MLMC_EINVAL;
+    const M2Table *t;
+    if ((s = m2_build(d, &t)) != MLMC_OK) return s;
+    if (rep == REP_FIXED) {
+      std::vector<int32_t> h(2 * n);
+      for (int j = 0; j < 2 * n; ++j) h[j] = (int32_t)std::llround(std::ldexp(m2_value(*t, d, j, rep, fZ), fZ));
+      CK(cudaMalloc(&p, sizeof(int32_t) * h.size()));
+      CK(cudaMemcpy(p, h.data(), sizeof(int32_t) * h.size(), cudaMemcpyHostToDevice));
+    } else if (rep == REP_FP16 || rep == REP_BF16) {
+      std::vector<uint16_t> h(2 * n);
+      for (int j = 0; j < 2 * n; ++j) {
+        const double v = m2_value(*t, d, j, rep, fZ);
+        h[j] = rep == REP_FP16 ? half_bits(v) : bf16_bits(v);
+      }
+      CK(cudaMalloc(&p, sizeof(uint16_t) * h.size()));
+      CK(cudaMemcpy(p, h.data(), sizeof(uint16_t) * h.size(), cudaMemcpyHostToDevice));
+    } else {
+      return MLMC_EINVAL;
+    }
+  } else if (method == 1 && full_signed) {
     const size_t es = (rep == REP_FP16 || rep == REP_BF16) ? 2 : 4;
     CK(cudaMalloc(&p, es * 2 * n));
     CK(launch_m1_signed(z64, d, rep, fZ, p, g.st));
@@ -236,8 +415,9 @@ bool params_ok(const mlmc_params *p) {
     return false;
   if (!(p->S0 > 0.0) || p->K < 0.0 || p->sigma < 0.0 || !(p->T > 0.0)) return false;
   if (p->payoff < 0 || p->payoff > 3 || p->scheme < 0 || p->scheme > 1) return false;
-  if (p->icdf_method != 1 && p->icdf_method != 3) return false;
+  if (p->icdf_method < 1 || p->icdf_method > 3) return false;
   if (p->icdf_bits < 2 || p->icdf_bits > 14) return false;
+  if (p->icdf_method == 2 && (p->icdf_bits % 2 || p->icdf_bits < 4)) return false;   // two fields of >= 2 bits
   if (p->formats && p->n_formats < 0) return false;
   if (p->rng_pack != 0 && p->rng_pack != 1) return false;
   if (p->reserved != 0) return false;
@@ -430,6 +610,13 @@ bool fast_fixed(const int e[7], const int f[7], int64_t con1, int64_t con1c, int
 // Largest |table value| in Z's fixed-point format, as the kernels evaluate it.
 int64_t table_zmax_fixed(const std::vector<double> &Z, int d, int method, int fZ) {
   int64_t zmax = 0;
+  if (method == 2) {
+    const M2Table *t;
+    if (m2_build(d, &t) != MLMC_OK) return INT64_MAX;
+    for (int j = 0; j < (1 << d); ++j)
+      zmax = std::max<int64_t>(zmax, std::llabs(std::llround(std::ldexp(m2_value(*t, d, j, REP_FIXED, fZ), fZ))));
+    return zmax;
+  }
   if (method == 1) {
     for (double v : Z) zmax = std::max<int64_t>(zmax, std::llabs((int64_t)std::floor(std::ldexp(v, fZ) + 0.5)));
     return zmax;
@@ -445,8 +632,6 @@ int64_t table_zmax_fixed(const std::vector<double> &Z, int d, int method, int fZ
   return zmax;
 }
 
-uint16_t half_bits(double x) { return __half_as_ushort(__double2half(x)); }
-uint16_t bf16_bits(double x) { return __bfloat16_as_ushort(__double2bfloat16(x)); }
 
 
 // Split an item's sample groups into chunks of `threads` x groups_per_thread.
@@ -594,8 +779,15 @@ mlmc_status build_item(const mlmc_work &w, int out_index, void *dump, BuiltItem 
     mlmc_status s = get_table(p->icdf_method, p->icdf_bits, rep, fZ, &tab, true);
     if (s != MLMC_OK) return s;
     it.ztab = tab;
-    b.smem = p->icdf_method == 1 ? (size_t)(1 << p->icdf_bits) * (fixed ? 4 : 2) : sizeof(M3Coef);
+    b.smem = p->icdf_method != 3 ? (size_t)(1 << p->icdf_bits) * (fixed ? 4 : 2) : sizeof(M3Coef);
     exact_int = (v == MLMC_FIXED_APPROX || v == MLMC_FP16_APPROX || v == MLMC_BF16_APPROX) ? 1 : 0;
+    if (p->icdf_method == 2 && !exact_int) {
+      // Method 2 coupling: the correction's exact path reads the interval ranks
+      const uint16_t *perm = nullptr;
+      if ((s = m2_perm_device(p->icdf_bits, &perm)) != MLMC_OK) return s;
+      it.perm = perm;
+      b.smem += sizeof(uint16_t) << p->icdf_bits;
+    }
   }
   it.unit = unit;
   it.unit_scale = std::ldexp(1.0f, -unit);
@@ -1132,11 +1324,19 @@ mlmc_status mlmc_default_format(const mlmc_params *p, int level, mlmc_format *ou
 }
 
 mlmc_status mlmc_icdf_table(int method, int d, int rep, int fZ, double *out) {
-  if ((method != 1 && method != 3) || d < 2 || d > 14 || rep < 0 || rep > 4 || !out) return MLMC_EINVAL;
+  if (method < 1 || method > 3 || d < 2 || d > 14 || rep < 0 || rep > 4 || !out) return MLMC_EINVAL;
   if (rep == REP_FIXED && (fZ < 0 || fZ > 28)) return MLMC_EINVAL;
   if (method == 3 && rep == REP_FP64) return MLMC_EINVAL;
+  if (method == 2 && (d % 2 || d < 4)) return MLMC_EINVAL;
   mlmc_status s = ensure_ctx();
   if (s != MLMC_OK) return s;
+  if (method == 2) {
+    // the host-built values the device tables are made of
+    const M2Table *t;
+    if ((s = m2_build(d, &t)) != MLMC_OK) return s;
+    for (int j = 0; j < (1 << (d - 1)); ++j) out[j] = m2_value(*t, d, j, rep, fZ);
+    return MLMC_OK;
+  }
   const void *tab = nullptr;
   if ((s = get_table(method, d, rep, fZ, &tab)) != MLMC_OK) return s;
   const int n = 1 << (d - 1);
@@ -1147,6 +1347,18 @@ mlmc_status mlmc_icdf_table(int method, int d, int rep, int fZ, double *out) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(g.st);
   cudaFree(dv);
   return e == cudaSuccess ? MLMC_OK : MLMC_ECUDA;
+}
+
+mlmc_status mlmc_icdf_method2(int d, double *x, uint32_t *perm, int *iterations) {
+  if (d % 2 || d < 4 || d > 14) return MLMC_EINVAL;
+  mlmc_status s = ensure_ctx();
+  if (s != MLMC_OK) return s;
+  const M2Table *t;
+  if ((s = m2_build(d, &t)) != MLMC_OK) return s;
+  if (x) std::memcpy(x, t->x.data(), sizeof(double) * t->x.size());
+  if (perm) std::memcpy(perm, t->pi.data(), sizeof(uint32_t) * t->pi.size());
+  if (iterations) *iterations = t->iterations;
+  return MLMC_OK;
 }
 
 mlmc_status mlmc_philox(const uint32_t *ctr, uint64_t n, uint64_t seed, uint32_t *out) {
@@ -1438,6 +1650,7 @@ extern "C" mlmc_status mlmc_level_noalloc(int level, uint64_t N, const mlmc_para
   if (!out || !params_ok(p)) return MLMC_EINVAL;
   if (level < 0 || level > 20 || (int)v < 0 || (int)v > 7) return MLMC_EINVAL;
   if (N > (1ULL << 58) || first_sample > (1ULL << (60 - level)) - N) return MLMC_EINVAL;
+  if (p->icdf_method == 2) return MLMC_EINVAL;   // its tables are built on the host, with allocation
   const cudaStream_t st = (cudaStream_t)stream;
   NoAllocScratch *S = nullptr;
   mlmc_status s = noalloc_scratch(&S);

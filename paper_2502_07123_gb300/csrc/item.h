@@ -79,7 +79,8 @@ struct ItemDesc {
   FixedConsts fx;
   FastFixed ff;
   uint16_t h_c1, h_c1c, h_c2, h_c3, h_S0, h_pad;  // binary16 / bfloat16 bit patterns
-  const void *ztab;        // device table for method 1 (int32 / half bits), or method-3 coefficients
+  const void *ztab;        // device table for methods 1 and 2 (int32 / half bits), or method-3 coefficients
+  const uint16_t *perm;    // method 2, correction estimators: interval rank pi(j) of every d-bit j
   // optional per-sample dump (device), indexed by sample - first
   void *dump;
 };

@@ -48,6 +48,12 @@ template <int EST, int AP, int SCHEME, int PC> struct MinCtas {
   static constexpr int value = (EST == EST_APPROX && AP == AP_FX32 && SCHEME == 0 && PC == PC_TERMINAL) ? 6 : 1;
 };
 
+// Bytes per entry of the shared-memory approximate-Normal table of a datapath.
+template <int AP>
+struct TabBytes {
+  static constexpr size_t value = (AP == AP_FIXED || AP == AP_FX32 || AP == AP_FX64) ? 4 : 2;
+};
+
 // KP > 1 (approximate-only estimators): KP samples advance in lockstep, lane L
 // reading bits [32 - d(L+1), 32 - dL) of the shared word (packed draws).
 template <int EST, int XP, int AP, int SCHEME, int PC, int KP = 1>
@@ -66,6 +72,8 @@ struct LevelSim {
 
   // ---- per-item constants (registers) ----
   int level, nsteps, payoff, d, dshift, method;
+  const uint16_t *perm_s;  // method 2 coupling of the exact path (shared memory), or nullptr
+  uint32_t low_mask;
   X c1, c2, c1c, c3, S0, K;
   // fixed point
   FixedConsts fx;
@@ -108,6 +116,11 @@ struct LevelSim {
     }
     unit_scale = it.unit_scale;
     smem_tab = tab;
+    perm_s = nullptr;
+    low_mask = (1u << dshift) - 1u;
+    if constexpr (EST == EST_CORR) {
+      if (it.perm) perm_s = (const uint16_t *)((const unsigned char *)tab + ((size_t)1 << it.d) * TabBytes<AP>::value);
+    }
   }
 
   __device__ __forceinline__ void begin() {
@@ -192,7 +205,7 @@ struct LevelSim {
   // Approximate Normal of J in Z's fixed-point format: Method 1 reads the
   // signed table at j = top d bits of J; Method 3 evaluates the class line.
   __device__ __forceinline__ int32_t fixed_z(uint32_t J) const {
-    if (method == 1) return ((const int32_t *)smem_tab)[J >> dshift];
+    if (method != 3) return ((const int32_t *)smem_tab)[J >> dshift];
     const ApproxIndex ai = approx_index(J, d);
     int32_t v;
     {
@@ -206,7 +219,7 @@ struct LevelSim {
   }
 
   __device__ __forceinline__ H half_z(uint32_t J) const {
-    if (method == 1) return HO::from_bits(((const uint16_t *)smem_tab)[J >> dshift]);
+    if (method != 3) return HO::from_bits(((const uint16_t *)smem_tab)[J >> dshift]);
     const ApproxIndex ai = approx_index(J, d);
     H v;
     {
@@ -221,9 +234,12 @@ struct LevelSim {
   template <bool COARSE>
   __device__ __forceinline__ void step(uint32_t J, int i) {
     if constexpr (HAS_EXACT) {
+      // Method 2 (Sec. 3.2): the exact path takes the uniform in the interval
+      // pi(j) that the approximate value of j is ranked at, with J's low bits
+      const uint32_t Je = perm_s ? (((uint32_t)perm_s[J >> dshift] << dshift) | (J & low_mask)) : J;
       X z;
-      if constexpr (XP == XP_F64) z = exact_normal_f64(J);
-      else z = exact_normal_f32(J);
+      if constexpr (XP == XP_F64) z = exact_normal_f64(Je);
+      else z = exact_normal_f32(Je);
       if constexpr (PC == PC_ASIAN) { if (i > 0) accF = accF + S; }
       S = fma(S, exact_inc(z, c1, X(1)), S);
       if constexpr (PC == PC_LOOKBACK) minF = fmin(minF, S);
@@ -508,7 +524,7 @@ __device__ __forceinline__ void run_chunk(const LaunchArgs &args, const ItemDesc
   if constexpr (AP != AP_NONE) {
     if (!staged || it.ztab != *staged) {
       if (staged) *staged = it.ztab;
-      if (it.method == 1) {
+      if (it.method != 3) {
         const int n = 1 << it.d;
         if constexpr (AP == AP_FIXED || AP == AP_FX32 || AP == AP_FX64) {
           const int32_t *src = (const int32_t *)it.ztab;
@@ -516,6 +532,10 @@ __device__ __forceinline__ void run_chunk(const LaunchArgs &args, const ItemDesc
         } else {
           const uint16_t *src = (const uint16_t *)it.ztab;
           for (int k = threadIdx.x; k < n; k += blockDim.x) ((uint16_t *)smem_tab)[k] = src[k];
+        }
+        if (it.perm) {   // after the table: the method-2 interval ranks
+          uint16_t *dst = (uint16_t *)(smem_tab + (size_t)n * TabBytes<AP>::value);
+          for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = it.perm[k];
         }
       } else {
         const uint32_t *src = (const uint32_t *)it.ztab;

@@ -145,6 +145,7 @@ def load():
         "mlmc_sensitivities": (st, [ctypes.c_int, ctypes.c_uint64, P(Params), ctypes.c_uint64, ctypes.c_uint64,
                                     P(Sensitivity), ctypes.c_void_p]),
         "mlmc_optimise_level": (st, [ctypes.c_int, P(Sensitivity), P(OptConfig), P(OptResult)]),
+        "mlmc_icdf_method2": (st, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, P(ctypes.c_int)]),
         "mlmc_default_format": (st, [P(Params), ctypes.c_int, P(Format)]),
         "mlmc_icdf_table": (st, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_double)]),
         "mlmc_philox": (st, [P(ctypes.c_uint32), ctypes.c_uint64, ctypes.c_uint64, P(ctypes.c_uint32)]),
@@ -476,6 +477,15 @@ def mlmc_icdf_table(method, d, rep, fZ=0):
     out = (ctypes.c_double * (1 << (d - 1)))()
     _check(load().mlmc_icdf_table(method, d, rep, fZ, out), "mlmc_icdf_table")
     return np.frombuffer(out, dtype=np.float64).copy()
+
+
+def mlmc_icdf_method2(d):
+    """Method-2 small table, interval ranks pi and least-squares iterations (mlmc_icdf_method2)."""
+    x = np.zeros(1 << (d // 2 - 1), dtype=np.float64)
+    pi = np.zeros(1 << d, dtype=np.uint32)
+    it = ctypes.c_int()
+    _check(load().mlmc_icdf_method2(d, x.ctypes.data, pi.ctypes.data, ctypes.byref(it)), "mlmc_icdf_method2")
+    return dict(x=x, pi=pi, iterations=it.value)
 
 
 def icdf_mse(d, method=1):
