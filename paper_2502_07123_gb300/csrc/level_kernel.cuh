@@ -56,7 +56,9 @@ struct TabBytes {
 
 // KP > 1 (approximate-only estimators): KP samples advance in lockstep, lane L
 // reading bits [32 - d(L+1), 32 - dL) of the shared word (packed draws).
-template <int EST, int XP, int AP, int SCHEME, int PC, int KP = 1>
+// M3: the item uses Method 3 (line evaluation) instead of a table lookup
+// (Methods 1 and 2); chosen once per chunk, so the step code has no branch on it.
+template <int EST, int XP, int AP, int SCHEME, int PC, int KP = 1, bool M3 = false>
 struct LevelSim {
   static_assert(KP == 1 || EST == EST_APPROX, "packed draws feed approximate-only estimators");
   static constexpr bool HAS_EXACT = (EST != EST_APPROX);
@@ -66,6 +68,8 @@ struct LevelSim {
   static constexpr bool FIXED = (AP == AP_FIXED || FAST);
   static constexpr bool HALF = (AP == AP_F16 || AP == AP_BF16);
   using AS = typename std::conditional<AP == AP_FX32, int32_t, int64_t>::type;  // fixed-point S
+  // saturation flag of the fast datapath: OR of (clamped ^ unclamped) for a 32-bit S
+  using SatT = typename std::conditional<AP == AP_FX32, uint32_t, bool>::type;
   using X = typename XType<XP>::T;
   using H = typename HType<AP>::T;
   using HO = HalfOps<H>;
@@ -87,7 +91,7 @@ struct LevelSim {
   // ---- per-sample state (approximate state per lane) ----
   X S, Sc, zprev, accF, accC, minF, minC;
   AS aS[KP], aSc[KP], aminF[KP], aminC[KP];
-  bool satb[KP];
+  SatT satb[KP];
   int64_t aaccF[KP], aaccC[KP];
   int32_t azprev[KP];
   H hS[KP], hSc[KP], hzprev[KP], hminF[KP], hminC[KP];
@@ -133,7 +137,7 @@ struct LevelSim {
       if constexpr (FIXED) {
         aS[l] = (AS)fx.S0; aSc[l] = (AS)fx.S0; aaccF[l] = 0; aaccC[l] = 0; aminF[l] = aS[l]; aminC[l] = aS[l];
         azprev[l] = 0;
-        satb[l] = false;
+        satb[l] = SatT(0);
       }
       if constexpr (HALF) {
         hS[l] = hS0; hSc[l] = hS0; hzprev[l] = HO::from_f(0.0f); hminF[l] = hS0; hminC[l] = hS0;
@@ -165,7 +169,7 @@ struct LevelSim {
   }
 
   // ---- fast fixed-point Algorithm-1 step (same values as fx_step while S stays in range) ----
-  __device__ __forceinline__ AS ff_step(AS s, int32_t z, int32_t c1r, int64_t m, bool &satb) {
+  __device__ __forceinline__ AS ff_step(AS s, int32_t z, int32_t c1r, int64_t m, SatT &satb) {
     const int32_t mul1 = (int32_t)(((int64_t)ff.con2 * z + ff.radd1) >> ff.rs1);
     int32_t acc = c1r + mul1 * ff.mulF1;
     if constexpr (MIL) {
@@ -184,7 +188,8 @@ struct LevelSim {
     // saturation of S (the only variable the host could not bound)
     const AS lim = (AS)ff.limS;
     const AS c = min(max(s, -lim), lim);
-    satb |= (c != s);
+    if constexpr (AP == AP_FX32) satb |= (uint32_t)(c ^ s);
+    else satb |= (c != s);
     return c;
   }
 
@@ -205,7 +210,7 @@ struct LevelSim {
   // Approximate Normal of J in Z's fixed-point format: Method 1 reads the
   // signed table at j = top d bits of J; Method 3 evaluates the class line.
   __device__ __forceinline__ int32_t fixed_z(uint32_t J) const {
-    if (method != 3) return ((const int32_t *)smem_tab)[J >> dshift];
+    if constexpr (!M3) return ((const int32_t *)smem_tab)[J >> dshift];
     const ApproxIndex ai = approx_index(J, d);
     int32_t v;
     {
@@ -219,7 +224,7 @@ struct LevelSim {
   }
 
   __device__ __forceinline__ H half_z(uint32_t J) const {
-    if (method != 3) return HO::from_bits(((const uint16_t *)smem_tab)[J >> dshift]);
+    if constexpr (!M3) return HO::from_bits(((const uint16_t *)smem_tab)[J >> dshift]);
     const ApproxIndex ai = approx_index(J, d);
     H v;
     {
@@ -231,8 +236,10 @@ struct LevelSim {
   }
 
   // One fine step i driven by J, and the coarse step after odd i (levels >= 1).
-  template <bool COARSE>
+  // PAR: parity of i when known at compile time (0 even, 1 odd), -1 otherwise.
+  template <bool COARSE, int PAR = -1>
   __device__ __forceinline__ void step(uint32_t J, int i) {
+    const bool odd = PAR >= 0 ? (PAR == 1) : ((i & 1) != 0);
     if constexpr (HAS_EXACT) {
       // Method 2 (Sec. 3.2): the exact path takes the uniform in the interval
       // pi(j) that the approximate value of j is ranked at, with J's low bits
@@ -244,7 +251,7 @@ struct LevelSim {
       S = fma(S, exact_inc(z, c1, X(1)), S);
       if constexpr (PC == PC_LOOKBACK) minF = fmin(minF, S);
       if constexpr (COARSE) {
-        if (i & 1) {
+        if (odd) {
           const X zc = zprev + z;
           if constexpr (PC == PC_ASIAN) { if (i > 1) accC = accC + Sc; }
           Sc = fma(Sc, exact_inc(zc, c1c, X(2)), Sc);
@@ -265,7 +272,7 @@ struct LevelSim {
           else aS[l] = fx_step(aS[l], z, fx.con1A, 1, sat[l]);
           if constexpr (PC == PC_LOOKBACK) aminF[l] = aS[l] < aminF[l] ? aS[l] : aminF[l];
           if constexpr (COARSE) {
-            if (i & 1) {
+            if (odd) {
               if constexpr (PC == PC_ASIAN) { if (i > 1) aaccC[l] += aSc[l]; }
               if constexpr (FAST) aSc[l] = ff_step(aSc[l], azprev[l] + z, ff.con1cr, ff.mcoarse, satb[l]);
               else aSc[l] = fx_step(aSc[l], azprev[l] + z, fx.con1cA, 2, sat[l]);
@@ -280,7 +287,7 @@ struct LevelSim {
           hS[l] = h_step(hS[l], z, hc1, HO::from_f(1.0f));
           if constexpr (PC == PC_LOOKBACK) hminF[l] = HO::to_f(hS[l]) < HO::to_f(hminF[l]) ? hS[l] : hminF[l];
           if constexpr (COARSE) {
-            if (i & 1) {
+            if (odd) {
               const H zc = HO::add(hzprev[l], z);
               if constexpr (PC == PC_ASIAN) { if (i > 1) haccC[l] = __fadd_rn(haccC[l], HO::to_f(hSc[l])); }
               hSc[l] = h_step(hSc[l], zc, hc1c, HO::from_f(2.0f));
@@ -498,6 +505,97 @@ __device__ __forceinline__ void block_reduce_write(ThreadAcc<EST, XP> &a, Partia
   }
 }
 
+// Simulate one chunk of an item (its table already in shared memory) and
+// write the CTA's Partial for it.
+template <int EST, int XP, int AP, int SCHEME, int PC, int KP, bool M3>
+__device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDesc &it, uint32_t gc,
+                                           const unsigned char *smem_tab) {
+  using Sim = LevelSim<EST, XP, AP, SCHEME, PC, KP, M3>;
+  Sim sim;
+  sim.load(it, smem_tab);
+  ThreadAcc<EST, XP> acc;
+  acc.init();
+
+  const uint32_t chunk = gc - it.chunk_begin;
+  const uint64_t per_chunk = (uint64_t)it.groups_per_thread * blockDim.x;
+  const uint64_t gbeg = it.g0 + (uint64_t)chunk * per_chunk;
+  const uint64_t gend = min(it.g1, gbeg + per_chunk);
+  const uint64_t first = it.first, last = it.first + it.N;
+  const int lev = it.level;
+  const uint4 ctr_hi = make_uint4(0, 0, it.ctr2, it.ctr3);
+  mlmc_sample_rec *dump = (mlmc_sample_rec *)it.dump;
+
+  const uint64_t gf0 = it.gf0, gf1 = it.gf1;
+  const uint32_t ng = gend > gbeg ? (uint32_t)(gend - gbeg) : 0u;
+  // A group is one Philox call's worth of packs (4 on level 0, 2 on level 1) or,
+  // from level 2, one pack over 2^l / 4 calls; a pack holds KP samples.
+  for (uint32_t r = threadIdx.x; r < ng; r += blockDim.x) {
+    const uint64_t g = gbeg + r;
+    const bool full = g >= gf0 && g < gf1;
+    if (lev >= 2) {
+      const uint64_t P = g;
+      const uint32_t calls = 1u << (lev - 2);
+      const uint64_t qbase = P * calls;
+      sim.begin();
+      for (uint32_t c = 0; c < calls; ++c) {
+        const uint64_t q = qbase + c;
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), ctr_hi.z, ctr_hi.w), args.rk);
+        const int i0 = (int)(c << 2);
+        sim.template step<true, 0>(w.x, i0);
+        sim.template step<true, 1>(w.y, i0 + 1);
+        sim.template step<true, 0>(w.z, i0 + 2);
+        sim.template step<true, 1>(w.w, i0 + 3);
+      }
+#pragma unroll
+      for (int l = 0; l < KP; ++l) {
+        const uint64_t s = P * KP + l;
+        const bool valid = full || (s >= first && s < last);
+        sim.finish(acc, l, valid, dump && valid ? dump + (s - first) : nullptr);
+      }
+    } else {
+      const uint4 w = it.enumerate ? enum_words(g, lev, it.d)
+                                   : philox4x32_10(make_uint4((uint32_t)g, (uint32_t)(g >> 32), ctr_hi.z, ctr_hi.w),
+                                                   args.rk);
+      const int ppg = lev == 1 ? 2 : 4;  // packs per group
+      const uint64_t s0 = (uint64_t)(ppg * KP) * g;
+      // samples s0 + k are valid for k in [klo, khi)
+      int klo = 0, khi = ppg * KP;
+      if (!full) {
+        klo = s0 >= first ? 0 : (int)min(first - s0, (uint64_t)(ppg * KP));
+        khi = last <= s0 ? 0 : (int)min(last - s0, (uint64_t)(ppg * KP));
+      }
+      if (lev == 1) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          sim.begin();
+          sim.template step<true, 0>(u == 0 ? w.x : w.z, 0);
+          sim.template step<true, 1>(u == 0 ? w.y : w.w, 1);
+#pragma unroll
+          for (int l = 0; l < KP; ++l) {
+            const int k = u * KP + l;
+            const bool valid = k >= klo && k < khi;
+            sim.finish(acc, l, valid, dump && valid ? dump + (s0 + k - first) : nullptr);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          sim.begin();
+          sim.template step<false>(word_of(w, u), 0);
+#pragma unroll
+          for (int l = 0; l < KP; ++l) {
+            const int k = u * KP + l;
+            const bool valid = k >= klo && k < khi;
+            sim.finish(acc, l, valid, dump && valid ? dump + (s0 + k - first) : nullptr);
+          }
+        }
+      }
+    }
+    if constexpr (EST == EST_APPROX && AP == AP_FX32 && PC == PC_TERMINAL) acc.flush_group();
+  }
+  block_reduce_write<EST, XP>(acc, args.partials + gc);
+}
+
 // One chunk (gc) of one launch: find its item, stage the item's table in shared
 // memory (unless *staged, when given, says that it is there already), simulate the chunk's sample groups
 // and write the CTA's Partial for the chunk.  Every thread has finished the
@@ -506,7 +604,6 @@ __device__ __forceinline__ void block_reduce_write(ThreadAcc<EST, XP> &a, Partia
 template <int EST, int XP, int AP, int SCHEME, int PC, int KP>
 __device__ __forceinline__ void run_chunk(const LaunchArgs &args, const ItemDesc *items, int n_items, uint32_t gc,
                                           const void **staged) {
-  using Sim = LevelSim<EST, XP, AP, SCHEME, PC, KP>;
   extern __shared__ __align__(16) unsigned char smem_tab[];
   __shared__ int s_item;
   if (threadIdx.x == 0) {
@@ -545,89 +642,12 @@ __device__ __forceinline__ void run_chunk(const LaunchArgs &args, const ItemDesc
       __syncthreads();
     }
   }
-  Sim sim;
-  sim.load(it, smem_tab);
-  ThreadAcc<EST, XP> acc;
-  acc.init();
-
-  const uint32_t chunk = gc - it.chunk_begin;
-  const uint64_t per_chunk = (uint64_t)it.groups_per_thread * blockDim.x;
-  const uint64_t gbeg = it.g0 + (uint64_t)chunk * per_chunk;
-  const uint64_t gend = min(it.g1, gbeg + per_chunk);
-  const uint64_t first = it.first, last = it.first + it.N;
-  const int lev = it.level;
-  const uint4 ctr_hi = make_uint4(0, 0, it.ctr2, it.ctr3);
-  mlmc_sample_rec *dump = (mlmc_sample_rec *)it.dump;
-
-  const uint64_t gf0 = it.gf0, gf1 = it.gf1;
-  const uint32_t ng = gend > gbeg ? (uint32_t)(gend - gbeg) : 0u;
-  // A group is one Philox call's worth of packs (4 on level 0, 2 on level 1) or,
-  // from level 2, one pack over 2^l / 4 calls; a pack holds KP samples.
-  for (uint32_t r = threadIdx.x; r < ng; r += blockDim.x) {
-    const uint64_t g = gbeg + r;
-    const bool full = g >= gf0 && g < gf1;
-    if (lev >= 2) {
-      const uint64_t P = g;
-      const uint32_t calls = 1u << (lev - 2);
-      const uint64_t qbase = P * calls;
-      sim.begin();
-      for (uint32_t c = 0; c < calls; ++c) {
-        const uint64_t q = qbase + c;
-        const uint4 w = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), ctr_hi.z, ctr_hi.w), args.rk);
-        const int i0 = (int)(c << 2);
-        sim.template step<true>(w.x, i0);
-        sim.template step<true>(w.y, i0 + 1);
-        sim.template step<true>(w.z, i0 + 2);
-        sim.template step<true>(w.w, i0 + 3);
-      }
-#pragma unroll
-      for (int l = 0; l < KP; ++l) {
-        const uint64_t s = P * KP + l;
-        const bool valid = full || (s >= first && s < last);
-        sim.finish(acc, l, valid, dump && valid ? dump + (s - first) : nullptr);
-      }
-    } else {
-      const uint4 w = it.enumerate ? enum_words(g, lev, it.d)
-                                   : philox4x32_10(make_uint4((uint32_t)g, (uint32_t)(g >> 32), ctr_hi.z, ctr_hi.w),
-                                                   args.rk);
-      const int ppg = lev == 1 ? 2 : 4;  // packs per group
-      const uint64_t s0 = (uint64_t)(ppg * KP) * g;
-      // samples s0 + k are valid for k in [klo, khi)
-      int klo = 0, khi = ppg * KP;
-      if (!full) {
-        klo = s0 >= first ? 0 : (int)min(first - s0, (uint64_t)(ppg * KP));
-        khi = last <= s0 ? 0 : (int)min(last - s0, (uint64_t)(ppg * KP));
-      }
-      if (lev == 1) {
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          sim.begin();
-          sim.template step<true>(u == 0 ? w.x : w.z, 0);
-          sim.template step<true>(u == 0 ? w.y : w.w, 1);
-#pragma unroll
-          for (int l = 0; l < KP; ++l) {
-            const int k = u * KP + l;
-            const bool valid = k >= klo && k < khi;
-            sim.finish(acc, l, valid, dump && valid ? dump + (s0 + k - first) : nullptr);
-          }
-        }
-      } else {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          sim.begin();
-          sim.template step<false>(word_of(w, u), 0);
-#pragma unroll
-          for (int l = 0; l < KP; ++l) {
-            const int k = u * KP + l;
-            const bool valid = k >= klo && k < khi;
-            sim.finish(acc, l, valid, dump && valid ? dump + (s0 + k - first) : nullptr);
-          }
-        }
-      }
-    }
-    if constexpr (EST == EST_APPROX && AP == AP_FX32 && PC == PC_TERMINAL) acc.flush_group();
+  if constexpr (AP == AP_NONE) {
+    chunk_body<EST, XP, AP, SCHEME, PC, KP, false>(args, it, gc, smem_tab);
+  } else {
+    if (it.method == 3) chunk_body<EST, XP, AP, SCHEME, PC, KP, true>(args, it, gc, smem_tab);
+    else chunk_body<EST, XP, AP, SCHEME, PC, KP, false>(args, it, gc, smem_tab);
   }
-  block_reduce_write<EST, XP>(acc, args.partials + gc);
 }
 
 // Static launch: CTA b runs chunk chunk0 + b of the launch.
