@@ -593,9 +593,6 @@ bool fast_fixed(const int e[7], const int f[7], int64_t con1, int64_t con1c, int
   const I snew = limS + mul2_abs * ((I)1 << shS);
   if (snew >= ((I)1 << 62)) return false;
   s64 = !(snew < ((I)1 << 31) - 1);
-  // the 32-bit datapath takes each rounded product as the low word of a funnel
-  // shift, which needs shift counts below 32
-  if (rs1 > 31 || rs2 > 31 || (milstein && rs3 > 31)) s64 = true;
   ff.con2 = (int32_t)con2;
   ff.con3 = (int32_t)con3;
   ff.con1r = (int32_t)(con1 + (int64_t)rsum);

@@ -168,28 +168,18 @@ struct LevelSim {
     return saturate(requant(s2, fx.q_S), fx.lim[6], sat);
   }
 
-  // Low 32 bits of x >> n for 0 <= n <= 31: one funnel shift of the word pair
-  // (the host routes items with larger shift counts to the 64-bit datapath).
-  static __device__ __forceinline__ int32_t lo32_shr(int64_t x, int n) {
-    return (int32_t)__funnelshift_r((uint32_t)x, (uint32_t)((uint64_t)x >> 32), (unsigned)n);
-  }
-
   // ---- fast fixed-point Algorithm-1 step (same values as fx_step while S stays in range) ----
   __device__ __forceinline__ AS ff_step(AS s, int32_t z, int32_t c1r, int64_t m, SatT &satb) {
-    int32_t mul1;
-    if constexpr (AP == AP_FX32) mul1 = lo32_shr((int64_t)ff.con2 * z + ff.radd1, ff.rs1);
-    else mul1 = (int32_t)(((int64_t)ff.con2 * z + ff.radd1) >> ff.rs1);
+    const int32_t mul1 = (int32_t)(((int64_t)ff.con2 * z + ff.radd1) >> ff.rs1);
     int32_t acc = c1r + mul1 * ff.mulF1;
     if constexpr (MIL) {
       const int64_t zz = (int64_t)z * z - m;
-      int32_t mul3;
-      if constexpr (AP == AP_FX32) mul3 = lo32_shr(ff.con3 * zz + ff.radd3, ff.rs3);
-      else mul3 = (int32_t)((ff.con3 * zz + ff.radd3) >> ff.rs3);
+      const int32_t mul3 = (int32_t)((ff.con3 * zz + ff.radd3) >> ff.rs3);
       acc += mul3 * ff.mulF1;
     }
     const int32_t sum1 = acc >> ff.rs_sum1;
     if constexpr (AP == AP_FX32) {
-      const int32_t mul2 = lo32_shr((int64_t)s * sum1 + ff.radd2, ff.rs2);
+      const int32_t mul2 = (int32_t)(((int64_t)s * sum1 + ff.radd2) >> ff.rs2);
       s = (int32_t)((uint32_t)s + (uint32_t)mul2 * (uint32_t)ff.mulS);
     } else {
       const int32_t mul2 = (int32_t)((int64_t)((uint64_t)s * (uint64_t)(int64_t)sum1 + (uint64_t)ff.radd2) >> ff.rs2);
