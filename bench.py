@@ -277,11 +277,11 @@ def main():
         "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "i64+f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "path_steps_per_step": steps_per_launch,
-                   "work_items": len(items), "kernels_per_step": info["kernels"] + 1,
+                   "work_items": len(items), "kernels_per_step": info["kernels"],
                    "ctas_per_step": info["ctas"], "l2": "flushed between steps (256 MiB write)",
                    "launch_shape": shape,
                    "wall_s": t_wall},
-        "gpu_launches": (info["kernels"] + 1) * args.steps,
+        "gpu_launches": info["kernels"] * args.steps,
         "kernel_ms": {str(f): sum(v) / len(v) for f, v in kern_ms.items()},
         "clocks": clocks.summary(),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": info["h2d_bytes"],

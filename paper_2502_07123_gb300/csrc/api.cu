@@ -57,6 +57,8 @@ struct mlmc_plan {
   ItemDesc *d_items = nullptr;
   Partial *d_partials = nullptr;
   DevSums *d_out = nullptr;
+  uint32_t *d_counters = nullptr;    // per item, zero between launches
+  std::vector<uint32_t> empty_out;   // out_index of items without samples (sums reset per launch)
   std::vector<cudaStream_t> aux;
   std::vector<cudaEvent_t> join;
   std::vector<cudaEvent_t> kstart, kstop;   // around each level kernel, on its stream
@@ -80,6 +82,8 @@ struct Arena {
   size_t cap_chunks = 0;
   DevSums *out = nullptr;
   size_t cap_out = 0;
+  uint32_t *counters = nullptr;
+  size_t cap_counters = 0;
   std::vector<cudaStream_t> aux;
   std::vector<cudaEvent_t> join, kstart, kstop;
   cudaEvent_t fork = nullptr, t0 = nullptr, t1 = nullptr;
@@ -834,7 +838,7 @@ __global__ void finalize_kernel(const ItemDesc *items, int n_items, const Partia
 
 void free_plan_device(mlmc_plan *pl) {
   if (pl->borrowed) {
-    pl->d_items = nullptr; pl->d_partials = nullptr; pl->d_out = nullptr;
+    pl->d_items = nullptr; pl->d_partials = nullptr; pl->d_out = nullptr; pl->d_counters = nullptr;
     pl->aux.clear(); pl->join.clear(); pl->kstart.clear(); pl->kstop.clear();
     pl->fork = pl->t0 = pl->t1 = nullptr;
     return;
@@ -842,6 +846,7 @@ void free_plan_device(mlmc_plan *pl) {
   if (pl->d_items) cudaFree(pl->d_items);
   if (pl->d_partials) cudaFree(pl->d_partials);
   if (pl->d_out) cudaFree(pl->d_out);
+  if (pl->d_counters) cudaFree(pl->d_counters);
   for (auto s : pl->aux) cudaStreamDestroy(s);
   for (auto e : pl->join) cudaEventDestroy(e);
   for (auto e : pl->kstart) cudaEventDestroy(e);
@@ -850,7 +855,7 @@ void free_plan_device(mlmc_plan *pl) {
   if (pl->fork) cudaEventDestroy(pl->fork);
   if (pl->t0) cudaEventDestroy(pl->t0);
   if (pl->t1) cudaEventDestroy(pl->t1);
-  pl->d_items = nullptr; pl->d_partials = nullptr; pl->d_out = nullptr;
+  pl->d_items = nullptr; pl->d_partials = nullptr; pl->d_out = nullptr; pl->d_counters = nullptr;
   pl->aux.clear(); pl->join.clear();
   pl->fork = pl->t0 = pl->t1 = nullptr;
 }
@@ -959,6 +964,7 @@ mlmc_status plan_create_impl(mlmc_plan **out, const mlmc_work *work, int n_work,
     ItemDesc it = built[i].it;
     it.chunk_begin = chunk;
     pl->items.push_back(it);
+    pl->empty_out.push_back(it.out_index);
   }
   pl->total_chunks = chunk;
   make_round_keys(seed, pl->rk);
@@ -966,13 +972,19 @@ mlmc_status plan_create_impl(mlmc_plan **out, const mlmc_work *work, int n_work,
   if (arena) {
     Arena &A = *arena;
     const size_t nl = pl->launches.size();
+    const size_t old_counters = A.cap_counters;
     if (!grow(A.items, A.cap_items, ni) || !grow(A.partials, A.cap_chunks, std::max<size_t>(1, chunk)) ||
-        !grow(A.out, A.cap_out, (size_t)n_work) || !arena_events(A, nl)) {
+        !grow(A.out, A.cap_out, (size_t)n_work) || !grow(A.counters, A.cap_counters, ni) ||
+        !arena_events(A, nl)) {
       delete pl;
       return MLMC_ENOMEM;
     }
+    if (A.cap_counters != old_counters && cudaMemset(A.counters, 0, sizeof(uint32_t) * A.cap_counters) != cudaSuccess) {
+      delete pl;
+      return MLMC_ECUDA;
+    }
     pl->borrowed = true;
-    pl->d_items = A.items; pl->d_partials = A.partials; pl->d_out = A.out;
+    pl->d_items = A.items; pl->d_partials = A.partials; pl->d_out = A.out; pl->d_counters = A.counters;
     pl->fork = A.fork; pl->t0 = A.t0; pl->t1 = A.t1;
     if (nl > 1) {
       pl->aux.assign(A.aux.begin(), A.aux.begin() + nl);
@@ -990,10 +1002,16 @@ mlmc_status plan_create_impl(mlmc_plan **out, const mlmc_work *work, int n_work,
   }
   if (cudaMalloc(&pl->d_items, sizeof(ItemDesc) * ni) != cudaSuccess ||
       cudaMalloc(&pl->d_partials, sizeof(Partial) * std::max<uint32_t>(1, chunk)) != cudaSuccess ||
-      cudaMalloc(&pl->d_out, sizeof(DevSums) * n_work) != cudaSuccess) {
+      cudaMalloc(&pl->d_out, sizeof(DevSums) * n_work) != cudaSuccess ||
+      cudaMalloc(&pl->d_counters, sizeof(uint32_t) * ni) != cudaSuccess) {
     free_plan_device(pl);
     delete pl;
     return MLMC_ENOMEM;
+  }
+  if (cudaMemset(pl->d_counters, 0, sizeof(uint32_t) * ni) != cudaSuccess) {
+    free_plan_device(pl);
+    delete pl;
+    return MLMC_ECUDA;
   }
   if (cudaMemcpy(pl->d_items, pl->items.data(), sizeof(ItemDesc) * ni, cudaMemcpyHostToDevice) != cudaSuccess) {
     free_plan_device(pl);
@@ -1039,6 +1057,8 @@ mlmc_status plan_launch_impl(mlmc_plan *pl, cudaStream_t st) {
     a.dyn = nullptr;
     a.partials = pl->d_partials;
     a.rk = pl->rk;
+    a.counters = pl->d_counters + L.item_off;
+    a.out = pl->d_out;
     CK(cudaEventRecord(pl->kstart[i], ls));
     CK(launch_by_family(L.family, L.scheme, L.pc, dim3(L.n_chunks), dim3(L.threads), L.smem, ls, a, nullptr));
     CK(cudaEventRecord(pl->kstop[i], ls));
@@ -1047,9 +1067,8 @@ mlmc_status plan_launch_impl(mlmc_plan *pl, cudaStream_t st) {
       CK(cudaStreamWaitEvent(st, pl->join[i], 0));
     }
   }
-  finalize_kernel<<<(unsigned)pl->items.size(), 32, 0, st>>>(pl->d_items, (int)pl->items.size(), pl->d_partials,
-                                                              pl->d_out);
-  CK(cudaGetLastError());
+  // items without samples: zero sums (no CTA writes them)
+  for (uint32_t o : pl->empty_out) CK(cudaMemsetAsync(pl->d_out + o, 0, sizeof(DevSums), st));
   CK(cudaEventRecord(pl->t1, st));
   pl->last_stream = st;
   pl->launched = true;
@@ -1803,6 +1822,8 @@ extern "C" mlmc_status mlmc_level_noalloc(int level, uint64_t N, const mlmc_para
   a.n_items = 1;
   a.chunk0 = 0;
   a.dyn = nullptr;
+  a.counters = nullptr;
+  a.out = nullptr;
   a.partials = S->partials;
   make_round_keys(seed, a.rk);
   if (it.n_chunks > 0) CK(launch_by_family(family, p->scheme, pc, dim3(it.n_chunks), dim3(threads), smem, st, a, nullptr));

@@ -505,6 +505,8 @@ mlmc_status capture(mlmc_engine *e) {
       a.partials = e->d_partials;
       a.rk = G.rk;
       a.dyn = e->d_dyn + live[i];
+      a.counters = nullptr;   // acc_kernel sums the partials
+      a.out = nullptr;
       if ((err = cudaStreamWaitEvent(ls, e->fork, 0)) != cudaSuccess) break;
       if ((err = launch_by_family(G.family, G.scheme, G.pc, dim3(G.grid), dim3(G.threads), G.smem, ls, a,
                                   nullptr)) != cudaSuccess)

@@ -124,6 +124,11 @@ struct LaunchArgs {
   Partial *partials;       // indexed by global chunk index
   RoundKeys rk;
   const DynLaunch *dyn;    // nullptr: one chunk per CTA, gridDim.x chunks
+  // per item of the launch, zero between launches: the CTA that finishes an
+  // item's last chunk sums its partials into out[out_index] (nullptr: a
+  // separate kernel does)
+  uint32_t *counters;
+  DevSums *out;
 };
 
 #if defined(__CUDACC__)

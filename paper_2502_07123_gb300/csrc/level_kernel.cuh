@@ -9,12 +9,14 @@
 // samples per call on level 0, 2 on level 1, one sample with 2^l / 4 calls
 // above), entirely in registers.  The approximate-Normal table of the item
 // lives in shared memory.  The only global-memory traffic is the work-item
-// descriptor, the table, one Partial record per CTA and the optional dump.
+// descriptor, the table, one Partial record per CTA, the item's sums (written
+// by the CTA that finishes its last chunk) and the optional dump.
 #pragma once
 #include <type_traits>
 
 #include "device_common.cuh"
 #include "mlmc.h"
+#include "reduce.cuh"
 
 namespace mlmc {
 
@@ -508,7 +510,7 @@ __device__ __forceinline__ void block_reduce_write(ThreadAcc<EST, XP> &a, Partia
 // Simulate one chunk of an item (its table already in shared memory) and
 // write the CTA's Partial for it.
 template <int EST, int XP, int AP, int SCHEME, int PC, int KP, bool M3>
-__device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDesc &it, uint32_t gc,
+__device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDesc &it, int item, uint32_t gc,
                                            const unsigned char *smem_tab) {
   using Sim = LevelSim<EST, XP, AP, SCHEME, PC, KP, M3>;
   Sim sim;
@@ -594,6 +596,25 @@ __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDes
     if constexpr (EST == EST_APPROX && AP == AP_FX32 && PC == PC_TERMINAL) acc.flush_group();
   }
   block_reduce_write<EST, XP>(acc, args.partials + gc);
+  if (args.counters) {
+    // the CTA that completes the item's last chunk sums all its partials, in
+    // chunk order (the partials of other CTAs are read through L2)
+    __shared__ int s_last;
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const uint32_t done = atomicAdd(args.counters + item, 1u) + 1u;
+      s_last = done == it.n_chunks;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x < 32) {
+      __threadfence();
+      const DevSums r = warp_sum_partials<true>(args.partials + it.chunk_begin, it.n_chunks);
+      if (threadIdx.x == 0) {
+        args.out[it.out_index] = r;
+        args.counters[item] = 0u;   // ready for the next launch
+      }
+    }
+  }
 }
 
 // One chunk (gc) of one launch: find its item, stage the item's table in shared
@@ -642,11 +663,12 @@ __device__ __forceinline__ void run_chunk(const LaunchArgs &args, const ItemDesc
       __syncthreads();
     }
   }
+  const int item = s_item;
   if constexpr (AP == AP_NONE) {
-    chunk_body<EST, XP, AP, SCHEME, PC, KP, false>(args, it, gc, smem_tab);
+    chunk_body<EST, XP, AP, SCHEME, PC, KP, false>(args, it, item, gc, smem_tab);
   } else {
-    if (it.method == 3) chunk_body<EST, XP, AP, SCHEME, PC, KP, true>(args, it, gc, smem_tab);
-    else chunk_body<EST, XP, AP, SCHEME, PC, KP, false>(args, it, gc, smem_tab);
+    if (it.method == 3) chunk_body<EST, XP, AP, SCHEME, PC, KP, true>(args, it, item, gc, smem_tab);
+    else chunk_body<EST, XP, AP, SCHEME, PC, KP, false>(args, it, item, gc, smem_tab);
   }
 }
 
