@@ -480,10 +480,11 @@ def time_to_eps(m, torch, eps=1e-3, seeds=(1, 2, 3)):
             prices.append(r["price"])
         out[name] = {"s_median": statistics.median(ts), "prices": prices, "L": r["L"], "N": r["N"]}
     # the same adaptive algorithm driven on the device: one request through a
-    # (created and warmed) engine's graph iteration instead of host-driven plans
+    # (created and warmed) engine, four iterations per CUDA-graph launch,
+    # instead of host-driven plans
     for name, mode in (("plain_fp32_graph", m.MODE_PLAIN_FP32),
                        ("nested_fixed_exact_low_graph", m.MODE_NESTED_FIXED_EXACT_LOW)):
-        eng = m.Engine(max_slots=1, max_level=10)
+        eng = m.Engine(max_slots=1, max_level=10, iters_per_launch=4)
         _engine_solve(eng, P, 1e-2, mode, 99)
         ts, prices = [], []
         for s in seeds:

@@ -12,7 +12,9 @@
 #include <cstring>
 #include <map>
 #include <new>
+#include <string>
 #include <tuple>
+#include <unordered_map>
 #include <vector>
 
 #include "item.h"
@@ -84,6 +86,10 @@ struct Arena {
   size_t cap_out = 0;
   uint32_t *counters = nullptr;
   size_t cap_counters = 0;
+  ItemDesc *h_items = nullptr;       // pinned staging of the work list
+  size_t cap_h_items = 0;
+  DevSums *h_out = nullptr;          // pinned staging of the results
+  size_t cap_h_out = 0;
   std::vector<cudaStream_t> aux;
   std::vector<cudaEvent_t> join, kstart, kstop;
   cudaEvent_t fork = nullptr, t0 = nullptr, t1 = nullptr;
@@ -101,6 +107,15 @@ struct Ctx {
   std::map<int, uint16_t *> m2_perm;                         // d -> device interval ranks (Method 2)
 };
 Ctx g;
+
+// Work items already built, by everything their constants depend on (params,
+// the level's format, level, variant, stream); the sample range is set per call.
+struct CachedItem {
+  BuiltItem b;
+  double disc;
+  int unit, exact_int;
+};
+std::unordered_map<std::string, CachedItem> g_item_cache;
 
 double g_cost[4] = {8.0, 1.0, 0.5, 1.5};
 const double g_cost_default[4] = {8.0, 1.0, 0.5, 1.5};
@@ -136,6 +151,8 @@ mlmc_status ensure_ctx() {
     g.m1_host.clear();
     g.m1_dev.clear();
     g.tables.clear();
+    g.m2_perm.clear();
+    g_item_cache.clear();
   }
   CK(cudaDeviceGetAttribute(&g.num_sms, cudaDevAttrMultiProcessorCount, dev));
   CK(cudaStreamCreateWithFlags(&g.st, cudaStreamNonBlocking));
@@ -816,6 +833,55 @@ mlmc_status build_item(const mlmc_work &w, int out_index, void *dump, BuiltItem 
   return MLMC_OK;
 }
 
+// build_item through the cache (flags 0): the constants, tables and family
+// come from the first build of the same (params, format, level, variant,
+// stream); the sample range and its groups are set for this call.
+mlmc_status build_item_cached(const mlmc_work &w, int out_index, void *dump, BuiltItem &b, double &disc, int &unit,
+                              int &exact_int) {
+  const mlmc_params *p = w.params;
+  if (w.flags != 0 || !params_ok(p) || w.level < 0 || w.level > 20)
+    return build_item(w, out_index, dump, b, disc, unit, exact_int);
+  std::string key;
+  key.reserve(96);
+  auto put = [&](const void *x, size_t n) { key.append((const char *)x, n); };
+  put(&p->S0, sizeof(double) * 5);
+  put(&p->payoff, sizeof(int32_t) * 4);
+  put(&p->request_id, sizeof(uint32_t));
+  put(&p->rng_pack, sizeof(int32_t));
+  const int has_fmt = p->formats ? (w.level < p->n_formats ? 1 : 2) : 0;
+  put(&has_fmt, sizeof has_fmt);
+  if (has_fmt == 1) put(&p->formats[w.level], sizeof(mlmc_format));
+  put(&w.level, sizeof(int32_t) * 2);     // level, variant
+  put(&w.stream, sizeof(int32_t));
+  auto f = g_item_cache.find(key);
+  if (f == g_item_cache.end()) {
+    mlmc_status s = build_item(w, out_index, dump, b, disc, unit, exact_int);
+    if (s != MLMC_OK) return s;
+    if (g_item_cache.size() > 8192) g_item_cache.clear();
+    g_item_cache.emplace(key, CachedItem{b, disc, unit, exact_int});
+    return MLMC_OK;
+  }
+  const int lev = w.level;
+  if (w.N > (1ULL << 58) || w.first_sample > (1ULL << (60 - lev)) - w.N) return MLMC_EINVAL;
+  b = f->second.b;
+  disc = f->second.disc;
+  unit = f->second.unit;
+  exact_int = f->second.exact_int;
+  ItemDesc &it = b.it;
+  it.first = w.first_sample;
+  it.N = w.N;
+  it.out_index = (uint32_t)out_index;
+  it.dump = dump;
+  const uint64_t spc = samples_per_group(lev, b.kp);
+  it.g0 = w.first_sample / spc;
+  it.g1 = w.N == 0 ? it.g0 : (w.first_sample + w.N + spc - 1) / spc;
+  it.gf0 = (w.first_sample + spc - 1) / spc;
+  it.gf1 = (w.first_sample + w.N) / spc;
+  if (it.gf1 < it.gf0) it.gf1 = it.gf0;
+  b.cost_step = g_cost[cost_kind_of(w.variant)];
+  return MLMC_OK;
+}
+
 void make_round_keys(uint64_t seed, RoundKeys &rk) {
   uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   for (int r = 0; r < 10; ++r) {
@@ -891,7 +957,8 @@ bool arena_events(Arena &A, size_t launches) {
 }
 
 mlmc_status plan_create_impl(mlmc_plan **out, const mlmc_work *work, int n_work, uint64_t seed,
-                             const mlmc_tuning *tuning, void *const *dumps, Arena *arena = nullptr) {
+                             const mlmc_tuning *tuning, void *const *dumps, Arena *arena = nullptr,
+                             bool defer_copy = false) {
   if (!out || !work || n_work <= 0) return MLMC_EINVAL;
   mlmc_status s = ensure_ctx();
   if (s != MLMC_OK) return s;
@@ -912,7 +979,8 @@ mlmc_status plan_create_impl(mlmc_plan **out, const mlmc_work *work, int n_work,
   std::vector<BuiltItem> built(n_work);
   std::vector<int> item_threads(n_work);
   for (int i = 0; i < n_work; ++i) {
-    s = build_item(work[i], i, dumps ? dumps[i] : nullptr, built[i], pl->disc[i], pl->unit[i], pl->exact_int[i]);
+    s = build_item_cached(work[i], i, dumps ? dumps[i] : nullptr, built[i], pl->disc[i], pl->unit[i],
+                          pl->exact_int[i]);
     if (s != MLMC_OK) { delete pl; return s; }
     int th, sp;
     tuning_for(built[i].family, built[i].scheme, built[i].pc, work[i].level, &th, &sp);
@@ -992,8 +1060,9 @@ mlmc_status plan_create_impl(mlmc_plan **out, const mlmc_work *work, int n_work,
     }
     pl->kstart.assign(A.kstart.begin(), A.kstart.begin() + nl);
     pl->kstop.assign(A.kstop.begin(), A.kstop.begin() + nl);
-    if (cudaMemcpyAsync(pl->d_items, pl->items.data(), sizeof(ItemDesc) * ni, cudaMemcpyHostToDevice, g.st) !=
-        cudaSuccess) {
+    if (!defer_copy &&
+        cudaMemcpyAsync(pl->d_items, pl->items.data(), sizeof(ItemDesc) * ni, cudaMemcpyHostToDevice, g.st) !=
+            cudaSuccess) {
       delete pl;
       return MLMC_ECUDA;
     }
@@ -1080,13 +1149,8 @@ double u128_to_double(uint64_t lo, uint64_t hi) {
   return (double)v;
 }
 
-mlmc_status plan_results_impl(mlmc_plan *pl, mlmc_sums *out) {
-  if (!pl->launched) return MLMC_ENOTREADY;
-  CK(cudaEventSynchronize(pl->t1));
-  float ms = 0.0f;
-  CK(cudaEventElapsedTime(&ms, pl->t0, pl->t1));
-  std::vector<DevSums> h(pl->n_work);
-  CK(cudaMemcpy(h.data(), pl->d_out, sizeof(DevSums) * pl->n_work, cudaMemcpyDeviceToHost));
+// Per-item results from the undiscounted device sums h (host copy).
+void convert_results(const mlmc_plan *pl, const DevSums *h, float ms, mlmc_sums *out) {
   for (int i = 0; i < pl->n_work; ++i) {
     mlmc_sums &o = out[i];
     std::memset(&o, 0, sizeof o);
@@ -1107,23 +1171,59 @@ mlmc_status plan_results_impl(mlmc_plan *pl, mlmc_sums *out) {
       o.sum2 = disc * disc * h[i].dsum2;
     }
   }
+}
+
+mlmc_status plan_results_impl(mlmc_plan *pl, mlmc_sums *out) {
+  if (!pl->launched) return MLMC_ENOTREADY;
+  CK(cudaEventSynchronize(pl->t1));
+  float ms = 0.0f;
+  CK(cudaEventElapsedTime(&ms, pl->t0, pl->t1));
+  std::vector<DevSums> h(pl->n_work);
+  CK(cudaMemcpy(h.data(), pl->d_out, sizeof(DevSums) * pl->n_work, cudaMemcpyDeviceToHost));
+  convert_results(pl, h.data(), ms, out);
   return MLMC_OK;
 }
 
+template <class T>
+bool grow_pinned(T *&p, size_t &cap, size_t need) {
+  if (need <= cap) return true;
+  if (p) cudaFreeHost(p);
+  p = nullptr;
+  cap = 0;
+  const size_t n = std::max<size_t>(need, 64);
+  if (cudaHostAlloc((void **)&p, sizeof(T) * n, cudaHostAllocDefault) != cudaSuccess) return false;
+  cap = n;
+  return true;
+}
+
+// One synchronous pass on stream st: work list to the device through pinned
+// staging, the launch, the sums back through pinned staging, one stream sync.
 mlmc_status run_sync(const mlmc_work *work, int n_work, uint64_t seed, const mlmc_tuning *tuning,
                      void *const *dumps, mlmc_sums *out, cudaStream_t st) {
   mlmc_plan *pl = nullptr;
-  mlmc_status s = plan_create_impl(&pl, work, n_work, seed, tuning, dumps, &g.arena);
+  mlmc_status s = plan_create_impl(&pl, work, n_work, seed, tuning, dumps, &g.arena, true);
   if (s != MLMC_OK) return s;
-  // the work list was copied on the context stream: order the launch after it
-  if (st != g.st) {
-    if (cudaEventRecord(g.arena.fork, g.st) != cudaSuccess || cudaStreamWaitEvent(st, g.arena.fork, 0) != cudaSuccess) {
-      delete pl;
-      return MLMC_ECUDA;
+  Arena &A = g.arena;
+  const size_t ni = pl->items.size();
+  do {
+    if (!grow_pinned(A.h_items, A.cap_h_items, ni) || !grow_pinned(A.h_out, A.cap_h_out, (size_t)n_work)) {
+      s = MLMC_ENOMEM;
+      break;
     }
-  }
-  s = plan_launch_impl(pl, st);
-  if (s == MLMC_OK) s = plan_results_impl(pl, out);
+    std::memcpy(A.h_items, pl->items.data(), sizeof(ItemDesc) * ni);
+    if (cudaMemcpyAsync(pl->d_items, A.h_items, sizeof(ItemDesc) * ni, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      s = MLMC_ECUDA;
+      break;
+    }
+    if ((s = plan_launch_impl(pl, st)) != MLMC_OK) break;
+    float ms = 0.0f;
+    if (cudaMemcpyAsync(A.h_out, pl->d_out, sizeof(DevSums) * n_work, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess || cudaEventElapsedTime(&ms, pl->t0, pl->t1) != cudaSuccess) {
+      s = MLMC_ECUDA;
+      break;
+    }
+    convert_results(pl, A.h_out, ms, out);
+  } while (0);
   free_plan_device(pl);
   delete pl;
   return s;
