@@ -1128,9 +1128,10 @@ mlmc_status plan_launch_impl(mlmc_plan *pl, cudaStream_t st) {
     a.rk = pl->rk;
     a.counters = pl->d_counters + L.item_off;
     a.out = pl->d_out;
-    CK(cudaEventRecord(pl->kstart[i], ls));
+    // per-kernel events only for plans a caller owns (mlmc_plan_kernel_time)
+    if (!pl->borrowed) CK(cudaEventRecord(pl->kstart[i], ls));
     CK(launch_by_family(L.family, L.scheme, L.pc, dim3(L.n_chunks), dim3(L.threads), L.smem, ls, a, nullptr));
-    CK(cudaEventRecord(pl->kstop[i], ls));
+    if (!pl->borrowed) CK(cudaEventRecord(pl->kstop[i], ls));
     if (fork) {
       CK(cudaEventRecord(pl->join[i], ls));
       CK(cudaStreamWaitEvent(st, pl->join[i], 0));
