@@ -596,17 +596,17 @@ __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDes
     if constexpr (EST == EST_APPROX && AP == AP_FX32 && PC == PC_TERMINAL) acc.flush_group();
   }
   block_reduce_write<EST, XP>(acc, args.partials + gc);
-  if (args.counters) {
+  if (args.counters && threadIdx.x < 32) {
     // the CTA that completes the item's last chunk sums all its partials, in
-    // chunk order (the partials of other CTAs are read through L2)
-    __shared__ int s_last;
+    // chunk order (the partials of other CTAs are read through L2); only its
+    // first warp takes part, the other warps are done
+    uint32_t last = 0;
     if (threadIdx.x == 0) {
       __threadfence();
-      const uint32_t done = atomicAdd(args.counters + item, 1u) + 1u;
-      s_last = done == it.n_chunks;
+      last = atomicAdd(args.counters + item, 1u) + 1u == it.n_chunks;
     }
-    __syncthreads();
-    if (s_last && threadIdx.x < 32) {
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (last) {
       __threadfence();
       const DevSums r = warp_sum_partials<true>(args.partials + it.chunk_begin, it.n_chunks);
       if (threadIdx.x == 0) {
