@@ -464,6 +464,10 @@ void default_format(const mlmc_params *p, int level, mlmc_format *out) {
   const double h = T / (double)(1LL << level);
   int f[7] = {12, 16 + level, 14 + level, 12 + level, 12 + level, 12 + level, 14 + level};
   for (int i = 0; i < 7; ++i) f[i] = std::min(24, std::max(10, f[i]));
+  // S keeps at most 21 fractional bits (the 32-bit datapath holds e_S + f_S <= 30
+  // for the test case), mul2 no more than S
+  f[F_S] = std::min(f[F_S], 21);
+  f[F_MUL2] = std::min(f[F_MUL2], f[F_S]);
   const double mul1_bound = std::max(16.0 * sig * std::sqrt(h), 128.0 * sig * sig * h);
   int e[7];
   e[F_Z] = 3;
@@ -668,6 +672,13 @@ mlmc_status chunk_built(BuiltItem &b, int threads, int spt) {
   return MLMC_OK;
 }
 
+// Packed draws of an item with fewer packs than one wave of resident threads
+// run one sample per thread: latency rather than throughput bounds such items.
+bool lane_split(uint64_t N) {
+  const uint64_t wave = 6ULL * 128ULL * (uint64_t)std::max(1, g.num_sms);
+  return N > 0 && (N + 2) / 3 < wave;
+}
+
 mlmc_status build_item(const mlmc_work &w, int out_index, void *dump, BuiltItem &b, double &disc, int &unit,
                        int &exact_int) {
   const mlmc_params *p = w.params;
@@ -707,6 +718,12 @@ mlmc_status build_item(const mlmc_work &w, int out_index, void *dump, BuiltItem 
     it.enumerate = 1;
   }
   if (KP == 0) return MLMC_EINVAL;
+  if (KP == 3 && lev >= 2 && lane_split(w.N)) {
+    // few samples: one sample per thread (three times the threads), the same
+    // packed draws (sample s reads lane s mod 3 of pack s / 3)
+    KP = 1;
+    it.lanes = 3;
+  }
   // sample groups (chunking into CTAs: chunk_built)
   const uint64_t spc = samples_per_group(lev, KP);
   it.g0 = w.first_sample / spc;
@@ -853,6 +870,8 @@ mlmc_status build_item_cached(const mlmc_work &w, int out_index, void *dump, Bui
   if (has_fmt == 1) put(&p->formats[w.level], sizeof(mlmc_format));
   put(&w.level, sizeof(int32_t) * 2);     // level, variant
   put(&w.stream, sizeof(int32_t));
+  const int split = lane_split(w.N) ? 1 : 0;   // the packed-draw layout depends on N
+  put(&split, sizeof split);
   auto f = g_item_cache.find(key);
   if (f == g_item_cache.end()) {
     mlmc_status s = build_item(w, out_index, dump, b, disc, unit, exact_int);

@@ -71,6 +71,8 @@ struct ItemDesc {
   uint32_t ctr2, ctr3;     // Philox counter words 2 and 3: level | stream << 8, request
   int32_t unit;            // approximate payoff unit exponent
   int32_t enumerate;       // 1: table indices enumerate samples instead of Philox draws
+  int32_t lanes;           // 3: packed draws with one sample per thread (sample s reads lane s mod 3
+                           // of pack s / 3); levels >= 2, approximate-only, KP = 1 kernels
   float unit_scale;        // 2^-unit (FP32, correction estimators)
   // exact path constants
   float c1f, c2f, c1cf, c3f, S0f, Kf;

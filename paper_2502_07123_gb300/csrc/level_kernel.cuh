@@ -535,7 +535,14 @@ __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDes
     const uint64_t g = gbeg + r;
     const bool full = g >= gf0 && g < gf1;
     if (lev >= 2) {
-      const uint64_t P = g;
+      uint64_t P = g;
+      uint32_t lsh = 0;   // lane-split packed draws: this sample's field to the top of the word
+      if constexpr (KP == 1 && EST == EST_APPROX) {
+        if (it.lanes > 1) {
+          P = g / 3u;
+          lsh = (uint32_t)it.d * (uint32_t)(g - P * 3u);
+        }
+      }
       const uint32_t calls = 1u << (lev - 2);
       const uint64_t qbase = P * calls;
       sim.begin();
@@ -543,14 +550,14 @@ __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDes
         const uint64_t q = qbase + c;
         const uint4 w = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), ctr_hi.z, ctr_hi.w), args.rk);
         const int i0 = (int)(c << 2);
-        sim.template step<true, 0>(w.x, i0);
-        sim.template step<true, 1>(w.y, i0 + 1);
-        sim.template step<true, 0>(w.z, i0 + 2);
-        sim.template step<true, 1>(w.w, i0 + 3);
+        sim.template step<true, 0>(w.x << lsh, i0);
+        sim.template step<true, 1>(w.y << lsh, i0 + 1);
+        sim.template step<true, 0>(w.z << lsh, i0 + 2);
+        sim.template step<true, 1>(w.w << lsh, i0 + 3);
       }
 #pragma unroll
       for (int l = 0; l < KP; ++l) {
-        const uint64_t s = P * KP + l;
+        const uint64_t s = KP == 1 ? g : P * KP + l;
         const bool valid = full || (s >= first && s < last);
         sim.finish(acc, l, valid, dump && valid ? dump + (s - first) : nullptr);
       }

@@ -54,7 +54,7 @@ def default_format(p: dict, level: int) -> dict:
     this is a stated schedule: fractional bits grow by one per level (the
     d_S,l+1 = d_S,l + 1 trend of Sec. 6.3) and follow the size ordering of
     Sec. 6.3 (con1 ~ h, con2/mul1/sum1/mul2 ~ sqrt(h), S ~ 1), clamped to
-    [10, 24].  Integer bits bound each variable's magnitude (for the rounded
+    [10, 24], with S (and mul2) capped at 21 fractional bits.  Integer bits bound each variable's magnitude (for the rounded
     constants con1, con2, S0 and K: their values rounded to f bits):
       Z     : |Z~| < 8 for every table size d <= 16 (coarse sums are exact),
       con1  : max(|r| 2h, sigma^2 h / 2) (the Milstein constant shares it),
@@ -76,6 +76,10 @@ def default_format(p: dict, level: int) -> dict:
         "S": 14 + level,
     }
     f = {k: min(24, max(10, v)) for k, v in f.items()}
+    # S keeps at most 21 fractional bits (the 32-bit fixed-point datapath holds
+    # e_S + f_S <= 30 for the test case's e_S = 9), mul2 no more than S
+    f["S"] = min(f["S"], 21)
+    f["mul2"] = min(f["mul2"], f["S"])
     mul1_bound = max(16.0 * sig * math.sqrt(h), 128.0 * sig * sig * h)
     e = {
         "Z": 3,
