@@ -214,6 +214,7 @@ def main():
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     kern_ms = {}
+    launch_ms = {}
     with ClockSampler(local) as clocks:
         barrier()
         t_wall = time.perf_counter()
@@ -225,6 +226,7 @@ def main():
             for j in range(info["kernels"]):
                 fam, ms = plan.kernel_time(j)
                 kern_ms.setdefault(fam, []).append(ms)
+                launch_ms.setdefault(j, []).append(ms)
         barrier()
         t_wall = time.perf_counter() - t_wall
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
@@ -249,28 +251,27 @@ def main():
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_value = info["path_steps"] / (statistics.median(e2e_ms) * 1e-3)
 
-    # roofline of the dominant kernel: the approximate fixed-point estimator with a
-    # 32-bit S (family 15 packed / 8: levels 0-7 of the workload; level 8 needs a
-    # 64-bit S), the approximate fixed-point family with the most work
-    # (the largest share of the serialised launch list); per-launch event times of
-    # kernels that overlap on forked streams do not rank them
-    fams = [f for f in (15, 8, 2) if f in kern_ms]
-    dom = fams[0] if fams else max(kern_ms, key=lambda f: sum(kern_ms[f]))
-    dom_ms = sum(kern_ms[dom]) / len(kern_ms[dom])
-    fam_steps = {8: sum(it["N"] << it["level"] for it in items
-                        if it["variant"] == m.FIXED_APPROX and it["level"] <= 7),
-                 2: sum(it["N"] << it["level"] for it in items if it["variant"] == m.FIXED_APPROX)}
-    fam_steps[15] = fam_steps[8]
-    fam_names = {8: "level_kernel<APPROX,F32,FX32,EM,terminal>", 2: "level_kernel<APPROX,F32,FIXED,EM,terminal>",
-                 15: "level_kernel<APPROX,F32,FX32,EM,terminal,packed x3>"}
+    # roofline of the dominant kernel: the launch of an approximate fixed-point
+    # family (15 packed / 8 one sample per thread, 32-bit S; 12 / 2 general)
+    # with the most path-steps, which holds the largest share of the serialised
+    # launch list; per-launch event times of kernels that overlap on forked
+    # streams do not rank them
+    fam_names = {15: "level_kernel<APPROX,F32,FX32,EM,terminal,packed x3>",
+                 8: "level_kernel<APPROX,F32,FX32,EM,terminal>",
+                 12: "level_kernel<APPROX,F32,FIXED,EM,terminal,packed x3>",
+                 2: "level_kernel<APPROX,F32,FIXED,EM,terminal>"}
+    launches = [plan.launch_info(j) for j in range(info["kernels"])]
+    cand = [(ps, j, fam) for j, (fam, _, _, ps) in enumerate(launches) if fam in fam_names]
     roofline = None
-    if dom in fam_steps:
-        achieved = OPS_APPROX_FIXED_EM * fam_steps[dom] / (dom_ms * 1e-3) / 1e12
+    if cand:
+        ps, j, dom = max(cand)
+        dom_ms = sum(launch_ms[j]) / len(launch_ms[j])
+        achieved = OPS_APPROX_FIXED_EM * ps / (dom_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Top/s",
                     "frac": achieved / ALU_PEAK_TOPS, "traffic": None,
                     "kernel": fam_names[dom],
                     "ms_per_launch": dom_ms, "ops_per_path_step": OPS_APPROX_FIXED_EM,
-                    "path_steps_per_launch": fam_steps[dom]}
+                    "path_steps_per_launch": ps}
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -462,7 +463,7 @@ def _engine_solve(eng, P, eps, mode, seed):
             return r
 
 
-def time_to_eps(m, torch, eps=1e-3, seeds=(1, 2, 3)):
+def time_to_eps(m, torch, eps=1e-3, seeds=tuple(range(1, 12))):
     """Wall time of mlmc_estimate at RMS error eps: nested fixed point vs plain FP32 (European call)."""
     p = W.params()
     P = m.make_params(p, d=10, method=1, formats=[W.default_format(p, lev) for lev in range(11)], rng_pack=1)

@@ -227,6 +227,11 @@ mlmc_status mlmc_plan_info(const mlmc_plan *plan, int *kernels, uint64_t *ctas,
  * fixed / binary16 / bfloat16).  Waits for that kernel.  MLMC_ENOTREADY before
  * the first launch, MLMC_EINVAL for k out of range. */
 mlmc_status mlmc_plan_kernel_time(const mlmc_plan *plan, int k, int *family, double *ms);
+/* Level-kernel launch k of the plan (0 <= k < kernels of mlmc_plan_info):
+ * its kernel family, work items, CTAs and fine path-steps (sum of N 2^l over
+ * its items); any output may be NULL.  MLMC_EINVAL for k out of range. */
+mlmc_status mlmc_plan_launch_info(const mlmc_plan *plan, int k, int *family, int *items, uint64_t *ctas,
+                                  uint64_t *path_steps);
 void mlmc_plan_destroy(mlmc_plan *plan);
 
 /* Host-buffer convenience: create, launch on `stream`, read results, destroy. */

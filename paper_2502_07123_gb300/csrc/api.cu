@@ -1357,6 +1357,24 @@ mlmc_status mlmc_plan_info(const mlmc_plan *plan, int *kernels, uint64_t *ctas, 
   return MLMC_OK;
 }
 
+mlmc_status mlmc_plan_launch_info(const mlmc_plan *plan, int k, int *family, int *items, uint64_t *ctas,
+                                  uint64_t *path_steps) {
+  if (!plan || k < 0 || k >= (int)plan->launches.size()) return MLMC_EINVAL;
+  const LaunchRec &L = plan->launches[k];
+  if (family) *family = L.family;
+  if (items) *items = L.n_items;
+  if (ctas) *ctas = L.n_chunks;
+  if (path_steps) {
+    uint64_t ps = 0;
+    for (int i = 0; i < L.n_items; ++i) {
+      const ItemDesc &it = plan->items[L.item_off + i];
+      ps += it.N << it.level;
+    }
+    *path_steps = ps;
+  }
+  return MLMC_OK;
+}
+
 mlmc_status mlmc_plan_kernel_time(const mlmc_plan *plan, int k, int *family, double *ms) {
   if (!plan || k < 0 || k >= (int)plan->launches.size()) return MLMC_EINVAL;
   if (!plan->launched) return MLMC_ENOTREADY;

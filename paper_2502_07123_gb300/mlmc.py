@@ -120,6 +120,8 @@ def load():
         "mlmc_plan_info": (st, [ctypes.c_void_p, P(ctypes.c_int), P(ctypes.c_uint64), P(ctypes.c_uint64),
                                 P(ctypes.c_uint64), P(ctypes.c_uint64)]),
         "mlmc_plan_kernel_time": (st, [ctypes.c_void_p, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_double)]),
+        "mlmc_plan_launch_info": (st, [ctypes.c_void_p, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int),
+                                       P(ctypes.c_uint64), P(ctypes.c_uint64)]),
         "mlmc_plan_destroy": (None, [ctypes.c_void_p]),
         "mlmc_run": (st, [P(Work), ctypes.c_int, ctypes.c_uint64, P(Tuning), P(Sums), ctypes.c_void_p]),
         "mlmc_estimate": (st, [ctypes.c_double, P(Params), ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
@@ -290,6 +292,14 @@ class Plan:
         _check(load().mlmc_plan_info(self._h, ctypes.byref(k), ctypes.byref(c), ctypes.byref(ps),
                                      ctypes.byref(hb), ctypes.byref(db)), "mlmc_plan_info")
         return dict(kernels=k.value, ctas=c.value, path_steps=ps.value, h2d_bytes=hb.value, d2h_bytes=db.value)
+
+    def launch_info(self, k):
+        """(family, items, ctas, path_steps) of level-kernel launch k."""
+        fam, items = ctypes.c_int(), ctypes.c_int()
+        ctas, ps = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load().mlmc_plan_launch_info(self._h, k, ctypes.byref(fam), ctypes.byref(items), ctypes.byref(ctas),
+                                            ctypes.byref(ps)), "mlmc_plan_launch_info")
+        return fam.value, items.value, ctas.value, ps.value
 
     def kernel_time(self, k):
         """(family, ms) of level kernel k of the last launch (CUDA events on its stream)."""
