@@ -305,7 +305,8 @@ mlmc_status mlmc_estimate(double eps, const mlmc_params *p, int mode, uint64_t s
  * params.  Errors: MLMC_EINVAL for bad arguments (params->formats, when
  * given, must cover levels 0..max_level), MLMC_ENOMEM, MLMC_ECUDA; a request
  * that cannot be admitted (for instance a format its constants do not fit,
- * or more than 32 launch classes) completes with that status from
+ * or more than 32 launch classes among the requests holding slots) completes
+ * with that status from
  * mlmc_engine_poll and a NaN price. */
 typedef struct {
   int32_t max_slots;             /* concurrent requests (0 = 256)                 */

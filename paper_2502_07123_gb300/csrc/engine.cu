@@ -547,13 +547,23 @@ mlmc_status group_of(mlmc_engine *e, const BuiltItem &b, int threads, uint64_t s
       return MLMC_OK;
     }
   }
-  if ((int)e->groups.size() >= GMAX) return MLMC_EINVAL;
   Group G;
   G.family = b.family; G.scheme = b.scheme; G.pc = b.pc; G.threads = threads; G.smem = b.smem; G.seed = seed;
   make_round_keys(seed, G.rk);
-  e->groups.push_back(G);
-  *gi = (int)e->groups.size() - 1;
-  return MLMC_OK;
+  if ((int)e->groups.size() < GMAX) {
+    e->groups.push_back(G);
+    *gi = (int)e->groups.size() - 1;
+    return MLMC_OK;
+  }
+  // all slots taken: reuse one that no admitted request refers to any more
+  for (int i = 0; i < (int)e->groups.size(); ++i)
+    if (e->groups[i].refs == 0) {
+      e->groups[i] = G;
+      e->dirty = true;
+      *gi = i;
+      return MLMC_OK;
+    }
+  return MLMC_EINVAL;
 }
 
 // Admit request idx into free slot sl: templates, metadata and initial state.

@@ -170,3 +170,16 @@ def test_engine_rejects_unfit_request_without_failing_others(m):
     res = _run(eng, [r_ok])
     eng.close()
     assert math.isfinite(res[r_ok]["price"])
+
+
+def test_engine_reuses_launch_classes_across_seeds(m):
+    """Launch classes include the seed: an engine serving one request at a time
+    with 40 different seeds reuses the classes of finished requests."""
+    p = W.params()
+    eng = m.Engine(max_slots=1, max_level=10)
+    for seed in range(40):
+        rid = eng.submit(_P(m, p, 1), 0.05, 5, 1000 + seed)
+        res = _run(eng, [rid])[rid]
+        assert math.isfinite(res["price"])
+    assert eng.graph_info()["groups"] <= 32
+    eng.close()
