@@ -594,10 +594,18 @@ mlmc_status admit(mlmc_engine *e, int sl, size_t idx, cudaStream_t st) {
       double disc;
       int unit, ei;
       mlmc_status s = build_item(w, 0, nullptr, b, disc, unit, ei);
-      if (s != MLMC_OK) return s;
-      int th, sp, gi;
-      tuning_for(b.family, b.scheme, b.pc, l, &th, &sp);
-      if ((s = group_of(e, b, th, r.seed, &gi)) != MLMC_OK) return s;
+      int th, sp, gi = -1;
+      if (s == MLMC_OK) {
+        tuning_for(b.family, b.scheme, b.pc, l, &th, &sp);
+        s = group_of(e, b, th, r.seed, &gi);
+      }
+      if (s != MLMC_OK) {
+        for (int g2 : gl) e->groups[g2].refs -= 1;   // release what this admission took
+        return s;
+      }
+      // hold the class at once, so that a later template of this request cannot reuse it
+      Group &G = e->groups[gi];
+      if (G.refs++ == 0 && !G.in_graph) e->dirty = true;
       const int t = l * 2 + k;
       tm[t] = b.it;
       TmplMeta &m = meta[t];
@@ -605,10 +613,6 @@ mlmc_status admit(mlmc_engine *e, int sl, size_t idx, cudaStream_t st) {
       m.unit = unit; m.exact_int = ei; m.level = l; m.est = k; m.disc = disc;
       gl.push_back(gi);
     }
-  for (int gi : gl) {
-    Group &G = e->groups[gi];
-    if (G.refs++ == 0 && !G.in_graph) e->dirty = true;
-  }
   e->slot_groups[sl] = gl;
   SlotState h;
   std::memset(&h, 0, sizeof h);
