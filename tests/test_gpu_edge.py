@@ -1,0 +1,112 @@
+"""Edge cases through the C ABI against the oracle: empty and one-sample
+items, the deepest levels, the smallest and largest table sizes, a
+zero-volatility market (every sample identical; zero variance; the
+adaptive driver must still terminate on the deterministic price), a zero
+strike, and the size limits (rejected before any launch)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import core
+from paper_2502_07123_gb300 import workloads as W
+from tests.gpu_helpers import compare_samples
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def m():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2502_07123_gb300 import mlmc
+    return mlmc
+
+
+def _P(m, p, lev_max=12, d=10, method=1, pack=0):
+    return m.make_params(p, d=d, method=method, formats=[W.default_format(p, k) for k in range(lev_max + 1)],
+                         rng_pack=pack)
+
+
+def test_empty_items_and_single_samples(m):
+    p = W.params()
+    P = _P(m, p)
+    items = [dict(params=P, level=3, variant=W.FIXED_APPROX, N=0),
+             dict(params=P, level=2, variant=W.CORR_FIXED, N=1, first_sample=77),
+             dict(params=P, level=0, variant=W.FP32_EXACT, N=0),
+             dict(params=P, level=5, variant=W.FIXED_APPROX, N=1, first_sample=5)]
+    for _ in range(2):                         # twice: the per-item counters reset
+        r = m.mlmc_run(items, 31)
+        assert r[0]["n"] == 0 and r[0]["sum"] == 0.0 and r[0]["isum"] == 0 and r[0]["sum2"] == 0.0
+        assert r[2]["n"] == 0 and r[2]["sum"] == 0.0
+        o1, _ = core.level(p, 2, 77, 1, core.CORR_FIXED, 31, fmt=W.default_format(p, 2))
+        o3, _ = core.level(p, 5, 5, 1, core.FIXED_APPROX, 31, fmt=W.default_format(p, 5))
+        assert r[3]["isum"] == o3["isum"]
+        assert r[1]["sum"] == pytest.approx(math.exp(-p["r"] * p["T"]) * o1["sum"], rel=1e-4, abs=1e-6)
+    assert m.mlmc_level(4, 0, P, W.FP32_EXACT, 1)["sum"] == 0.0
+
+
+@pytest.mark.parametrize("level", [10, 12])
+@pytest.mark.parametrize("variant", [core.FP32_EXACT, core.FIXED_APPROX, core.CORR_FIXED, core.FP16_APPROX])
+def test_deep_levels(m, level, variant):
+    p = W.params(payoff=W.EURO)
+    fm = [W.default_format(p, k) for k in range(level + 1)]
+    P = m.make_params(p, d=10, method=1, formats=fm)
+    _, od = core.level(p, level, 3, 40, variant, 8, fmt=fm[level], dump=True)
+    _, gd = m.mlmc_level_dump(level, 40, P, variant, 8, 3)
+    compare_samples(variant, p, gd, od)
+
+
+@pytest.mark.parametrize("d", [2, 3, 14])
+@pytest.mark.parametrize("variant", [core.FIXED_APPROX, core.CORR_FIXED, core.CORR_FP16])
+def test_table_size_extremes(m, d, variant):
+    p = W.params(payoff=W.DIGITAL)
+    fm = [W.default_format(p, k) for k in range(3)]
+    P = m.make_params(p, d=d, method=1, formats=fm)
+    _, od = core.level(p, 2, 0, 500, variant, 12, d=d, fmt=fm[2], dump=True)
+    _, gd = m.mlmc_level_dump(2, 500, P, variant, 12, 0)
+    compare_samples(variant, p, gd, od)
+
+
+def test_zero_volatility(m):
+    """sigma = 0: every path is S0 (1 + r h)^n; corrections and level variances vanish
+    on the exact path, and the adaptive driver stops at the deterministic price."""
+    p = W.params(sigma=0.0)
+    P = _P(m, p, 10)
+    g = m.mlmc_level_dump(3, 64, P, W.FP32_EXACT, 5)[1]
+    sf = p["S0"] * (1 + p["r"] / 8) ** 8
+    np.testing.assert_allclose(g["sf"], sf, rtol=1e-6)
+    assert np.all(g["sf"] == g["sf"][0])
+    _, od = core.level(p, 3, 0, 64, core.CORR_FIXED, 5, fmt=W.default_format(p, 3), dump=True)
+    _, gd = m.mlmc_level_dump(3, 64, P, W.CORR_FIXED, 5)
+    compare_samples(core.CORR_FIXED, p, gd, od)
+    for mode in (1, 2, 5):
+        r = m.mlmc_estimate(1e-3, P, mode, 3, 10)
+        L = r["L"]
+        exact_em = math.exp(-p["r"] * p["T"]) * max(p["S0"] * (1 + p["r"] / 2 ** L) ** (2 ** L) - p["K"], 0.0)
+        assert math.isfinite(r["price"]) and r["stderr"] < 1e-3
+        assert abs(r["price"] - exact_em) < 2e-3, (mode, r, exact_em)
+
+
+def test_zero_strike(m):
+    """K = 0: the call is the forward; E[e^{-rT} S_N] = S0 (1 + r h)^N e^{-rT} on level L."""
+    p = W.params(K=0.0)
+    P = _P(m, p, 10)
+    r = m.mlmc_estimate(0.02, P, 5, 9, 10)
+    assert abs(r["price"] - p["S0"]) < 4 * r["stderr"] + 0.02
+
+
+def test_size_limits_rejected(m):
+    P = _P(m, W.params())
+    with pytest.raises(m.MLMCError) as e:
+        m.mlmc_level(2, (1 << 58) + 1, P, W.FP32_EXACT, 1)
+    assert e.value.status == m.EINVAL
+    with pytest.raises(m.MLMCError) as e:
+        m.mlmc_level(10, 100, P, W.FP32_EXACT, 1, first_sample=(1 << 50))
+    assert e.value.status == m.EINVAL
+    with pytest.raises(m.MLMCError) as e:
+        m.mlmc_level(21, 100, P, W.FP32_EXACT, 1)
+    assert e.value.status == m.EINVAL
