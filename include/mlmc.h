@@ -312,7 +312,10 @@ typedef struct {
   int32_t max_slots;             /* concurrent requests (0 = 256)                 */
   int32_t max_level;             /* L_max of every request, 2..20                 */
   uint64_t device_bytes_budget;  /* bytes of per-slot device memory, 0 = any      */
-  int32_t iters_per_launch;      /* engine iterations per graph launch, 0..64 (0 = 1) */
+  int32_t iters_per_launch;      /* engine iterations per graph launch, 1..64 (0 = 1);
+                                    -n (n <= 4096): one launch iterates on the device
+                                    (a conditional WHILE graph node) until no admitted
+                                    request is left running, at most n iterations */
   int32_t reserved;              /* must be 0 */
 } mlmc_engine_config;
 typedef struct mlmc_engine mlmc_engine;
@@ -320,7 +323,11 @@ mlmc_status mlmc_engine_create(mlmc_engine **e, const mlmc_engine_config *cfg);
 /* Copies *p (and its format table); mode as mlmc_estimate. */
 mlmc_status mlmc_engine_submit(mlmc_engine *e, const mlmc_params *p, double eps, int mode, uint64_t seed,
                                uint64_t *req_id);
-/* One graph launch on `stream` (synchronous; NULL = the default stream).
+/* One graph launch on `stream` (synchronous; NULL = the default stream); with
+ * a negative iters_per_launch the launch runs until every request admitted
+ * by this step has completed (or the partial array must grow, or the
+ * iteration cap is reached), so requests submitted meanwhile wait for the
+ * next step.
  * *active = requests holding a slot after the step, *queued = requests
  * waiting for one (either may be NULL). */
 mlmc_status mlmc_engine_step(mlmc_engine *e, void *stream, int *active, int *queued);
@@ -341,7 +348,8 @@ void mlmc_engine_destroy(mlmc_engine *e);
 /* Batched adaptive MLMC: n independent requests (params[i], eps[i]), all in
  * `mode` with `seed` (distinct params[i].request_id), run to completion in one
  * engine of n slots: every graph launch covers iters_per_launch iterations of
- * all requests.  Outputs (host arrays of n; stderr_out and L may be NULL):
+ * all requests (negative: the whole run in one launch, a device-side loop;
+ * see mlmc_engine_config).  Outputs (host arrays of n; stderr_out and L may be NULL):
  * price, standard error, final level; *launches = graph launches (may be
  * NULL).  Each result equals what mlmc_estimate returns for that request.
  * Errors as the engine functions; MLMC_ETIMEOUT after 100000 launches. */

@@ -411,6 +411,7 @@ struct mlmc_engine {
   unsigned long long *d_run_n = nullptr;
   DynLaunch *d_dyn = nullptr;
   EngStatus *d_status = nullptr;
+  uint32_t *d_iter = nullptr;                  // iterations of the running launch (loop control)
   Partial *d_partials = nullptr;
   unsigned long long cap_chunks = 0;
   // pinned host copies of the reports
@@ -452,9 +453,114 @@ void release(mlmc_engine *e) {
   if (e->cs) cudaStreamDestroy(e->cs);
   cudaFree(e->d_slots); cudaFree(e->d_rep); cudaFree(e->d_tmpl); cudaFree(e->d_run); cudaFree(e->d_meta);
   cudaFree(e->d_tnch); cudaFree(e->d_run_nch); cudaFree(e->d_run_cb); cudaFree(e->d_run_src); cudaFree(e->d_run_n);
-  cudaFree(e->d_dyn); cudaFree(e->d_status); cudaFree(e->d_partials);
+  cudaFree(e->d_dyn); cudaFree(e->d_status); cudaFree(e->d_partials); cudaFree(e->d_iter);
   if (e->h_rep) cudaFreeHost(e->h_rep);
   if (e->h_status) cudaFreeHost(e->h_status);
+}
+
+// One engine iteration, enqueued on the capture stream e->cs (live: the launch
+// classes in the graph).
+cudaError_t enqueue_iteration(mlmc_engine *e, const std::vector<int> &live) {
+  const int n_tmpl = e->max_slots * e->il;
+  sched_kernel<<<1, 1024, 0, e->cs>>>(e->d_slots, e->d_meta, n_tmpl, e->il, (int)e->groups.size(), e->cap_chunks,
+                                      e->num_sms, e->d_tnch, e->d_run_src, e->d_run_nch, e->d_run_cb, e->d_dyn,
+                                      e->d_status);
+  fill_kernel<<<(n_tmpl + 127) / 128, 128, 0, e->cs>>>(e->d_slots, e->d_meta, e->d_tmpl, e->il, e->num_sms,
+                                                       e->d_run_src, e->d_run_nch, e->d_run_cb, e->d_status,
+                                                       e->d_run, e->d_run_n);
+  cudaError_t err = cudaEventRecord(e->fork, e->cs);
+  for (size_t i = 0; i < live.size() && err == cudaSuccess; ++i) {
+    const Group &G = e->groups[live[i]];
+    cudaStream_t ls = e->aux[i];
+    LaunchArgs a;
+    a.items = e->d_run;
+    a.n_items = 0;
+    a.chunk0 = 0;
+    a.partials = e->d_partials;
+    a.rk = G.rk;
+    a.dyn = e->d_dyn + live[i];
+    a.counters = nullptr;   // acc_kernel sums the partials
+    a.out = nullptr;
+    if ((err = cudaStreamWaitEvent(ls, e->fork, 0)) != cudaSuccess) break;
+    if ((err = launch_by_family(G.family, G.scheme, G.pc, dim3(G.grid), dim3(G.threads), G.smem, ls, a,
+                                nullptr)) != cudaSuccess)
+      break;
+    if ((err = cudaEventRecord(e->join[i], ls)) != cudaSuccess) break;
+    err = cudaStreamWaitEvent(e->cs, e->join[i], 0);
+  }
+  if (err != cudaSuccess) return err;
+  acc_kernel<<<(n_tmpl + 3) / 4, 128, 0, e->cs>>>(e->d_slots, e->d_meta, e->il, e->d_run_src, e->d_run_nch,
+                                                  e->d_run_cb, e->d_run_n, e->d_partials, e->d_status);
+  decide_kernel<<<(e->max_slots + 127) / 128, 128, 0, e->cs>>>(e->d_slots, e->d_rep, e->max_slots, e->d_status);
+  return cudaGetLastError();
+}
+
+// Copies of the per-slot reports and the status to pinned host memory.
+cudaError_t enqueue_reports(mlmc_engine *e) {
+  cudaError_t err = cudaMemcpyAsync(e->h_rep, e->d_rep, sizeof(SlotReport) * e->max_slots, cudaMemcpyDeviceToHost,
+                                    e->cs);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(e->h_status, e->d_status, sizeof(EngStatus), cudaMemcpyDeviceToHost, e->cs);
+  return err;
+}
+
+// Keep iterating while a slot is still active, the partial array sufficed and
+// fewer than `cap` iterations ran in this launch (the counter is zeroed by the
+// host before each launch).
+__global__ void loop_control_kernel(cudaGraphConditionalHandle h, const EngStatus *status, uint32_t *iter,
+                                    uint32_t cap) {
+  const uint32_t k = ++*iter;
+  cudaGraphSetConditional(h, (status->active > 0 && !status->overflow && k < cap) ? 1u : 0u);
+}
+
+// The whole adaptive run as one graph launch: a conditional WHILE node whose
+// body is one iteration plus the loop control, then the report copies.
+mlmc_status capture_until_done(mlmc_engine *e, const std::vector<int> &live) {
+  cudaGraph_t g = nullptr;
+  MLMC_CK(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h;
+  cudaGraphNodeParams cp = {};
+  cudaGraphNode_t cond = nullptr;
+  cudaError_t err = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault);
+  if (err == cudaSuccess) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    err = cudaGraphAddNode(&cond, g, nullptr, nullptr, 0, &cp);
+  }
+  if (err == cudaSuccess) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    err = cudaStreamBeginCaptureToGraph(e->cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (err == cudaSuccess) {
+      cudaError_t e2 = enqueue_iteration(e, live);
+      if (e2 == cudaSuccess) {
+        loop_control_kernel<<<1, 1, 0, e->cs>>>(h, e->d_status, e->d_iter, (uint32_t)(-e->iters));
+        e2 = cudaGetLastError();
+      }
+      cudaGraph_t out = nullptr;
+      err = cudaStreamEndCapture(e->cs, &out);
+      if (e2 != cudaSuccess) err = e2;
+    }
+  }
+  if (err == cudaSuccess) {
+    err = cudaStreamBeginCaptureToGraph(e->cs, g, &cond, nullptr, 1, cudaStreamCaptureModeThreadLocal);
+    if (err == cudaSuccess) {
+      cudaError_t e2 = enqueue_reports(e);
+      cudaGraph_t out = nullptr;
+      err = cudaStreamEndCapture(e->cs, &out);
+      if (e2 != cudaSuccess) err = e2;
+    }
+  }
+  if (err == cudaSuccess) err = cudaGraphInstantiate(&e->exec, g, 0);
+  if (err != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return MLMC_ECUDA;
+  }
+  e->graph = g;
+  e->dirty = false;
+  e->captures += 1;
+  return MLMC_OK;
 }
 
 // Capture `iters` iterations (and the report copies) as one CUDA graph.
@@ -484,46 +590,11 @@ mlmc_status capture(mlmc_engine *e) {
     MLMC_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     e->join.push_back(ev);
   }
-  const int n_tmpl = e->max_slots * e->il;
+  if (e->iters < 0) return capture_until_done(e, live);
   MLMC_CK(cudaStreamBeginCapture(e->cs, cudaStreamCaptureModeThreadLocal));
   cudaError_t err = cudaSuccess;
-  for (int k = 0; k < e->iters && err == cudaSuccess; ++k) {
-    sched_kernel<<<1, 1024, 0, e->cs>>>(e->d_slots, e->d_meta, n_tmpl, e->il, (int)e->groups.size(), e->cap_chunks,
-                                        e->num_sms, e->d_tnch, e->d_run_src, e->d_run_nch, e->d_run_cb, e->d_dyn,
-                                        e->d_status);
-    fill_kernel<<<(n_tmpl + 127) / 128, 128, 0, e->cs>>>(e->d_slots, e->d_meta, e->d_tmpl, e->il, e->num_sms,
-                                                         e->d_run_src, e->d_run_nch, e->d_run_cb, e->d_status,
-                                                         e->d_run, e->d_run_n);
-    err = cudaEventRecord(e->fork, e->cs);
-    for (size_t i = 0; i < live.size() && err == cudaSuccess; ++i) {
-      const Group &G = e->groups[live[i]];
-      cudaStream_t ls = e->aux[i];
-      LaunchArgs a;
-      a.items = e->d_run;
-      a.n_items = 0;
-      a.chunk0 = 0;
-      a.partials = e->d_partials;
-      a.rk = G.rk;
-      a.dyn = e->d_dyn + live[i];
-      a.counters = nullptr;   // acc_kernel sums the partials
-      a.out = nullptr;
-      if ((err = cudaStreamWaitEvent(ls, e->fork, 0)) != cudaSuccess) break;
-      if ((err = launch_by_family(G.family, G.scheme, G.pc, dim3(G.grid), dim3(G.threads), G.smem, ls, a,
-                                  nullptr)) != cudaSuccess)
-        break;
-      if ((err = cudaEventRecord(e->join[i], ls)) != cudaSuccess) break;
-      err = cudaStreamWaitEvent(e->cs, e->join[i], 0);
-    }
-    if (err != cudaSuccess) break;
-    acc_kernel<<<(n_tmpl + 3) / 4, 128, 0, e->cs>>>(e->d_slots, e->d_meta, e->il, e->d_run_src, e->d_run_nch,
-                                                    e->d_run_cb, e->d_run_n, e->d_partials, e->d_status);
-    decide_kernel<<<(e->max_slots + 127) / 128, 128, 0, e->cs>>>(e->d_slots, e->d_rep, e->max_slots, e->d_status);
-    err = cudaGetLastError();
-  }
-  if (err == cudaSuccess)
-    err = cudaMemcpyAsync(e->h_rep, e->d_rep, sizeof(SlotReport) * e->max_slots, cudaMemcpyDeviceToHost, e->cs);
-  if (err == cudaSuccess)
-    err = cudaMemcpyAsync(e->h_status, e->d_status, sizeof(EngStatus), cudaMemcpyDeviceToHost, e->cs);
+  for (int k = 0; k < e->iters && err == cudaSuccess; ++k) err = enqueue_iteration(e, live);
+  if (err == cudaSuccess) err = enqueue_reports(e);
   cudaGraph_t gr = nullptr;
   const cudaError_t end = cudaStreamEndCapture(e->cs, &gr);
   if (err != cudaSuccess || end != cudaSuccess) {
@@ -649,7 +720,7 @@ extern "C" {
 
 mlmc_status mlmc_engine_create(mlmc_engine **out, const mlmc_engine_config *cfg) {
   if (!out || !cfg || cfg->max_level < 2 || cfg->max_level > MAXL - 1) return MLMC_EINVAL;
-  if (cfg->iters_per_launch < 0 || cfg->iters_per_launch > 64 || cfg->reserved != 0) return MLMC_EINVAL;
+  if (cfg->iters_per_launch < -4096 || cfg->iters_per_launch > 64 || cfg->reserved != 0) return MLMC_EINVAL;
   mlmc_status s = ensure_ctx();
   if (s != MLMC_OK) return s;
   const int il = (cfg->max_level + 1) * 2;
@@ -665,7 +736,7 @@ mlmc_status mlmc_engine_create(mlmc_engine **out, const mlmc_engine_config *cfg)
   e->max_slots = slots;
   e->max_level = cfg->max_level;
   e->il = il;
-  e->iters = cfg->iters_per_launch > 0 ? cfg->iters_per_launch : 1;
+  e->iters = cfg->iters_per_launch != 0 ? cfg->iters_per_launch : 1;
   e->num_sms = ctx_num_sms();
   const size_t nt = (size_t)slots * il;
   e->cap_chunks = std::max<unsigned long long>(4ULL * nt, 1ULL << 16);
@@ -673,6 +744,7 @@ mlmc_status mlmc_engine_create(mlmc_engine **out, const mlmc_engine_config *cfg)
             dev_alloc(&e->d_run, nt) && dev_alloc(&e->d_meta, nt) && dev_alloc(&e->d_tnch, nt) &&
             dev_alloc(&e->d_run_nch, nt) && dev_alloc(&e->d_run_cb, nt) && dev_alloc(&e->d_run_src, nt) &&
             dev_alloc(&e->d_run_n, nt) && dev_alloc(&e->d_dyn, GMAX) && dev_alloc(&e->d_status, 1) &&
+            dev_alloc(&e->d_iter, 1) &&
             dev_alloc(&e->d_partials, e->cap_chunks) &&
             cudaHostAlloc((void **)&e->h_rep, sizeof(SlotReport) * slots, cudaHostAllocDefault) == cudaSuccess &&
             cudaHostAlloc((void **)&e->h_status, sizeof(EngStatus), cudaHostAllocDefault) == cudaSuccess &&
@@ -763,6 +835,7 @@ mlmc_status mlmc_engine_step(mlmc_engine *e, void *stream, int *active_out, int 
         const mlmc_status s = capture(e);
         if (s != MLMC_OK) return s;
       }
+      if (e->iters < 0) MLMC_CK(cudaMemsetAsync(e->d_iter, 0, sizeof(uint32_t), st));
       MLMC_CK(cudaGraphLaunch(e->exec, st));
       MLMC_CK(cudaStreamSynchronize(st));
       e->launches += 1;

@@ -183,3 +183,17 @@ def test_engine_reuses_launch_classes_across_seeds(m):
         assert math.isfinite(res["price"])
     assert eng.graph_info()["groups"] <= 32
     eng.close()
+
+
+def test_batch_in_one_device_loop(m):
+    """iters_per_launch < 0: the whole batch runs as one graph launch whose
+    conditional WHILE node iterates on the device until every request is
+    done; the results equal mlmc_estimate's."""
+    opts = W.batched_options(10, seed=8)
+    plist = [_P(m, o, 400 + i) for i, o in enumerate(opts)]
+    eps = [max(o["eps"], 4e-3) * 5 for o in opts]
+    out = m.mlmc_batch_estimate(plist, eps, 5, 17, max_level=10, iters_per_launch=-4096)
+    for i in range(len(opts)):
+        ref = m.mlmc_estimate(eps[i], plist[i], 5, 17, 10)
+        assert out["price"][i] == ref["price"] and out["stderr"][i] == ref["stderr"], i
+    assert out["launches"] <= 3      # one, plus a relaunch per growth of the partial array
