@@ -343,10 +343,11 @@ def _accuracy(done, opts, max_level):
             "max_level": max_level}
 
 
-def batched_run(m, n=256, seed=7, mode=5, iters_per_launch=2, max_level=14):
-    """The batched workload: all n options submitted at once to one engine, every
-    graph launch running iters_per_launch iterations of all of them (what
-    mlmc_batch_estimate does, with the engine's counters kept)."""
+def batched_run(m, n=256, seed=7, mode=5, iters_per_launch=-4096, max_level=14):
+    """The batched workload: all n options submitted at once to one engine; with a
+    negative iters_per_launch the whole adaptive run of all of them is one graph
+    launch iterating on the device (what mlmc_batch_estimate does, with the
+    engine's counters kept)."""
     opts = W.batched_options(n, seed)
     eng = m.Engine(max_slots=n, max_level=max_level, iters_per_launch=iters_per_launch)
     _engine_solve(eng, _engine_params(m, opts[0], 0, max_level), 1e-2, mode, 99)   # warm tables and kernels
