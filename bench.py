@@ -166,6 +166,8 @@ def main():
     ap.add_argument("--no-tte", action="store_true")
     ap.add_argument("--no-serving-sample", action="store_true")
     ap.add_argument("--no-optimiser", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="also run the level-kernel throughput sweep (Milstein; payoffs x variants x levels)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shape (128 threads, 256 path-steps per thread)")
     ap.add_argument("--serving", action="store_true",
@@ -291,6 +293,8 @@ def main():
     }
     if rank == 0 and not args.no_tte:
         out["time_to_eps"] = time_to_eps(m, torch)
+    if rank == 0 and world == 1 and args.sweep:
+        out["sweep"] = sweep_run(m, torch)
     if rank == 0 and world == 1 and not args.no_optimiser:
         out["bitwidth_optimiser"] = optimiser_run(m, torch)
     if rank == 0 and world == 1 and not args.no_serving_sample:
@@ -416,6 +420,37 @@ def serving_run(m, rate, n=400, seed=11, mode=5, max_level=14, eps_range=(1e-4, 
            "path_steps_per_s": (st["path_steps"] - s0["path_steps"]) / wall}
     out.update(_accuracy(done, opts, max_level))
     return out
+
+
+def sweep_run(m, torch, levels=(2, 6, 10), paths=1 << 22, sigmas=(0.1, 0.2, 0.4)):
+    """Level-kernel throughput sweep: Milstein, European / Asian / lookback, the
+    variants of the library, 2^22 paths per point; path-steps/s of one level
+    kernel launch by CUDA events (median of 5 after 2 warm-up launches)."""
+    variants = (("fp64_exact", W.FP64_EXACT), ("fp32_exact", W.FP32_EXACT), ("fp16_approx", W.FP16_APPROX),
+                ("bf16_approx", W.BF16_APPROX), ("fixed_approx", W.FIXED_APPROX),
+                ("nested_corr_fixed", W.CORR_FIXED))
+    rows = []
+    for pay_name, pay in (("euro", W.EURO), ("asian", W.ASIAN), ("lookback", W.LOOKBACK)):
+        for sig in sigmas:
+            p = W.params(payoff=pay, scheme=W.MILSTEIN, sigma=sig)
+            P = m.make_params(p, d=10, method=1, formats=[W.default_format(p, k) for k in range(11)], rng_pack=1)
+            for lev in levels:
+                n = paths if lev < 10 else paths >> 2
+                for vname, v in variants:
+                    if v == W.FP64_EXACT and lev == 10:
+                        n = paths >> 4          # FP64 is slow on this part: a smaller sample
+                    plan = m.Plan([dict(params=P, level=lev, variant=v, N=n)], 7)
+                    for _ in range(2):
+                        plan.launch()
+                    ts = []
+                    for _ in range(5):
+                        plan.launch()
+                        ts.append(plan.kernel_time(0)[1])
+                    plan.close()
+                    ms = statistics.median(ts)
+                    rows.append({"payoff": pay_name, "sigma": sig, "level": lev, "variant": vname, "paths": n,
+                                 "ms": ms, "path_steps_per_s": (n << lev) / (ms * 1e-3)})
+    return {"scheme": "milstein", "rows": rows}
 
 
 def optimiser_run(m, torch, levels=range(9), n_sens=1_000_000, n_check=400_000):
