@@ -601,6 +601,8 @@ bool fast_fixed(const int e[7], const int f[7], int64_t con1, int64_t con1c, int
   if (milstein) {
     const I one = (I)1 << (2 * fZ);
     const I zz_max = zc * zc - one, zz_min = -2 * one;
+    // Z~^2 - m in 32 bits (the kernel forms con3 (Z~^2 - m) as one 32x32 product)
+    if (zc * zc >= ((I)1 << 31) - 1 || 2 * one >= ((I)1 << 31)) return false;
     if ((I)con3 * zz_max + r3 >= ((I)1 << 62) || zc * zc >= ((I)1 << 62)) return false;
     const I a = floor_shift((I)con3 * zz_max + r3, rs3), b = floor_shift((I)con3 * zz_min + r3, rs3);
     mul3_abs = std::max(a < 0 ? -a : a, b < 0 ? -b : b);

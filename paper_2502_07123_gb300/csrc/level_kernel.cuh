@@ -175,8 +175,9 @@ struct LevelSim {
     const int32_t mul1 = (int32_t)(((int64_t)ff.con2 * z + ff.radd1) >> ff.rs1);
     int32_t acc = c1r + mul1 * ff.mulF1;
     if constexpr (MIL) {
-      const int64_t zz = (int64_t)z * z - m;
-      const int32_t mul3 = (int32_t)((ff.con3 * zz + ff.radd3) >> ff.rs3);
+      // |Z~^2 - m| < 2^31 on this datapath (host-checked): one 32 x 32 product
+      const int32_t zz = z * z - (int32_t)m;
+      const int32_t mul3 = (int32_t)(((int64_t)ff.con3 * zz + ff.radd3) >> ff.rs3);
       acc += mul3 * ff.mulF1;
     }
     const int32_t sum1 = acc >> ff.rs_sum1;

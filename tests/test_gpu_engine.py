@@ -197,3 +197,22 @@ def test_batch_in_one_device_loop(m):
         ref = m.mlmc_estimate(eps[i], plist[i], 5, 17, 10)
         assert out["price"][i] == ref["price"] and out["stderr"][i] == ref["stderr"], i
     assert out["launches"] <= 3      # one, plus a relaunch per growth of the partial array
+
+
+@pytest.mark.parametrize("mode", [3, 5, 6])
+def test_engine_mixed_methods_equal_estimate(m, mode):
+    """Requests with Methods 1, 2 and 3 (and packed / unpacked draws) share the
+    engine's launches; each result equals mlmc_estimate's."""
+    p = W.params(payoff=W.EURO)
+    reqs = []
+    for i, (method, pack) in enumerate(((1, 1), (2, 1), (3, 0), (2, 0))):
+        P = m.make_params(p, d=10, method=method, formats=[W.default_format(p, k) for k in range(11)],
+                          request=50 + i, rng_pack=pack)
+        reqs.append(P)
+    eng = m.Engine(max_slots=8, max_level=10)
+    rids = [eng.submit(P, 0.03, mode, 23) for P in reqs]
+    res = _run(eng, rids)
+    eng.close()
+    for P, rid in zip(reqs, rids):
+        ref = m.mlmc_estimate(0.03, P, mode, 23, 10)
+        assert res[rid]["price"] == ref["price"] and res[rid]["stderr"] == ref["stderr"]
