@@ -23,7 +23,10 @@
  *   - A `void *stream` argument is a cudaStream_t (NULL = legacy default stream).
  *   - The library allocates its own device memory (tables, work lists, scratch)
  *     lazily on the current CUDA device and keeps it until process exit.
- *   - Calls from several host threads must be serialised by the caller.
+ *   - Calls may come from several host threads: the entry points that use the
+ *     library's shared state (context, tables, caches, engines) take one
+ *     process-wide lock, so such calls run one at a time (a call that waits
+ *     for the GPU, like mlmc_engine_step, holds it while it waits).
  *   - There is no CPU fallback: without a usable CUDA device every compute
  *     entry point returns MLMC_ECUDA.
  */
@@ -195,9 +198,9 @@ mlmc_status mlmc_level_dump(int level, uint64_t N, const mlmc_params *p, mlmc_va
  * (a cudaStream_t, NULL = legacy default stream) and the call returns after
  * synchronising it; seconds = 0.  The first call on a device looks up the
  * array's device address, so make that first call before any stream capture.
- * Every call overwrites the whole array; calls that overlap on the GPU (from
- * several host threads, or enqueued on different streams) race and must be
- * serialised by the caller.  Errors as mlmc_level. */
+ * Every call overwrites the whole array; calls are serialised by the library
+ * lock and each returns after its stream has finished, so they cannot
+ * overlap on the GPU.  Errors as mlmc_level. */
 mlmc_status mlmc_level_noalloc(int level, uint64_t N, const mlmc_params *p, mlmc_variant v,
                                uint64_t seed, uint64_t first_sample, mlmc_sums *out, void *stream);
 

@@ -11,6 +11,7 @@
 #include <cstdint>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <tuple>
@@ -1252,6 +1253,10 @@ mlmc_status run_sync(const mlmc_work *work, int n_work, uint64_t seed, const mlm
 }
 
 cudaStream_t ctx_stream() { return g.st; }
+std::recursive_mutex &api_mutex() {
+  static std::recursive_mutex m;
+  return m;
+}
 int ctx_num_sms() { return g.num_sms; }
 double cost_of_variant(int variant) { return g_cost[cost_kind_of(variant)]; }
 mlmc_status plan_create_transient(mlmc_plan **out, const mlmc_work *work, int n_work, uint64_t seed,
@@ -1311,6 +1316,7 @@ extern "C" {
 
 mlmc_status mlmc_level(int level, uint64_t N, const mlmc_params *p, mlmc_variant v, uint64_t seed,
                        uint64_t first_sample, mlmc_sums *out) {
+  MLMC_API_LOCK();
   if (!out) return MLMC_EINVAL;
   mlmc_work w;
   std::memset(&w, 0, sizeof w);
@@ -1322,6 +1328,7 @@ mlmc_status mlmc_level(int level, uint64_t N, const mlmc_params *p, mlmc_variant
 
 mlmc_status mlmc_level_dump(int level, uint64_t N, const mlmc_params *p, mlmc_variant v, uint64_t seed,
                             uint64_t first_sample, int32_t stream, mlmc_sample *d_samples, mlmc_sums *out) {
+  MLMC_API_LOCK();
   if (!out || (N > 0 && !d_samples)) return MLMC_EINVAL;
   mlmc_work w;
   std::memset(&w, 0, sizeof w);
@@ -1335,15 +1342,18 @@ mlmc_status mlmc_level_dump(int level, uint64_t N, const mlmc_params *p, mlmc_va
 
 mlmc_status mlmc_plan_create(mlmc_plan **plan, const mlmc_work *work, int n_work, uint64_t seed,
                              const mlmc_tuning *tuning) {
+  MLMC_API_LOCK();
   return plan_create_impl(plan, work, n_work, seed, tuning, nullptr);
 }
 
 mlmc_status mlmc_plan_launch(mlmc_plan *plan, void *stream) {
+  MLMC_API_LOCK();
   if (!plan) return MLMC_EINVAL;
   return plan_launch_impl(plan, (cudaStream_t)stream);
 }
 
 mlmc_status mlmc_plan_results(mlmc_plan *plan, mlmc_sums *out) {
+  MLMC_API_LOCK();
   if (!plan || !out) return MLMC_EINVAL;
   return plan_results_impl(plan, out);
 }
@@ -1391,6 +1401,7 @@ mlmc_status mlmc_plan_kernel_time(const mlmc_plan *plan, int k, int *family, dou
 }
 
 void mlmc_plan_destroy(mlmc_plan *plan) {
+  MLMC_API_LOCK();
   if (!plan) return;
   if (plan->launched) cudaEventSynchronize(plan->t1);
   free_plan_device(plan);
@@ -1398,6 +1409,7 @@ void mlmc_plan_destroy(mlmc_plan *plan) {
 }
 
 mlmc_status mlmc_autotune(const mlmc_work *work, int n_work, uint64_t seed, int reps, mlmc_tuning *chosen) {
+  MLMC_API_LOCK();
   if (!work || n_work <= 0 || reps < 1 || reps > 1000) return MLMC_EINVAL;
   mlmc_status s = ensure_ctx();
   if (s != MLMC_OK) return s;
@@ -1462,15 +1474,20 @@ mlmc_status mlmc_autotune(const mlmc_work *work, int n_work, uint64_t seed, int 
   return MLMC_OK;
 }
 
-void mlmc_tuning_reset(void) { g_tune.clear(); }
+void mlmc_tuning_reset(void) {
+  MLMC_API_LOCK();
+  g_tune.clear();
+}
 
 mlmc_status mlmc_run(const mlmc_work *work, int n_work, uint64_t seed, const mlmc_tuning *tuning,
                      mlmc_sums *out, void *stream) {
+  MLMC_API_LOCK();
   if (!out) return MLMC_EINVAL;
   return run_sync(work, n_work, seed, tuning, nullptr, out, (cudaStream_t)stream);
 }
 
 mlmc_status mlmc_cost_model(int kind, double cost_per_step) {
+  MLMC_API_LOCK();
   if (kind < 0 || kind > 3 || !std::isfinite(cost_per_step)) return MLMC_EINVAL;
   g_cost[kind] = cost_per_step > 0.0 ? cost_per_step : g_cost_default[kind];
   return MLMC_OK;
@@ -1483,6 +1500,7 @@ mlmc_status mlmc_default_format(const mlmc_params *p, int level, mlmc_format *ou
 }
 
 mlmc_status mlmc_icdf_table(int method, int d, int rep, int fZ, double *out) {
+  MLMC_API_LOCK();
   if (method < 1 || method > 3 || d < 2 || d > 14 || rep < 0 || rep > 4 || !out) return MLMC_EINVAL;
   if (rep == REP_FIXED && (fZ < 0 || fZ > 28)) return MLMC_EINVAL;
   if (method == 3 && rep == REP_FP64) return MLMC_EINVAL;
@@ -1509,6 +1527,7 @@ mlmc_status mlmc_icdf_table(int method, int d, int rep, int fZ, double *out) {
 }
 
 mlmc_status mlmc_icdf_method2(int d, double *x, uint32_t *perm, int *iterations) {
+  MLMC_API_LOCK();
   if (d % 2 || d < 4 || d > 14) return MLMC_EINVAL;
   mlmc_status s = ensure_ctx();
   if (s != MLMC_OK) return s;
@@ -1521,6 +1540,7 @@ mlmc_status mlmc_icdf_method2(int d, double *x, uint32_t *perm, int *iterations)
 }
 
 mlmc_status mlmc_philox(const uint32_t *ctr, uint64_t n, uint64_t seed, uint32_t *out) {
+  MLMC_API_LOCK();
   if ((!ctr || !out) && n) return MLMC_EINVAL;
   if (n == 0) return MLMC_OK;
   mlmc_status s = ensure_ctx();
@@ -1601,6 +1621,7 @@ void optimal_counts(const std::vector<double> &V, const std::vector<double> &C, 
 extern "C" mlmc_status mlmc_estimate(double eps, const mlmc_params *p, int mode, uint64_t seed, int max_level,
                                      double *price, double *stderr_out, int *Lout, uint64_t *N_l,
                                      int cap_levels) {
+  MLMC_API_LOCK();
   EstPlan ep;
   if (!(eps > 0.0) || !std::isfinite(eps) || !params_ok(p) || !est_plan(mode, ep)) return MLMC_EINVAL;
   if (max_level < 2 || max_level > 20 || cap_levels <= max_level || !price || !stderr_out || !Lout || !N_l)
@@ -1806,6 +1827,7 @@ int64_t noalloc_zmax(const double *Z, int d, int method, int fZ, const M3Coef &c
 
 extern "C" mlmc_status mlmc_level_noalloc(int level, uint64_t N, const mlmc_params *p, mlmc_variant v,
                                           uint64_t seed, uint64_t first_sample, mlmc_sums *out, void *stream) {
+  MLMC_API_LOCK();
   if (!out || !params_ok(p)) return MLMC_EINVAL;
   if (level < 0 || level > 20 || (int)v < 0 || (int)v > 7) return MLMC_EINVAL;
   if (N > (1ULL << 58) || first_sample > (1ULL << (60 - level)) - N) return MLMC_EINVAL;

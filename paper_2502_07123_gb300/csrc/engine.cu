@@ -719,6 +719,7 @@ void free_slot_groups(mlmc_engine *e, int sl) {
 extern "C" {
 
 mlmc_status mlmc_engine_create(mlmc_engine **out, const mlmc_engine_config *cfg) {
+  MLMC_API_LOCK();
   if (!out || !cfg || cfg->max_level < 2 || cfg->max_level > MAXL - 1) return MLMC_EINVAL;
   if (cfg->iters_per_launch < -4096 || cfg->iters_per_launch > 64 || cfg->reserved != 0) return MLMC_EINVAL;
   mlmc_status s = ensure_ctx();
@@ -772,6 +773,7 @@ mlmc_status mlmc_engine_create(mlmc_engine **out, const mlmc_engine_config *cfg)
 
 mlmc_status mlmc_engine_submit(mlmc_engine *e, const mlmc_params *p, double eps, int mode, uint64_t seed,
                                uint64_t *req_id) {
+  MLMC_API_LOCK();
   int ne, v[2];
   if (!e || !p || !req_id || !params_ok(p) || !(eps > 0.0) || !std::isfinite(eps) || !mode_variants(mode, ne, v))
     return MLMC_EINVAL;
@@ -802,6 +804,7 @@ mlmc_status mlmc_engine_submit(mlmc_engine *e, const mlmc_params *p, double eps,
 }
 
 mlmc_status mlmc_engine_step(mlmc_engine *e, void *stream, int *active_out, int *queued_out) {
+  MLMC_API_LOCK();
   if (!e) return MLMC_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   // 1. admit waiting requests into free slots
@@ -883,6 +886,7 @@ mlmc_status mlmc_engine_step(mlmc_engine *e, void *stream, int *active_out, int 
 
 mlmc_status mlmc_engine_poll(mlmc_engine *e, uint64_t req_id, double *price, double *stderr_out, int *L,
                              int *done, double *latency_s) {
+  MLMC_API_LOCK();
   if (!e) return MLMC_EINVAL;
   auto it = e->by_id.find(req_id);
   if (it == e->by_id.end()) return MLMC_EINVAL;
@@ -899,6 +903,7 @@ mlmc_status mlmc_engine_poll(mlmc_engine *e, uint64_t req_id, double *price, dou
 
 mlmc_status mlmc_engine_stats(const mlmc_engine *e, uint64_t *steps, uint64_t *launches, uint64_t *path_steps,
                               int *slots) {
+  MLMC_API_LOCK();
   if (!e) return MLMC_EINVAL;
   if (steps) *steps = e->steps;
   if (launches) *launches = e->launches;
@@ -909,6 +914,7 @@ mlmc_status mlmc_engine_stats(const mlmc_engine *e, uint64_t *steps, uint64_t *l
 
 mlmc_status mlmc_engine_graph_info(const mlmc_engine *e, int *groups, int *captures, int *iters_per_launch,
                                    uint64_t *partial_capacity) {
+  MLMC_API_LOCK();
   if (!e) return MLMC_EINVAL;
   if (groups) {
     int n = 0;
@@ -922,6 +928,7 @@ mlmc_status mlmc_engine_graph_info(const mlmc_engine *e, int *groups, int *captu
 }
 
 void mlmc_engine_destroy(mlmc_engine *e) {
+  MLMC_API_LOCK();
   if (!e) return;
   if (e->cs) cudaStreamSynchronize(e->cs);
   release(e);
@@ -931,6 +938,7 @@ void mlmc_engine_destroy(mlmc_engine *e) {
 mlmc_status mlmc_batch_estimate(const mlmc_params *params, const double *eps, int n, int mode, uint64_t seed,
                                 int max_level, int iters_per_launch, double *price, double *stderr_out, int *L,
                                 int *launches, void *stream) {
+  MLMC_API_LOCK();
   if (!params || !eps || n <= 0 || !price) return MLMC_EINVAL;
   mlmc_engine_config cfg;
   std::memset(&cfg, 0, sizeof cfg);

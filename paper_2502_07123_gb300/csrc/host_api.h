@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <mutex>
 #include <vector>
 
 #include "item.h"
@@ -19,6 +20,12 @@ namespace mlmc_host {
   } while (0)
 
 struct Arena;
+
+// The library's context (streams, tables, caches, staging buffers, tuning
+// table) is shared by every call: the public entry points hold this lock, so
+// calls from several host threads are serialised.
+std::recursive_mutex &api_mutex();
+#define MLMC_API_LOCK() std::lock_guard<std::recursive_mutex> mlmc_api_lock_(mlmc_host::api_mutex())
 
 // Initialise (once per device) the library's context on the current device.
 mlmc_status ensure_ctx();

@@ -242,6 +242,7 @@ __global__ void sens_finalize_kernel(const SensPartial *part, const double *inst
 
 extern "C" mlmc_status mlmc_sensitivities(int level, uint64_t N, const mlmc_params *p, uint64_t seed,
                                           uint64_t first_sample, mlmc_sensitivity *out, double *inst_out) {
+  MLMC_API_LOCK();
   using namespace mlmc_host;
   if (!out || !p || !params_ok(p) || level < 0 || level > SENS_MAX_LEVEL || N == 0) return MLMC_EINVAL;
   if (p->payoff != MLMC_EURO || p->scheme != MLMC_EULER) return MLMC_EINVAL;

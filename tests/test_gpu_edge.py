@@ -110,3 +110,26 @@ def test_size_limits_rejected(m):
     with pytest.raises(m.MLMCError) as e:
         m.mlmc_level(21, 100, P, W.FP32_EXACT, 1)
     assert e.value.status == m.EINVAL
+
+
+def test_calls_from_several_threads(m):
+    """Concurrent calls from host threads are serialised by the library and give
+    the results of the same calls made one after another."""
+    import threading
+    p = W.params()
+    P = _P(m, p, 8, pack=1)
+    cases = [(lev, v) for lev in (1, 3, 6) for v in (W.FIXED_APPROX, W.CORR_FIXED, W.FP32_EXACT)]
+    seq = [m.mlmc_level(lev, 20_000, P, v, 99) for lev, v in cases]
+    out = [None] * len(cases)
+
+    def work(i):
+        lev, v = cases[i]
+        out[i] = m.mlmc_level(lev, 20_000, P, v, 99)
+
+    ts = [threading.Thread(target=work, args=(i,)) for i in range(len(cases))]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    for a, b in zip(seq, out):
+        assert a["sum"] == b["sum"] and a["sum2"] == b["sum2"]
