@@ -58,9 +58,11 @@ struct TabBytes {
 
 // KP > 1 (approximate-only estimators): KP samples advance in lockstep, lane L
 // reading bits [32 - d(L+1), 32 - dL) of the shared word (packed draws).
-// M3: the item uses Method 3 (line evaluation) instead of a table lookup
-// (Methods 1 and 2); chosen once per chunk, so the step code has no branch on it.
-template <int EST, int XP, int AP, int SCHEME, int PC, int KP = 1, bool M3 = false>
+// MSEL: 0 the item uses a table lookup (Methods 1 and 2), 1 the line
+// evaluation of Method 3, 2 either, chosen per step (only the per-sample
+// dump instantiation); chosen once per chunk, so the hot step code has no
+// branch on the method.
+template <int EST, int XP, int AP, int SCHEME, int PC, int KP = 1, int MSEL = 0>
 struct LevelSim {
   static_assert(KP == 1 || EST == EST_APPROX, "packed draws feed approximate-only estimators");
   static constexpr bool HAS_EXACT = (EST != EST_APPROX);
@@ -213,7 +215,10 @@ struct LevelSim {
   // Approximate Normal of J in Z's fixed-point format: Method 1 reads the
   // signed table at j = top d bits of J; Method 3 evaluates the class line.
   __device__ __forceinline__ int32_t fixed_z(uint32_t J) const {
-    if constexpr (!M3) return ((const int32_t *)smem_tab)[J >> dshift];
+    if constexpr (MSEL == 0) return ((const int32_t *)smem_tab)[J >> dshift];
+    if constexpr (MSEL == 2) {
+      if (method != 3) return ((const int32_t *)smem_tab)[J >> dshift];
+    }
     const ApproxIndex ai = approx_index(J, d);
     int32_t v;
     {
@@ -227,7 +232,10 @@ struct LevelSim {
   }
 
   __device__ __forceinline__ H half_z(uint32_t J) const {
-    if constexpr (!M3) return HO::from_bits(((const uint16_t *)smem_tab)[J >> dshift]);
+    if constexpr (MSEL == 0) return HO::from_bits(((const uint16_t *)smem_tab)[J >> dshift]);
+    if constexpr (MSEL == 2) {
+      if (method != 3) return HO::from_bits(((const uint16_t *)smem_tab)[J >> dshift]);
+    }
     const ApproxIndex ai = approx_index(J, d);
     H v;
     {
@@ -510,10 +518,10 @@ __device__ __forceinline__ void block_reduce_write(ThreadAcc<EST, XP> &a, Partia
 
 // Simulate one chunk of an item (its table already in shared memory) and
 // write the CTA's Partial for it.
-template <int EST, int XP, int AP, int SCHEME, int PC, int KP, bool M3>
+template <int EST, int XP, int AP, int SCHEME, int PC, int KP, int MSEL, bool DUMP>
 __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDesc &it, int item, uint32_t gc,
                                            const unsigned char *smem_tab) {
-  using Sim = LevelSim<EST, XP, AP, SCHEME, PC, KP, M3>;
+  using Sim = LevelSim<EST, XP, AP, SCHEME, PC, KP, MSEL>;
   Sim sim;
   sim.load(it, smem_tab);
   ThreadAcc<EST, XP> acc;
@@ -526,7 +534,8 @@ __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDes
   const uint64_t first = it.first, last = it.first + it.N;
   const int lev = it.level;
   const uint4 ctr_hi = make_uint4(0, 0, it.ctr2, it.ctr3);
-  mlmc_sample_rec *dump = (mlmc_sample_rec *)it.dump;
+  // per-sample records only in the DUMP instantiation (parity runs)
+  mlmc_sample_rec *dump = DUMP ? (mlmc_sample_rec *)it.dump : nullptr;
 
   const uint64_t gf0 = it.gf0, gf1 = it.gf1;
   const uint32_t ng = gend > gbeg ? (uint32_t)(gend - gbeg) : 0u;
@@ -560,7 +569,7 @@ __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDes
       for (int l = 0; l < KP; ++l) {
         const uint64_t s = KP == 1 ? g : P * KP + l;
         const bool valid = full || (s >= first && s < last);
-        sim.finish(acc, l, valid, dump && valid ? dump + (s - first) : nullptr);
+        sim.finish(acc, l, valid, DUMP && valid ? dump + (s - first) : nullptr);
       }
     } else {
       const uint4 w = it.enumerate ? enum_words(g, lev, it.d)
@@ -584,7 +593,7 @@ __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDes
           for (int l = 0; l < KP; ++l) {
             const int k = u * KP + l;
             const bool valid = k >= klo && k < khi;
-            sim.finish(acc, l, valid, dump && valid ? dump + (s0 + k - first) : nullptr);
+            sim.finish(acc, l, valid, DUMP && valid ? dump + (s0 + k - first) : nullptr);
           }
         }
       } else {
@@ -596,7 +605,7 @@ __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDes
           for (int l = 0; l < KP; ++l) {
             const int k = u * KP + l;
             const bool valid = k >= klo && k < khi;
-            sim.finish(acc, l, valid, dump && valid ? dump + (s0 + k - first) : nullptr);
+            sim.finish(acc, l, valid, DUMP && valid ? dump + (s0 + k - first) : nullptr);
           }
         }
       }
@@ -630,7 +639,7 @@ __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDes
 // and write the CTA's Partial for the chunk.  Every thread has finished the
 // previous chunk before the table is overwritten (block_reduce_write ends with
 // a barrier).
-template <int EST, int XP, int AP, int SCHEME, int PC, int KP>
+template <int EST, int XP, int AP, int SCHEME, int PC, int KP, bool ALLOW_DUMP>
 __device__ __forceinline__ void run_chunk(const LaunchArgs &args, const ItemDesc *items, int n_items, uint32_t gc,
                                           const void **staged) {
   extern __shared__ __align__(16) unsigned char smem_tab[];
@@ -672,11 +681,13 @@ __device__ __forceinline__ void run_chunk(const LaunchArgs &args, const ItemDesc
     }
   }
   const int item = s_item;
-  if constexpr (AP == AP_NONE) {
-    chunk_body<EST, XP, AP, SCHEME, PC, KP, false>(args, it, item, gc, smem_tab);
+  if (ALLOW_DUMP && it.dump) {
+    if constexpr (ALLOW_DUMP) chunk_body<EST, XP, AP, SCHEME, PC, KP, 2, true>(args, it, item, gc, smem_tab);
+  } else if constexpr (AP == AP_NONE) {
+    chunk_body<EST, XP, AP, SCHEME, PC, KP, 0, false>(args, it, item, gc, smem_tab);
   } else {
-    if (it.method == 3) chunk_body<EST, XP, AP, SCHEME, PC, KP, true>(args, it, item, gc, smem_tab);
-    else chunk_body<EST, XP, AP, SCHEME, PC, KP, false>(args, it, item, gc, smem_tab);
+    if (it.method == 3) chunk_body<EST, XP, AP, SCHEME, PC, KP, 1, false>(args, it, item, gc, smem_tab);
+    else chunk_body<EST, XP, AP, SCHEME, PC, KP, 0, false>(args, it, item, gc, smem_tab);
   }
 }
 
@@ -684,7 +695,7 @@ __device__ __forceinline__ void run_chunk(const LaunchArgs &args, const ItemDesc
 template <int EST, int XP, int AP, int SCHEME, int PC, int KP>
 __global__ void __launch_bounds__(LAUNCH_THREADS, MinCtas<EST, AP, SCHEME, PC>::value)
 level_kernel(const __grid_constant__ LaunchArgs args) {
-  run_chunk<EST, XP, AP, SCHEME, PC, KP>(args, args.items, args.n_items, args.chunk0 + blockIdx.x, nullptr);
+  run_chunk<EST, XP, AP, SCHEME, PC, KP, true>(args, args.items, args.n_items, args.chunk0 + blockIdx.x, nullptr);
 }
 
 // Device-scheduled launch (fixed grid, captured once in a CUDA graph): the item
@@ -696,7 +707,8 @@ level_kernel_dyn(const __grid_constant__ LaunchArgs args) {
   const DynLaunch d = *args.dyn;
   const void *staged = nullptr;
   for (uint32_t rel = blockIdx.x; rel < d.n_chunks; rel += gridDim.x)
-    run_chunk<EST, XP, AP, SCHEME, PC, KP>(args, args.items + d.item_off, (int)d.n_items, d.chunk0 + rel, &staged);
+    run_chunk<EST, XP, AP, SCHEME, PC, KP, false>(args, args.items + d.item_off, (int)d.n_items, d.chunk0 + rel,
+                                                  &staged);
 }
 
 }  // namespace mlmc
