@@ -34,7 +34,8 @@ UNIT = "path-steps/s"
 WORKLOAD = ("nested MLMC step: euro+digital call GBM, EM, levels 0-8, N~ 1e7..1e4 fixed-point approx "
             "(packed draws) + 1e4 FP32-fixed corrections")
 
-# Algorithmic 32-bit lane operations per fine path-step (roofline section):
+# Algorithmic 32-bit lane operations per fine path-step (approximate fixed-point
+# estimator, Euler-Maruyama, terminal payoff):
 #   Philox4x32-10: 10 rounds x (2 wide multiplies + 2 three-input XORs) / 4 words = 10
 #   table index, lookup and sign: 5
 #   fixed-point Algorithm-1 fine step (2 products, 2 sums, 4 roundings): 10
@@ -42,6 +43,14 @@ WORKLOAD = ("nested MLMC step: euro+digital call GBM, EM, levels 0-8, N~ 1e7..1e
 OPS_APPROX_FIXED_EM = 30.5
 # SM issue peak: 152 SMs x 4 schedulers x 32 lanes x 2070 MHz (one warp instruction per scheduler per clock)
 ALU_PEAK_TOPS = 152 * 4 * 32 * 2.070e9 / 1e12
+# DRAM bytes (read + write) of the dominant launch, from one ncu capture of this
+# bench command (dram__bytes_read.sum + dram__bytes_write.sum, family 15 launch of
+# 51,213,208 path-steps):
+#   ncu --set full --clock-control none -k regex:level_kernel -c 3 -o prof \
+#       python bench.py --steps 3 --warmup 3 --no-cpu-baseline --no-tte \
+#       --no-serving-sample --no-autotune --no-optimiser
+# keyed by (family, path-steps per launch); another launch reports null
+DOMINANT_TRAFFIC = {(15, 51213208): 114432}
 
 
 def build_items(m, rank=0):
@@ -270,7 +279,7 @@ def main():
         dom_ms = sum(launch_ms[j]) / len(launch_ms[j])
         achieved = OPS_APPROX_FIXED_EM * ps / (dom_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Top/s",
-                    "frac": achieved / ALU_PEAK_TOPS, "traffic": None,
+                    "frac": achieved / ALU_PEAK_TOPS, "traffic": DOMINANT_TRAFFIC.get((dom, ps)),
                     "kernel": fam_names[dom],
                     "ms_per_launch": dom_ms, "ops_per_path_step": OPS_APPROX_FIXED_EM,
                     "path_steps_per_launch": ps}
