@@ -99,6 +99,30 @@ template <> struct HalfOps<__nv_bfloat16> {
   static __device__ __forceinline__ __nv_bfloat16 neg(__nv_bfloat16 a) { return __hneg(a); }
 };
 
+// Paired (x2) form: one instruction rounds both halves of a 32-bit register,
+// each exactly as the scalar operation of HalfOps would.
+template <class H> struct HalfOps2;
+template <> struct HalfOps2<__half> {
+  using T = __half2;
+  static __device__ __forceinline__ T mul(T a, T b) { return __hmul2_rn(a, b); }
+  static __device__ __forceinline__ T add(T a, T b) { return __hadd2_rn(a, b); }
+  static __device__ __forceinline__ T sub(T a, T b) { return __hsub2_rn(a, b); }
+  static __device__ __forceinline__ T pack(__half lo, __half hi) { return __halves2half2(lo, hi); }
+  static __device__ __forceinline__ T splat(__half a) { return __half2half2(a); }
+  static __device__ __forceinline__ __half lo(T a) { return __low2half(a); }
+  static __device__ __forceinline__ __half hi(T a) { return __high2half(a); }
+};
+template <> struct HalfOps2<__nv_bfloat16> {
+  using T = __nv_bfloat162;
+  static __device__ __forceinline__ T mul(T a, T b) { return __hmul2_rn(a, b); }
+  static __device__ __forceinline__ T add(T a, T b) { return __hadd2_rn(a, b); }
+  static __device__ __forceinline__ T sub(T a, T b) { return __hsub2_rn(a, b); }
+  static __device__ __forceinline__ T pack(__nv_bfloat16 lo, __nv_bfloat16 hi) { return __halves2bfloat162(lo, hi); }
+  static __device__ __forceinline__ T splat(__nv_bfloat16 a) { return __bfloat162bfloat162(a); }
+  static __device__ __forceinline__ __nv_bfloat16 lo(T a) { return __low2bfloat16(a); }
+  static __device__ __forceinline__ __nv_bfloat16 hi(T a) { return __high2bfloat16(a); }
+};
+
 // Kahan-compensated FP32 sum (error bounded by ~2 ulp of the sum of |terms|).
 struct KahanF {
   float s, c;

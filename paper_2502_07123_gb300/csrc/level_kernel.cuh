@@ -71,12 +71,16 @@ struct LevelSim {
   static constexpr bool FAST = (AP == AP_FX32 || AP == AP_FX64);
   static constexpr bool FIXED = (AP == AP_FIXED || FAST);
   static constexpr bool HALF = (AP == AP_F16 || AP == AP_BF16);
+  // packed half draws: lanes 0 and 1 share paired (x2) registers, lane 2 is scalar
+  static constexpr bool PAIR = HALF && KP == 3;
   using AS = typename std::conditional<AP == AP_FX32, int32_t, int64_t>::type;  // fixed-point S
   // saturation flag of the fast datapath: OR of (clamped ^ unclamped) for a 32-bit S
   using SatT = typename std::conditional<AP == AP_FX32, uint32_t, bool>::type;
   using X = typename XType<XP>::T;
   using H = typename HType<AP>::T;
   using HO = HalfOps<H>;
+  using HO2 = HalfOps2<H>;
+  using H2 = typename HO2::T;
 
   // ---- per-item constants (registers) ----
   int level, nsteps, payoff, d, dshift, method;
@@ -88,6 +92,7 @@ struct LevelSim {
   FastFixed ff;
   // half
   H hc1, hc1c, hc2, hc3, hS0;
+  H2 pc1, pc1c, pc2, pc3;
   float K32;
   float unit_scale;
   const void *smem_tab;
@@ -99,6 +104,7 @@ struct LevelSim {
   int64_t aaccF[KP], aaccC[KP];
   int32_t azprev[KP];
   H hS[KP], hSc[KP], hzprev[KP], hminF[KP], hminC[KP];
+  H2 pS, pSc, pzprev;   // lanes 0 and 1 when PAIR (hS[0..1] etc. then unused)
   float haccF[KP], haccC[KP];
   uint32_t sat[KP];
 
@@ -121,6 +127,9 @@ struct LevelSim {
       hc2 = HO::from_bits(it.h_c2); hc3 = HO::from_bits(it.h_c3);
       hS0 = HO::from_bits(it.h_S0);
       K32 = it.Kf;
+      if constexpr (PAIR) {
+        pc1 = HO2::splat(hc1); pc1c = HO2::splat(hc1c); pc2 = HO2::splat(hc2); pc3 = HO2::splat(hc3);
+      }
     }
     unit_scale = it.unit_scale;
     smem_tab = tab;
@@ -148,6 +157,9 @@ struct LevelSim {
         haccF[l] = __fmul_rn(0.5f, HO::to_f(hS0)); haccC[l] = haccF[l];
       }
       sat[l] = 0;
+    }
+    if constexpr (PAIR) {
+      pS = HO2::splat(hS0); pSc = pS; pzprev = HO2::splat(HO::from_f(0.0f));
     }
   }
 
@@ -211,6 +223,29 @@ struct LevelSim {
     const H mul2 = HO::mul(s, sum1);
     return HO::add(s, mul2);
   }
+  // the same step on two lanes at once
+  __device__ __forceinline__ H2 h2_step(H2 s, H2 z, H2 cc1, H2 mh) const {
+    const H2 mul1 = HO2::mul(pc2, z);
+    H2 sum1 = HO2::add(cc1, mul1);
+    if constexpr (MIL) {
+      const H2 sq = HO2::mul(z, z);
+      const H2 sqm = HO2::sub(sq, mh);
+      const H2 mul3 = HO2::mul(pc3, sqm);
+      sum1 = HO2::add(sum1, mul3);
+    }
+    const H2 mul2 = HO2::mul(s, sum1);
+    return HO2::add(s, mul2);
+  }
+  // lane l's half state (fine / coarse)
+  __device__ __forceinline__ H lane_S(int l) const {
+    if constexpr (PAIR) { if (l == 0) return HO2::lo(pS); if (l == 1) return HO2::hi(pS); }
+    return hS[l];
+  }
+  __device__ __forceinline__ H lane_Sc(int l) const {
+    if constexpr (PAIR) { if (l == 0) return HO2::lo(pSc); if (l == 1) return HO2::hi(pSc); }
+    return hSc[l];
+  }
+  __device__ __forceinline__ static void lane_min(H &mn, H x) { mn = HO::to_f(x) < HO::to_f(mn) ? x : mn; }
 
   // Approximate Normal of J in Z's fixed-point format: Method 1 reads the
   // signed table at j = top d bits of J; Method 3 evaluates the class line.
@@ -272,7 +307,44 @@ struct LevelSim {
         }
       }
     }
-    if constexpr (HAS_APPROX) {
+    if constexpr (PAIR) {
+      // Algorithm-1 arithmetic of lanes 0 and 1 in paired instructions; lane 2 alone
+      const H z0 = half_z(J), z1 = half_z(J << d), z2 = half_z(J << (2 * d));
+      const H2 z01 = HO2::pack(z0, z1);
+      if constexpr (PC == PC_ASIAN) {
+        if (i > 0) {
+          haccF[0] = __fadd_rn(haccF[0], HO::to_f(HO2::lo(pS)));
+          haccF[1] = __fadd_rn(haccF[1], HO::to_f(HO2::hi(pS)));
+          haccF[2] = __fadd_rn(haccF[2], HO::to_f(hS[2]));
+        }
+      }
+      pS = h2_step(pS, z01, pc1, HO2::splat(HO::from_f(1.0f)));
+      hS[2] = h_step(hS[2], z2, hc1, HO::from_f(1.0f));
+      if constexpr (PC == PC_LOOKBACK) {
+        lane_min(hminF[0], HO2::lo(pS)); lane_min(hminF[1], HO2::hi(pS)); lane_min(hminF[2], hS[2]);
+      }
+      if constexpr (COARSE) {
+        if (odd) {
+          const H2 zc01 = HO2::add(pzprev, z01);
+          const H zc2 = HO::add(hzprev[2], z2);
+          if constexpr (PC == PC_ASIAN) {
+            if (i > 1) {
+              haccC[0] = __fadd_rn(haccC[0], HO::to_f(HO2::lo(pSc)));
+              haccC[1] = __fadd_rn(haccC[1], HO::to_f(HO2::hi(pSc)));
+              haccC[2] = __fadd_rn(haccC[2], HO::to_f(hSc[2]));
+            }
+          }
+          pSc = h2_step(pSc, zc01, pc1c, HO2::splat(HO::from_f(2.0f)));
+          hSc[2] = h_step(hSc[2], zc2, hc1c, HO::from_f(2.0f));
+          if constexpr (PC == PC_LOOKBACK) {
+            lane_min(hminC[0], HO2::lo(pSc)); lane_min(hminC[1], HO2::hi(pSc)); lane_min(hminC[2], hSc[2]);
+          }
+        } else {
+          pzprev = z01;
+          hzprev[2] = z2;
+        }
+      }
+    } else if constexpr (HAS_APPROX) {
 #pragma unroll
       for (int l = 0; l < KP; ++l) {
         const uint32_t Jl = l == 0 ? J : (J << (d * l));  // this lane's field at the top
@@ -385,8 +457,8 @@ struct LevelSim {
     }
     if constexpr (HALF) {
       if constexpr (HAS_APPROX) {
-        qf = half_payoff(hS[l], haccF[l], hminF[l], nsteps);
-        if (level > 0) qc = half_payoff(hSc[l], haccC[l], hminC[l], nsteps >> 1);
+        qf = half_payoff(lane_S(l), haccF[l], hminF[l], nsteps);
+        if (level > 0) qc = half_payoff(lane_Sc(l), haccC[l], hminC[l], nsteps >> 1);
       }
     }
     if (!valid) return;
@@ -421,8 +493,8 @@ struct LevelSim {
         r.af = ldexp((double)afS, -fx.fS);
         r.ac = level > 0 ? ldexp((double)acS, -fx.fS) : 0.0;
       } else if constexpr (HALF) {
-        r.af = HAS_APPROX ? (double)HO::to_f(hS[l]) : 0.0;
-        r.ac = (HAS_APPROX && level > 0) ? (double)HO::to_f(hSc[l]) : 0.0;
+        r.af = HAS_APPROX ? (double)HO::to_f(lane_S(l)) : 0.0;
+        r.ac = (HAS_APPROX && level > 0) ? (double)HO::to_f(lane_Sc(l)) : 0.0;
       } else {
         r.af = 0.0; r.ac = 0.0;
       }

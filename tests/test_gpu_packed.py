@@ -66,3 +66,21 @@ def test_packing_rules(m):
         a = m.mlmc_level(3, 2000, Pp, v, 5)
         b = m.mlmc_level(3, 2000, Pu, v, 5)
         assert a["sum"] == b["sum"] and a["sum2"] == b["sum2"]
+
+
+# Items with at least one wave of packs run three lockstep lanes per thread; on
+# the binary16 / bfloat16 datapaths lanes 0 and 1 share paired (x2) instructions.
+WIDE = [(v, s, pay) for v in (core.FP16_APPROX, core.BF16_APPROX) for s in (W.EULER, W.MILSTEIN)
+        for pay in (W.EURO, W.DIGITAL, W.ASIAN, W.LOOKBACK)]
+
+
+@pytest.mark.parametrize("variant,scheme,payoff", WIDE)
+def test_packed_half_pairs(m, variant, scheme, payoff):
+    p = W.params(scheme=scheme, payoff=payoff, sigma=0.3)
+    level, first, N = 3, 7, 400_003                    # > 6 x 128 x 152 packs: not lane-split
+    method = 3 if payoff % 2 else 1
+    P = m.make_params(p, d=10, method=method, request=3, rng_pack=1)
+    gs, gd = m.mlmc_level_dump(level, N, P, variant, 21, first)
+    os_, od = core.level(p, level, first, N, variant, 21, request=3, d=10, method=method, dump=True, pack=1)
+    assert gs["isum"] == os_["isum"] and gs["isum2"] == os_["isum2"]
+    compare_samples(variant, p, gd, od)
