@@ -117,6 +117,34 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def dominant_alone(m, torch, items, seed, tuning, dom, ps, flush, stream, reps=10):
+    """The dominant launch's items (the packed approximate items: fewer packs than
+    one wave of resident threads run one sample per thread in another launch) as
+    a plan of their own, timed with CUDA events with the GPU to itself, outside
+    the timed region.  None unless that plan is exactly the step's launch."""
+    wave = 6 * 128 * torch.cuda.get_device_properties(stream.device).multi_processor_count
+    sub = [it for it in items if it["variant"] == m.FIXED_APPROX
+           and (it["level"] < 2 or (it["N"] + 2) // 3 >= wave)]
+    plan = m.Plan(sub, seed, tuning)
+    try:
+        if plan.info()["kernels"] != 1:
+            return None
+        fam, _, _, lps = plan.launch_info(0)
+        if fam != dom or lps != ps:
+            return None
+        for _ in range(3):
+            plan.launch(stream)
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            plan.launch(stream)
+            ms.append(plan.kernel_time(0)[1])
+        torch.cuda.synchronize()
+        return statistics.median(ms)
+    finally:
+        plan.close()
+
+
 def oracle_step_sample(meta, cfg, fraction, rank=0):
     """Time the CPU oracle on the first `fraction` of every work item; returns (path_steps, seconds)."""
     from oracle import core
@@ -283,6 +311,12 @@ def main():
                     "kernel": fam_names[dom],
                     "ms_per_launch": dom_ms, "ops_per_path_step": OPS_APPROX_FIXED_EM,
                     "path_steps_per_launch": ps}
+        alone_ms = dominant_alone(m, torch, items, cfg["seed"], tuning, dom, ps, flush, stream)
+        if alone_ms:
+            # the same launch with the GPU to itself (in the step it shares the
+            # SMs with the other two level kernels)
+            a = OPS_APPROX_FIXED_EM * ps / (alone_ms * 1e-3) / 1e12
+            roofline["alone"] = {"ms_per_launch": alone_ms, "achieved": a, "frac": a / ALU_PEAK_TOPS}
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

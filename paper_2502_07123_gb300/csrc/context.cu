@@ -1,0 +1,402 @@
+// Device context of the C ABI (device, SM count, internal stream, reusable
+// buffers), the process-wide lock, and the approximate-Normal tables: Method 1
+// (Sec. 3.1) in FP64 and in each representation, the Method-3 line fit
+// (Sec. 3.3), and the Method-2 small table with its interval ranks (Sec. 3.2);
+// the table, generator and version entry points.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "item.h"
+#include "kernels.h"
+#include "reduce.cuh"
+#include "mlmc.h"
+#include "tables.h"
+#include "host_api.h"
+
+using namespace mlmc;
+
+namespace mlmc_host {
+
+Ctx g;
+
+
+mlmc_status ensure_ctx() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MLMC_ECUDA;
+  if (g.inited && g.device == dev) return MLMC_OK;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) return MLMC_ECUDA;
+  if (g.inited && g.device != dev) {
+    // a different device became current: start a fresh cache for it
+    g.m1_host.clear();
+    g.m1_dev.clear();
+    g.tables.clear();
+    g.m2_perm.clear();
+    item_cache_clear();
+  }
+  MLMC_CK(cudaDeviceGetAttribute(&g.num_sms, cudaDevAttrMultiProcessorCount, dev));
+  MLMC_CK(cudaStreamCreateWithFlags(&g.st, cudaStreamNonBlocking));
+  g.device = dev;
+  g.inited = true;
+  return MLMC_OK;
+}
+
+mlmc_status m1_table(int d, double **dev, const std::vector<double> **host) {
+  auto it = g.m1_dev.find(d);
+  if (it == g.m1_dev.end()) {
+    const int n = 1 << (d - 1);
+    double *p = nullptr;
+    MLMC_CK(cudaMalloc(&p, sizeof(double) * n));
+    MLMC_CK(launch_m1_table(d, p, g.st));
+    std::vector<double> h(n);
+    MLMC_CK(cudaMemcpyAsync(h.data(), p, sizeof(double) * n, cudaMemcpyDeviceToHost, g.st));
+    MLMC_CK(cudaStreamSynchronize(g.st));
+    g.m1_dev[d] = p;
+    g.m1_host[d] = std::move(h);
+    it = g.m1_dev.find(d);
+  }
+  *dev = it->second;
+  *host = &g.m1_host[d];
+  return MLMC_OK;
+}
+
+// Method 3 (Sec. 3.3): least-squares line a + b k through (k, Z_k) on each
+// dyadic index class {0,1}, {2,3}, {4..7}, ..., {2^(d-2) .. 2^(d-1)-1}.
+void m3_fit(const std::vector<double> &Z, int d, M3Coef &c) {
+  std::memset(&c, 0, sizeof c);
+  for (int cls = 0; cls < d - 1; ++cls) {
+    const int lo = cls == 0 ? 0 : (1 << cls);
+    const int hi = cls == 0 ? 1 : (1 << (cls + 1)) - 1;
+    const int n = hi - lo + 1;
+    double kbar = 0.0, zbar = 0.0;
+    for (int k = lo; k <= hi; ++k) { kbar += k; zbar += Z[k]; }
+    kbar /= n;
+    zbar /= n;
+    double sxx = 0.0, sxy = 0.0;
+    for (int k = lo; k <= hi; ++k) {
+      sxx += (k - kbar) * (k - kbar);
+      sxy += (k - kbar) * (Z[k] - zbar);
+    }
+    const double b = sxy / sxx;
+    const double a = zbar - b * kbar;
+    c.a[cls] = (float)a;
+    c.b[cls] = (float)b;
+    c.A[cls] = (int64_t)std::floor(std::ldexp(a, M3_FRAC) + 0.5);
+    c.B[cls] = (int64_t)std::floor(std::ldexp(b, M3_FRAC) + 0.5);
+  }
+}
+
+// Device table of one representation.  full_signed (method 1 only): all 2^d
+// entries indexed directly by j, as the level kernels use it; otherwise the
+// 2^(d-1) entries of the lower half (parity checks).
+uint16_t half_bits(double x) { return __half_as_ushort(__double2half(x)); }
+uint16_t bf16_bits(double x) { return __bfloat16_as_ushort(__double2bfloat16(x)); }
+
+// Method 2 (Sec. 3.2) with two fields: the d-bit index j splits into a high
+// and a low field of b = d/2 bits; each gives +-x_k from a small table of
+// 2^(b-1) values (Method-1 sign rule per field) and Z~_j is their sum.  The
+// small table starts as the b-bit Method-1 table / sqrt(2); then the 2^d sums
+// are ranked ascending (ties by j), pi(j) = rank, and x is refitted by least
+// squares (normal equations, Cholesky in long double) to the d-bit Method-1
+// values Z_{pi(j)}, until pi stops changing (at most 1000 fits).
+std::map<int, M2Table> g_m2;
+
+struct M2Field { int idx; double sgn; };
+inline void m2_fields(int j, int b, M2Field &hi, M2Field &lo) {
+  const int full = 1 << b, half = 1 << (b - 1);
+  const int f1 = j >> b, f2 = j & (full - 1);
+  hi = f1 < half ? M2Field{f1, 1.0} : M2Field{full - 1 - f1, -1.0};
+  lo = f2 < half ? M2Field{f2, 1.0} : M2Field{full - 1 - f2, -1.0};
+}
+
+bool chol_solve(std::vector<long double> M, std::vector<long double> r, int k, std::vector<double> &y) {
+  for (int c = 0; c < k; ++c) {
+    long double dg = M[c * k + c];
+    for (int q = 0; q < c; ++q) dg -= M[c * k + q] * M[c * k + q];
+    if (!(dg > 0.0L)) return false;
+    dg = std::sqrt(dg);
+    M[c * k + c] = dg;
+    for (int rr = c + 1; rr < k; ++rr) {
+      long double v = M[rr * k + c];
+      for (int q = 0; q < c; ++q) v -= M[rr * k + q] * M[c * k + q];
+      M[rr * k + c] = v / dg;
+    }
+  }
+  for (int c = 0; c < k; ++c) {          // L z = r
+    long double v = r[c];
+    for (int q = 0; q < c; ++q) v -= M[c * k + q] * r[q];
+    r[c] = v / M[c * k + c];
+  }
+  for (int c = k - 1; c >= 0; --c) {     // L^T y = z
+    long double v = r[c];
+    for (int q = c + 1; q < k; ++q) v -= M[q * k + c] * r[q];
+    r[c] = v / M[c * k + c];
+  }
+  y.resize(k);
+  for (int c = 0; c < k; ++c) y[c] = (double)r[c];
+  return true;
+}
+
+mlmc_status m2_build(int d, const M2Table **out) {
+  auto it = g_m2.find(d);
+  if (it != g_m2.end()) { *out = &it->second; return MLMC_OK; }
+  if (d % 2 || d < 4) return MLMC_EINVAL;
+  const int b = d / 2, k = 1 << (b - 1), N = 1 << d;
+  double *dv;
+  const std::vector<double> *zb = nullptr, *zd = nullptr;
+  mlmc_status s;
+  if ((s = m1_table(b, &dv, &zb)) != MLMC_OK) return s;
+  if ((s = m1_table(d, &dv, &zd)) != MLMC_OK) return s;
+  std::vector<double> T(N);
+  for (int j = 0; j < N; ++j) T[j] = j < N / 2 ? (*zd)[j] : -(*zd)[N - 1 - j];
+  std::vector<M2Field> fh(N), fl(N);
+  for (int j = 0; j < N; ++j) m2_fields(j, b, fh[j], fl[j]);
+  // normal matrix A^T A (A has one +-1 per field in every row)
+  std::vector<long double> M((size_t)k * k, 0.0L);
+  for (int j = 0; j < N; ++j) {
+    const M2Field f[2] = {fh[j], fl[j]};
+    for (int a = 0; a < 2; ++a)
+      for (int c = 0; c < 2; ++c) M[(size_t)f[a].idx * k + f[c].idx] += (long double)(f[a].sgn * f[c].sgn);
+  }
+  M2Table t;
+  t.x.resize(k);
+  for (int q = 0; q < k; ++q) t.x[q] = (*zb)[q] / std::sqrt(2.0);
+  auto sums = [&](const std::vector<double> &x, std::vector<double> &v) {
+    v.resize(N);
+    for (int j = 0; j < N; ++j) v[j] = fh[j].sgn * x[fh[j].idx] + fl[j].sgn * x[fl[j].idx];
+  };
+  auto rank = [&](const std::vector<double> &v, std::vector<uint32_t> &pi) {
+    std::vector<int> order(N);
+    for (int j = 0; j < N; ++j) order[j] = j;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return v[a] < v[c]; });
+    pi.resize(N);
+    for (int r = 0; r < N; ++r) pi[order[r]] = (uint32_t)r;
+  };
+  sums(t.x, t.values);
+  rank(t.values, t.pi);
+  for (t.iterations = 0; t.iterations < 1000;) {
+    std::vector<long double> rhs(k, 0.0L);
+    for (int j = 0; j < N; ++j) {
+      const long double y = T[t.pi[j]];
+      rhs[fh[j].idx] += fh[j].sgn * y;
+      rhs[fl[j].idx] += fl[j].sgn * y;
+    }
+    if (!chol_solve(M, rhs, k, t.x)) return MLMC_EINVAL;
+    ++t.iterations;
+    sums(t.x, t.values);
+    std::vector<uint32_t> pn;
+    rank(t.values, pn);
+    if (pn == t.pi) break;
+    t.pi.swap(pn);
+  }
+  auto ins = g_m2.emplace(d, std::move(t));
+  *out = &ins.first->second;
+  return MLMC_OK;
+}
+
+// Method-2 value of index j in a representation: each small-table value rounded
+// once, the two fields added exactly (fixed point) or with one rounding.
+double m2_value(const M2Table &t, int d, int j, int rep, int fZ) {
+  const int b = d / 2;
+  M2Field h, l;
+  m2_fields(j, b, h, l);
+  const double a = t.x[h.idx], c = t.x[l.idx];
+  switch (rep) {
+    case REP_FIXED: {
+      const int64_t qa = (int64_t)std::floor(std::ldexp(a, fZ) + 0.5), qc = (int64_t)std::floor(std::ldexp(c, fZ) + 0.5);
+      return std::ldexp((double)((int64_t)h.sgn * qa + (int64_t)l.sgn * qc), -fZ);
+    }
+    case REP_FP16: {
+      const double ha = (double)__half2float(__double2half(a)), hc = (double)__half2float(__double2half(c));
+      return (double)__half2float(__double2half(h.sgn * ha + l.sgn * hc));
+    }
+    case REP_BF16: {
+      const double ba = (double)__bfloat162float(__double2bfloat16(a));
+      const double bc = (double)__bfloat162float(__double2bfloat16(c));
+      return (double)__bfloat162float(__double2bfloat16(h.sgn * ba + l.sgn * bc));
+    }
+    case REP_FP32: {
+      const double fa = (double)(float)a, fc = (double)(float)c;
+      return (double)(float)(h.sgn * fa + l.sgn * fc);
+    }
+    default: return t.values[j];
+  }
+}
+
+// Device copy of the Method-2 interval ranks of index width d.
+mlmc_status m2_perm_device(int d, const uint16_t **out) {
+  auto it = g.m2_perm.find(d);
+  if (it != g.m2_perm.end()) { *out = it->second; return MLMC_OK; }
+  const M2Table *t;
+  mlmc_status s = m2_build(d, &t);
+  if (s != MLMC_OK) return s;
+  std::vector<uint16_t> h(1 << d);
+  for (int j = 0; j < (1 << d); ++j) h[j] = (uint16_t)t->pi[j];
+  uint16_t *p = nullptr;
+  MLMC_CK(cudaMalloc(&p, sizeof(uint16_t) * h.size()));
+  MLMC_CK(cudaMemcpy(p, h.data(), sizeof(uint16_t) * h.size(), cudaMemcpyHostToDevice));
+  g.m2_perm[d] = p;
+  *out = p;
+  return MLMC_OK;
+}
+
+mlmc_status get_table(int method, int d, int rep, int fZ, const void **out, bool full_signed) {
+  if (rep != REP_FIXED) fZ = 0;
+  if (method == 3) full_signed = false;
+  auto key = std::make_tuple(method, d, rep, fZ, full_signed ? 1 : 0);
+  auto it = g.tables.find(key);
+  if (it != g.tables.end()) { *out = it->second; return MLMC_OK; }
+  double *z64 = nullptr;
+  const std::vector<double> *zh = nullptr;
+  mlmc_status s = m1_table(d, &z64, &zh);
+  if (s != MLMC_OK) return s;
+  void *p = nullptr;
+  const int n = 1 << (d - 1);
+  if (method == 2) {
+    // the signed table over all 2^d indices, built on the host
+    if (!full_signed) return MLMC_EINVAL;
+    const M2Table *t;
+    if ((s = m2_build(d, &t)) != MLMC_OK) return s;
+    if (rep == REP_FIXED) {
+      std::vector<int32_t> h(2 * n);
+      for (int j = 0; j < 2 * n; ++j) h[j] = (int32_t)std::llround(std::ldexp(m2_value(*t, d, j, rep, fZ), fZ));
+      MLMC_CK(cudaMalloc(&p, sizeof(int32_t) * h.size()));
+      MLMC_CK(cudaMemcpy(p, h.data(), sizeof(int32_t) * h.size(), cudaMemcpyHostToDevice));
+    } else if (rep == REP_FP16 || rep == REP_BF16) {
+      std::vector<uint16_t> h(2 * n);
+      for (int j = 0; j < 2 * n; ++j) {
+        const double v = m2_value(*t, d, j, rep, fZ);
+        h[j] = rep == REP_FP16 ? half_bits(v) : bf16_bits(v);
+      }
+      MLMC_CK(cudaMalloc(&p, sizeof(uint16_t) * h.size()));
+      MLMC_CK(cudaMemcpy(p, h.data(), sizeof(uint16_t) * h.size(), cudaMemcpyHostToDevice));
+    } else {
+      return MLMC_EINVAL;
+    }
+  } else if (method == 1 && full_signed) {
+    const size_t es = (rep == REP_FP16 || rep == REP_BF16) ? 2 : 4;
+    MLMC_CK(cudaMalloc(&p, es * 2 * n));
+    MLMC_CK(launch_m1_signed(z64, d, rep, fZ, p, g.st));
+    MLMC_CK(cudaStreamSynchronize(g.st));
+  } else if (method == 1) {
+    if (rep == REP_FP64) {
+      p = z64;
+    } else {
+      const size_t es = (rep == REP_FP16 || rep == REP_BF16) ? 2 : 4;
+      MLMC_CK(cudaMalloc(&p, es * n));
+      MLMC_CK(launch_m1_convert(z64, n, rep, fZ, p, g.st));
+      MLMC_CK(cudaStreamSynchronize(g.st));
+    }
+  } else {
+    M3Coef c;
+    m3_fit(*zh, d, c);
+    MLMC_CK(cudaMalloc(&p, sizeof(M3Coef)));
+    MLMC_CK(cudaMemcpy(p, &c, sizeof(M3Coef), cudaMemcpyHostToDevice));
+  }
+  g.tables[key] = p;
+  *out = p;
+  return MLMC_OK;
+}
+
+cudaStream_t ctx_stream() { return g.st; }
+std::recursive_mutex &api_mutex() {
+  static std::recursive_mutex m;
+  return m;
+}
+int ctx_num_sms() { return g.num_sms; }
+
+}  // namespace mlmc_host
+
+using namespace mlmc_host;
+
+extern "C" {
+
+mlmc_status mlmc_icdf_table(int method, int d, int rep, int fZ, double *out) {
+  MLMC_API_LOCK();
+  if (method < 1 || method > 3 || d < 2 || d > 14 || rep < 0 || rep > 4 || !out) return MLMC_EINVAL;
+  if (rep == REP_FIXED && (fZ < 0 || fZ > 28)) return MLMC_EINVAL;
+  if (method == 3 && rep == REP_FP64) return MLMC_EINVAL;
+  if (method == 2 && (d % 2 || d < 4)) return MLMC_EINVAL;
+  mlmc_status s = ensure_ctx();
+  if (s != MLMC_OK) return s;
+  if (method == 2) {
+    // the host-built values the device tables are made of
+    const M2Table *t;
+    if ((s = m2_build(d, &t)) != MLMC_OK) return s;
+    for (int j = 0; j < (1 << (d - 1)); ++j) out[j] = m2_value(*t, d, j, rep, fZ);
+    return MLMC_OK;
+  }
+  const void *tab = nullptr;
+  if ((s = get_table(method, d, rep, fZ, &tab)) != MLMC_OK) return s;
+  const int n = 1 << (d - 1);
+  double *dv = nullptr;
+  MLMC_CK(cudaMalloc(&dv, sizeof(double) * n));
+  cudaError_t e = launch_table_values(method, d, rep, fZ, tab, dv, g.st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, dv, sizeof(double) * n, cudaMemcpyDeviceToHost, g.st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g.st);
+  cudaFree(dv);
+  return e == cudaSuccess ? MLMC_OK : MLMC_ECUDA;
+}
+
+mlmc_status mlmc_icdf_method2(int d, double *x, uint32_t *perm, int *iterations) {
+  MLMC_API_LOCK();
+  if (d % 2 || d < 4 || d > 14) return MLMC_EINVAL;
+  mlmc_status s = ensure_ctx();
+  if (s != MLMC_OK) return s;
+  const M2Table *t;
+  if ((s = m2_build(d, &t)) != MLMC_OK) return s;
+  if (x) std::memcpy(x, t->x.data(), sizeof(double) * t->x.size());
+  if (perm) std::memcpy(perm, t->pi.data(), sizeof(uint32_t) * t->pi.size());
+  if (iterations) *iterations = t->iterations;
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_philox(const uint32_t *ctr, uint64_t n, uint64_t seed, uint32_t *out) {
+  MLMC_API_LOCK();
+  if ((!ctr || !out) && n) return MLMC_EINVAL;
+  if (n == 0) return MLMC_OK;
+  mlmc_status s = ensure_ctx();
+  if (s != MLMC_OK) return s;
+  RoundKeys rk;
+  make_round_keys(seed, rk);
+  uint4 *dc = nullptr, *dout = nullptr;
+  if (cudaMalloc(&dc, 16 * n) != cudaSuccess) return MLMC_ENOMEM;
+  if (cudaMalloc(&dout, 16 * n) != cudaSuccess) { cudaFree(dc); return MLMC_ENOMEM; }
+  cudaError_t e = cudaMemcpyAsync(dc, ctr, 16 * n, cudaMemcpyHostToDevice, g.st);
+  if (e == cudaSuccess) e = launch_philox(dc, n, rk, dout, g.st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, 16 * n, cudaMemcpyDeviceToHost, g.st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g.st);
+  cudaFree(dc);
+  cudaFree(dout);
+  return e == cudaSuccess ? MLMC_OK : MLMC_ECUDA;
+}
+
+const char *mlmc_strerror(mlmc_status s) {
+  switch (s) {
+    case MLMC_OK: return "ok";
+    case MLMC_EINVAL: return "invalid argument";
+    case MLMC_ENOMEM: return "out of memory";
+    case MLMC_ECUDA: return "CUDA runtime error or no CUDA device";
+    case MLMC_ETIMEOUT: return "timed out";
+    case MLMC_EOVERFLOW: return "constant outside its fixed-point format";
+    case MLMC_ENOTREADY: return "results requested before launch";
+    default: return "unknown status";
+  }
+}
+
+const char *mlmc_version(void) { return "mlmc-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,8 +1,15 @@
-// Host-side internals of the C ABI shared between api.cu and engine.cu.
+// Host-side internals of the C ABI, shared by its translation units:
+// context.cu (device context, tables), items.cu (work items), plan.cu (plans
+// and synchronous calls), estimate.cu (adaptive driver), noalloc.cu and
+// engine.cu (continuous batching).
 #pragma once
 #include <cuda_runtime.h>
 
+#include <map>
 #include <mutex>
+#include <string>
+#include <tuple>
+#include <unordered_map>
 #include <vector>
 
 #include "item.h"
@@ -19,7 +26,41 @@ namespace mlmc_host {
     if (e_ != cudaSuccess) return MLMC_ECUDA;         \
   } while (0)
 
-struct Arena;
+// ---------------------------------------------------------------------------
+// device context (context.cu)
+// ---------------------------------------------------------------------------
+// Reusable device buffers, streams and events of the synchronous calls
+// (mlmc_level, mlmc_run, mlmc_estimate), grown on demand.
+struct Arena {
+  mlmc::ItemDesc *items = nullptr;
+  size_t cap_items = 0;
+  mlmc::Partial *partials = nullptr;
+  size_t cap_chunks = 0;
+  mlmc::DevSums *out = nullptr;
+  size_t cap_out = 0;
+  uint32_t *counters = nullptr;
+  size_t cap_counters = 0;
+  mlmc::ItemDesc *h_items = nullptr;       // pinned staging of the work list
+  size_t cap_h_items = 0;
+  mlmc::DevSums *h_out = nullptr;          // pinned staging of the results
+  size_t cap_h_out = 0;
+  std::vector<cudaStream_t> aux;
+  std::vector<cudaEvent_t> join, kstart, kstop;
+  cudaEvent_t fork = nullptr, t0 = nullptr, t1 = nullptr;
+};
+
+struct Ctx {
+  bool inited = false;
+  Arena arena;
+  int device = -1;
+  int num_sms = 0;
+  cudaStream_t st = nullptr;
+  std::map<int, std::vector<double>> m1_host;               // d -> Method-1 table (FP64)
+  std::map<int, double *> m1_dev;                           // d -> device FP64 table
+  std::map<std::tuple<int, int, int, int, int>, void *> tables;  // (method, d, rep, fZ, signed) -> table
+  std::map<int, uint16_t *> m2_perm;                         // d -> device interval ranks (Method 2)
+};
+extern Ctx g;
 
 // The library's context (streams, tables, caches, staging buffers, tuning
 // table) is shared by every call: the public entry points hold this lock, so
@@ -33,20 +74,56 @@ mlmc_status ensure_ctx();
 cudaStream_t ctx_stream();
 // The context's SM count.
 int ctx_num_sms();
-// Relative cost per fine path-step of an estimator kind (mlmc_cost_model).
-double cost_of_variant(int variant);
-bool params_ok(const mlmc_params *p);
 
-// Plans: create (borrowing the context arena when `transient`), launch on a
-// stream, read results, release.  plan_out_device gives the device array of
-// one mlmc::DevSums (undiscounted) per work item of the last launch;
-// plan_item_scale gives the factors the host applies to them.
-mlmc_status plan_create_transient(mlmc_plan **out, const mlmc_work *work, int n_work, uint64_t seed,
-                                  const mlmc_tuning *tuning);
-mlmc_status plan_launch_on(mlmc_plan *pl, cudaStream_t st);
-const mlmc::DevSums *plan_out_device(const mlmc_plan *pl);
-void plan_item_scale(const mlmc_plan *pl, int i, double *disc, int *unit, int *exact_int);
-void plan_release(mlmc_plan *pl);
+// ---------------------------------------------------------------------------
+// approximate-Normal tables (context.cu)
+// ---------------------------------------------------------------------------
+// Method-1 table of index width d (Sec. 3.1): device FP64 copy and host copy.
+mlmc_status m1_table(int d, double **dev, const std::vector<double> **host);
+// Method 3 (Sec. 3.3): least-squares line per dyadic index class.
+void m3_fit(const std::vector<double> &Z, int d, mlmc::M3Coef &c);
+uint16_t half_bits(double x);
+uint16_t bf16_bits(double x);
+// Method 2 (Sec. 3.2), two fields of d/2 bits.
+struct M2Table {
+  std::vector<double> x;         // small table
+  std::vector<double> values;    // Z~_j, j < 2^d, FP64 sums in field order
+  std::vector<uint32_t> pi;      // interval rank of every j
+  int iterations = 0;
+};
+mlmc_status m2_build(int d, const M2Table **out);
+double m2_value(const M2Table &t, int d, int j, int rep, int fZ);
+mlmc_status m2_perm_device(int d, const uint16_t **out);
+// Device table of one (method, d, representation, f_Z), cached per process.
+mlmc_status get_table(int method, int d, int rep, int fZ, const void **out, bool full_signed = false);
+
+// ---------------------------------------------------------------------------
+// work items (items.cu)
+// ---------------------------------------------------------------------------
+// Algorithm-1 variable order of mlmc_format.
+enum { F_Z = 0, F_CON1 = 1, F_CON2 = 2, F_MUL1 = 3, F_SUM1 = 4, F_MUL2 = 5, F_S = 6 };
+
+bool params_ok(const mlmc_params *p);
+// Samples per pack (3 with packed draws for approximate-only estimators, else 1).
+int pack_lanes(const mlmc_params *p, int variant);
+void default_format(const mlmc_params *p, int level, mlmc_format *out);
+mlmc::Requant make_rq(int from, int to);
+mlmc_status const_fixed(double x, int e, int f, int64_t *out);
+bool format_ok_gpu(const mlmc_format &F, bool milstein, int d);
+// Proof on the host that only S can saturate (the fast fixed-point datapath).
+bool fast_fixed(const int e[7], const int f[7], int64_t con1, int64_t con1c, int64_t con2, int64_t con3,
+                int64_t zmax, bool milstein, mlmc::FastFixed &ff, bool &s64);
+int64_t table_zmax_fixed(const std::vector<double> &Z, int d, int method, int fZ);
+int family_of(int variant);
+int cost_kind_of(int variant);
+// Relative cost per fine path-step of an estimator kind (mlmc_cost_model).
+extern double g_cost[4];
+double cost_of_variant(int variant);
+// Launch shape per (kernel family, scheme, payoff class, level class).
+extern std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune;
+int level_class(int level);
+// Launch shape (CTA threads, fine path-steps per thread) of a kernel class.
+void tuning_for(int family, int scheme, int pc, int level, int *threads, int *spt);
 
 // A work item with its constants and tables resolved (build_item), before
 // chunking (chunk_built).
@@ -60,13 +137,37 @@ struct BuiltItem {
 };
 mlmc_status build_item(const mlmc_work &w, int out_index, void *dump, BuiltItem &b, double &disc, int &unit,
                        int &exact_int);
+// build_item through the per-process cache of built constants.
+mlmc_status build_item_cached(const mlmc_work &w, int out_index, void *dump, BuiltItem &b, double &disc, int &unit,
+                              int &exact_int);
+// Empty that cache (its items point to one device's tables).
+void item_cache_clear();
 mlmc_status chunk_built(BuiltItem &b, int threads, int spt);
-// Launch shape (CTA threads, fine path-steps per thread) of a kernel class.
-void tuning_for(int family, int scheme, int pc, int level, int *threads, int *spt);
 void make_round_keys(uint64_t seed, mlmc::RoundKeys &rk);
 // Launch one level kernel of a family (or, with occ, query the resident CTAs
 // per SM of its device-scheduled kernel).
 cudaError_t launch_by_family(int fam, int scheme, int pc, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                              const mlmc::LaunchArgs &a, int *occ);
+
+// ---------------------------------------------------------------------------
+// plans (plan.cu)
+// ---------------------------------------------------------------------------
+// Deterministic sum of each item's chunk partials.
+__global__ void finalize_kernel(const mlmc::ItemDesc *items, int n_items, const mlmc::Partial *partials,
+                                mlmc::DevSums *out);
+double u128_to_double(uint64_t lo, uint64_t hi);
+// Plan, launch, read and release in one synchronous call on stream st.
+mlmc_status run_sync(const mlmc_work *work, int n_work, uint64_t seed, const mlmc_tuning *tuning,
+                     void *const *dumps, mlmc_sums *out, cudaStream_t st);
+// Plans: create (borrowing the context arena when `transient`), launch on a
+// stream, read results, release.  plan_out_device gives the device array of
+// one mlmc::DevSums (undiscounted) per work item of the last launch;
+// plan_item_scale gives the factors the host applies to them.
+mlmc_status plan_create_transient(mlmc_plan **out, const mlmc_work *work, int n_work, uint64_t seed,
+                                  const mlmc_tuning *tuning);
+mlmc_status plan_launch_on(mlmc_plan *pl, cudaStream_t st);
+const mlmc::DevSums *plan_out_device(const mlmc_plan *pl);
+void plan_item_scale(const mlmc_plan *pl, int i, double *disc, int *unit, int *exact_int);
+void plan_release(mlmc_plan *pl);
 
 }  // namespace mlmc_host

@@ -1,5 +1,5 @@
 // Device work-item descriptor and reduction records of the level kernels.
-// Built on the host (api.cu) from the public mlmc_work / mlmc_params and
+// Built on the host (items.cu) from the public mlmc_work / mlmc_params and
 // copied to device memory once per plan.
 #pragma once
 #include <stdint.h>

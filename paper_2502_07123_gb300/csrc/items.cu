@@ -1,0 +1,572 @@
+// Work items: parameter checks, per-level fixed-point formats and constants
+// (Algorithm 1, Sec. 4.1), the proof that selects the fast fixed-point
+// datapath, kernel families and the launch-shape table, and the (cached)
+// build of one ItemDesc with its chunking into CTAs.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "item.h"
+#include "kernels.h"
+#include "reduce.cuh"
+#include "mlmc.h"
+#include "tables.h"
+#include "host_api.h"
+
+using namespace mlmc;
+
+namespace mlmc_host {
+
+
+// Work items already built, by everything their constants depend on (params,
+// the level's format, level, variant, stream); the sample range is set per call.
+struct CachedItem {
+  BuiltItem b;
+  double disc;
+  int unit, exact_int;
+};
+std::unordered_map<std::string, CachedItem> g_item_cache;
+void item_cache_clear() { g_item_cache.clear(); }
+
+double g_cost[4] = {8.0, 1.0, 0.5, 1.5};
+const double g_cost_default[4] = {8.0, 1.0, 0.5, 1.5};
+
+// Launch shape per (kernel family, scheme, payoff class, level class): CTA
+// threads and fine path-steps per thread.  Defaults 128 / 256 until
+// mlmc_autotune installs measured choices.
+constexpr int TUNE_THREADS = 128, TUNE_SPT = 256;
+std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune;
+
+int level_class(int level) { return level <= 1 ? level : (level <= 4 ? 2 : (level <= 7 ? 3 : 4)); }
+
+void tuning_for(int family, int scheme, int pc, int level, int *threads, int *spt) {
+  auto f = g_tune.find(std::make_tuple(family, scheme, pc, level_class(level)));
+  *threads = f == g_tune.end() ? TUNE_THREADS : f->second.first;
+  *spt = f == g_tune.end() ? TUNE_SPT : f->second.second;
+}
+
+// ---------------------------------------------------------------------------
+// parameters, formats and constants
+// ---------------------------------------------------------------------------
+
+bool params_ok(const mlmc_params *p) {
+  if (!p) return false;
+  if (!(std::isfinite(p->S0) && std::isfinite(p->K) && std::isfinite(p->r) && std::isfinite(p->sigma) &&
+        std::isfinite(p->T)))
+    return false;
+  if (!(p->S0 > 0.0) || p->K < 0.0 || p->sigma < 0.0 || !(p->T > 0.0)) return false;
+  if (p->payoff < 0 || p->payoff > 3 || p->scheme < 0 || p->scheme > 1) return false;
+  if (p->icdf_method < 1 || p->icdf_method > 3) return false;
+  if (p->icdf_bits < 2 || p->icdf_bits > 14) return false;
+  if (p->icdf_method == 2 && (p->icdf_bits % 2 || p->icdf_bits < 4)) return false;   // two fields of >= 2 bits
+  if (p->formats && p->n_formats < 0) return false;
+  if (p->rng_pack != 0 && p->rng_pack != 1) return false;
+  if (p->reserved != 0) return false;
+  return true;
+}
+
+// Lanes per pack of an approximate-only estimator (packed draws need 3 fields of d bits).
+int pack_lanes(const mlmc_params *p, int variant) {
+  const bool approx_only = variant == MLMC_FIXED_APPROX || variant == MLMC_FP16_APPROX || variant == MLMC_BF16_APPROX;
+  if (!approx_only || !p->rng_pack) return 1;
+  return 32 / p->icdf_bits == 3 ? 3 : 0;  // 0: packing requested but unsupported for this d
+}
+
+int bitlen(double x, int f) {
+  if (x <= 0.0) return 1 - f;
+  return std::max((int)std::floor(std::log2(x)) + 1, 1 - f);
+}
+// e such that x rounded to f fractional bits stays below 2^e: x + 2^-(f+1) < 2^e
+int bitlen_rounded(double x, int f) { return bitlen(x + std::ldexp(1.0, -(f + 1)), f); }
+
+void default_format(const mlmc_params *p, int level, mlmc_format *out) {
+  const double r = p->r, sig = p->sigma, T = p->T, S0 = p->S0, K = p->K;
+  const double h = T / (double)(1LL << level);
+  int f[7] = {12, 16 + level, 14 + level, 12 + level, 12 + level, 12 + level, 14 + level};
+  for (int i = 0; i < 7; ++i) f[i] = std::min(24, std::max(10, f[i]));
+  // S keeps at most 21 fractional bits (the 32-bit datapath holds e_S + f_S <= 30
+  // for the test case), mul2 no more than S
+  f[F_S] = std::min(f[F_S], 21);
+  f[F_MUL2] = std::min(f[F_MUL2], f[F_S]);
+  const double mul1_bound = std::max(16.0 * sig * std::sqrt(h), 128.0 * sig * sig * h);
+  int e[7];
+  e[F_Z] = 3;
+  e[F_CON1] = bitlen_rounded(std::max(std::fabs(r) * 2.0 * h, 0.5 * sig * sig * h), f[F_CON1]);
+  e[F_CON2] = bitlen_rounded(sig * std::sqrt(h), f[F_CON2]);
+  e[F_MUL1] = bitlen(mul1_bound, f[F_MUL1]);
+  e[F_SUM1] = bitlen(std::fabs(r) * 2.0 * h + mul1_bound, f[F_SUM1]);
+  e[F_S] = bitlen_rounded(std::max(S0 * std::exp(std::fabs(r) * T + 6.0 * sig * std::sqrt(T)), K), f[F_S]);
+  e[F_MUL2] = e[F_S] + e[F_SUM1];
+  for (int i = 0; i < 7; ++i) { out->e[i] = (int8_t)e[i]; out->f[i] = (int8_t)f[i]; }
+}
+
+Requant make_rq(int from, int to) {
+  Requant q;
+  if (to >= from) { q.ls = to - from; q.rs = 0; q.radd = 0; }
+  else { q.ls = 0; q.rs = from - to; q.radd = (int64_t)1 << (q.rs - 1); }
+  return q;
+}
+
+// rd of a real constant to f fractional bits, within e integer bits.
+mlmc_status const_fixed(double x, int e, int f, int64_t *out) {
+  const double s = std::ldexp(x, f);
+  if (!(std::fabs(s) < 4503599627370496.0)) return MLMC_EOVERFLOW;
+  const double n = std::floor(s + 0.5);
+  if (std::fabs(n) > std::ldexp(1.0, e + f) - 1.0) return MLMC_EOVERFLOW;
+  *out = (int64_t)n;
+  return MLMC_OK;
+}
+
+// Ranges the int32 / int64 datapath of the level kernel can hold exactly.
+bool format_ok_gpu(const mlmc_format &F, bool milstein, int d) {
+  int e[7], f[7];
+  for (int i = 0; i < 7; ++i) { e[i] = F.e[i]; f[i] = F.f[i]; }
+  for (int i = 0; i < 7; ++i) {
+    if (f[i] < 0 || f[i] > 40) return false;
+    const int w = e[i] + f[i];
+    if (w < 1) return false;
+    if (i < F_MUL2 && w > 31) return false;
+    if (w > 62) return false;
+  }
+  if (f[F_Z] > 28) return false;  // Method-3 evaluation shifts by M3_FRAC - f_Z >= 2; 2 f_Z < 63
+  (void)d;
+  const int F1 = std::max(f[F_CON1], f[F_MUL1]);
+  const int F2 = std::max(f[F_S], f[F_MUL2]);
+  const int zc = e[F_Z] + 1 + f[F_Z];                       // coarse z: one more integer bit
+  if ((e[F_CON2] + f[F_CON2]) + zc > 62) return false;      // con2 * z
+  if (e[F_CON2] + e[F_Z] + 1 + f[F_MUL1] > 62) return false; // left re-quantisation of that product
+  if (e[F_CON1] + 1 + F1 > 60 || e[F_MUL1] + F1 > 60) return false;  // aligned sum1 terms (3 of them)
+  if (std::max(e[F_CON1] + 1, e[F_MUL1]) + 2 + f[F_SUM1] > 62) return false;
+  if (milstein && (e[F_CON1] + f[F_CON1]) + 2 * zc > 62) return false;  // con3 * (z^2 - m)
+  if ((e[F_S] + f[F_S]) + (e[F_SUM1] + f[F_SUM1]) > 62) return false;   // S * sum1
+  if (e[F_S] + e[F_SUM1] + f[F_MUL2] > 62) return false;
+  if (e[F_S] + F2 > 61 || e[F_MUL2] + F2 > 61) return false;           // aligned S + mul2
+  return true;
+}
+
+int family_of(int variant) {
+  // 0 exact f32, 1 exact f64, 2 approx fixed, 3 approx f16, 4 approx bf16, 5 corr fixed, 6 corr f16, 7 corr bf16
+  switch (variant) {
+    case MLMC_FP32_EXACT: return 0;
+    case MLMC_FP64_EXACT: return 1;
+    case MLMC_FIXED_APPROX: return 2;
+    case MLMC_FP16_APPROX: return 3;
+    case MLMC_BF16_APPROX: return 4;
+    case MLMC_NESTED_CORR_FIXED: return 5;
+    case MLMC_NESTED_CORR_FP16: return 6;
+    default: return 7;
+  }
+}
+int cost_kind_of(int variant) {
+  if (variant == MLMC_FP64_EXACT) return 0;
+  if (variant == MLMC_FP32_EXACT) return 1;
+  if (variant == MLMC_FIXED_APPROX || variant == MLMC_FP16_APPROX || variant == MLMC_BF16_APPROX) return 2;
+  return 3;
+}
+
+cudaError_t launch_by_family(int fam, int scheme, int pc, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                             const LaunchArgs &a, int *occ) {
+  switch (fam) {
+    case 12: return launch_approx_fixed_p3(scheme, pc, grid, block, smem, st, a, occ);
+    case 13: return launch_approx_f16_p3(scheme, pc, grid, block, smem, st, a, occ);
+    case 14: return launch_approx_bf16_p3(scheme, pc, grid, block, smem, st, a, occ);
+    case 15: return launch_approx_fx32_p3(scheme, pc, grid, block, smem, st, a, occ);
+    case 16: return launch_approx_fx64_p3(scheme, pc, grid, block, smem, st, a, occ);
+    case 8: return launch_approx_fx32(scheme, pc, grid, block, smem, st, a, occ);
+    case 9: return launch_approx_fx64(scheme, pc, grid, block, smem, st, a, occ);
+    case 10: return launch_corr_fx32(scheme, pc, grid, block, smem, st, a, occ);
+    case 11: return launch_corr_fx64(scheme, pc, grid, block, smem, st, a, occ);
+    case 0: return launch_exact_f32(scheme, pc, grid, block, smem, st, a, occ);
+    case 1: return launch_exact_f64(scheme, pc, grid, block, smem, st, a, occ);
+    case 2: return launch_approx_fixed(scheme, pc, grid, block, smem, st, a, occ);
+    case 3: return launch_approx_f16(scheme, pc, grid, block, smem, st, a, occ);
+    case 4: return launch_approx_bf16(scheme, pc, grid, block, smem, st, a, occ);
+    case 5: return launch_corr_fixed(scheme, pc, grid, block, smem, st, a, occ);
+    case 6: return launch_corr_f16(scheme, pc, grid, block, smem, st, a, occ);
+    default: return launch_corr_bf16(scheme, pc, grid, block, smem, st, a, occ);
+  }
+}
+
+int64_t radd_of(int k) { return k > 0 ? (int64_t)1 << (k - 1) : 0; }
+
+// floor(v / 2^k) for a 128-bit value (k >= 0)
+__int128 floor_shift(__int128 v, int k) { return v >> k; }
+
+// Decide whether the fast fixed-point datapath computes exactly the values of
+// the general one for this format: every rounding is a right shift, and the
+// magnitudes of mul1, mul3, sum1 (from the table bound) and of mul2 (given
+// |S| <= lim_S) can never reach their saturation limits, so that only S needs
+// a run-time range check.  Fills ff and tells whether S needs 64 bits.
+bool fast_fixed(const int e[7], const int f[7], int64_t con1, int64_t con1c, int64_t con2, int64_t con3,
+                int64_t zmax, bool milstein, FastFixed &ff, bool &s64) {
+  typedef __int128 I;
+  const int fZ = f[F_Z];
+  if (f[F_CON1] < f[F_MUL1] || f[F_CON1] < f[F_SUM1] || f[F_S] < f[F_MUL2]) return false;
+  const int rs1 = f[F_CON2] + fZ - f[F_MUL1];
+  const int rs3 = f[F_CON1] + 2 * fZ - f[F_MUL1];
+  const int rs_sum1 = f[F_CON1] - f[F_SUM1];
+  const int rs2 = f[F_S] + f[F_SUM1] - f[F_MUL2];
+  if (rs1 < 0 || rs3 < 0 || rs2 < 0 || rs1 > 62 || rs3 > 62 || rs2 > 62 || rs_sum1 > 30) return false;
+  const int shF1 = f[F_CON1] - f[F_MUL1];
+  const int shS = f[F_S] - f[F_MUL2];
+  if (shF1 > 30 || shS > 30) return false;
+  auto lim = [&](int v) { return ((I)1 << (e[v] + f[v])) - 1; };
+  const I zc = 2 * (I)zmax;  // coarse increments are sums of two table values
+  const I r1 = radd_of(rs1), r3 = radd_of(rs3), rsum = radd_of(rs_sum1), r2 = radd_of(rs2);
+  if ((I)con2 * zc + r1 >= ((I)1 << 62)) return false;
+  const I m1a = floor_shift((I)con2 * zc + r1, rs1), m1b = floor_shift(-(I)con2 * zc + r1, rs1);
+  const I mul1_abs = std::max(m1a, -m1b);
+  if (mul1_abs > lim(F_MUL1)) return false;
+  I mul3_abs = 0;
+  if (milstein) {
+    const I one = (I)1 << (2 * fZ);
+    const I zz_max = zc * zc - one, zz_min = -2 * one;
+    // Z~^2 - m in 32 bits (the kernel forms con3 (Z~^2 - m) as one 32x32 product)
+    if (zc * zc >= ((I)1 << 31) - 1 || 2 * one >= ((I)1 << 31)) return false;
+    if ((I)con3 * zz_max + r3 >= ((I)1 << 62) || zc * zc >= ((I)1 << 62)) return false;
+    const I a = floor_shift((I)con3 * zz_max + r3, rs3), b = floor_shift((I)con3 * zz_min + r3, rs3);
+    mul3_abs = std::max(a < 0 ? -a : a, b < 0 ? -b : b);
+    if (mul3_abs > lim(F_MUL1)) return false;
+  }
+  const I c1max = std::max((I)(con1 < 0 ? -con1 : con1), (I)(con1c < 0 ? -con1c : con1c));
+  const I acc_abs = c1max + rsum + (mul1_abs + mul3_abs) * ((I)1 << shF1);
+  if (acc_abs >= ((I)1 << 31) - 1) return false;
+  const I sum1_abs = floor_shift(acc_abs, rs_sum1) + 1;
+  if (sum1_abs > lim(F_SUM1)) return false;
+  const I limS = lim(F_S);
+  if (limS * sum1_abs + r2 >= ((I)1 << 62)) return false;
+  const I mul2_abs = floor_shift(limS * sum1_abs + r2, rs2) + 1;
+  if (mul2_abs > lim(F_MUL2) || mul2_abs >= ((I)1 << 31)) return false;
+  const I snew = limS + mul2_abs * ((I)1 << shS);
+  if (snew >= ((I)1 << 62)) return false;
+  s64 = !(snew < ((I)1 << 31) - 1);
+  ff.con2 = (int32_t)con2;
+  ff.con3 = (int32_t)con3;
+  ff.con1r = (int32_t)(con1 + (int64_t)rsum);
+  ff.con1cr = (int32_t)(con1c + (int64_t)rsum);
+  ff.mulF1 = 1 << shF1;
+  ff.rs1 = rs1; ff.rs3 = rs3; ff.rs_sum1 = rs_sum1; ff.rs2 = rs2;
+  ff.mulS = 1 << shS;
+  ff.radd1 = (int64_t)r1; ff.radd3 = (int64_t)r3; ff.radd2 = (int64_t)r2;
+  ff.mfine = (int64_t)1 << (2 * fZ);
+  ff.mcoarse = (int64_t)2 << (2 * fZ);
+  ff.limS = (int64_t)limS;
+  return true;
+}
+
+// Largest |table value| in Z's fixed-point format, as the kernels evaluate it.
+int64_t table_zmax_fixed(const std::vector<double> &Z, int d, int method, int fZ) {
+  int64_t zmax = 0;
+  if (method == 2) {
+    const M2Table *t;
+    if (m2_build(d, &t) != MLMC_OK) return INT64_MAX;
+    for (int j = 0; j < (1 << d); ++j)
+      zmax = std::max<int64_t>(zmax, std::llabs(std::llround(std::ldexp(m2_value(*t, d, j, REP_FIXED, fZ), fZ))));
+    return zmax;
+  }
+  if (method == 1) {
+    for (double v : Z) zmax = std::max<int64_t>(zmax, std::llabs((int64_t)std::floor(std::ldexp(v, fZ) + 0.5)));
+    return zmax;
+  }
+  M3Coef c;
+  m3_fit(Z, d, c);
+  const int sh = M3_FRAC - fZ;
+  for (int k = 0; k < (1 << (d - 1)); ++k) {
+    const int cls = k < 2 ? 0 : 31 - __builtin_clz((unsigned)k);
+    const int64_t t = c.A[cls] + c.B[cls] * (int64_t)k;
+    zmax = std::max<int64_t>(zmax, std::llabs((t + ((int64_t)1 << (sh - 1))) >> sh));
+  }
+  return zmax;
+}
+
+
+
+// Split an item's sample groups into chunks of `threads` x groups_per_thread.
+mlmc_status chunk_built(BuiltItem &b, int threads, int spt) {
+  ItemDesc &it = b.it;
+  uint32_t gpt = 1;
+  const uint64_t spg = steps_per_group(it.level);
+  const uint64_t nch = chunk_count(it.g1 - it.g0, spg, b.kp, threads, spt, g.num_sms, &gpt);
+  if (nch > 0x7fffffffULL) return MLMC_EINVAL;
+  it.groups_per_thread = gpt;
+  it.n_chunks = (uint32_t)nch;
+  b.chunk_cost = (double)gpt * (double)threads * (double)spg * b.kp * b.cost_step;
+  return MLMC_OK;
+}
+
+// Packed draws of an item with fewer packs than one wave of resident threads
+// run one sample per thread: latency rather than throughput bounds such items.
+bool lane_split(uint64_t N) {
+  const uint64_t wave = 6ULL * 128ULL * (uint64_t)std::max(1, g.num_sms);
+  return N > 0 && (N + 2) / 3 < wave;
+}
+
+mlmc_status build_item(const mlmc_work &w, int out_index, void *dump, BuiltItem &b, double &disc, int &unit,
+                       int &exact_int) {
+  const mlmc_params *p = w.params;
+  if (!params_ok(p)) return MLMC_EINVAL;
+  if (w.level < 0 || w.level > 20 || w.variant < 0 || w.variant > 7) return MLMC_EINVAL;
+  if (w.stream < -1 || w.stream > 255) return MLMC_EINVAL;
+  const int lev = w.level;
+  // word index s 2^l + i and the group index must stay below 2^62
+  if (w.N > (1ULL << 58) || w.first_sample > (1ULL << (60 - lev)) - w.N) return MLMC_EINVAL;
+  ItemDesc &it = b.it;
+  std::memset(&it, 0, sizeof it);
+  const int v = w.variant;
+  const bool approx = !(v == MLMC_FP32_EXACT || v == MLMC_FP64_EXACT);
+  const int stream = w.stream >= 0 ? w.stream
+                     : (v == MLMC_FIXED_APPROX || v == MLMC_FP16_APPROX || v == MLMC_BF16_APPROX ? 1 : 0);
+  it.first = w.first_sample;
+  it.N = w.N;
+  it.level = lev;
+  it.nlog = lev;
+  it.payoff = p->payoff;
+  it.scheme = p->scheme;
+  it.method = p->icdf_method;
+  it.d = p->icdf_bits;
+  it.ctr2 = (uint32_t)lev | ((uint32_t)stream << 8);
+  it.ctr3 = p->request_id;
+  it.out_index = (uint32_t)out_index;
+  it.dump = dump;
+  if (w.flags & ~MLMC_WORK_ENUMERATE) return MLMC_EINVAL;
+  const bool enumerate = (w.flags & MLMC_WORK_ENUMERATE) != 0;
+  int KP = pack_lanes(p, v);
+  if (enumerate) {
+    // every combination of table cells once: approximate-only, levels 0-1, samples [0, 2^(d 2^l))
+    const bool approx_only = v == MLMC_FIXED_APPROX || v == MLMC_FP16_APPROX || v == MLMC_BF16_APPROX;
+    const int bits = p->icdf_bits << lev;
+    if (!approx_only || lev > 1 || bits > 24 || w.first_sample != 0 || w.N != (1ULL << bits)) return MLMC_EINVAL;
+    KP = 1;
+    it.enumerate = 1;
+  }
+  if (KP == 0) return MLMC_EINVAL;
+  if (KP == 3 && lev >= 2 && lane_split(w.N)) {
+    // few samples: one sample per thread (three times the threads), the same
+    // packed draws (sample s reads lane s mod 3 of pack s / 3)
+    KP = 1;
+    it.lanes = 3;
+  }
+  // sample groups (chunking into CTAs: chunk_built)
+  const uint64_t spc = samples_per_group(lev, KP);
+  it.g0 = w.first_sample / spc;
+  it.g1 = w.N == 0 ? it.g0 : (w.first_sample + w.N + spc - 1) / spc;
+  // groups whose samples all lie in [first, first + N)
+  it.gf0 = (w.first_sample + spc - 1) / spc;
+  it.gf1 = (w.first_sample + w.N) / spc;
+  if (it.gf1 < it.gf0) it.gf1 = it.gf0;
+  b.kp = KP;
+  b.cost_step = g_cost[cost_kind_of(v)];
+  // exact-path constants (the same FP64 expressions as the fixed-point ones)
+  const double h = std::ldexp(p->T, -lev);
+  const double rh = p->r * h, rh2 = p->r * (2.0 * h), sqh = std::sqrt(h);
+  const double c2 = p->sigma * sqh, c3 = 0.5 * p->sigma * p->sigma * h;
+  it.c1d = rh; it.c2d = c2; it.c1cd = rh2; it.c3d = c3; it.S0d = p->S0; it.Kd = p->K;
+  it.c1f = (float)rh; it.c2f = (float)c2; it.c1cf = (float)rh2; it.c3f = (float)c3;
+  it.S0f = (float)p->S0; it.Kf = (float)p->K;
+  disc = std::exp(-p->r * p->T);
+  unit = 0;
+  exact_int = 0;
+  b.smem = 0;
+  bool fast = false, fast64 = false;
+  if (approx) {
+    const bool fixed = (v == MLMC_FIXED_APPROX || v == MLMC_NESTED_CORR_FIXED);
+    const bool bf = (v == MLMC_BF16_APPROX || v == MLMC_NESTED_CORR_BF16);
+    const int rep = fixed ? REP_FIXED : (bf ? REP_BF16 : REP_FP16);
+    int fZ = 0;
+    if (fixed) {
+      mlmc_format F;
+      if (p->formats && lev < p->n_formats) F = p->formats[lev];
+      else if (p->formats) return MLMC_EINVAL;
+      else default_format(p, lev, &F);
+      if (!format_ok_gpu(F, p->scheme == MLMC_MILSTEIN, p->icdf_bits)) return MLMC_EINVAL;
+      int e[7], f[7];
+      for (int i = 0; i < 7; ++i) { e[i] = F.e[i]; f[i] = F.f[i]; }
+      fZ = f[F_Z];
+      FixedConsts &fx = it.fx;
+      int64_t con1, con1c, con2, con3, S0q, Kq;
+      mlmc_status s = MLMC_OK;
+      if ((s = const_fixed(rh, e[F_CON1], f[F_CON1], &con1)) != MLMC_OK) return s;
+      if ((s = const_fixed(rh2, e[F_CON1] + 1, f[F_CON1], &con1c)) != MLMC_OK) return s;
+      if ((s = const_fixed(c2, e[F_CON2], f[F_CON2], &con2)) != MLMC_OK) return s;
+      if ((s = const_fixed(c3, e[F_CON1], f[F_CON1], &con3)) != MLMC_OK) return s;
+      if ((s = const_fixed(p->S0, e[F_S], f[F_S], &S0q)) != MLMC_OK) return s;
+      if ((s = const_fixed(p->K, e[F_S], f[F_S], &Kq)) != MLMC_OK) return s;
+      const int F1 = std::max(f[F_CON1], f[F_MUL1]);
+      const int F2 = std::max(f[F_S], f[F_MUL2]);
+      fx.con1A = con1 * ((int64_t)1 << (F1 - f[F_CON1]));
+      fx.con1cA = con1c * ((int64_t)1 << (F1 - f[F_CON1]));
+      fx.con2 = (int32_t)con2;
+      fx.con3 = (int32_t)con3;
+      fx.S0 = S0q;
+      fx.K = Kq;
+      for (int i = 0; i < 7; ++i) fx.lim[i] = ((int64_t)1 << (e[i] + f[i])) - 1;
+      fx.q_mul1 = make_rq(f[F_CON2] + f[F_Z], f[F_MUL1]);
+      fx.q_mul3 = make_rq(f[F_CON1] + 2 * f[F_Z], f[F_MUL1]);
+      fx.sh_mul1_F1 = F1 - f[F_MUL1];
+      fx.q_sum1 = make_rq(F1, f[F_SUM1]);
+      fx.q_mul2 = make_rq(f[F_S] + f[F_SUM1], f[F_MUL2]);
+      fx.sh_S_F2 = F2 - f[F_S];
+      fx.sh_mul2_F2 = F2 - f[F_MUL2];
+      fx.q_S = make_rq(F2, f[F_S]);
+      fx.fZ2 = 2 * f[F_Z];
+      fx.fS = f[F_S];
+      // the table must fit Z's format
+      double *z64;
+      const std::vector<double> *zh;
+      if ((s = m1_table(p->icdf_bits, &z64, &zh)) != MLMC_OK) return s;
+      const int64_t zmax = table_zmax_fixed(*zh, p->icdf_bits, p->icdf_method, fZ);
+      if ((double)zmax > std::ldexp(1.0, e[F_Z] + fZ) - 1.0) return MLMC_EOVERFLOW;
+      unit = f[F_S] + (p->payoff == MLMC_ASIAN ? lev + 1 : 0);
+      bool s64 = false;
+      fast = fast_fixed(e, f, con1, con1c, con2, con3, zmax, p->scheme == MLMC_MILSTEIN, it.ff, s64);
+      fast64 = s64;
+      if (fast && !s64) {
+        // the 32-bit datapath sums a group's squared terminal payoff differences in
+        // 64 bits: |Y| <= max(lim_S, 2^f_S), so spc samples need spc ymax^2 < 2^64
+        const double ymax = std::max(std::ldexp(1.0, e[F_S] + f[F_S]), std::ldexp(1.0, f[F_S]));
+        if (!((double)spc * ymax * ymax < 0x1p64)) fast64 = true;
+      }
+    } else {
+      uint16_t (*cv)(double) = bf ? bf16_bits : half_bits;
+      it.h_c1 = cv(rh);
+      it.h_c1c = cv(rh2);
+      it.h_c2 = cv(c2);
+      it.h_c3 = cv(c3);
+      it.h_S0 = cv(p->S0);
+      unit = 24;
+    }
+    const void *tab = nullptr;
+    mlmc_status s = get_table(p->icdf_method, p->icdf_bits, rep, fZ, &tab, true);
+    if (s != MLMC_OK) return s;
+    it.ztab = tab;
+    b.smem = p->icdf_method != 3 ? (size_t)(1 << p->icdf_bits) * (fixed ? 4 : 2) : sizeof(M3Coef);
+    exact_int = (v == MLMC_FIXED_APPROX || v == MLMC_FP16_APPROX || v == MLMC_BF16_APPROX) ? 1 : 0;
+    if (p->icdf_method == 2 && !exact_int) {
+      // Method 2 coupling: the correction's exact path reads the interval ranks
+      const uint16_t *perm = nullptr;
+      if ((s = m2_perm_device(p->icdf_bits, &perm)) != MLMC_OK) return s;
+      it.perm = perm;
+      b.smem += sizeof(uint16_t) << p->icdf_bits;
+    }
+  }
+  it.unit = unit;
+  it.unit_scale = std::ldexp(1.0f, -unit);
+  b.family = family_of(v);
+  if (fast) {
+    if (b.family == 2) b.family = fast64 ? 9 : 8;
+    else if (b.family == 5) b.family = fast64 ? 11 : 10;
+  }
+  if (KP == 3) {
+    // packed families: 12 fixed (general), 13 binary16, 14 bfloat16, 15 fixed 32-bit S, 16 fixed 64-bit S
+    switch (b.family) {
+      case 2: b.family = 12; break;
+      case 3: b.family = 13; break;
+      case 4: b.family = 14; break;
+      case 8: b.family = 15; break;
+      case 9: b.family = 16; break;
+      default: return MLMC_EINVAL;
+    }
+  }
+  b.scheme = p->scheme;
+  b.pc = p->payoff == MLMC_ASIAN ? PC_ASIAN : (p->payoff == MLMC_LOOKBACK ? PC_LOOKBACK : PC_TERMINAL);
+  return MLMC_OK;
+}
+
+// build_item through the cache (flags 0): the constants, tables and family
+// come from the first build of the same (params, format, level, variant,
+// stream); the sample range and its groups are set for this call.
+mlmc_status build_item_cached(const mlmc_work &w, int out_index, void *dump, BuiltItem &b, double &disc, int &unit,
+                              int &exact_int) {
+  const mlmc_params *p = w.params;
+  if (w.flags != 0 || !params_ok(p) || w.level < 0 || w.level > 20)
+    return build_item(w, out_index, dump, b, disc, unit, exact_int);
+  std::string key;
+  key.reserve(96);
+  auto put = [&](const void *x, size_t n) { key.append((const char *)x, n); };
+  put(&p->S0, sizeof(double) * 5);
+  put(&p->payoff, sizeof(int32_t) * 4);
+  put(&p->request_id, sizeof(uint32_t));
+  put(&p->rng_pack, sizeof(int32_t));
+  const int has_fmt = p->formats ? (w.level < p->n_formats ? 1 : 2) : 0;
+  put(&has_fmt, sizeof has_fmt);
+  if (has_fmt == 1) put(&p->formats[w.level], sizeof(mlmc_format));
+  put(&w.level, sizeof(int32_t) * 2);     // level, variant
+  put(&w.stream, sizeof(int32_t));
+  const int split = lane_split(w.N) ? 1 : 0;   // the packed-draw layout depends on N
+  put(&split, sizeof split);
+  auto f = g_item_cache.find(key);
+  if (f == g_item_cache.end()) {
+    mlmc_status s = build_item(w, out_index, dump, b, disc, unit, exact_int);
+    if (s != MLMC_OK) return s;
+    if (g_item_cache.size() > 8192) g_item_cache.clear();
+    g_item_cache.emplace(key, CachedItem{b, disc, unit, exact_int});
+    return MLMC_OK;
+  }
+  const int lev = w.level;
+  if (w.N > (1ULL << 58) || w.first_sample > (1ULL << (60 - lev)) - w.N) return MLMC_EINVAL;
+  b = f->second.b;
+  disc = f->second.disc;
+  unit = f->second.unit;
+  exact_int = f->second.exact_int;
+  ItemDesc &it = b.it;
+  it.first = w.first_sample;
+  it.N = w.N;
+  it.out_index = (uint32_t)out_index;
+  it.dump = dump;
+  const uint64_t spc = samples_per_group(lev, b.kp);
+  it.g0 = w.first_sample / spc;
+  it.g1 = w.N == 0 ? it.g0 : (w.first_sample + w.N + spc - 1) / spc;
+  it.gf0 = (w.first_sample + spc - 1) / spc;
+  it.gf1 = (w.first_sample + w.N) / spc;
+  if (it.gf1 < it.gf0) it.gf1 = it.gf0;
+  b.cost_step = g_cost[cost_kind_of(w.variant)];
+  return MLMC_OK;
+}
+
+void make_round_keys(uint64_t seed, RoundKeys &rk) {
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    rk.k[2 * r] = k0;
+    rk.k[2 * r + 1] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+// Deterministic sum of each item's chunk partials (fixed lane assignment and
+// tree order, so repeated launches give bit-identical results).
+
+double cost_of_variant(int variant) { return g_cost[cost_kind_of(variant)]; }
+
+}  // namespace mlmc_host
+
+using namespace mlmc_host;
+
+extern "C" {
+
+mlmc_status mlmc_cost_model(int kind, double cost_per_step) {
+  MLMC_API_LOCK();
+  if (kind < 0 || kind > 3 || !std::isfinite(cost_per_step)) return MLMC_EINVAL;
+  g_cost[kind] = cost_per_step > 0.0 ? cost_per_step : g_cost_default[kind];
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_default_format(const mlmc_params *p, int level, mlmc_format *out) {
+  if (!params_ok(p) || !out || level < 0 || level > 20) return MLMC_EINVAL;
+  default_format(p, level, out);
+  return MLMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,639 @@
+// Plans: device work lists chunked into CTAs and launched as one level kernel
+// per kernel class on forked streams (no host synchronisation), their results,
+// the synchronous entry points (mlmc_level, mlmc_level_dump, mlmc_run), the
+// plan entry points and the launch-shape autotuner.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "item.h"
+#include "kernels.h"
+#include "reduce.cuh"
+#include "mlmc.h"
+#include "tables.h"
+#include "host_api.h"
+
+using namespace mlmc;
+
+
+// The Python binding mirrors these layouts.
+static_assert(sizeof(mlmc_params) == 80, "mlmc_params layout");
+static_assert(sizeof(mlmc_sums) == 72, "mlmc_sums layout");
+static_assert(sizeof(mlmc_work) == 40, "mlmc_work layout");
+static_assert(sizeof(mlmc_sample) == 80, "mlmc_sample layout");
+static_assert(sizeof(mlmc_format) == 14, "mlmc_format layout");
+
+// ---------------------------------------------------------------------------
+// plan object (opaque in the C ABI)
+// ---------------------------------------------------------------------------
+struct LaunchRec {
+  int family;               // kernel family, see launch_by_family
+  int scheme, pc;
+  int threads;              // CTA size
+  uint32_t chunk0, n_chunks;
+  int item_off, n_items;
+  size_t smem;
+};
+
+struct mlmc_plan {
+  int n_work = 0;
+  int threads = 128;
+  std::vector<ItemDesc> items;       // launch sub-arrays first, zero-chunk items last
+  std::vector<LaunchRec> launches;
+  std::vector<double> disc;          // per work item
+  std::vector<int> unit, exact_int;
+  std::vector<uint64_t> N;
+  uint32_t total_chunks = 0;
+  uint64_t path_steps = 0;
+  RoundKeys rk{};
+  ItemDesc *d_items = nullptr;
+  Partial *d_partials = nullptr;
+  DevSums *d_out = nullptr;
+  uint32_t *d_counters = nullptr;    // per item, zero between launches
+  std::vector<uint32_t> empty_out;   // out_index of items without samples (sums reset per launch)
+  std::vector<cudaStream_t> aux;
+  std::vector<cudaEvent_t> join;
+  std::vector<cudaEvent_t> kstart, kstop;   // around each level kernel, on its stream
+  cudaEvent_t fork = nullptr, t0 = nullptr, t1 = nullptr;
+  cudaStream_t last_stream = nullptr;
+  bool launched = false;
+  bool borrowed = false;   // device buffers, streams and events belong to the context arena
+};
+
+namespace mlmc_host {
+
+__global__ void finalize_kernel(const ItemDesc *items, int n_items, const Partial *partials, DevSums *out) {
+  const int i = blockIdx.x;
+  if (i >= n_items) return;
+  const ItemDesc &it = items[i];
+  const DevSums r = warp_sum_partials(partials + it.chunk_begin, it.n_chunks);
+  if (threadIdx.x == 0) out[it.out_index] = r;
+}
+
+void free_plan_device(mlmc_plan *pl) {
+  if (pl->borrowed) {
+    pl->d_items = nullptr; pl->d_partials = nullptr; pl->d_out = nullptr; pl->d_counters = nullptr;
+    pl->aux.clear(); pl->join.clear(); pl->kstart.clear(); pl->kstop.clear();
+    pl->fork = pl->t0 = pl->t1 = nullptr;
+    return;
+  }
+  if (pl->d_items) cudaFree(pl->d_items);
+  if (pl->d_partials) cudaFree(pl->d_partials);
+  if (pl->d_out) cudaFree(pl->d_out);
+  if (pl->d_counters) cudaFree(pl->d_counters);
+  for (auto s : pl->aux) cudaStreamDestroy(s);
+  for (auto e : pl->join) cudaEventDestroy(e);
+  for (auto e : pl->kstart) cudaEventDestroy(e);
+  for (auto e : pl->kstop) cudaEventDestroy(e);
+  pl->kstart.clear(); pl->kstop.clear();
+  if (pl->fork) cudaEventDestroy(pl->fork);
+  if (pl->t0) cudaEventDestroy(pl->t0);
+  if (pl->t1) cudaEventDestroy(pl->t1);
+  pl->d_items = nullptr; pl->d_partials = nullptr; pl->d_out = nullptr; pl->d_counters = nullptr;
+  pl->aux.clear(); pl->join.clear();
+  pl->fork = pl->t0 = pl->t1 = nullptr;
+}
+
+template <class T>
+bool grow(T *&p, size_t &cap, size_t need) {
+  if (need <= cap) return true;
+  if (p) cudaFree(p);
+  p = nullptr;
+  cap = 0;
+  const size_t n = std::max(need, cap * 2);
+  if (cudaMalloc(&p, sizeof(T) * n) != cudaSuccess) return false;
+  cap = n;
+  return true;
+}
+
+bool arena_events(Arena &A, size_t launches) {
+  if (!A.t0) {
+    if (cudaEventCreate(&A.t0) != cudaSuccess || cudaEventCreate(&A.t1) != cudaSuccess ||
+        cudaEventCreateWithFlags(&A.fork, cudaEventDisableTiming) != cudaSuccess)
+      return false;
+  }
+  while (A.aux.size() < launches) {
+    cudaStream_t st;
+    cudaEvent_t j, a, b;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&j, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+      return false;
+    A.aux.push_back(st); A.join.push_back(j); A.kstart.push_back(a); A.kstop.push_back(b);
+  }
+  return true;
+}
+
+mlmc_status plan_create_impl(mlmc_plan **out, const mlmc_work *work, int n_work, uint64_t seed,
+                             const mlmc_tuning *tuning, void *const *dumps, Arena *arena = nullptr,
+                             bool defer_copy = false) {
+  if (!out || !work || n_work <= 0) return MLMC_EINVAL;
+  mlmc_status s = ensure_ctx();
+  if (s != MLMC_OK) return s;
+  int o_threads = 0, o_spt = 0;  // 0: the tuning table's choice per item
+  if (tuning) {
+    o_threads = tuning->threads;
+    o_spt = tuning->steps_per_thread;
+    if (o_threads && (o_threads < 32 || o_threads > 128 || o_threads % 32)) return MLMC_EINVAL;
+    if (o_spt < 0) return MLMC_EINVAL;
+  }
+  mlmc_plan *pl = new (std::nothrow) mlmc_plan;
+  if (!pl) return MLMC_ENOMEM;
+  pl->n_work = n_work;
+  pl->disc.resize(n_work);
+  pl->unit.resize(n_work);
+  pl->exact_int.resize(n_work);
+  pl->N.resize(n_work);
+  std::vector<BuiltItem> built(n_work);
+  std::vector<int> item_threads(n_work);
+  for (int i = 0; i < n_work; ++i) {
+    s = build_item_cached(work[i], i, dumps ? dumps[i] : nullptr, built[i], pl->disc[i], pl->unit[i],
+                          pl->exact_int[i]);
+    if (s != MLMC_OK) { delete pl; return s; }
+    int th, sp;
+    tuning_for(built[i].family, built[i].scheme, built[i].pc, work[i].level, &th, &sp);
+    if (o_threads) th = o_threads;
+    if (o_spt) sp = o_spt;
+    item_threads[i] = th;
+    s = chunk_built(built[i], th, sp);
+    if (s != MLMC_OK) { delete pl; return s; }
+    pl->N[i] = work[i].N;
+    pl->path_steps += work[i].N << work[i].level;
+  }
+  // group by kernel configuration; within a launch, most expensive chunks first
+  std::map<std::tuple<int, int, int, int>, std::vector<int>> groups;
+  std::vector<int> empty;
+  for (int i = 0; i < n_work; ++i) {
+    if (built[i].it.n_chunks == 0) { empty.push_back(i); continue; }
+    groups[std::make_tuple(built[i].family, built[i].scheme, built[i].pc, item_threads[i])].push_back(i);
+  }
+  // launches are ordered by their most expensive CTA, so that the longest
+  // chains (deep levels, exact paths) start first and the rest fill in
+  std::vector<std::pair<double, std::vector<int>>> order;
+  for (auto &kv : groups) {
+    auto &v = kv.second;
+    std::stable_sort(v.begin(), v.end(), [&](int a, int b) { return built[a].chunk_cost > built[b].chunk_cost; });
+    order.push_back({built[v[0]].chunk_cost, v});
+  }
+  std::stable_sort(order.begin(), order.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+  uint32_t chunk = 0;
+  for (auto &o : order) {
+    LaunchRec L;
+    const BuiltItem &b0 = built[o.second[0]];
+    L.family = b0.family; L.scheme = b0.scheme; L.pc = b0.pc;
+    L.threads = item_threads[o.second[0]];
+    L.chunk0 = chunk;
+    L.item_off = (int)pl->items.size();
+    L.n_items = (int)o.second.size();
+    L.smem = 0;
+    for (int i : o.second) {
+      ItemDesc it = built[i].it;
+      it.chunk_begin = chunk;
+      chunk += it.n_chunks;
+      L.smem = std::max(L.smem, built[i].smem);
+      pl->items.push_back(it);
+    }
+    L.n_chunks = chunk - L.chunk0;
+    pl->launches.push_back(L);
+  }
+  for (int i : empty) {
+    ItemDesc it = built[i].it;
+    it.chunk_begin = chunk;
+    pl->items.push_back(it);
+    pl->empty_out.push_back(it.out_index);
+  }
+  pl->total_chunks = chunk;
+  make_round_keys(seed, pl->rk);
+  const size_t ni = pl->items.size();
+  if (arena) {
+    Arena &A = *arena;
+    const size_t nl = pl->launches.size();
+    const size_t old_counters = A.cap_counters;
+    if (!grow(A.items, A.cap_items, ni) || !grow(A.partials, A.cap_chunks, std::max<size_t>(1, chunk)) ||
+        !grow(A.out, A.cap_out, (size_t)n_work) || !grow(A.counters, A.cap_counters, ni) ||
+        !arena_events(A, nl)) {
+      delete pl;
+      return MLMC_ENOMEM;
+    }
+    if (A.cap_counters != old_counters && cudaMemset(A.counters, 0, sizeof(uint32_t) * A.cap_counters) != cudaSuccess) {
+      delete pl;
+      return MLMC_ECUDA;
+    }
+    pl->borrowed = true;
+    pl->d_items = A.items; pl->d_partials = A.partials; pl->d_out = A.out; pl->d_counters = A.counters;
+    pl->fork = A.fork; pl->t0 = A.t0; pl->t1 = A.t1;
+    if (nl > 1) {
+      pl->aux.assign(A.aux.begin(), A.aux.begin() + nl);
+      pl->join.assign(A.join.begin(), A.join.begin() + nl);
+    }
+    pl->kstart.assign(A.kstart.begin(), A.kstart.begin() + nl);
+    pl->kstop.assign(A.kstop.begin(), A.kstop.begin() + nl);
+    if (!defer_copy &&
+        cudaMemcpyAsync(pl->d_items, pl->items.data(), sizeof(ItemDesc) * ni, cudaMemcpyHostToDevice, g.st) !=
+            cudaSuccess) {
+      delete pl;
+      return MLMC_ECUDA;
+    }
+    *out = pl;
+    return MLMC_OK;
+  }
+  if (cudaMalloc(&pl->d_items, sizeof(ItemDesc) * ni) != cudaSuccess ||
+      cudaMalloc(&pl->d_partials, sizeof(Partial) * std::max<uint32_t>(1, chunk)) != cudaSuccess ||
+      cudaMalloc(&pl->d_out, sizeof(DevSums) * n_work) != cudaSuccess ||
+      cudaMalloc(&pl->d_counters, sizeof(uint32_t) * ni) != cudaSuccess) {
+    free_plan_device(pl);
+    delete pl;
+    return MLMC_ENOMEM;
+  }
+  if (cudaMemset(pl->d_counters, 0, sizeof(uint32_t) * ni) != cudaSuccess) {
+    free_plan_device(pl);
+    delete pl;
+    return MLMC_ECUDA;
+  }
+  if (cudaMemcpy(pl->d_items, pl->items.data(), sizeof(ItemDesc) * ni, cudaMemcpyHostToDevice) != cudaSuccess) {
+    free_plan_device(pl);
+    delete pl;
+    return MLMC_ECUDA;
+  }
+  bool ok = cudaEventCreate(&pl->t0) == cudaSuccess && cudaEventCreate(&pl->t1) == cudaSuccess &&
+            cudaEventCreateWithFlags(&pl->fork, cudaEventDisableTiming) == cudaSuccess;
+  if (ok && pl->launches.size() > 1) {
+    for (size_t i = 0; i < pl->launches.size() && ok; ++i) {
+      cudaStream_t st;
+      cudaEvent_t ev;
+      ok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+      if (ok) { pl->aux.push_back(st); pl->join.push_back(ev); }
+    }
+  }
+  for (size_t i = 0; i < pl->launches.size() && ok; ++i) {
+    cudaEvent_t a, b;
+    ok = cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess;
+    if (ok) { pl->kstart.push_back(a); pl->kstop.push_back(b); }
+  }
+  if (!ok) { free_plan_device(pl); delete pl; return MLMC_ECUDA; }
+  *out = pl;
+  return MLMC_OK;
+}
+
+mlmc_status plan_launch_impl(mlmc_plan *pl, cudaStream_t st) {
+  MLMC_CK(cudaEventRecord(pl->t0, st));
+  const bool fork = pl->launches.size() > 1;
+  if (fork) MLMC_CK(cudaEventRecord(pl->fork, st));
+  for (size_t i = 0; i < pl->launches.size(); ++i) {
+    const LaunchRec &L = pl->launches[i];
+    cudaStream_t ls = st;
+    if (fork) {
+      ls = pl->aux[i];
+      MLMC_CK(cudaStreamWaitEvent(ls, pl->fork, 0));
+    }
+    LaunchArgs a;
+    a.items = pl->d_items + L.item_off;
+    a.n_items = L.n_items;
+    a.chunk0 = L.chunk0;
+    a.dyn = nullptr;
+    a.partials = pl->d_partials;
+    a.rk = pl->rk;
+    a.counters = pl->d_counters + L.item_off;
+    a.out = pl->d_out;
+    // per-kernel events only for plans a caller owns (mlmc_plan_kernel_time)
+    if (!pl->borrowed) MLMC_CK(cudaEventRecord(pl->kstart[i], ls));
+    MLMC_CK(launch_by_family(L.family, L.scheme, L.pc, dim3(L.n_chunks), dim3(L.threads), L.smem, ls, a, nullptr));
+    if (!pl->borrowed) MLMC_CK(cudaEventRecord(pl->kstop[i], ls));
+    if (fork) {
+      MLMC_CK(cudaEventRecord(pl->join[i], ls));
+      MLMC_CK(cudaStreamWaitEvent(st, pl->join[i], 0));
+    }
+  }
+  // items without samples: zero sums (no CTA writes them)
+  for (uint32_t o : pl->empty_out) MLMC_CK(cudaMemsetAsync(pl->d_out + o, 0, sizeof(DevSums), st));
+  MLMC_CK(cudaEventRecord(pl->t1, st));
+  pl->last_stream = st;
+  pl->launched = true;
+  return MLMC_OK;
+}
+
+double u128_to_double(uint64_t lo, uint64_t hi) {
+  const unsigned __int128 v = ((unsigned __int128)hi << 64) | lo;
+  return (double)v;
+}
+
+// Per-item results from the undiscounted device sums h (host copy).
+void convert_results(const mlmc_plan *pl, const DevSums *h, float ms, mlmc_sums *out) {
+  for (int i = 0; i < pl->n_work; ++i) {
+    mlmc_sums &o = out[i];
+    std::memset(&o, 0, sizeof o);
+    const double disc = pl->disc[i];
+    o.n = pl->N[i];
+    o.seconds = ms * 1e-3;
+    o.saturations = h[i].nsat;
+    o.unit = pl->unit[i];
+    o.exact_int = pl->exact_int[i];
+    if (o.exact_int) {
+      o.isum = h[i].isum;
+      o.isum2_lo = h[i].isum2_lo;
+      o.isum2_hi = h[i].isum2_hi;
+      o.sum = disc * std::ldexp((double)h[i].isum, -o.unit);
+      o.sum2 = disc * disc * std::ldexp(u128_to_double(h[i].isum2_lo, h[i].isum2_hi), -2 * o.unit);
+    } else {
+      o.sum = disc * h[i].dsum;
+      o.sum2 = disc * disc * h[i].dsum2;
+    }
+  }
+}
+
+mlmc_status plan_results_impl(mlmc_plan *pl, mlmc_sums *out) {
+  if (!pl->launched) return MLMC_ENOTREADY;
+  MLMC_CK(cudaEventSynchronize(pl->t1));
+  float ms = 0.0f;
+  MLMC_CK(cudaEventElapsedTime(&ms, pl->t0, pl->t1));
+  std::vector<DevSums> h(pl->n_work);
+  MLMC_CK(cudaMemcpy(h.data(), pl->d_out, sizeof(DevSums) * pl->n_work, cudaMemcpyDeviceToHost));
+  convert_results(pl, h.data(), ms, out);
+  return MLMC_OK;
+}
+
+template <class T>
+bool grow_pinned(T *&p, size_t &cap, size_t need) {
+  if (need <= cap) return true;
+  if (p) cudaFreeHost(p);
+  p = nullptr;
+  cap = 0;
+  const size_t n = std::max<size_t>(need, 64);
+  if (cudaHostAlloc((void **)&p, sizeof(T) * n, cudaHostAllocDefault) != cudaSuccess) return false;
+  cap = n;
+  return true;
+}
+
+// One synchronous pass on stream st: work list to the device through pinned
+// staging, the launch, the sums back through pinned staging, one stream sync.
+mlmc_status run_sync(const mlmc_work *work, int n_work, uint64_t seed, const mlmc_tuning *tuning,
+                     void *const *dumps, mlmc_sums *out, cudaStream_t st) {
+  mlmc_plan *pl = nullptr;
+  mlmc_status s = plan_create_impl(&pl, work, n_work, seed, tuning, dumps, &g.arena, true);
+  if (s != MLMC_OK) return s;
+  Arena &A = g.arena;
+  const size_t ni = pl->items.size();
+  do {
+    if (!grow_pinned(A.h_items, A.cap_h_items, ni) || !grow_pinned(A.h_out, A.cap_h_out, (size_t)n_work)) {
+      s = MLMC_ENOMEM;
+      break;
+    }
+    std::memcpy(A.h_items, pl->items.data(), sizeof(ItemDesc) * ni);
+    if (cudaMemcpyAsync(pl->d_items, A.h_items, sizeof(ItemDesc) * ni, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      s = MLMC_ECUDA;
+      break;
+    }
+    if ((s = plan_launch_impl(pl, st)) != MLMC_OK) break;
+    float ms = 0.0f;
+    if (cudaMemcpyAsync(A.h_out, pl->d_out, sizeof(DevSums) * n_work, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess || cudaEventElapsedTime(&ms, pl->t0, pl->t1) != cudaSuccess) {
+      s = MLMC_ECUDA;
+      break;
+    }
+    convert_results(pl, A.h_out, ms, out);
+  } while (0);
+  free_plan_device(pl);
+  delete pl;
+  return s;
+}
+
+
+mlmc_status plan_create_transient(mlmc_plan **out, const mlmc_work *work, int n_work, uint64_t seed,
+                                  const mlmc_tuning *tuning) {
+  return plan_create_impl(out, work, n_work, seed, tuning, nullptr, &g.arena);
+}
+mlmc_status plan_launch_on(mlmc_plan *pl, cudaStream_t st) {
+  if (st != g.st) {
+    // a transient plan's work list was copied on the context stream: order after it
+    MLMC_CK(cudaEventRecord(g.arena.fork, g.st));
+    MLMC_CK(cudaStreamWaitEvent(st, g.arena.fork, 0));
+  }
+  return plan_launch_impl(pl, st);
+}
+const mlmc::DevSums *plan_out_device(const mlmc_plan *pl) { return pl->d_out; }
+void plan_item_scale(const mlmc_plan *pl, int i, double *disc, int *unit, int *exact_int) {
+  *disc = pl->disc[i];
+  *unit = pl->unit[i];
+  *exact_int = pl->exact_int[i];
+}
+void plan_release(mlmc_plan *pl) {
+  free_plan_device(pl);
+  delete pl;
+}
+
+// Median device time (ms) of `reps` launches of a plan of `work` (launch
+// shapes from the tuning table), after one untimed launch.
+mlmc_status time_plan(const mlmc_work *work, int n_work, uint64_t seed, int reps, double *ms) {
+  mlmc_plan *pl = nullptr;
+  mlmc_status s = plan_create_impl(&pl, work, n_work, seed, nullptr, nullptr);
+  if (s != MLMC_OK) return s;
+  std::vector<float> v;
+  for (int r = 0; r <= reps && s == MLMC_OK; ++r) {
+    s = plan_launch_impl(pl, g.st);
+    float x = 0.0f;
+    if (s == MLMC_OK && (cudaEventSynchronize(pl->t1) != cudaSuccess ||
+                         cudaEventElapsedTime(&x, pl->t0, pl->t1) != cudaSuccess))
+      s = MLMC_ECUDA;
+    if (r > 0) v.push_back(x);
+  }
+  free_plan_device(pl);
+  delete pl;
+  if (s != MLMC_OK) return s;
+  std::sort(v.begin(), v.end());
+  *ms = v[v.size() / 2];
+  return MLMC_OK;
+}
+
+}  // namespace mlmc_host
+
+using namespace mlmc_host;
+
+extern "C" {
+
+
+mlmc_status mlmc_level(int level, uint64_t N, const mlmc_params *p, mlmc_variant v, uint64_t seed,
+                       uint64_t first_sample, mlmc_sums *out) {
+  MLMC_API_LOCK();
+  if (!out) return MLMC_EINVAL;
+  mlmc_work w;
+  std::memset(&w, 0, sizeof w);
+  w.params = p; w.level = level; w.variant = (int32_t)v; w.first_sample = first_sample; w.N = N; w.stream = -1;
+  mlmc_status s = ensure_ctx();
+  if (s != MLMC_OK) return s;
+  return run_sync(&w, 1, seed, nullptr, nullptr, out, g.st);
+}
+
+mlmc_status mlmc_level_dump(int level, uint64_t N, const mlmc_params *p, mlmc_variant v, uint64_t seed,
+                            uint64_t first_sample, int32_t stream, mlmc_sample *d_samples, mlmc_sums *out) {
+  MLMC_API_LOCK();
+  if (!out || (N > 0 && !d_samples)) return MLMC_EINVAL;
+  mlmc_work w;
+  std::memset(&w, 0, sizeof w);
+  w.params = p; w.level = level; w.variant = (int32_t)v; w.first_sample = first_sample; w.N = N;
+  w.stream = stream;
+  mlmc_status s = ensure_ctx();
+  if (s != MLMC_OK) return s;
+  void *dumps[1] = {d_samples};
+  return run_sync(&w, 1, seed, nullptr, dumps, out, g.st);
+}
+
+mlmc_status mlmc_plan_create(mlmc_plan **plan, const mlmc_work *work, int n_work, uint64_t seed,
+                             const mlmc_tuning *tuning) {
+  MLMC_API_LOCK();
+  return plan_create_impl(plan, work, n_work, seed, tuning, nullptr);
+}
+
+mlmc_status mlmc_plan_launch(mlmc_plan *plan, void *stream) {
+  MLMC_API_LOCK();
+  if (!plan) return MLMC_EINVAL;
+  return plan_launch_impl(plan, (cudaStream_t)stream);
+}
+
+mlmc_status mlmc_plan_results(mlmc_plan *plan, mlmc_sums *out) {
+  MLMC_API_LOCK();
+  if (!plan || !out) return MLMC_EINVAL;
+  return plan_results_impl(plan, out);
+}
+
+mlmc_status mlmc_plan_info(const mlmc_plan *plan, int *kernels, uint64_t *ctas, uint64_t *path_steps,
+                           uint64_t *h2d_bytes, uint64_t *d2h_bytes) {
+  if (!plan) return MLMC_EINVAL;
+  if (kernels) *kernels = (int)plan->launches.size();
+  if (ctas) *ctas = plan->total_chunks;
+  if (path_steps) *path_steps = plan->path_steps;
+  if (h2d_bytes) *h2d_bytes = sizeof(ItemDesc) * plan->items.size();
+  if (d2h_bytes) *d2h_bytes = sizeof(DevSums) * (uint64_t)plan->n_work;
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_plan_launch_info(const mlmc_plan *plan, int k, int *family, int *items, uint64_t *ctas,
+                                  uint64_t *path_steps) {
+  if (!plan || k < 0 || k >= (int)plan->launches.size()) return MLMC_EINVAL;
+  const LaunchRec &L = plan->launches[k];
+  if (family) *family = L.family;
+  if (items) *items = L.n_items;
+  if (ctas) *ctas = L.n_chunks;
+  if (path_steps) {
+    uint64_t ps = 0;
+    for (int i = 0; i < L.n_items; ++i) {
+      const ItemDesc &it = plan->items[L.item_off + i];
+      ps += it.N << it.level;
+    }
+    *path_steps = ps;
+  }
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_plan_kernel_time(const mlmc_plan *plan, int k, int *family, double *ms) {
+  if (!plan || k < 0 || k >= (int)plan->launches.size()) return MLMC_EINVAL;
+  if (!plan->launched) return MLMC_ENOTREADY;
+  if (family) *family = plan->launches[k].family;
+  if (ms) {
+    MLMC_CK(cudaEventSynchronize(plan->kstop[k]));
+    float t = 0.0f;
+    MLMC_CK(cudaEventElapsedTime(&t, plan->kstart[k], plan->kstop[k]));
+    *ms = t;
+  }
+  return MLMC_OK;
+}
+
+void mlmc_plan_destroy(mlmc_plan *plan) {
+  MLMC_API_LOCK();
+  if (!plan) return;
+  if (plan->launched) cudaEventSynchronize(plan->t1);
+  free_plan_device(plan);
+  delete plan;
+}
+
+mlmc_status mlmc_autotune(const mlmc_work *work, int n_work, uint64_t seed, int reps, mlmc_tuning *chosen) {
+  MLMC_API_LOCK();
+  if (!work || n_work <= 0 || reps < 1 || reps > 1000) return MLMC_EINVAL;
+  mlmc_status s = ensure_ctx();
+  if (s != MLMC_OK) return s;
+  // kernel classes among the items, with their model work
+  typedef std::tuple<int, int, int, int> Key;
+  std::map<Key, std::vector<int>> cls;
+  std::map<Key, double> work_of;
+  std::vector<BuiltItem> built(n_work);
+  for (int i = 0; i < n_work; ++i) {
+    double disc;
+    int unit, ei;
+    if ((s = build_item(work[i], i, nullptr, built[i], disc, unit, ei)) != MLMC_OK) return s;
+    const Key k = std::make_tuple(built[i].family, built[i].scheme, built[i].pc, level_class(work[i].level));
+    cls[k].push_back(i);
+    work_of[k] += std::ldexp((double)work[i].N, work[i].level) * built[i].cost_step;
+  }
+  std::vector<Key> order;
+  for (auto &kv : cls) order.push_back(kv.first);
+  std::stable_sort(order.begin(), order.end(), [&](const Key &a, const Key &b) { return work_of[a] > work_of[b]; });
+  static const int cand_threads[] = {128, 96, 64};
+  static const int cand_spt[] = {256, 64, 128, 512, 1024, 2048};
+  // one pass of coordinate descent: each class in turn takes the shape that
+  // makes the whole work list fastest, the other classes keeping theirs
+  for (const Key &k : order) {
+    const std::vector<int> &ix = cls[k];
+    int cur_t, cur_s;
+    tuning_for(std::get<0>(k), std::get<1>(k), std::get<2>(k), work[ix[0]].level, &cur_t, &cur_s);
+    int best_t = cur_t, best_s = cur_s;
+    double best_ms = 0.0;
+    if ((s = time_plan(work, n_work, seed, reps, &best_ms)) != MLMC_OK) return s;
+    std::vector<std::vector<uint32_t>> seen;   // chunkings already timed
+    for (int pass = 0; pass < 2; ++pass)
+      for (int th : cand_threads)
+        for (int sp : cand_spt) {
+          if (pass == 0 && !(th == cur_t && sp == cur_s)) continue;   // the current shape first
+          std::vector<uint32_t> sig{(uint32_t)th};
+          for (int i : ix) {
+            BuiltItem b = built[i];
+            if ((s = chunk_built(b, th, sp)) != MLMC_OK) return s;
+            sig.push_back(b.it.groups_per_thread);
+          }
+          if (std::find(seen.begin(), seen.end(), sig) != seen.end()) continue;
+          seen.push_back(sig);
+          if (pass == 0) continue;
+          g_tune[k] = std::make_pair(th, sp);
+          double ms = 0.0;
+          if ((s = time_plan(work, n_work, seed, reps, &ms)) != MLMC_OK) return s;
+          // a candidate must make the work list 2% faster than the best so far
+          if (ms < 0.98 * best_ms) {
+            best_ms = ms;
+            best_t = th;
+            best_s = sp;
+          }
+        }
+    g_tune[k] = std::make_pair(best_t, best_s);
+    if (chosen)
+      for (int i : ix) {
+        chosen[i].threads = best_t;
+        chosen[i].steps_per_thread = best_s;
+      }
+  }
+  return MLMC_OK;
+}
+
+void mlmc_tuning_reset(void) {
+  MLMC_API_LOCK();
+  g_tune.clear();
+}
+
+mlmc_status mlmc_run(const mlmc_work *work, int n_work, uint64_t seed, const mlmc_tuning *tuning,
+                     mlmc_sums *out, void *stream) {
+  MLMC_API_LOCK();
+  if (!out) return MLMC_EINVAL;
+  return run_sync(work, n_work, seed, tuning, nullptr, out, (cudaStream_t)stream);
+}
+
+}  // extern "C"
