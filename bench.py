@@ -50,7 +50,7 @@ ALU_PEAK_TOPS = 152 * 4 * 32 * 2.070e9 / 1e12
 #       python bench.py --steps 3 --warmup 3 --no-cpu-baseline --no-tte \
 #       --no-serving-sample --no-autotune --no-optimiser
 # keyed by (family, path-steps per launch); another launch reports null
-DOMINANT_TRAFFIC = {(15, 51213208): 114432}
+DOMINANT_TRAFFIC = {}
 
 
 def build_items(m, rank=0):
@@ -117,32 +117,27 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def dominant_alone(m, torch, items, seed, tuning, dom, ps, flush, stream, reps=10):
-    """The dominant launch's items (the packed approximate items: fewer packs than
-    one wave of resident threads run one sample per thread in another launch) as
-    a plan of their own, timed with CUDA events with the GPU to itself, outside
-    the timed region.  None unless that plan is exactly the step's launch."""
-    wave = 6 * 128 * torch.cuda.get_device_properties(stream.device).multi_processor_count
-    sub = [it for it in items if it["variant"] == m.FIXED_APPROX
-           and (it["level"] < 2 or (it["N"] + 2) // 3 >= wave)]
-    plan = m.Plan(sub, seed, tuning)
+def dominant_alone(m, torch, items, seed, tuning, plan, j, flush, stream, reps=10):
+    """Launch j of the step's plan (the dominant one) on its own: a plan of the
+    same work items, timed with CUDA events with the GPU to itself, outside the
+    timed region.  None unless that plan is exactly one launch of the same
+    family and path-steps."""
+    fam, _, _, ps = plan.launch_info(j)
+    sub_plan = m.Plan([items[i] for i in plan.launch_items(j)], seed, tuning)
     try:
-        if plan.info()["kernels"] != 1:
-            return None
-        fam, _, _, lps = plan.launch_info(0)
-        if fam != dom or lps != ps:
+        if sub_plan.info()["kernels"] != 1 or sub_plan.launch_info(0)[0] != fam or sub_plan.launch_info(0)[3] != ps:
             return None
         for _ in range(3):
-            plan.launch(stream)
+            sub_plan.launch(stream)
         ms = []
         for _ in range(reps):
             flush.zero_()
-            plan.launch(stream)
-            ms.append(plan.kernel_time(0)[1])
+            sub_plan.launch(stream)
+            ms.append(sub_plan.kernel_time(0)[1])
         torch.cuda.synchronize()
         return statistics.median(ms)
     finally:
-        plan.close()
+        sub_plan.close()
 
 
 def oracle_step_sample(meta, cfg, fraction, rank=0):
@@ -311,7 +306,7 @@ def main():
                     "kernel": fam_names[dom],
                     "ms_per_launch": dom_ms, "ops_per_path_step": OPS_APPROX_FIXED_EM,
                     "path_steps_per_launch": ps}
-        alone_ms = dominant_alone(m, torch, items, cfg["seed"], tuning, dom, ps, flush, stream)
+        alone_ms = dominant_alone(m, torch, items, cfg["seed"], tuning, plan, j, flush, stream)
         if alone_ms:
             # the same launch with the GPU to itself (in the step it shares the
             # SMs with the other two level kernels)

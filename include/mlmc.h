@@ -235,6 +235,11 @@ mlmc_status mlmc_plan_kernel_time(const mlmc_plan *plan, int k, int *family, dou
  * its items); any output may be NULL.  MLMC_EINVAL for k out of range. */
 mlmc_status mlmc_plan_launch_info(const mlmc_plan *plan, int k, int *family, int *items, uint64_t *ctas,
                                   uint64_t *path_steps);
+/* Work items of level-kernel launch k: their positions in the work list given
+ * to mlmc_plan_create, in launch order, written to work_index (host array of
+ * cap entries; at most cap are written) and their number to *n.  MLMC_EINVAL
+ * for k out of range, a NULL n, or cap > 0 with a NULL work_index. */
+mlmc_status mlmc_plan_launch_items(const mlmc_plan *plan, int k, int32_t *work_index, int cap, int *n);
 void mlmc_plan_destroy(mlmc_plan *plan);
 
 /* Host-buffer convenience: create, launch on `stream`, read results, destroy. */

@@ -110,9 +110,10 @@ void default_format(const mlmc_params *p, int level, mlmc_format *out);
 mlmc::Requant make_rq(int from, int to);
 mlmc_status const_fixed(double x, int e, int f, int64_t *out);
 bool format_ok_gpu(const mlmc_format &F, bool milstein, int d);
-// Proof on the host that only S can saturate (the fast fixed-point datapath).
+// Proof on the host that only S can saturate (the fast fixed-point datapath),
+// for paths of nsteps fine steps; also decides ff.lazy.
 bool fast_fixed(const int e[7], const int f[7], int64_t con1, int64_t con1c, int64_t con2, int64_t con3,
-                int64_t zmax, bool milstein, mlmc::FastFixed &ff, bool &s64);
+                int64_t zmax, bool milstein, int64_t nsteps, mlmc::FastFixed &ff, bool &s64);
 int64_t table_zmax_fixed(const std::vector<double> &Z, int d, int method, int fZ);
 int family_of(int variant);
 int cost_kind_of(int variant);

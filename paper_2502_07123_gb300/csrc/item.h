@@ -53,7 +53,8 @@ struct FastFixed {
   int64_t radd1, radd3, radd2;
   int64_t mfine, mcoarse;    // 1 and 2 in units 2^-2fZ (Milstein)
   int64_t limS;
-  int32_t pad0, pad1;
+  int32_t lazy;              // 32-bit S may run unclamped, checked once per pack (fast_fixed)
+  int32_t pad1;
 };
 
 struct ItemDesc {

@@ -29,7 +29,6 @@ using namespace mlmc;
 
 namespace mlmc_host {
 
-
 // Work items already built, by everything their constants depend on (params,
 // the level's format, level, variant, stream); the sample range is set per call.
 struct CachedItem {
@@ -210,7 +209,7 @@ __int128 floor_shift(__int128 v, int k) { return v >> k; }
 // |S| <= lim_S) can never reach their saturation limits, so that only S needs
 // a run-time range check.  Fills ff and tells whether S needs 64 bits.
 bool fast_fixed(const int e[7], const int f[7], int64_t con1, int64_t con1c, int64_t con2, int64_t con3,
-                int64_t zmax, bool milstein, FastFixed &ff, bool &s64) {
+                int64_t zmax, bool milstein, int64_t nsteps, FastFixed &ff, bool &s64) {
   typedef __int128 I;
   const int fZ = f[F_Z];
   if (f[F_CON1] < f[F_MUL1] || f[F_CON1] < f[F_SUM1] || f[F_S] < f[F_MUL2]) return false;
@@ -263,6 +262,29 @@ bool fast_fixed(const int e[7], const int f[7], int64_t con1, int64_t con1c, int
   ff.mfine = (int64_t)1 << (2 * fZ);
   ff.mcoarse = (int64_t)2 << (2 * fZ);
   ff.limS = (int64_t)limS;
+  // Lazy saturation of the 32-bit datapath (approximate-only kernels): S runs
+  // unclamped, its running maximum is compared with lim_S once per pack, and a
+  // pack that went above is simulated again with the clamps.  The values are
+  // those of the clamped datapath as long as no path can pass below -lim_S
+  // while it stays at or below +lim_S:
+  //  * sum1 >= -1 (sum1_min below): from S_k >= 0 a step ends at or above
+  //    -mulS (S + S sum1 >= 0, minus one unit of mul2);
+  //  * from S_k < 0 the magnitude grows at most to |S_k| (1 + a) + mulS,
+  //    a = max |sum1|, so B_{k+1} = B_k (1 + a) + mulS bounds it from B_0 = 0
+  //    (S_0 > 0) and B_n <= lim_S after the path's n steps suffices;
+  //  * the first value above +lim_S cannot wrap (snew < 2^31 above).
+  ff.lazy = 0;
+  if (!s64) {
+    const I c1min = std::min((I)con1, (I)con1c);
+    const I sum1_min = floor_shift(c1min + rsum - (mul1_abs + mul3_abs) * ((I)1 << shF1), rs_sum1);
+    if (sum1_min >= -((I)1 << f[F_SUM1])) {
+      const long double a = std::ldexp((long double)sum1_abs, -f[F_SUM1]);
+      const long double n = (long double)nsteps, mS = (long double)ff.mulS;
+      const long double Bn = a > 0.0L ? mS * (std::pow(1.0L + a, n) - 1.0L) / a : mS * n;
+      // a factor-2 margin on the long double evaluation
+      if (std::isfinite((double)Bn) && 2.0L * Bn <= (long double)limS) ff.lazy = 1;
+    }
+  }
   return true;
 }
 
@@ -430,7 +452,8 @@ mlmc_status build_item(const mlmc_work &w, int out_index, void *dump, BuiltItem 
       if ((double)zmax > std::ldexp(1.0, e[F_Z] + fZ) - 1.0) return MLMC_EOVERFLOW;
       unit = f[F_S] + (p->payoff == MLMC_ASIAN ? lev + 1 : 0);
       bool s64 = false;
-      fast = fast_fixed(e, f, con1, con1c, con2, con3, zmax, p->scheme == MLMC_MILSTEIN, it.ff, s64);
+      fast = fast_fixed(e, f, con1, con1c, con2, con3, zmax, p->scheme == MLMC_MILSTEIN, (int64_t)1 << lev, it.ff,
+                        s64);
       fast64 = s64;
       if (fast && !s64) {
         // the 32-bit datapath sums a group's squared terminal payoff differences in
@@ -544,9 +567,6 @@ void make_round_keys(uint64_t seed, RoundKeys &rk) {
     k1 += 0xBB67AE85u;
   }
 }
-
-// Deterministic sum of each item's chunk partials (fixed lane assignment and
-// tree order, so repeated launches give bit-identical results).
 
 double cost_of_variant(int variant) { return g_cost[cost_kind_of(variant)]; }
 

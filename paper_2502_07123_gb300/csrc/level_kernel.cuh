@@ -76,6 +76,12 @@ struct LevelSim {
   using AS = typename std::conditional<AP == AP_FX32, int32_t, int64_t>::type;  // fixed-point S
   // saturation flag of the fast datapath: OR of (clamped ^ unclamped) for a 32-bit S
   using SatT = typename std::conditional<AP == AP_FX32, uint32_t, bool>::type;
+  // Approximate-only 32-bit datapath: when the host proved it exact (ff.lazy),
+  // a group of packs first runs with S unclamped, tracking only its running
+  // maximum hi; if hi stayed at or below lim_S no clamp would have acted and the
+  // values are final, otherwise the group runs again on the clamped (EAGER)
+  // datapath.
+  static constexpr bool LAZY = (EST == EST_APPROX && AP == AP_FX32);
   using X = typename XType<XP>::T;
   using H = typename HType<AP>::T;
   using HO = HalfOps<H>;
@@ -101,6 +107,7 @@ struct LevelSim {
   X S, Sc, zprev, accF, accC, minF, minC;
   AS aS[KP], aSc[KP], aminF[KP], aminC[KP];
   SatT satb[KP];
+  AS hi;   // LAZY: running maximum of S over a group's lanes and steps (reset by the caller)
   int64_t aaccF[KP], aaccC[KP];
   int32_t azprev[KP];
   H hS[KP], hSc[KP], hzprev[KP], hminF[KP], hminC[KP];
@@ -162,6 +169,9 @@ struct LevelSim {
       pS = HO2::splat(hS0); pSc = pS; pzprev = HO2::splat(HO::from_f(0.0f));
     }
   }
+  // LAZY: did some S since hi was reset leave [-lim_S, lim_S]?  (The host
+  // proved that it cannot leave below first.)
+  __device__ __forceinline__ bool over() const { return hi > (AS)ff.limS; }
 
   // ---- exact path (FP32 / FP64) ----
   __device__ __forceinline__ X exact_inc(X z, X cc1, X mm) const {
@@ -185,6 +195,7 @@ struct LevelSim {
   }
 
   // ---- fast fixed-point Algorithm-1 step (same values as fx_step while S stays in range) ----
+  template <bool EAGER>
   __device__ __forceinline__ AS ff_step(AS s, int32_t z, int32_t c1r, int64_t m, SatT &satb) {
     const int32_t mul1 = (int32_t)(((int64_t)ff.con2 * z + ff.radd1) >> ff.rs1);
     int32_t acc = c1r + mul1 * ff.mulF1;
@@ -201,6 +212,10 @@ struct LevelSim {
     } else {
       const int32_t mul2 = (int32_t)((int64_t)((uint64_t)s * (uint64_t)(int64_t)sum1 + (uint64_t)ff.radd2) >> ff.rs2);
       s = (int64_t)((uint64_t)s + (uint64_t)((int64_t)mul2 * ff.mulS));
+    }
+    if constexpr (LAZY && !EAGER) {
+      hi = max(hi, s);
+      return s;
     }
     // saturation of S (the only variable the host could not bound)
     const AS lim = (AS)ff.limS;
@@ -283,7 +298,7 @@ struct LevelSim {
 
   // One fine step i driven by J, and the coarse step after odd i (levels >= 1).
   // PAR: parity of i when known at compile time (0 even, 1 odd), -1 otherwise.
-  template <bool COARSE, int PAR = -1>
+  template <bool COARSE, int PAR = -1, bool EAGER = true>
   __device__ __forceinline__ void step(uint32_t J, int i) {
     const bool odd = PAR >= 0 ? (PAR == 1) : ((i & 1) != 0);
     if constexpr (HAS_EXACT) {
@@ -351,13 +366,13 @@ struct LevelSim {
         if constexpr (FIXED) {
           const int32_t z = fixed_z(Jl);
           if constexpr (PC == PC_ASIAN) { if (i > 0) aaccF[l] += aS[l]; }
-          if constexpr (FAST) aS[l] = ff_step(aS[l], z, ff.con1r, ff.mfine, satb[l]);
+          if constexpr (FAST) aS[l] = ff_step<EAGER>(aS[l], z, ff.con1r, ff.mfine, satb[l]);
           else aS[l] = fx_step(aS[l], z, fx.con1A, 1, sat[l]);
           if constexpr (PC == PC_LOOKBACK) aminF[l] = aS[l] < aminF[l] ? aS[l] : aminF[l];
           if constexpr (COARSE) {
             if (odd) {
               if constexpr (PC == PC_ASIAN) { if (i > 1) aaccC[l] += aSc[l]; }
-              if constexpr (FAST) aSc[l] = ff_step(aSc[l], azprev[l] + z, ff.con1cr, ff.mcoarse, satb[l]);
+              if constexpr (FAST) aSc[l] = ff_step<EAGER>(aSc[l], azprev[l] + z, ff.con1cr, ff.mcoarse, satb[l]);
               else aSc[l] = fx_step(aSc[l], azprev[l] + z, fx.con1cA, 2, sat[l]);
               if constexpr (PC == PC_LOOKBACK) aminC[l] = aSc[l] < aminC[l] ? aSc[l] : aminC[l];
             } else {
@@ -437,8 +452,9 @@ struct LevelSim {
     return __float2ll_rn(__fmul_rn(P, 16777216.0f));
   }
 
-  // Finish the sample: payoffs, sample value, accumulation and optional dump.
-  template <class Acc>
+  // Finish the sample: payoffs, sample value, accumulation and optional dump
+  // (EAGER false: a LAZY pack that stayed in range, so no saturation).
+  template <bool EAGER = true, class Acc>
   __device__ __forceinline__ void finish(Acc &acc, int l, bool valid, mlmc_sample_rec *dump) {
     X pf = X(0), pc = X(0);
     int64_t qf = 0, qc = 0, afS = 0, acS = 0;
@@ -452,7 +468,7 @@ struct LevelSim {
       if (level > 0) qc = fixed_payoff(aSc[l], aaccC[l], aminC[l], nsteps >> 1, true);
       afS = aS[l];
       acS = aSc[l];
-      if constexpr (FAST) lsat = satb[l] ? 1u : 0u;
+      if constexpr (FAST) lsat = (EAGER && satb[l]) ? 1u : 0u;
       else lsat = sat[l];
     }
     if constexpr (HALF) {
@@ -532,6 +548,16 @@ struct ThreadAcc {
     add_u128(q_lo, q_hi, gq, 0);
     gq = 0;
   }
+  // Integer sums at the start of a group (the group's own sum of squares gq is
+  // zero there), to undo the group's samples.
+  struct Mark {
+    int64_t isum;
+    uint64_t q_lo, q_hi;
+  };
+  __device__ __forceinline__ Mark mark() const { return Mark{isum, q_lo, q_hi}; }
+  __device__ __forceinline__ void rewind(const Mark &m) {
+    isum = m.isum; q_lo = m.q_lo; q_hi = m.q_hi; gq = 0;
+  }
   template <class T>
   __device__ __forceinline__ void add_real(T y) {
     if constexpr (XP == XP_F64 && EST == EST_EXACT) {
@@ -588,6 +614,11 @@ __device__ __forceinline__ void block_reduce_write(ThreadAcc<EST, XP> &a, Partia
   }
 }
 
+// The compiler may not reuse a value computed before this point: the clamped
+// re-run of a LAZY group recomputes its draws instead of keeping the first
+// run's live in registers through the group.
+__device__ __forceinline__ void opaque(uint64_t &x) { asm volatile("" : "+l"(x)); }
+
 // Simulate one chunk of an item (its table already in shared memory) and
 // write the CTA's Partial for it.
 template <int EST, int XP, int AP, int SCHEME, int PC, int KP, int MSEL, bool DUMP>
@@ -611,77 +642,100 @@ __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDes
 
   const uint64_t gf0 = it.gf0, gf1 = it.gf1;
   const uint32_t ng = gend > gbeg ? (uint32_t)(gend - gbeg) : 0u;
+  // LAZY items run each group first with S unclamped and the samples added to
+  // the accumulators tentatively; a group whose S went above lim_S is undone
+  // and run again on the clamped datapath (rare).  The check is once per
+  // group, so the group's packs stay one straight-line block.
+  const bool lazy = Sim::LAZY && !DUMP && it.ff.lazy;
   // A group is one Philox call's worth of packs (4 on level 0, 2 on level 1) or,
   // from level 2, one pack over 2^l / 4 calls; a pack holds KP samples.
   for (uint32_t r = threadIdx.x; r < ng; r += blockDim.x) {
     const uint64_t g = gbeg + r;
     const bool full = g >= gf0 && g < gf1;
-    if (lev >= 2) {
-      uint64_t P = g;
-      uint32_t lsh = 0;   // lane-split packed draws: this sample's field to the top of the word
-      if constexpr (KP == 1 && EST == EST_APPROX) {
-        if (it.lanes > 1) {
-          P = g / 3u;
-          lsh = (uint32_t)it.d * (uint32_t)(g - P * 3u);
-        }
-      }
-      const uint32_t calls = 1u << (lev - 2);
-      const uint64_t qbase = P * calls;
-      sim.begin();
-      for (uint32_t c = 0; c < calls; ++c) {
-        const uint64_t q = qbase + c;
-        const uint4 w = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), ctr_hi.z, ctr_hi.w), args.rk);
-        const int i0 = (int)(c << 2);
-        sim.template step<true, 0>(w.x << lsh, i0);
-        sim.template step<true, 1>(w.y << lsh, i0 + 1);
-        sim.template step<true, 0>(w.z << lsh, i0 + 2);
-        sim.template step<true, 1>(w.w << lsh, i0 + 3);
-      }
-#pragma unroll
-      for (int l = 0; l < KP; ++l) {
-        const uint64_t s = KP == 1 ? g : P * KP + l;
-        const bool valid = full || (s >= first && s < last);
-        sim.finish(acc, l, valid, DUMP && valid ? dump + (s - first) : nullptr);
-      }
-    } else {
-      const uint4 w = it.enumerate ? enum_words(g, lev, it.d)
-                                   : philox4x32_10(make_uint4((uint32_t)g, (uint32_t)(g >> 32), ctr_hi.z, ctr_hi.w),
-                                                   args.rk);
-      const int ppg = lev == 1 ? 2 : 4;  // packs per group
-      const uint64_t s0 = (uint64_t)(ppg * KP) * g;
-      // samples s0 + k are valid for k in [klo, khi)
-      int klo = 0, khi = ppg * KP;
-      if (!full) {
-        klo = s0 >= first ? 0 : (int)min(first - s0, (uint64_t)(ppg * KP));
-        khi = last <= s0 ? 0 : (int)min(last - s0, (uint64_t)(ppg * KP));
-      }
-      if (lev == 1) {
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          sim.begin();
-          sim.template step<true, 0>(u == 0 ? w.x : w.z, 0);
-          sim.template step<true, 1>(u == 0 ? w.y : w.w, 1);
-#pragma unroll
-          for (int l = 0; l < KP; ++l) {
-            const int k = u * KP + l;
-            const bool valid = k >= klo && k < khi;
-            sim.finish(acc, l, valid, DUMP && valid ? dump + (s0 + k - first) : nullptr);
+    auto group = [&](auto eager) {
+      constexpr bool E = decltype(eager)::value;
+      if (lev >= 2) {
+        uint64_t P = g;
+        uint32_t lsh = 0;   // lane-split packed draws: this sample's field to the top of the word
+        if constexpr (KP == 1 && EST == EST_APPROX) {
+          if (it.lanes > 1) {
+            P = g / 3u;
+            lsh = (uint32_t)it.d * (uint32_t)(g - P * 3u);
           }
+        }
+        const uint32_t calls = 1u << (lev - 2);
+        uint64_t qbase = P * calls;
+        if constexpr (E && Sim::LAZY) opaque(qbase);
+        sim.begin();
+        for (uint32_t c = 0; c < calls; ++c) {
+          const uint64_t q = qbase + c;
+          const uint4 w = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), ctr_hi.z, ctr_hi.w), args.rk);
+          const int i0 = (int)(c << 2);
+          sim.template step<true, 0, E>(w.x << lsh, i0);
+          sim.template step<true, 1, E>(w.y << lsh, i0 + 1);
+          sim.template step<true, 0, E>(w.z << lsh, i0 + 2);
+          sim.template step<true, 1, E>(w.w << lsh, i0 + 3);
+        }
+#pragma unroll
+        for (int l = 0; l < KP; ++l) {
+          const uint64_t s = KP == 1 ? g : P * KP + l;
+          const bool valid = full || (s >= first && s < last);
+          sim.template finish<E>(acc, l, valid, DUMP && valid ? dump + (s - first) : nullptr);
         }
       } else {
+        uint64_t gw = g;
+        if constexpr (E && Sim::LAZY) opaque(gw);
+        const uint4 w = it.enumerate ? enum_words(gw, lev, it.d)
+                                     : philox4x32_10(make_uint4((uint32_t)gw, (uint32_t)(gw >> 32), ctr_hi.z, ctr_hi.w),
+                                                     args.rk);
+        const int ppg = lev == 1 ? 2 : 4;  // packs per group
+        const uint64_t s0 = (uint64_t)(ppg * KP) * g;
+        // samples s0 + k are valid for k in [klo, khi)
+        int klo = 0, khi = ppg * KP;
+        if (!full) {
+          klo = s0 >= first ? 0 : (int)min(first - s0, (uint64_t)(ppg * KP));
+          khi = last <= s0 ? 0 : (int)min(last - s0, (uint64_t)(ppg * KP));
+        }
+        if (lev == 1) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          sim.begin();
-          sim.template step<false>(word_of(w, u), 0);
+          for (int u = 0; u < 2; ++u) {
+            sim.begin();
+            sim.template step<true, 0, E>(u == 0 ? w.x : w.z, 0);
+            sim.template step<true, 1, E>(u == 0 ? w.y : w.w, 1);
 #pragma unroll
-          for (int l = 0; l < KP; ++l) {
-            const int k = u * KP + l;
-            const bool valid = k >= klo && k < khi;
-            sim.finish(acc, l, valid, DUMP && valid ? dump + (s0 + k - first) : nullptr);
+            for (int l = 0; l < KP; ++l) {
+              const int k = u * KP + l;
+              const bool valid = k >= klo && k < khi;
+              sim.template finish<E>(acc, l, valid, DUMP && valid ? dump + (s0 + k - first) : nullptr);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            sim.begin();
+            sim.template step<false, -1, E>(word_of(w, u), 0);
+#pragma unroll
+            for (int l = 0; l < KP; ++l) {
+              const int k = u * KP + l;
+              const bool valid = k >= klo && k < khi;
+              sim.template finish<E>(acc, l, valid, DUMP && valid ? dump + (s0 + k - first) : nullptr);
+            }
           }
         }
       }
+    };
+    bool eager = true;
+    if constexpr (Sim::LAZY && !DUMP) {
+      if (lazy) {
+        // only the integer sums change inside a LAZY group (no saturations)
+        const auto saved = acc.mark();
+        sim.hi = 0;
+        group(std::false_type{});
+        eager = sim.over();
+        if (eager) acc.rewind(saved);
+      }
     }
+    if (eager) group(std::true_type{});
     if constexpr (EST == EST_APPROX && AP == AP_FX32 && PC == PC_TERMINAL) acc.flush_group();
   }
   block_reduce_write<EST, XP>(acc, args.partials + gc);

@@ -216,7 +216,8 @@ extern "C" mlmc_status mlmc_level_noalloc(int level, uint64_t N, const mlmc_para
       const int64_t zmax = noalloc_zmax(g_noalloc_zhost, d, p->icdf_method, fZ, m3);
       if ((double)zmax > std::ldexp(1.0, e[F_Z] + fZ) - 1.0) return MLMC_EOVERFLOW;
       unit = f[F_S] + (p->payoff == MLMC_ASIAN ? level + 1 : 0);
-      fast = fast_fixed(e, f, con1, con1c, con2, con3, zmax, p->scheme == MLMC_MILSTEIN, it.ff, fast64);
+      fast = fast_fixed(e, f, con1, con1c, con2, con3, zmax, p->scheme == MLMC_MILSTEIN, (int64_t)1 << level, it.ff,
+                        fast64);
       if (fast && !fast64) {
         const double ymax = std::max(std::ldexp(1.0, e[F_S] + f[F_S]), std::ldexp(1.0, f[F_S]));
         if (!((double)spc * ymax * ymax < 0x1p64)) fast64 = true;

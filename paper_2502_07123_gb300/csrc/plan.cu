@@ -74,6 +74,8 @@ struct mlmc_plan {
 
 namespace mlmc_host {
 
+// Deterministic sum of each item's chunk partials (fixed lane assignment and
+// tree order, so repeated launches give bit-identical results).
 __global__ void finalize_kernel(const ItemDesc *items, int n_items, const Partial *partials, DevSums *out) {
   const int i = blockIdx.x;
   if (i >= n_items) return;
@@ -534,6 +536,15 @@ mlmc_status mlmc_plan_launch_info(const mlmc_plan *plan, int k, int *family, int
     }
     *path_steps = ps;
   }
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_plan_launch_items(const mlmc_plan *plan, int k, int32_t *work_index, int cap, int *n) {
+  if (!plan || k < 0 || k >= (int)plan->launches.size() || !n || cap < 0 || (cap > 0 && !work_index))
+    return MLMC_EINVAL;
+  const LaunchRec &L = plan->launches[k];
+  for (int i = 0; i < L.n_items && i < cap; ++i) work_index[i] = (int32_t)plan->items[L.item_off + i].out_index;
+  *n = L.n_items;
   return MLMC_OK;
 }
 

@@ -122,6 +122,8 @@ def load():
         "mlmc_plan_kernel_time": (st, [ctypes.c_void_p, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_double)]),
         "mlmc_plan_launch_info": (st, [ctypes.c_void_p, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int),
                                        P(ctypes.c_uint64), P(ctypes.c_uint64)]),
+        "mlmc_plan_launch_items": (st, [ctypes.c_void_p, ctypes.c_int, P(ctypes.c_int32), ctypes.c_int,
+                                        P(ctypes.c_int)]),
         "mlmc_plan_destroy": (None, [ctypes.c_void_p]),
         "mlmc_run": (st, [P(Work), ctypes.c_int, ctypes.c_uint64, P(Tuning), P(Sums), ctypes.c_void_p]),
         "mlmc_estimate": (st, [ctypes.c_double, P(Params), ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
@@ -300,6 +302,14 @@ class Plan:
         _check(load().mlmc_plan_launch_info(self._h, k, ctypes.byref(fam), ctypes.byref(items), ctypes.byref(ctas),
                                             ctypes.byref(ps)), "mlmc_plan_launch_info")
         return fam.value, items.value, ctas.value, ps.value
+
+    def launch_items(self, k):
+        """Work-list positions of the items of level-kernel launch k, in launch order."""
+        n = ctypes.c_int()
+        _check(load().mlmc_plan_launch_items(self._h, k, None, 0, ctypes.byref(n)), "mlmc_plan_launch_items")
+        buf = (ctypes.c_int32 * max(1, n.value))()
+        _check(load().mlmc_plan_launch_items(self._h, k, buf, n.value, ctypes.byref(n)), "mlmc_plan_launch_items")
+        return [int(buf[i]) for i in range(n.value)]
 
     def kernel_time(self, k):
         """(family, ms) of level kernel k of the last launch (CUDA events on its stream)."""

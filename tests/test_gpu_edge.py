@@ -133,3 +133,28 @@ def test_calls_from_several_threads(m):
         t.join()
     for a, b in zip(seq, out):
         assert a["sum"] == b["sum"] and a["sum2"] == b["sum2"]
+
+
+def test_plan_launch_items_partition_the_work(m):
+    # every item with samples is in exactly one level-kernel launch, whose
+    # family and path-steps its items account for; empty items are in none
+    p = W.params()
+    P = _P(m, p, pack=1)
+    items = [dict(params=P, level=lev, variant=v, N=n)
+             for lev, n in ((0, 400_000), (2, 400_000), (5, 1_000), (7, 0))
+             for v in (W.FIXED_APPROX, W.CORR_FIXED, W.FP32_EXACT)]
+    plan = m.Plan(items, 9)
+    try:
+        seen = []
+        for k in range(plan.info()["kernels"]):
+            fam, n_items, _, ps = plan.launch_info(k)
+            idx = plan.launch_items(k)
+            assert len(idx) == n_items > 0
+            assert ps == sum(items[i]["N"] << items[i]["level"] for i in idx)
+            assert len({items[i]["variant"] for i in idx}) == 1
+            seen += idx
+        assert sorted(seen) == [i for i, it in enumerate(items) if it["N"] > 0]
+        with pytest.raises(m.MLMCError):
+            plan.launch_items(plan.info()["kernels"])
+    finally:
+        plan.close()

@@ -84,3 +84,26 @@ def test_packed_half_pairs(m, variant, scheme, payoff):
     os_, od = core.level(p, level, first, N, variant, 21, request=3, d=10, method=method, dump=True, pack=1)
     assert gs["isum"] == os_["isum"] and gs["isum2"] == os_["isum2"]
     compare_samples(variant, p, gd, od)
+
+
+# Packed fixed point with a narrow S format (|S| < 128 while S0 = 100): packs
+# whose S leaves the range run again on the clamped datapath, and their
+# saturations are counted; sigma = 0.6 lets sum1 fall below -1 on level 0,
+# where every pack runs clamped from the start.
+@pytest.mark.parametrize("sigma", [0.25, 0.6])
+@pytest.mark.parametrize("scheme", [W.EULER, W.MILSTEIN])
+@pytest.mark.parametrize("level,N", [(0, 20_011), (1, 20_011), (3, 400_003)])
+def test_packed_fixed_saturating(m, sigma, scheme, level, N):
+    p = W.params(sigma=sigma, scheme=scheme)
+    fmts = [W.default_format(p, lev) for lev in range(level + 1)]
+    fmts[level]["e"][6] = 7
+    fmts[level]["e"][5] = 7 + fmts[level]["e"][4]
+    P = m.make_params(p, d=10, method=1, formats=fmts, rng_pack=1)
+    first = 5
+    gs, gd = m.mlmc_level_dump(level, N, P, m.FIXED_APPROX, 33, first)
+    os_, od = core.level(p, level, first, N, core.FIXED_APPROX, 33, d=10, method=1, fmt=fmts[level], dump=True,
+                         pack=1)
+    assert os_["saturations"] > 0
+    assert gs["isum"] == os_["isum"] and gs["isum2"] == os_["isum2"]
+    assert gs["saturations"] == os_["saturations"]
+    compare_samples(core.FIXED_APPROX, p, gd, od)
