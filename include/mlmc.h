@@ -89,9 +89,9 @@ typedef struct {
   int32_t payoff;               /* mlmc_payoff                                   */
   int32_t scheme;               /* mlmc_scheme                                   */
   int32_t icdf_method;          /* 1: piecewise constant on uniform intervals (Sec. 3.1);
-                                   2: sum of two table variables of d/2 bits with the
+                                   2: sum of n table variables of d/n bits with the
                                       least-squares / permutation optimisation (Sec. 3.2;
-                                      d even, >= 4); the correction estimators' exact
+                                      n = icdf_fields); the correction estimators' exact
                                       path then uses the uniform in interval pi(j),
                                       U = 2^-d pi(j) + 2^-32 ((J mod 2^(32-d)) + 1/2);
                                    3: piecewise linear on dyadic intervals (Sec. 3.3) */
@@ -106,7 +106,9 @@ typedef struct {
                                    the word its pack P reads at each step; 0: one word
                                    per step.  Ignored by exact and correction estimators,
                                    which need all 32 bits of J (Sec. 3.1 coupling). */
-  int32_t reserved;             /* must be 0 */
+  int32_t icdf_fields;          /* Method 2: n, the number of fields (0 means 2); n
+                                   divides d with at least 2 bits per field.  Must be 0
+                                   for methods 1 and 3. */
 } mlmc_params;
 
 /* Per-level result.  sum/sum2 are discounted FP64 sums of Y and Y^2.  When
@@ -452,17 +454,25 @@ mlmc_status mlmc_default_format(const mlmc_params *p, int level, mlmc_format *ou
  * rep: 0 fp64, 1 fp32, 2 fp16, 3 bf16, 4 fixed with fZ fractional bits.
  * method 3 values are the a + b k evaluations the kernels use. */
 mlmc_status mlmc_icdf_table(int method, int d, int rep, int fZ, double *out);
-/* Method 2 (Sec. 3.2): the optimised small table x (host array of 2^(d/2-1)
- * doubles, or NULL), the interval rank pi(j) of every j < 2^d (host array of
- * 2^d, or NULL) and the number of least-squares fits until pi stopped
- * changing (at most 1000).  The small table starts as the (d/2)-bit Method-1
- * table / sqrt(2); each fit solves the normal equations for
- * sum_j (Z_{pi(j)} - Z~_j)^2 with Z_k the d-bit Method-1 values, then the 2^d
- * sums are ranked again (ascending, ties by j).  Table values of method 2 in
- * every representation: each x rounded once, the two fields added exactly
- * (fixed point) or with one rounding.  MLMC_EINVAL for odd d or d outside
- * [4, 14]. */
-mlmc_status mlmc_icdf_method2(int d, double *x, uint32_t *perm, int *iterations);
+/* Method 2 (Sec. 3.2) with n fields (0 means 2) of b = d/n bits, the first
+ * field the top bits of j: the optimised small table x (host array of
+ * 2^(b-1) doubles, or NULL), the interval rank pi(j) of every j < 2^d (host
+ * array of 2^d, or NULL) and the number of least-squares fits made.  Z~_j is
+ * sum_k c_k x_k, c_k the net count of +x_k minus -x_k among j's fields (the
+ * Method-1 sign rule per field), over the nonzero c_k in ascending k.  The
+ * small table starts as the b-bit Method-1 table / sqrt(n); each fit solves the
+ * normal equations for sum_j (Z_{pi(j)} - Z~_j)^2 with Z_k the d-bit Method-1
+ * values, then the 2^d sums are ranked again (ascending, ties by j); the fits
+ * stop when pi equals the previous or any earlier permutation (for n > 2 the
+ * iteration can alternate between permutations), at most 1000.  MLMC_EINVAL
+ * unless n divides d, d/n >= 2 and d <= 14. */
+mlmc_status mlmc_icdf_method2(int d, int n, double *x, uint32_t *perm, int *iterations);
+/* Method-2 values of every index k < 2^(d-1) in a representation (as
+ * mlmc_icdf_table): each x rounded once, then sum_k c_k x_k exactly (fixed
+ * point, fZ fractional bits) or with one rounding per product and per
+ * addition (fp32 / fp16 / bf16); rep 0 gives the FP64 sums.  mlmc_icdf_table
+ * with method 2 is this with n = 2. */
+mlmc_status mlmc_icdf_method2_table(int d, int n, int rep, int fZ, double *out);
 
 /* Philox4x32-10 words computed on the GPU for n counters (for parity testing):
  * ctr is a host array of 4n words, out a host array of 4n words. */

@@ -183,10 +183,10 @@ class OracleError(RuntimeError):
 
 
 def level(p, lev, first, N, variant, seed, request=0, stream=None, d=10, method=1,
-          fmt=None, dump=False, pack=0, enumerate=0):
+          fmt=None, dump=False, pack=0, enumerate=0, fields=2):
     """Simulate samples [first, first+N) of one level; return (sums dict, dump array or None).
 
-    p: dict with S0, K, r, sigma, T, payoff, scheme.
+    p: dict with S0, K, r, sigma, T, payoff, scheme; fields: n of Method 2.
     """
     from . import tables
     if stream is None:
@@ -197,14 +197,14 @@ def level(p, lev, first, N, variant, seed, request=0, stream=None, d=10, method=
     rep = approx_rep(variant)
     if rep is not None:
         fZ = int(fmt["f"][0]) if rep == "fixed" else 0
-        ztab = np.ascontiguousarray(tables.table(d, method, rep, fZ), dtype=np.float64)
+        ztab = np.ascontiguousarray(tables.table(d, method, rep, fZ, fields), dtype=np.float64)
     if rep == "fixed":
         F = make_format(fmt)
     S = Sums()
     out = np.zeros(N, dtype=SAMPLE_DTYPE) if dump else None
     perm = None
     if method == 2 and variant in (CORR_FIXED, CORR_FP16, CORR_BF16):
-        perm = np.ascontiguousarray(tables.m2_optimise(d)["pi"], dtype=np.uint32)
+        perm = np.ascontiguousarray(tables.m2_optimise(d, fields)["pi"], dtype=np.uint32)
     st = lib().or_level(ctypes.byref(P), int(lev), int(first), int(N), int(variant), int(seed),
                         int(request), int(stream), int(d),
                         ztab.ctypes.data if ztab is not None else None,

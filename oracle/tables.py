@@ -16,12 +16,20 @@ evaluated here in mpmath at 40 significant digits and rounded once.
 Method 2 (Sec. 3.2): the d-bit index j is split into n fields of b = d/n bits
 (the first field is the top bits); each field gives X = +-x_k from a small
 table of 2^(b-1) values with the Method-1 sign rule, and the approximate
-Normal is the sum of the n values.  The small table starts as the b-bit
+Normal is the sum of the n values.  Reading (summation order): the sum is
+formed as sum_k c_k x_k over the small-table indices k in ascending order,
+c_k the net count of +x_k minus -x_k among the fields (terms with c_k = 0
+left out), so that indices whose fields hold the same values in another
+order, or a cancelling pair, get the identical FP64 sum (exactly tied and
+ranked by j), as the mathematical sum does; for n = 2 this is the plain sum.  The small table starts as the b-bit
 Method-1 table divided by sqrt(n); then, repeatedly, the 2^d sums are sorted
 ascending (ties by j), which defines the permutation pi (pi(j) = rank of
 Z~_j), and the small table is refitted by least squares to the d-bit
 Method-1 values of the intervals the sums are ranked at, Z_{pi(j)}, until pi
-no longer changes.  The exact path uses the uniform in interval pi(j) with
+no longer changes.  Reading (cycles): for n > 2 the iteration can alternate
+between permutations for ever (period 2 at (d, n) = (8, 4) and (12, 3)); it
+stops when the new permutation equals any earlier one, convergence being the
+case of the last one, and keeps the last fit with its own ranking.  The exact path uses the uniform in interval pi(j) with
 J's low bits: U = 2^-d pi(j) + 2^-32 ((J mod 2^(32-d)) + 1/2).
 
 Method 3 (Sec. 3.3): Z_k is replaced by a + b k on each dyadic index class.
@@ -133,7 +141,7 @@ def m1_full(d: int) -> np.ndarray:
 
 
 def _m2_fields(d: int, n: int):
-    """Per field i: (index into the small table, sign) for every j < 2^d."""
+    """Per field i (top bits first): (index into the small table, sign) for every j < 2^d."""
     b = d // n
     full, half = 1 << b, 1 << (b - 1)
     j = np.arange(1 << d)
@@ -157,11 +165,15 @@ def m2_design(d: int, n: int) -> np.ndarray:
 
 
 def m2_sums(x: np.ndarray, d: int, n: int) -> np.ndarray:
-    """Z~_j = X^(1) + ... + X^(n) in FP64, added in field order."""
-    acc = None
-    for idx, sgn in _m2_fields(d, n):
-        v = sgn * x[idx]
-        acc = v if acc is None else acc + v
+    """Z~_j = X^(1) + ... + X^(n) in FP64 as sum_k c_k x_k: the nonzero net counts
+    c_k (row j of the design matrix) in ascending k, each product and each
+    addition rounded once, from +0."""
+    A = m2_design(d, n)
+    acc = np.zeros(1 << d)
+    for k in range(A.shape[1]):
+        c = A[:, k]
+        nz = c != 0
+        acc[nz] = acc[nz] + c[nz] * x[k]
     return acc
 
 
@@ -194,14 +206,17 @@ def m2_optimise(d: int, n: int = 2, max_iter: int = 1000):
     v0 = m2_sums(x0, d, n)
     pi0 = m2_rank(v0)
     x, pi, it = x0, pi0, 0
+    seen = {pi0.tobytes()}
     while it < max_iter:
         x = np.linalg.lstsq(A, T[pi], rcond=None)[0]
         it += 1
         v = m2_sums(x, d, n)
         new = m2_rank(v)
-        if np.array_equal(new, pi):
-            break
+        key = new.tobytes()
         pi = new
+        if key in seen:          # converged, or back in an earlier state
+            break
+        seen.add(key)
     v = m2_sums(x, d, n)
     return {"x": x, "values": v, "pi": pi, "iterations": it, "x0": x0, "mse0": m2_mse(v0, pi0, d),
             "mse": m2_mse(v, pi, d)}
@@ -209,13 +224,13 @@ def m2_optimise(d: int, n: int = 2, max_iter: int = 1000):
 
 def m2_table(d: int, rep: str, fZ: int = 0, n: int = 2) -> np.ndarray:
     """Method-2 values of every j < 2^d in a representation: each small-table value
-    rounded once (fixed: to fZ bits; fp16 / bf16; fp32), then the fields added in
-    order, exactly in fixed point and with one rounding per addition otherwise."""
+    rounded once (fixed: to fZ bits; fp16 / bf16; fp32), then sum_k c_k x_k over
+    the nonzero net counts in ascending k, exactly in fixed point and otherwise
+    with one rounding per product c_k x_k and per addition."""
     import math
     res = m2_optimise(d, n)
     x = res["x"]
-    b = d // n
-    full, half = 1 << b, 1 << (b - 1)
+    A = m2_design(d, n).astype(np.int64)
     if rep == "fp64":
         return res["values"]
     if rep == "fixed":
@@ -228,27 +243,25 @@ def m2_table(d: int, rep: str, fZ: int = 0, n: int = 2) -> np.ndarray:
         xq = [float(np.float32(v)) for v in x]
     else:
         raise ValueError(rep)
+    def rnd(v):
+        if rep == "fp16":
+            return float(_round_fp16(np.array([v]))[0])
+        if rep == "bf16":
+            return float(_round_bf16(np.array([v]))[0])
+        if rep == "fp32":
+            return float(np.float32(v))
+        return v                           # fixed: integers, exact
+
     out = np.empty(1 << d)
     for j in range(1 << d):
-        acc = None
-        for i in range(n):
-            f = (j >> (b * (n - 1 - i))) & (full - 1)
-            v = xq[f] if f < half else -xq[full - 1 - f]
-            if acc is None:
-                acc = v
-            elif rep == "fixed":
-                acc = acc + v
-            elif rep == "fp16":
-                acc = float(_round_fp16(np.array([acc + v]))[0])
-            elif rep == "bf16":
-                acc = float(_round_bf16(np.array([acc + v]))[0])
-            else:
-                acc = float(np.float32(acc + v))
+        acc = 0
+        for k in np.nonzero(A[j])[0]:
+            acc = rnd(acc + rnd(int(A[j, k]) * xq[k]))
         out[j] = math.ldexp(acc, -fZ) if rep == "fixed" else acc
     return out
 
 
-def table(d: int, method: int, rep: str, fZ: int = 0) -> np.ndarray:
+def table(d: int, method: int, rep: str, fZ: int = 0, fields: int = 2) -> np.ndarray:
     """Approximate-Normal value for every table index k < 2^(d-1), as float64.
 
     rep is one of 'fp64', 'fp32', 'fp16', 'bf16', 'fixed' (fixed values are
@@ -270,7 +283,7 @@ def table(d: int, method: int, rep: str, fZ: int = 0) -> np.ndarray:
             return np.array([math.ldexp(round_fixed(v, fZ), -fZ) for v in z64])
         raise ValueError(rep)
     if method == 2:
-        return m2_table(d, rep, fZ)[:half]
+        return m2_table(d, rep, fZ, fields)[:half]
     if method != 3:
         raise ValueError("method must be 1, 2 or 3")
     coef = m3_coefficients_fp64(d)

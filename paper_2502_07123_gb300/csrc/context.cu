@@ -99,27 +99,35 @@ void m3_fit(const std::vector<double> &Z, int d, M3Coef &c) {
   }
 }
 
-// Device table of one representation.  full_signed (method 1 only): all 2^d
-// entries indexed directly by j, as the level kernels use it; otherwise the
-// 2^(d-1) entries of the lower half (parity checks).
 uint16_t half_bits(double x) { return __half_as_ushort(__double2half(x)); }
 uint16_t bf16_bits(double x) { return __bfloat16_as_ushort(__double2bfloat16(x)); }
 
-// Method 2 (Sec. 3.2) with two fields: the d-bit index j splits into a high
-// and a low field of b = d/2 bits; each gives +-x_k from a small table of
-// 2^(b-1) values (Method-1 sign rule per field) and Z~_j is their sum.  The
-// small table starts as the b-bit Method-1 table / sqrt(2); then the 2^d sums
-// are ranked ascending (ties by j), pi(j) = rank, and x is refitted by least
-// squares (normal equations, Cholesky in long double) to the d-bit Method-1
-// values Z_{pi(j)}, until pi stops changing (at most 1000 fits).
-std::map<int, M2Table> g_m2;
+// Method 2 (Sec. 3.2) with n fields: the d-bit index j splits into n fields
+// of b = d/n bits (top bits first); each gives +-x_k from a small table of
+// 2^(b-1) values (Method-1 sign rule per field) and Z~_j is their sum, formed
+// as sum_k c_k x_k over the nonzero net counts c_k of +x_k minus -x_k in
+// ascending k (fields holding the same values in another order, or a
+// cancelling pair, then give the identical FP64 sum).  The small table starts
+// as the b-bit Method-1 table / sqrt(n); then the 2^d sums are ranked
+// ascending (ties by j), pi(j) = rank, and x is refitted by least squares
+// (normal equations, Cholesky in long double) to the d-bit Method-1 values
+// Z_{pi(j)}, until pi equals the previous or any earlier permutation (for
+// n > 2 the iteration can alternate between two for ever), at most 1000 fits.
+std::map<std::pair<int, int>, M2Table> g_m2;
 
-struct M2Field { int idx; double sgn; };
-inline void m2_fields(int j, int b, M2Field &hi, M2Field &lo) {
-  const int full = 1 << b, half = 1 << (b - 1);
-  const int f1 = j >> b, f2 = j & (full - 1);
-  hi = f1 < half ? M2Field{f1, 1.0} : M2Field{full - 1 - f1, -1.0};
-  lo = f2 < half ? M2Field{f2, 1.0} : M2Field{full - 1 - f2, -1.0};
+bool m2_shape_ok(int d, int n) { return n >= 2 && d <= 14 && d % n == 0 && d / n >= 2; }
+
+// Net count c_k of every index j (row-major, 2^d rows of 2^(b-1)).
+std::vector<int8_t> m2_counts(int d, int n) {
+  const int b = d / n, full = 1 << b, half = 1 << (b - 1), N = 1 << d;
+  std::vector<int8_t> c((size_t)N * half, 0);
+  for (int j = 0; j < N; ++j)
+    for (int i = 0; i < n; ++i) {
+      const int f = (j >> (b * (n - 1 - i))) & (full - 1);
+      if (f < half) ++c[(size_t)j * half + f];
+      else --c[(size_t)j * half + (full - 1 - f)];
+    }
+  return c;
 }
 
 bool chol_solve(std::vector<long double> M, std::vector<long double> r, int k, std::vector<double> &y) {
@@ -150,11 +158,11 @@ bool chol_solve(std::vector<long double> M, std::vector<long double> r, int k, s
   return true;
 }
 
-mlmc_status m2_build(int d, const M2Table **out) {
-  auto it = g_m2.find(d);
+mlmc_status m2_build(int d, int n, const M2Table **out) {
+  auto it = g_m2.find(std::make_pair(d, n));
   if (it != g_m2.end()) { *out = &it->second; return MLMC_OK; }
-  if (d % 2 || d < 4) return MLMC_EINVAL;
-  const int b = d / 2, k = 1 << (b - 1), N = 1 << d;
+  if (!m2_shape_ok(d, n)) return MLMC_EINVAL;
+  const int b = d / n, k = 1 << (b - 1), N = 1 << d;
   double *dv;
   const std::vector<double> *zb = nullptr, *zd = nullptr;
   mlmc_status s;
@@ -162,21 +170,30 @@ mlmc_status m2_build(int d, const M2Table **out) {
   if ((s = m1_table(d, &dv, &zd)) != MLMC_OK) return s;
   std::vector<double> T(N);
   for (int j = 0; j < N; ++j) T[j] = j < N / 2 ? (*zd)[j] : -(*zd)[N - 1 - j];
-  std::vector<M2Field> fh(N), fl(N);
-  for (int j = 0; j < N; ++j) m2_fields(j, b, fh[j], fl[j]);
-  // normal matrix A^T A (A has one +-1 per field in every row)
-  std::vector<long double> M((size_t)k * k, 0.0L);
-  for (int j = 0; j < N; ++j) {
-    const M2Field f[2] = {fh[j], fl[j]};
-    for (int a = 0; a < 2; ++a)
-      for (int c = 0; c < 2; ++c) M[(size_t)f[a].idx * k + f[c].idx] += (long double)(f[a].sgn * f[c].sgn);
-  }
   M2Table t;
+  t.n = n;
+  t.c = m2_counts(d, n);
+  const int8_t *C = t.c.data();
+  // normal matrix A^T A (row j of A holds the net counts)
+  std::vector<long double> M((size_t)k * k, 0.0L);
+  for (int j = 0; j < N; ++j)
+    for (int a = 0; a < k; ++a) {
+      const int ca = C[(size_t)j * k + a];
+      if (!ca) continue;
+      for (int q = 0; q < k; ++q) M[(size_t)a * k + q] += (long double)(ca * C[(size_t)j * k + q]);
+    }
   t.x.resize(k);
-  for (int q = 0; q < k; ++q) t.x[q] = (*zb)[q] / std::sqrt(2.0);
+  for (int q = 0; q < k; ++q) t.x[q] = (*zb)[q] / std::sqrt((double)n);
   auto sums = [&](const std::vector<double> &x, std::vector<double> &v) {
     v.resize(N);
-    for (int j = 0; j < N; ++j) v[j] = fh[j].sgn * x[fh[j].idx] + fl[j].sgn * x[fl[j].idx];
+    for (int j = 0; j < N; ++j) {
+      double acc = 0.0;
+      for (int q = 0; q < k; ++q) {
+        const int cq = C[(size_t)j * k + q];
+        if (cq) acc = acc + (double)cq * x[q];
+      }
+      v[j] = acc;
+    }
   };
   auto rank = [&](const std::vector<double> &v, std::vector<uint32_t> &pi) {
     std::vector<int> order(N);
@@ -187,76 +204,82 @@ mlmc_status m2_build(int d, const M2Table **out) {
   };
   sums(t.x, t.values);
   rank(t.values, t.pi);
+  std::vector<std::vector<uint32_t>> seen{t.pi};
   for (t.iterations = 0; t.iterations < 1000;) {
     std::vector<long double> rhs(k, 0.0L);
     for (int j = 0; j < N; ++j) {
       const long double y = T[t.pi[j]];
-      rhs[fh[j].idx] += fh[j].sgn * y;
-      rhs[fl[j].idx] += fl[j].sgn * y;
+      for (int q = 0; q < k; ++q) {
+        const int cq = C[(size_t)j * k + q];
+        if (cq) rhs[q] += cq * y;
+      }
     }
     if (!chol_solve(M, rhs, k, t.x)) return MLMC_EINVAL;
     ++t.iterations;
     sums(t.x, t.values);
-    std::vector<uint32_t> pn;
-    rank(t.values, pn);
-    if (pn == t.pi) break;
-    t.pi.swap(pn);
+    rank(t.values, t.pi);
+    if (std::find(seen.begin(), seen.end(), t.pi) != seen.end()) break;   // converged or cycling
+    seen.push_back(t.pi);
   }
-  auto ins = g_m2.emplace(d, std::move(t));
+  auto ins = g_m2.emplace(std::make_pair(d, n), std::move(t));
   *out = &ins.first->second;
   return MLMC_OK;
 }
 
-// Method-2 value of index j in a representation: each small-table value rounded
-// once, the two fields added exactly (fixed point) or with one rounding.
+// Method-2 value of index j in a representation: each small-table value
+// rounded once, then sum_k c_k x_k over the nonzero net counts in ascending k,
+// exactly in fixed point and otherwise with one rounding per product and per
+// addition.
 double m2_value(const M2Table &t, int d, int j, int rep, int fZ) {
-  const int b = d / 2;
-  M2Field h, l;
-  m2_fields(j, b, h, l);
-  const double a = t.x[h.idx], c = t.x[l.idx];
-  switch (rep) {
-    case REP_FIXED: {
-      const int64_t qa = (int64_t)std::floor(std::ldexp(a, fZ) + 0.5), qc = (int64_t)std::floor(std::ldexp(c, fZ) + 0.5);
-      return std::ldexp((double)((int64_t)h.sgn * qa + (int64_t)l.sgn * qc), -fZ);
+  const int k = 1 << (d / t.n - 1);
+  const int8_t *C = t.c.data() + (size_t)j * k;
+  auto rnd = [&](double v) -> double {
+    switch (rep) {
+      case REP_FP16: return (double)__half2float(__double2half(v));
+      case REP_BF16: return (double)__bfloat162float(__double2bfloat16(v));
+      case REP_FP32: return (double)(float)v;
+      default: return v;
     }
-    case REP_FP16: {
-      const double ha = (double)__half2float(__double2half(a)), hc = (double)__half2float(__double2half(c));
-      return (double)__half2float(__double2half(h.sgn * ha + l.sgn * hc));
-    }
-    case REP_BF16: {
-      const double ba = (double)__bfloat162float(__double2bfloat16(a));
-      const double bc = (double)__bfloat162float(__double2bfloat16(c));
-      return (double)__bfloat162float(__double2bfloat16(h.sgn * ba + l.sgn * bc));
-    }
-    case REP_FP32: {
-      const double fa = (double)(float)a, fc = (double)(float)c;
-      return (double)(float)(h.sgn * fa + l.sgn * fc);
-    }
-    default: return t.values[j];
+  };
+  if (rep == REP_FIXED) {
+    int64_t acc = 0;
+    for (int q = 0; q < k; ++q)
+      if (C[q]) acc += (int64_t)C[q] * (int64_t)std::floor(std::ldexp(t.x[q], fZ) + 0.5);
+    return std::ldexp((double)acc, -fZ);
   }
+  if (rep != REP_FP16 && rep != REP_BF16 && rep != REP_FP32) return t.values[j];
+  double acc = 0.0;
+  for (int q = 0; q < k; ++q)
+    if (C[q]) acc = rnd(acc + rnd((double)C[q] * rnd(t.x[q])));
+  return acc;
 }
 
-// Device copy of the Method-2 interval ranks of index width d.
-mlmc_status m2_perm_device(int d, const uint16_t **out) {
-  auto it = g.m2_perm.find(d);
+// Device copy of the Method-2 interval ranks of (d, n).
+mlmc_status m2_perm_device(int d, int n, const uint16_t **out) {
+  auto it = g.m2_perm.find(std::make_pair(d, n));
   if (it != g.m2_perm.end()) { *out = it->second; return MLMC_OK; }
   const M2Table *t;
-  mlmc_status s = m2_build(d, &t);
+  mlmc_status s = m2_build(d, n, &t);
   if (s != MLMC_OK) return s;
   std::vector<uint16_t> h(1 << d);
   for (int j = 0; j < (1 << d); ++j) h[j] = (uint16_t)t->pi[j];
   uint16_t *p = nullptr;
   MLMC_CK(cudaMalloc(&p, sizeof(uint16_t) * h.size()));
   MLMC_CK(cudaMemcpy(p, h.data(), sizeof(uint16_t) * h.size(), cudaMemcpyHostToDevice));
-  g.m2_perm[d] = p;
+  g.m2_perm[std::make_pair(d, n)] = p;
   *out = p;
   return MLMC_OK;
 }
 
-mlmc_status get_table(int method, int d, int rep, int fZ, const void **out, bool full_signed) {
+// Device table of one representation.  full_signed (method 1 only): all 2^d
+// entries indexed directly by j, as the level kernels use it; otherwise the
+// 2^(d-1) entries of the lower half (parity checks).  Method 2 (always the
+// full signed table) takes its field count n from fields.
+mlmc_status get_table(int method, int d, int rep, int fZ, const void **out, bool full_signed, int fields) {
   if (rep != REP_FIXED) fZ = 0;
   if (method == 3) full_signed = false;
-  auto key = std::make_tuple(method, d, rep, fZ, full_signed ? 1 : 0);
+  if (method != 2) fields = 0;
+  auto key = std::make_tuple(method, d, rep, fZ, full_signed ? 1 : 0, fields);
   auto it = g.tables.find(key);
   if (it != g.tables.end()) { *out = it->second; return MLMC_OK; }
   double *z64 = nullptr;
@@ -269,7 +292,7 @@ mlmc_status get_table(int method, int d, int rep, int fZ, const void **out, bool
     // the signed table over all 2^d indices, built on the host
     if (!full_signed) return MLMC_EINVAL;
     const M2Table *t;
-    if ((s = m2_build(d, &t)) != MLMC_OK) return s;
+    if ((s = m2_build(d, fields, &t)) != MLMC_OK) return s;
     if (rep == REP_FIXED) {
       std::vector<int32_t> h(2 * n);
       for (int j = 0; j < 2 * n; ++j) h[j] = (int32_t)std::llround(std::ldexp(m2_value(*t, d, j, rep, fZ), fZ));
@@ -329,16 +352,9 @@ mlmc_status mlmc_icdf_table(int method, int d, int rep, int fZ, double *out) {
   if (method < 1 || method > 3 || d < 2 || d > 14 || rep < 0 || rep > 4 || !out) return MLMC_EINVAL;
   if (rep == REP_FIXED && (fZ < 0 || fZ > 28)) return MLMC_EINVAL;
   if (method == 3 && rep == REP_FP64) return MLMC_EINVAL;
-  if (method == 2 && (d % 2 || d < 4)) return MLMC_EINVAL;
+  if (method == 2) return mlmc_icdf_method2_table(d, 2, rep, fZ, out);
   mlmc_status s = ensure_ctx();
   if (s != MLMC_OK) return s;
-  if (method == 2) {
-    // the host-built values the device tables are made of
-    const M2Table *t;
-    if ((s = m2_build(d, &t)) != MLMC_OK) return s;
-    for (int j = 0; j < (1 << (d - 1)); ++j) out[j] = m2_value(*t, d, j, rep, fZ);
-    return MLMC_OK;
-  }
   const void *tab = nullptr;
   if ((s = get_table(method, d, rep, fZ, &tab)) != MLMC_OK) return s;
   const int n = 1 << (d - 1);
@@ -351,13 +367,28 @@ mlmc_status mlmc_icdf_table(int method, int d, int rep, int fZ, double *out) {
   return e == cudaSuccess ? MLMC_OK : MLMC_ECUDA;
 }
 
-mlmc_status mlmc_icdf_method2(int d, double *x, uint32_t *perm, int *iterations) {
+mlmc_status mlmc_icdf_method2_table(int d, int n, int rep, int fZ, double *out) {
   MLMC_API_LOCK();
-  if (d % 2 || d < 4 || d > 14) return MLMC_EINVAL;
+  if (n == 0) n = 2;
+  if (!m2_shape_ok(d, n) || rep < 0 || rep > 4 || !out) return MLMC_EINVAL;
+  if (rep == REP_FIXED && (fZ < 0 || fZ > 28)) return MLMC_EINVAL;
+  mlmc_status s = ensure_ctx();
+  if (s != MLMC_OK) return s;
+  // the host-built values the device tables are made of
+  const M2Table *t;
+  if ((s = m2_build(d, n, &t)) != MLMC_OK) return s;
+  for (int j = 0; j < (1 << (d - 1)); ++j) out[j] = m2_value(*t, d, j, rep, fZ);
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_icdf_method2(int d, int n, double *x, uint32_t *perm, int *iterations) {
+  MLMC_API_LOCK();
+  if (n == 0) n = 2;
+  if (!m2_shape_ok(d, n)) return MLMC_EINVAL;
   mlmc_status s = ensure_ctx();
   if (s != MLMC_OK) return s;
   const M2Table *t;
-  if ((s = m2_build(d, &t)) != MLMC_OK) return s;
+  if ((s = m2_build(d, n, &t)) != MLMC_OK) return s;
   if (x) std::memcpy(x, t->x.data(), sizeof(double) * t->x.size());
   if (perm) std::memcpy(perm, t->pi.data(), sizeof(uint32_t) * t->pi.size());
   if (iterations) *iterations = t->iterations;

@@ -57,8 +57,8 @@ struct Ctx {
   cudaStream_t st = nullptr;
   std::map<int, std::vector<double>> m1_host;               // d -> Method-1 table (FP64)
   std::map<int, double *> m1_dev;                           // d -> device FP64 table
-  std::map<std::tuple<int, int, int, int, int>, void *> tables;  // (method, d, rep, fZ, signed) -> table
-  std::map<int, uint16_t *> m2_perm;                         // d -> device interval ranks (Method 2)
+  std::map<std::tuple<int, int, int, int, int, int>, void *> tables;  // (method, d, rep, fZ, signed, n) -> table
+  std::map<std::pair<int, int>, uint16_t *> m2_perm;         // (d, n) -> device interval ranks (Method 2)
 };
 extern Ctx g;
 
@@ -84,18 +84,24 @@ mlmc_status m1_table(int d, double **dev, const std::vector<double> **host);
 void m3_fit(const std::vector<double> &Z, int d, mlmc::M3Coef &c);
 uint16_t half_bits(double x);
 uint16_t bf16_bits(double x);
-// Method 2 (Sec. 3.2), two fields of d/2 bits.
+// Method 2 (Sec. 3.2), n fields of d/n bits.
 struct M2Table {
+  int n = 2;
+  std::vector<int8_t> c;         // net count of every small-table index in every j
   std::vector<double> x;         // small table
-  std::vector<double> values;    // Z~_j, j < 2^d, FP64 sums in field order
+  std::vector<double> values;    // Z~_j, j < 2^d, FP64 sums (ascending index)
   std::vector<uint32_t> pi;      // interval rank of every j
   int iterations = 0;
 };
-mlmc_status m2_build(int d, const M2Table **out);
+// n divides d, at least 2 bits per field, d <= 14.
+bool m2_shape_ok(int d, int n);
+mlmc_status m2_build(int d, int n, const M2Table **out);
 double m2_value(const M2Table &t, int d, int j, int rep, int fZ);
-mlmc_status m2_perm_device(int d, const uint16_t **out);
-// Device table of one (method, d, representation, f_Z), cached per process.
-mlmc_status get_table(int method, int d, int rep, int fZ, const void **out, bool full_signed = false);
+mlmc_status m2_perm_device(int d, int n, const uint16_t **out);
+// Device table of one (method, d, representation, f_Z[, Method-2 fields]),
+// cached per process.
+mlmc_status get_table(int method, int d, int rep, int fZ, const void **out, bool full_signed = false,
+                      int fields = 0);
 
 // ---------------------------------------------------------------------------
 // work items (items.cu)
@@ -104,6 +110,8 @@ mlmc_status get_table(int method, int d, int rep, int fZ, const void **out, bool
 enum { F_Z = 0, F_CON1 = 1, F_CON2 = 2, F_MUL1 = 3, F_SUM1 = 4, F_MUL2 = 5, F_S = 6 };
 
 bool params_ok(const mlmc_params *p);
+// Fields n of Method 2 (icdf_fields, 0 meaning 2).
+int m2_fields_of(const mlmc_params *p);
 // Samples per pack (3 with packed draws for approximate-only estimators, else 1).
 int pack_lanes(const mlmc_params *p, int variant);
 void default_format(const mlmc_params *p, int level, mlmc_format *out);
@@ -114,7 +122,7 @@ bool format_ok_gpu(const mlmc_format &F, bool milstein, int d);
 // for paths of nsteps fine steps; also decides ff.lazy.
 bool fast_fixed(const int e[7], const int f[7], int64_t con1, int64_t con1c, int64_t con2, int64_t con3,
                 int64_t zmax, bool milstein, int64_t nsteps, mlmc::FastFixed &ff, bool &s64);
-int64_t table_zmax_fixed(const std::vector<double> &Z, int d, int method, int fZ);
+int64_t table_zmax_fixed(const std::vector<double> &Z, int d, int method, int fZ, int fields);
 int family_of(int variant);
 int cost_kind_of(int variant);
 // Relative cost per fine path-step of an estimator kind (mlmc_cost_model).

@@ -69,12 +69,14 @@ bool params_ok(const mlmc_params *p) {
   if (p->payoff < 0 || p->payoff > 3 || p->scheme < 0 || p->scheme > 1) return false;
   if (p->icdf_method < 1 || p->icdf_method > 3) return false;
   if (p->icdf_bits < 2 || p->icdf_bits > 14) return false;
-  if (p->icdf_method == 2 && (p->icdf_bits % 2 || p->icdf_bits < 4)) return false;   // two fields of >= 2 bits
+  if (p->icdf_method == 2 && !m2_shape_ok(p->icdf_bits, m2_fields_of(p))) return false;   // n | d, >= 2 bits each
+  if (p->icdf_method != 2 && p->icdf_fields != 0) return false;
   if (p->formats && p->n_formats < 0) return false;
   if (p->rng_pack != 0 && p->rng_pack != 1) return false;
-  if (p->reserved != 0) return false;
   return true;
 }
+
+int m2_fields_of(const mlmc_params *p) { return p->icdf_fields ? p->icdf_fields : 2; }
 
 // Lanes per pack of an approximate-only estimator (packed draws need 3 fields of d bits).
 int pack_lanes(const mlmc_params *p, int variant) {
@@ -289,11 +291,11 @@ bool fast_fixed(const int e[7], const int f[7], int64_t con1, int64_t con1c, int
 }
 
 // Largest |table value| in Z's fixed-point format, as the kernels evaluate it.
-int64_t table_zmax_fixed(const std::vector<double> &Z, int d, int method, int fZ) {
+int64_t table_zmax_fixed(const std::vector<double> &Z, int d, int method, int fZ, int fields) {
   int64_t zmax = 0;
   if (method == 2) {
     const M2Table *t;
-    if (m2_build(d, &t) != MLMC_OK) return INT64_MAX;
+    if (m2_build(d, fields, &t) != MLMC_OK) return INT64_MAX;
     for (int j = 0; j < (1 << d); ++j)
       zmax = std::max<int64_t>(zmax, std::llabs(std::llround(std::ldexp(m2_value(*t, d, j, REP_FIXED, fZ), fZ))));
     return zmax;
@@ -448,7 +450,7 @@ mlmc_status build_item(const mlmc_work &w, int out_index, void *dump, BuiltItem 
       double *z64;
       const std::vector<double> *zh;
       if ((s = m1_table(p->icdf_bits, &z64, &zh)) != MLMC_OK) return s;
-      const int64_t zmax = table_zmax_fixed(*zh, p->icdf_bits, p->icdf_method, fZ);
+      const int64_t zmax = table_zmax_fixed(*zh, p->icdf_bits, p->icdf_method, fZ, m2_fields_of(p));
       if ((double)zmax > std::ldexp(1.0, e[F_Z] + fZ) - 1.0) return MLMC_EOVERFLOW;
       unit = f[F_S] + (p->payoff == MLMC_ASIAN ? lev + 1 : 0);
       bool s64 = false;
@@ -471,7 +473,7 @@ mlmc_status build_item(const mlmc_work &w, int out_index, void *dump, BuiltItem 
       unit = 24;
     }
     const void *tab = nullptr;
-    mlmc_status s = get_table(p->icdf_method, p->icdf_bits, rep, fZ, &tab, true);
+    mlmc_status s = get_table(p->icdf_method, p->icdf_bits, rep, fZ, &tab, true, m2_fields_of(p));
     if (s != MLMC_OK) return s;
     it.ztab = tab;
     b.smem = p->icdf_method != 3 ? (size_t)(1 << p->icdf_bits) * (fixed ? 4 : 2) : sizeof(M3Coef);
@@ -479,7 +481,7 @@ mlmc_status build_item(const mlmc_work &w, int out_index, void *dump, BuiltItem 
     if (p->icdf_method == 2 && !exact_int) {
       // Method 2 coupling: the correction's exact path reads the interval ranks
       const uint16_t *perm = nullptr;
-      if ((s = m2_perm_device(p->icdf_bits, &perm)) != MLMC_OK) return s;
+      if ((s = m2_perm_device(p->icdf_bits, m2_fields_of(p), &perm)) != MLMC_OK) return s;
       it.perm = perm;
       b.smem += sizeof(uint16_t) << p->icdf_bits;
     }
@@ -521,7 +523,7 @@ mlmc_status build_item_cached(const mlmc_work &w, int out_index, void *dump, Bui
   put(&p->S0, sizeof(double) * 5);
   put(&p->payoff, sizeof(int32_t) * 4);
   put(&p->request_id, sizeof(uint32_t));
-  put(&p->rng_pack, sizeof(int32_t));
+  put(&p->rng_pack, sizeof(int32_t) * 2);   // rng_pack, icdf_fields
   const int has_fmt = p->formats ? (w.level < p->n_formats ? 1 : 2) : 0;
   put(&has_fmt, sizeof has_fmt);
   if (has_fmt == 1) put(&p->formats[w.level], sizeof(mlmc_format));

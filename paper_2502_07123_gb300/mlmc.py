@@ -42,7 +42,7 @@ class Params(ctypes.Structure):
                 ("payoff", ctypes.c_int32), ("scheme", ctypes.c_int32),
                 ("icdf_method", ctypes.c_int32), ("icdf_bits", ctypes.c_int32),
                 ("formats", ctypes.POINTER(Format)), ("n_formats", ctypes.c_int32),
-                ("request_id", ctypes.c_uint32), ("rng_pack", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("request_id", ctypes.c_uint32), ("rng_pack", ctypes.c_int32), ("icdf_fields", ctypes.c_int32)]
 
 
 class Sums(ctypes.Structure):
@@ -149,7 +149,8 @@ def load():
         "mlmc_sensitivities": (st, [ctypes.c_int, ctypes.c_uint64, P(Params), ctypes.c_uint64, ctypes.c_uint64,
                                     P(Sensitivity), ctypes.c_void_p]),
         "mlmc_optimise_level": (st, [ctypes.c_int, P(Sensitivity), P(OptConfig), P(OptResult)]),
-        "mlmc_icdf_method2": (st, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, P(ctypes.c_int)]),
+        "mlmc_icdf_method2": (st, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, P(ctypes.c_int)]),
+        "mlmc_icdf_method2_table": (st, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_double)]),
         "mlmc_default_format": (st, [P(Params), ctypes.c_int, P(Format)]),
         "mlmc_icdf_table": (st, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_double)]),
         "mlmc_philox": (st, [P(ctypes.c_uint32), ctypes.c_uint64, ctypes.c_uint64, P(ctypes.c_uint32)]),
@@ -175,7 +176,7 @@ def _sums_dict(s):
     return d
 
 
-def make_params(p, d=10, method=1, formats=None, request=0, rng_pack=0):
+def make_params(p, d=10, method=1, formats=None, request=0, rng_pack=0, fields=0):
     """Build an mlmc_params from a dict (S0, K, r, sigma, T, payoff, scheme).
 
     formats: None (library default schedule) or a list, indexed by level, of
@@ -187,7 +188,7 @@ def make_params(p, d=10, method=1, formats=None, request=0, rng_pack=0):
     P.icdf_method, P.icdf_bits = int(method), int(d)
     P.request_id = int(request)
     P.rng_pack = int(rng_pack)
-    P.reserved = 0
+    P.icdf_fields = int(fields)
     if formats is not None:
         arr = (Format * len(formats))()
         for i, fm in enumerate(formats):
@@ -499,13 +500,21 @@ def mlmc_icdf_table(method, d, rep, fZ=0):
     return np.frombuffer(out, dtype=np.float64).copy()
 
 
-def mlmc_icdf_method2(d):
-    """Method-2 small table, interval ranks pi and least-squares iterations (mlmc_icdf_method2)."""
-    x = np.zeros(1 << (d // 2 - 1), dtype=np.float64)
+def mlmc_icdf_method2(d, n=2):
+    """Method-2 small table, interval ranks pi and least-squares fits of n fields (mlmc_icdf_method2)."""
+    n = n or 2
+    x = np.zeros(1 << max(0, d // n - 1), dtype=np.float64)
     pi = np.zeros(1 << d, dtype=np.uint32)
     it = ctypes.c_int()
-    _check(load().mlmc_icdf_method2(d, x.ctypes.data, pi.ctypes.data, ctypes.byref(it)), "mlmc_icdf_method2")
+    _check(load().mlmc_icdf_method2(d, n, x.ctypes.data, pi.ctypes.data, ctypes.byref(it)), "mlmc_icdf_method2")
     return dict(x=x, pi=pi, iterations=it.value)
+
+
+def mlmc_icdf_method2_table(d, n, rep, fZ=0):
+    """Method-2 values of the indices k < 2^(d-1) in a representation (mlmc_icdf_method2_table)."""
+    out = (ctypes.c_double * (1 << (d - 1)))()
+    _check(load().mlmc_icdf_method2_table(d, n, rep, fZ, out), "mlmc_icdf_method2_table")
+    return np.frombuffer(out, dtype=np.float64).copy()
 
 
 def icdf_mse(d, method=1):

@@ -2,7 +2,8 @@
 interval ranks and the iteration count, the table values in every
 representation (bit for bit), per-sample parity of approximate and
 correction estimators (fixed point and binary16; the correction's exact path
-reads the uniform of interval pi(j)), packed draws, and a nested price."""
+reads the uniform of interval pi(j)), packed draws, and a nested price; two
+fields and n = 3, 4, 6, 7 fields."""
 import math
 
 import numpy as np
@@ -84,3 +85,52 @@ def test_noalloc_rejects_method2(m):
     with pytest.raises(m.MLMCError) as e:
         m.mlmc_level_noalloc(2, 1000, P, core.FIXED_APPROX, 1)
     assert e.value.status == m.EINVAL
+
+
+# n fields of d/n bits: (d, n) with 2 to 4 bits per field
+FIELDS = [(6, 3), (9, 3), (12, 3), (8, 4), (12, 4), (12, 6), (14, 7)]
+
+
+@pytest.mark.parametrize("d,n", FIELDS)
+def test_n_fields_small_table_and_ranks(m, d, n):
+    g = m.mlmc_icdf_method2(d, n)
+    r = T.m2_optimise(d, n)
+    assert g["iterations"] == r["iterations"]
+    np.testing.assert_allclose(g["x"], r["x"], rtol=1e-11, atol=1e-13)
+    np.testing.assert_array_equal(g["pi"], r["pi"])
+
+
+@pytest.mark.parametrize("d,n", FIELDS)
+def test_n_fields_table_values(m, d, n):
+    for rep, name, fZ in ((4, "fixed", 12), (2, "fp16", 0), (3, "bf16", 0), (1, "fp32", 0)):
+        g = m.mlmc_icdf_method2_table(d, n, rep, fZ)
+        np.testing.assert_array_equal(g, T.table(d, 2, name, fZ, n), err_msg="%s" % name)
+    np.testing.assert_allclose(m.mlmc_icdf_method2_table(d, n, 0), T.table(d, 2, "fp64", 0, n), rtol=1e-11,
+                               atol=1e-13)
+
+
+@pytest.mark.parametrize("variant", [core.FIXED_APPROX, core.CORR_FIXED, core.FP16_APPROX, core.CORR_BF16])
+@pytest.mark.parametrize("d,n", [(9, 3), (12, 4)])
+@pytest.mark.parametrize("level", [0, 3])
+def test_n_fields_samples_match_oracle(m, variant, d, n, level):
+    p = W.params(payoff=W.EURO)
+    fm = [W.default_format(p, lev) for lev in range(level + 1)]
+    P = m.make_params(p, d=d, method=2, formats=fm, fields=n)
+    N, first, seed = 300, 5, 607
+    _, od = core.level(p, level, first, N, variant, seed, d=d, method=2, fmt=fm[level], dump=True, fields=n)
+    _, gd = m.mlmc_level_dump(level, N, P, variant, seed, first)
+    compare_samples(variant, p, gd, od)
+
+
+def test_n_fields_rules(m):
+    p = W.params()
+    for d, n in ((10, 3), (10, 4), (8, 8), (16, 4)):     # n must divide d with >= 2 bits per field, d <= 14
+        with pytest.raises(m.MLMCError) as e:
+            m.mlmc_level(2, 100, m.make_params(p, d=d, method=2, fields=n), core.FIXED_APPROX, 1)
+        assert e.value.status == m.EINVAL
+    with pytest.raises(m.MLMCError):
+        m.mlmc_level(2, 100, m.make_params(p, d=10, method=1, fields=2), core.FIXED_APPROX, 1)
+    # n = 0 is n = 2
+    a = m.mlmc_level(3, 5000, m.make_params(p, d=10, method=2, fields=0), core.CORR_FIXED, 4)
+    b = m.mlmc_level(3, 5000, m.make_params(p, d=10, method=2, fields=2), core.CORR_FIXED, 4)
+    assert a["sum"] == b["sum"] and a["sum2"] == b["sum2"]
