@@ -51,12 +51,36 @@ def test_least_squares_optimal_at_fixed_point(d):
 
 
 def test_n_fields_general():
-    """n = 3 and 4 fields: the same construction converges and beats its start."""
-    for d, n in ((9, 3), (8, 4)):
+    """n = 3, 4, 6 fields: the iteration stops (converged or back in an earlier
+    permutation), beats its start, and returns the ranking of its own values;
+    the sums are A x, antisymmetric, and identical for indices whose fields are
+    the same values in another order."""
+    for d, n in ((9, 3), (12, 3), (8, 4), (12, 4), (12, 6)):
         r = T.m2_optimise(d, n)
         assert r["iterations"] < 1000
         assert r["mse"] < r["mse0"]
-        np.testing.assert_array_equal(T.m2_rank(r["values"]), r["pi"])
+        v = r["values"]
+        np.testing.assert_array_equal(T.m2_rank(v), r["pi"])
+        assert sorted(r["pi"].tolist()) == list(range(1 << d))
+        np.testing.assert_allclose(v, T.m2_design(d, n) @ r["x"], rtol=0, atol=1e-13)
+        np.testing.assert_array_equal(v[::-1], -v)
+        b = d // n
+        j = np.arange(1 << d)
+        fields = [(j >> (b * (n - 1 - i))) & ((1 << b) - 1) for i in range(n)]
+        rolled = sum(fields[(i + 1) % n] << (b * (n - 1 - i)) for i in range(n))
+        np.testing.assert_array_equal(v[rolled], v)
+
+
+def test_two_field_sums_are_the_plain_sum():
+    """For n = 2 the ordered net-count sum is x_a +- x_b as written."""
+    d = 10
+    r = T.m2_optimise(d)
+    x, b = r["x"], d // 2
+    for jj in range(0, 1 << d, 37):
+        f1, f2 = jj >> b, jj & ((1 << b) - 1)
+        a = x[f1] if f1 < (1 << (b - 1)) else -x[(1 << b) - 1 - f1]
+        c = x[f2] if f2 < (1 << (b - 1)) else -x[(1 << b) - 1 - f2]
+        assert r["values"][jj] == a + c
 
 
 def test_mse_against_monte_carlo_with_coupled_uniform():
