@@ -43,11 +43,17 @@ template <> struct HType<AP_BF16> { using T = __nv_bfloat16; };
 constexpr int MAX_THREADS = 256;
 // Register budget: the approximate fixed-point Euler kernel with terminal payoffs
 // (the bulk of the nested estimator) runs with 6 resident 128-thread CTAs per SM
-// (<= 85 registers per thread), measured faster than its natural ~100 registers;
-// every other instantiation keeps its natural allocation (a cap there spills).
+// (80 registers per thread), measured faster than its natural ~100 registers.
+// The matching correction kernel (static launch) takes the same budget, 80
+// instead of 111 registers: alone it is 2% slower, but beside the approximate
+// kernels of a work list its CTAs fit next to theirs and the step is 3% faster
+// (its device-scheduled form would spill there and keeps its allocation).
+// Every other instantiation keeps its natural allocation (a cap there spills).
 constexpr int LAUNCH_THREADS = 128;
-template <int EST, int AP, int SCHEME, int PC> struct MinCtas {
-  static constexpr int value = (EST == EST_APPROX && AP == AP_FX32 && SCHEME == 0 && PC == PC_TERMINAL) ? 6 : 1;
+template <int EST, int AP, int SCHEME, int PC, bool DYN = false> struct MinCtas {
+  static constexpr bool EM_TERMINAL_FX32 = AP == AP_FX32 && SCHEME == 0 && PC == PC_TERMINAL;
+  static constexpr int value =
+      (EM_TERMINAL_FX32 && (EST == EST_APPROX || (EST == EST_CORR && !DYN))) ? 6 : 1;
 };
 
 // Bytes per entry of the shared-memory approximate-Normal table of a datapath.
@@ -828,7 +834,7 @@ level_kernel(const __grid_constant__ LaunchArgs args) {
 // and chunk counts come from args.dyn, written on the device before the
 // launch; CTA b runs chunks b, b + gridDim.x, ...
 template <int EST, int XP, int AP, int SCHEME, int PC, int KP>
-__global__ void __launch_bounds__(LAUNCH_THREADS, MinCtas<EST, AP, SCHEME, PC>::value)
+__global__ void __launch_bounds__(LAUNCH_THREADS, MinCtas<EST, AP, SCHEME, PC, true>::value)
 level_kernel_dyn(const __grid_constant__ LaunchArgs args) {
   const DynLaunch d = *args.dyn;
   const void *staged = nullptr;
