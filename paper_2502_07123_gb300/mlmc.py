@@ -176,6 +176,24 @@ def _sums_dict(s):
     return d
 
 
+SUMS_DTYPE = np.dtype([(k, {ctypes.c_double: "<f8", ctypes.c_uint64: "<u8", ctypes.c_int64: "<i8",
+                            ctypes.c_int32: "<i4"}[t]) for k, t in Sums._fields_])
+
+
+def _sums_list(out, raw=False):
+    """Results of an mlmc_sums array: a structured array (raw) or one dict per item."""
+    a = np.frombuffer(out, dtype=SUMS_DTYPE).copy()
+    if raw:
+        return a
+    names = SUMS_DTYPE.names
+    res = []
+    for row in a.tolist():
+        d = dict(zip(names, row))
+        d["isum2"] = (d["isum2_hi"] << 64) | d["isum2_lo"]
+        res.append(d)
+    return res
+
+
 def make_params(p, d=10, method=1, formats=None, request=0, rng_pack=0, fields=0):
     """Build an mlmc_params from a dict (S0, K, r, sigma, T, payoff, scheme).
 
@@ -237,20 +255,27 @@ def mlmc_level_noalloc(level, N, params, variant, seed, first_sample=0, stream=N
     return _sums_dict(s)
 
 
+class WorkList:
+    """A work list marshalled once (the mlmc_work array and the params it points
+    to), for repeated mlmc_run / Plan calls on the same items."""
+
+    def __init__(self, items):
+        items = list(items)
+        self.arr = (Work * len(items))()
+        self.keep = [it["params"] for it in items]
+        P = ctypes.POINTER(Params)
+        for i, it in enumerate(items):
+            self.arr[i] = Work(P(it["params"]), int(it["level"]), int(it["variant"]), int(it.get("first_sample", 0)),
+                               int(it["N"]), int(it.get("stream", -1)), int(it.get("flags", 0)))
+
+    def __len__(self):
+        return len(self.arr)
+
+
 def _works(items):
-    """items: list of dict(params=Params, level, variant, first_sample=0, N, stream=-1)."""
-    arr = (Work * len(items))()
-    keep = []
-    for i, it in enumerate(items):
-        keep.append(it["params"])
-        arr[i].params = ctypes.pointer(it["params"])
-        arr[i].level = int(it["level"])
-        arr[i].variant = int(it["variant"])
-        arr[i].first_sample = int(it.get("first_sample", 0))
-        arr[i].N = int(it["N"])
-        arr[i].stream = int(it.get("stream", -1))
-        arr[i].flags = int(it.get("flags", 0))
-    return arr, keep
+    """items: a WorkList, or a list of dict(params=Params, level, variant, first_sample=0, N, stream=-1)."""
+    wl = items if isinstance(items, WorkList) else WorkList(items)
+    return wl.arr, wl.keep
 
 
 def _tuning(tuning):
@@ -276,7 +301,7 @@ class Plan:
     def __init__(self, items, seed, tuning=None):
         L = load()
         self._arr, self._keep = _works(items)
-        self.n = len(items)
+        self.n = len(self._arr)
         self._h = ctypes.c_void_p()
         _check(L.mlmc_plan_create(ctypes.byref(self._h), self._arr, self.n, seed, _tuning(tuning)),
                "mlmc_plan_create")
@@ -284,10 +309,10 @@ class Plan:
     def launch(self, stream=None):
         _check(load().mlmc_plan_launch(self._h, _stream_handle(stream)), "mlmc_plan_launch")
 
-    def results(self):
+    def results(self, raw=False):
         out = (Sums * self.n)()
         _check(load().mlmc_plan_results(self._h, out), "mlmc_plan_results")
-        return [_sums_dict(out[i]) for i in range(self.n)]
+        return _sums_list(out, raw)
 
     def info(self):
         k = ctypes.c_int()
@@ -332,12 +357,14 @@ class Plan:
             pass
 
 
-def mlmc_run(items, seed, tuning=None, stream=None):
+def mlmc_run(items, seed, tuning=None, stream=None, raw=False):
+    """Plan, launch, read and release (mlmc_run); items a list of dicts or a WorkList.
+    Returns one dict per item, or with raw a structured array (SUMS_DTYPE)."""
     L = load()
     arr, keep = _works(items)
-    out = (Sums * len(items))()
-    _check(L.mlmc_run(arr, len(items), seed, _tuning(tuning), out, _stream_handle(stream)), "mlmc_run")
-    return [_sums_dict(out[i]) for i in range(len(items))]
+    out = (Sums * len(arr))()
+    _check(L.mlmc_run(arr, len(arr), seed, _tuning(tuning), out, _stream_handle(stream)), "mlmc_run")
+    return _sums_list(out, raw)
 
 
 def mlmc_sensitivities(level, N, params, seed, first_sample=0, per_instance=False):
@@ -390,8 +417,8 @@ def mlmc_autotune(items, seed, reps=5):
     (mlmc_autotune); returns the chosen (threads, steps_per_thread) per item."""
     L = load()
     arr, keep = _works(items)
-    out = (Tuning * len(items))()
-    _check(L.mlmc_autotune(arr, len(items), seed, reps, out), "mlmc_autotune")
+    out = (Tuning * len(arr))()
+    _check(L.mlmc_autotune(arr, len(arr), seed, reps, out), "mlmc_autotune")
     return [(t.threads, t.steps_per_thread) for t in out]
 
 

@@ -158,3 +158,27 @@ def test_plan_launch_items_partition_the_work(m):
             plan.launch_items(plan.info()["kernels"])
     finally:
         plan.close()
+
+
+def test_worklist_and_raw_results(m):
+    # a marshalled-once work list and the structured-array results give the
+    # same sums as the list-of-dicts call
+    p = W.params()
+    P = _P(m, p, pack=1)
+    items = [dict(params=P, level=lev, variant=v, N=2000 + lev, first_sample=lev)
+             for lev in (0, 2, 5) for v in (W.FIXED_APPROX, W.CORR_FIXED, W.FP32_EXACT)]
+    a = m.mlmc_run(items, 21)
+    wl = m.WorkList(items)
+    b = m.mlmc_run(wl, 21)
+    raw = m.mlmc_run(wl, 21, raw=True)
+    plan = m.Plan(wl, 21)
+    try:
+        plan.launch()
+        c = plan.results(raw=True)
+    finally:
+        plan.close()
+    for i, x in enumerate(a):
+        assert x["isum"] == b[i]["isum"] and x["isum2"] == b[i]["isum2"] and x["sum"] == b[i]["sum"]
+        assert raw[i]["sum"] == x["sum"] and raw[i]["sum2"] == x["sum2"] and raw[i]["isum"] == x["isum"]
+        assert (int(raw[i]["isum2_hi"]) << 64 | int(raw[i]["isum2_lo"])) == x["isum2"]
+        assert c[i]["sum"] == x["sum"] and c[i]["n"] == x["n"]
