@@ -419,11 +419,14 @@ struct LevelSim {
       return x - mn;
     }
   }
+  // PAY: the terminal payoff when known at compile time (0 European, 1 digital), -1 otherwise
+  template <int PAY = -1>
   __device__ __forceinline__ int64_t fixed_payoff(int64_t x, int64_t inner, int64_t mn, int steps, bool coarse) const {
     if constexpr (PC == PC_TERMINAL && AP == AP_FX32) {
       // S, K < 2^31 on this datapath: 32-bit arithmetic
       const int32_t x32 = (int32_t)x, K32v = (int32_t)fx.K;
-      const int32_t v = payoff == 1 ? (int32_t)1 << fx.fS : x32 - K32v;
+      const bool digital = PAY >= 0 ? PAY == 1 : payoff == 1;
+      const int32_t v = digital ? (int32_t)1 << fx.fS : x32 - K32v;
       return x32 > K32v ? v : 0;
     } else if constexpr (PC == PC_TERMINAL) {
       if (payoff == 1) return x > fx.K ? ((int64_t)1 << fx.fS) : 0;
@@ -460,7 +463,7 @@ struct LevelSim {
 
   // Finish the sample: payoffs, sample value, accumulation and optional dump
   // (EAGER false: a LAZY pack that stayed in range, so no saturation).
-  template <bool EAGER = true, class Acc>
+  template <bool EAGER = true, int PAY = -1, class Acc>
   __device__ __forceinline__ void finish(Acc &acc, int l, bool valid, mlmc_sample_rec *dump) {
     X pf = X(0), pc = X(0);
     int64_t qf = 0, qc = 0, afS = 0, acS = 0;
@@ -470,8 +473,8 @@ struct LevelSim {
       if (level > 0) pc = exact_payoff(Sc, accC, minC, nsteps >> 1);
     }
     if constexpr (FIXED) {
-      qf = fixed_payoff(aS[l], aaccF[l], aminF[l], nsteps, false);
-      if (level > 0) qc = fixed_payoff(aSc[l], aaccC[l], aminC[l], nsteps >> 1, true);
+      qf = fixed_payoff<PAY>(aS[l], aaccF[l], aminF[l], nsteps, false);
+      if (level > 0) qc = fixed_payoff<PAY>(aSc[l], aaccC[l], aminC[l], nsteps >> 1, true);
       afS = aS[l];
       acS = aSc[l];
       if constexpr (FAST) lsat = (EAGER && satb[l]) ? 1u : 0u;
@@ -483,29 +486,35 @@ struct LevelSim {
         if (level > 0) qc = half_payoff(lane_Sc(l), haccC[l], hminC[l], nsteps >> 1);
       }
     }
-    if (!valid) return;
     double ydump;
-    if constexpr (EST == EST_EXACT) {
-      const X y = pf - pc;
-      acc.add_real(y);
-      ydump = (double)y;
-    } else if constexpr (EST == EST_APPROX) {
-      const int64_t yi = qf - qc;
+    if constexpr (EST == EST_APPROX) {
+      // integer sums: a sample outside the item's range adds zero, so the
+      // range test does not branch the group's straight-line code
+      const int64_t yi = valid ? qf - qc : 0;
       if constexpr (AP == AP_FX32 && PC == PC_TERMINAL) {
         // |Y| < 2^31 here and the host bounds a group's sum of squares below 2^64
         acc.add_group((int32_t)yi);
       } else {
         acc.add_int(yi);
       }
+      acc.nsat += valid ? lsat : 0u;
+      if (!valid) return;
       ydump = (double)yi * (double)unit_scale;
     } else {
-      const float yx = (float)(pf - pc);
-      const float ya = __fmul_rn(__ll2float_rn(qf - qc), unit_scale);
-      const float y = __fsub_rn(yx, ya);
-      acc.add_real(y);
-      ydump = (double)y;
+      if (!valid) return;
+      if constexpr (EST == EST_EXACT) {
+        const X y = pf - pc;
+        acc.add_real(y);
+        ydump = (double)y;
+      } else {
+        const float yx = (float)(pf - pc);
+        const float ya = __fmul_rn(__ll2float_rn(qf - qc), unit_scale);
+        const float y = __fsub_rn(yx, ya);
+        acc.add_real(y);
+        ydump = (double)y;
+      }
+      acc.nsat += lsat;
     }
-    acc.nsat += lsat;
     if (dump) {
       mlmc_sample_rec r;
       r.pf = (double)pf; r.pc = (double)pc;
@@ -620,6 +629,8 @@ __device__ __forceinline__ void block_reduce_write(ThreadAcc<EST, XP> &a, Partia
   }
 }
 
+template <int P> using PayTag = std::integral_constant<int, P>;
+
 // The compiler may not reuse a value computed before this point: the clamped
 // re-run of a LAZY group recomputes its draws instead of keeping the first
 // run's live in registers through the group.
@@ -653,13 +664,18 @@ __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDes
   // and run again on the clamped datapath (rare).  The check is once per
   // group, so the group's packs stay one straight-line block.
   const bool lazy = Sim::LAZY && !DUMP && it.ff.lazy;
+  const bool digital = it.payoff == 1;
   // A group is one Philox call's worth of packs (4 on level 0, 2 on level 1) or,
   // from level 2, one pack over 2^l / 4 calls; a pack holds KP samples.
   for (uint32_t r = threadIdx.x; r < ng; r += blockDim.x) {
     const uint64_t g = gbeg + r;
     const bool full = g >= gf0 && g < gf1;
-    auto group = [&](auto eager) {
+    // FULL (compile time): every sample of the group is in the item's range, so
+    // no per-sample range test splits the group's straight-line code
+    auto group = [&](auto eager, auto fulltag, auto paytag) {
       constexpr bool E = decltype(eager)::value;
+      constexpr bool FULL = decltype(fulltag)::value;
+      constexpr int PAY = decltype(paytag)::value;
       if (lev >= 2) {
         uint64_t P = g;
         uint32_t lsh = 0;   // lane-split packed draws: this sample's field to the top of the word
@@ -685,8 +701,8 @@ __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDes
 #pragma unroll
         for (int l = 0; l < KP; ++l) {
           const uint64_t s = KP == 1 ? g : P * KP + l;
-          const bool valid = full || (s >= first && s < last);
-          sim.template finish<E>(acc, l, valid, DUMP && valid ? dump + (s - first) : nullptr);
+          const bool valid = FULL || full || (s >= first && s < last);
+          sim.template finish<E, PAY>(acc, l, valid, DUMP && valid ? dump + (s - first) : nullptr);
         }
       } else {
         uint64_t gw = g;
@@ -698,7 +714,7 @@ __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDes
         const uint64_t s0 = (uint64_t)(ppg * KP) * g;
         // samples s0 + k are valid for k in [klo, khi)
         int klo = 0, khi = ppg * KP;
-        if (!full) {
+        if (!FULL && !full) {
           klo = s0 >= first ? 0 : (int)min(first - s0, (uint64_t)(ppg * KP));
           khi = last <= s0 ? 0 : (int)min(last - s0, (uint64_t)(ppg * KP));
         }
@@ -711,8 +727,8 @@ __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDes
 #pragma unroll
             for (int l = 0; l < KP; ++l) {
               const int k = u * KP + l;
-              const bool valid = k >= klo && k < khi;
-              sim.template finish<E>(acc, l, valid, DUMP && valid ? dump + (s0 + k - first) : nullptr);
+              const bool valid = FULL || (k >= klo && k < khi);
+              sim.template finish<E, PAY>(acc, l, valid, DUMP && valid ? dump + (s0 + k - first) : nullptr);
             }
           }
         } else {
@@ -723,25 +739,34 @@ __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDes
 #pragma unroll
             for (int l = 0; l < KP; ++l) {
               const int k = u * KP + l;
-              const bool valid = k >= klo && k < khi;
-              sim.template finish<E>(acc, l, valid, DUMP && valid ? dump + (s0 + k - first) : nullptr);
+              const bool valid = FULL || (k >= klo && k < khi);
+              sim.template finish<E, PAY>(acc, l, valid, DUMP && valid ? dump + (s0 + k - first) : nullptr);
             }
           }
         }
       }
     };
-    bool eager = true;
     if constexpr (Sim::LAZY && !DUMP) {
-      if (lazy) {
-        // only the integer sums change inside a LAZY group (no saturations)
+      // the lazy run takes full groups only; a partial group (at most one at
+      // each end of an item) and a redone group run the clamped datapath
+      bool eager = true;
+      if (lazy && full) {
+        // only the integer sums change inside a LAZY group (no saturations);
+        // the terminal payoff is a compile-time choice on this path
         const auto saved = acc.mark();
         sim.hi = 0;
-        group(std::false_type{});
+        if (digital) group(std::false_type{}, std::true_type{}, PayTag<1>{});
+        else group(std::false_type{}, std::true_type{}, PayTag<0>{});
         eager = sim.over();
         if (eager) acc.rewind(saved);
       }
+      if (eager) group(std::true_type{}, std::false_type{}, PayTag<-1>{});
+    } else if constexpr (!DUMP) {
+      if (full) group(std::true_type{}, std::true_type{}, PayTag<-1>{});
+      else group(std::true_type{}, std::false_type{}, PayTag<-1>{});
+    } else {
+      group(std::true_type{}, std::false_type{}, PayTag<-1>{});
     }
-    if (eager) group(std::true_type{});
     if constexpr (EST == EST_APPROX && AP == AP_FX32 && PC == PC_TERMINAL) acc.flush_group();
   }
   block_reduce_write<EST, XP>(acc, args.partials + gc);
