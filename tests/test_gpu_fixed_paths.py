@@ -61,5 +61,9 @@ def test_fixed_datapaths(m, kind, variant, scheme, payoff, level):
     if variant == core.FIXED_APPROX:
         assert gs["isum"] == os_["isum"] and gs["isum2"] == os_["isum2"]
         assert gs["saturations"] == os_["saturations"]
+        # without per-sample records (the lazy 32-bit datapath where it applies)
+        ls = m.mlmc_level(level, N, P, variant, seed, first)
+        assert ls["isum"] == os_["isum"] and ls["isum2"] == os_["isum2"]
+        assert ls["saturations"] == os_["saturations"]
     if kind == "saturating_S":
         assert os_["saturations"] > 0

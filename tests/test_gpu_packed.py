@@ -107,3 +107,8 @@ def test_packed_fixed_saturating(m, sigma, scheme, level, N):
     assert gs["isum"] == os_["isum"] and gs["isum2"] == os_["isum2"]
     assert gs["saturations"] == os_["saturations"]
     compare_samples(core.FIXED_APPROX, p, gd, od)
+    # the same samples without per-sample records: the lazy path (groups redone
+    # clamped when S leaves its range) gives the same integer sums and counts
+    ls = m.mlmc_level(level, N, P, m.FIXED_APPROX, 33, first)
+    assert ls["isum"] == os_["isum"] and ls["isum2"] == os_["isum2"]
+    assert ls["saturations"] == os_["saturations"]
