@@ -659,12 +659,11 @@ __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDes
 
   const uint64_t gf0 = it.gf0, gf1 = it.gf1;
   const uint32_t ng = gend > gbeg ? (uint32_t)(gend - gbeg) : 0u;
-  // LAZY items run each group first with S unclamped and the samples added to
-  // the accumulators tentatively; a group whose S went above lim_S is undone
-  // and run again on the clamped datapath (rare).  The check is once per
-  // group, so the group's packs stay one straight-line block.
+  // LAZY items run each full group first with S unclamped and the samples
+  // added to the accumulators tentatively; a group whose S went above lim_S is
+  // undone and run again on the clamped datapath (rare).  The check is once
+  // per group, so the group's packs stay one straight-line block.
   const bool lazy = Sim::LAZY && !DUMP && it.ff.lazy;
-  const bool digital = it.payoff == 1;
   // A group is one Philox call's worth of packs (4 on level 0, 2 on level 1) or,
   // from level 2, one pack over 2^l / 4 calls; a pack holds KP samples.
   for (uint32_t r = threadIdx.x; r < ng; r += blockDim.x) {
@@ -755,7 +754,7 @@ __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDes
         // the terminal payoff is a compile-time choice on this path
         const auto saved = acc.mark();
         sim.hi = 0;
-        if (digital) group(std::false_type{}, std::true_type{}, PayTag<1>{});
+        if (it.payoff == 1) group(std::false_type{}, std::true_type{}, PayTag<1>{});
         else group(std::false_type{}, std::true_type{}, PayTag<0>{});
         eager = sim.over();
         if (eager) acc.rewind(saved);
