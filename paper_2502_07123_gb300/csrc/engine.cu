@@ -480,6 +480,7 @@ cudaError_t enqueue_iteration(mlmc_engine *e, const std::vector<int> &live) {
     a.rk = G.rk;
     a.dyn = e->d_dyn + live[i];
     a.counters = nullptr;   // acc_kernel sums the partials
+    a.dump = 0;
     a.out = nullptr;
     if ((err = cudaStreamWaitEvent(ls, e->fork, 0)) != cudaSuccess) break;
     if ((err = launch_by_family(G.family, G.scheme, G.pc, dim3(G.grid), dim3(G.threads), G.smem, ls, a,

@@ -132,6 +132,9 @@ struct LaunchArgs {
   // separate kernel does)
   uint32_t *counters;
   DevSums *out;
+  // nonzero: some item of the launch writes per-sample records (the launch
+  // uses the kernel that holds the record-writing code)
+  int dump;
 };
 
 #if defined(__CUDACC__)

@@ -637,8 +637,10 @@ template <int P> using PayTag = std::integral_constant<int, P>;
 __device__ __forceinline__ void opaque(uint64_t &x) { asm volatile("" : "+l"(x)); }
 
 // Simulate one chunk of an item (its table already in shared memory) and
-// write the CTA's Partial for it.
-template <int EST, int XP, int AP, int SCHEME, int PC, int KP, int MSEL, bool DUMP>
+// write the CTA's Partial for it.  DYN (device-scheduled kernel) only keeps the
+// instantiations of the static and device-scheduled kernels apart, so that
+// each is compiled inline into its own kernel.
+template <int EST, int XP, int AP, int SCHEME, int PC, int KP, int MSEL, bool DUMP, bool DYN>
 __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDesc &it, int item, uint32_t gc,
                                            const unsigned char *smem_tab) {
   using Sim = LevelSim<EST, XP, AP, SCHEME, PC, KP, MSEL>;
@@ -795,7 +797,7 @@ __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDes
 // and write the CTA's Partial for the chunk.  Every thread has finished the
 // previous chunk before the table is overwritten (block_reduce_write ends with
 // a barrier).
-template <int EST, int XP, int AP, int SCHEME, int PC, int KP, bool ALLOW_DUMP>
+template <int EST, int XP, int AP, int SCHEME, int PC, int KP, bool ALLOW_DUMP, bool DYN>
 __device__ __forceinline__ void run_chunk(const LaunchArgs &args, const ItemDesc *items, int n_items, uint32_t gc,
                                           const void **staged) {
   extern __shared__ __align__(16) unsigned char smem_tab[];
@@ -838,12 +840,12 @@ __device__ __forceinline__ void run_chunk(const LaunchArgs &args, const ItemDesc
   }
   const int item = s_item;
   if (ALLOW_DUMP && it.dump) {
-    if constexpr (ALLOW_DUMP) chunk_body<EST, XP, AP, SCHEME, PC, KP, 2, true>(args, it, item, gc, smem_tab);
+    if constexpr (ALLOW_DUMP) chunk_body<EST, XP, AP, SCHEME, PC, KP, 2, true, DYN>(args, it, item, gc, smem_tab);
   } else if constexpr (AP == AP_NONE) {
-    chunk_body<EST, XP, AP, SCHEME, PC, KP, 0, false>(args, it, item, gc, smem_tab);
+    chunk_body<EST, XP, AP, SCHEME, PC, KP, 0, false, DYN>(args, it, item, gc, smem_tab);
   } else {
-    if (it.method == 3) chunk_body<EST, XP, AP, SCHEME, PC, KP, 1, false>(args, it, item, gc, smem_tab);
-    else chunk_body<EST, XP, AP, SCHEME, PC, KP, 0, false>(args, it, item, gc, smem_tab);
+    if (it.method == 3) chunk_body<EST, XP, AP, SCHEME, PC, KP, 1, false, DYN>(args, it, item, gc, smem_tab);
+    else chunk_body<EST, XP, AP, SCHEME, PC, KP, 0, false, DYN>(args, it, item, gc, smem_tab);
   }
 }
 
@@ -851,7 +853,18 @@ __device__ __forceinline__ void run_chunk(const LaunchArgs &args, const ItemDesc
 template <int EST, int XP, int AP, int SCHEME, int PC, int KP>
 __global__ void __launch_bounds__(LAUNCH_THREADS, MinCtas<EST, AP, SCHEME, PC>::value)
 level_kernel(const __grid_constant__ LaunchArgs args) {
-  run_chunk<EST, XP, AP, SCHEME, PC, KP, true>(args, args.items, args.n_items, args.chunk0 + blockIdx.x, nullptr);
+  run_chunk<EST, XP, AP, SCHEME, PC, KP, false, false>(args, args.items, args.n_items, args.chunk0 + blockIdx.x,
+                                                      nullptr);
+}
+
+// The same for launches with per-sample records (parity runs): a kernel of
+// its own, so that the record-writing code does not weigh on the register
+// allocation of the launches without records.
+template <int EST, int XP, int AP, int SCHEME, int PC, int KP>
+__global__ void __launch_bounds__(LAUNCH_THREADS, MinCtas<EST, AP, SCHEME, PC>::value)
+level_kernel_dump(const __grid_constant__ LaunchArgs args) {
+  run_chunk<EST, XP, AP, SCHEME, PC, KP, true, false>(args, args.items, args.n_items, args.chunk0 + blockIdx.x,
+                                                     nullptr);
 }
 
 // Device-scheduled launch (fixed grid, captured once in a CUDA graph): the item
@@ -863,8 +876,8 @@ level_kernel_dyn(const __grid_constant__ LaunchArgs args) {
   const DynLaunch d = *args.dyn;
   const void *staged = nullptr;
   for (uint32_t rel = blockIdx.x; rel < d.n_chunks; rel += gridDim.x)
-    run_chunk<EST, XP, AP, SCHEME, PC, KP, false>(args, args.items + d.item_off, (int)d.n_items, d.chunk0 + rel,
-                                                  &staged);
+    run_chunk<EST, XP, AP, SCHEME, PC, KP, false, true>(args, args.items + d.item_off, (int)d.n_items,
+                                                        d.chunk0 + rel, &staged);
 }
 
 }  // namespace mlmc
@@ -873,7 +886,8 @@ namespace mlmc {
 
 template <int EST, int XP, int AP, int SCHEME, int PC, int KP>
 cudaError_t launch_one(dim3 grid, dim3 block, size_t smem, cudaStream_t st, const LaunchArgs &a, int *occ) {
-  auto k = (a.dyn || occ) ? level_kernel_dyn<EST, XP, AP, SCHEME, PC, KP> : level_kernel<EST, XP, AP, SCHEME, PC, KP>;
+  auto k = (a.dyn || occ) ? level_kernel_dyn<EST, XP, AP, SCHEME, PC, KP>
+                          : (a.dump ? level_kernel_dump<EST, XP, AP, SCHEME, PC, KP> : level_kernel<EST, XP, AP, SCHEME, PC, KP>);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

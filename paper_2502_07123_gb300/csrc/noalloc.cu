@@ -274,6 +274,7 @@ extern "C" mlmc_status mlmc_level_noalloc(int level, uint64_t N, const mlmc_para
   a.chunk0 = 0;
   a.dyn = nullptr;
   a.counters = nullptr;
+  a.dump = 0;
   a.out = nullptr;
   a.partials = S->partials;
   make_round_keys(seed, a.rk);

@@ -45,6 +45,7 @@ struct LaunchRec {
   uint32_t chunk0, n_chunks;
   int item_off, n_items;
   size_t smem;
+  bool dump;                // an item writes per-sample records
 };
 
 struct mlmc_plan {
@@ -200,11 +201,13 @@ mlmc_status plan_create_impl(mlmc_plan **out, const mlmc_work *work, int n_work,
     L.item_off = (int)pl->items.size();
     L.n_items = (int)o.second.size();
     L.smem = 0;
+    L.dump = false;
     for (int i : o.second) {
       ItemDesc it = built[i].it;
       it.chunk_begin = chunk;
       chunk += it.n_chunks;
       L.smem = std::max(L.smem, built[i].smem);
+      L.dump = L.dump || it.dump != nullptr;
       pl->items.push_back(it);
     }
     L.n_chunks = chunk - L.chunk0;
@@ -310,6 +313,7 @@ mlmc_status plan_launch_impl(mlmc_plan *pl, cudaStream_t st) {
     a.rk = pl->rk;
     a.counters = pl->d_counters + L.item_off;
     a.out = pl->d_out;
+    a.dump = L.dump ? 1 : 0;
     // per-kernel events only for plans a caller owns (mlmc_plan_kernel_time)
     if (!pl->borrowed) MLMC_CK(cudaEventRecord(pl->kstart[i], ls));
     MLMC_CK(launch_by_family(L.family, L.scheme, L.pc, dim3(L.n_chunks), dim3(L.threads), L.smem, ls, a, nullptr));
