@@ -48,12 +48,15 @@ constexpr int MAX_THREADS = 256;
 // instead of 111 registers: alone it is 2% slower, but beside the approximate
 // kernels of a work list its CTAs fit next to theirs and the step is 3% faster
 // (its device-scheduled form would spill there and keeps its allocation).
+// The approximate 32-bit fixed-point Asian kernels run 4 CTAs per SM (<= 128
+// registers, measured 8-16% faster than their natural ~144).
 // Every other instantiation keeps its natural allocation (a cap there spills).
 constexpr int LAUNCH_THREADS = 128;
 template <int EST, int AP, int SCHEME, int PC, bool DYN = false> struct MinCtas {
   static constexpr bool EM_TERMINAL_FX32 = AP == AP_FX32 && SCHEME == 0 && PC == PC_TERMINAL;
   static constexpr int value =
-      (EM_TERMINAL_FX32 && (EST == EST_APPROX || (EST == EST_CORR && !DYN))) ? 6 : 1;
+      (EM_TERMINAL_FX32 && (EST == EST_APPROX || (EST == EST_CORR && !DYN))) ? 6
+      : ((EST == EST_APPROX && AP == AP_FX32 && PC == PC_ASIAN) ? 4 : 1);
 };
 
 // Bytes per entry of the shared-memory approximate-Normal table of a datapath.
@@ -487,18 +490,20 @@ struct LevelSim {
       }
     }
     double ydump;
-    if constexpr (EST == EST_APPROX) {
-      // integer sums: a sample outside the item's range adds zero, so the
-      // range test does not branch the group's straight-line code
-      const int64_t yi = valid ? qf - qc : 0;
-      if constexpr (AP == AP_FX32 && PC == PC_TERMINAL) {
-        // |Y| < 2^31 here and the host bounds a group's sum of squares below 2^64
-        acc.add_group((int32_t)yi);
-      } else {
-        acc.add_int(yi);
-      }
+    if constexpr (EST == EST_APPROX && AP == AP_FX32 && PC == PC_TERMINAL) {
+      // a sample outside the item's range adds zero to the group sums, so the
+      // range test does not branch the group's straight-line code (|Y| < 2^31
+      // here and the host bounds a group's sum of squares below 2^64)
+      const int32_t yi = valid ? (int32_t)(qf - qc) : 0;
+      acc.add_group(yi);
       acc.nsat += valid ? lsat : 0u;
       if (!valid) return;
+      ydump = (double)yi * (double)unit_scale;
+    } else if constexpr (EST == EST_APPROX) {
+      if (!valid) return;
+      const int64_t yi = qf - qc;
+      acc.add_int(yi);
+      acc.nsat += lsat;
       ydump = (double)yi * (double)unit_scale;
     } else {
       if (!valid) return;
@@ -756,16 +761,21 @@ __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDes
         // the terminal payoff is a compile-time choice on this path
         const auto saved = acc.mark();
         sim.hi = 0;
-        if (it.payoff == 1) group(std::false_type{}, std::true_type{}, PayTag<1>{});
-        else group(std::false_type{}, std::true_type{}, PayTag<0>{});
+        if constexpr (PC == PC_TERMINAL) {
+          if (it.payoff == 1) group(std::false_type{}, std::true_type{}, PayTag<1>{});
+          else group(std::false_type{}, std::true_type{}, PayTag<0>{});
+        } else {
+          // path-dependent payoffs: one sample per step carries more state, and a
+          // FULL instantiation costs registers more than the range test costs
+          group(std::false_type{}, std::false_type{}, PayTag<-1>{});
+        }
         eager = sim.over();
         if (eager) acc.rewind(saved);
       }
       if (eager) group(std::true_type{}, std::false_type{}, PayTag<-1>{});
-    } else if constexpr (!DUMP) {
-      if (full) group(std::true_type{}, std::true_type{}, PayTag<-1>{});
-      else group(std::true_type{}, std::false_type{}, PayTag<-1>{});
     } else {
+      // other datapaths: one instantiation (a FULL one beside it raised the
+      // packed binary16 kernels from ~115 to ~165 registers and cost 9%)
       group(std::true_type{}, std::false_type{}, PayTag<-1>{});
     }
     if constexpr (EST == EST_APPROX && AP == AP_FX32 && PC == PC_TERMINAL) acc.flush_group();
