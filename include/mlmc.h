@@ -208,9 +208,10 @@ mlmc_status mlmc_level_noalloc(int level, uint64_t N, const mlmc_params *p, mlmc
 
 /* ---- batched work lists ---------------------------------------------------
  * A plan holds a device-resident work list; launching it enqueues one level
- * kernel per kernel configuration (concurrently, on forked streams) and a
- * finalize kernel, all on `stream`, with no host synchronisation and no host
- * <-> device copy.  Results stay on the device until mlmc_plan_results.
+ * kernel per kernel configuration (concurrently, on forked streams joined
+ * back to `stream`; in each, the CTA that finishes an item's last chunk sums
+ * the item's chunk partials in chunk order), with no host synchronisation and
+ * no host <-> device copy.  Results stay on the device until mlmc_plan_results.
  * Work items are simulated in order of decreasing cost per CTA.
  * Errors as mlmc_level; a plan with n_work = 0 is MLMC_EINVAL. */
 mlmc_status mlmc_plan_create(mlmc_plan **plan, const mlmc_work *work, int n_work,
