@@ -6,8 +6,8 @@
 //
 // Layout: one CTA processes one chunk of one work item; each thread simulates
 // groups of samples whose uniforms come from one Philox call per group (4
-// samples per call on level 0, 2 on level 1, one sample with 2^l / 4 calls
-// above), entirely in registers.  The approximate-Normal table of the item
+// packs per call on level 0, 2 on level 1, one pack over 2^l / 4 calls above;
+// a pack is one sample, or three with packed draws), entirely in registers.  The approximate-Normal table of the item
 // lives in shared memory.  The only global-memory traffic is the work-item
 // descriptor, the table, one Partial record per CTA, the item's sums (written
 // by the CTA that finishes its last chunk) and the optional dump.
@@ -897,7 +897,8 @@ namespace mlmc {
 template <int EST, int XP, int AP, int SCHEME, int PC, int KP>
 cudaError_t launch_one(dim3 grid, dim3 block, size_t smem, cudaStream_t st, const LaunchArgs &a, int *occ) {
   auto k = (a.dyn || occ) ? level_kernel_dyn<EST, XP, AP, SCHEME, PC, KP>
-                          : (a.dump ? level_kernel_dump<EST, XP, AP, SCHEME, PC, KP> : level_kernel<EST, XP, AP, SCHEME, PC, KP>);
+            : a.dump       ? level_kernel_dump<EST, XP, AP, SCHEME, PC, KP>
+                           : level_kernel<EST, XP, AP, SCHEME, PC, KP>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
