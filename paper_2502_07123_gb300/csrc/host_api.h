@@ -15,8 +15,6 @@
 #include "item.h"
 #include "mlmc.h"
 
-struct mlmc_plan;
-
 namespace mlmc_host {
 
 // Status-returning wrapper of a CUDA call.
@@ -168,15 +166,5 @@ double u128_to_double(uint64_t lo, uint64_t hi);
 // Plan, launch, read and release in one synchronous call on stream st.
 mlmc_status run_sync(const mlmc_work *work, int n_work, uint64_t seed, const mlmc_tuning *tuning,
                      void *const *dumps, mlmc_sums *out, cudaStream_t st);
-// Plans: create (borrowing the context arena when `transient`), launch on a
-// stream, read results, release.  plan_out_device gives the device array of
-// one mlmc::DevSums (undiscounted) per work item of the last launch;
-// plan_item_scale gives the factors the host applies to them.
-mlmc_status plan_create_transient(mlmc_plan **out, const mlmc_work *work, int n_work, uint64_t seed,
-                                  const mlmc_tuning *tuning);
-mlmc_status plan_launch_on(mlmc_plan *pl, cudaStream_t st);
-const mlmc::DevSums *plan_out_device(const mlmc_plan *pl);
-void plan_item_scale(const mlmc_plan *pl, int i, double *disc, int *unit, int *exact_int);
-void plan_release(mlmc_plan *pl);
 
 }  // namespace mlmc_host

@@ -417,29 +417,6 @@ mlmc_status run_sync(const mlmc_work *work, int n_work, uint64_t seed, const mlm
 }
 
 
-mlmc_status plan_create_transient(mlmc_plan **out, const mlmc_work *work, int n_work, uint64_t seed,
-                                  const mlmc_tuning *tuning) {
-  return plan_create_impl(out, work, n_work, seed, tuning, nullptr, &g.arena);
-}
-mlmc_status plan_launch_on(mlmc_plan *pl, cudaStream_t st) {
-  if (st != g.st) {
-    // a transient plan's work list was copied on the context stream: order after it
-    MLMC_CK(cudaEventRecord(g.arena.fork, g.st));
-    MLMC_CK(cudaStreamWaitEvent(st, g.arena.fork, 0));
-  }
-  return plan_launch_impl(pl, st);
-}
-const mlmc::DevSums *plan_out_device(const mlmc_plan *pl) { return pl->d_out; }
-void plan_item_scale(const mlmc_plan *pl, int i, double *disc, int *unit, int *exact_int) {
-  *disc = pl->disc[i];
-  *unit = pl->unit[i];
-  *exact_int = pl->exact_int[i];
-}
-void plan_release(mlmc_plan *pl) {
-  free_plan_device(pl);
-  delete pl;
-}
-
 // Median device time (ms) of `reps` launches of a plan of `work` (launch
 // shapes from the tuning table), after one untimed launch.
 mlmc_status time_plan(const mlmc_work *work, int n_work, uint64_t seed, int reps, double *ms) {
