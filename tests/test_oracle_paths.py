@@ -151,3 +151,146 @@ def test_adaptive_nested_exact_low_levels_black_scholes():
     ref = black_scholes_call(p["S0"], p["K"], p["r"], p["sigma"], p["T"])
     assert abs(res["price"] - ref) < 3 * math.sqrt(res["var"]) + eps / math.sqrt(2)
     assert res["N"][0][0] == 1 << 10 and res["N"][1][0] == 1 << 20
+
+
+# ---------------------------------------------------------------------------
+# Exact-path Asian and lookback payoffs.  These payoffs come from the workload
+# configurations, not from the paper, and have no closed form for the price
+# under Euler-Maruyama in general; each pin below is a case the mathematics
+# fixes: means that E[Z] = 0 and E[Z^2 - 1] = 0 determine, deterministic paths,
+# and the first two levels, whose expectations reduce to one-dimensional
+# integrals of the Normal density.
+# ---------------------------------------------------------------------------
+def _call_on_normal(mu, s):
+    """E[(mu + s Z)^+] for a standard Normal Z."""
+    return mu * norm.cdf(mu / s) + s * norm.pdf(mu / s)
+
+
+def _put_on_normal(k, mu, s):
+    """E[(k - (mu + s Z))^+]."""
+    return (k - mu) * norm.cdf((k - mu) / s) + s * norm.pdf((k - mu) / s)
+
+
+def _trapezoid_mean(S0, a, n):
+    """E of the trapezoidal average over n steps of a path with E[S_i] = S0 a^i."""
+    return (0.5 * S0 + sum(S0 * a**i for i in range(1, n)) + 0.5 * S0 * a**n) / n
+
+
+@pytest.mark.parametrize("scheme", [W.EULER, W.MILSTEIN])
+@pytest.mark.parametrize("level", [0, 1, 2, 3, 4])
+def test_asian_average_mean_closed_form(scheme, level):
+    """With K = 0 the Asian payoff is the trapezoidal average itself, whose mean is
+    fixed by E[S_i] = S0 (1 + r h)^i on the fine grid and S0 (1 + 2 r h)^k on the
+    coarse one (both schemes).  A wrong end weight or a dropped inner point moves
+    the mean by S0 / (2n) or more, far beyond four standard errors."""
+    p = W.params(payoff=W.ASIAN, scheme=scheme, K=0.0, sigma=0.3)
+    N = 40_000
+    _, dump = core.level(p, level, 0, N, core.FP64_EXACT, 41 + level, dump=True)
+    n, h = 2**level, p["T"] / 2**level
+    ref_f = _trapezoid_mean(p["S0"], 1 + p["r"] * h, n)
+    se = dump["pf"].std() / math.sqrt(N)
+    assert abs(dump["pf"].mean() - ref_f) < 4 * se, (dump["pf"].mean(), ref_f, se)
+    if level > 0:
+        ref_c = _trapezoid_mean(p["S0"], 1 + 2 * p["r"] * h, n // 2)
+        se = dump["pc"].std() / math.sqrt(N)
+        assert abs(dump["pc"].mean() - ref_c) < 4 * se, (dump["pc"].mean(), ref_c, se)
+    else:
+        assert np.all(dump["pc"] == 0.0)
+
+
+@pytest.mark.parametrize("level", [0, 1, 3, 5])
+@pytest.mark.parametrize("r", [0.05, -0.05])
+def test_deterministic_paths_asian_and_lookback(level, r):
+    """sigma = 0: S_i = S0 (1 + r h)^i exactly, so the average, the minimum (S0 when
+    r > 0, S_N when r < 0) and both payoffs have closed forms on each grid."""
+    n, T, S0 = 2**level, 1.0, 100.0
+    h = T / n
+    a, ac = 1 + r * h, 1 + 2 * r * h
+    for K in (95.0, 105.0):
+        p = W.params(payoff=W.ASIAN, sigma=0.0, r=r, K=K)
+        _, dump = core.level(p, level, 0, 8, core.FP64_EXACT, 3, dump=True)
+        ref_f = max(_trapezoid_mean(S0, a, n) - K, 0.0)
+        assert np.allclose(dump["pf"], ref_f, rtol=1e-12, atol=1e-12)
+        if level > 0:
+            assert np.allclose(dump["pc"], max(_trapezoid_mean(S0, ac, n // 2) - K, 0.0), rtol=1e-12, atol=1e-12)
+    p = W.params(payoff=W.LOOKBACK, sigma=0.0, r=r)
+    _, dump = core.level(p, level, 0, 8, core.FP64_EXACT, 3, dump=True)
+    ref_f = S0 * (a**n - 1) if r > 0 else 0.0
+    assert np.allclose(dump["pf"], ref_f, rtol=1e-12, atol=1e-12)
+    if level > 0:
+        ref_c = S0 * (ac ** (n // 2) - 1) if r > 0 else 0.0
+        assert np.allclose(dump["pc"], ref_c, rtol=1e-12, atol=1e-12)
+
+
+def test_lookback_level0_is_call_struck_at_S0():
+    """One step: S_1 - min(S0, S_1) = max(S_1 - S0, 0) sample by sample, with mean
+    S0 E[(r T + sigma sqrt(T) Z)^+] (Euler-Maruyama)."""
+    p = W.params(payoff=W.LOOKBACK, sigma=0.3)
+    N = 100_000
+    _, dump = core.level(p, 0, 0, N, core.FP64_EXACT, 5, dump=True)
+    assert np.array_equal(dump["pf"], np.maximum(dump["sf"] - p["S0"], 0.0))
+    ref = p["S0"] * _call_on_normal(p["r"] * p["T"], p["sigma"] * math.sqrt(p["T"]))
+    se = dump["pf"].std() / math.sqrt(N)
+    assert abs(dump["pf"].mean() - ref) < 4 * se
+
+
+def test_level1_asian_and_lookback_by_quadrature():
+    """Level 1 (two fine steps, one coarse step), Euler-Maruyama: with
+    a_i = 1 + r h + sigma sqrt(h) Z_i the fine payoffs are functions of (a_1, a_2)
+    that are linear in a_2 for fixed a_1, so their means are one-dimensional
+    integrals over Z_1 of closed-form Normal expectations; the coarse step has
+    a_c = 1 + r T + sigma sqrt(T) Z'."""
+    from scipy.integrate import quad
+    S0, K, r, sig, T = 100.0, 100.0, 0.05, 0.3, 1.0
+    h = T / 2
+    mu, s = 1 + r * h, sig * math.sqrt(h)
+    N = 100_000
+
+    def over_z1(f):
+        return quad(lambda z: f(mu + s * z) * norm.pdf(z), -9, 9, epsabs=1e-12, epsrel=1e-12, limit=400)[0]
+
+    # lookback: S0 E[a1 a2 - min(1, a1, a1 a2)]; E[min(m, a1 a2)] = m - a1 E[(m / a1 - a2)^+]
+    def lb_inner(a1):
+        m = min(1.0, a1)
+        return m - a1 * _put_on_normal(m / a1, mu, s)
+    lb_f = S0 * (mu * mu - over_z1(lb_inner))
+    lb_c = S0 * _call_on_normal(r * T, sig * math.sqrt(T))
+    # Asian: average (S0/2 + S1 + S2/2) / 2 - K = A + B a2 with B = S0 a1 / 4
+    def as_inner(a1):
+        A, B = S0 * (0.5 + a1) / 2 - K, S0 * a1 / 4
+        return B * _call_on_normal(A / B + mu, s)
+    as_f = over_z1(as_inner)
+    as_c = 0.5 * S0 * _call_on_normal(2 + r * T - 2 * K / S0, sig * math.sqrt(T))
+    for payoff, rf, rc in ((W.LOOKBACK, lb_f, lb_c), (W.ASIAN, as_f, as_c)):
+        p = W.params(payoff=payoff, sigma=sig, K=K)
+        _, dump = core.level(p, 1, 0, N, core.FP64_EXACT, 9 + payoff, dump=True)
+        for col, ref in (("pf", rf), ("pc", rc)):
+            x = dump[col]
+            se = x.std() / math.sqrt(N)
+            assert abs(x.mean() - ref) < 4 * se, (payoff, col, x.mean(), ref, se)
+        y = dump["pf"] - dump["pc"]
+        assert abs(y.mean() - (rf - rc)) < 4 * y.std() / math.sqrt(N)
+
+
+def test_lookback_fine_level_discrete_monitoring():
+    """Level 6 against the continuously monitored floating-strike lookback
+    (Goldman-Sosin-Gatto) with the Broadie-Glasserman-Kou shift of the minimum,
+    m_discrete ~ m_continuous exp(beta sigma sqrt(h)), beta = -zeta(1/2)/sqrt(2 pi):
+    E[S_N - min] ~ S0 (1 + r h)^N - E[m_cont] exp(beta sigma sqrt(h)).  The tolerance is
+    four standard errors plus 8h for the O(h) remainder of the shift and the Euler
+    weak error; the minimum over the coarse grid instead of the fine one would be
+    off by about 0.5 here, over twice the tolerance."""
+    S0, r, sig, T, lev = 100.0, 0.05, 0.2, 1.0, 6
+    a1 = (r + sig * sig / 2) * math.sqrt(T) / sig
+    a2 = a1 - sig * math.sqrt(T)
+    a3 = (-r + sig * sig / 2) * math.sqrt(T) / sig
+    price = (S0 * norm.cdf(a1) - S0 * sig * sig / (2 * r) * norm.cdf(-a1)
+             - S0 * math.exp(-r * T) * (norm.cdf(a2) - sig * sig / (2 * r) * norm.cdf(-a3)))
+    e_min = S0 * math.exp(r * T) - math.exp(r * T) * price     # E[min over [0, T]]
+    beta = 0.5825971579390106
+    h, n = T / 2**lev, 2**lev
+    ref = S0 * (1 + r * h) ** n - e_min * math.exp(beta * sig * math.sqrt(h))
+    N = 100_000
+    _, dump = core.level(W.params(payoff=W.LOOKBACK), lev, 0, N, core.FP64_EXACT, 3, dump=True)
+    se = dump["pf"].std() / math.sqrt(N)
+    assert abs(dump["pf"].mean() - ref) < 4 * se + 8 * h, (dump["pf"].mean(), ref, se)
