@@ -53,7 +53,9 @@ ALU_PEAK_TOPS = 152 * 4 * 32 * 2.070e9 / 1e12
 DOMINANT_TRAFFIC = {(15, 51213208): 138240}
 
 
-def build_items(m, rank=0):
+def build_items(m, rank=0, formats=None):
+    """The nested workload's work items (per-level formats: the default schedule,
+    or `formats`, a list indexed by level)."""
     cfg = W.nested_config()
     items, meta = [], []
     cache = {}
@@ -61,8 +63,8 @@ def build_items(m, rank=0):
         p = it["params"]
         key = p["payoff"]
         if key not in cache:
-            cache[key] = m.make_params(p, d=cfg["d"], method=cfg["method"],
-                                       formats=[W.default_format(p, lev) for lev in range(9)],
+            fm = formats[:9] if formats else [W.default_format(p, lev) for lev in range(9)]
+            cache[key] = m.make_params(p, d=cfg["d"], method=cfg["method"], formats=fm,
                                        request=it["request"], rng_pack=cfg["rng_pack"])
         items.append(dict(params=cache[key], level=it["level"], variant=it["variant"],
                           first_sample=rank * it["N"], N=it["N"]))
@@ -200,8 +202,9 @@ def main():
     ap.add_argument("--no-optimiser", action="store_true")
     ap.add_argument("--sweep", action="store_true",
                     help="also run the level-kernel throughput sweep (Milstein; payoffs x variants x levels)")
-    ap.add_argument("--no-autotune", action="store_true",
-                    help="keep the default launch shape (128 threads, 256 path-steps per thread)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time launch shapes per kernel class first and use the fastest (the default is the "
+                         "library's fixed shape table, so that a profile of the same command sees the same launches)")
     ap.add_argument("--serving", action="store_true",
                     help="also run the batched (256 options) and serving (Poisson arrivals) workloads")
     args = ap.parse_args()
@@ -223,11 +226,11 @@ def main():
 
     items, meta, cfg = build_items(m, rank)
     tuning = None
-    shape = "default 128 threads x 256 path-steps per thread"
+    shape = "library default shape table"
     if args.threads or args.steps_per_thread:
         tuning = dict(threads=args.threads, steps_per_thread=args.steps_per_thread)
         shape = "fixed %d threads x %d path-steps per thread" % (args.threads, args.steps_per_thread)
-    elif not args.no_autotune:
+    elif args.autotune:
         # launch shape per kernel class, timed on this GPU (outside the timed region)
         shapes = m.mlmc_autotune(items, cfg["seed"], reps=3)
         shape = "autotuned per kernel class: " + ", ".join("%dx%d" % t for t in sorted(set(shapes)))
@@ -332,12 +335,14 @@ def main():
                 "d2h_bytes_per_step": info["d2h_bytes"], "ms": statistics.median(e2e_ms)},
         "roofline": roofline,
     }
+    formats_opt = None
+    if rank == 0 and world == 1 and not args.no_optimiser:
+        out["bitwidth_optimiser"], formats_opt = optimiser_run(m, torch)
+        out["nested_step_optimised_widths"] = nested_step_with_formats(m, torch, formats_opt, flush, stream)
     if rank == 0 and not args.no_tte:
-        out["time_to_eps"] = time_to_eps(m, torch)
+        out["time_to_eps"] = time_to_eps(m, torch, formats_opt=formats_opt)
     if rank == 0 and world == 1 and args.sweep:
         out["sweep"] = sweep_run(m, torch)
-    if rank == 0 and world == 1 and not args.no_optimiser:
-        out["bitwidth_optimiser"] = optimiser_run(m, torch)
     if rank == 0 and world == 1 and not args.no_serving_sample:
         # bounded serving sample: 200 requests drawn as the serving workload at
         # 1000 req/s, accuracies in the coarser half [1e-3, 1e-2] of its range
@@ -494,14 +499,15 @@ def sweep_run(m, torch, levels=(2, 6, 10), paths=1 << 22, sigmas=(0.1, 0.2, 0.4)
     return {"scheme": "milstein", "rows": rows}
 
 
-def optimiser_run(m, torch, levels=range(9), n_sens=1_000_000, n_check=400_000):
+def optimiser_run(m, torch, levels=range(11), n_sens=1_000_000, n_check=400_000):
     """Offline bit-width optimisation of the test case (Sec. 4-6): error-model
     statistics from 10^6 exact paths per level on the GPU, optimal widths and table
     size (paper's FPGA cost model, C_RNG = 1e4), then the GPU fixed-point correction
-    estimator run with those widths to check the model (Var <= V'_corr)."""
+    estimator run with those widths to check the model (Var <= V'_corr).  Returns
+    the report and the optimised formats of every level."""
     mse = [0.0, 0.0] + [m.icdf_mse(d) for d in range(2, 15)]
     p = W.params()
-    rows = []
+    rows, formats = [], []
     sens_ms = None
     for lev in levels:
         P = m.make_params(p)
@@ -509,26 +515,64 @@ def optimiser_run(m, torch, levels=range(9), n_sens=1_000_000, n_check=400_000):
         t0 = time.perf_counter()
         s = m.mlmc_sensitivities(lev, n_sens, P, 77)
         dt = time.perf_counter() - t0
-        if lev == max(levels):
+        if lev == 8:
             sens_ms = dt * 1e3
         o = m.mlmc_optimise_level(lev, s, lut_mse=mse, lut_max_bits=14)
-        lut = o["lut_bits"]
+        formats.append(o["format"])
+        # lut_bits 0: no table of at most 14 bits meets the model's bound; use 14
+        lut = o["lut_bits"] or 14
         fmts = [W.default_format(p, k) for k in range(lev)] + [o["format"]]
         res = m.mlmc_level(lev, n_check, m.make_params(p, d=lut, method=1, formats=fmts), W.CORR_FIXED, 5)
         mean = res["sum"] / n_check
         var = res["sum2"] / n_check - mean * mean
         v_corr = (math.sqrt(o["v_corr"]) + s["B"][0] * math.sqrt(mse[lut])) ** 2
         v_ind = o["v_indep"] + s["A"][0] * mse[lut]
-        rows.append({"level": lev, "d": o["d"], "e": o["e"], "lut_bits": lut,
+        rows.append({"level": lev, "d": o["d"], "e": o["e"], "lut_bits": o["lut_bits"], "lut_bits_run": lut,
                      "level_cost_ratio": o["level_cost_ratio"], "V": s["var"], "v_indep_ext": v_ind,
                      "v_corr_ext": v_corr, "var_corrections_measured": var, "bound_holds": var <= v_corr,
                      "saturations": res["saturations"]})
-    top = max(levels)
     return {"paths_per_level": n_sens, "cost_model": "FPGA eq. cost_sq, C_RNG = 1e4 per step",
             "variables": ["Z", "con1", "con2", "mul1", "sum1", "mul2", "S"],
-            "sensitivity_ms_level_%d" % top: sens_ms,
-            "sensitivity_path_steps_per_s": n_sens * (1 << top) / (sens_ms * 1e-3) if sens_ms else None,
-            "levels": rows}
+            "sensitivity_ms_level_8": sens_ms,
+            "sensitivity_path_steps_per_s": n_sens * (1 << 8) / (sens_ms * 1e-3) if sens_ms else None,
+            "levels": rows}, formats
+
+
+def nested_step_with_formats(m, torch, formats, flush, stream, reps=10):
+    """The nested workload's step with other fixed-point formats (the optimiser's,
+    table d = 10 kept): device time per step and the per-level variance of the
+    corrections, beside the same figures with the default formats."""
+    out = {}
+    for name, fm in (("default_formats", None), ("optimised_formats", formats)):
+        items, meta, cfg = build_items(m, formats=fm)
+        plan = m.Plan(items, cfg["seed"])
+        for _ in range(3):
+            plan.launch(stream)
+        st = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+        en = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+        for k in range(reps):
+            flush.zero_()
+            st[k].record(stream)
+            plan.launch(stream)
+            en[k].record(stream)
+        torch.cuda.synchronize()
+        res = plan.results()
+        plan.close()
+        ms = statistics.median(a.elapsed_time(b) for a, b in zip(st, en))
+        var_corr = {}
+        sat = 0
+        for it, r in zip(meta, res):
+            sat += r["saturations"]
+            if it["variant"] == W.CORR_FIXED and it["params"]["payoff"] == W.EURO:
+                mean = r["sum"] / r["n"]
+                var_corr[it["level"]] = r["sum2"] / r["n"] - mean * mean
+        out[name] = {"ms_per_step": ms, "path_steps_per_s": plan_steps(items) / (ms * 1e-3),
+                     "var_corrections_euro": [var_corr[k] for k in sorted(var_corr)], "saturations": sat}
+    return out
+
+
+def plan_steps(items):
+    return sum(it["N"] << it["level"] for it in items)
 
 
 def _engine_solve(eng, P, eps, mode, seed):
@@ -540,45 +584,67 @@ def _engine_solve(eng, P, eps, mode, seed):
             return r
 
 
-def time_to_eps(m, torch, eps=1e-3, seeds=tuple(range(1, 12))):
-    """Wall time of mlmc_estimate at RMS error eps: nested fixed point vs plain FP32 (European call)."""
+def time_to_eps(m, torch, eps=1e-3, seeds=tuple(range(1, 12)), formats_opt=None):
+    """Wall time of mlmc_estimate at RMS error eps (European call, median of the
+    seeds): plain FP32 MLMC against the nested estimator (Sec. 2.2) with its
+    approximate path in fixed point, binary16 and bfloat16, each with the Method-1
+    and the Method-3 table (Sec. 3.1, 3.3); the paper's nested estimator samples
+    every level, the exact-low modes compute the approximate terms of levels 0-1
+    by enumeration instead.  With formats_opt, the fixed-point runs again with the
+    bit-width optimiser's formats.  Accuracy: RMS over the seeds of
+    (price - Black-Scholes) / eps."""
     p = W.params()
-    P = m.make_params(p, d=10, method=1, formats=[W.default_format(p, lev) for lev in range(11)], rng_pack=1)
-    out = {"eps": eps}
-    for name, mode in (("plain_fp32", m.MODE_PLAIN_FP32), ("nested_fixed", m.MODE_NESTED_FIXED),
-                       ("nested_fixed_exact_low", m.MODE_NESTED_FIXED_EXACT_LOW),
-                       ("nested_fp16_exact_low", m.MODE_NESTED_FP16_EXACT_LOW)):
-        m.mlmc_estimate(1e-2, P, mode, 99, 10)   # warm tables and contexts
+    bs = _bs_price(p)
+    fm = [W.default_format(p, lev) for lev in range(11)]
+
+    def P(method=1, formats=fm):
+        return m.make_params(p, d=10, method=method, formats=formats, rng_pack=1)
+
+    configs = [("plain_fp32", m.MODE_PLAIN_FP32, P())]
+    for tag, method in (("m1", 1), ("m3", 3)):
+        configs += [("nested_fixed_" + tag, m.MODE_NESTED_FIXED, P(method)),
+                    ("nested_fp16_" + tag, m.MODE_NESTED_FP16, P(method)),
+                    ("nested_bf16_" + tag, m.MODE_NESTED_BF16, P(method)),
+                    ("nested_fixed_exact_low_" + tag, m.MODE_NESTED_FIXED_EXACT_LOW, P(method)),
+                    ("nested_fp16_exact_low_" + tag, m.MODE_NESTED_FP16_EXACT_LOW, P(method))]
+    if formats_opt:
+        configs += [("nested_fixed_m1_optimised_widths", m.MODE_NESTED_FIXED, P(1, formats_opt)),
+                    ("nested_fixed_exact_low_m1_optimised_widths", m.MODE_NESTED_FIXED_EXACT_LOW, P(1, formats_opt))]
+    out = {"eps": eps, "payoff": "european call", "seeds": len(seeds)}
+    for name, mode, PP in configs:
+        m.mlmc_estimate(1e-2, PP, mode, 99, 10)   # warm tables and contexts
         ts, prices = [], []
-        for s in seeds:
+        for s_ in seeds:
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            r = m.mlmc_estimate(eps, P, mode, s, 10)
+            r = m.mlmc_estimate(eps, PP, mode, s_, 10)
             ts.append(time.perf_counter() - t0)
             prices.append(r["price"])
-        out[name] = {"s_median": statistics.median(ts), "prices": prices, "L": r["L"], "N": r["N"]}
+        out[name] = {"s_median": statistics.median(ts), "prices": prices, "L": r["L"], "N": r["N"],
+                     "rms_err_over_eps": math.sqrt(sum((x - bs) ** 2 for x in prices) / len(prices)) / eps}
+    for name, _, _ in configs[1:]:
+        out["speedup_%s_vs_plain_fp32" % name] = out["plain_fp32"]["s_median"] / out[name]["s_median"]
     # the same adaptive algorithm driven on the device: one request through a
     # (created and warmed) engine, four iterations per CUDA-graph launch,
     # instead of host-driven plans
     for name, mode in (("plain_fp32_graph", m.MODE_PLAIN_FP32),
-                       ("nested_fixed_exact_low_graph", m.MODE_NESTED_FIXED_EXACT_LOW)):
+                       ("nested_fixed_exact_low_m1_graph", m.MODE_NESTED_FIXED_EXACT_LOW)):
+        PP = P()
         eng = m.Engine(max_slots=1, max_level=10, iters_per_launch=4)
-        _engine_solve(eng, P, 1e-2, mode, 99)
+        _engine_solve(eng, PP, 1e-2, mode, 99)
         ts, prices = [], []
-        for s in seeds:
+        for s_ in seeds:
             torch.cuda.synchronize()
             l0 = eng.stats()["launches"]
             t0 = time.perf_counter()
-            r = _engine_solve(eng, P, eps, mode, s)
+            r = _engine_solve(eng, PP, eps, mode, s_)
             ts.append(time.perf_counter() - t0)
             prices.append(r["price"])
         out[name] = {"s_median": statistics.median(ts), "prices": prices, "L": r["L"],
                      "graph_launches": eng.stats()["launches"] - l0}
         eng.close()
-    for name in ("nested_fixed", "nested_fixed_exact_low", "nested_fp16_exact_low", "nested_fixed_exact_low_graph"):
-        out["speedup_%s_vs_plain_fp32" % name] = out["plain_fp32"]["s_median"] / out[name]["s_median"]
-    out["speedup_nested_fixed_exact_low_graph_vs_plain_fp32_graph"] = (
-        out["plain_fp32_graph"]["s_median"] / out["nested_fixed_exact_low_graph"]["s_median"])
+    out["speedup_nested_fixed_exact_low_m1_graph_vs_plain_fp32_graph"] = (
+        out["plain_fp32_graph"]["s_median"] / out["nested_fixed_exact_low_m1_graph"]["s_median"])
     return out
 
 

@@ -188,21 +188,25 @@ mlmc_status mlmc_level_dump(int level, uint64_t N, const mlmc_params *p, mlmc_va
  * memory is owned by another allocator (a framework's caching pool, or memory
  * reserved up front), a latency-critical loop in which a cudaMalloc would
  * synchronise the device, or code whose memory budget has been fixed ahead.
- * It computes exactly what mlmc_level computes (same kernels, same chunking)
- * and calls no cudaMalloc, cudaFree or other allocating routine, on the host
- * side of CUDA or the device.  Its scratch (per-CTA partial sums, the work
- * item, the tables and the result record) is one file-scope device array of
- * about 0.9 MiB that every GPU which loads the library keeps until exit.
- * Limits: at most 16384 CTAs (128 threads each) per call -- larger sample
- * counts return MLMC_EINVAL; icdf_bits <= 14; icdf_method 1 or 3 (Method 2's
- * tables are built on the host and need allocation: MLMC_EINVAL).  All work
- * is enqueued on `stream`
- * (a cudaStream_t, NULL = legacy default stream) and the call returns after
- * synchronising it; seconds = 0.  The first call on a device looks up the
- * array's device address, so make that first call before any stream capture.
- * Every call overwrites the whole array; calls are serialised by the library
- * lock and each returns after its stream has finished, so they cannot
- * overlap on the GPU.  Errors as mlmc_level. */
+ * It computes exactly what mlmc_level computes: the work item is built and
+ * chunked by the same code (same kernels, chunking and packed-draw layout,
+ * hence the same sums), and it calls no cudaMalloc, cudaFree or other
+ * allocating routine.  Its scratch (per-CTA partial sums, the work item, the
+ * tables and the result record) is one file-scope device array of about
+ * 0.9 MiB that every GPU which loads the library keeps until exit; its device
+ * address is looked up on every call.  CUDA loads a kernel's code on its first
+ * launch on a device (lazy module loading), which takes device memory once:
+ * a caller that must see no change at all makes one call of each kind of
+ * estimator up front.  The first call for each table size d also reads the
+ * FP64 table back to the host, which synchronises the stream midway.
+ * Limits: at most 16384 CTAs per call -- larger sample counts return
+ * MLMC_EINVAL; icdf_bits <= 14; icdf_method 1 or 3 (Method 2's tables are
+ * built on the host and need allocation: MLMC_EINVAL).  All work is enqueued
+ * on `stream` (a cudaStream_t, NULL = legacy default stream) and the call
+ * returns after synchronising it; seconds = 0.  Every call writes every part
+ * of the array that it reads, and calls are serialised by the library lock
+ * and each returns after its stream has finished, so they cannot overlap on
+ * the GPU.  Errors as mlmc_level. */
 mlmc_status mlmc_level_noalloc(int level, uint64_t N, const mlmc_params *p, mlmc_variant v,
                                uint64_t seed, uint64_t first_sample, mlmc_sums *out, void *stream);
 
@@ -474,6 +478,19 @@ mlmc_status mlmc_icdf_method2(int d, int n, double *x, uint32_t *perm, int *iter
  * addition (fp32 / fp16 / bf16); rep 0 gives the FP64 sums.  mlmc_icdf_table
  * with method 2 is this with n = 2. */
 mlmc_status mlmc_icdf_method2_table(int d, int n, int rep, int fZ, double *out);
+
+/* Mean square error E[(Z - Z~)^2] of the approximate Normal with d table bits
+ * (Sec. 3.4, eq. mse_dyadic), from the library's FP64 Method-1 table Z_k (the
+ * mean of Phi^{-1} over interval k, built on the GPU):
+ *   method 1: 1 - 2^(1-d) sum_{k < 2^(d-1)} Z_k^2;
+ *   method 3: the Method-1 value plus 2^(1-d) sum_k (a_c + b_c k - Z_k)^2 with
+ *             the FP64 least-squares lines of the dyadic classes;
+ *   method 2: the Method-1 value plus 2^-d sum_{j < 2^d} (Z_pi(j) - Z~_j)^2 for
+ *             the coupled uniform drawn in interval pi(j) (fields n, 0 means 2).
+ * fields must be 0 for methods 1 and 3.  *out (host) receives the MSE.
+ * MLMC_EINVAL for d outside [2, 14] or a bad method / field count;
+ * MLMC_ECUDA without a GPU. */
+mlmc_status mlmc_icdf_mse(int method, int d, int fields, double *out);
 
 /* Philox4x32-10 words computed on the GPU for n counters (for parity testing):
  * ctr is a host array of 4n words, out a host array of 4n words. */

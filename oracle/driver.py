@@ -167,20 +167,37 @@ def mlmc(eps, p, seed, mode=PLAIN_FP64, cost=None, fmt_of_level=None, d=10, meth
     return dict(price=price, var=var, L=L, N=N)
 
 
-def price_on_schedule(p, seed, mode, N, fmt_of_level=None, d=10, method=1, request=0):
-    """Price from fixed per-(level, estimator) sample counts N[l][k] (samples [0, N))."""
+def price_on_schedule(p, seed, mode, N, fmt_of_level=None, d=10, method=1, request=0, pack=0, dump=False):
+    """Price and variance from fixed per-(level, estimator) sample counts N[l][k]
+    (samples [0, N) of each term; entries beyond the mode's estimators are
+    ignored).  Approximate-only terms read packed draws when pack is set.  In the
+    modes with exact low levels, the approximate term of such a level is the mean
+    over every combination of table cells (N[l][0] = 2^(d 2^l)) and adds no
+    variance.  With dump, also returns every term's per-sample records."""
     plan = estimator_plan(mode)
+    exact = exact_levels(mode, d)
     disc = math.exp(-p["r"] * p["T"])
     price, var = 0.0, 0.0
-    sums = []
+    sums, dumps = [], []
     for lev, row in enumerate(N):
-        srow = []
-        for k, n in enumerate(row):
+        srow, drow = [], []
+        for k, n in enumerate(row[:len(plan)]):
+            v = plan[k]
+            is_exact = k == 0 and lev in exact
+            approx_only = v in (core.FIXED_APPROX, core.FP16_APPROX, core.BF16_APPROX)
             fmt = fmt_of_level(lev) if fmt_of_level else None
-            s, _ = core.level(p, lev, 0, n, plan[k], seed, request=request, d=d, method=method, fmt=fmt)
+            s, dm = core.level(p, lev, 0, n, v, seed, request=request, d=d, method=method, fmt=fmt,
+                               dump=dump, pack=pack if approx_only and not is_exact else 0,
+                               enumerate=1 if is_exact else 0)
             m = disc * s["sum"] / n
             price += m
-            var += max(disc * disc * s["sum2"] / n - m * m, 0.0) / n
+            if not is_exact:
+                var += max(disc * disc * s["sum2"] / n - m * m, 0.0) / n
             srow.append(s)
+            drow.append(dm)
         sums.append(srow)
-    return dict(price=price, var=var, sums=sums)
+        dumps.append(drow)
+    out = dict(price=price, var=var, sums=sums)
+    if dump:
+        out["dumps"] = dumps
+    return out

@@ -75,8 +75,7 @@ mlmc_status m1_table(int d, double **dev, const std::vector<double> **host) {
 
 // Method 3 (Sec. 3.3): least-squares line a + b k through (k, Z_k) on each
 // dyadic index class {0,1}, {2,3}, {4..7}, ..., {2^(d-2) .. 2^(d-1)-1}.
-void m3_fit(const std::vector<double> &Z, int d, M3Coef &c) {
-  std::memset(&c, 0, sizeof c);
+void m3_fit_fp64(const double *Z, int d, double *a, double *b) {
   for (int cls = 0; cls < d - 1; ++cls) {
     const int lo = cls == 0 ? 0 : (1 << cls);
     const int hi = cls == 0 ? 1 : (1 << (cls + 1)) - 1;
@@ -90,12 +89,20 @@ void m3_fit(const std::vector<double> &Z, int d, M3Coef &c) {
       sxx += (k - kbar) * (k - kbar);
       sxy += (k - kbar) * (Z[k] - zbar);
     }
-    const double b = sxy / sxx;
-    const double a = zbar - b * kbar;
-    c.a[cls] = (float)a;
-    c.b[cls] = (float)b;
-    c.A[cls] = (int64_t)std::floor(std::ldexp(a, M3_FRAC) + 0.5);
-    c.B[cls] = (int64_t)std::floor(std::ldexp(b, M3_FRAC) + 0.5);
+    b[cls] = sxy / sxx;
+    a[cls] = zbar - b[cls] * kbar;
+  }
+}
+
+void m3_fit(const double *Z, int d, M3Coef &c) {
+  std::memset(&c, 0, sizeof c);
+  double a[16], b[16];
+  m3_fit_fp64(Z, d, a, b);
+  for (int cls = 0; cls < d - 1; ++cls) {
+    c.a[cls] = (float)a[cls];
+    c.b[cls] = (float)b[cls];
+    c.A[cls] = (int64_t)std::floor(std::ldexp(a[cls], M3_FRAC) + 0.5);
+    c.B[cls] = (int64_t)std::floor(std::ldexp(b[cls], M3_FRAC) + 0.5);
   }
 }
 
@@ -325,13 +332,35 @@ mlmc_status get_table(int method, int d, int rep, int fZ, const void **out, bool
     }
   } else {
     M3Coef c;
-    m3_fit(*zh, d, c);
+    m3_fit(zh->data(), d, c);
     MLMC_CK(cudaMalloc(&p, sizeof(M3Coef)));
     MLMC_CK(cudaMemcpy(p, &c, sizeof(M3Coef), cudaMemcpyHostToDevice));
   }
   g.tables[key] = p;
   *out = p;
   return MLMC_OK;
+}
+
+// Tables of the device context (cached per process, allocated on first use).
+struct CtxTables final : TableSource {
+  int num_sms() const override { return g.num_sms; }
+  mlmc_status zmax_fixed(int method, int d, int fZ, int fields, int64_t *out) override {
+    double *z64 = nullptr;
+    const std::vector<double> *zh = nullptr;
+    mlmc_status s = m1_table(d, &z64, &zh);
+    if (s != MLMC_OK) return s;
+    *out = table_zmax_fixed(zh->data(), d, method, fZ, fields);
+    return MLMC_OK;
+  }
+  mlmc_status device_table(int method, int d, int rep, int fZ, int fields, const void **out) override {
+    return get_table(method, d, rep, fZ, out, true, fields);
+  }
+  mlmc_status m2_perm(int d, int fields, const uint16_t **out) override { return m2_perm_device(d, fields, out); }
+};
+
+TableSource &ctx_tables() {
+  static CtxTables t;
+  return t;
 }
 
 cudaStream_t ctx_stream() { return g.st; }
@@ -365,6 +394,55 @@ mlmc_status mlmc_icdf_table(int method, int d, int rep, int fZ, double *out) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(g.st);
   cudaFree(dv);
   return e == cudaSuccess ? MLMC_OK : MLMC_ECUDA;
+}
+
+mlmc_status mlmc_icdf_mse(int method, int d, int fields, double *out) {
+  MLMC_API_LOCK();
+  if (!out || method < 1 || method > 3 || d < 2 || d > 14) return MLMC_EINVAL;
+  if (method != 2 && fields != 0) return MLMC_EINVAL;
+  if (method == 2 && fields == 0) fields = 2;
+  if (method == 2 && !m2_shape_ok(d, fields)) return MLMC_EINVAL;
+  mlmc_status s = ensure_ctx();
+  if (s != MLMC_OK) return s;
+  double *z64 = nullptr;
+  const std::vector<double> *zh = nullptr;
+  if ((s = m1_table(d, &z64, &zh)) != MLMC_OK) return s;
+  const double *Z = zh->data();
+  const int half = 1 << (d - 1);
+  // Method 1: Z~ is the mean of Phi^{-1} over its interval, so the cross term
+  // cancels and E[(Z - Z~)^2] = E[Z^2] - E[Z~^2] = 1 - 2^(1-d) sum_k Z_k^2
+  double s2 = 0.0;
+  for (int k = 0; k < half; ++k) s2 += Z[k] * Z[k];
+  const double mse1 = 1.0 - std::ldexp(s2, 1 - d);
+  if (method == 1) {
+    *out = mse1;
+    return MLMC_OK;
+  }
+  // any other value v_j on interval j adds its distance from the interval mean
+  // (eq. mse_dyadic): MSE = MSE_1 + 2^-d sum_j (Z_j - v_j)^2 over all 2^d intervals
+  double extra = 0.0;
+  if (method == 3) {
+    double a[16], b[16];
+    m3_fit_fp64(Z, d, a, b);
+    for (int k = 0; k < half; ++k) {
+      const int cls = k < 2 ? 0 : 31 - __builtin_clz((unsigned)k);
+      const double dv = a[cls] + b[cls] * (double)k - Z[k];
+      extra += dv * dv;
+    }
+    *out = mse1 + std::ldexp(extra, 1 - d);   // both halves, by symmetry
+    return MLMC_OK;
+  }
+  // Method 2: U is drawn in interval pi(j), whose mean is the d-bit Method-1 value Z_pi(j)
+  const M2Table *t;
+  if ((s = m2_build(d, fields, &t)) != MLMC_OK) return s;
+  for (int j = 0; j < 2 * half; ++j) {
+    const int q = (int)t->pi[j];
+    const double zq = q < half ? Z[q] : -Z[2 * half - 1 - q];
+    const double dv = zq - t->values[j];
+    extra += dv * dv;
+  }
+  *out = mse1 + std::ldexp(extra, -d);
+  return MLMC_OK;
 }
 
 mlmc_status mlmc_icdf_method2_table(int d, int n, int rep, int fZ, double *out) {

@@ -1,6 +1,6 @@
 // Device building blocks of the level kernels: Philox4x32-10, the exact and
 // approximate Normal maps of Sec. 3, fixed-point re-quantisation (Sec. 4.1)
-// and compensated FP32 accumulation.
+// and 128-bit integer accumulation.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -121,19 +121,6 @@ template <> struct HalfOps2<__nv_bfloat16> {
   static __device__ __forceinline__ T splat(__nv_bfloat16 a) { return __bfloat162bfloat162(a); }
   static __device__ __forceinline__ __nv_bfloat16 lo(T a) { return __low2bfloat16(a); }
   static __device__ __forceinline__ __nv_bfloat16 hi(T a) { return __high2bfloat16(a); }
-};
-
-// Kahan-compensated FP32 sum (error bounded by ~2 ulp of the sum of |terms|).
-struct KahanF {
-  float s, c;
-  __device__ __forceinline__ void init() { s = 0.0f; c = 0.0f; }
-  __device__ __forceinline__ void add(float x) {
-    const float y = __fsub_rn(x, c);
-    const float t = __fadd_rn(s, y);
-    c = __fsub_rn(__fsub_rn(t, s), y);
-    s = t;
-  }
-  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
 // 128-bit unsigned accumulation of squares of int64 values.

@@ -665,7 +665,7 @@ mlmc_status admit(mlmc_engine *e, int sl, size_t idx, cudaStream_t st) {
       BuiltItem b;
       double disc;
       int unit, ei;
-      mlmc_status s = build_item(w, 0, nullptr, b, disc, unit, ei);
+      mlmc_status s = build_item(w, 0, nullptr, b, disc, unit, ei, ctx_tables());
       int th, sp, gi = -1;
       if (s == MLMC_OK) {
         tuning_for(b.family, b.scheme, b.pc, l, &th, &sp);

@@ -78,8 +78,11 @@ int ctx_num_sms();
 // ---------------------------------------------------------------------------
 // Method-1 table of index width d (Sec. 3.1): device FP64 copy and host copy.
 mlmc_status m1_table(int d, double **dev, const std::vector<double> **host);
-// Method 3 (Sec. 3.3): least-squares line per dyadic index class.
-void m3_fit(const std::vector<double> &Z, int d, mlmc::M3Coef &c);
+// Method 3 (Sec. 3.3): least-squares line a + b k per dyadic index class of
+// the lower-half Method-1 table Z (2^(d-1) values), in FP64 (a, b: d-1 each).
+void m3_fit_fp64(const double *Z, int d, double *a, double *b);
+// The same lines in the representations the kernels read.
+void m3_fit(const double *Z, int d, mlmc::M3Coef &c);
 uint16_t half_bits(double x);
 uint16_t bf16_bits(double x);
 // Method 2 (Sec. 3.2), n fields of d/n bits.
@@ -120,7 +123,7 @@ bool format_ok_gpu(const mlmc_format &F, bool milstein, int d);
 // for paths of nsteps fine steps; also decides ff.lazy.
 bool fast_fixed(const int e[7], const int f[7], int64_t con1, int64_t con1c, int64_t con2, int64_t con3,
                 int64_t zmax, bool milstein, int64_t nsteps, mlmc::FastFixed &ff, bool &s64);
-int64_t table_zmax_fixed(const std::vector<double> &Z, int d, int method, int fZ, int fields);
+int64_t table_zmax_fixed(const double *Z, int d, int method, int fZ, int fields);
 int family_of(int variant);
 int cost_kind_of(int variant);
 // Relative cost per fine path-step of an estimator kind (mlmc_cost_model).
@@ -142,14 +145,35 @@ struct BuiltItem {
   double cost_step;     // model cost per fine path-step
   double chunk_cost;    // model cost of one chunk (set by chunk_built)
 };
+// Where build_item takes the approximate-Normal tables from and how many SMs
+// the item is chunked for: the context's cached tables (ctx_tables(), which
+// allocate device memory on first use) or mlmc_level_noalloc's fixed scratch.
+struct TableSource {
+  virtual ~TableSource() {}
+  virtual int num_sms() const = 0;
+  // largest |value| of the (method, d, fields) table in Z's fixed-point format fZ
+  virtual mlmc_status zmax_fixed(int method, int d, int fZ, int fields, int64_t *out) = 0;
+  // device table the level kernels read (full signed table for methods 1 and 2,
+  // the class lines for method 3)
+  virtual mlmc_status device_table(int method, int d, int rep, int fZ, int fields, const void **out) = 0;
+  // device copy of Method 2's interval ranks
+  virtual mlmc_status m2_perm(int d, int fields, const uint16_t **out) = 0;
+};
+TableSource &ctx_tables();
+// Packed draws of an item of N samples run one sample per thread when the
+// packs do not fill one wave of resident threads on num_sms SMs.
+bool lane_split(uint64_t N, int num_sms);
+// The sample range [first, first + N) of a level keeps every Philox word
+// index s 2^l + i and group index below 2^62.
+bool sample_range_ok(int level, uint64_t first, uint64_t N);
 mlmc_status build_item(const mlmc_work &w, int out_index, void *dump, BuiltItem &b, double &disc, int &unit,
-                       int &exact_int);
+                       int &exact_int, TableSource &src);
 // build_item through the per-process cache of built constants.
 mlmc_status build_item_cached(const mlmc_work &w, int out_index, void *dump, BuiltItem &b, double &disc, int &unit,
                               int &exact_int);
 // Empty that cache (its items point to one device's tables).
 void item_cache_clear();
-mlmc_status chunk_built(BuiltItem &b, int threads, int spt);
+mlmc_status chunk_built(BuiltItem &b, int threads, int spt, int num_sms);
 void make_round_keys(uint64_t seed, mlmc::RoundKeys &rk);
 // Launch one level kernel of a family (or, with occ, query the resident CTAs
 // per SM of its device-scheduled kernel).

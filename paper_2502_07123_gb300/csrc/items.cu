@@ -291,7 +291,7 @@ bool fast_fixed(const int e[7], const int f[7], int64_t con1, int64_t con1c, int
 }
 
 // Largest |table value| in Z's fixed-point format, as the kernels evaluate it.
-int64_t table_zmax_fixed(const std::vector<double> &Z, int d, int method, int fZ, int fields) {
+int64_t table_zmax_fixed(const double *Z, int d, int method, int fZ, int fields) {
   int64_t zmax = 0;
   if (method == 2) {
     const M2Table *t;
@@ -301,7 +301,8 @@ int64_t table_zmax_fixed(const std::vector<double> &Z, int d, int method, int fZ
     return zmax;
   }
   if (method == 1) {
-    for (double v : Z) zmax = std::max<int64_t>(zmax, std::llabs((int64_t)std::floor(std::ldexp(v, fZ) + 0.5)));
+    for (int k = 0; k < (1 << (d - 1)); ++k)
+      zmax = std::max<int64_t>(zmax, std::llabs((int64_t)std::floor(std::ldexp(Z[k], fZ) + 0.5)));
     return zmax;
   }
   M3Coef c;
@@ -318,11 +319,11 @@ int64_t table_zmax_fixed(const std::vector<double> &Z, int d, int method, int fZ
 
 
 // Split an item's sample groups into chunks of `threads` x groups_per_thread.
-mlmc_status chunk_built(BuiltItem &b, int threads, int spt) {
+mlmc_status chunk_built(BuiltItem &b, int threads, int spt, int num_sms) {
   ItemDesc &it = b.it;
   uint32_t gpt = 1;
   const uint64_t spg = steps_per_group(it.level);
-  const uint64_t nch = chunk_count(it.g1 - it.g0, spg, b.kp, threads, spt, g.num_sms, &gpt);
+  const uint64_t nch = chunk_count(it.g1 - it.g0, spg, b.kp, threads, spt, num_sms, &gpt);
   if (nch > 0x7fffffffULL) return MLMC_EINVAL;
   it.groups_per_thread = gpt;
   it.n_chunks = (uint32_t)nch;
@@ -332,20 +333,26 @@ mlmc_status chunk_built(BuiltItem &b, int threads, int spt) {
 
 // Packed draws of an item with fewer packs than one wave of resident threads
 // run one sample per thread: latency rather than throughput bounds such items.
-bool lane_split(uint64_t N) {
-  const uint64_t wave = 6ULL * 128ULL * (uint64_t)std::max(1, g.num_sms);
+bool lane_split(uint64_t N, int num_sms) {
+  const uint64_t wave = 6ULL * 128ULL * (uint64_t)std::max(1, num_sms);
   return N > 0 && (N + 2) / 3 < wave;
 }
 
+// N is bounded before the subtraction, so that the test cannot wrap.
+bool sample_range_ok(int level, uint64_t first, uint64_t N) {
+  const uint64_t words = 1ULL << (60 - level);
+  return N <= (1ULL << 58) && N <= words && first <= words - N;
+}
+
 mlmc_status build_item(const mlmc_work &w, int out_index, void *dump, BuiltItem &b, double &disc, int &unit,
-                       int &exact_int) {
+                       int &exact_int, TableSource &src) {
   const mlmc_params *p = w.params;
   if (!params_ok(p)) return MLMC_EINVAL;
   if (w.level < 0 || w.level > 20 || w.variant < 0 || w.variant > 7) return MLMC_EINVAL;
   if (w.stream < -1 || w.stream > 255) return MLMC_EINVAL;
   const int lev = w.level;
   // word index s 2^l + i and the group index must stay below 2^62
-  if (w.N > (1ULL << 58) || w.first_sample > (1ULL << (60 - lev)) - w.N) return MLMC_EINVAL;
+  if (!sample_range_ok(lev, w.first_sample, w.N)) return MLMC_EINVAL;
   ItemDesc &it = b.it;
   std::memset(&it, 0, sizeof it);
   const int v = w.variant;
@@ -376,7 +383,7 @@ mlmc_status build_item(const mlmc_work &w, int out_index, void *dump, BuiltItem 
     it.enumerate = 1;
   }
   if (KP == 0) return MLMC_EINVAL;
-  if (KP == 3 && lev >= 2 && lane_split(w.N)) {
+  if (KP == 3 && lev >= 2 && lane_split(w.N, src.num_sms())) {
     // few samples: one sample per thread (three times the threads), the same
     // packed draws (sample s reads lane s mod 3 of pack s / 3)
     KP = 1;
@@ -447,17 +454,21 @@ mlmc_status build_item(const mlmc_work &w, int out_index, void *dump, BuiltItem 
       fx.fZ2 = 2 * f[F_Z];
       fx.fS = f[F_S];
       // the table must fit Z's format
-      double *z64;
-      const std::vector<double> *zh;
-      if ((s = m1_table(p->icdf_bits, &z64, &zh)) != MLMC_OK) return s;
-      const int64_t zmax = table_zmax_fixed(*zh, p->icdf_bits, p->icdf_method, fZ, m2_fields_of(p));
+      int64_t zmax = 0;
+      if ((s = src.zmax_fixed(p->icdf_method, p->icdf_bits, fZ, m2_fields_of(p), &zmax)) != MLMC_OK) return s;
       if ((double)zmax > std::ldexp(1.0, e[F_Z] + fZ) - 1.0) return MLMC_EOVERFLOW;
       unit = f[F_S] + (p->payoff == MLMC_ASIAN ? lev + 1 : 0);
       bool s64 = false;
       fast = fast_fixed(e, f, con1, con1c, con2, con3, zmax, p->scheme == MLMC_MILSTEIN, (int64_t)1 << lev, it.ff,
                         s64);
       fast64 = s64;
-      if (fast && !s64) {
+      // the 32-bit datapath keeps (Z~, fine sum1) pairs in shared memory (2^d x 8
+      // bytes: d <= 12) and rounds products by one funnel shift (shifts below 32)
+      if (fast && !fast64 &&
+          (p->icdf_bits > 12 || it.ff.rs1 > 31 || it.ff.rs2 > 31 ||
+           (p->scheme == MLMC_MILSTEIN && it.ff.rs3 > 31)))
+        fast64 = true;
+      if (fast && !fast64) {
         // the 32-bit datapath sums a group's squared terminal payoff differences in
         // 64 bits: |Y| <= max(lim_S, 2^f_S), so spc samples need spc ymax^2 < 2^64
         const double ymax = std::max(std::ldexp(1.0, e[F_S] + f[F_S]), std::ldexp(1.0, f[F_S]));
@@ -473,7 +484,7 @@ mlmc_status build_item(const mlmc_work &w, int out_index, void *dump, BuiltItem 
       unit = 24;
     }
     const void *tab = nullptr;
-    mlmc_status s = get_table(p->icdf_method, p->icdf_bits, rep, fZ, &tab, true, m2_fields_of(p));
+    mlmc_status s = src.device_table(p->icdf_method, p->icdf_bits, rep, fZ, m2_fields_of(p), &tab);
     if (s != MLMC_OK) return s;
     it.ztab = tab;
     b.smem = p->icdf_method != 3 ? (size_t)(1 << p->icdf_bits) * (fixed ? 4 : 2) : sizeof(M3Coef);
@@ -481,7 +492,7 @@ mlmc_status build_item(const mlmc_work &w, int out_index, void *dump, BuiltItem 
     if (p->icdf_method == 2 && !exact_int) {
       // Method 2 coupling: the correction's exact path reads the interval ranks
       const uint16_t *perm = nullptr;
-      if ((s = m2_perm_device(p->icdf_bits, m2_fields_of(p), &perm)) != MLMC_OK) return s;
+      if ((s = src.m2_perm(p->icdf_bits, m2_fields_of(p), &perm)) != MLMC_OK) return s;
       it.perm = perm;
       b.smem += sizeof(uint16_t) << p->icdf_bits;
     }
@@ -504,6 +515,11 @@ mlmc_status build_item(const mlmc_work &w, int out_index, void *dump, BuiltItem 
       default: return MLMC_EINVAL;
     }
   }
+  if (b.family == 8 || b.family == 10 || b.family == 15) {
+    // the 32-bit datapath's shared-memory table: (Z~_j, fine sum1_j) pairs for
+    // every method (Method 3's lines are evaluated into it), then Method 2's ranks
+    b.smem = ((size_t)8 << p->icdf_bits) + (it.perm ? (sizeof(uint16_t) << p->icdf_bits) : 0);
+  }
   b.scheme = p->scheme;
   b.pc = p->payoff == MLMC_ASIAN ? PC_ASIAN : (p->payoff == MLMC_LOOKBACK ? PC_LOOKBACK : PC_TERMINAL);
   return MLMC_OK;
@@ -516,7 +532,7 @@ mlmc_status build_item_cached(const mlmc_work &w, int out_index, void *dump, Bui
                               int &exact_int) {
   const mlmc_params *p = w.params;
   if (w.flags != 0 || !params_ok(p) || w.level < 0 || w.level > 20)
-    return build_item(w, out_index, dump, b, disc, unit, exact_int);
+    return build_item(w, out_index, dump, b, disc, unit, exact_int, ctx_tables());
   std::string key;
   key.reserve(96);
   auto put = [&](const void *x, size_t n) { key.append((const char *)x, n); };
@@ -529,18 +545,18 @@ mlmc_status build_item_cached(const mlmc_work &w, int out_index, void *dump, Bui
   if (has_fmt == 1) put(&p->formats[w.level], sizeof(mlmc_format));
   put(&w.level, sizeof(int32_t) * 2);     // level, variant
   put(&w.stream, sizeof(int32_t));
-  const int split = lane_split(w.N) ? 1 : 0;   // the packed-draw layout depends on N
+  const int split = lane_split(w.N, g.num_sms) ? 1 : 0;   // the packed-draw layout depends on N
   put(&split, sizeof split);
   auto f = g_item_cache.find(key);
   if (f == g_item_cache.end()) {
-    mlmc_status s = build_item(w, out_index, dump, b, disc, unit, exact_int);
+    mlmc_status s = build_item(w, out_index, dump, b, disc, unit, exact_int, ctx_tables());
     if (s != MLMC_OK) return s;
     if (g_item_cache.size() > 8192) g_item_cache.clear();
     g_item_cache.emplace(key, CachedItem{b, disc, unit, exact_int});
     return MLMC_OK;
   }
   const int lev = w.level;
-  if (w.N > (1ULL << 58) || w.first_sample > (1ULL << (60 - lev)) - w.N) return MLMC_EINVAL;
+  if (!sample_range_ok(lev, w.first_sample, w.N)) return MLMC_EINVAL;
   b = f->second.b;
   disc = f->second.disc;
   unit = f->second.unit;

@@ -59,11 +59,37 @@ template <int EST, int AP, int SCHEME, int PC, bool DYN = false> struct MinCtas 
       : ((EST == EST_APPROX && AP == AP_FX32 && PC == PC_ASIAN) ? 4 : 1);
 };
 
-// Bytes per entry of the shared-memory approximate-Normal table of a datapath.
+// Bytes per entry of the shared-memory approximate-Normal table of a datapath:
+// the 32-bit fast fixed-point datapath keeps (Z~_j, sum1 of a fine step) pairs.
 template <int AP>
 struct TabBytes {
-  static constexpr size_t value = (AP == AP_FIXED || AP == AP_FX32 || AP == AP_FX64) ? 4 : 2;
+  static constexpr size_t value = AP == AP_FX32 ? 8 : ((AP == AP_FIXED || AP == AP_FX64) ? 4 : 2);
 };
+
+// sum1 of one fast fixed-point step of Algorithm 1 from its Normal increment z:
+// mul1 = rd(con2 z), [Milstein: mul3 = rd(con3 (z^2 - m))], sum1 = rd(con1 + mul1
+// [+ mul3]).  c1r: con1 (fine) or con1_c (coarse) with sum1's rounding half unit;
+// m: 1 (fine) or 2 (coarse) in units 2^-2fZ.  F32: the host proved every
+// rounding shift below 32, so a product's rounded value is one funnel shift of
+// its two words.
+template <bool MIL, bool F32>
+__device__ __forceinline__ int32_t ff_sum1(const FastFixed &ff, int32_t z, int32_t c1r, int64_t m) {
+  int32_t mul1;
+  const int64_t p1 = (int64_t)ff.con2 * z + ff.radd1;
+  if constexpr (F32) mul1 = (int32_t)__funnelshift_r((uint32_t)p1, (uint32_t)((uint64_t)p1 >> 32), ff.rs1);
+  else mul1 = (int32_t)(p1 >> ff.rs1);
+  int32_t acc = c1r + mul1 * ff.mulF1;
+  if constexpr (MIL) {
+    // |Z~^2 - m| < 2^31 on this datapath (host-checked): one 32 x 32 product
+    const int32_t zz = z * z - (int32_t)m;
+    const int64_t p3 = (int64_t)ff.con3 * zz + ff.radd3;
+    int32_t mul3;
+    if constexpr (F32) mul3 = (int32_t)__funnelshift_r((uint32_t)p3, (uint32_t)((uint64_t)p3 >> 32), ff.rs3);
+    else mul3 = (int32_t)(p3 >> ff.rs3);
+    acc += mul3 * ff.mulF1;
+  }
+  return acc >> ff.rs_sum1;
+}
 
 // KP > 1 (approximate-only estimators): KP samples advance in lockstep, lane L
 // reading bits [32 - d(L+1), 32 - dL) of the shared word (packed draws).
@@ -99,6 +125,8 @@ struct LevelSim {
 
   // ---- per-item constants (registers) ----
   int level, nsteps, payoff, d, dshift, method;
+  // FX32: byte offset of lane l's table entry = rotr(word, rot[l]) & off_mask
+  uint32_t rot[KP], off_mask;
   const uint16_t *perm_s;  // method 2 coupling of the exact path (shared memory), or nullptr
   uint32_t low_mask;
   X c1, c2, c1c, c3, S0, K;
@@ -149,6 +177,12 @@ struct LevelSim {
     }
     unit_scale = it.unit_scale;
     smem_tab = tab;
+    if constexpr (AP == AP_FX32) {
+      // lane l's field, bits [32 - d(l+1), 32 - d l) of the word, lands at bits [3, 3 + d)
+#pragma unroll
+      for (int l = 0; l < KP; ++l) rot[l] = (uint32_t)(32 - it.d * (l + 1) - 3) & 31u;
+      off_mask = ((1u << it.d) - 1u) << 3;
+    }
     perm_s = nullptr;
     low_mask = (1u << dshift) - 1u;
     if constexpr (EST == EST_CORR) {
@@ -204,19 +238,12 @@ struct LevelSim {
   }
 
   // ---- fast fixed-point Algorithm-1 step (same values as fx_step while S stays in range) ----
+  // The S update of a step whose sum1 is known: mul2 = rd(S sum1), S = rd(S + mul2).
   template <bool EAGER>
-  __device__ __forceinline__ AS ff_step(AS s, int32_t z, int32_t c1r, int64_t m, SatT &satb) {
-    const int32_t mul1 = (int32_t)(((int64_t)ff.con2 * z + ff.radd1) >> ff.rs1);
-    int32_t acc = c1r + mul1 * ff.mulF1;
-    if constexpr (MIL) {
-      // |Z~^2 - m| < 2^31 on this datapath (host-checked): one 32 x 32 product
-      const int32_t zz = z * z - (int32_t)m;
-      const int32_t mul3 = (int32_t)(((int64_t)ff.con3 * zz + ff.radd3) >> ff.rs3);
-      acc += mul3 * ff.mulF1;
-    }
-    const int32_t sum1 = acc >> ff.rs_sum1;
+  __device__ __forceinline__ AS ff_apply(AS s, int32_t sum1, SatT &satb) {
     if constexpr (AP == AP_FX32) {
-      const int32_t mul2 = (int32_t)(((int64_t)s * sum1 + ff.radd2) >> ff.rs2);
+      const int64_t p2 = (int64_t)s * sum1 + ff.radd2;
+      const int32_t mul2 = (int32_t)__funnelshift_r((uint32_t)p2, (uint32_t)((uint64_t)p2 >> 32), ff.rs2);
       s = (int32_t)((uint32_t)s + (uint32_t)mul2 * (uint32_t)ff.mulS);
     } else {
       const int32_t mul2 = (int32_t)((int64_t)((uint64_t)s * (uint64_t)(int64_t)sum1 + (uint64_t)ff.radd2) >> ff.rs2);
@@ -232,6 +259,15 @@ struct LevelSim {
     if constexpr (AP == AP_FX32) satb |= (uint32_t)(c ^ s);
     else satb |= (c != s);
     return c;
+  }
+  template <bool EAGER>
+  __device__ __forceinline__ AS ff_step(AS s, int32_t z, int32_t c1r, int64_t m, SatT &satb) {
+    return ff_apply<EAGER>(s, ff_sum1<MIL, AP == AP_FX32>(ff, z, c1r, m), satb);
+  }
+  // FX32: (Z~, sum1 of a fine step) of lane l of word w, from the shared-memory pairs
+  __device__ __forceinline__ int2 fx32_entry(uint32_t w, int l) const {
+    const uint32_t off = __funnelshift_r(w, w, rot[l]) & off_mask;
+    return *(const int2 *)((const unsigned char *)smem_tab + off);
   }
 
   // ---- half-precision step (one rounding per operation) ----
@@ -368,6 +404,25 @@ struct LevelSim {
           hzprev[2] = z2;
         }
       }
+    } else if constexpr (AP == AP_FX32) {
+      // the fine step's sum1 comes with Z~ from the table; the coarse step forms
+      // its own from Z~_2k + Z~_2k+1
+#pragma unroll
+      for (int l = 0; l < KP; ++l) {
+        const int2 e = fx32_entry(J, l);
+        if constexpr (PC == PC_ASIAN) { if (i > 0) aaccF[l] += aS[l]; }
+        aS[l] = ff_apply<EAGER>(aS[l], e.y, satb[l]);
+        if constexpr (PC == PC_LOOKBACK) aminF[l] = aS[l] < aminF[l] ? aS[l] : aminF[l];
+        if constexpr (COARSE) {
+          if (odd) {
+            if constexpr (PC == PC_ASIAN) { if (i > 1) aaccC[l] += aSc[l]; }
+            aSc[l] = ff_step<EAGER>(aSc[l], azprev[l] + e.x, ff.con1cr, ff.mcoarse, satb[l]);
+            if constexpr (PC == PC_LOOKBACK) aminC[l] = aSc[l] < aminC[l] ? aSc[l] : aminC[l];
+          } else {
+            azprev[l] = e.x;
+          }
+        }
+      }
     } else if constexpr (HAS_APPROX) {
 #pragma unroll
       for (int l = 0; l < KP; ++l) {
@@ -415,7 +470,8 @@ struct LevelSim {
       const X dd = x - K;
       return dd > X(0) ? dd : X(0);
     } else if constexpr (PC == PC_ASIAN) {
-      const X avg = (acc + X(0.5) * x) * (X(1) / X(steps));
+      // one explicit multiply-add: every instantiation rounds the average alike
+      const X avg = fma(X(0.5), x, acc) * (X(1) / X(steps));
       const X dd = avg - K;
       return dd > X(0) ? dd : X(0);
     } else {
@@ -466,18 +522,20 @@ struct LevelSim {
 
   // Finish the sample: payoffs, sample value, accumulation and optional dump
   // (EAGER false: a LAZY pack that stayed in range, so no saturation).
-  template <bool EAGER = true, int PAY = -1, class Acc>
+  // LV: 0 on level 0 (no coarse path), 1 on levels >= 1, -1 not known at compile time.
+  template <bool EAGER = true, int PAY = -1, int LV = -1, class Acc>
   __device__ __forceinline__ void finish(Acc &acc, int l, bool valid, mlmc_sample_rec *dump) {
     X pf = X(0), pc = X(0);
     int64_t qf = 0, qc = 0, afS = 0, acS = 0;
     uint32_t lsat = 0;
+    const bool coarse = LV >= 0 ? LV == 1 : level > 0;
     if constexpr (HAS_EXACT) {
       pf = exact_payoff(S, accF, minF, nsteps);
-      if (level > 0) pc = exact_payoff(Sc, accC, minC, nsteps >> 1);
+      if (coarse) pc = exact_payoff(Sc, accC, minC, nsteps >> 1);
     }
     if constexpr (FIXED) {
       qf = fixed_payoff<PAY>(aS[l], aaccF[l], aminF[l], nsteps, false);
-      if (level > 0) qc = fixed_payoff<PAY>(aSc[l], aaccC[l], aminC[l], nsteps >> 1, true);
+      if (coarse) qc = fixed_payoff<PAY>(aSc[l], aaccC[l], aminC[l], nsteps >> 1, true);
       afS = aS[l];
       acS = aSc[l];
       if constexpr (FAST) lsat = (EAGER && satb[l]) ? 1u : 0u;
@@ -486,7 +544,7 @@ struct LevelSim {
     if constexpr (HALF) {
       if constexpr (HAS_APPROX) {
         qf = half_payoff(lane_S(l), haccF[l], hminF[l], nsteps);
-        if (level > 0) qc = half_payoff(lane_Sc(l), haccC[l], hminC[l], nsteps >> 1);
+        if (coarse) qc = half_payoff(lane_Sc(l), haccC[l], hminC[l], nsteps >> 1);
       }
     }
     double ydump;
@@ -540,18 +598,25 @@ struct LevelSim {
   }
 };
 
+// Samples of an FP32 real-valued estimator summed in a float pair before each
+// FP64 flush (see ThreadAcc::add_real).
+constexpr int REAL_FLUSH_SAMPLES = 8;
+
 // Per-thread accumulator
 template <int EST, int XP>
 struct ThreadAcc {
   // integer estimators
   int64_t isum;
   uint64_t q_lo, q_hi;
-  // FP32 estimators (Kahan), FP64 estimators
-  KahanF ks, kq;
+  // real-valued estimators: FP64 sums (FP64 exact path: every sample; FP32
+  // paths and corrections: the float pairs below, flushed)
   double ds, dq;
+  // float pairs (s + c) of sum Y and sum Y^2 since the last flush
+  float fs, fc, fs2, fc2;
   uint32_t nsat;
   __device__ __forceinline__ void init() {
-    isum = 0; q_lo = 0; q_hi = 0; gq = 0; ks.init(); kq.init(); ds = 0.0; dq = 0.0; nsat = 0;
+    isum = 0; q_lo = 0; q_hi = 0; gq = 0; ds = 0.0; dq = 0.0; nsat = 0;
+    fs = 0.0f; fc = 0.0f; fs2 = 0.0f; fc2 = 0.0f;
   }
   __device__ __forceinline__ void add_int(int64_t y) {
     isum += y;
@@ -578,14 +643,45 @@ struct ThreadAcc {
   __device__ __forceinline__ void rewind(const Mark &m) {
     isum = m.isum; q_lo = m.q_lo; q_hi = m.q_hi; gq = 0;
   }
+  // s + y = t + e exactly (Knuth's TwoSum, six FP32 operations); e goes to c.
+  static __device__ __forceinline__ void two_sum_into(float &s, float &c, float y) {
+    const float t = __fadd_rn(s, y);
+    const float z = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(y, z));
+    s = t;
+    c = __fadd_rn(c, e);
+  }
+  // A real sample.  FP64 samples are added in FP64.  An FP32 sample y enters
+  // the float pair (fs, fc) by TwoSum, so fs + fc misses sum y only by the
+  // roundings of the additions into fc; y^2 = p + pe exactly (p = fl(y y),
+  // pe = fma(y, y, -p)) enters (fs2, fc2) the same way.  With at most K =
+  // REAL_FLUSH_SAMPLES samples between flushes (|fc| <= k u sum |y| after k of
+  // them, |fc2| <= (k+1) u sum y^2, u = 2^-24) those roundings total at most
+  // u^2 K(K+1)/2 sum |y| and 2 u^2 (K(K+1)/2 + K) sum y^2: below 1.3e-13 of
+  // sum |y| and 3.2e-13 of sum y^2.  A flush adds each float, exactly widened,
+  // into the FP64 sums, so the thread's sums are within about 3.5e-13 of the
+  // exact sums of its samples, at one FP64 operation per sample.
   template <class T>
   __device__ __forceinline__ void add_real(T y) {
     if constexpr (XP == XP_F64 && EST == EST_EXACT) {
       ds += (double)y;
       dq = fma((double)y, (double)y, dq);
     } else {
-      ks.add((float)y);
-      kq.add(__fmul_rn((float)y, (float)y));
+      const float yf = (float)y;
+      two_sum_into(fs, fc, yf);
+      const float p = __fmul_rn(yf, yf);
+      const float pe = __fmaf_rn(yf, yf, -p);
+      two_sum_into(fs2, fc2, p);
+      fc2 = __fadd_rn(fc2, pe);
+    }
+  }
+  __device__ __forceinline__ void flush_real() {
+    if constexpr (!(XP == XP_F64 && EST == EST_EXACT) && EST != EST_APPROX) {
+      ds += (double)fs;
+      ds += (double)fc;
+      dq += (double)fs2;
+      dq += (double)fc2;
+      fs = 0.0f; fc = 0.0f; fs2 = 0.0f; fc2 = 0.0f;
     }
   }
 };
@@ -598,9 +694,7 @@ template <int EST, int XP>
 __device__ __forceinline__ void block_reduce_write(ThreadAcc<EST, XP> &a, Partial *out) {
   int64_t isum = a.isum;
   uint64_t lo = a.q_lo, hi = a.q_hi;
-  double ds, dq;
-  if constexpr (XP == XP_F64 && EST == EST_EXACT) { ds = a.ds; dq = a.dq; }
-  else { ds = a.ks.value(); dq = a.kq.value(); }
+  double ds = a.ds, dq = a.dq;
   uint64_t ns = a.nsat;
 #pragma unroll
   for (int m = 16; m >= 1; m >>= 1) {
@@ -673,6 +767,11 @@ __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDes
   const bool lazy = Sim::LAZY && !DUMP && it.ff.lazy;
   // A group is one Philox call's worth of packs (4 on level 0, 2 on level 1) or,
   // from level 2, one pack over 2^l / 4 calls; a pack holds KP samples.
+  // Real-valued estimators flush their float pairs every `flush_groups` groups
+  // (at most REAL_FLUSH_SAMPLES samples).
+  constexpr bool REAL = EST != EST_APPROX && !(XP == XP_F64 && EST == EST_EXACT);
+  const uint32_t flush_groups = REAL ? (uint32_t)REAL_FLUSH_SAMPLES / (uint32_t)samples_per_group(lev, KP) : 0u;
+  uint32_t since_flush = 0;
   for (uint32_t r = threadIdx.x; r < ng; r += blockDim.x) {
     const uint64_t g = gbeg + r;
     const bool full = g >= gf0 && g < gf1;
@@ -708,7 +807,7 @@ __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDes
         for (int l = 0; l < KP; ++l) {
           const uint64_t s = KP == 1 ? g : P * KP + l;
           const bool valid = FULL || full || (s >= first && s < last);
-          sim.template finish<E, PAY>(acc, l, valid, DUMP && valid ? dump + (s - first) : nullptr);
+          sim.template finish<E, PAY, 1>(acc, l, valid, DUMP && valid ? dump + (s - first) : nullptr);
         }
       } else {
         uint64_t gw = g;
@@ -734,7 +833,7 @@ __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDes
             for (int l = 0; l < KP; ++l) {
               const int k = u * KP + l;
               const bool valid = FULL || (k >= klo && k < khi);
-              sim.template finish<E, PAY>(acc, l, valid, DUMP && valid ? dump + (s0 + k - first) : nullptr);
+              sim.template finish<E, PAY, 1>(acc, l, valid, DUMP && valid ? dump + (s0 + k - first) : nullptr);
             }
           }
         } else {
@@ -746,7 +845,7 @@ __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDes
             for (int l = 0; l < KP; ++l) {
               const int k = u * KP + l;
               const bool valid = FULL || (k >= klo && k < khi);
-              sim.template finish<E, PAY>(acc, l, valid, DUMP && valid ? dump + (s0 + k - first) : nullptr);
+              sim.template finish<E, PAY, 0>(acc, l, valid, DUMP && valid ? dump + (s0 + k - first) : nullptr);
             }
           }
         }
@@ -779,7 +878,14 @@ __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDes
       group(std::true_type{}, std::false_type{}, PayTag<-1>{});
     }
     if constexpr (EST == EST_APPROX && AP == AP_FX32 && PC == PC_TERMINAL) acc.flush_group();
+    if constexpr (REAL) {
+      if (++since_flush == flush_groups) {
+        acc.flush_real();
+        since_flush = 0;
+      }
+    }
   }
+  acc.flush_real();
   block_reduce_write<EST, XP>(acc, args.partials + gc);
   if (args.counters && threadIdx.x < 32) {
     // the CTA that completes the item's last chunk sums all its partials, in
@@ -824,7 +930,35 @@ __device__ __forceinline__ void run_chunk(const LaunchArgs &args, const ItemDesc
   const ItemDesc &it = items[s_item];
   // stage the approximate-Normal table in shared memory (every thread has
   // finished the previous chunk: block_reduce_write ends with a barrier)
-  if constexpr (AP != AP_NONE) {
+  if constexpr (AP == AP_FX32) {
+    // (Z~_j, sum1 of a fine step from Z~_j) for every index j: Method 1 and 2
+    // values from the item's table, Method 3 values from its class lines (the
+    // arithmetic of LevelSim::fixed_z); sum1 by the datapath's own step code.
+    // The table depends on the item's constants as well, so it is staged for
+    // every chunk.
+    const int n = 1 << it.d;
+    int2 *dst = (int2 *)smem_tab;
+    const M3Coef *m3 = (const M3Coef *)it.ztab;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      int32_t z;
+      if (it.method != 3) {
+        z = ((const int32_t *)it.ztab)[k];
+      } else {
+        const ApproxIndex ai = approx_index((uint32_t)k << (32 - it.d), it.d);
+        const int c = m3_class(ai.idx);
+        const int64_t t = m3->A[c] + m3->B[c] * (int64_t)ai.idx;
+        const int sh = M3_FRAC - it.fx.fZ2 / 2;
+        const int32_t v = (int32_t)((t + ((int64_t)1 << (sh - 1))) >> sh);
+        z = ai.neg ? -v : v;
+      }
+      dst[k] = make_int2(z, ff_sum1<SCHEME == 1, true>(it.ff, z, it.ff.con1r, it.ff.mfine));
+    }
+    if (it.perm) {   // after the table: the method-2 interval ranks
+      uint16_t *pd = (uint16_t *)(smem_tab + (size_t)n * TabBytes<AP>::value);
+      for (int k = threadIdx.x; k < n; k += blockDim.x) pd[k] = it.perm[k];
+    }
+    __syncthreads();
+  } else if constexpr (AP != AP_NONE) {
     if (!staged || it.ztab != *staged) {
       if (staged) *staged = it.ztab;
       if (it.method != 3) {
@@ -851,7 +985,8 @@ __device__ __forceinline__ void run_chunk(const LaunchArgs &args, const ItemDesc
   const int item = s_item;
   if (ALLOW_DUMP && it.dump) {
     if constexpr (ALLOW_DUMP) chunk_body<EST, XP, AP, SCHEME, PC, KP, 2, true, DYN>(args, it, item, gc, smem_tab);
-  } else if constexpr (AP == AP_NONE) {
+  } else if constexpr (AP == AP_NONE || AP == AP_FX32) {
+    // no method choice: exact paths, and the FX32 table that holds every method's values
     chunk_body<EST, XP, AP, SCHEME, PC, KP, 0, false, DYN>(args, it, item, gc, smem_tab);
   } else {
     if (it.method == 3) chunk_body<EST, XP, AP, SCHEME, PC, KP, 1, false, DYN>(args, it, item, gc, smem_tab);

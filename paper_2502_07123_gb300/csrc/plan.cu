@@ -170,7 +170,7 @@ mlmc_status plan_create_impl(mlmc_plan **out, const mlmc_work *work, int n_work,
     if (o_threads) th = o_threads;
     if (o_spt) sp = o_spt;
     item_threads[i] = th;
-    s = chunk_built(built[i], th, sp);
+    s = chunk_built(built[i], th, sp, g.num_sms);
     if (s != MLMC_OK) { delete pl; return s; }
     pl->N[i] = work[i].N;
     pl->path_steps += work[i].N << work[i].level;
@@ -563,7 +563,7 @@ mlmc_status mlmc_autotune(const mlmc_work *work, int n_work, uint64_t seed, int 
   for (int i = 0; i < n_work; ++i) {
     double disc;
     int unit, ei;
-    if ((s = build_item(work[i], i, nullptr, built[i], disc, unit, ei)) != MLMC_OK) return s;
+    if ((s = build_item(work[i], i, nullptr, built[i], disc, unit, ei, ctx_tables())) != MLMC_OK) return s;
     const Key k = std::make_tuple(built[i].family, built[i].scheme, built[i].pc, level_class(work[i].level));
     cls[k].push_back(i);
     work_of[k] += std::ldexp((double)work[i].N, work[i].level) * built[i].cost_step;
@@ -590,7 +590,7 @@ mlmc_status mlmc_autotune(const mlmc_work *work, int n_work, uint64_t seed, int 
           std::vector<uint32_t> sig{(uint32_t)th};
           for (int i : ix) {
             BuiltItem b = built[i];
-            if ((s = chunk_built(b, th, sp)) != MLMC_OK) return s;
+            if ((s = chunk_built(b, th, sp, g.num_sms)) != MLMC_OK) return s;
             sig.push_back(b.it.groups_per_thread);
           }
           if (std::find(seen.begin(), seen.end(), sig) != seen.end()) continue;

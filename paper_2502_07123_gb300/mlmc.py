@@ -153,6 +153,7 @@ def load():
         "mlmc_icdf_method2_table": (st, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_double)]),
         "mlmc_default_format": (st, [P(Params), ctypes.c_int, P(Format)]),
         "mlmc_icdf_table": (st, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_double)]),
+        "mlmc_icdf_mse": (st, [ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_double)]),
         "mlmc_philox": (st, [P(ctypes.c_uint32), ctypes.c_uint64, ctypes.c_uint64, P(ctypes.c_uint32)]),
         "mlmc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "mlmc_version": (ctypes.c_char_p, []),
@@ -544,15 +545,12 @@ def mlmc_icdf_method2_table(d, n, rep, fZ=0):
     return np.frombuffer(out, dtype=np.float64).copy()
 
 
-def icdf_mse(d, method=1):
-    """Mean square error E[(Z - Z~)^2] of the approximate Normal with d table bits,
-    from the library's FP64 table: Z~ is the conditional mean of Z on each cell
-    (method 1), so E[(Z - Z~)^2] = 1 - E[Z~^2] = 1 - 2^(1-d) sum_k Z_k^2; for
-    method 3 the cross term does not vanish and this returns None."""
-    if method != 1:
-        return None
-    z = mlmc_icdf_table(1, d, 0)
-    return 1.0 - float(np.sum(z * z)) * 2.0 ** (1 - d)
+def icdf_mse(d, method=1, fields=0):
+    """Mean square error E[(Z - Z~)^2] of the approximate Normal with d table bits
+    (mlmc_icdf_mse)."""
+    out = ctypes.c_double()
+    _check(load().mlmc_icdf_mse(int(method), int(d), int(fields), ctypes.byref(out)), "mlmc_icdf_mse")
+    return out.value
 
 
 def mlmc_philox(ctr, seed):

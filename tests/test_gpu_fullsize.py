@@ -1,7 +1,9 @@
 """Full-size parity of the nested workload in the launch configuration the
 benchmark times (one plan over all 36 work items): exact integer sums of every
-approximate item equal the oracle's; correction sums agree within the FP32 path
-bound; sampled samples of each item agree one by one."""
+approximate item equal the oracle's; every sample of each correction item
+agrees with the oracle's within the FP32 path bound and the plan's correction
+sums are the FP64 sums of those samples; sampled samples of the approximate
+items agree one by one."""
 import math
 
 import numpy as np
@@ -35,7 +37,7 @@ def test_nested_workload_full_size(m):
     res2 = plan.results()
     for a, b in zip(res, res2):         # deterministic across launches
         assert a["sum"] == b["sum"] and a["sum2"] == b["sum2"] and a["isum"] == b["isum"]
-    for it, r in zip(meta, res):
+    for k, (it, r) in enumerate(zip(meta, res)):
         p = it["params"]
         fmt = W.default_format(p, it["level"])
         assert r["n"] == it["N"]
@@ -45,16 +47,17 @@ def test_nested_workload_full_size(m):
             assert r["isum"] == o["isum"] and r["isum2"] == o["isum2"], it
             assert r["saturations"] == o["saturations"]
         else:
-            o, od = core.level(p, it["level"], 0, it["N"], it["variant"], cfg["seed"], request=it["request"],
+            # every sample of the correction item against the oracle, and the
+            # plan's sums against the FP64 sums of those samples (1e-12 of sum |Y|)
+            _, od = core.level(p, it["level"], 0, it["N"], it["variant"], cfg["seed"], request=it["request"],
                                d=cfg["d"], method=cfg["method"], fmt=fmt, dump=True)
+            P = items[k]["params"]
+            _, gd = m.mlmc_level_dump(it["level"], it["N"], P, it["variant"], cfg["seed"], 0)
+            compare_samples(it["variant"], p, gd, od)
             disc = math.exp(-p["r"] * p["T"])
-            scale = np.sum(np.maximum(np.abs(od["sf"]), p["K"]) + np.abs(od["sc"]))
-            tol = 8e-5 * disc * scale
-            if p["payoff"] == W.DIGITAL:
-                near = np.sum((np.abs(od["sf"] - p["K"]) < 4e-5 * od["sf"]) |
-                              (np.abs(od["sc"] - p["K"]) < 4e-5 * np.abs(od["sc"])))
-                tol += disc * (near + 1)
-            assert abs(r["sum"] - disc * o["sum"]) <= tol, it
+            y = gd["y"]
+            assert abs(r["sum"] - disc * math.fsum(y.tolist())) <= 1e-12 * disc * np.sum(np.abs(y)), it
+            assert abs(r["sum2"] - disc * disc * math.fsum((y * y).tolist())) <= 1e-12 * disc * disc * np.sum(y * y)
 
 
 def test_nested_workload_sampled_samples(m):

@@ -79,7 +79,8 @@ def test_sample_parity(m, variant, scheme, payoff, level):
 @pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("level", [0, 1, 3, 7])
 def test_multichunk_sums(m, variant, level):
-    """Many small CTAs and a ragged tail: the reduction must reproduce the oracle's sums."""
+    """Many small CTAs and a ragged tail: integer sums equal the oracle's, real sums
+    are the FP64 sums of samples that match the oracle's one by one."""
     p = W.params(payoff=W.EURO)
     fmts = [W.default_format(p, lev) for lev in range(level + 1)]
     P = m.make_params(p, d=10, method=1, formats=fmts)
@@ -94,6 +95,10 @@ def test_multichunk_sums(m, variant, level):
         assert res["isum"] == o["isum"] and res["isum2"] == o["isum2"]
         assert res["sum"] == disc * o["sum"]
     else:
-        rt = 1e-12 if variant == core.FP64_EXACT else 1e-5
-        scale = np.sum(np.maximum(np.abs(od["sf"]), p["K"]) + np.abs(od["sc"]))
-        assert abs(res["sum"] - disc * o["sum"]) <= 8 * rt * disc * scale
+        # real samples: each agrees with the oracle's within the path bound, and
+        # the product kernel's sums are the FP64 sums of exactly these samples
+        _, gd = m.mlmc_level_dump(level, N, P, variant, 77, first)
+        compare_samples(variant, p, gd, od)
+        y = gd["y"]
+        assert abs(res["sum"] - disc * math.fsum(y.tolist())) <= 1e-12 * disc * np.sum(np.abs(y))
+        assert abs(res["sum2"] - disc * disc * math.fsum((y * y).tolist())) <= 1e-12 * disc * disc * np.sum(y * y)
