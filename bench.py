@@ -41,6 +41,14 @@ WORKLOAD = ("nested MLMC step: euro+digital call GBM, EM, levels 0-8, N~ 1e7..1e
 #   fixed-point Algorithm-1 fine step (2 products, 2 sums, 4 roundings): 10
 #   coarse step every other fine step: (1 + 10) / 2 = 5.5
 OPS_APPROX_FIXED_EM = 30.5
+# Correction estimator (FP32 exact minus fixed point on the same J), Euler-Maruyama:
+#   Philox4x32-10, one word per path-step: 10
+#   exact Normal: U = 2^-32 (J + 1/2) with the symmetric fold 3, Phi^-1 in single
+#     precision as a published algorithm computes it (Giles 2012: one logarithm,
+#     a degree-8 polynomial by Horner, 8 further operations) 17
+#   exact fine step 2 (increment, S update); coarse every other step (3) / 2 = 1.5
+#   approximate part: index, lookup and sign 5, fine Algorithm-1 step 10, coarse 5.5
+OPS_CORR_FIXED_EM = 54.0
 # SM issue peak: 152 SMs x 4 schedulers x 32 lanes x 2070 MHz (one warp instruction per scheduler per clock)
 ALU_PEAK_TOPS = 152 * 4 * 32 * 2.070e9 / 1e12
 # DRAM bytes (read + write) of the dominant launch, from one ncu capture of this
@@ -291,12 +299,13 @@ def main():
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_value = info["path_steps"] / (statistics.median(e2e_ms) * 1e-3)
 
-    # roofline of the dominant kernel: the launch of an approximate fixed-point
-    # family (15 packed / 8 one sample per thread, 32-bit S; 12 / 2 general)
-    # with the most path-steps, which holds the largest share of the serialised
-    # launch list; per-launch event times of kernels that overlap on forked
-    # streams do not rank them
-    fam_names = {15: "level_kernel<APPROX,F32,FX32,EM,terminal,packed x3>",
+    # roofline of the dominant kernel: the launch with the most path-steps among
+    # the fixed-point families (17: the merged nested launch of the approximate
+    # and correction chunks; 15 / 8: approximate packed / one sample per thread,
+    # 32-bit S; 12 / 2 general).  Its algorithmic ops are each estimator's ops
+    # per path-step times that estimator's path-steps in the launch.
+    fam_names = {17: "nested_kernel<FX32,EM,terminal> (approximate packed + one sample per thread + correction)",
+                 15: "level_kernel<APPROX,F32,FX32,EM,terminal,packed x3>",
                  8: "level_kernel<APPROX,F32,FX32,EM,terminal>",
                  12: "level_kernel<APPROX,F32,FIXED,EM,terminal,packed x3>",
                  2: "level_kernel<APPROX,F32,FIXED,EM,terminal>"}
@@ -305,18 +314,24 @@ def main():
     roofline = None
     if cand:
         ps, j, dom = max(cand)
+        idx = plan.launch_items(j)
+        ps_a = sum(items[i]["N"] << items[i]["level"] for i in idx if items[i]["variant"] != W.CORR_FIXED)
+        ps_c = sum(items[i]["N"] << items[i]["level"] for i in idx if items[i]["variant"] == W.CORR_FIXED)
+        ops = OPS_APPROX_FIXED_EM * ps_a + OPS_CORR_FIXED_EM * ps_c
         dom_ms = sum(launch_ms[j]) / len(launch_ms[j])
-        achieved = OPS_APPROX_FIXED_EM * ps / (dom_ms * 1e-3) / 1e12
+        achieved = ops / (dom_ms * 1e-3) / 1e12
+        fam_, _, ctas_, _ = launches[j]
         roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Top/s",
                     "frac": achieved / ALU_PEAK_TOPS, "traffic": DOMINANT_TRAFFIC.get((dom, ps)),
-                    "kernel": fam_names[dom],
-                    "ms_per_launch": dom_ms, "ops_per_path_step": OPS_APPROX_FIXED_EM,
-                    "path_steps_per_launch": ps}
+                    "kernel": fam_names[dom], "ctas": ctas_,
+                    "ms_per_launch": dom_ms,
+                    "ops_per_path_step": {"approximate": OPS_APPROX_FIXED_EM, "correction": OPS_CORR_FIXED_EM},
+                    "path_steps_per_launch": ps, "approximate_path_steps": ps_a, "correction_path_steps": ps_c}
         alone_ms = dominant_alone(m, torch, items, cfg["seed"], tuning, plan, j, flush, stream)
         if alone_ms:
-            # the same launch with the GPU to itself (in the step it shares the
-            # SMs with the other two level kernels)
-            a = OPS_APPROX_FIXED_EM * ps / (alone_ms * 1e-3) / 1e12
+            # the same launch with the GPU to itself (in the step it may share the
+            # SMs with other level kernels)
+            a = ops / (alone_ms * 1e-3) / 1e12
             roofline["alone"] = {"ms_per_launch": alone_ms, "achieved": a, "frac": a / ALU_PEAK_TOPS}
 
     out = {
@@ -344,10 +359,10 @@ def main():
     if rank == 0 and world == 1 and args.sweep:
         out["sweep"] = sweep_run(m, torch)
     if rank == 0 and world == 1 and not args.no_serving_sample:
-        # bounded serving sample: 200 requests drawn as the serving workload at
-        # 1000 req/s, accuracies in the coarser half [1e-3, 1e-2] of its range
-        # (--serving runs the full range; its tail of eps ~ 1e-4 requests takes minutes)
-        out["serving_sample"] = serving_run(m, 1000, n=200, eps_range=(1e-3, 1e-2))
+        # bounded serving samples: 200 requests drawn as the serving workload at
+        # 100, 1000 and 10000 req/s, accuracies in the coarser half [1e-3, 1e-2] of
+        # its range (--serving runs the full range; its eps ~ 1e-4 tail takes minutes)
+        out["serving_sample"] = [serving_run(m, rate, n=200, eps_range=(1e-3, 1e-2)) for rate in (100, 1000, 10000)]
     if rank == 0 and world == 1 and args.serving:
         out["batched"] = batched_run(m)
         out["serving"] = [serving_run(m, rate) for rate in (100, 1000, 10000)]
@@ -384,13 +399,18 @@ def _engine_params(m, o, request, max_level=10):
 
 
 def _accuracy(done, opts, max_level):
-    """RMS of (price - Black-Scholes) / eps over the European and digital requests,
-    and the number of requests that stopped at the maximum level."""
+    """RMS of (price - Black-Scholes) / eps over the European and digital requests;
+    the requests that stopped at the maximum level, with their final bias
+    estimate over the target eps / sqrt(2) (above 1: the bias test was not met,
+    the result is flagged as not converged)."""
     errs = [(done[i]["price"] - _bs_price(o)) / o["eps"] for i, o in enumerate(opts) if _bs_price(o) is not None]
-    at_max = sum(1 for i in range(len(opts)) if done[i]["L"] >= max_level)
+    at_max = [i for i in range(len(opts)) if done[i]["L"] >= max_level]
+    ratio = {i: done[i].get("bias_estimate", float("nan")) / (opts[i]["eps"] / math.sqrt(2)) for i in at_max}
     return {"rms_err_over_eps_vs_black_scholes": math.sqrt(sum(e * e for e in errs) / len(errs)),
-            "checked_against_black_scholes": len(errs), "stopped_at_max_level": at_max,
-            "max_level": max_level}
+            "checked_against_black_scholes": len(errs), "stopped_at_max_level": len(at_max),
+            "max_level": max_level,
+            "not_converged": sum(1 for v in ratio.values() if v > 1.0),
+            "bias_over_target_at_max_level": sorted(ratio.values())}
 
 
 def batched_run(m, n=256, seed=7, mode=5, iters_per_launch=-4096, max_level=14):
@@ -411,6 +431,7 @@ def batched_run(m, n=256, seed=7, mode=5, iters_per_launch=-4096, max_level=14):
             if i not in done:
                 res = eng.poll(r)
                 if res is not None:
+                    res.update(bias_estimate=eng.request_info(r)["bias_estimate"])
                     done[i] = res
     wall = time.perf_counter() - t0
     st = eng.stats()
@@ -452,6 +473,7 @@ def serving_run(m, rate, n=400, seed=11, mode=5, max_level=14, eps_range=(1e-4, 
             if i not in done:
                 res = eng.poll(rids[i])
                 if res is not None:
+                    res.update(bias_estimate=eng.request_info(rids[i])["bias_estimate"])
                     done[i] = res
     wall = time.perf_counter() - t0
     st = eng.stats()

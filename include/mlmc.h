@@ -351,6 +351,16 @@ mlmc_status mlmc_engine_step(mlmc_engine *e, void *stream, int *active, int *que
  * Returns the request's status (MLMC_OK unless its admission failed). */
 mlmc_status mlmc_engine_poll(mlmc_engine *e, uint64_t req_id, double *price, double *stderr_out, int *L,
                              int *done, double *latency_s);
+/* The schedule and bias test of a completed request: N_l[l * 2 + k] = samples
+ * of estimator k on level l (k = 0: plain or approximate, k = 1: correction;
+ * host array of 2 * cap_levels, zero beyond the final level L) and
+ * *bias_estimate (may be NULL) = the remaining-bias estimate of the final
+ * bias test, max(|m_L|, |m_{L-1}| / 2) with the level means floored as in
+ * mlmc_estimate; a request that stopped at max_level with this above
+ * eps / sqrt(2) did not reach its bias target.  MLMC_ENOTREADY before the
+ * request has completed; a request whose admission failed returns its status. */
+mlmc_status mlmc_engine_request_info(mlmc_engine *e, uint64_t req_id, uint64_t *N_l, int cap_levels,
+                                     double *bias_estimate);
 /* Engine counters: steps taken, graph launches, fine path-steps simulated, slots. */
 mlmc_status mlmc_engine_stats(const mlmc_engine *e, uint64_t *steps, uint64_t *launches,
                               uint64_t *path_steps, int *slots);

@@ -60,12 +60,13 @@ struct SlotState {
   double Vext[MAXL][2];                // extrapolated variance of a level not yet sampled
   unsigned long long N[MAXL][2], dN[MAXL][2];
   double price, se;
+  double rem;                          // remaining-bias estimate of the final bias test
 };
 
 // What the host reads back after each graph launch, per slot.
 struct SlotReport {
   int32_t active, done, L, pad;
-  double price, se;
+  double price, se, rem;
 };
 
 // Per (slot, level, estimator) template: what the scheduler needs beside the ItemDesc.
@@ -318,6 +319,7 @@ __global__ void decide_kernel(SlotState *slots, SlotReport *rep, int n_slots, En
           }
         s.price = pr;
         s.se = __dsqrt_rn(var);
+        s.rem = rem;
         s.done = 1;
       } else {
         const int L = ++s.L;
@@ -334,6 +336,7 @@ __global__ void decide_kernel(SlotState *slots, SlotReport *rep, int n_slots, En
   r.L = s.L;
   r.price = s.price;
   r.se = s.se;
+  r.rem = s.rem;
   if (s.active && !s.done) atomicAdd(&status->active, 1);
   if (s.active && s.done) atomicAdd(&status->done, 1);
 }
@@ -352,6 +355,8 @@ struct Request {
   double price, se;
   int L;
   int exact_mask;                     // bit l: approximate term of level l computed by enumeration
+  double rem;                         // final remaining-bias estimate
+  std::vector<uint64_t> N;            // samples per (level, estimator) at completion, level-major
 };
 
 int exact_mask_of(int mode, int d) {
@@ -866,7 +871,13 @@ mlmc_status mlmc_engine_step(mlmc_engine *e, void *stream, int *active_out, int 
         r.price = hr.price;
         r.se = hr.se;
         r.L = hr.L;
+        r.rem = hr.rem;
         r.t_done = t;
+        // the request's schedule, read before the slot is cleared (the launch
+        // has finished: its stream was synchronised above)
+        r.N.assign((size_t)MAXL * 2, 0);
+        MLMC_CK(cudaMemcpy(r.N.data(), &e->d_slots[sl].N[0][0], sizeof(unsigned long long) * MAXL * 2,
+                           cudaMemcpyDeviceToHost));
         SlotState z;
         std::memset(&z, 0, sizeof z);
         MLMC_CK(cudaMemcpyAsync(e->d_slots + sl, &z, sizeof z, cudaMemcpyHostToDevice, st));
@@ -900,6 +911,22 @@ mlmc_status mlmc_engine_poll(mlmc_engine *e, uint64_t req_id, double *price, dou
     if (latency_s) *latency_s = r.t_done - r.t_submit;
   }
   return r.status;
+}
+
+mlmc_status mlmc_engine_request_info(mlmc_engine *e, uint64_t req_id, uint64_t *N_l, int cap_levels,
+                                     double *bias_estimate) {
+  MLMC_API_LOCK();
+  if (!e || cap_levels < 0 || (cap_levels > 0 && !N_l)) return MLMC_EINVAL;
+  auto it = e->by_id.find(req_id);
+  if (it == e->by_id.end()) return MLMC_EINVAL;
+  const Request &r = e->reqs[it->second];
+  if (!r.done) return MLMC_ENOTREADY;
+  if (r.status != MLMC_OK) return r.status;
+  for (int l = 0; l < cap_levels; ++l)
+    for (int k = 0; k < 2; ++k)
+      N_l[2 * l + k] = (l < MAXL && l <= r.L && !r.N.empty()) ? r.N[(size_t)l * 2 + k] : 0;
+  if (bias_estimate) *bias_estimate = r.rem;
+  return MLMC_OK;
 }
 
 mlmc_status mlmc_engine_stats(const mlmc_engine *e, uint64_t *steps, uint64_t *launches, uint64_t *path_steps,

@@ -137,7 +137,7 @@ extern "C" mlmc_status mlmc_estimate(double eps, const mlmc_params *p, int mode,
           }
       if (work.empty()) break;
       res.resize(work.size());
-      s = run_sync(work.data(), (int)work.size(), seed, nullptr, nullptr, res.data(), g.st);
+      s = run_sync(work.data(), (int)work.size(), seed, nullptr, nullptr, res.data(), g.st, false);
       if (s != MLMC_OK) return s;
       for (size_t j = 0; j < work.size(); ++j) {
         const int l = idx[j].first, k = idx[j].second;

@@ -173,7 +173,8 @@ mlmc_status build_item_cached(const mlmc_work &w, int out_index, void *dump, Bui
                               int &exact_int);
 // Empty that cache (its items point to one device's tables).
 void item_cache_clear();
-mlmc_status chunk_built(BuiltItem &b, int threads, int spt, int num_sms);
+// floor: at least four CTAs per SM for this item alone (see chunk_count).
+mlmc_status chunk_built(BuiltItem &b, int threads, int spt, int num_sms, bool floor = true);
 void make_round_keys(uint64_t seed, mlmc::RoundKeys &rk);
 // Launch one level kernel of a family (or, with occ, query the resident CTAs
 // per SM of its device-scheduled kernel).
@@ -189,6 +190,6 @@ __global__ void finalize_kernel(const mlmc::ItemDesc *items, int n_items, const 
 double u128_to_double(uint64_t lo, uint64_t hi);
 // Plan, launch, read and release in one synchronous call on stream st.
 mlmc_status run_sync(const mlmc_work *work, int n_work, uint64_t seed, const mlmc_tuning *tuning,
-                     void *const *dumps, mlmc_sums *out, cudaStream_t st);
+                     void *const *dumps, mlmc_sums *out, cudaStream_t st, bool launch_chunking);
 
 }  // namespace mlmc_host

@@ -74,6 +74,9 @@ struct ItemDesc {
   int32_t enumerate;       // 1: table indices enumerate samples instead of Philox draws
   int32_t lanes;           // 3: packed draws with one sample per thread (sample s reads lane s mod 3
                            // of pack s / 3); levels >= 2, approximate-only, KP = 1 kernels
+  int32_t kind;            // in a merged nested launch: 0 approximate packed, 1 approximate one
+                           // sample per thread, 2 correction (nested_kernel)
+  int32_t kind_pad;
   float unit_scale;        // 2^-unit (FP32, correction estimators)
   // exact path constants
   float c1f, c2f, c1cf, c3f, S0f, Kf;
@@ -152,17 +155,17 @@ MLMC_HD inline uint64_t samples_per_group(int level, int kp) {
 MLMC_HD inline uint64_t steps_per_group(int level) { return level >= 2 ? (1ULL << level) : 4ULL; }
 
 // Chunking of an item of `groups` sample groups for CTAs of `threads` threads:
-// about spt fine path-steps per thread (at least one group), but no fewer than
-// four CTAs per SM while the item has that many groups.  Returns the number of
-// chunks (CTAs) and sets *gpt, the groups per thread.
+// about spt fine path-steps per thread (at least one group), but (with floor)
+// no fewer than four CTAs per SM while the item has that many groups.  Returns
+// the number of chunks (CTAs) and sets *gpt, the groups per thread.
 MLMC_HD inline uint64_t chunk_count(uint64_t groups, uint64_t spg, int kp, int threads, int spt, int num_sms,
-                                    uint32_t *gpt) {
+                                    uint32_t *gpt, bool floor = true) {
   uint64_t G = (uint64_t)spt / (spg * (uint64_t)kp);
   if (G < 1) G = 1;
   const uint64_t min_ctas = 4ULL * (uint64_t)(num_sms > 1 ? num_sms : 1);
   uint64_t cap = (groups + (uint64_t)threads * min_ctas - 1) / ((uint64_t)threads * min_ctas);
   if (cap < 1) cap = 1;
-  if (G > cap) G = cap;
+  if (floor && G > cap) G = cap;
   *gpt = (uint32_t)G;
   const uint64_t per_chunk = G * (uint64_t)threads;
   return (groups + per_chunk - 1) / per_chunk;

@@ -185,6 +185,7 @@ cudaError_t launch_by_family(int fam, int scheme, int pc, dim3 grid, dim3 block,
     case 14: return launch_approx_bf16_p3(scheme, pc, grid, block, smem, st, a, occ);
     case 15: return launch_approx_fx32_p3(scheme, pc, grid, block, smem, st, a, occ);
     case 16: return launch_approx_fx64_p3(scheme, pc, grid, block, smem, st, a, occ);
+    case 17: return launch_nested_fx32(scheme, pc, grid, block, smem, st, a, occ);
     case 8: return launch_approx_fx32(scheme, pc, grid, block, smem, st, a, occ);
     case 9: return launch_approx_fx64(scheme, pc, grid, block, smem, st, a, occ);
     case 10: return launch_corr_fx32(scheme, pc, grid, block, smem, st, a, occ);
@@ -224,7 +225,9 @@ bool fast_fixed(const int e[7], const int f[7], int64_t con1, int64_t con1c, int
   const int shS = f[F_S] - f[F_MUL2];
   if (shF1 > 30 || shS > 30) return false;
   auto lim = [&](int v) { return ((I)1 << (e[v] + f[v])) - 1; };
-  const I zc = 2 * (I)zmax;  // coarse increments are sums of two table values
+  // coarse increments are sums of two table values; level 0 (one step) has no
+  // coarse path, so its increments are single table values
+  const I zc = nsteps > 1 ? 2 * (I)zmax : (I)zmax;
   const I r1 = radd_of(rs1), r3 = radd_of(rs3), rsum = radd_of(rs_sum1), r2 = radd_of(rs2);
   if ((I)con2 * zc + r1 >= ((I)1 << 62)) return false;
   const I m1a = floor_shift((I)con2 * zc + r1, rs1), m1b = floor_shift(-(I)con2 * zc + r1, rs1);
@@ -319,11 +322,11 @@ int64_t table_zmax_fixed(const double *Z, int d, int method, int fZ, int fields)
 
 
 // Split an item's sample groups into chunks of `threads` x groups_per_thread.
-mlmc_status chunk_built(BuiltItem &b, int threads, int spt, int num_sms) {
+mlmc_status chunk_built(BuiltItem &b, int threads, int spt, int num_sms, bool floor) {
   ItemDesc &it = b.it;
   uint32_t gpt = 1;
   const uint64_t spg = steps_per_group(it.level);
-  const uint64_t nch = chunk_count(it.g1 - it.g0, spg, b.kp, threads, spt, num_sms, &gpt);
+  const uint64_t nch = chunk_count(it.g1 - it.g0, spg, b.kp, threads, spt, num_sms, &gpt, floor);
   if (nch > 0x7fffffffULL) return MLMC_EINVAL;
   it.groups_per_thread = gpt;
   it.n_chunks = (uint32_t)nch;

@@ -27,5 +27,8 @@ MLMC_FAMILY(launch_approx_f16_p3)
 MLMC_FAMILY(launch_approx_bf16_p3)
 MLMC_FAMILY(launch_approx_fx32_p3)
 MLMC_FAMILY(launch_approx_fx64_p3)
+// family 17: merged nested launch of families 15, 8 and 10 (Euler-Maruyama,
+// terminal payoffs; per-item kind in ItemDesc::kind)
+MLMC_FAMILY(launch_nested_fx32)
 #undef MLMC_FAMILY
 }  // namespace mlmc

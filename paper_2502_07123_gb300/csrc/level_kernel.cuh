@@ -117,6 +117,8 @@ struct LevelSim {
   // values are final, otherwise the group runs again on the clamped (EAGER)
   // datapath.
   static constexpr bool LAZY = (EST == EST_APPROX && AP == AP_FX32);
+  static constexpr int KPV = KP;
+  static constexpr int ESTV = EST;
   using X = typename XType<XP>::T;
   using H = typename HType<AP>::T;
   using HO = HalfOps<H>;
@@ -615,33 +617,41 @@ struct ThreadAcc {
   float fs, fc, fs2, fc2;
   uint32_t nsat;
   __device__ __forceinline__ void init() {
-    isum = 0; q_lo = 0; q_hi = 0; gq = 0; ds = 0.0; dq = 0.0; nsat = 0;
+    isum = 0; q_lo = 0; q_hi = 0; gsum = 0; gq = 0; ds = 0.0; dq = 0.0; nsat = 0;
     fs = 0.0f; fc = 0.0f; fs2 = 0.0f; fc2 = 0.0f;
   }
   __device__ __forceinline__ void add_int(int64_t y) {
     isum += y;
     add_square(q_lo, q_hi, y);
   }
-  // Two wide multiply-adds per sample (FMA pipe): sum y and the group's sum of
-  // y^2 in 64 bits; flush_group() adds the latter into the 128-bit total.
+  // Two wide multiply-adds per sample (FMA pipe): the group's sum of y and of
+  // y^2 in 64 bits; flush_group() adds them into the totals (and
+  // discard_group() drops a group that must be redone).
+  int64_t gsum;
   uint64_t gq;
   __device__ __forceinline__ void add_group(int32_t y) {
-    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(isum) : "r"(y), "r"(1));
+    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(gsum) : "r"(y), "r"(1));
     asm("mad.wide.s32 %0, %1, %1, %0;" : "+l"(gq) : "r"(y));
   }
   __device__ __forceinline__ void flush_group() {
+    isum += gsum;
     add_u128(q_lo, q_hi, gq, 0);
+    gsum = 0;
     gq = 0;
   }
-  // Integer sums at the start of a group (the group's own sum of squares gq is
-  // zero there), to undo the group's samples.
+  __device__ __forceinline__ void discard_group() {
+    gsum = 0;
+    gq = 0;
+  }
+  // Integer sums at the start of a group, to undo the group's samples (the
+  // path-dependent payoffs add each sample to the totals directly).
   struct Mark {
     int64_t isum;
     uint64_t q_lo, q_hi;
   };
   __device__ __forceinline__ Mark mark() const { return Mark{isum, q_lo, q_hi}; }
   __device__ __forceinline__ void rewind(const Mark &m) {
-    isum = m.isum; q_lo = m.q_lo; q_hi = m.q_hi; gq = 0;
+    isum = m.isum; q_lo = m.q_lo; q_hi = m.q_hi;
   }
   // s + y = t + e exactly (Knuth's TwoSum, six FP32 operations); e goes to c.
   static __device__ __forceinline__ void two_sum_into(float &s, float &c, float y) {
@@ -690,21 +700,27 @@ template <class T>
 __device__ __forceinline__ T shfl_xor(T v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
 
 // Reduce the CTA's thread accumulators into one Partial (thread 0 writes it).
+// Approximate-only estimators have integer sums only, the others real sums
+// only, so each shuffles just its own.
 template <int EST, int XP>
 __device__ __forceinline__ void block_reduce_write(ThreadAcc<EST, XP> &a, Partial *out) {
-  int64_t isum = a.isum;
-  uint64_t lo = a.q_lo, hi = a.q_hi;
-  double ds = a.ds, dq = a.dq;
-  uint64_t ns = a.nsat;
+  constexpr bool INT = EST == EST_APPROX;
+  int64_t isum = INT ? a.isum : 0;
+  uint64_t lo = INT ? a.q_lo : 0, hi = INT ? a.q_hi : 0;
+  double ds = INT ? 0.0 : a.ds, dq = INT ? 0.0 : a.dq;
+  uint32_t ns = a.nsat;
 #pragma unroll
   for (int m = 16; m >= 1; m >>= 1) {
-    isum += shfl_xor((long long)isum, m);
-    const uint64_t olo = (uint64_t)shfl_xor((unsigned long long)lo, m);
-    const uint64_t ohi = (uint64_t)shfl_xor((unsigned long long)hi, m);
-    add_u128(lo, hi, olo, ohi);
-    ds += shfl_xor(ds, m);
-    dq += shfl_xor(dq, m);
-    ns += (uint64_t)shfl_xor((unsigned long long)ns, m);
+    if constexpr (INT) {
+      isum += shfl_xor((long long)isum, m);
+      const uint64_t olo = (uint64_t)shfl_xor((unsigned long long)lo, m);
+      const uint64_t ohi = (uint64_t)shfl_xor((unsigned long long)hi, m);
+      add_u128(lo, hi, olo, ohi);
+    } else {
+      ds += shfl_xor(ds, m);
+      dq += shfl_xor(dq, m);
+    }
+    ns += shfl_xor(ns, m);
   }
   __shared__ Partial wp[LAUNCH_THREADS / 32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -735,8 +751,147 @@ template <int P> using PayTag = std::integral_constant<int, P>;
 // run's live in registers through the group.
 __device__ __forceinline__ void opaque(uint64_t &x) { asm volatile("" : "+l"(x)); }
 
+// The samples of group g of a chunk, for a level class LC known at compile
+// time (0: level 0, 1: level 1, 2: levels >= 2).  A group is one Philox call's
+// worth of packs (4 on level 0, 2 on level 1) or, from level 2, one pack over
+// 2^l / 4 calls; a pack holds KP samples.  E: the clamped datapath (LAZY
+// kernels; always true elsewhere); FULL: every sample of the group is in the
+// item's range at compile time (then no per-sample range test splits the
+// group's straight-line code); full: the same known at run time; PAY: the
+// terminal payoff when fixed at compile time (0 European, 1 digital, -1 not).
+template <int LC, bool E, bool FULL, int PAY, bool DUMP, class Sim, class Acc>
+__device__ __forceinline__ void run_group(Sim &sim, Acc &acc, const LaunchArgs &args, const ItemDesc &it, uint64_t g,
+                                          bool full, uint64_t first, uint64_t last, mlmc_sample_rec *dump) {
+  constexpr int KP = Sim::KPV;
+  if constexpr (LC == 2) {
+    uint64_t P = g;
+    uint32_t lsh = 0;   // lane-split packed draws: this sample's field to the top of the word
+    if constexpr (KP == 1 && Sim::ESTV == EST_APPROX) {
+      if (it.lanes > 1) {
+        P = g / 3u;
+        lsh = (uint32_t)it.d * (uint32_t)(g - P * 3u);
+      }
+    }
+    const uint32_t calls = 1u << (it.level - 2);
+    uint64_t qbase = P * calls;
+    if constexpr (E && Sim::LAZY) opaque(qbase);
+    sim.begin();
+    for (uint32_t c = 0; c < calls; ++c) {
+      const uint64_t q = qbase + c;
+      const uint4 w = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), it.ctr2, it.ctr3), args.rk);
+      const int i0 = (int)(c << 2);
+      sim.template step<true, 0, E>(w.x << lsh, i0);
+      sim.template step<true, 1, E>(w.y << lsh, i0 + 1);
+      sim.template step<true, 0, E>(w.z << lsh, i0 + 2);
+      sim.template step<true, 1, E>(w.w << lsh, i0 + 3);
+    }
+#pragma unroll
+    for (int l = 0; l < KP; ++l) {
+      const uint64_t s = KP == 1 ? g : P * KP + l;
+      const bool valid = FULL || full || (s >= first && s < last);
+      sim.template finish<E, PAY, 1>(acc, l, valid, DUMP && valid ? dump + (s - first) : nullptr);
+    }
+  } else {
+    uint64_t gw = g;
+    if constexpr (E && Sim::LAZY) opaque(gw);
+    const uint4 w = it.enumerate ? enum_words(gw, LC, it.d)
+                                 : philox4x32_10(make_uint4((uint32_t)gw, (uint32_t)(gw >> 32), it.ctr2, it.ctr3),
+                                                 args.rk);
+    constexpr int PPG = LC == 1 ? 2 : 4;  // packs per group
+    const uint64_t s0 = (uint64_t)(PPG * KP) * g;
+    // samples s0 + k are valid for k in [klo, khi)
+    int klo = 0, khi = PPG * KP;
+    if (!FULL && !full) {
+      klo = s0 >= first ? 0 : (int)min(first - s0, (uint64_t)(PPG * KP));
+      khi = last <= s0 ? 0 : (int)min(last - s0, (uint64_t)(PPG * KP));
+    }
+    if constexpr (LC == 1) {
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        sim.begin();
+        sim.template step<true, 0, E>(u == 0 ? w.x : w.z, 0);
+        sim.template step<true, 1, E>(u == 0 ? w.y : w.w, 1);
+#pragma unroll
+        for (int l = 0; l < KP; ++l) {
+          const int k = u * KP + l;
+          const bool valid = FULL || (k >= klo && k < khi);
+          sim.template finish<E, PAY, 1>(acc, l, valid, DUMP && valid ? dump + (s0 + k - first) : nullptr);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        sim.begin();
+        sim.template step<false, -1, E>(word_of(w, u), 0);
+#pragma unroll
+        for (int l = 0; l < KP; ++l) {
+          const int k = u * KP + l;
+          const bool valid = FULL || (k >= klo && k < khi);
+          sim.template finish<E, PAY, 0>(acc, l, valid, DUMP && valid ? dump + (s0 + k - first) : nullptr);
+        }
+      }
+    }
+  }
+}
+
+// A thread's groups of one chunk, groups gbeg + r for r = threadIdx.x,
+// threadIdx.x + blockDim.x, ... < ng, of level class LC; groups with r in
+// [rf0, rf1) lie entirely in the item's range.  LAZY items run each such group
+// first with S unclamped and its samples added tentatively; a group whose S
+// went above lim_S is dropped and run again on the clamped datapath (rare).
+// PAYF: the terminal payoff of the lazy run (terminal payoff classes).
+template <int LC, int PAYF, bool DUMP, int EST, int XP, int AP, int PC, class Sim>
+__device__ __forceinline__ void group_loop(Sim &sim, ThreadAcc<EST, XP> &acc, const LaunchArgs &args,
+                                           const ItemDesc &it, uint64_t gbeg, uint32_t ng, uint32_t rf0, uint32_t rf1,
+                                           bool lazy, mlmc_sample_rec *dump) {
+  const uint64_t first = it.first, last = it.first + it.N;
+  // Real-valued estimators flush their float pairs every `flush_groups`
+  // groups (at most REAL_FLUSH_SAMPLES samples).
+  constexpr bool REAL = EST != EST_APPROX && !(XP == XP_F64 && EST == EST_EXACT);
+  constexpr uint32_t FLUSH_GROUPS =
+      REAL ? (uint32_t)REAL_FLUSH_SAMPLES / (uint32_t)(Sim::KPV * (LC == 2 ? 1 : (LC == 1 ? 2 : 4))) : 0u;
+  uint32_t since_flush = 0;
+  for (uint32_t r = threadIdx.x; r < ng; r += blockDim.x) {
+    const uint64_t g = gbeg + r;
+    const bool full = r >= rf0 && r < rf1;
+    if constexpr (Sim::LAZY && !DUMP) {
+      bool eager = true;
+      if (lazy && full) {
+        sim.hi = 0;
+        if constexpr (PC == PC_TERMINAL) {
+          // the group's sums stay in their own accumulator until the group is kept
+          run_group<LC, false, true, PAYF, DUMP>(sim, acc, args, it, g, true, first, last, dump);
+          eager = sim.over();
+          if (eager) acc.discard_group();
+        } else {
+          // path-dependent payoffs: one sample per step carries more state, and a
+          // FULL instantiation costs registers more than the range test costs
+          const auto saved = acc.mark();
+          run_group<LC, false, false, -1, DUMP>(sim, acc, args, it, g, true, first, last, dump);
+          eager = sim.over();
+          if (eager) acc.rewind(saved);
+        }
+      }
+      if (eager) run_group<LC, true, false, -1, DUMP>(sim, acc, args, it, g, full, first, last, dump);
+    } else {
+      // other datapaths: one instantiation (a FULL one beside it raised the
+      // packed binary16 kernels from ~115 to ~165 registers and cost 9%)
+      run_group<LC, true, false, -1, DUMP>(sim, acc, args, it, g, full, first, last, dump);
+    }
+    if constexpr (EST == EST_APPROX && AP == AP_FX32 && PC == PC_TERMINAL) acc.flush_group();
+    if constexpr (REAL) {
+      if (++since_flush == FLUSH_GROUPS) {
+        acc.flush_real();
+        since_flush = 0;
+      }
+    }
+  }
+}
+
 // Simulate one chunk of an item (its table already in shared memory) and
-// write the CTA's Partial for it.  DYN (device-scheduled kernel) only keeps the
+// write the CTA's Partial for it.  The level class and (on the lazy terminal
+// path) the payoff are fixed once per chunk, so the group loop carries no
+// branch on them.  DYN (device-scheduled kernel) only keeps the
 // instantiations of the static and device-scheduled kernels apart, so that
 // each is compiled inline into its own kernel.
 template <int EST, int XP, int AP, int SCHEME, int PC, int KP, int MSEL, bool DUMP, bool DYN>
@@ -752,138 +907,31 @@ __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDes
   const uint64_t per_chunk = (uint64_t)it.groups_per_thread * blockDim.x;
   const uint64_t gbeg = it.g0 + (uint64_t)chunk * per_chunk;
   const uint64_t gend = min(it.g1, gbeg + per_chunk);
-  const uint64_t first = it.first, last = it.first + it.N;
-  const int lev = it.level;
-  const uint4 ctr_hi = make_uint4(0, 0, it.ctr2, it.ctr3);
+  const uint32_t ng = gend > gbeg ? (uint32_t)(gend - gbeg) : 0u;
+  // the chunk's groups [rf0, rf1) (relative to gbeg) lie entirely in the item's range
+  const uint64_t gf0 = max(it.gf0, gbeg), gf1 = min(it.gf1, gend);
+  const uint32_t rf0 = gf0 < gf1 ? (uint32_t)(gf0 - gbeg) : 0u;
+  const uint32_t rf1 = gf0 < gf1 ? (uint32_t)(gf1 - gbeg) : 0u;
   // per-sample records only in the DUMP instantiation (parity runs)
   mlmc_sample_rec *dump = DUMP ? (mlmc_sample_rec *)it.dump : nullptr;
-
-  const uint64_t gf0 = it.gf0, gf1 = it.gf1;
-  const uint32_t ng = gend > gbeg ? (uint32_t)(gend - gbeg) : 0u;
-  // LAZY items run each full group first with S unclamped and the samples
-  // added to the accumulators tentatively; a group whose S went above lim_S is
-  // undone and run again on the clamped datapath (rare).  The check is once
-  // per group, so the group's packs stay one straight-line block.
   const bool lazy = Sim::LAZY && !DUMP && it.ff.lazy;
-  // A group is one Philox call's worth of packs (4 on level 0, 2 on level 1) or,
-  // from level 2, one pack over 2^l / 4 calls; a pack holds KP samples.
-  // Real-valued estimators flush their float pairs every `flush_groups` groups
-  // (at most REAL_FLUSH_SAMPLES samples).
-  constexpr bool REAL = EST != EST_APPROX && !(XP == XP_F64 && EST == EST_EXACT);
-  const uint32_t flush_groups = REAL ? (uint32_t)REAL_FLUSH_SAMPLES / (uint32_t)samples_per_group(lev, KP) : 0u;
-  uint32_t since_flush = 0;
-  for (uint32_t r = threadIdx.x; r < ng; r += blockDim.x) {
-    const uint64_t g = gbeg + r;
-    const bool full = g >= gf0 && g < gf1;
-    // FULL (compile time): every sample of the group is in the item's range, so
-    // no per-sample range test splits the group's straight-line code
-    auto group = [&](auto eager, auto fulltag, auto paytag) {
-      constexpr bool E = decltype(eager)::value;
-      constexpr bool FULL = decltype(fulltag)::value;
-      constexpr int PAY = decltype(paytag)::value;
-      if (lev >= 2) {
-        uint64_t P = g;
-        uint32_t lsh = 0;   // lane-split packed draws: this sample's field to the top of the word
-        if constexpr (KP == 1 && EST == EST_APPROX) {
-          if (it.lanes > 1) {
-            P = g / 3u;
-            lsh = (uint32_t)it.d * (uint32_t)(g - P * 3u);
-          }
-        }
-        const uint32_t calls = 1u << (lev - 2);
-        uint64_t qbase = P * calls;
-        if constexpr (E && Sim::LAZY) opaque(qbase);
-        sim.begin();
-        for (uint32_t c = 0; c < calls; ++c) {
-          const uint64_t q = qbase + c;
-          const uint4 w = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), ctr_hi.z, ctr_hi.w), args.rk);
-          const int i0 = (int)(c << 2);
-          sim.template step<true, 0, E>(w.x << lsh, i0);
-          sim.template step<true, 1, E>(w.y << lsh, i0 + 1);
-          sim.template step<true, 0, E>(w.z << lsh, i0 + 2);
-          sim.template step<true, 1, E>(w.w << lsh, i0 + 3);
-        }
-#pragma unroll
-        for (int l = 0; l < KP; ++l) {
-          const uint64_t s = KP == 1 ? g : P * KP + l;
-          const bool valid = FULL || full || (s >= first && s < last);
-          sim.template finish<E, PAY, 1>(acc, l, valid, DUMP && valid ? dump + (s - first) : nullptr);
-        }
-      } else {
-        uint64_t gw = g;
-        if constexpr (E && Sim::LAZY) opaque(gw);
-        const uint4 w = it.enumerate ? enum_words(gw, lev, it.d)
-                                     : philox4x32_10(make_uint4((uint32_t)gw, (uint32_t)(gw >> 32), ctr_hi.z, ctr_hi.w),
-                                                     args.rk);
-        const int ppg = lev == 1 ? 2 : 4;  // packs per group
-        const uint64_t s0 = (uint64_t)(ppg * KP) * g;
-        // samples s0 + k are valid for k in [klo, khi)
-        int klo = 0, khi = ppg * KP;
-        if (!FULL && !full) {
-          klo = s0 >= first ? 0 : (int)min(first - s0, (uint64_t)(ppg * KP));
-          khi = last <= s0 ? 0 : (int)min(last - s0, (uint64_t)(ppg * KP));
-        }
-        if (lev == 1) {
-#pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            sim.begin();
-            sim.template step<true, 0, E>(u == 0 ? w.x : w.z, 0);
-            sim.template step<true, 1, E>(u == 0 ? w.y : w.w, 1);
-#pragma unroll
-            for (int l = 0; l < KP; ++l) {
-              const int k = u * KP + l;
-              const bool valid = FULL || (k >= klo && k < khi);
-              sim.template finish<E, PAY, 1>(acc, l, valid, DUMP && valid ? dump + (s0 + k - first) : nullptr);
-            }
-          }
-        } else {
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            sim.begin();
-            sim.template step<false, -1, E>(word_of(w, u), 0);
-#pragma unroll
-            for (int l = 0; l < KP; ++l) {
-              const int k = u * KP + l;
-              const bool valid = FULL || (k >= klo && k < khi);
-              sim.template finish<E, PAY, 0>(acc, l, valid, DUMP && valid ? dump + (s0 + k - first) : nullptr);
-            }
-          }
-        }
-      }
-    };
-    if constexpr (Sim::LAZY && !DUMP) {
-      // the lazy run takes full groups only; a partial group (at most one at
-      // each end of an item) and a redone group run the clamped datapath
-      bool eager = true;
-      if (lazy && full) {
-        // only the integer sums change inside a LAZY group (no saturations);
-        // the terminal payoff is a compile-time choice on this path
-        const auto saved = acc.mark();
-        sim.hi = 0;
-        if constexpr (PC == PC_TERMINAL) {
-          if (it.payoff == 1) group(std::false_type{}, std::true_type{}, PayTag<1>{});
-          else group(std::false_type{}, std::true_type{}, PayTag<0>{});
-        } else {
-          // path-dependent payoffs: one sample per step carries more state, and a
-          // FULL instantiation costs registers more than the range test costs
-          group(std::false_type{}, std::false_type{}, PayTag<-1>{});
-        }
-        eager = sim.over();
-        if (eager) acc.rewind(saved);
-      }
-      if (eager) group(std::true_type{}, std::false_type{}, PayTag<-1>{});
-    } else {
-      // other datapaths: one instantiation (a FULL one beside it raised the
-      // packed binary16 kernels from ~115 to ~165 registers and cost 9%)
-      group(std::true_type{}, std::false_type{}, PayTag<-1>{});
-    }
-    if constexpr (EST == EST_APPROX && AP == AP_FX32 && PC == PC_TERMINAL) acc.flush_group();
-    if constexpr (REAL) {
-      if (++since_flush == flush_groups) {
-        acc.flush_real();
-        since_flush = 0;
-      }
-    }
+  const int lc = it.level >= 2 ? 2 : it.level;
+  auto loop = [&](auto lctag, auto paytag) {
+    group_loop<decltype(lctag)::value, decltype(paytag)::value, DUMP, EST, XP, AP, PC>(sim, acc, args, it, gbeg, ng,
+                                                                                      rf0, rf1, lazy, dump);
+  };
+  using L0 = std::integral_constant<int, 0>;
+  using L1 = std::integral_constant<int, 1>;
+  using L2 = std::integral_constant<int, 2>;
+  if constexpr (Sim::LAZY && !DUMP && PC == PC_TERMINAL) {
+    const bool dig = it.payoff == 1;
+    if (lc == 0) { if (dig) loop(L0{}, PayTag<1>{}); else loop(L0{}, PayTag<0>{}); }
+    else if (lc == 1) { if (dig) loop(L1{}, PayTag<1>{}); else loop(L1{}, PayTag<0>{}); }
+    else { if (dig) loop(L2{}, PayTag<1>{}); else loop(L2{}, PayTag<0>{}); }
+  } else {
+    if (lc == 0) loop(L0{}, PayTag<-1>{});
+    else if (lc == 1) loop(L1{}, PayTag<-1>{});
+    else loop(L2{}, PayTag<-1>{});
   }
   acc.flush_real();
   block_reduce_write<EST, XP>(acc, args.partials + gc);
@@ -908,14 +956,12 @@ __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDes
   }
 }
 
-// One chunk (gc) of one launch: find its item, stage the item's table in shared
-// memory (unless *staged, when given, says that it is there already), simulate the chunk's sample groups
-// and write the CTA's Partial for the chunk.  Every thread has finished the
-// previous chunk before the table is overwritten (block_reduce_write ends with
-// a barrier).
-template <int EST, int XP, int AP, int SCHEME, int PC, int KP, bool ALLOW_DUMP, bool DYN>
-__device__ __forceinline__ void run_chunk(const LaunchArgs &args, const ItemDesc *items, int n_items, uint32_t gc,
-                                          const void **staged) {
+// Find the item of chunk gc (the last with chunk_begin <= gc) and stage its
+// approximate-Normal table in shared memory (unless *staged, when given, says
+// that it is there already).  Every thread has finished the previous chunk
+// before the table is overwritten (block_reduce_write ends with a barrier).
+template <int AP, int SCHEME>
+__device__ __forceinline__ int stage_chunk(const ItemDesc *items, int n_items, uint32_t gc, const void **staged) {
   extern __shared__ __align__(16) unsigned char smem_tab[];
   __shared__ int s_item;
   if (threadIdx.x == 0) {
@@ -927,9 +973,8 @@ __device__ __forceinline__ void run_chunk(const LaunchArgs &args, const ItemDesc
     s_item = lo;
   }
   __syncthreads();
-  const ItemDesc &it = items[s_item];
-  // stage the approximate-Normal table in shared memory (every thread has
-  // finished the previous chunk: block_reduce_write ends with a barrier)
+  const int item = s_item;
+  const ItemDesc &it = items[item];
   if constexpr (AP == AP_FX32) {
     // (Z~_j, sum1 of a fine step from Z~_j) for every index j: Method 1 and 2
     // values from the item's table, Method 3 values from its class lines (the
@@ -963,7 +1008,7 @@ __device__ __forceinline__ void run_chunk(const LaunchArgs &args, const ItemDesc
       if (staged) *staged = it.ztab;
       if (it.method != 3) {
         const int n = 1 << it.d;
-        if constexpr (AP == AP_FIXED || AP == AP_FX32 || AP == AP_FX64) {
+        if constexpr (AP == AP_FIXED || AP == AP_FX64) {
           const int32_t *src = (const int32_t *)it.ztab;
           for (int k = threadIdx.x; k < n; k += blockDim.x) ((int32_t *)smem_tab)[k] = src[k];
         } else {
@@ -982,7 +1027,17 @@ __device__ __forceinline__ void run_chunk(const LaunchArgs &args, const ItemDesc
       __syncthreads();
     }
   }
-  const int item = s_item;
+  return item;
+}
+
+// One chunk (gc) of one launch: its item and table (stage_chunk), then the
+// chunk's sample groups and the CTA's Partial for the chunk.
+template <int EST, int XP, int AP, int SCHEME, int PC, int KP, bool ALLOW_DUMP, bool DYN>
+__device__ __forceinline__ void run_chunk(const LaunchArgs &args, const ItemDesc *items, int n_items, uint32_t gc,
+                                          const void **staged) {
+  extern __shared__ __align__(16) unsigned char smem_tab[];
+  const int item = stage_chunk<AP, SCHEME>(items, n_items, gc, staged);
+  const ItemDesc &it = items[item];
   if (ALLOW_DUMP && it.dump) {
     if constexpr (ALLOW_DUMP) chunk_body<EST, XP, AP, SCHEME, PC, KP, 2, true, DYN>(args, it, item, gc, smem_tab);
   } else if constexpr (AP == AP_NONE || AP == AP_FX32) {
@@ -1023,6 +1078,23 @@ level_kernel_dyn(const __grid_constant__ LaunchArgs args) {
   for (uint32_t rel = blockIdx.x; rel < d.n_chunks; rel += gridDim.x)
     run_chunk<EST, XP, AP, SCHEME, PC, KP, false, true>(args, args.items + d.item_off, (int)d.n_items,
                                                         d.chunk0 + rel, &staged);
+}
+
+// A merged launch of the nested estimator's three 32-bit fixed-point kernel
+// families for one (scheme, payoff class): approximate with packed draws
+// (kind 0), approximate one sample per thread (kind 1) and correction (kind 2).
+// Its chunks run the same chunk bodies as the separate launches, in one grid
+// ordered by decreasing CTA cost, so the longest chains start first and the
+// short chunks of every family fill in behind them.
+template <int AP, int SCHEME, int PC>
+__global__ void __launch_bounds__(LAUNCH_THREADS, 6) nested_kernel(const __grid_constant__ LaunchArgs args) {
+  extern __shared__ __align__(16) unsigned char smem_tab[];
+  const uint32_t gc = args.chunk0 + blockIdx.x;
+  const int item = stage_chunk<AP, SCHEME>(args.items, args.n_items, gc, nullptr);
+  const ItemDesc &it = args.items[item];
+  if (it.kind == 0) chunk_body<EST_APPROX, XP_F32, AP, SCHEME, PC, 3, 0, false, false>(args, it, item, gc, smem_tab);
+  else if (it.kind == 1) chunk_body<EST_APPROX, XP_F32, AP, SCHEME, PC, 1, 0, false, false>(args, it, item, gc, smem_tab);
+  else chunk_body<EST_CORR, XP_F32, AP, SCHEME, PC, 1, 0, false, false>(args, it, item, gc, smem_tab);
 }
 
 }  // namespace mlmc

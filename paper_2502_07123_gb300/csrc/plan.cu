@@ -139,9 +139,12 @@ bool arena_events(Arena &A, size_t launches) {
   return true;
 }
 
+// launch_chunking: chunk the items of each launch together (see below); false
+// keeps every item's chunking independent of the other items (mlmc_level,
+// mlmc_estimate, whose results then equal the engine's, which chunks per item).
 mlmc_status plan_create_impl(mlmc_plan **out, const mlmc_work *work, int n_work, uint64_t seed,
-                             const mlmc_tuning *tuning, void *const *dumps, Arena *arena = nullptr,
-                             bool defer_copy = false) {
+                             const mlmc_tuning *tuning, void *const *dumps, bool launch_chunking,
+                             Arena *arena = nullptr, bool defer_copy = false) {
   if (!out || !work || n_work <= 0) return MLMC_EINVAL;
   mlmc_status s = ensure_ctx();
   if (s != MLMC_OK) return s;
@@ -160,7 +163,7 @@ mlmc_status plan_create_impl(mlmc_plan **out, const mlmc_work *work, int n_work,
   pl->exact_int.resize(n_work);
   pl->N.resize(n_work);
   std::vector<BuiltItem> built(n_work);
-  std::vector<int> item_threads(n_work);
+  std::vector<int> item_threads(n_work), item_spt(n_work);
   for (int i = 0; i < n_work; ++i) {
     s = build_item_cached(work[i], i, dumps ? dumps[i] : nullptr, built[i], pl->disc[i], pl->unit[i],
                           pl->exact_int[i]);
@@ -170,10 +173,32 @@ mlmc_status plan_create_impl(mlmc_plan **out, const mlmc_work *work, int n_work,
     if (o_threads) th = o_threads;
     if (o_spt) sp = o_spt;
     item_threads[i] = th;
+    item_spt[i] = sp;
     s = chunk_built(built[i], th, sp, g.num_sms);
     if (s != MLMC_OK) { delete pl; return s; }
     pl->N[i] = work[i].N;
     pl->path_steps += work[i].N << work[i].level;
+  }
+  // The nested estimator's 32-bit fixed-point families with Euler-Maruyama and
+  // a terminal payoff (15 approximate packed, 8 approximate one sample per
+  // thread, 10 correction) share one launch of the merged kernel (family 17)
+  // when more than one of them is present: the same chunk bodies, one grid.
+  {
+    auto kind_of = [&](int i) {
+      const BuiltItem &b = built[i];
+      if (b.scheme != MLMC_EULER || b.pc != PC_TERMINAL || b.it.dump) return -1;
+      return b.family == 15 ? 0 : (b.family == 8 ? 1 : (b.family == 10 ? 2 : -1));
+    };
+    int seen = 0;
+    for (int i = 0; i < n_work; ++i)
+      if (kind_of(i) >= 0 && built[i].it.n_chunks > 0) seen |= 1 << kind_of(i);
+    if (seen & (seen - 1))
+      for (int i = 0; i < n_work; ++i) {
+        const int k = kind_of(i);
+        if (k < 0) continue;
+        built[i].it.kind = k;
+        built[i].family = 17;
+      }
   }
   // group by kernel configuration; within a launch, most expensive chunks first
   std::map<std::tuple<int, int, int, int>, std::vector<int>> groups;
@@ -181,6 +206,26 @@ mlmc_status plan_create_impl(mlmc_plan **out, const mlmc_work *work, int n_work,
   for (int i = 0; i < n_work; ++i) {
     if (built[i].it.n_chunks == 0) { empty.push_back(i); continue; }
     groups[std::make_tuple(built[i].family, built[i].scheme, built[i].pc, item_threads[i])].push_back(i);
+  }
+  if (launch_chunking) {
+    // An item alone keeps at least four CTAs per SM (chunk_count), which splits
+    // the items of a long work list into chunks of a few dozen path-steps per
+    // thread.  When the launch as a whole has that many CTAs without the floor,
+    // each item is chunked by its path-steps per thread alone.
+    for (auto &kv : groups) {
+      std::vector<BuiltItem> alt;
+      uint64_t total = 0;
+      for (int i : kv.second) {
+        alt.push_back(built[i]);
+        if ((s = chunk_built(alt.back(), item_threads[i], item_spt[i], g.num_sms, false)) != MLMC_OK) {
+          delete pl;
+          return s;
+        }
+        total += alt.back().it.n_chunks;
+      }
+      if (total >= 4ULL * (uint64_t)g.num_sms)
+        for (size_t j = 0; j < kv.second.size(); ++j) built[kv.second[j]] = alt[j];
+    }
   }
   // launches are ordered by their most expensive CTA, so that the longest
   // chains (deep levels, exact paths) start first and the rest fill in
@@ -386,9 +431,9 @@ bool grow_pinned(T *&p, size_t &cap, size_t need) {
 // One synchronous pass on stream st: work list to the device through pinned
 // staging, the launch, the sums back through pinned staging, one stream sync.
 mlmc_status run_sync(const mlmc_work *work, int n_work, uint64_t seed, const mlmc_tuning *tuning,
-                     void *const *dumps, mlmc_sums *out, cudaStream_t st) {
+                     void *const *dumps, mlmc_sums *out, cudaStream_t st, bool launch_chunking) {
   mlmc_plan *pl = nullptr;
-  mlmc_status s = plan_create_impl(&pl, work, n_work, seed, tuning, dumps, &g.arena, true);
+  mlmc_status s = plan_create_impl(&pl, work, n_work, seed, tuning, dumps, launch_chunking, &g.arena, true);
   if (s != MLMC_OK) return s;
   Arena &A = g.arena;
   const size_t ni = pl->items.size();
@@ -421,7 +466,7 @@ mlmc_status run_sync(const mlmc_work *work, int n_work, uint64_t seed, const mlm
 // shapes from the tuning table), after one untimed launch.
 mlmc_status time_plan(const mlmc_work *work, int n_work, uint64_t seed, int reps, double *ms) {
   mlmc_plan *pl = nullptr;
-  mlmc_status s = plan_create_impl(&pl, work, n_work, seed, nullptr, nullptr);
+  mlmc_status s = plan_create_impl(&pl, work, n_work, seed, nullptr, nullptr, true);
   if (s != MLMC_OK) return s;
   std::vector<float> v;
   for (int r = 0; r <= reps && s == MLMC_OK; ++r) {
@@ -456,7 +501,7 @@ mlmc_status mlmc_level(int level, uint64_t N, const mlmc_params *p, mlmc_variant
   w.params = p; w.level = level; w.variant = (int32_t)v; w.first_sample = first_sample; w.N = N; w.stream = -1;
   mlmc_status s = ensure_ctx();
   if (s != MLMC_OK) return s;
-  return run_sync(&w, 1, seed, nullptr, nullptr, out, g.st);
+  return run_sync(&w, 1, seed, nullptr, nullptr, out, g.st, false);
 }
 
 mlmc_status mlmc_level_dump(int level, uint64_t N, const mlmc_params *p, mlmc_variant v, uint64_t seed,
@@ -470,13 +515,13 @@ mlmc_status mlmc_level_dump(int level, uint64_t N, const mlmc_params *p, mlmc_va
   mlmc_status s = ensure_ctx();
   if (s != MLMC_OK) return s;
   void *dumps[1] = {d_samples};
-  return run_sync(&w, 1, seed, nullptr, dumps, out, g.st);
+  return run_sync(&w, 1, seed, nullptr, dumps, out, g.st, false);
 }
 
 mlmc_status mlmc_plan_create(mlmc_plan **plan, const mlmc_work *work, int n_work, uint64_t seed,
                              const mlmc_tuning *tuning) {
   MLMC_API_LOCK();
-  return plan_create_impl(plan, work, n_work, seed, tuning, nullptr);
+  return plan_create_impl(plan, work, n_work, seed, tuning, nullptr, true);
 }
 
 mlmc_status mlmc_plan_launch(mlmc_plan *plan, void *stream) {
@@ -625,7 +670,7 @@ mlmc_status mlmc_run(const mlmc_work *work, int n_work, uint64_t seed, const mlm
                      mlmc_sums *out, void *stream) {
   MLMC_API_LOCK();
   if (!out) return MLMC_EINVAL;
-  return run_sync(work, n_work, seed, tuning, nullptr, out, (cudaStream_t)stream);
+  return run_sync(work, n_work, seed, tuning, nullptr, out, (cudaStream_t)stream, true);
 }
 
 }  // extern "C"

@@ -136,6 +136,8 @@ def load():
         "mlmc_engine_step": (st, [ctypes.c_void_p, ctypes.c_void_p, P(ctypes.c_int), P(ctypes.c_int)]),
         "mlmc_engine_poll": (st, [ctypes.c_void_p, ctypes.c_uint64, P(ctypes.c_double), P(ctypes.c_double),
                                   P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_double)]),
+        "mlmc_engine_request_info": (st, [ctypes.c_void_p, ctypes.c_uint64, P(ctypes.c_uint64), ctypes.c_int,
+                                          P(ctypes.c_double)]),
         "mlmc_engine_stats": (st, [ctypes.c_void_p, P(ctypes.c_uint64), P(ctypes.c_uint64), P(ctypes.c_uint64),
                                    P(ctypes.c_int)]),
         "mlmc_engine_graph_info": (st, [ctypes.c_void_p, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int),
@@ -485,6 +487,18 @@ class Engine:
         if not done.value:
             return None
         return dict(price=pr.value, stderr=se.value, L=lev.value, latency_s=lat.value)
+
+    def request_info(self, rid, cap_levels=21):
+        """Schedule N[l] = [N_approx_or_plain, N_corr] per level and the final
+        remaining-bias estimate of a completed request (mlmc_engine_request_info)."""
+        Nl = (ctypes.c_uint64 * (2 * cap_levels))()
+        rem = ctypes.c_double()
+        _check(load().mlmc_engine_request_info(self._h, rid, Nl, cap_levels, ctypes.byref(rem)),
+               "mlmc_engine_request_info")
+        N = [[int(Nl[2 * l]), int(Nl[2 * l + 1])] for l in range(cap_levels)]
+        while N and N[-1] == [0, 0]:
+            N.pop()
+        return dict(N=N, bias_estimate=rem.value)
 
     def stats(self):
         a, b, c = (ctypes.c_uint64() for _ in range(3))

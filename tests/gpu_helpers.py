@@ -64,3 +64,30 @@ def y_tolerance(variant, p, o):
     if variant in CORR:
         tol = tol + 2.0**-22 * np.abs(o["y"] - (o["pf"] - o["pc"])) + 1e-30
     return tol
+
+
+def schedule_bounds(mode, p, dumps, N, d=10):
+    """Bounds on |price_gpu - price_oracle| and |var_gpu - var_oracle| for a
+    schedule N[l][k] priced by the oracle with per-sample records `dumps`
+    (oracle.driver.price_on_schedule(..., dump=True)): the mean of each term's
+    per-sample bounds, and the bound those imply for its variance estimate;
+    enumerated terms (exact low levels) carry no variance."""
+    import math
+    from oracle import driver
+    plan = driver.estimator_plan(mode)
+    exact = driver.exact_levels(mode, d)
+    disc = math.exp(-p["r"] * p["T"])
+    tol_p, tol_v, terms = 0.0, 0.0, 0
+    for lev, row in enumerate(N):
+        for k, n in enumerate(row[:len(plan)]):
+            terms += 1
+            dm_rec = dumps[lev][k]
+            t = disc * y_tolerance(plan[k], p, dm_rec)
+            y = disc * dm_rec["y"]
+            dm = float(np.sum(t)) / n
+            tol_p += dm
+            if not (k == 0 and lev in exact):
+                m_ = float(np.mean(y))
+                d2 = float(np.sum((2 * np.abs(y) + t) * t)) / n
+                tol_v += (d2 + (2 * abs(m_) + dm) * dm) / n
+    return tol_p, tol_v, terms

@@ -9,14 +9,11 @@ approximate terms of levels 0 and 1.  Integer terms are then identical; the
 real-valued terms differ only by the per-sample FP32 path bound, so the price
 must agree within the mean of those bounds and the variance within the bound
 they imply for sum Y^2, plus FP64 rounding."""
-import math
-
-import numpy as np
 import pytest
 
-from oracle import core, driver
+from oracle import driver
 from paper_2502_07123_gb300 import workloads as W
-from tests.gpu_helpers import y_tolerance
+from tests.gpu_helpers import schedule_bounds
 
 pytestmark = pytest.mark.gpu
 
@@ -42,23 +39,7 @@ def test_estimate_equals_oracle_on_the_same_schedule(m, mode, payoff, seed):
     P = m.make_params(p, d=10, method=1, formats=fmts, rng_pack=1)
     r = m.mlmc_estimate(eps, P, mode, seed, 10)
     o = driver.price_on_schedule(p, seed, mode, r["N"], fmt_of_level=lambda lev: fmts[lev], pack=1, dump=True)
-    plan = driver.estimator_plan(mode)
-    exact = driver.exact_levels(mode, 10)
-    disc = math.exp(-p["r"] * p["T"])
-    tol_p, tol_v, terms = 0.0, 0.0, 0
-    for lev, row in enumerate(r["N"]):
-        for k, n in enumerate(row[:len(plan)]):
-            assert n > 0
-            terms += 1
-            d = o["dumps"][lev][k]
-            t = disc * y_tolerance(plan[k], p, d)           # per-sample bound (discounted)
-            y = disc * d["y"]
-            dm = float(np.sum(t)) / n                        # bound on the term's mean
-            tol_p += dm
-            if not (k == 0 and lev in exact):
-                m_ = float(np.mean(y))
-                d2 = float(np.sum((2 * np.abs(y) + t) * t)) / n   # bound on the mean of Y^2
-                tol_v += (d2 + (2 * abs(m_) + dm) * dm) / n
+    tol_p, tol_v, terms = schedule_bounds(mode, p, o["dumps"], r["N"])
     var_gpu = r["stderr"] ** 2
     assert abs(r["price"] - o["price"]) <= tol_p + 1e-12 * terms * (abs(o["price"]) + 1.0), \
         (r["price"], o["price"], tol_p)
