@@ -52,13 +52,13 @@ OPS_CORR_FIXED_EM = 54.0
 # SM issue peak: 152 SMs x 4 schedulers x 32 lanes x 2070 MHz (one warp instruction per scheduler per clock)
 ALU_PEAK_TOPS = 152 * 4 * 32 * 2.070e9 / 1e12
 # DRAM bytes (read + write) of the dominant launch, from one ncu capture of this
-# bench command (dram__bytes_read.sum + dram__bytes_write.sum, family 15 launch of
-# 51,213,208 path-steps):
-#   ncu --set full --clock-control none -k regex:level_kernel -c 3 -o prof \
+# bench command (dram__bytes_read.sum + dram__bytes_write.sum of the merged
+# nested launch, family 17, 80,148,728 path-steps):
+#   ncu --set full --clock-control none -k regex:^nested_kernel -s 2 -c 1 -o prof \
 #       python bench.py --steps 3 --warmup 3 --no-cpu-baseline --no-tte \
-#       --no-serving-sample --no-autotune --no-optimiser
+#       --no-serving-sample --no-optimiser
 # keyed by (family, path-steps per launch); another launch reports null
-DOMINANT_TRAFFIC = {(15, 51213208): 138240}
+DOMINANT_TRAFFIC = {(17, 80148728): 170752}
 
 
 def build_items(m, rank=0, formats=None):
@@ -150,48 +150,93 @@ def dominant_alone(m, torch, items, seed, tuning, plan, j, flush, stream, reps=1
         sub_plan.close()
 
 
-def oracle_step_sample(meta, cfg, fraction, rank=0):
-    """Time the CPU oracle on the first `fraction` of every work item; returns (path_steps, seconds)."""
+def _oracle_share(task):
+    """One host process's share of the oracle sample: (meta item, first sample,
+    count) triples; returns the path-steps simulated."""
     from oracle import core
+    shares, cfg = task
     steps = 0
-    t0 = time.perf_counter()
-    for it in meta:
-        n = max(1, int(it["N"] * fraction))
+    for it, first, n in shares:
         p = it["params"]
         fmt = W.default_format(p, it["level"]) if it["variant"] in (W.FIXED_APPROX, W.CORR_FIXED) else None
-        core.level(p, it["level"], rank * it["N"], n, it["variant"], cfg["seed"], request=it["request"],
+        core.level(p, it["level"], first, n, it["variant"], cfg["seed"], request=it["request"],
                    d=cfg["d"], method=cfg["method"], fmt=fmt,
                    pack=cfg["rng_pack"] if it["variant"] == W.FIXED_APPROX else 0)
         steps += n << it["level"]
-    return steps, time.perf_counter() - t0
+    return steps
+
+
+class OraclePool:
+    """The CPU oracle on every host core: spawned worker processes (started
+    after the GPU is in use, so never forked), each taking a contiguous share
+    of every work item's samples."""
+
+    def __init__(self):
+        import multiprocessing as mp
+        from oracle import build as ob
+        ob.build()
+        try:
+            self.cores = len(os.sched_getaffinity(0))
+        except AttributeError:
+            self.cores = os.cpu_count() or 1
+        self.pool = mp.get_context("spawn").Pool(self.cores)
+        self.pool.map(_oracle_share, [([], {})] * self.cores)   # start and import in every worker
+
+    def step(self, meta, cfg, fraction, rank=0):
+        """Samples [rank N, rank N + fraction N) of every item; returns (path_steps, seconds)."""
+        shares = [[] for _ in range(self.cores)]
+        for it in meta:
+            n = max(1, int(it["N"] * fraction))
+            base = rank * it["N"]
+            for c in range(self.cores):
+                lo, hi = n * c // self.cores, n * (c + 1) // self.cores
+                if hi > lo:
+                    shares[c].append((it, base + lo, hi - lo))
+        t0 = time.perf_counter()
+        steps = sum(self.pool.map(_oracle_share, [(sh, cfg) for sh in shares]))
+        return steps, time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
 
 
 def run_reference(args):
-    """Reference arm: the CPU oracle on the host cores, same workload, bounded sample per step."""
+    """Reference arm: the CPU oracle on all host cores, same workload, one step's
+    first `--ref-fraction` of every work item per step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from oracle import build as ob
-    ob.build()
-    items_meta = W.nested_config()
-    meta = items_meta["items"]
+    cfg = W.nested_config()
+    meta = cfg["items"]
     frac = args.ref_fraction
-    for _ in range(args.warmup):
-        oracle_step_sample(meta, items_meta, frac * 0.1)
-    tot_steps, tot_s = 0, 0.0
-    for _ in range(args.steps):
-        s, dt = oracle_step_sample(meta, items_meta, frac)
-        tot_steps += s
-        tot_s += dt
+    pool = OraclePool()
+    try:
+        for _ in range(args.warmup):
+            pool.step(meta, cfg, frac * 0.1)
+        tot_steps, tot_s = 0, 0.0
+        for _ in range(args.steps):
+            s_, dt = pool.step(meta, cfg, frac)
+            tot_steps += s_
+            tot_s += dt
+    finally:
+        pool.close()
     v = tot_steps / tot_s
+    sample = "first %.3g of every work item per step, split over %d processes" % (frac, pool.cores)
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "first %.3g of every work item" % frac},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "first %.3g of every work item per step" % frac},
+        "data": "synthetic", "config": workload_config(),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": pool.cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def workload_config():
+    """The benchmark's workload (the same for both arms)."""
+    cfg = W.nested_config()
+    return {"workload": WORKLOAD, "path_steps_per_step": sum(it["N"] << it["level"] for it in cfg["items"]),
+            "work_items": len(cfg["items"]), "l2": "flushed between steps (256 MiB write)"}
 
 
 def main():
@@ -202,8 +247,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--steps-per-thread", type=int, default=0)
-    ap.add_argument("--cpu-fraction", type=float, default=0.25)
-    ap.add_argument("--ref-fraction", type=float, default=0.1)
+    ap.add_argument("--cpu-fraction", type=float, default=1.0)
+    ap.add_argument("--ref-fraction", type=float, default=1.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tte", action="store_true")
     ap.add_argument("--no-serving-sample", action="store_true")
@@ -215,6 +260,8 @@ def main():
                          "library's fixed shape table, so that a profile of the same command sees the same launches)")
     ap.add_argument("--serving", action="store_true",
                     help="also run the batched (256 options) and serving (Poisson arrivals) workloads")
+    ap.add_argument("--serving-n", type=int, default=200,
+                    help="requests per arrival rate of --serving (full accuracy range)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -338,11 +385,9 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "i64+f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "path_steps_per_step": steps_per_launch,
-                   "work_items": len(items), "kernels_per_step": info["kernels"],
-                   "ctas_per_step": info["ctas"], "l2": "flushed between steps (256 MiB write)",
-                   "launch_shape": shape,
-                   "wall_s": t_wall},
+        "config": workload_config(),
+        "launch": {"kernels_per_step": info["kernels"], "ctas_per_step": info["ctas"], "launch_shape": shape,
+                   "path_steps_per_step_all_ranks": steps_per_launch, "wall_s": t_wall},
         "gpu_launches": info["kernels"] * args.steps,
         "kernel_ms": {str(f): sum(v) / len(v) for f, v in kern_ms.items()},
         "clocks": clocks.summary(),
@@ -365,14 +410,16 @@ def main():
         out["serving_sample"] = [serving_run(m, rate, n=200, eps_range=(1e-3, 1e-2)) for rate in (100, 1000, 10000)]
     if rank == 0 and world == 1 and args.serving:
         out["batched"] = batched_run(m)
-        out["serving"] = [serving_run(m, rate) for rate in (100, 1000, 10000)]
+        out["serving"] = [serving_run(m, rate, n=args.serving_n) for rate in (100, 1000, 10000)]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        from oracle import build as ob
-        ob.build()
-        steps_c, secs = oracle_step_sample(meta, cfg, args.cpu_fraction)
-        out["cpu_baseline"] = {"value": steps_c / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-                               "sample": "first %.3g of every work item of one step (%d path-steps, %.1f s)"
-                                         % (args.cpu_fraction, steps_c, secs)}
+        pool = OraclePool()
+        try:
+            steps_c, secs = pool.step(meta, cfg, args.cpu_fraction)
+        finally:
+            pool.close()
+        out["cpu_baseline"] = {"value": steps_c / secs, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+                               "sample": "first %.3g of every work item of one step (%d path-steps, %.1f s), "
+                                         "split over %d processes" % (args.cpu_fraction, steps_c, secs, pool.cores)}
     if rank == 0:
         print(json.dumps(out))
     plan.close()
@@ -490,34 +537,61 @@ def serving_run(m, rate, n=400, seed=11, mode=5, max_level=14, eps_range=(1e-4, 
     return out
 
 
-def sweep_run(m, torch, levels=(2, 6, 10), paths=1 << 22, sigmas=(0.1, 0.2, 0.4)):
-    """Level-kernel throughput sweep: Milstein, European / Asian / lookback, the
-    variants of the library, 2^22 paths per point; path-steps/s of one level
-    kernel launch by CUDA events (median of 5 after 2 warm-up launches)."""
+def sweep_run(m, torch, levels=(0, 2, 4, 6, 8, 10), sizes=(1 << 20, 1 << 24, 1 << 28), grid_n=1 << 22,
+              sigmas=(0.1, 0.2, 0.4)):
+    """Level-kernel throughput sweep (Milstein): path-steps/s of one level-kernel
+    launch by CUDA events (median of 5 after 2 warm-up launches, L2 flushed).
+    (a) sizes: European call, sigma = 0.2, every variant, N in `sizes` paths at
+    each level; (b) grid: European / Asian / lookback x sigma x level x variant
+    at `grid_n` paths.  A point holds at most 2^32 path-steps (2^28 for FP64,
+    which runs at 1/64 of the FP32 rate on this part): N is reduced to fit."""
     variants = (("fp64_exact", W.FP64_EXACT), ("fp32_exact", W.FP32_EXACT), ("fp16_approx", W.FP16_APPROX),
                 ("bf16_approx", W.BF16_APPROX), ("fixed_approx", W.FIXED_APPROX),
                 ("nested_corr_fixed", W.CORR_FIXED))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def point(P, lev, v, n):
+        plan = m.Plan([dict(params=P, level=lev, variant=v, N=n)], 7)
+        for _ in range(2):
+            plan.launch()
+        ts = []
+        for _ in range(5):
+            flush.zero_()
+            plan.launch()
+            ts.append(plan.kernel_time(0)[1])
+        plan.close()
+        ms = statistics.median(ts)
+        return ms, (n << lev) / (ms * 1e-3)
+
+    def cap(n, lev, v):
+        lim = 1 << (28 if v == W.FP64_EXACT else 32)
+        return max(1, min(n, lim >> lev))
+
     rows = []
+    params = {}
+
+    def P_of(pay, sig):
+        if (pay, sig) not in params:
+            p = W.params(payoff=pay, scheme=W.MILSTEIN, sigma=sig)
+            params[(pay, sig)] = m.make_params(p, d=10, method=1, formats=[W.default_format(p, k) for k in range(11)],
+                                               rng_pack=1)
+        return params[(pay, sig)]
+
+    for n0 in sizes:
+        for lev in levels:
+            for vname, v in variants:
+                n = cap(n0, lev, v)
+                ms, rate = point(P_of(W.EURO, 0.2), lev, v, n)
+                rows.append({"part": "sizes", "payoff": "euro", "sigma": 0.2, "level": lev, "variant": vname,
+                             "paths": n, "ms": ms, "path_steps_per_s": rate})
     for pay_name, pay in (("euro", W.EURO), ("asian", W.ASIAN), ("lookback", W.LOOKBACK)):
         for sig in sigmas:
-            p = W.params(payoff=pay, scheme=W.MILSTEIN, sigma=sig)
-            P = m.make_params(p, d=10, method=1, formats=[W.default_format(p, k) for k in range(11)], rng_pack=1)
             for lev in levels:
-                n = paths if lev < 10 else paths >> 2
                 for vname, v in variants:
-                    if v == W.FP64_EXACT and lev == 10:
-                        n = paths >> 4          # FP64 is slow on this part: a smaller sample
-                    plan = m.Plan([dict(params=P, level=lev, variant=v, N=n)], 7)
-                    for _ in range(2):
-                        plan.launch()
-                    ts = []
-                    for _ in range(5):
-                        plan.launch()
-                        ts.append(plan.kernel_time(0)[1])
-                    plan.close()
-                    ms = statistics.median(ts)
-                    rows.append({"payoff": pay_name, "sigma": sig, "level": lev, "variant": vname, "paths": n,
-                                 "ms": ms, "path_steps_per_s": (n << lev) / (ms * 1e-3)})
+                    n = cap(grid_n, lev, v)
+                    ms, rate = point(P_of(pay, sig), lev, v, n)
+                    rows.append({"part": "grid", "payoff": pay_name, "sigma": sig, "level": lev, "variant": vname,
+                                 "paths": n, "ms": ms, "path_steps_per_s": rate})
     return {"scheme": "milstein", "rows": rows}
 
 
