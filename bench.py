@@ -336,13 +336,13 @@ def main():
 
     # end-to-end: the same work through the host-buffer C-ABI call (plan build,
     # H2D of the work descriptors through pinned staging, launch, D2H of the
-    # sums, results as Python dicts) on a work list marshalled once
+    # sums, results as one structured array) on a work list marshalled once
     work = m.WorkList(items)
     e2e_ms = []
     for _ in range(max(3, min(10, args.steps))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        m.mlmc_run(work, cfg["seed"], tuning)
+        m.mlmc_run(work, cfg["seed"], tuning, raw=True)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_value = info["path_steps"] / (statistics.median(e2e_ms) * 1e-3)
 
@@ -460,7 +460,7 @@ def _accuracy(done, opts, max_level):
             "bias_over_target_at_max_level": sorted(ratio.values())}
 
 
-def batched_run(m, n=256, seed=7, mode=5, iters_per_launch=-4096, max_level=14):
+def batched_run(m, n=256, seed=7, mode=5, iters_per_launch=-4096, max_level=16):
     """The batched workload: all n options submitted at once to one engine; with a
     negative iters_per_launch the whole adaptive run of all of them is one graph
     launch iterating on the device (what mlmc_batch_estimate does, with the
@@ -495,7 +495,7 @@ def batched_run(m, n=256, seed=7, mode=5, iters_per_launch=-4096, max_level=14):
     return out
 
 
-def serving_run(m, rate, n=400, seed=11, mode=5, max_level=14, eps_range=(1e-4, 1e-2)):
+def serving_run(m, rate, n=400, seed=11, mode=5, max_level=16, eps_range=(1e-4, 1e-2)):
     """Poisson arrivals at `rate` req/s, options drawn as the batched workload;
     requests are admitted while others run (continuous batching)."""
     arrivals = W.poisson_arrivals(rate, n, seed)

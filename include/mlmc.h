@@ -456,7 +456,9 @@ mlmc_status mlmc_cost_model(int kind, double cost_per_step);
 /* ---- host helpers (no GPU needed) ---------------------------------------- */
 /* The default fixed-point schedule for a level (used when params->formats is NULL).
  * Fractional bits f = {12, 16+l, 14+l, 12+l, 12+l, 12+l, 14+l} clamped to [10, 24]
- * (one more bit per level, Sec. 6.3), then f_S capped at 21 and f_mul2 at f_S.  Integer bits e are the smallest with
+ * (one more bit per level, Sec. 6.3), then f_S capped at 21 and f_mul2 at f_S,
+ * and where e_S + f_S would exceed 30, f_S = max(10, 30 - e_S) (e_S then
+ * recomputed).  Integer bits e are the smallest with
  * |x| < 2^e (and e + f >= 1) for these bounds, h = T 2^-l (for con1, con2 and
  * S, whose bounds include rounded constants: x + 2^-(f+1) < 2^e):
  *   Z~ 8;  con1 max(|r| 2h, sigma^2 h / 2);  con2 sigma sqrt(h);

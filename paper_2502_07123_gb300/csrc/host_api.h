@@ -131,6 +131,8 @@ extern double g_cost[4];
 double cost_of_variant(int variant);
 // Launch shape per (kernel family, scheme, payoff class, level class).
 extern std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune;
+// Incremented on every change of g_tune (keys of the plan cache).
+extern uint64_t g_tune_gen;
 int level_class(int level);
 // Launch shape (CTA threads, fine path-steps per thread) of a kernel class.
 void tuning_for(int family, int scheme, int pc, int level, int *threads, int *spt);
@@ -171,8 +173,10 @@ mlmc_status build_item(const mlmc_work &w, int out_index, void *dump, BuiltItem 
 // build_item through the per-process cache of built constants.
 mlmc_status build_item_cached(const mlmc_work &w, int out_index, void *dump, BuiltItem &b, double &disc, int &unit,
                               int &exact_int);
-// Empty that cache (its items point to one device's tables).
+// Empty that cache and the plan cache (their items point to one device's tables).
 void item_cache_clear();
+// Empty mlmc_run's cache of host-built plans (plan.cu).
+void plan_cache_clear();
 // floor: at least four CTAs per SM for this item alone (see chunk_count).
 mlmc_status chunk_built(BuiltItem &b, int threads, int spt, int num_sms, bool floor = true);
 void make_round_keys(uint64_t seed, mlmc::RoundKeys &rk);

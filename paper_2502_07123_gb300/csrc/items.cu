@@ -37,7 +37,10 @@ struct CachedItem {
   int unit, exact_int;
 };
 std::unordered_map<std::string, CachedItem> g_item_cache;
-void item_cache_clear() { g_item_cache.clear(); }
+void item_cache_clear() {
+  g_item_cache.clear();
+  plan_cache_clear();
+}
 
 double g_cost[4] = {8.0, 1.0, 0.5, 1.5};
 const double g_cost_default[4] = {8.0, 1.0, 0.5, 1.5};
@@ -47,6 +50,7 @@ const double g_cost_default[4] = {8.0, 1.0, 0.5, 1.5};
 // mlmc_autotune installs measured choices.
 constexpr int TUNE_THREADS = 128, TUNE_SPT = 256;
 std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune;
+uint64_t g_tune_gen = 0;
 
 int level_class(int level) { return level <= 1 ? level : (level <= 4 ? 2 : (level <= 7 ? 3 : 4)); }
 
@@ -108,7 +112,15 @@ void default_format(const mlmc_params *p, int level, mlmc_format *out) {
   e[F_CON2] = bitlen_rounded(sig * std::sqrt(h), f[F_CON2]);
   e[F_MUL1] = bitlen(mul1_bound, f[F_MUL1]);
   e[F_SUM1] = bitlen(std::fabs(r) * 2.0 * h + mul1_bound, f[F_SUM1]);
-  e[F_S] = bitlen_rounded(std::max(S0 * std::exp(std::fabs(r) * T + 6.0 * sig * std::sqrt(T)), K), f[F_S]);
+  const double smax = std::max(S0 * std::exp(std::fabs(r) * T + 6.0 * sig * std::sqrt(T)), K);
+  e[F_S] = bitlen_rounded(smax, f[F_S]);
+  if (e[F_S] + f[F_S] > 30) {
+    // a wide S (high volatility, long maturity) gives up fractional bits down to
+    // 10 so that S keeps to 30 bits and the 32-bit datapath
+    f[F_S] = std::max(10, 30 - e[F_S]);
+    f[F_MUL2] = std::min(f[F_MUL2], f[F_S]);
+    e[F_S] = bitlen_rounded(smax, f[F_S]);
+  }
   e[F_MUL2] = e[F_S] + e[F_SUM1];
   for (int i = 0; i < 7; ++i) { out->e[i] = (int8_t)e[i]; out->f[i] = (int8_t)f[i]; }
 }

@@ -979,8 +979,10 @@ __device__ __forceinline__ int stage_chunk(const ItemDesc *items, int n_items, u
     // (Z~_j, sum1 of a fine step from Z~_j) for every index j: Method 1 and 2
     // values from the item's table, Method 3 values from its class lines (the
     // arithmetic of LevelSim::fixed_z); sum1 by the datapath's own step code.
-    // The table depends on the item's constants as well, so it is staged for
-    // every chunk.
+    // The table depends on the item's constants as well, so a persistent CTA
+    // (staged != nullptr) keeps it while its chunks stay in the same item.
+    if (staged && *staged == (const void *)&it) return item;
+    if (staged) *staged = (const void *)&it;
     const int n = 1 << it.d;
     int2 *dst = (int2 *)smem_tab;
     const M3Coef *m3 = (const M3Coef *)it.ztab;

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstddef>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -139,6 +140,47 @@ bool arena_events(Arena &A, size_t launches) {
   return true;
 }
 
+// Host part of a plan, as mlmc_run's plan cache keeps it.
+struct PlanHost {
+  std::vector<ItemDesc> items;
+  std::vector<LaunchRec> launches;
+  std::vector<double> disc;
+  std::vector<int> unit, exact_int;
+  std::vector<uint64_t> N;
+  uint64_t path_steps;
+  uint32_t total_chunks;
+  std::vector<uint32_t> empty_out;
+};
+std::unordered_map<std::string, PlanHost> g_plan_cache;
+void plan_cache_clear() { g_plan_cache.clear(); }
+
+// The bytes a plan's host part depends on: the device, the explicit shape, the
+// shape table's generation and the cost model, and every work item with its
+// parameters' contents (the format table by value, not by address).  Empty:
+// not cacheable.
+std::string plan_key(const mlmc_work *work, int n, const mlmc_tuning *tuning) {
+  std::string k;
+  k.reserve((size_t)n * 200 + 64);
+  auto put = [&](const void *x, size_t b) { k.append((const char *)x, b); };
+  const int32_t dev = g.device;
+  const int32_t th = tuning ? tuning->threads : 0, sp = tuning ? tuning->steps_per_thread : 0;
+  put(&dev, 4); put(&th, 4); put(&sp, 4); put(&n, 4);
+  put(&g_tune_gen, sizeof g_tune_gen);
+  put(g_cost, sizeof(double) * 4);
+  for (int i = 0; i < n; ++i) {
+    const mlmc_work &w = work[i];
+    const mlmc_params *p = w.params;
+    if (!p || (p->formats && (p->n_formats < 0 || p->n_formats > 64))) return std::string();
+    put(&w.level, 4); put(&w.variant, 4); put(&w.first_sample, 8); put(&w.N, 8); put(&w.stream, 4); put(&w.flags, 4);
+    put(p, offsetof(mlmc_params, formats));
+    put(&p->n_formats, sizeof(mlmc_params) - offsetof(mlmc_params, n_formats));
+    const int32_t nf = p->formats ? p->n_formats : -1;
+    put(&nf, 4);
+    if (p->formats) put(p->formats, sizeof(mlmc_format) * (size_t)p->n_formats);
+  }
+  return k;
+}
+
 // launch_chunking: chunk the items of each launch together (see below); false
 // keeps every item's chunking independent of the other items (mlmc_level,
 // mlmc_estimate, whose results then equal the engine's, which chunks per item).
@@ -157,114 +199,138 @@ mlmc_status plan_create_impl(mlmc_plan **out, const mlmc_work *work, int n_work,
   }
   mlmc_plan *pl = new (std::nothrow) mlmc_plan;
   if (!pl) return MLMC_ENOMEM;
-  pl->n_work = n_work;
-  pl->disc.resize(n_work);
-  pl->unit.resize(n_work);
-  pl->exact_int.resize(n_work);
-  pl->N.resize(n_work);
-  std::vector<BuiltItem> built(n_work);
-  std::vector<int> item_threads(n_work), item_spt(n_work);
-  for (int i = 0; i < n_work; ++i) {
-    s = build_item_cached(work[i], i, dumps ? dumps[i] : nullptr, built[i], pl->disc[i], pl->unit[i],
-                          pl->exact_int[i]);
-    if (s != MLMC_OK) { delete pl; return s; }
-    int th, sp;
-    tuning_for(built[i].family, built[i].scheme, built[i].pc, work[i].level, &th, &sp);
-    if (o_threads) th = o_threads;
-    if (o_spt) sp = o_spt;
-    item_threads[i] = th;
-    item_spt[i] = sp;
-    s = chunk_built(built[i], th, sp, g.num_sms);
-    if (s != MLMC_OK) { delete pl; return s; }
-    pl->N[i] = work[i].N;
-    pl->path_steps += work[i].N << work[i].level;
-  }
-  // The nested estimator's 32-bit fixed-point families with Euler-Maruyama and
-  // a terminal payoff (15 approximate packed, 8 approximate one sample per
-  // thread, 10 correction) share one launch of the merged kernel (family 17)
-  // when more than one of them is present: the same chunk bodies, one grid.
-  {
-    auto kind_of = [&](int i) {
-      const BuiltItem &b = built[i];
-      if (b.scheme != MLMC_EULER || b.pc != PC_TERMINAL || b.it.dump) return -1;
-      return b.family == 15 ? 0 : (b.family == 8 ? 1 : (b.family == 10 ? 2 : -1));
-    };
-    int seen = 0;
-    for (int i = 0; i < n_work; ++i)
-      if (kind_of(i) >= 0 && built[i].it.n_chunks > 0) seen |= 1 << kind_of(i);
-    if (seen & (seen - 1))
-      for (int i = 0; i < n_work; ++i) {
-        const int k = kind_of(i);
-        if (k < 0) continue;
-        built[i].it.kind = k;
-        built[i].family = 17;
-      }
-  }
-  // group by kernel configuration; within a launch, most expensive chunks first
-  std::map<std::tuple<int, int, int, int>, std::vector<int>> groups;
-  std::vector<int> empty;
-  for (int i = 0; i < n_work; ++i) {
-    if (built[i].it.n_chunks == 0) { empty.push_back(i); continue; }
-    groups[std::make_tuple(built[i].family, built[i].scheme, built[i].pc, item_threads[i])].push_back(i);
-  }
-  if (launch_chunking) {
-    // An item alone keeps at least four CTAs per SM (chunk_count), which splits
-    // the items of a long work list into chunks of a few dozen path-steps per
-    // thread.  When the launch as a whole has that many CTAs without the floor,
-    // each item is chunked by its path-steps per thread alone.
-    for (auto &kv : groups) {
-      std::vector<BuiltItem> alt;
-      uint64_t total = 0;
-      for (int i : kv.second) {
-        alt.push_back(built[i]);
-        if ((s = chunk_built(alt.back(), item_threads[i], item_spt[i], g.num_sms, false)) != MLMC_OK) {
-          delete pl;
-          return s;
-        }
-        total += alt.back().it.n_chunks;
-      }
-      if (total >= 4ULL * (uint64_t)g.num_sms)
-        for (size_t j = 0; j < kv.second.size(); ++j) built[kv.second[j]] = alt[j];
+  // The host part of the plan: items, chunking, launches (everything but the
+  // round keys and the device buffers).
+  auto build = [&]() -> mlmc_status {
+    pl->n_work = n_work;
+    pl->disc.resize(n_work);
+    pl->unit.resize(n_work);
+    pl->exact_int.resize(n_work);
+    pl->N.resize(n_work);
+    std::vector<BuiltItem> built(n_work);
+    std::vector<int> item_threads(n_work), item_spt(n_work);
+    for (int i = 0; i < n_work; ++i) {
+      s = build_item_cached(work[i], i, dumps ? dumps[i] : nullptr, built[i], pl->disc[i], pl->unit[i],
+                            pl->exact_int[i]);
+      if (s != MLMC_OK) return s;
+      int th, sp;
+      tuning_for(built[i].family, built[i].scheme, built[i].pc, work[i].level, &th, &sp);
+      if (o_threads) th = o_threads;
+      if (o_spt) sp = o_spt;
+      item_threads[i] = th;
+      item_spt[i] = sp;
+      s = chunk_built(built[i], th, sp, g.num_sms);
+      if (s != MLMC_OK) return s;
+      pl->N[i] = work[i].N;
+      pl->path_steps += work[i].N << work[i].level;
     }
-  }
-  // launches are ordered by their most expensive CTA, so that the longest
-  // chains (deep levels, exact paths) start first and the rest fill in
-  std::vector<std::pair<double, std::vector<int>>> order;
-  for (auto &kv : groups) {
-    auto &v = kv.second;
-    std::stable_sort(v.begin(), v.end(), [&](int a, int b) { return built[a].chunk_cost > built[b].chunk_cost; });
-    order.push_back({built[v[0]].chunk_cost, v});
-  }
-  std::stable_sort(order.begin(), order.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
-  uint32_t chunk = 0;
-  for (auto &o : order) {
-    LaunchRec L;
-    const BuiltItem &b0 = built[o.second[0]];
-    L.family = b0.family; L.scheme = b0.scheme; L.pc = b0.pc;
-    L.threads = item_threads[o.second[0]];
-    L.chunk0 = chunk;
-    L.item_off = (int)pl->items.size();
-    L.n_items = (int)o.second.size();
-    L.smem = 0;
-    L.dump = false;
-    for (int i : o.second) {
+    // The nested estimator's 32-bit fixed-point families with Euler-Maruyama and
+    // a terminal payoff (15 approximate packed, 8 approximate one sample per
+    // thread, 10 correction) share one launch of the merged kernel (family 17)
+    // when more than one of them is present: the same chunk bodies, one grid.
+    {
+      auto kind_of = [&](int i) {
+        const BuiltItem &b = built[i];
+        if (b.scheme != MLMC_EULER || b.pc != PC_TERMINAL || b.it.dump) return -1;
+        return b.family == 15 ? 0 : (b.family == 8 ? 1 : (b.family == 10 ? 2 : -1));
+      };
+      int seen = 0;
+      for (int i = 0; i < n_work; ++i)
+        if (kind_of(i) >= 0 && built[i].it.n_chunks > 0) seen |= 1 << kind_of(i);
+      if (seen & (seen - 1))
+        for (int i = 0; i < n_work; ++i) {
+          const int k = kind_of(i);
+          if (k < 0) continue;
+          built[i].it.kind = k;
+          built[i].family = 17;
+        }
+    }
+    // group by kernel configuration; within a launch, most expensive chunks first
+    std::map<std::tuple<int, int, int, int>, std::vector<int>> groups;
+    std::vector<int> empty;
+    for (int i = 0; i < n_work; ++i) {
+      if (built[i].it.n_chunks == 0) { empty.push_back(i); continue; }
+      groups[std::make_tuple(built[i].family, built[i].scheme, built[i].pc, item_threads[i])].push_back(i);
+    }
+    if (launch_chunking) {
+      // An item alone keeps at least four CTAs per SM (chunk_count), which splits
+      // the items of a long work list into chunks of a few dozen path-steps per
+      // thread.  When the launch as a whole has that many CTAs without the floor,
+      // each item is chunked by its path-steps per thread alone.
+      for (auto &kv : groups) {
+        std::vector<BuiltItem> alt;
+        uint64_t total = 0;
+        for (int i : kv.second) {
+          alt.push_back(built[i]);
+          if ((s = chunk_built(alt.back(), item_threads[i], item_spt[i], g.num_sms, false)) != MLMC_OK) {
+            return s;
+          }
+          total += alt.back().it.n_chunks;
+        }
+        if (total >= 4ULL * (uint64_t)g.num_sms)
+          for (size_t j = 0; j < kv.second.size(); ++j) built[kv.second[j]] = alt[j];
+      }
+    }
+    // launches are ordered by their most expensive CTA, so that the longest
+    // chains (deep levels, exact paths) start first and the rest fill in
+    std::vector<std::pair<double, std::vector<int>>> order;
+    for (auto &kv : groups) {
+      auto &v = kv.second;
+      std::stable_sort(v.begin(), v.end(), [&](int a, int b) { return built[a].chunk_cost > built[b].chunk_cost; });
+      order.push_back({built[v[0]].chunk_cost, v});
+    }
+    std::stable_sort(order.begin(), order.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+    uint32_t chunk = 0;
+    for (auto &o : order) {
+      LaunchRec L;
+      const BuiltItem &b0 = built[o.second[0]];
+      L.family = b0.family; L.scheme = b0.scheme; L.pc = b0.pc;
+      L.threads = item_threads[o.second[0]];
+      L.chunk0 = chunk;
+      L.item_off = (int)pl->items.size();
+      L.n_items = (int)o.second.size();
+      L.smem = 0;
+      L.dump = false;
+      for (int i : o.second) {
+        ItemDesc it = built[i].it;
+        it.chunk_begin = chunk;
+        chunk += it.n_chunks;
+        L.smem = std::max(L.smem, built[i].smem);
+        L.dump = L.dump || it.dump != nullptr;
+        pl->items.push_back(it);
+      }
+      L.n_chunks = chunk - L.chunk0;
+      pl->launches.push_back(L);
+    }
+    for (int i : empty) {
       ItemDesc it = built[i].it;
       it.chunk_begin = chunk;
-      chunk += it.n_chunks;
-      L.smem = std::max(L.smem, built[i].smem);
-      L.dump = L.dump || it.dump != nullptr;
       pl->items.push_back(it);
+      pl->empty_out.push_back(it.out_index);
     }
-    L.n_chunks = chunk - L.chunk0;
-    pl->launches.push_back(L);
+    pl->total_chunks = chunk;
+    return MLMC_OK;
+  };
+  // mlmc_run's plans are kept by the bytes of everything their host part
+  // depends on, so that a work list run again skips the build.
+  const bool cacheable = arena && launch_chunking && !dumps;
+  std::string key = cacheable ? plan_key(work, n_work, tuning) : std::string();
+  auto hit = key.empty() ? g_plan_cache.end() : g_plan_cache.find(key);
+  if (hit != g_plan_cache.end()) {
+    const PlanHost &h = hit->second;
+    pl->n_work = n_work;
+    pl->items = h.items; pl->launches = h.launches; pl->disc = h.disc; pl->unit = h.unit;
+    pl->exact_int = h.exact_int; pl->N = h.N; pl->path_steps = h.path_steps; pl->total_chunks = h.total_chunks;
+    pl->empty_out = h.empty_out;
+  } else {
+    if ((s = build()) != MLMC_OK) { delete pl; return s; }
+    if (!key.empty()) {
+      if (g_plan_cache.size() >= 64) g_plan_cache.clear();
+      g_plan_cache.emplace(std::move(key), PlanHost{pl->items, pl->launches, pl->disc, pl->unit, pl->exact_int,
+                                                   pl->N, pl->path_steps, pl->total_chunks, pl->empty_out});
+    }
   }
-  for (int i : empty) {
-    ItemDesc it = built[i].it;
-    it.chunk_begin = chunk;
-    pl->items.push_back(it);
-    pl->empty_out.push_back(it.out_index);
-  }
-  pl->total_chunks = chunk;
+  const uint32_t chunk = pl->total_chunks;
   make_round_keys(seed, pl->rk);
   const size_t ni = pl->items.size();
   if (arena) {
@@ -642,6 +708,7 @@ mlmc_status mlmc_autotune(const mlmc_work *work, int n_work, uint64_t seed, int 
           seen.push_back(sig);
           if (pass == 0) continue;
           g_tune[k] = std::make_pair(th, sp);
+          ++g_tune_gen;
           double ms = 0.0;
           if ((s = time_plan(work, n_work, seed, reps, &ms)) != MLMC_OK) return s;
           // a candidate must make the work list 2% faster than the best so far
@@ -652,6 +719,7 @@ mlmc_status mlmc_autotune(const mlmc_work *work, int n_work, uint64_t seed, int 
           }
         }
     g_tune[k] = std::make_pair(best_t, best_s);
+    ++g_tune_gen;
     if (chosen)
       for (int i : ix) {
         chosen[i].threads = best_t;
@@ -664,6 +732,7 @@ mlmc_status mlmc_autotune(const mlmc_work *work, int n_work, uint64_t seed, int 
 void mlmc_tuning_reset(void) {
   MLMC_API_LOCK();
   g_tune.clear();
+  ++g_tune_gen;
 }
 
 mlmc_status mlmc_run(const mlmc_work *work, int n_work, uint64_t seed, const mlmc_tuning *tuning,

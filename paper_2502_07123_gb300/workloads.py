@@ -54,7 +54,8 @@ def default_format(p: dict, level: int) -> dict:
     this is a stated schedule: fractional bits grow by one per level (the
     d_S,l+1 = d_S,l + 1 trend of Sec. 6.3) and follow the size ordering of
     Sec. 6.3 (con1 ~ h, con2/mul1/sum1/mul2 ~ sqrt(h), S ~ 1), clamped to
-    [10, 24], with S (and mul2) capped at 21 fractional bits.  Integer bits bound each variable's magnitude (for the rounded
+    [10, 24], with S (and mul2) capped at 21 fractional bits, and at 30 - e_S
+    (not below 10) where S's integer bits would make it wider than 30 bits.  Integer bits bound each variable's magnitude (for the rounded
     constants con1, con2, S0 and K: their values rounded to f bits):
       Z     : |Z~| < 8 for every table size d <= 16 (coarse sums are exact),
       con1  : max(|r| 2h, sigma^2 h / 2) (the Milstein constant shares it),
@@ -89,6 +90,12 @@ def default_format(p: dict, level: int) -> dict:
         "sum1": _bitlen(abs(r) * 2.0 * h + mul1_bound, f["sum1"]),
         "S": _bitlen_rounded(max(S0 * math.exp(abs(r) * T + 6.0 * sig * math.sqrt(T)), K), f["S"]),
     }
+    if e["S"] + f["S"] > 30:
+        # a wide S (high volatility, long maturity) gives up fractional bits down
+        # to 10 so that S keeps to 30 bits
+        f["S"] = max(10, 30 - e["S"])
+        f["mul2"] = min(f["mul2"], f["S"])
+        e["S"] = _bitlen_rounded(max(S0 * math.exp(abs(r) * T + 6.0 * sig * math.sqrt(T)), K), f["S"])
     e["mul2"] = e["S"] + e["sum1"]
     return {"e": [e[v] for v in FORMAT_VARS], "f": [f[v] for v in FORMAT_VARS]}
 

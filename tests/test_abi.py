@@ -51,12 +51,19 @@ def test_struct_layouts(lib):
 
 def test_default_format_matches_input_schedule(lib):
     from paper_2502_07123_gb300 import workloads as W
+    wide = 0
     for over in ({}, {"sigma": 0.4}, {"sigma": 0.1, "r": 0.0}, {"S0": 80.0, "K": 120.0, "T": 2.0},
-                 {"scheme": W.MILSTEIN, "sigma": 0.5, "T": 0.25}):
+                 {"scheme": W.MILSTEIN, "sigma": 0.5, "T": 0.25},
+                 {"S0": 120.0, "K": 80.0, "sigma": 0.5, "T": 2.0}, {"S0": 5000.0, "K": 5000.0, "sigma": 0.3}):
         p = W.params(**over)
         P = lib.make_params(p)
         for lev in range(0, 21):
-            assert lib.mlmc_default_format(P, lev) == W.default_format(p, lev), (over, lev)
+            f = W.default_format(p, lev)
+            assert lib.mlmc_default_format(P, lev) == f, (over, lev)
+            # S keeps to 30 bits (32-bit datapath) unless that would leave fewer than 10 fractional bits
+            assert f["e"][6] + f["f"][6] <= 30 or f["f"][6] == 10
+            wide += f["f"][6] < min(21, 14 + lev)
+    assert wide > 0     # the cases above include options whose S gives up fractional bits
 
 
 def test_strerror_and_version(lib):

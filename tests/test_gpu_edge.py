@@ -187,3 +187,53 @@ def test_worklist_and_raw_results(m):
         assert raw[i]["sum"] == x["sum"] and raw[i]["sum2"] == x["sum2"] and raw[i]["isum"] == x["isum"]
         assert (int(raw[i]["isum2_hi"]) << 64 | int(raw[i]["isum2_lo"])) == x["isum2"]
         assert c[i]["sum"] == x["sum"] and c[i]["n"] == x["n"]
+
+
+def test_merged_nested_launch_equals_separate_items(m):
+    # approximate (packed and one sample per thread) and correction items of the
+    # 32-bit fixed-point datapath share one launch of the merged kernel (family
+    # 17); each item's sums equal those of the item run alone: integer sums bit
+    # for bit, real sums to FP64 rounding (the chunkings differ)
+    p = W.params(payoff=W.DIGITAL)
+    P = _P(m, p, pack=1)
+    items = [dict(params=P, level=0, variant=W.FIXED_APPROX, N=300_001, first_sample=7),
+             dict(params=P, level=3, variant=W.FIXED_APPROX, N=5_000),
+             dict(params=P, level=6, variant=W.FIXED_APPROX, N=40_000),
+             dict(params=P, level=1, variant=W.CORR_FIXED, N=20_000, first_sample=3),
+             dict(params=P, level=7, variant=W.CORR_FIXED, N=3_000)]
+    plan = m.Plan(items, 21)
+    try:
+        assert plan.info()["kernels"] == 1 and plan.launch_info(0)[0] == 17
+        plan.launch()
+        res = plan.results()
+    finally:
+        plan.close()
+    for it, r in zip(items, res):
+        one = m.mlmc_level(it["level"], it["N"], P, it["variant"], 21, it.get("first_sample", 0))
+        if it["variant"] == W.FIXED_APPROX:
+            assert r["isum"] == one["isum"] and r["isum2"] == one["isum2"] and r["sum"] == one["sum"]
+        else:
+            assert abs(r["sum"] - one["sum"]) <= 1e-12 * (r["n"] * r["sum2"]) ** 0.5
+            assert abs(r["sum2"] - one["sum2"]) <= 1e-12 * r["sum2"]
+
+
+def test_run_plan_cache_follows_the_work_list(m):
+    # mlmc_run keeps host-built plans by the contents of the work list: the same
+    # list gives the same bits, and a parameter changed in place (the same ctypes
+    # objects, so the same pointers) gives the result of the new parameters
+    p = W.params()
+    P = _P(m, p, pack=1)
+    items = [dict(params=P, level=2, variant=W.FIXED_APPROX, N=50_000),
+             dict(params=P, level=4, variant=W.CORR_FIXED, N=3_000)]
+    work = m.WorkList(items)
+
+    def sums(res):   # everything but the launch's device time
+        return [{k: v for k, v in r.items() if k != "seconds"} for r in res]
+    a = sums(m.mlmc_run(work, 5))
+    assert sums(m.mlmc_run(work, 5)) == a
+    P.sigma = 0.25
+    c = m.mlmc_run(work, 5)
+    ref = m.mlmc_level(2, 50_000, P, W.FIXED_APPROX, 5)
+    assert c[0]["isum"] == ref["isum"] and c[0]["isum2"] == ref["isum2"] and c[0]["isum"] != a[0]["isum"]
+    P.sigma = p["sigma"]
+    assert sums(m.mlmc_run(work, 5)) == a
