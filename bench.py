@@ -151,19 +151,21 @@ def dominant_alone(m, torch, items, seed, tuning, plan, j, flush, stream, reps=1
 
 
 def _oracle_share(task):
-    """One host process's share of the oracle sample: (meta item, first sample,
-    count) triples; returns the path-steps simulated."""
+    """One host process's share of the oracle sample: (item index, meta item,
+    first sample, count) quadruples; returns the path-steps simulated and the
+    oracle's sums of each share."""
     from oracle import core
     shares, cfg = task
-    steps = 0
-    for it, first, n in shares:
+    steps, sums = 0, []
+    for k, it, first, n in shares:
         p = it["params"]
         fmt = W.default_format(p, it["level"]) if it["variant"] in (W.FIXED_APPROX, W.CORR_FIXED) else None
-        core.level(p, it["level"], first, n, it["variant"], cfg["seed"], request=it["request"],
-                   d=cfg["d"], method=cfg["method"], fmt=fmt,
-                   pack=cfg["rng_pack"] if it["variant"] == W.FIXED_APPROX else 0)
+        o, _ = core.level(p, it["level"], first, n, it["variant"], cfg["seed"], request=it["request"],
+                          d=cfg["d"], method=cfg["method"], fmt=fmt,
+                          pack=cfg["rng_pack"] if it["variant"] == W.FIXED_APPROX else 0)
         steps += n << it["level"]
-    return steps
+        sums.append((k, o["sum"], o["sum2"], o["isum"], o["isum2"]))
+    return steps, sums
 
 
 class OraclePool:
@@ -182,19 +184,31 @@ class OraclePool:
         self.pool = mp.get_context("spawn").Pool(self.cores)
         self.pool.map(_oracle_share, [([], {})] * self.cores)   # start and import in every worker
 
-    def step(self, meta, cfg, fraction, rank=0):
-        """Samples [rank N, rank N + fraction N) of every item; returns (path_steps, seconds)."""
+    def step(self, meta, cfg, fraction, rank=0, sums=None):
+        """Samples [rank N, rank N + fraction N) of every item; returns (path_steps,
+        seconds); with a list `sums`, also each item's oracle sums (undiscounted:
+        sum, sum2, exact integer isum, isum2) appended to it."""
         shares = [[] for _ in range(self.cores)]
-        for it in meta:
+        for k, it in enumerate(meta):
             n = max(1, int(it["N"] * fraction))
             base = rank * it["N"]
             for c in range(self.cores):
                 lo, hi = n * c // self.cores, n * (c + 1) // self.cores
                 if hi > lo:
-                    shares[c].append((it, base + lo, hi - lo))
+                    shares[c].append((k, it, base + lo, hi - lo))
         t0 = time.perf_counter()
-        steps = sum(self.pool.map(_oracle_share, [(sh, cfg) for sh in shares]))
-        return steps, time.perf_counter() - t0
+        out = self.pool.map(_oracle_share, [(sh, cfg) for sh in shares])
+        dt = time.perf_counter() - t0
+        if sums is not None:
+            acc = [[0.0, 0.0, 0, 0] for _ in meta]
+            for _, part in out:
+                for k, s1, s2, i1, i2 in part:
+                    acc[k][0] += s1
+                    acc[k][1] += s2
+                    acc[k][2] += i1
+                    acc[k][3] += i2
+            sums.extend(acc)
+        return sum(x[0] for x in out), dt
 
     def close(self):
         self.pool.close()
@@ -413,13 +427,28 @@ def main():
         out["serving"] = [serving_run(m, rate, n=args.serving_n) for rate in (100, 1000, 10000)]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         pool = OraclePool()
+        osums = []
         try:
-            steps_c, secs = pool.step(meta, cfg, args.cpu_fraction)
+            steps_c, secs = pool.step(meta, cfg, args.cpu_fraction, sums=osums)
         finally:
             pool.close()
         out["cpu_baseline"] = {"value": steps_c / secs, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
                                "sample": "first %.3g of every work item of one step (%d path-steps, %.1f s), "
                                          "split over %d processes" % (args.cpu_fraction, steps_c, secs, pool.cores)}
+        if args.cpu_fraction == 1.0:
+            # the step's results against the FP64 oracle on the same samples: the
+            # integer (approximate) items exactly, the real-valued (correction)
+            # items by |sum difference| / sqrt(n sum2)
+            int_equal, real_err = 0, []
+            for it, r, o in zip(meta, res, osums):
+                disc = math.exp(-it["params"]["r"] * it["params"]["T"])
+                if r["exact_int"]:
+                    int_equal += int(r["isum"] == o[2] and r["isum2"] == o[3])
+                else:
+                    real_err.append(abs(r["sum"] - disc * o[0]) / math.sqrt(r["n"] * disc * disc * o[1]))
+            out["cpu_baseline"]["step_vs_oracle"] = {
+                "integer_items_bit_equal": "%d of %d" % (int_equal, sum(1 for r in res if r["exact_int"])),
+                "real_items_max_rel_err_of_sum": max(real_err) if real_err else None}
     if rank == 0:
         print(json.dumps(out))
     plan.close()

@@ -751,6 +751,15 @@ template <int P> using PayTag = std::integral_constant<int, P>;
 // run's live in registers through the group.
 __device__ __forceinline__ void opaque(uint64_t &x) { asm volatile("" : "+l"(x)); }
 
+// The item fields the group code reads, copied into registers once per chunk
+// (read through the item reference they would be loaded again for every
+// group: the kernel's stores to global memory might alias them).
+struct GroupCtx {
+  uint32_t ctr2, ctr3;
+  int d, level, enumerate, lanes;
+  uint64_t first, last;
+};
+
 // The samples of group g of a chunk, for a level class LC known at compile
 // time (0: level 0, 1: level 1, 2: levels >= 2).  A group is one Philox call's
 // worth of packs (4 on level 0, 2 on level 1) or, from level 2, one pack over
@@ -760,7 +769,7 @@ __device__ __forceinline__ void opaque(uint64_t &x) { asm volatile("" : "+l"(x))
 // group's straight-line code); full: the same known at run time; PAY: the
 // terminal payoff when fixed at compile time (0 European, 1 digital, -1 not).
 template <int LC, bool E, bool FULL, int PAY, bool DUMP, class Sim, class Acc>
-__device__ __forceinline__ void run_group(Sim &sim, Acc &acc, const LaunchArgs &args, const ItemDesc &it, uint64_t g,
+__device__ __forceinline__ void run_group(Sim &sim, Acc &acc, const LaunchArgs &args, const GroupCtx &it, uint64_t g,
                                           bool full, uint64_t first, uint64_t last, mlmc_sample_rec *dump) {
   constexpr int KP = Sim::KPV;
   if constexpr (LC == 2) {
@@ -842,9 +851,9 @@ __device__ __forceinline__ void run_group(Sim &sim, Acc &acc, const LaunchArgs &
 // PAYF: the terminal payoff of the lazy run (terminal payoff classes).
 template <int LC, int PAYF, bool DUMP, int EST, int XP, int AP, int PC, class Sim>
 __device__ __forceinline__ void group_loop(Sim &sim, ThreadAcc<EST, XP> &acc, const LaunchArgs &args,
-                                           const ItemDesc &it, uint64_t gbeg, uint32_t ng, uint32_t rf0, uint32_t rf1,
+                                           const GroupCtx &it, uint64_t gbeg, uint32_t ng, uint32_t rf0, uint32_t rf1,
                                            bool lazy, mlmc_sample_rec *dump) {
-  const uint64_t first = it.first, last = it.first + it.N;
+  const uint64_t first = it.first, last = it.last;
   // Real-valued estimators flush their float pairs every `flush_groups`
   // groups (at most REAL_FLUSH_SAMPLES samples).
   constexpr bool REAL = EST != EST_APPROX && !(XP == XP_F64 && EST == EST_EXACT);
@@ -916,8 +925,11 @@ __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDes
   mlmc_sample_rec *dump = DUMP ? (mlmc_sample_rec *)it.dump : nullptr;
   const bool lazy = Sim::LAZY && !DUMP && it.ff.lazy;
   const int lc = it.level >= 2 ? 2 : it.level;
+  GroupCtx gx;
+  gx.ctr2 = it.ctr2; gx.ctr3 = it.ctr3; gx.d = it.d; gx.level = it.level; gx.enumerate = it.enumerate;
+  gx.lanes = it.lanes; gx.first = it.first; gx.last = it.first + it.N;
   auto loop = [&](auto lctag, auto paytag) {
-    group_loop<decltype(lctag)::value, decltype(paytag)::value, DUMP, EST, XP, AP, PC>(sim, acc, args, it, gbeg, ng,
+    group_loop<decltype(lctag)::value, decltype(paytag)::value, DUMP, EST, XP, AP, PC>(sim, acc, args, gx, gbeg, ng,
                                                                                       rf0, rf1, lazy, dump);
   };
   using L0 = std::integral_constant<int, 0>;

@@ -231,9 +231,9 @@ def test_run_plan_cache_follows_the_work_list(m):
         return [{k: v for k, v in r.items() if k != "seconds"} for r in res]
     a = sums(m.mlmc_run(work, 5))
     assert sums(m.mlmc_run(work, 5)) == a
-    P.sigma = 0.25
+    P.K = 102.0      # within the format table built for K = 100
     c = m.mlmc_run(work, 5)
     ref = m.mlmc_level(2, 50_000, P, W.FIXED_APPROX, 5)
     assert c[0]["isum"] == ref["isum"] and c[0]["isum2"] == ref["isum2"] and c[0]["isum"] != a[0]["isum"]
-    P.sigma = p["sigma"]
+    P.K = p["K"]
     assert sums(m.mlmc_run(work, 5)) == a
