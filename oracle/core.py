@@ -14,12 +14,16 @@ from . import build as _build
 EURO, DIGITAL, ASIAN, LOOKBACK = 0, 1, 2, 3
 EULER, MILSTEIN = 0, 1
 FP64_EXACT, FP32_EXACT, FP16_APPROX, BF16_APPROX, FIXED_APPROX, CORR_FIXED, CORR_FP16, CORR_BF16 = range(8)
+# half-precision increments with S in FP32
+FP16S_APPROX, BF16S_APPROX, CORR_FP16S, CORR_BF16S = range(8, 12)
 VARIANT_NAMES = ["fp64_exact", "fp32_exact", "fp16_approx", "bf16_approx", "fixed_approx",
-                 "corr_fixed", "corr_fp16", "corr_bf16"]
+                 "corr_fixed", "corr_fp16", "corr_bf16", "fp16s_approx", "bf16s_approx", "corr_fp16s", "corr_bf16s"]
+CORR_VARIANTS = (CORR_FIXED, CORR_FP16, CORR_BF16, CORR_FP16S, CORR_BF16S)
+APPROX_ONLY_VARIANTS = (FP16_APPROX, BF16_APPROX, FIXED_APPROX, FP16S_APPROX, BF16S_APPROX)
 
 
 def has_exact(v):
-    return v in (FP64_EXACT, FP32_EXACT, CORR_FIXED, CORR_FP16, CORR_BF16)
+    return v in (FP64_EXACT, FP32_EXACT) + CORR_VARIANTS
 
 
 def has_approx(v):
@@ -29,16 +33,16 @@ def has_approx(v):
 def approx_rep(v):
     if v in (FIXED_APPROX, CORR_FIXED):
         return "fixed"
-    if v in (FP16_APPROX, CORR_FP16):
+    if v in (FP16_APPROX, CORR_FP16, FP16S_APPROX, CORR_FP16S):
         return "fp16"
-    if v in (BF16_APPROX, CORR_BF16):
+    if v in (BF16_APPROX, CORR_BF16, BF16S_APPROX, CORR_BF16S):
         return "bf16"
     return None
 
 
 def default_stream(v):
     """Approximate-only estimators draw from stream 1, all others from stream 0."""
-    return 1 if v in (FP16_APPROX, BF16_APPROX, FIXED_APPROX) else 0
+    return 1 if v in APPROX_ONLY_VARIANTS else 0
 
 
 class Params(ctypes.Structure):
@@ -203,7 +207,7 @@ def level(p, lev, first, N, variant, seed, request=0, stream=None, d=10, method=
     S = Sums()
     out = np.zeros(N, dtype=SAMPLE_DTYPE) if dump else None
     perm = None
-    if method == 2 and variant in (CORR_FIXED, CORR_FP16, CORR_BF16):
+    if method == 2 and variant in CORR_VARIANTS:
         perm = np.ascontiguousarray(tables.m2_optimise(d, fields)["pi"], dtype=np.uint32)
     st = lib().or_level(ctypes.byref(P), int(lev), int(first), int(N), int(variant), int(seed),
                         int(request), int(stream), int(d),

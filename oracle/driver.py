@@ -55,6 +55,8 @@ def bias_estimate(means, alpha=1.0):
 
 
 PLAIN_FP64, PLAIN_FP32, NESTED_FIXED, NESTED_FP16, NESTED_BF16, NESTED_FIXED_EXACT_LOW, NESTED_FP16_EXACT_LOW = range(7)
+# half-precision increments with S in FP32
+NESTED_FP16S, NESTED_BF16S, NESTED_FP16S_EXACT_LOW, NESTED_BF16S_EXACT_LOW = range(7, 11)
 
 # Levels whose approximate level difference is computed exactly, by enumerating
 # the 2^(d 2^l) combinations of table cells (d 2^l <= EXACT_MAX_BITS).
@@ -62,7 +64,7 @@ EXACT_MAX_BITS = 20
 
 
 def exact_levels(mode, d):
-    if mode not in (NESTED_FIXED_EXACT_LOW, NESTED_FP16_EXACT_LOW):
+    if mode not in (NESTED_FIXED_EXACT_LOW, NESTED_FP16_EXACT_LOW, NESTED_FP16S_EXACT_LOW, NESTED_BF16S_EXACT_LOW):
         return set()
     return {lev for lev in (0, 1) if (d << lev) <= EXACT_MAX_BITS}
 
@@ -77,6 +79,10 @@ def estimator_plan(mode):
         NESTED_BF16: [core.BF16_APPROX, core.CORR_BF16],
         NESTED_FIXED_EXACT_LOW: [core.FIXED_APPROX, core.CORR_FIXED],
         NESTED_FP16_EXACT_LOW: [core.FP16_APPROX, core.CORR_FP16],
+        NESTED_FP16S: [core.FP16S_APPROX, core.CORR_FP16S],
+        NESTED_BF16S: [core.BF16S_APPROX, core.CORR_BF16S],
+        NESTED_FP16S_EXACT_LOW: [core.FP16S_APPROX, core.CORR_FP16S],
+        NESTED_BF16S_EXACT_LOW: [core.BF16S_APPROX, core.CORR_BF16S],
     }[mode]
 
 
@@ -184,7 +190,7 @@ def price_on_schedule(p, seed, mode, N, fmt_of_level=None, d=10, method=1, reque
         for k, n in enumerate(row[:len(plan)]):
             v = plan[k]
             is_exact = k == 0 and lev in exact
-            approx_only = v in (core.FIXED_APPROX, core.FP16_APPROX, core.BF16_APPROX)
+            approx_only = v in core.APPROX_ONLY_VARIANTS
             fmt = fmt_of_level(lev) if fmt_of_level else None
             s, dm = core.level(p, lev, 0, n, v, seed, request=request, d=d, method=method, fmt=fmt,
                                dump=dump, pack=pack if approx_only and not is_exact else 0,

@@ -35,7 +35,9 @@ enum { OR_EURO = 0, OR_DIGITAL = 1, OR_ASIAN = 2, OR_LOOKBACK = 3 };
 enum { OR_EULER = 0, OR_MILSTEIN = 1 };
 enum {
   OR_FP64_EXACT = 0, OR_FP32_EXACT = 1, OR_FP16_APPROX = 2, OR_BF16_APPROX = 3,
-  OR_FIXED_APPROX = 4, OR_CORR_FIXED = 5, OR_CORR_FP16 = 6, OR_CORR_BF16 = 7
+  OR_FIXED_APPROX = 4, OR_CORR_FIXED = 5, OR_CORR_FP16 = 6, OR_CORR_BF16 = 7,
+  /* half-precision increments with S in FP32 */
+  OR_FP16S_APPROX = 8, OR_BF16S_APPROX = 9, OR_CORR_FP16S = 10, OR_CORR_BF16S = 11
 };
 /* fixed-point variable order (Algorithm 1): Z~, con1, con2, mul1, sum1, mul2, S */
 enum { V_Z = 0, V_CON1 = 1, V_CON2 = 2, V_MUL1 = 3, V_SUM1 = 4, V_MUL2 = 5, V_S = 6 };
@@ -312,13 +314,18 @@ static uint32_t exact_J(const level_cfg *c, uint64_t s, int i) {
   return J;
 }
 
-static int has_exact(int v) { return v == OR_FP64_EXACT || v == OR_FP32_EXACT || v >= OR_CORR_FIXED; }
+static int is_corr(int v) {
+  return v == OR_CORR_FIXED || v == OR_CORR_FP16 || v == OR_CORR_BF16 || v == OR_CORR_FP16S || v == OR_CORR_BF16S;
+}
+static int has_exact(int v) { return v == OR_FP64_EXACT || v == OR_FP32_EXACT || is_corr(v); }
 static int has_approx(int v) { return v != OR_FP64_EXACT && v != OR_FP32_EXACT; }
 static int approx_kind(int v) { /* 0 fixed, 1 fp16, 2 bf16 */
   if (v == OR_FIXED_APPROX || v == OR_CORR_FIXED) return 0;
-  if (v == OR_FP16_APPROX || v == OR_CORR_FP16) return 1;
+  if (v == OR_FP16_APPROX || v == OR_CORR_FP16 || v == OR_FP16S_APPROX || v == OR_CORR_FP16S) return 1;
   return 2;
 }
+/* half-precision increments with S (and its path functionals) in FP32 */
+static int s32_path(int v) { return v >= OR_FP16S_APPROX; }
 
 /* ---- exact path (FP64), literal paper form of the coarse path ---------- */
 static void exact_sample(const level_cfg *c, uint64_t s, or_sample *out) {
@@ -476,6 +483,22 @@ static double half_step(const level_cfg *c, double S, double z, double c1, int m
   return rh_sum(c, S, mul2, bad);
 }
 
+/* The same increment sum1 in half precision; S in FP32: mul2 = fl32(S sum1),
+ * S = fl32(S + mul2), one rounding each (sum1 is exact in FP32). */
+static float half_step_s32(const level_cfg *c, float S, double z, double c1, int milstein_m, int *bad) {
+  double mul1 = rh(c, c->hc2 * z);
+  double sum1 = rh_sum(c, c1, mul1, bad);
+  if (milstein_m) {
+    double sq = rh(c, z * z);
+    double sqm = rh_sum(c, sq, -(double)milstein_m, bad);
+    double mul3 = rh(c, c->hc3 * sqm);
+    sum1 = rh_sum(c, sum1, mul3, bad);
+  }
+  const float s1 = (float)sum1;
+  const float mul2 = S * s1;
+  return S + mul2;
+}
+
 /* FP32 payoff of a half path (each float operation rounds once) */
 typedef struct { float first, acc, last, minv; int64_t steps; } h_acc;
 static void h_start(h_acc *a, float s0) { a->first = s0; a->acc = 0.5f * s0; a->last = s0; a->minv = s0; a->steps = 0; }
@@ -505,21 +528,33 @@ static int64_t h_payoff(const level_cfg *c, const h_acc *a) {
 
 static int half_sample(const level_cfg *c, uint64_t s, or_sample *out) {
   int milstein = c->p->scheme == OR_MILSTEIN;
+  int s32 = s32_path(c->variant);
   int bad = 0;
   double S = c->hS0, Sc = c->hS0, zprev = 0.0;
+  float Sf = (float)c->p->S0, Scf = Sf;   /* FP32 S of the s32 variants */
   h_acc af, ac;
-  h_start(&af, (float)c->hS0);
-  h_start(&ac, (float)c->hS0);
+  h_start(&af, s32 ? Sf : (float)c->hS0);
+  h_start(&ac, s32 ? Sf : (float)c->hS0);
   for (int i = 0; i < c->n; ++i) {
     uint32_t J = approx_draw(c, s, i);
     uint32_t idx; int neg;
     approx_index(J, c->d, &idx, &neg);
     double z = neg ? -c->ztab[idx] : c->ztab[idx];
-    S = half_step(c, S, z, c->hc1, milstein ? 1 : 0, &bad);
+    if (s32) {
+      Sf = half_step_s32(c, Sf, z, c->hc1, milstein ? 1 : 0, &bad);
+      S = Sf;
+    } else {
+      S = half_step(c, S, z, c->hc1, milstein ? 1 : 0, &bad);
+    }
     h_push(&af, (float)S);
     if (c->level > 0 && (i & 1)) {
       double zc = rh_sum(c, zprev, z, &bad);
-      Sc = half_step(c, Sc, zc, c->hc1c, milstein ? 2 : 0, &bad);
+      if (s32) {
+        Scf = half_step_s32(c, Scf, zc, c->hc1c, milstein ? 2 : 0, &bad);
+        Sc = Scf;
+      } else {
+        Sc = half_step(c, Sc, zc, c->hc1c, milstein ? 2 : 0, &bad);
+      }
       h_push(&ac, (float)Sc);
     }
     zprev = z;
@@ -556,7 +591,7 @@ int or_level(const or_params *p, int level, uint64_t first, uint64_t N, int vari
              uint64_t seed, uint32_t request, uint32_t stream,
              int d, const double *ztab, const or_format *fmt, int pack, int enumerate,
              or_sums *sums, or_sample *dump, const uint32_t *perm) {
-  if (level < 0 || level > 20 || variant < 0 || variant > 7) return OR_EINVAL;
+  if (level < 0 || level > 20 || variant < 0 || variant > 11) return OR_EINVAL;
   if (enumerate && (has_exact(variant) || level > 1 || (d << level) > 24)) return OR_EINVAL;
   /* packed draws only feed approximate-only estimators (their uniforms need d bits, not 32) */
   if (pack && (has_exact(variant) || d < 2 || 32 / d < 2)) return OR_EINVAL;
@@ -566,7 +601,7 @@ int or_level(const or_params *p, int level, uint64_t first, uint64_t N, int vari
   c.p = p; c.level = level; c.n = 1 << level; c.variant = variant; c.d = d; c.pack = pack;
   c.enumerate = enumerate;
   c.seed = seed; c.request = request; c.stream = stream;
-  c.perm = variant >= OR_CORR_FIXED ? perm : 0;   /* the correction's exact path */
+  c.perm = is_corr(variant) ? perm : 0;   /* the correction's exact path */
   c.h = ldexp(p->T, -level);
   c.ztab = ztab;
   int approx = has_approx(variant), exact = has_exact(variant);
