@@ -445,7 +445,9 @@ def main():
                 if r["exact_int"]:
                     int_equal += int(r["isum"] == o[2] and r["isum2"] == o[3])
                 else:
-                    real_err.append(abs(r["sum"] - disc * o[0]) / math.sqrt(r["n"] * disc * disc * o[1]))
+                    scale = math.sqrt(r["n"] * disc * disc * o[1])    # >= sum |Y|; zero if every Y is
+                    diff = abs(r["sum"] - disc * o[0])
+                    real_err.append(diff / scale if scale > 0 else (0.0 if diff == 0 else float("inf")))
             out["cpu_baseline"]["step_vs_oracle"] = {
                 "integer_items_bit_equal": "%d of %d" % (int_equal, sum(1 for r in res if r["exact_int"])),
                 "real_items_max_rel_err_of_sum": max(real_err) if real_err else None}
@@ -712,7 +714,8 @@ def _engine_solve(eng, P, eps, mode, seed):
 def time_to_eps(m, torch, eps=1e-3, seeds=tuple(range(1, 12)), formats_opt=None):
     """Wall time of mlmc_estimate at RMS error eps (European call, median of the
     seeds): plain FP32 MLMC against the nested estimator (Sec. 2.2) with its
-    approximate path in fixed point, binary16 and bfloat16, each with the Method-1
+    approximate path in fixed point, binary16 and bfloat16 (all variables, or
+    the increments with S in FP32: fp16s / bf16s), each with the Method-1
     and the Method-3 table (Sec. 3.1, 3.3); the paper's nested estimator samples
     every level, the exact-low modes compute the approximate terms of levels 0-1
     by enumeration instead.  With formats_opt, the fixed-point runs again with the
@@ -730,8 +733,12 @@ def time_to_eps(m, torch, eps=1e-3, seeds=tuple(range(1, 12)), formats_opt=None)
         configs += [("nested_fixed_" + tag, m.MODE_NESTED_FIXED, P(method)),
                     ("nested_fp16_" + tag, m.MODE_NESTED_FP16, P(method)),
                     ("nested_bf16_" + tag, m.MODE_NESTED_BF16, P(method)),
+                    ("nested_fp16s_" + tag, m.MODE_NESTED_FP16S, P(method)),
+                    ("nested_bf16s_" + tag, m.MODE_NESTED_BF16S, P(method)),
                     ("nested_fixed_exact_low_" + tag, m.MODE_NESTED_FIXED_EXACT_LOW, P(method)),
-                    ("nested_fp16_exact_low_" + tag, m.MODE_NESTED_FP16_EXACT_LOW, P(method))]
+                    ("nested_fp16_exact_low_" + tag, m.MODE_NESTED_FP16_EXACT_LOW, P(method)),
+                    ("nested_fp16s_exact_low_" + tag, m.MODE_NESTED_FP16S_EXACT_LOW, P(method)),
+                    ("nested_bf16s_exact_low_" + tag, m.MODE_NESTED_BF16S_EXACT_LOW, P(method))]
     if formats_opt:
         configs += [("nested_fixed_m1_optimised_widths", m.MODE_NESTED_FIXED, P(1, formats_opt)),
                     ("nested_fixed_exact_low_m1_optimised_widths", m.MODE_NESTED_FIXED_EXACT_LOW, P(1, formats_opt))]

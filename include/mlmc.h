@@ -71,7 +71,14 @@ typedef enum {
   MLMC_FIXED_APPROX = 4,
   MLMC_NESTED_CORR_FIXED = 5,
   MLMC_NESTED_CORR_FP16 = 6,
-  MLMC_NESTED_CORR_BF16 = 7
+  MLMC_NESTED_CORR_BF16 = 7,
+  /* binary16 / bfloat16 increments (one rounding per operation, as above)
+   * with S, its running average and minimum in FP32: mul2 = fl32(S sum1),
+   * S = fl32(S + mul2) */
+  MLMC_FP16S_APPROX = 8,
+  MLMC_BF16S_APPROX = 9,
+  MLMC_NESTED_CORR_FP16S = 10,
+  MLMC_NESTED_CORR_BF16S = 11
 } mlmc_variant;
 
 /* Fixed-point format of the Algorithm-1 variables on one level (Sec. 4.1):
@@ -234,7 +241,10 @@ mlmc_status mlmc_plan_info(const mlmc_plan *plan, int *kernels, uint64_t *ctas,
 /* Device time (ms, CUDA events on the kernel's own stream) of level kernel k of
  * the last launch, and its family (0 exact FP32, 1 exact FP64, 2 approximate
  * fixed, 3 approximate binary16, 4 approximate bfloat16, 5/6/7 correction with
- * fixed / binary16 / bfloat16).  Waits for that kernel.  MLMC_ENOTREADY before
+ * fixed / binary16 / bfloat16; 8-16 the same estimators' other datapaths
+ * (fast fixed point, packed draws), 17 the merged nested launch, 18-23 binary16 /
+ * bfloat16 with FP32 S: approximate 18 / 19, correction 20 / 21, approximate
+ * with packed draws 22 / 23).  Waits for that kernel.  MLMC_ENOTREADY before
  * the first launch, MLMC_EINVAL for k out of range. */
 mlmc_status mlmc_plan_kernel_time(const mlmc_plan *plan, int k, int *family, double *ms);
 /* Level-kernel launch k of the plan (0 <= k < kernels of mlmc_plan_info):
@@ -280,8 +290,10 @@ void mlmc_tuning_reset(void);
  * L from 2 up to max_level, 10^4 initial samples per level and estimator,
  * sample counts N = ceil(lambda sqrt(V/C)) with lambda = (eps^2/2)^-1 sum sqrt(V C)
  * over every (level, estimator) term.  mode: 0 plain FP64, 1 plain FP32,
- * 2 nested fixed point, 3 nested binary16, 4 nested bfloat16, 5 and 6 nested
- * fixed point / binary16 whose approximate terms on levels 0 and 1 (when
+ * 2 nested fixed point, 3 nested binary16, 4 nested bfloat16, 7 and 8 nested
+ * binary16 / bfloat16 increments with S in FP32; 5, 6, 9 and 10 nested
+ * fixed point / binary16 / binary16 with FP32 S / bfloat16 with FP32 S whose
+ * approximate terms on levels 0 and 1 (when
  * d 2^l <= 20) are computed exactly, by enumerating the 2^(d 2^l) combinations
  * of table cells (MLMC_WORK_ENUMERATE), and then carry no variance and take no
  * further samples (the approximate Normal has finitely many values; the

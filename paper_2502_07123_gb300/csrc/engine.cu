@@ -360,7 +360,7 @@ struct Request {
 };
 
 int exact_mask_of(int mode, int d) {
-  if (mode != 5 && mode != 6) return 0;
+  if (mode != 5 && mode != 6 && mode != 9 && mode != 10) return 0;
   int m = 0;
   for (int l = 0; l <= 1; ++l)
     if ((d << l) <= 20) m |= 1 << l;
@@ -381,6 +381,8 @@ bool mode_variants(int mode, int &ne, int v[2]) {
     case 4: ne = 2; v[0] = MLMC_BF16_APPROX; v[1] = MLMC_NESTED_CORR_BF16; return true;
     case 5: ne = 2; v[0] = MLMC_FIXED_APPROX; v[1] = MLMC_NESTED_CORR_FIXED; return true;
     case 6: ne = 2; v[0] = MLMC_FP16_APPROX; v[1] = MLMC_NESTED_CORR_FP16; return true;
+    case 7: case 9: ne = 2; v[0] = MLMC_FP16S_APPROX; v[1] = MLMC_NESTED_CORR_FP16S; return true;
+    case 8: case 10: ne = 2; v[0] = MLMC_BF16S_APPROX; v[1] = MLMC_NESTED_CORR_BF16S; return true;
     default: return false;
   }
 }

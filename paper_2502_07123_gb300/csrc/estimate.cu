@@ -48,6 +48,10 @@ bool est_plan(int mode, EstPlan &e) {
     case 4: e = {2, {MLMC_BF16_APPROX, MLMC_NESTED_CORR_BF16}, false}; return true;
     case 5: e = {2, {MLMC_FIXED_APPROX, MLMC_NESTED_CORR_FIXED}, true}; return true;
     case 6: e = {2, {MLMC_FP16_APPROX, MLMC_NESTED_CORR_FP16}, true}; return true;
+    case 7: e = {2, {MLMC_FP16S_APPROX, MLMC_NESTED_CORR_FP16S}, false}; return true;
+    case 8: e = {2, {MLMC_BF16S_APPROX, MLMC_NESTED_CORR_BF16S}, false}; return true;
+    case 9: e = {2, {MLMC_FP16S_APPROX, MLMC_NESTED_CORR_FP16S}, true}; return true;
+    case 10: e = {2, {MLMC_BF16S_APPROX, MLMC_NESTED_CORR_BF16S}, true}; return true;
     default: return false;
   }
 }

@@ -113,6 +113,8 @@ enum { F_Z = 0, F_CON1 = 1, F_CON2 = 2, F_MUL1 = 3, F_SUM1 = 4, F_MUL2 = 5, F_S 
 bool params_ok(const mlmc_params *p);
 // Fields n of Method 2 (icdf_fields, 0 meaning 2).
 int m2_fields_of(const mlmc_params *p);
+// Approximate-only estimator variants (integer samples, stream 1, packable draws).
+bool approx_only_variant(int v);
 // Samples per pack (3 with packed draws for approximate-only estimators, else 1).
 int pack_lanes(const mlmc_params *p, int variant);
 void default_format(const mlmc_params *p, int level, mlmc_format *out);

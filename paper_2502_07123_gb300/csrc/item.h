@@ -14,7 +14,8 @@ enum Xp : int { XP_NONE = 0, XP_F32 = 1, XP_F64 = 2 };
 // AP_FIXED is the general fixed-point datapath (64-bit, saturating every
 // variable); AP_FX32 / AP_FX64 are the fast datapath for formats whose bounds
 // the host has proven (32-bit values, S in 32 or 64 bits, only S range-checked).
-enum Ap : int { AP_NONE = 0, AP_FIXED = 1, AP_F16 = 2, AP_BF16 = 3, AP_FX32 = 4, AP_FX64 = 5 };
+// AP_F16S / AP_BF16S: binary16 / bfloat16 increments with S in FP32.
+enum Ap : int { AP_NONE = 0, AP_FIXED = 1, AP_F16 = 2, AP_BF16 = 3, AP_FX32 = 4, AP_FX64 = 5, AP_F16S = 6, AP_BF16S = 7 };
 // payoff classes that need different path functionals
 enum PayClass : int { PC_TERMINAL = 0, PC_ASIAN = 1, PC_LOOKBACK = 2 };
 

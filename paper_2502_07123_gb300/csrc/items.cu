@@ -83,8 +83,13 @@ bool params_ok(const mlmc_params *p) {
 int m2_fields_of(const mlmc_params *p) { return p->icdf_fields ? p->icdf_fields : 2; }
 
 // Lanes per pack of an approximate-only estimator (packed draws need 3 fields of d bits).
+bool approx_only_variant(int v) {
+  return v == MLMC_FIXED_APPROX || v == MLMC_FP16_APPROX || v == MLMC_BF16_APPROX || v == MLMC_FP16S_APPROX ||
+         v == MLMC_BF16S_APPROX;
+}
+
 int pack_lanes(const mlmc_params *p, int variant) {
-  const bool approx_only = variant == MLMC_FIXED_APPROX || variant == MLMC_FP16_APPROX || variant == MLMC_BF16_APPROX;
+  const bool approx_only = approx_only_variant(variant);
   if (!approx_only || !p->rng_pack) return 1;
   return 32 / p->icdf_bits == 3 ? 3 : 0;  // 0: packing requested but unsupported for this d
 }
@@ -170,7 +175,8 @@ bool format_ok_gpu(const mlmc_format &F, bool milstein, int d) {
 }
 
 int family_of(int variant) {
-  // 0 exact f32, 1 exact f64, 2 approx fixed, 3 approx f16, 4 approx bf16, 5 corr fixed, 6 corr f16, 7 corr bf16
+  // 0 exact f32, 1 exact f64, 2 approx fixed, 3 approx f16, 4 approx bf16, 5 corr fixed, 6 corr f16, 7 corr bf16,
+  // 18 / 19 approx f16 / bf16 with FP32 S, 20 / 21 corr f16 / bf16 with FP32 S
   switch (variant) {
     case MLMC_FP32_EXACT: return 0;
     case MLMC_FP64_EXACT: return 1;
@@ -179,13 +185,17 @@ int family_of(int variant) {
     case MLMC_BF16_APPROX: return 4;
     case MLMC_NESTED_CORR_FIXED: return 5;
     case MLMC_NESTED_CORR_FP16: return 6;
-    default: return 7;
+    case MLMC_NESTED_CORR_BF16: return 7;
+    case MLMC_FP16S_APPROX: return 18;
+    case MLMC_BF16S_APPROX: return 19;
+    case MLMC_NESTED_CORR_FP16S: return 20;
+    default: return 21;
   }
 }
 int cost_kind_of(int variant) {
   if (variant == MLMC_FP64_EXACT) return 0;
   if (variant == MLMC_FP32_EXACT) return 1;
-  if (variant == MLMC_FIXED_APPROX || variant == MLMC_FP16_APPROX || variant == MLMC_BF16_APPROX) return 2;
+  if (approx_only_variant(variant)) return 2;
   return 3;
 }
 
@@ -198,6 +208,12 @@ cudaError_t launch_by_family(int fam, int scheme, int pc, dim3 grid, dim3 block,
     case 15: return launch_approx_fx32_p3(scheme, pc, grid, block, smem, st, a, occ);
     case 16: return launch_approx_fx64_p3(scheme, pc, grid, block, smem, st, a, occ);
     case 17: return launch_nested_fx32(scheme, pc, grid, block, smem, st, a, occ);
+    case 18: return launch_approx_f16s(scheme, pc, grid, block, smem, st, a, occ);
+    case 19: return launch_approx_bf16s(scheme, pc, grid, block, smem, st, a, occ);
+    case 20: return launch_corr_f16s(scheme, pc, grid, block, smem, st, a, occ);
+    case 21: return launch_corr_bf16s(scheme, pc, grid, block, smem, st, a, occ);
+    case 22: return launch_approx_f16s_p3(scheme, pc, grid, block, smem, st, a, occ);
+    case 23: return launch_approx_bf16s_p3(scheme, pc, grid, block, smem, st, a, occ);
     case 8: return launch_approx_fx32(scheme, pc, grid, block, smem, st, a, occ);
     case 9: return launch_approx_fx64(scheme, pc, grid, block, smem, st, a, occ);
     case 10: return launch_corr_fx32(scheme, pc, grid, block, smem, st, a, occ);
@@ -363,7 +379,7 @@ mlmc_status build_item(const mlmc_work &w, int out_index, void *dump, BuiltItem 
                        int &exact_int, TableSource &src) {
   const mlmc_params *p = w.params;
   if (!params_ok(p)) return MLMC_EINVAL;
-  if (w.level < 0 || w.level > 20 || w.variant < 0 || w.variant > 7) return MLMC_EINVAL;
+  if (w.level < 0 || w.level > 20 || w.variant < 0 || w.variant > 11) return MLMC_EINVAL;
   if (w.stream < -1 || w.stream > 255) return MLMC_EINVAL;
   const int lev = w.level;
   // word index s 2^l + i and the group index must stay below 2^62
@@ -372,8 +388,7 @@ mlmc_status build_item(const mlmc_work &w, int out_index, void *dump, BuiltItem 
   std::memset(&it, 0, sizeof it);
   const int v = w.variant;
   const bool approx = !(v == MLMC_FP32_EXACT || v == MLMC_FP64_EXACT);
-  const int stream = w.stream >= 0 ? w.stream
-                     : (v == MLMC_FIXED_APPROX || v == MLMC_FP16_APPROX || v == MLMC_BF16_APPROX ? 1 : 0);
+  const int stream = w.stream >= 0 ? w.stream : (approx_only_variant(v) ? 1 : 0);
   it.first = w.first_sample;
   it.N = w.N;
   it.level = lev;
@@ -391,7 +406,7 @@ mlmc_status build_item(const mlmc_work &w, int out_index, void *dump, BuiltItem 
   int KP = pack_lanes(p, v);
   if (enumerate) {
     // every combination of table cells once: approximate-only, levels 0-1, samples [0, 2^(d 2^l))
-    const bool approx_only = v == MLMC_FIXED_APPROX || v == MLMC_FP16_APPROX || v == MLMC_BF16_APPROX;
+    const bool approx_only = approx_only_variant(v);
     const int bits = p->icdf_bits << lev;
     if (!approx_only || lev > 1 || bits > 24 || w.first_sample != 0 || w.N != (1ULL << bits)) return MLMC_EINVAL;
     KP = 1;
@@ -428,7 +443,8 @@ mlmc_status build_item(const mlmc_work &w, int out_index, void *dump, BuiltItem 
   bool fast = false, fast64 = false;
   if (approx) {
     const bool fixed = (v == MLMC_FIXED_APPROX || v == MLMC_NESTED_CORR_FIXED);
-    const bool bf = (v == MLMC_BF16_APPROX || v == MLMC_NESTED_CORR_BF16);
+    const bool bf = (v == MLMC_BF16_APPROX || v == MLMC_NESTED_CORR_BF16 || v == MLMC_BF16S_APPROX ||
+                     v == MLMC_NESTED_CORR_BF16S);
     const int rep = fixed ? REP_FIXED : (bf ? REP_BF16 : REP_FP16);
     int fZ = 0;
     if (fixed) {
@@ -503,7 +519,7 @@ mlmc_status build_item(const mlmc_work &w, int out_index, void *dump, BuiltItem 
     if (s != MLMC_OK) return s;
     it.ztab = tab;
     b.smem = p->icdf_method != 3 ? (size_t)(1 << p->icdf_bits) * (fixed ? 4 : 2) : sizeof(M3Coef);
-    exact_int = (v == MLMC_FIXED_APPROX || v == MLMC_FP16_APPROX || v == MLMC_BF16_APPROX) ? 1 : 0;
+    exact_int = approx_only_variant(v) ? 1 : 0;
     if (p->icdf_method == 2 && !exact_int) {
       // Method 2 coupling: the correction's exact path reads the interval ranks
       const uint16_t *perm = nullptr;
@@ -527,6 +543,8 @@ mlmc_status build_item(const mlmc_work &w, int out_index, void *dump, BuiltItem 
       case 4: b.family = 14; break;
       case 8: b.family = 15; break;
       case 9: b.family = 16; break;
+      case 18: b.family = 22; break;
+      case 19: b.family = 23; break;
       default: return MLMC_EINVAL;
     }
   }

@@ -30,5 +30,12 @@ MLMC_FAMILY(launch_approx_fx64_p3)
 // family 17: merged nested launch of families 15, 8 and 10 (Euler-Maruyama,
 // terminal payoffs; per-item kind in ItemDesc::kind)
 MLMC_FAMILY(launch_nested_fx32)
+// families 18-23: binary16 / bfloat16 increments with S in FP32
+MLMC_FAMILY(launch_approx_f16s)
+MLMC_FAMILY(launch_approx_bf16s)
+MLMC_FAMILY(launch_corr_f16s)
+MLMC_FAMILY(launch_corr_bf16s)
+MLMC_FAMILY(launch_approx_f16s_p3)
+MLMC_FAMILY(launch_approx_bf16s_p3)
 #undef MLMC_FAMILY
 }  // namespace mlmc

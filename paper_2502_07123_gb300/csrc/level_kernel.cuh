@@ -39,6 +39,7 @@ template <int XP> struct XType { using T = float; };
 template <> struct XType<XP_F64> { using T = double; };
 template <int AP> struct HType { using T = __half; };
 template <> struct HType<AP_BF16> { using T = __nv_bfloat16; };
+template <> struct HType<AP_BF16S> { using T = __nv_bfloat16; };
 
 constexpr int MAX_THREADS = 256;
 // Register budget: the approximate fixed-point Euler kernel with terminal payoffs
@@ -105,9 +106,11 @@ struct LevelSim {
   static constexpr bool MIL = (SCHEME == 1);
   static constexpr bool FAST = (AP == AP_FX32 || AP == AP_FX64);
   static constexpr bool FIXED = (AP == AP_FIXED || FAST);
-  static constexpr bool HALF = (AP == AP_F16 || AP == AP_BF16);
+  static constexpr bool HALF = (AP == AP_F16 || AP == AP_BF16 || AP == AP_F16S || AP == AP_BF16S);
+  // half increments with S (and its average and minimum) in FP32
+  static constexpr bool S32 = (AP == AP_F16S || AP == AP_BF16S);
   // packed half draws: lanes 0 and 1 share paired (x2) registers, lane 2 is scalar
-  static constexpr bool PAIR = HALF && KP == 3;
+  static constexpr bool PAIR = HALF && KP == 3 && !S32;
   using AS = typename std::conditional<AP == AP_FX32, int32_t, int64_t>::type;  // fixed-point S
   // saturation flag of the fast datapath: OR of (clamped ^ unclamped) for a 32-bit S
   using SatT = typename std::conditional<AP == AP_FX32, uint32_t, bool>::type;
@@ -124,6 +127,9 @@ struct LevelSim {
   using HO = HalfOps<H>;
   using HO2 = HalfOps2<H>;
   using H2 = typename HO2::T;
+  using HS = typename std::conditional<S32, float, H>::type;   // S of the half datapaths
+  static __device__ __forceinline__ float sf(float x) { return x; }
+  static __device__ __forceinline__ float sf(H x) { return HO::to_f(x); }
 
   // ---- per-item constants (registers) ----
   int level, nsteps, payoff, d, dshift, method;
@@ -136,7 +142,8 @@ struct LevelSim {
   FixedConsts fx;
   FastFixed ff;
   // half
-  H hc1, hc1c, hc2, hc3, hS0;
+  H hc1, hc1c, hc2, hc3;
+  HS hS0;
   H2 pc1, pc1c, pc2, pc3;
   float K32;
   float unit_scale;
@@ -149,7 +156,8 @@ struct LevelSim {
   AS hi;   // LAZY: running maximum of S over a group's lanes and steps (reset by the caller)
   int64_t aaccF[KP], aaccC[KP];
   int32_t azprev[KP];
-  H hS[KP], hSc[KP], hzprev[KP], hminF[KP], hminC[KP];
+  HS hS[KP], hSc[KP], hminF[KP], hminC[KP];
+  H hzprev[KP];
   H2 pS, pSc, pzprev;   // lanes 0 and 1 when PAIR (hS[0..1] etc. then unused)
   float haccF[KP], haccC[KP];
   uint32_t sat[KP];
@@ -171,7 +179,8 @@ struct LevelSim {
     if constexpr (HALF) {
       hc1 = HO::from_bits(it.h_c1); hc1c = HO::from_bits(it.h_c1c);
       hc2 = HO::from_bits(it.h_c2); hc3 = HO::from_bits(it.h_c3);
-      hS0 = HO::from_bits(it.h_S0);
+      if constexpr (S32) hS0 = it.S0f;
+      else hS0 = HO::from_bits(it.h_S0);
       K32 = it.Kf;
       if constexpr (PAIR) {
         pc1 = HO2::splat(hc1); pc1c = HO2::splat(hc1c); pc2 = HO2::splat(hc2); pc3 = HO2::splat(hc3);
@@ -206,7 +215,7 @@ struct LevelSim {
       }
       if constexpr (HALF) {
         hS[l] = hS0; hSc[l] = hS0; hzprev[l] = HO::from_f(0.0f); hminF[l] = hS0; hminC[l] = hS0;
-        haccF[l] = __fmul_rn(0.5f, HO::to_f(hS0)); haccC[l] = haccF[l];
+        haccF[l] = __fmul_rn(0.5f, sf(hS0)); haccC[l] = haccF[l];
       }
       sat[l] = 0;
     }
@@ -273,7 +282,9 @@ struct LevelSim {
   }
 
   // ---- half-precision step (one rounding per operation) ----
-  __device__ __forceinline__ H h_step(H s, H z, H cc1, H mh) const {
+  // With S32 only the increment sum1 is in half precision; S is updated in
+  // FP32 (mul2 = fl32(S sum1), S = fl32(S + mul2)).
+  __device__ __forceinline__ HS h_step(HS s, H z, H cc1, H mh) const {
     const H mul1 = HO::mul(hc2, z);
     H sum1 = HO::add(cc1, mul1);
     if constexpr (MIL) {
@@ -282,8 +293,12 @@ struct LevelSim {
       const H mul3 = HO::mul(hc3, sqm);
       sum1 = HO::add(sum1, mul3);
     }
-    const H mul2 = HO::mul(s, sum1);
-    return HO::add(s, mul2);
+    if constexpr (S32) {
+      return __fadd_rn(s, __fmul_rn(s, HO::to_f(sum1)));
+    } else {
+      const H mul2 = HO::mul(s, sum1);
+      return HO::add(s, mul2);
+    }
   }
   // the same step on two lanes at once
   __device__ __forceinline__ H2 h2_step(H2 s, H2 z, H2 cc1, H2 mh) const {
@@ -299,15 +314,15 @@ struct LevelSim {
     return HO2::add(s, mul2);
   }
   // lane l's half state (fine / coarse)
-  __device__ __forceinline__ H lane_S(int l) const {
+  __device__ __forceinline__ HS lane_S(int l) const {
     if constexpr (PAIR) { if (l == 0) return HO2::lo(pS); if (l == 1) return HO2::hi(pS); }
     return hS[l];
   }
-  __device__ __forceinline__ H lane_Sc(int l) const {
+  __device__ __forceinline__ HS lane_Sc(int l) const {
     if constexpr (PAIR) { if (l == 0) return HO2::lo(pSc); if (l == 1) return HO2::hi(pSc); }
     return hSc[l];
   }
-  __device__ __forceinline__ static void lane_min(H &mn, H x) { mn = HO::to_f(x) < HO::to_f(mn) ? x : mn; }
+  __device__ __forceinline__ static void lane_min(HS &mn, HS x) { mn = sf(x) < sf(mn) ? x : mn; }
 
   // Approximate Normal of J in Z's fixed-point format: Method 1 reads the
   // signed table at j = top d bits of J; Method 3 evaluates the class line.
@@ -447,15 +462,15 @@ struct LevelSim {
           }
         } else {
           const H z = half_z(Jl);
-          if constexpr (PC == PC_ASIAN) { if (i > 0) haccF[l] = __fadd_rn(haccF[l], HO::to_f(hS[l])); }
+          if constexpr (PC == PC_ASIAN) { if (i > 0) haccF[l] = __fadd_rn(haccF[l], sf(hS[l])); }
           hS[l] = h_step(hS[l], z, hc1, HO::from_f(1.0f));
-          if constexpr (PC == PC_LOOKBACK) hminF[l] = HO::to_f(hS[l]) < HO::to_f(hminF[l]) ? hS[l] : hminF[l];
+          if constexpr (PC == PC_LOOKBACK) lane_min(hminF[l], hS[l]);
           if constexpr (COARSE) {
             if (odd) {
               const H zc = HO::add(hzprev[l], z);
-              if constexpr (PC == PC_ASIAN) { if (i > 1) haccC[l] = __fadd_rn(haccC[l], HO::to_f(hSc[l])); }
+              if constexpr (PC == PC_ASIAN) { if (i > 1) haccC[l] = __fadd_rn(haccC[l], sf(hSc[l])); }
               hSc[l] = h_step(hSc[l], zc, hc1c, HO::from_f(2.0f));
-              if constexpr (PC == PC_LOOKBACK) hminC[l] = HO::to_f(hSc[l]) < HO::to_f(hminC[l]) ? hSc[l] : hminC[l];
+              if constexpr (PC == PC_LOOKBACK) lane_min(hminC[l], hSc[l]);
             } else {
               hzprev[l] = z;
             }
@@ -501,9 +516,9 @@ struct LevelSim {
       return x - mn;
     }
   }
-  __device__ __forceinline__ int64_t half_payoff(H x, float acc, H mn, int steps) const {
+  __device__ __forceinline__ int64_t half_payoff(HS x, float acc, HS mn, int steps) const {
     float P;
-    const float xf = HO::to_f(x);
+    const float xf = sf(x);
     if constexpr (PC == PC_TERMINAL) {
       if (payoff == 1) {
         P = xf > K32 ? 1.0f : 0.0f;
@@ -517,7 +532,7 @@ struct LevelSim {
       const float dd = __fsub_rn(avg, K32);
       P = dd > 0.0f ? dd : 0.0f;
     } else {
-      P = __fsub_rn(xf, HO::to_f(mn));
+      P = __fsub_rn(xf, sf(mn));
     }
     return __float2ll_rn(__fmul_rn(P, 16777216.0f));
   }
@@ -589,8 +604,8 @@ struct LevelSim {
         r.af = ldexp((double)afS, -fx.fS);
         r.ac = level > 0 ? ldexp((double)acS, -fx.fS) : 0.0;
       } else if constexpr (HALF) {
-        r.af = HAS_APPROX ? (double)HO::to_f(lane_S(l)) : 0.0;
-        r.ac = (HAS_APPROX && level > 0) ? (double)HO::to_f(lane_Sc(l)) : 0.0;
+        r.af = HAS_APPROX ? (double)sf(lane_S(l)) : 0.0;
+        r.ac = (HAS_APPROX && level > 0) ? (double)sf(lane_Sc(l)) : 0.0;
       } else {
         r.af = 0.0; r.ac = 0.0;
       }

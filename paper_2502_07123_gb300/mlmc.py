@@ -19,8 +19,11 @@ EULER, MILSTEIN = 0, 1
 EURO, DIGITAL, ASIAN, LOOKBACK = 0, 1, 2, 3
 FP64_EXACT, FP32_EXACT, FP16_APPROX, BF16_APPROX, FIXED_APPROX, NESTED_CORR_FIXED, NESTED_CORR_FP16, \
     NESTED_CORR_BF16 = range(8)
+# binary16 / bfloat16 increments with S in FP32
+FP16S_APPROX, BF16S_APPROX, NESTED_CORR_FP16S, NESTED_CORR_BF16S = range(8, 12)
 MODE_PLAIN_FP64, MODE_PLAIN_FP32, MODE_NESTED_FIXED, MODE_NESTED_FP16, MODE_NESTED_BF16, \
     MODE_NESTED_FIXED_EXACT_LOW, MODE_NESTED_FP16_EXACT_LOW = range(7)
+MODE_NESTED_FP16S, MODE_NESTED_BF16S, MODE_NESTED_FP16S_EXACT_LOW, MODE_NESTED_BF16S_EXACT_LOW = range(7, 11)
 WORK_ENUMERATE = 1
 REP_FP64, REP_FP32, REP_FP16, REP_BF16, REP_FIXED = range(5)
 

@@ -17,6 +17,8 @@ import numpy as np
 EURO, DIGITAL, ASIAN, LOOKBACK = 0, 1, 2, 3
 EULER, MILSTEIN = 0, 1
 FP64_EXACT, FP32_EXACT, FP16_APPROX, BF16_APPROX, FIXED_APPROX, CORR_FIXED, CORR_FP16, CORR_BF16 = range(8)
+# binary16 / bfloat16 increments with S in FP32
+FP16S_APPROX, BF16S_APPROX, CORR_FP16S, CORR_BF16S = range(8, 12)
 
 # Fixed-point variable order of Algorithm 1
 FORMAT_VARS = ("Z", "con1", "con2", "mul1", "sum1", "mul2", "S")

@@ -8,8 +8,8 @@ RTOL_F32 = 1e-5
 # FP64 exact path: GPU normcdfinv / fused multiply-adds against the oracle's Newton inverse
 RTOL_F64 = 1e-12
 
-APPROX_ONLY = (core.FIXED_APPROX, core.FP16_APPROX, core.BF16_APPROX)
-CORR = (core.CORR_FIXED, core.CORR_FP16, core.CORR_BF16)
+APPROX_ONLY = core.APPROX_ONLY_VARIANTS
+CORR = core.CORR_VARIANTS
 
 
 def exact_rtol(variant):

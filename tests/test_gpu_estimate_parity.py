@@ -31,7 +31,9 @@ def m():
 
 @pytest.mark.parametrize("mode,payoff,seed", [(driver.PLAIN_FP32, W.EURO, 3), (driver.NESTED_FIXED, W.EURO, 4),
                                               (driver.NESTED_FIXED_EXACT_LOW, W.EURO, 5),
-                                              (driver.NESTED_FIXED, W.ASIAN, 6)])
+                                              (driver.NESTED_FIXED, W.ASIAN, 6),
+                                              (driver.NESTED_FP16S_EXACT_LOW, W.EURO, 7),
+                                              (driver.NESTED_BF16S, W.DIGITAL, 8)])
 def test_estimate_equals_oracle_on_the_same_schedule(m, mode, payoff, seed):
     eps = 0.05
     p = W.params(payoff=payoff)

@@ -55,7 +55,8 @@ def test_icdf_tables_bit_exact(m, d, method):
 
 
 VARIANTS = [core.FP64_EXACT, core.FP32_EXACT, core.FP16_APPROX, core.BF16_APPROX, core.FIXED_APPROX,
-            core.CORR_FIXED, core.CORR_FP16, core.CORR_BF16]
+            core.CORR_FIXED, core.CORR_FP16, core.CORR_BF16, core.FP16S_APPROX, core.BF16S_APPROX,
+            core.CORR_FP16S, core.CORR_BF16S]
 CASES = [(v, s, pay, lev) for v in VARIANTS for s in (W.EULER, W.MILSTEIN)
          for pay in (W.EURO, W.DIGITAL, W.ASIAN, W.LOOKBACK) for lev in (0, 1, 2, 5)]
 
@@ -102,3 +103,21 @@ def test_multichunk_sums(m, variant, level):
         y = gd["y"]
         assert abs(res["sum"] - disc * math.fsum(y.tolist())) <= 1e-12 * disc * np.sum(np.abs(y))
         assert abs(res["sum2"] - disc * disc * math.fsum((y * y).tolist())) <= 1e-12 * disc * disc * np.sum(y * y)
+
+
+@pytest.mark.parametrize("variant", [core.FP16S_APPROX, core.BF16S_APPROX])
+@pytest.mark.parametrize("payoff", [W.EURO, W.ASIAN, W.LOOKBACK])
+@pytest.mark.parametrize("level,N", [(0, 4001), (1, 3001), (3, 1001), (6, 301), (4, 200_001)])
+def test_fp32_s_packed_draws(m, variant, payoff, level, N):
+    """Half increments with FP32 S, three samples per Philox word (and, for deep
+    items below one wave, one of them per thread): records and exact integer
+    sums equal the oracle's."""
+    p = W.params(payoff=payoff, scheme=W.MILSTEIN if level % 2 else W.EULER, sigma=0.25)
+    P = m.make_params(p, d=10, method=3 if level == 3 else 1, rng_pack=1)
+    method = 3 if level == 3 else 1
+    seed, first = 70 + level, 2
+    gs, gd = m.mlmc_level_dump(level, N, P, variant, seed, first)
+    os_, od = core.level(p, level, first, N, variant, seed, d=10, method=method, dump=True, pack=1)
+    compare_samples(variant, p, gd, od)
+    run = m.mlmc_level(level, N, P, variant, seed, first)
+    assert run["isum"] == os_["isum"] and run["isum2"] == os_["isum2"]

@@ -48,7 +48,8 @@ def check_sums(res, y, disc):
     assert abs(res["sum2"] - ref2) <= tol2, (res["sum2"], ref2, tol2)
 
 
-REAL = [core.FP32_EXACT, core.FP64_EXACT, core.CORR_FIXED, core.CORR_FP16, core.CORR_BF16]
+REAL = [core.FP32_EXACT, core.FP64_EXACT, core.CORR_FIXED, core.CORR_FP16, core.CORR_BF16, core.CORR_FP16S,
+        core.CORR_BF16S]
 CASES = [(v, pay, lev) for v in REAL for pay in (W.EURO, W.DIGITAL, W.ASIAN, W.LOOKBACK) for lev in (0, 1, 3, 6)]
 
 
