@@ -495,8 +495,18 @@ def batched_run(m, n=256, seed=7, mode=5, iters_per_launch=-4096, max_level=16):
     """The batched workload: all n options submitted at once to one engine; with a
     negative iters_per_launch the whole adaptive run of all of them is one graph
     launch iterating on the device (what mlmc_batch_estimate does, with the
-    engine's counters kept)."""
+    engine's counters kept).  The launch shapes (CTA threads, path-steps per
+    thread) are autotuned first on a work list of the same kernel classes (eight
+    of the options, approximate and correction items on levels 0-12) and
+    installed for the engine's admissions; the default table is restored after."""
     opts = W.batched_options(n, seed)
+    tune_items = []
+    for i, o in enumerate(opts[:8]):
+        P = _engine_params(m, o, 1000 + i, max_level)
+        for lev in range(0, 13):
+            tune_items.append(dict(params=P, level=lev, variant=W.FIXED_APPROX, N=max(2000, (1 << 22) >> lev)))
+            tune_items.append(dict(params=P, level=lev, variant=W.CORR_FIXED, N=max(1000, (1 << 18) >> lev)))
+    shapes = m.mlmc_autotune(tune_items, seed, reps=3)
     eng = m.Engine(max_slots=n, max_level=max_level, iters_per_launch=iters_per_launch)
     _engine_solve(eng, _engine_params(m, opts[0], 0, max_level), 1e-2, mode, 99)   # warm tables and kernels
     s0 = eng.stats()
@@ -515,8 +525,10 @@ def batched_run(m, n=256, seed=7, mode=5, iters_per_launch=-4096, max_level=16):
     st = eng.stats()
     gi = eng.graph_info()
     eng.close()
+    m.mlmc_tuning_reset()
     lat = sorted(done[i]["latency_s"] for i in range(n))
     out = {"requests": n, "mode": mode, "wall_s": wall, "requests_per_s": n / wall,
+           "autotuned_shapes": sorted({"%dx%d" % t for t in shapes}),
            "graph_launches": st["launches"] - s0["launches"], "iters_per_launch": iters_per_launch,
            "graph_captures": gi["captures"], "launch_classes": gi["groups"],
            "path_steps": st["path_steps"] - s0["path_steps"],

@@ -44,7 +44,7 @@ def _run(eng, rids):
     raise AssertionError("engine did not finish")
 
 
-@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("mode", [1, 2, 9])
 def test_engine_equals_estimate_and_is_mix_independent(m, mode):
     pA = W.params(payoff=W.EURO)
     eps = 0.02
