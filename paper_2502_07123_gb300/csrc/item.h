@@ -47,10 +47,13 @@ struct FixedConsts {
 // unit before an arithmetic right shift; left alignments are multiplications.
 struct FastFixed {
   int32_t con2, con3;
-  int32_t con1r, con1cr;     // con1, con1_c plus the rounding half unit of sum1
-  int32_t mulF1;             // 2^(f_con1 - f_mul1): mul1, mul3 onto the sum1 accumulation grid
-  int32_t rs1, rs3, rs_sum1, rs2;
-  int32_t mulS;              // 2^(f_S - f_mul2)
+  int32_t con1r, con1cr;     // con1, con1_c on the sum1 accumulation grid F1 = max(f_con1, f_mul1),
+                             // plus the rounding half unit of sum1
+  int32_t mulF1;             // 2^(F1 - f_mul1): mul1, mul3 onto that grid
+  int32_t rs1, rs3, rs_sum1; // rs_sum1 = F1 - f_sum1
+  int32_t rs2;               // shift of S sum1: f_S + f_sum1 - f_mul2, or f_sum1 when mul2 is finer
+                             // than S (the rounding of S + mul2 folded in)
+  int32_t mulS;              // 2^(f_S - f_mul2) when S is the finer, else 1
   int64_t radd1, radd3, radd2;
   int64_t mfine, mcoarse;    // 1 and 2 in units 2^-2fZ (Milstein)
   int64_t limS;

@@ -239,19 +239,31 @@ __int128 floor_shift(__int128 v, int k) { return v >> k; }
 // magnitudes of mul1, mul3, sum1 (from the table bound) and of mul2 (given
 // |S| <= lim_S) can never reach their saturation limits, so that only S needs
 // a run-time range check.  Fills ff and tells whether S needs 64 bits.
+//
+// Terms are aligned on the finer of the two grids of each sum (con1 and mul1
+// on F1 = max(f_con1, f_mul1); S and mul2 on max(f_S, f_mul2)), as Algorithm 1's
+// exact alignment does.  When mul2 is finer than S (k = f_mul2 - f_S > 0),
+// S + mul2 is rounded back to S's format by a second shift; with floor shifts
+// and an unsaturated mul2 the two roundings are one:
+//   floor((floor((P + r2) / 2^rs2) + 2^(k-1)) / 2^k)
+//     = floor((P + r2 + 2^(k-1) 2^rs2) / 2^(rs2 + k)),    P = S sum1,
+// so the step adds that single shift of P to S (rs2 + k = f_sum1).
 bool fast_fixed(const int e[7], const int f[7], int64_t con1, int64_t con1c, int64_t con2, int64_t con3,
                 int64_t zmax, bool milstein, int64_t nsteps, FastFixed &ff, bool &s64) {
   typedef __int128 I;
   const int fZ = f[F_Z];
-  if (f[F_CON1] < f[F_MUL1] || f[F_CON1] < f[F_SUM1] || f[F_S] < f[F_MUL2]) return false;
+  const int F1 = std::max(f[F_CON1], f[F_MUL1]);
+  if (f[F_SUM1] > F1) return false;   // a finer sum1 is a left shift, not a rounding
   const int rs1 = f[F_CON2] + fZ - f[F_MUL1];
   const int rs3 = f[F_CON1] + 2 * fZ - f[F_MUL1];
-  const int rs_sum1 = f[F_CON1] - f[F_SUM1];
+  const int rs_sum1 = F1 - f[F_SUM1];
   const int rs2 = f[F_S] + f[F_SUM1] - f[F_MUL2];
   if (rs1 < 0 || rs3 < 0 || rs2 < 0 || rs1 > 62 || rs3 > 62 || rs2 > 62 || rs_sum1 > 30) return false;
-  const int shF1 = f[F_CON1] - f[F_MUL1];
-  const int shS = f[F_S] - f[F_MUL2];
-  if (shF1 > 30 || shS > 30) return false;
+  const int shC1 = F1 - f[F_CON1];                    // con1 onto the sum1 accumulation grid
+  const int shF1 = F1 - f[F_MUL1];                    // mul1, mul3 onto it
+  const int shS = std::max(f[F_S] - f[F_MUL2], 0);    // mul2 onto S's grid (S the finer)
+  const int k2 = std::max(f[F_MUL2] - f[F_S], 0);     // S + mul2 back to S's grid (mul2 the finer)
+  if (shC1 > 30 || shF1 > 30 || shS > 30 || rs2 + k2 > 62) return false;
   auto lim = [&](int v) { return ((I)1 << (e[v] + f[v])) - 1; };
   // coarse increments are sums of two table values; level 0 (one step) has no
   // coarse path, so its increments are single table values
@@ -272,26 +284,33 @@ bool fast_fixed(const int e[7], const int f[7], int64_t con1, int64_t con1c, int
     mul3_abs = std::max(a < 0 ? -a : a, b < 0 ? -b : b);
     if (mul3_abs > lim(F_MUL1)) return false;
   }
-  const I c1max = std::max((I)(con1 < 0 ? -con1 : con1), (I)(con1c < 0 ? -con1c : con1c));
+  const I c1 = (I)con1 * ((I)1 << shC1), c1c = (I)con1c * ((I)1 << shC1);
+  const I c1max = std::max(c1 < 0 ? -c1 : c1, c1c < 0 ? -c1c : c1c);
   const I acc_abs = c1max + rsum + (mul1_abs + mul3_abs) * ((I)1 << shF1);
   if (acc_abs >= ((I)1 << 31) - 1) return false;
   const I sum1_abs = floor_shift(acc_abs, rs_sum1) + 1;
   if (sum1_abs > lim(F_SUM1)) return false;
   const I limS = lim(F_S);
-  if (limS * sum1_abs + r2 >= ((I)1 << 62)) return false;
-  const I mul2_abs = floor_shift(limS * sum1_abs + r2, rs2) + 1;
-  if (mul2_abs > lim(F_MUL2) || mul2_abs >= ((I)1 << 31)) return false;
-  const I snew = limS + mul2_abs * ((I)1 << shS);
+  // the rounding constant of the step's single shift (r2 alone when k2 = 0)
+  const I radd2 = r2 + (k2 > 0 ? ((I)1 << (k2 - 1)) * ((I)1 << rs2) : 0);
+  if (limS * sum1_abs + radd2 >= ((I)1 << 62)) return false;
+  const I mul2_abs = floor_shift(limS * sum1_abs + r2, rs2) + 1;   // the format's mul2
+  if (mul2_abs > lim(F_MUL2)) return false;
+  // what the step adds to S, in S's units
+  const I add_abs = k2 > 0 ? floor_shift(limS * sum1_abs + radd2, rs2 + k2) + 1 : mul2_abs * ((I)1 << shS);
+  if (k2 == 0 && mul2_abs >= ((I)1 << 31)) return false;
+  if (add_abs >= ((I)1 << 31)) return false;
+  const I snew = limS + add_abs;
   if (snew >= ((I)1 << 62)) return false;
   s64 = !(snew < ((I)1 << 31) - 1);
   ff.con2 = (int32_t)con2;
   ff.con3 = (int32_t)con3;
-  ff.con1r = (int32_t)(con1 + (int64_t)rsum);
-  ff.con1cr = (int32_t)(con1c + (int64_t)rsum);
+  ff.con1r = (int32_t)(c1 + rsum);
+  ff.con1cr = (int32_t)(c1c + rsum);
   ff.mulF1 = 1 << shF1;
-  ff.rs1 = rs1; ff.rs3 = rs3; ff.rs_sum1 = rs_sum1; ff.rs2 = rs2;
+  ff.rs1 = rs1; ff.rs3 = rs3; ff.rs_sum1 = rs_sum1; ff.rs2 = rs2 + k2;
   ff.mulS = 1 << shS;
-  ff.radd1 = (int64_t)r1; ff.radd3 = (int64_t)r3; ff.radd2 = (int64_t)r2;
+  ff.radd1 = (int64_t)r1; ff.radd3 = (int64_t)r3; ff.radd2 = (int64_t)radd2;
   ff.mfine = (int64_t)1 << (2 * fZ);
   ff.mcoarse = (int64_t)2 << (2 * fZ);
   ff.limS = (int64_t)limS;
@@ -308,7 +327,7 @@ bool fast_fixed(const int e[7], const int f[7], int64_t con1, int64_t con1c, int
   //  * the first value above +lim_S cannot wrap (snew < 2^31 above).
   ff.lazy = 0;
   if (!s64) {
-    const I c1min = std::min((I)con1, (I)con1c);
+    const I c1min = std::min(c1, c1c);
     const I sum1_min = floor_shift(c1min + rsum - (mul1_abs + mul3_abs) * ((I)1 << shF1), rs_sum1);
     if (sum1_min >= -((I)1 << f[F_SUM1])) {
       const long double a = std::ldexp((long double)sum1_abs, -f[F_SUM1]);

@@ -991,13 +991,23 @@ template <int AP, int SCHEME>
 __device__ __forceinline__ int stage_chunk(const ItemDesc *items, int n_items, uint32_t gc, const void **staged) {
   extern __shared__ __align__(16) unsigned char smem_tab[];
   __shared__ int s_item;
-  if (threadIdx.x == 0) {
-    int lo = 0, hi = n_items - 1;
-    while (lo < hi) {  // last item with chunk_begin <= gc
-      const int mid = (lo + hi + 1) >> 1;
-      if (items[mid].chunk_begin <= gc) lo = mid; else hi = mid - 1;
+  if (threadIdx.x < 32) {
+    // last item with chunk_begin <= gc (chunk_begin is non-decreasing and
+    // items[0].chunk_begin <= gc): warp 0 samples 32 evenly spaced items per
+    // round, one load each, and narrows to the stride after the last sample
+    // at or before gc; one round for up to 32 items, two for up to 1024
+    const int lane = threadIdx.x;
+    int lo = 0, span = n_items;
+    while (true) {
+      const int stride = span > 32 ? (span + 31) / 32 : 1;
+      const int k = lo + lane * stride;
+      const bool le = lane * stride < span && items[k].chunk_begin <= gc;
+      const int last = __popc(__ballot_sync(0xffffffffu, le)) - 1;
+      lo += last * stride;
+      if (stride == 1) break;
+      span = min(stride, span - last * stride);
     }
-    s_item = lo;
+    if (lane == 0) s_item = lo;
   }
   __syncthreads();
   const int item = s_item;
