@@ -289,7 +289,12 @@ void mlmc_tuning_reset(void);
  * Giles (2008): variance target eps^2/2, bias target eps/sqrt(2), weak order 1,
  * L from 2 up to max_level, 10^4 initial samples per level and estimator,
  * sample counts N = ceil(lambda sqrt(V/C)) with lambda = (eps^2/2)^-1 sum sqrt(V C)
- * over every (level, estimator) term.  mode: 0 plain FP64, 1 plain FP32,
+ * over every (level, estimator) term.  Each round runs every term's pending
+ * samples and recomputes the counts; once every remaining top-up is at most
+ * 1% of its term's samples (the form of the loop in Giles 2015) the bias test
+ * runs, and a new level's first samples run in the same round as those
+ * top-ups; the result is returned when nothing is pending and the bias test
+ * passed or L = max_level.  mode: 0 plain FP64, 1 plain FP32,
  * 2 nested fixed point, 3 nested binary16, 4 nested bfloat16, 7 and 8 nested
  * binary16 / bfloat16 increments with S in FP32; 5, 6, 9 and 10 nested
  * fixed point / binary16 / binary16 with FP32 S / bfloat16 with FP32 S whose
@@ -302,7 +307,7 @@ void mlmc_tuning_reset(void);
  * Outputs (host): *price, *stderr_out, *L; N_l[l * 2 + k] = samples of
  * estimator k on level l (k = 0: plain or approximate, k = 1: correction), for
  * l <= *L (caller array of 2 * cap_levels).  Errors as mlmc_level, MLMC_EINVAL
- * if cap_levels <= max_level. */
+ * if cap_levels <= max_level, MLMC_ETIMEOUT after 100000 rounds. */
 mlmc_status mlmc_estimate(double eps, const mlmc_params *p, int mode, uint64_t seed,
                           int max_level, double *price, double *stderr_out, int *L,
                           uint64_t *N_l, int cap_levels);

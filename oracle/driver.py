@@ -12,9 +12,14 @@ level difference and the exact-minus-approximate correction) and the same
 formula applies over all 2(L+1) terms with one multiplier lambda_M.
 
 The adaptive loop is the one of Giles (2008), which Sec. 6 says the on-line
-phase follows, with these stated constants (the paper gives none): variance
-target (1 - theta) eps^2 with theta = 1/2, bias target sqrt(theta) eps,
-weak order alpha = 1 (Euler-Maruyama), extrapolated variance decay beta
+phase follows, in the form Giles (2015) gives it: each round evaluates every
+pending sample and recomputes the optimal counts; the bias test (and with it
+a new level) waits only until every remaining top-up is at most
+ALMOST_DONE = 1% of its term's samples, so a new level's first samples run in
+the same round as those small top-ups; the run ends when nothing is pending
+and the test passed (or L = L_max).  Stated constants (the paper gives none):
+variance target (1 - theta) eps^2 with theta = 1/2, bias target sqrt(theta)
+eps, weak order alpha = 1 (Euler-Maruyama), extrapolated variance decay beta
 (1 for Euler-Maruyama, 2 for Milstein) for a newly added level, L_min = 2,
 N_init = 10^4, L_max = 10.  Costs follow the model C = 2^l c_kind, so the
 sample counts are deterministic functions of the sums.
@@ -57,6 +62,10 @@ def bias_estimate(means, alpha=1.0):
 PLAIN_FP64, PLAIN_FP32, NESTED_FIXED, NESTED_FP16, NESTED_BF16, NESTED_FIXED_EXACT_LOW, NESTED_FP16_EXACT_LOW = range(7)
 # half-precision increments with S in FP32
 NESTED_FP16S, NESTED_BF16S, NESTED_FP16S_EXACT_LOW, NESTED_BF16S_EXACT_LOW = range(7, 11)
+
+# The bias test runs once every pending top-up is at most this fraction of its
+# term's samples.
+ALMOST_DONE = 0.01
 
 # Levels whose approximate level difference is computed exactly, by enumerating
 # the 2^(d 2^l) combinations of table cells (d 2^l <= EXACT_MAX_BITS).
@@ -136,20 +145,26 @@ def mlmc(eps, p, seed, mode=PLAIN_FP64, cost=None, fmt_of_level=None, d=10, meth
         N[lev][k] += count
 
     while True:
-        while any(x > 0 for row in dN for x in row):
-            for lev in range(L + 1):
-                for k in range(ne):
-                    if dN[lev][k] > 0:
-                        run(lev, k, dN[lev][k])
-            Nopt = optimal_n(*_vc(), (1.0 - theta) * eps * eps)
-            for lev in range(L + 1):
-                for k in range(ne):
-                    want = int(math.ceil(Nopt[lev * ne + k]))
-                    dN[lev][k] = max(0, want - N[lev][k])
+        # one round: every pending sample, then the optimal counts again
+        for lev in range(L + 1):
+            for k in range(ne):
+                if dN[lev][k] > 0:
+                    run(lev, k, dN[lev][k])
+        Nopt = optimal_n(*_vc(), (1.0 - theta) * eps * eps)
+        for lev in range(L + 1):
+            for k in range(ne):
+                want = int(math.ceil(Nopt[lev * ne + k]))
+                dN[lev][k] = max(0, want - N[lev][k])
+        # the bias test waits until every remaining top-up is small
+        if any(dN[lev][k] > ALMOST_DONE * N[lev][k] for lev in range(L + 1) for k in range(ne)):
+            continue
         means = [sum(S1[lev][k] / N[lev][k] for k in range(ne)) for lev in range(L + 1)]
         if bias_estimate(means) <= math.sqrt(theta) * eps or L >= L_max:
-            break
-        # add a level with extrapolated variances
+            if all(x == 0 for row in dN for x in row):
+                break
+            continue
+        # add a level with extrapolated variances; its first samples run in the
+        # same round as the remaining top-ups
         L += 1
         N.append([0] * ne)
         S1.append([0.0] * ne)

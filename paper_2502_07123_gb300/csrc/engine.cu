@@ -50,6 +50,9 @@ namespace {
 constexpr int MAXL = 21;
 constexpr int GMAX = 32;                          // launch groups per engine
 constexpr unsigned long long NCAP = 1ULL << 34;   // samples of one item per iteration
+// bias test once every pending top-up is at most this fraction of its term's
+// samples (the value mlmc_estimate uses)
+constexpr double ALMOST_DONE = 0.01;
 
 struct SlotState {
   int32_t active, done, L, ne;
@@ -291,10 +294,15 @@ __global__ void decide_kernel(SlotState *slots, SlotReport *rep, int n_slots, En
   SlotReport &r = rep[i];
   if (s.active && !s.done) {
     update_dn(s);
-    bool any = false;
+    // the bias test once every remaining top-up is within ALMOST_DONE of its
+    // term's samples (mlmc_estimate's loop, operation for operation)
+    bool any = false, small = true;
     for (int l = 0; l <= s.L; ++l)
-      for (int k = 0; k < s.ne; ++k) any |= s.dN[l][k] > 0;
-    if (!any) {
+      for (int k = 0; k < s.ne; ++k) {
+        any |= s.dN[l][k] > 0;
+        small &= !(__ull2double_rn(s.dN[l][k]) > __dmul_rn(ALMOST_DONE, __ull2double_rn(s.N[l][k])));
+      }
+    if (small) {
       // bias estimate from the last two level means (weak order 1), with the
       // floor |m_l| >= |m_{l-1}| / (2 * 2^alpha) from level 2 on
       double mprev = 0.0, mL = 0.0, mL1 = 0.0;
@@ -309,7 +317,14 @@ __global__ void decide_kernel(SlotState *slots, SlotReport *rep, int n_slots, En
       }
       double rem = __ddiv_rn(fabs(mL), 1.0);
       rem = fmax(rem, __ddiv_rn(__ddiv_rn(fabs(mL1), 2.0), 1.0));
-      if (rem <= s.sqrt_theta_eps || s.L >= s.max_level) {
+      if (rem > s.sqrt_theta_eps && s.L < s.max_level) {
+        const int L = ++s.L;
+        for (int k = 0; k < s.ne; ++k) {
+          s.N[L][k] = 0; s.dN[L][k] = 0; s.S1[L][k] = 0.0; s.S2[L][k] = 0.0;
+          s.Vext[L][k] = __ddiv_rn(fmax(level_var(s, L - 1, k), 1e-300), s.beta_factor);
+        }
+        update_dn(s);
+      } else if (!any) {
         double pr = 0.0, var = 0.0;
         for (int l = 0; l <= s.L; ++l)
           for (int k = 0; k < s.ne; ++k) {
@@ -321,13 +336,6 @@ __global__ void decide_kernel(SlotState *slots, SlotReport *rep, int n_slots, En
         s.se = __dsqrt_rn(var);
         s.rem = rem;
         s.done = 1;
-      } else {
-        const int L = ++s.L;
-        for (int k = 0; k < s.ne; ++k) {
-          s.N[L][k] = 0; s.dN[L][k] = 0; s.S1[L][k] = 0.0; s.S2[L][k] = 0.0;
-          s.Vext[L][k] = __ddiv_rn(fmax(level_var(s, L - 1, k), 1e-300), s.beta_factor);
-        }
-        update_dn(s);
       }
     }
   }

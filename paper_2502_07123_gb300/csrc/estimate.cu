@@ -1,6 +1,7 @@
 // The adaptive MLMC driver mlmc_estimate: the Giles (2008) loop to RMS error
-// eps with the nested variant of Sec. 2.2 (approximate levels plus
-// corrections), host-driven over synchronous plans.
+// eps, in the form of Giles (2015) that tests the bias once the remaining
+// top-ups are small, with the nested variant of Sec. 2.2 (approximate levels
+// plus corrections), host-driven over synchronous plans.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -38,6 +39,10 @@ struct EstPlan {
 
 // Levels whose approximate level difference is a finite sum over 2^(d 2^l) <= 2^20 cells.
 constexpr int EXACT_MAX_BITS = 20;
+// The bias test runs once every pending top-up is at most this fraction of its
+// term's samples (Giles 2015's form of the loop); a bound on the rounds.
+constexpr double ALMOST_DONE = 0.01;
+constexpr int MAX_ROUNDS = 100000;
 
 bool est_plan(int mode, EstPlan &e) {
   switch (mode) {
@@ -123,23 +128,27 @@ extern "C" mlmc_status mlmc_estimate(double eps, const mlmc_params *p, int mode,
         dN[l][k] = want > N[l][k] ? want - N[l][k] : 0;
       }
   };
-  for (int iter = 0; iter < 1000; ++iter) {
-    bool any = true;
-    while (any) {
-      work.clear();
-      idx.clear();
-      for (int l = 0; l <= L; ++l)
-        for (int k = 0; k < ne; ++k)
-          if (dN[l][k] > 0) {
-            mlmc_work w;
-            std::memset(&w, 0, sizeof w);
-            w.params = p; w.level = l; w.variant = ep.variant[k]; w.first_sample = N[l][k]; w.N = dN[l][k];
-            w.stream = -1;
-            w.flags = is_exact(l, k) ? MLMC_WORK_ENUMERATE : 0;
-            work.push_back(w);
-            idx.push_back({l, k});
-          }
-      if (work.empty()) break;
+  // One synchronous round per pass: the pending samples of every term, new
+  // optimal counts, and (once every remaining top-up is within ALMOST_DONE of
+  // its term's samples) the bias test, which may add a level whose first
+  // samples then run in the same round as those top-ups.  The run ends when
+  // nothing is pending and the bias test passed (or L = max_level).
+  for (int round = 0;; ++round) {
+    if (round >= MAX_ROUNDS) return MLMC_ETIMEOUT;
+    work.clear();
+    idx.clear();
+    for (int l = 0; l <= L; ++l)
+      for (int k = 0; k < ne; ++k)
+        if (dN[l][k] > 0) {
+          mlmc_work w;
+          std::memset(&w, 0, sizeof w);
+          w.params = p; w.level = l; w.variant = ep.variant[k]; w.first_sample = N[l][k]; w.N = dN[l][k];
+          w.stream = -1;
+          w.flags = is_exact(l, k) ? MLMC_WORK_ENUMERATE : 0;
+          work.push_back(w);
+          idx.push_back({l, k});
+        }
+    if (!work.empty()) {
       res.resize(work.size());
       s = run_sync(work.data(), (int)work.size(), seed, nullptr, nullptr, res.data(), g.st, false);
       if (s != MLMC_OK) return s;
@@ -149,11 +158,15 @@ extern "C" mlmc_status mlmc_estimate(double eps, const mlmc_params *p, int mode,
         S2[l][k] += res[j].sum2;
         N[l][k] += work[j].N;
       }
-      update_dn();
-      any = false;
-      for (int l = 0; l <= L; ++l)
-        for (int k = 0; k < ne; ++k) any |= dN[l][k] > 0;
     }
+    update_dn();
+    bool any = false, small = true;
+    for (int l = 0; l <= L; ++l)
+      for (int k = 0; k < ne; ++k) {
+        any |= dN[l][k] > 0;
+        small &= !((double)dN[l][k] > ALMOST_DONE * (double)N[l][k]);
+      }
+    if (!small) continue;
     // bias test on the last two levels (weak order alpha)
     std::vector<double> means(L + 1, 0.0);
     for (int l = 0; l <= L; ++l) {
@@ -164,16 +177,19 @@ extern "C" mlmc_status mlmc_estimate(double eps, const mlmc_params *p, int mode,
     }
     double rem = std::fabs(means[L]) / (std::pow(2.0, alpha) - 1.0);
     rem = std::max(rem, std::fabs(means[L - 1]) / std::pow(2.0, alpha) / (std::pow(2.0, alpha) - 1.0));
-    if (rem <= std::sqrt(theta) * eps || L >= max_level) break;
-    L += 1;
-    N.push_back(std::vector<uint64_t>(ne, 0));
-    dN.push_back(std::vector<uint64_t>(ne, 0));
-    S1.push_back(std::vector<double>(ne, 0.0));
-    S2.push_back(std::vector<double>(ne, 0.0));
-    std::vector<double> ve(ne);
-    for (int k = 0; k < ne; ++k) ve[k] = std::max(level_var(L - 1, k), 1e-300) / std::pow(2.0, beta);
-    Vext.push_back(ve);
-    update_dn();
+    if (rem > std::sqrt(theta) * eps && L < max_level) {
+      L += 1;
+      N.push_back(std::vector<uint64_t>(ne, 0));
+      dN.push_back(std::vector<uint64_t>(ne, 0));
+      S1.push_back(std::vector<double>(ne, 0.0));
+      S2.push_back(std::vector<double>(ne, 0.0));
+      std::vector<double> ve(ne);
+      for (int k = 0; k < ne; ++k) ve[k] = std::max(level_var(L - 1, k), 1e-300) / std::pow(2.0, beta);
+      Vext.push_back(ve);
+      update_dn();
+      continue;
+    }
+    if (!any) break;
   }
   double pr = 0.0, var = 0.0;
   for (int l = 0; l <= L; ++l)

@@ -188,7 +188,7 @@ SUMS_DTYPE = np.dtype([(k, {ctypes.c_double: "<f8", ctypes.c_uint64: "<u8", ctyp
 
 def _sums_list(out, raw=False):
     """Results of an mlmc_sums array: a structured array (raw) or one dict per item."""
-    a = np.frombuffer(out, dtype=SUMS_DTYPE).copy()
+    a = np.frombuffer(out, dtype=SUMS_DTYPE)   # a view that keeps `out` alive
     if raw:
         return a
     names = SUMS_DTYPE.names
@@ -292,10 +292,26 @@ def _tuning(tuning):
     return ctypes.byref(t)
 
 
+_raw_stream = None
+
+
+def _current_raw_stream():
+    """torch's current stream on the current device as a raw cudaStream_t
+    (without building a torch.cuda.Stream object on every call)."""
+    global _raw_stream
+    if _raw_stream is None:
+        import torch
+        get = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+        if get is None:
+            _raw_stream = lambda: torch.cuda.current_stream().cuda_stream
+        else:
+            _raw_stream = lambda: get(torch.cuda.current_device())
+    return _raw_stream()
+
+
 def _stream_handle(stream):
     if stream is None:
-        import torch
-        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        return ctypes.c_void_p(_current_raw_stream())
     if isinstance(stream, int):
         return ctypes.c_void_p(stream)
     return ctypes.c_void_p(stream.cuda_stream)
