@@ -40,7 +40,8 @@ struct Arena {
   size_t cap_counters = 0;
   mlmc::ItemDesc *h_items = nullptr;       // pinned staging of the work list
   size_t cap_h_items = 0;
-  mlmc::DevSums *h_out = nullptr;          // pinned staging of the results
+  mlmc::DevSums *h_out = nullptr;          // pinned, mapped: the results, written by the kernels
+  mlmc::DevSums *d_hout = nullptr;         // its device address
   size_t cap_h_out = 0;
   std::vector<cudaStream_t> aux;
   std::vector<cudaEvent_t> join, kstart, kstop;

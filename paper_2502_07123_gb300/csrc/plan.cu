@@ -72,6 +72,7 @@ struct mlmc_plan {
   cudaStream_t last_stream = nullptr;
   bool launched = false;
   bool borrowed = false;   // device buffers, streams and events belong to the context arena
+  bool out_on_host = false;  // d_out is the device address of mapped pinned host memory
 };
 
 namespace mlmc_host {
@@ -434,8 +435,10 @@ mlmc_status plan_launch_impl(mlmc_plan *pl, cudaStream_t st) {
       MLMC_CK(cudaStreamWaitEvent(st, pl->join[i], 0));
     }
   }
-  // items without samples: zero sums (no CTA writes them)
-  for (uint32_t o : pl->empty_out) MLMC_CK(cudaMemsetAsync(pl->d_out + o, 0, sizeof(DevSums), st));
+  // items without samples: zero sums (no CTA writes them; host-side results
+  // are zeroed by the host before the launch)
+  if (!pl->out_on_host)
+    for (uint32_t o : pl->empty_out) MLMC_CK(cudaMemsetAsync(pl->d_out + o, 0, sizeof(DevSums), st));
   MLMC_CK(cudaEventRecord(pl->t1, st));
   pl->last_stream = st;
   pl->launched = true;
@@ -483,19 +486,28 @@ mlmc_status plan_results_impl(mlmc_plan *pl, mlmc_sums *out) {
 }
 
 template <class T>
-bool grow_pinned(T *&p, size_t &cap, size_t need) {
+bool grow_pinned(T *&p, size_t &cap, size_t need, T **dev = nullptr) {
   if (need <= cap) return true;
   if (p) cudaFreeHost(p);
   p = nullptr;
   cap = 0;
+  if (dev) *dev = nullptr;
   const size_t n = std::max<size_t>(need, 64);
-  if (cudaHostAlloc((void **)&p, sizeof(T) * n, cudaHostAllocDefault) != cudaSuccess) return false;
+  if (cudaHostAlloc((void **)&p, sizeof(T) * n, dev ? cudaHostAllocMapped : cudaHostAllocDefault) != cudaSuccess)
+    return false;
+  if (dev && cudaHostGetDevicePointer((void **)dev, p, 0) != cudaSuccess) {
+    cudaFreeHost(p);
+    p = nullptr;
+    return false;
+  }
   cap = n;
   return true;
 }
 
 // One synchronous pass on stream st: work list to the device through pinned
-// staging, the launch, the sums back through pinned staging, one stream sync.
+// staging, the launch, one stream sync.  The CTA that completes an item writes
+// its sums straight into mapped pinned host memory, so no copy back is queued
+// (a small device-to-host copy costs about as much as the launch itself).
 mlmc_status run_sync(const mlmc_work *work, int n_work, uint64_t seed, const mlmc_tuning *tuning,
                      void *const *dumps, mlmc_sums *out, cudaStream_t st, bool launch_chunking) {
   mlmc_plan *pl = nullptr;
@@ -504,7 +516,8 @@ mlmc_status run_sync(const mlmc_work *work, int n_work, uint64_t seed, const mlm
   Arena &A = g.arena;
   const size_t ni = pl->items.size();
   do {
-    if (!grow_pinned(A.h_items, A.cap_h_items, ni) || !grow_pinned(A.h_out, A.cap_h_out, (size_t)n_work)) {
+    if (!grow_pinned(A.h_items, A.cap_h_items, ni) ||
+        !grow_pinned(A.h_out, A.cap_h_out, (size_t)n_work, &A.d_hout)) {
       s = MLMC_ENOMEM;
       break;
     }
@@ -513,10 +526,14 @@ mlmc_status run_sync(const mlmc_work *work, int n_work, uint64_t seed, const mlm
       s = MLMC_ECUDA;
       break;
     }
+    // results in host memory: items without samples are zeroed here (no CTA
+    // writes them), the others by their last CTA
+    pl->d_out = A.d_hout;
+    pl->out_on_host = true;
+    for (uint32_t o : pl->empty_out) std::memset(&A.h_out[o], 0, sizeof(DevSums));
     if ((s = plan_launch_impl(pl, st)) != MLMC_OK) break;
     float ms = 0.0f;
-    if (cudaMemcpyAsync(A.h_out, pl->d_out, sizeof(DevSums) * n_work, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess || cudaEventElapsedTime(&ms, pl->t0, pl->t1) != cudaSuccess) {
+    if (cudaStreamSynchronize(st) != cudaSuccess || cudaEventElapsedTime(&ms, pl->t0, pl->t1) != cudaSuccess) {
       s = MLMC_ECUDA;
       break;
     }
