@@ -349,8 +349,9 @@ def main():
     res = plan.results()
 
     # end-to-end: the same work through the host-buffer C-ABI call (plan build,
-    # H2D of the work descriptors through pinned staging, launch, D2H of the
-    # sums, results as one structured array) on a work list marshalled once
+    # H2D of the work descriptors through pinned staging, launch, the sums
+    # written device-to-host into mapped pinned memory by each item's last CTA,
+    # results as one structured array) on a work list marshalled once
     work = m.WorkList(items)
     e2e_ms = []
     for _ in range(max(3, min(10, args.steps))):
