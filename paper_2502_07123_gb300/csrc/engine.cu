@@ -98,34 +98,56 @@ __device__ double level_var(const SlotState &s, int l, int k) {
   return v > 0.0 ? v : 0.0;
 }
 
-// dN = ceil(lambda sqrt(V/C)) - N over all levels <= L and estimators (mlmc_estimate's update).
-// Level variance with the floor V_l >= V_{l-1} / (2 * 2^beta) from level 2 on.
-__device__ double floored_var(const SlotState &s, int l, int k, double &vprev) {
-  double v = level_var(s, l, k);
-  if (l >= 2) v = fmax(v, __ddiv_rn(__dmul_rn(0.5, vprev), s.beta_factor));
-  vprev = v;
-  return fmax(v, 1e-300);
-}
+// Per-warp scratch of a slot's decision (shared memory beside the slot's copy):
+// per (level, estimator) term, level-major.
+struct DecideScratch {
+  double v[2 * MAXL];     // floored level variances
+  double a[2 * MAXL];     // sqrt(V C); then S1 / N
+  double q[2 * MAXL];     // sqrt(V / C); then the variance of the mean
+  double lam;
+};
 
-__device__ void update_dn(SlotState &s) {
-  double lam = 0.0;
-  double vp[2] = {0.0, 0.0};
-  for (int l = 0; l <= s.L; ++l)
-    for (int k = 0; k < s.ne; ++k) {
-      const double V = floored_var(s, l, k, vp[k]);
-      const double C = ldexp(s.cost[k], l);
-      lam = __dadd_rn(lam, __dsqrt_rn(__dmul_rn(V, C)));
+// dN = ceil(lambda sqrt(V/C)) - N over all levels <= L and estimators
+// (mlmc_estimate's update, operation for operation): each term's divisions and
+// square roots on its own lane of the warp, the level-order parts (the floor
+// V_l >= V_{l-1} / (2 * 2^beta) from level 2 on, the sum for lambda) on one
+// lane.  Dividing by the power of two 2^beta is multiplying by its exact
+// reciprocal: the same correctly rounded value.
+__device__ void update_dn(SlotState &s, DecideScratch &d, int lane) {
+  const int ne = s.ne, T = (s.L + 1) * ne;
+  for (int t = lane; t < T; t += 32) d.v[t] = level_var(s, t / ne, t % ne);
+  __syncwarp();
+  if (lane < ne) {
+    const double inv_bf = __ddiv_rn(1.0, s.beta_factor);
+    double vprev = 0.0;
+    for (int l = 0; l <= s.L; ++l) {
+      const int t = l * ne + lane;
+      double v = d.v[t];
+      if (l >= 2) v = fmax(v, __dmul_rn(__dmul_rn(0.5, vprev), inv_bf));
+      vprev = v;
+      d.v[t] = fmax(v, 1e-300);
     }
-  lam = __ddiv_rn(lam, s.var_target);
-  vp[0] = vp[1] = 0.0;
-  for (int l = 0; l <= s.L; ++l)
-    for (int k = 0; k < s.ne; ++k) {
-      const double V = floored_var(s, l, k, vp[k]);
-      const double C = ldexp(s.cost[k], l);
-      const double x = V > 0.0 ? __dmul_rn(lam, __dsqrt_rn(__ddiv_rn(V, C))) : 0.0;
-      const unsigned long long want = (unsigned long long)ceil(fmin(x, 1e18));
-      s.dN[l][k] = want > s.N[l][k] ? want - s.N[l][k] : 0ULL;
-    }
+  }
+  __syncwarp();
+  for (int t = lane; t < T; t += 32) {
+    const double C = ldexp(s.cost[t % ne], t / ne);
+    d.a[t] = __dsqrt_rn(__dmul_rn(d.v[t], C));
+    d.q[t] = __dsqrt_rn(__ddiv_rn(d.v[t], C));
+  }
+  __syncwarp();
+  if (lane == 0) {
+    double lam = 0.0;
+    for (int t = 0; t < T; ++t) lam = __dadd_rn(lam, d.a[t]);
+    d.lam = __ddiv_rn(lam, s.var_target);
+  }
+  __syncwarp();
+  for (int t = lane; t < T; t += 32) {
+    const int l = t / ne, k = t % ne;
+    const double x = d.v[t] > 0.0 ? __dmul_rn(d.lam, d.q[t]) : 0.0;
+    const unsigned long long want = (unsigned long long)ceil(fmin(x, 1e18));
+    s.dN[l][k] = want > s.N[l][k] ? want - s.N[l][k] : 0ULL;
+  }
+  __syncwarp();
 }
 
 // Pending work of template t (slot t / il): samples [first, first + N).
@@ -286,67 +308,117 @@ __global__ void acc_kernel(SlotState *slots, const TmplMeta *meta, int il, const
   atomicAdd(&status->path_steps, run_n[j] << m.level);
 }
 
-// Per slot: new sample counts, the bias test, a new level, or completion.
-__global__ void decide_kernel(SlotState *slots, SlotReport *rep, int n_slots, EngStatus *status) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_slots || status->overflow) return;
-  SlotState &s = slots[i];
-  SlotReport &r = rep[i];
+// Per slot: new sample counts, the bias test, a new level, or completion; the
+// warp's lanes share the per-term arithmetic (update_dn), the level-order sums
+// run on lane 0.  s is the slot's state in shared memory (decide_kernel).
+__device__ void decide_slot(SlotState &s, DecideScratch &d, SlotReport &r, EngStatus *status, int lane) {
   if (s.active && !s.done) {
-    update_dn(s);
+    update_dn(s, d, lane);
     // the bias test once every remaining top-up is within ALMOST_DONE of its
     // term's samples (mlmc_estimate's loop, operation for operation)
+    const int ne = s.ne, T = (s.L + 1) * ne;
     bool any = false, small = true;
-    for (int l = 0; l <= s.L; ++l)
-      for (int k = 0; k < s.ne; ++k) {
-        any |= s.dN[l][k] > 0;
-        small &= !(__ull2double_rn(s.dN[l][k]) > __dmul_rn(ALMOST_DONE, __ull2double_rn(s.N[l][k])));
-      }
+    for (int t = lane; t < T; t += 32) {
+      const int l = t / ne, k = t % ne;
+      any |= s.dN[l][k] > 0;
+      small &= !(__ull2double_rn(s.dN[l][k]) > __dmul_rn(ALMOST_DONE, __ull2double_rn(s.N[l][k])));
+    }
+    any = __any_sync(0xffffffffu, any);
+    small = __all_sync(0xffffffffu, small);
     if (small) {
       // bias estimate from the last two level means (weak order 1), with the
-      // floor |m_l| >= |m_{l-1}| / (2 * 2^alpha) from level 2 on
-      double mprev = 0.0, mL = 0.0, mL1 = 0.0;
-      for (int l = 0; l <= s.L; ++l) {
-        double ml = 0.0;
-        for (int k = 0; k < s.ne; ++k) ml = __dadd_rn(ml, __ddiv_rn(s.S1[l][k], __ull2double_rn(s.N[l][k])));
-        ml = fabs(ml);
-        if (l >= 2) ml = fmax(ml, __ddiv_rn(__dmul_rn(0.5, mprev), 2.0));
-        if (l == s.L - 1) mL1 = ml;
-        if (l == s.L) mL = ml;
-        mprev = ml;
-      }
-      double rem = __ddiv_rn(fabs(mL), 1.0);
-      rem = fmax(rem, __ddiv_rn(__ddiv_rn(fabs(mL1), 2.0), 1.0));
-      if (rem > s.sqrt_theta_eps && s.L < s.max_level) {
-        const int L = ++s.L;
-        for (int k = 0; k < s.ne; ++k) {
-          s.N[L][k] = 0; s.dN[L][k] = 0; s.S1[L][k] = 0.0; s.S2[L][k] = 0.0;
-          s.Vext[L][k] = __ddiv_rn(fmax(level_var(s, L - 1, k), 1e-300), s.beta_factor);
+      // floor |m_l| >= |m_{l-1}| / (2 * 2^alpha) from level 2 on (the division
+      // by 2^alpha = 2 as a multiplication by 1/2)
+      for (int t = lane; t < T; t += 32) d.a[t] = __ddiv_rn(s.S1[t / ne][t % ne], __ull2double_rn(s.N[t / ne][t % ne]));
+      __syncwarp();
+      int add = 0, fin = 0;
+      double rem = 0.0;
+      if (lane == 0) {
+        double mprev = 0.0, mL = 0.0, mL1 = 0.0;
+        for (int l = 0; l <= s.L; ++l) {
+          double ml = 0.0;
+          for (int k = 0; k < ne; ++k) ml = __dadd_rn(ml, d.a[l * ne + k]);
+          ml = fabs(ml);
+          if (l >= 2) ml = fmax(ml, __dmul_rn(__dmul_rn(0.5, mprev), 0.5));
+          if (l == s.L - 1) mL1 = ml;
+          if (l == s.L) mL = ml;
+          mprev = ml;
         }
-        update_dn(s);
-      } else if (!any) {
-        double pr = 0.0, var = 0.0;
-        for (int l = 0; l <= s.L; ++l)
-          for (int k = 0; k < s.ne; ++k) {
-            const double n = __ull2double_rn(s.N[l][k]);
-            pr = __dadd_rn(pr, __ddiv_rn(s.S1[l][k], n));
-            var = __dadd_rn(var, __ddiv_rn(level_var(s, l, k), n));
+        rem = fabs(mL);
+        rem = fmax(rem, __dmul_rn(fabs(mL1), 0.5));
+        if (rem > s.sqrt_theta_eps && s.L < s.max_level) {
+          add = 1;
+          const int L = ++s.L;
+          for (int k = 0; k < ne; ++k) {
+            s.N[L][k] = 0; s.dN[L][k] = 0; s.S1[L][k] = 0.0; s.S2[L][k] = 0.0;
+            s.Vext[L][k] = __ddiv_rn(fmax(level_var(s, L - 1, k), 1e-300), s.beta_factor);
           }
-        s.price = pr;
-        s.se = __dsqrt_rn(var);
-        s.rem = rem;
-        s.done = 1;
+        } else if (!any) {
+          fin = 1;
+        }
+      }
+      add = __shfl_sync(0xffffffffu, add, 0);
+      fin = __shfl_sync(0xffffffffu, fin, 0);
+      rem = __shfl_sync(0xffffffffu, rem, 0);
+      __syncwarp();
+      if (add) {
+        update_dn(s, d, lane);
+      } else if (fin) {
+        for (int t = lane; t < T; t += 32) {
+          const int l = t / ne, k = t % ne;
+          const double n = __ull2double_rn(s.N[l][k]);
+          d.a[t] = __ddiv_rn(s.S1[l][k], n);
+          d.q[t] = __ddiv_rn(level_var(s, l, k), n);
+        }
+        __syncwarp();
+        if (lane == 0) {
+          double pr = 0.0, var = 0.0;
+          for (int t = 0; t < T; ++t) {
+            pr = __dadd_rn(pr, d.a[t]);
+            var = __dadd_rn(var, d.q[t]);
+          }
+          s.price = pr;
+          s.se = __dsqrt_rn(var);
+          s.rem = rem;
+          s.done = 1;
+        }
+        __syncwarp();
       }
     }
   }
-  r.active = s.active;
-  r.done = s.done;
-  r.L = s.L;
-  r.price = s.price;
-  r.se = s.se;
-  r.rem = s.rem;
-  if (s.active && !s.done) atomicAdd(&status->active, 1);
-  if (s.active && s.done) atomicAdd(&status->done, 1);
+  if (lane == 0) {
+    r.active = s.active;
+    r.done = s.done;
+    r.L = s.L;
+    r.price = s.price;
+    r.se = s.se;
+    r.rem = s.rem;
+    if (s.active && !s.done) atomicAdd(&status->active, 1);
+    if (s.active && s.done) atomicAdd(&status->done, 1);
+  }
+}
+
+// One warp per slot: the slot's state is copied into shared memory by the
+// warp's lanes, the decision runs on that copy over the warp (its FP64
+// divisions and square roots, one chain per slot on one lane before, took
+// ~65 us per iteration on this part), and the copy is written back.
+constexpr int DECIDE_WARPS = 4;
+static_assert(sizeof(SlotState) % 8 == 0, "the slot state is copied in 8-byte words");
+__global__ void __launch_bounds__(DECIDE_WARPS * 32) decide_kernel(SlotState *slots, SlotReport *rep, int n_slots,
+                                                                    EngStatus *status) {
+  __shared__ SlotState sh[DECIDE_WARPS];
+  __shared__ DecideScratch scratch[DECIDE_WARPS];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * DECIDE_WARPS + warp;
+  if (i >= n_slots || status->overflow) return;   // uniform over the warp
+  constexpr int WORDS = (int)(sizeof(SlotState) / 8);
+  unsigned long long *g = (unsigned long long *)&slots[i];
+  unsigned long long *l = (unsigned long long *)&sh[warp];
+  for (int w = lane; w < WORDS; w += 32) l[w] = g[w];
+  __syncwarp();
+  decide_slot(sh[warp], scratch[warp], rep[i], status, lane);
+  __syncwarp();
+  for (int w = lane; w < WORDS; w += 32) g[w] = l[w];
 }
 
 struct Request {
@@ -507,7 +579,8 @@ cudaError_t enqueue_iteration(mlmc_engine *e, const std::vector<int> &live) {
   if (err != cudaSuccess) return err;
   acc_kernel<<<(n_tmpl + 3) / 4, 128, 0, e->cs>>>(e->d_slots, e->d_meta, e->il, e->d_run_src, e->d_run_nch,
                                                   e->d_run_cb, e->d_run_n, e->d_partials, e->d_status);
-  decide_kernel<<<(e->max_slots + 127) / 128, 128, 0, e->cs>>>(e->d_slots, e->d_rep, e->max_slots, e->d_status);
+  decide_kernel<<<(e->max_slots + DECIDE_WARPS - 1) / DECIDE_WARPS, DECIDE_WARPS * 32, 0, e->cs>>>(
+      e->d_slots, e->d_rep, e->max_slots, e->d_status);
   return cudaGetLastError();
 }
 
