@@ -44,9 +44,14 @@ def _run(eng, rids):
     raise AssertionError("engine did not finish")
 
 
-@pytest.mark.parametrize("mode", [1, 2, 9])
-def test_engine_equals_estimate_and_is_mix_independent(m, mode):
-    pA = W.params(payoff=W.EURO)
+@pytest.mark.parametrize("mode,scheme,payoff", [(1, W.EULER, W.EURO), (2, W.EULER, W.EURO), (9, W.EULER, W.EURO),
+                                                (5, W.EULER, W.EURO), (2, W.MILSTEIN, W.ASIAN)])
+def test_engine_equals_estimate_and_is_mix_independent(m, mode, scheme, payoff):
+    """The device-side decision (a warp per slot) takes mlmc_estimate's FP64
+    operations in mlmc_estimate's order: the same request gives the same price,
+    standard error and L alone, in a mix, and through mlmc_estimate (exact low
+    levels in mode 5; Milstein's variance decay 2^-2 in the last case)."""
+    pA = W.params(payoff=payoff, scheme=scheme)
     eps = 0.02
     ref = m.mlmc_estimate(eps, _P(m, pA, 17), mode, 5, 10)
     # alone
