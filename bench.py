@@ -53,12 +53,12 @@ OPS_CORR_FIXED_EM = 54.0
 ALU_PEAK_TOPS = 152 * 4 * 32 * 2.070e9 / 1e12
 # DRAM bytes (read + write) of the dominant launch, from one ncu capture of this
 # bench command (dram__bytes_read.sum + dram__bytes_write.sum of the merged
-# nested launch, family 17, 80,148,728 path-steps):
+# nested launch in its pre-scaled form, family 24, 80,148,728 path-steps):
 #   ncu --set full --clock-control none -k regex:^nested_kernel -s 2 -c 1 -o prof \
 #       python bench.py --steps 3 --warmup 3 --no-cpu-baseline --no-tte \
 #       --no-serving-sample --no-optimiser
 # keyed by (family, path-steps per launch); another launch reports null
-DOMINANT_TRAFFIC = {(17, 80148728): 169216}
+DOMINANT_TRAFFIC = {(24, 80148728): 166656}
 
 
 def build_items(m, rank=0, formats=None):
@@ -362,11 +362,13 @@ def main():
     e2e_value = info["path_steps"] / (statistics.median(e2e_ms) * 1e-3)
 
     # roofline of the dominant kernel: the launch with the most path-steps among
-    # the fixed-point families (17: the merged nested launch of the approximate
-    # and correction chunks; 15 / 8: approximate packed / one sample per thread,
+    # the fixed-point families (24 / 17: the merged nested launch of the approximate
+    # and correction chunks, with / without the pre-scaled product; 15 / 8: approximate packed / one sample per thread,
     # 32-bit S; 12 / 2 general).  Its algorithmic ops are each estimator's ops
     # per path-step times that estimator's path-steps in the launch.
-    fam_names = {17: "nested_kernel<FX32,EM,terminal> (approximate packed + one sample per thread + correction)",
+    fam_names = {24: "nested_kernel<FX32,EM,terminal,pre-scaled> (approximate packed + one sample per thread + "
+                     "correction)",
+                 17: "nested_kernel<FX32,EM,terminal> (approximate packed + one sample per thread + correction)",
                  15: "level_kernel<APPROX,F32,FX32,EM,terminal,packed x3>",
                  8: "level_kernel<APPROX,F32,FX32,EM,terminal>",
                  12: "level_kernel<APPROX,F32,FIXED,EM,terminal,packed x3>",

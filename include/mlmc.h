@@ -242,9 +242,10 @@ mlmc_status mlmc_plan_info(const mlmc_plan *plan, int *kernels, uint64_t *ctas,
  * the last launch, and its family (0 exact FP32, 1 exact FP64, 2 approximate
  * fixed, 3 approximate binary16, 4 approximate bfloat16, 5/6/7 correction with
  * fixed / binary16 / bfloat16; 8-16 the same estimators' other datapaths
- * (fast fixed point, packed draws), 17 the merged nested launch, 18-23 binary16 /
- * bfloat16 with FP32 S: approximate 18 / 19, correction 20 / 21, approximate
- * with packed draws 22 / 23).  Waits for that kernel.  MLMC_ENOTREADY before
+ * (fast fixed point, packed draws), 17 the merged nested launch (24: the same
+ * with the pre-scaled product, when every item's increment fits it), 18-23
+ * binary16 / bfloat16 with FP32 S: approximate 18 / 19, correction 20 / 21,
+ * approximate with packed draws 22 / 23).  Waits for that kernel.  MLMC_ENOTREADY before
  * the first launch, MLMC_EINVAL for k out of range. */
 mlmc_status mlmc_plan_kernel_time(const mlmc_plan *plan, int k, int *family, double *ms);
 /* Level-kernel launch k of the plan (0 <= k < kernels of mlmc_plan_info):

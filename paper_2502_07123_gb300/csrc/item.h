@@ -58,7 +58,9 @@ struct FastFixed {
   int64_t mfine, mcoarse;    // 1 and 2 in units 2^-2fZ (Milstein)
   int64_t limS;
   int32_t lazy;              // 32-bit S may run unclamped, checked once per pack (fast_fixed)
-  int32_t pad1;
+  int32_t pre_ok;            // |sum1| < 2^(rs2 - 1): sum1 2^(32 - rs2) fits 32 bits, so the rounded
+                             // product S sum1 is the high word of one 64-bit multiply-add
+                             // (the merged nested kernel's pre-scaled form, family 24)
 };
 
 struct ItemDesc {

@@ -207,7 +207,8 @@ cudaError_t launch_by_family(int fam, int scheme, int pc, dim3 grid, dim3 block,
     case 14: return launch_approx_bf16_p3(scheme, pc, grid, block, smem, st, a, occ);
     case 15: return launch_approx_fx32_p3(scheme, pc, grid, block, smem, st, a, occ);
     case 16: return launch_approx_fx64_p3(scheme, pc, grid, block, smem, st, a, occ);
-    case 17: return launch_nested_fx32(scheme, pc, grid, block, smem, st, a, occ);
+    case 17: return launch_nested_fx32(scheme, pc, grid, block, smem, st, a, occ, false);
+    case 24: return launch_nested_fx32(scheme, pc, grid, block, smem, st, a, occ, true);
     case 18: return launch_approx_f16s(scheme, pc, grid, block, smem, st, a, occ);
     case 19: return launch_approx_bf16s(scheme, pc, grid, block, smem, st, a, occ);
     case 20: return launch_corr_f16s(scheme, pc, grid, block, smem, st, a, occ);
@@ -311,6 +312,10 @@ bool fast_fixed(const int e[7], const int f[7], int64_t con1, int64_t con1c, int
   ff.rs1 = rs1; ff.rs3 = rs3; ff.rs_sum1 = rs_sum1; ff.rs2 = rs2 + k2;
   ff.mulS = 1 << shS;
   ff.radd1 = (int64_t)r1; ff.radd3 = (int64_t)r3; ff.radd2 = (int64_t)radd2;
+  // the pre-scaled product: sum1 2^(32 - rs2) and radd2 2^(32 - rs2) in range,
+  // |S| < 2^31 (32-bit S) so the 64-bit product cannot overflow
+  const int rs2t = rs2 + k2;
+  ff.pre_ok = rs2t >= 1 && rs2t <= 31 && sum1_abs < ((I)1 << (rs2t - 1)) && radd2 < ((I)1 << 31);
   ff.mfine = (int64_t)1 << (2 * fZ);
   ff.mcoarse = (int64_t)2 << (2 * fZ);
   ff.limS = (int64_t)limS;

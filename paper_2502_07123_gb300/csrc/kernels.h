@@ -27,9 +27,10 @@ MLMC_FAMILY(launch_approx_f16_p3)
 MLMC_FAMILY(launch_approx_bf16_p3)
 MLMC_FAMILY(launch_approx_fx32_p3)
 MLMC_FAMILY(launch_approx_fx64_p3)
-// family 17: merged nested launch of families 15, 8 and 10 (Euler-Maruyama,
-// terminal payoffs; per-item kind in ItemDesc::kind)
-MLMC_FAMILY(launch_nested_fx32)
+// families 17 / 24: merged nested launch of families 15, 8 and 10 (Euler-Maruyama,
+// terminal payoffs; per-item kind in ItemDesc::kind); 24: pre-scaled sum1 form
+cudaError_t launch_nested_fx32(int scheme, int pc, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                               const LaunchArgs &a, int *occ, bool pre);
 // families 18-23: binary16 / bfloat16 increments with S in FP32
 MLMC_FAMILY(launch_approx_f16s)
 MLMC_FAMILY(launch_approx_bf16s)

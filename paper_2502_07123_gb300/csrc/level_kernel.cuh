@@ -98,7 +98,11 @@ __device__ __forceinline__ int32_t ff_sum1(const FastFixed &ff, int32_t z, int32
 // evaluation of Method 3, 2 either, chosen per step (only the per-sample
 // dump instantiation); chosen once per chunk, so the hot step code has no
 // branch on the method.
-template <int EST, int XP, int AP, int SCHEME, int PC, int KP = 1, int MSEL = 0>
+// PRE (merged nested kernel, family 24): the 32-bit fast datapath's sum1
+// arrives multiplied by 2^(32 - rs2) (the host proved that it fits), so the
+// rounded product rd(S sum1) is the high word of one 64-bit multiply-add: no
+// funnel shift on the ALU pipe, which bounds that kernel.
+template <int EST, int XP, int AP, int SCHEME, int PC, int KP = 1, int MSEL = 0, bool PRE = false>
 struct LevelSim {
   static_assert(KP == 1 || EST == EST_APPROX, "packed draws feed approximate-only estimators");
   static constexpr bool HAS_EXACT = (EST != EST_APPROX);
@@ -134,6 +138,8 @@ struct LevelSim {
   // ---- per-item constants (registers) ----
   int level, nsteps, payoff, d, dshift, method;
   // FX32: byte offset of lane l's table entry = rotr(word, rot[l]) & off_mask
+  int32_t pre2;            // PRE: 2^(32 - rs2), and radd2 times it
+  int64_t radd2p;
   uint32_t rot[KP], off_mask;
   const uint16_t *perm_s;  // method 2 coupling of the exact path (shared memory), or nullptr
   uint32_t low_mask;
@@ -176,6 +182,10 @@ struct LevelSim {
     }
     if constexpr (FIXED) fx = it.fx;
     if constexpr (FAST) ff = it.ff;
+    if constexpr (AP == AP_FX32 && PRE) {
+      pre2 = 1 << (32 - it.ff.rs2);
+      radd2p = (int64_t)((uint64_t)it.ff.radd2 << (32 - it.ff.rs2));
+    }
     if constexpr (HALF) {
       hc1 = HO::from_bits(it.h_c1); hc1c = HO::from_bits(it.h_c1c);
       hc2 = HO::from_bits(it.h_c2); hc3 = HO::from_bits(it.h_c3);
@@ -252,7 +262,11 @@ struct LevelSim {
   // The S update of a step whose sum1 is known: mul2 = rd(S sum1), S = rd(S + mul2).
   template <bool EAGER>
   __device__ __forceinline__ AS ff_apply(AS s, int32_t sum1, SatT &satb) {
-    if constexpr (AP == AP_FX32) {
+    if constexpr (AP == AP_FX32 && PRE) {
+      const int64_t p2 = (int64_t)s * sum1 + radd2p;
+      const int32_t mul2 = (int32_t)((uint64_t)p2 >> 32);
+      s = (int32_t)((uint32_t)s + (uint32_t)mul2 * (uint32_t)ff.mulS);
+    } else if constexpr (AP == AP_FX32) {
       const int64_t p2 = (int64_t)s * sum1 + ff.radd2;
       const int32_t mul2 = (int32_t)__funnelshift_r((uint32_t)p2, (uint32_t)((uint64_t)p2 >> 32), ff.rs2);
       s = (int32_t)((uint32_t)s + (uint32_t)mul2 * (uint32_t)ff.mulS);
@@ -273,7 +287,8 @@ struct LevelSim {
   }
   template <bool EAGER>
   __device__ __forceinline__ AS ff_step(AS s, int32_t z, int32_t c1r, int64_t m, SatT &satb) {
-    return ff_apply<EAGER>(s, ff_sum1<MIL, AP == AP_FX32>(ff, z, c1r, m), satb);
+    if constexpr (AP == AP_FX32 && PRE) return ff_apply<EAGER>(s, ff_sum1<MIL, true>(ff, z, c1r, m) * pre2, satb);
+    else return ff_apply<EAGER>(s, ff_sum1<MIL, AP == AP_FX32>(ff, z, c1r, m), satb);
   }
   // FX32: (Z~, sum1 of a fine step) of lane l of word w, from the shared-memory pairs
   __device__ __forceinline__ int2 fx32_entry(uint32_t w, int l) const {
@@ -918,10 +933,10 @@ __device__ __forceinline__ void group_loop(Sim &sim, ThreadAcc<EST, XP> &acc, co
 // branch on them.  DYN (device-scheduled kernel) only keeps the
 // instantiations of the static and device-scheduled kernels apart, so that
 // each is compiled inline into its own kernel.
-template <int EST, int XP, int AP, int SCHEME, int PC, int KP, int MSEL, bool DUMP, bool DYN>
+template <int EST, int XP, int AP, int SCHEME, int PC, int KP, int MSEL, bool DUMP, bool DYN, bool PRE = false>
 __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDesc &it, int item, uint32_t gc,
                                            const unsigned char *smem_tab) {
-  using Sim = LevelSim<EST, XP, AP, SCHEME, PC, KP, MSEL>;
+  using Sim = LevelSim<EST, XP, AP, SCHEME, PC, KP, MSEL, PRE>;
   Sim sim;
   sim.load(it, smem_tab);
   ThreadAcc<EST, XP> acc;
@@ -987,7 +1002,7 @@ __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDes
 // approximate-Normal table in shared memory (unless *staged, when given, says
 // that it is there already).  Every thread has finished the previous chunk
 // before the table is overwritten (block_reduce_write ends with a barrier).
-template <int AP, int SCHEME>
+template <int AP, int SCHEME, bool PRE = false>
 __device__ __forceinline__ int stage_chunk(const ItemDesc *items, int n_items, uint32_t gc, const void **staged) {
   extern __shared__ __align__(16) unsigned char smem_tab[];
   __shared__ int s_item;
@@ -1035,7 +1050,8 @@ __device__ __forceinline__ int stage_chunk(const ItemDesc *items, int n_items, u
         const int32_t v = (int32_t)((t + ((int64_t)1 << (sh - 1))) >> sh);
         z = ai.neg ? -v : v;
       }
-      dst[k] = make_int2(z, ff_sum1<SCHEME == 1, true>(it.ff, z, it.ff.con1r, it.ff.mfine));
+      const int32_t sum1 = ff_sum1<SCHEME == 1, true>(it.ff, z, it.ff.con1r, it.ff.mfine);
+      dst[k] = make_int2(z, PRE ? sum1 * (1 << (32 - it.ff.rs2)) : sum1);
     }
     if (it.perm) {   // after the table: the method-2 interval ranks
       uint16_t *pd = (uint16_t *)(smem_tab + (size_t)n * TabBytes<AP>::value);
@@ -1125,15 +1141,19 @@ level_kernel_dyn(const __grid_constant__ LaunchArgs args) {
 // Its chunks run the same chunk bodies as the separate launches, in one grid
 // ordered by decreasing CTA cost, so the longest chains start first and the
 // short chunks of every family fill in behind them.
-template <int AP, int SCHEME, int PC>
+// PRE: every item's sum1 fits the pre-scaled product (family 24; see LevelSim).
+template <int AP, int SCHEME, int PC, bool PRE>
 __global__ void __launch_bounds__(LAUNCH_THREADS, 6) nested_kernel(const __grid_constant__ LaunchArgs args) {
   extern __shared__ __align__(16) unsigned char smem_tab[];
   const uint32_t gc = args.chunk0 + blockIdx.x;
-  const int item = stage_chunk<AP, SCHEME>(args.items, args.n_items, gc, nullptr);
+  const int item = stage_chunk<AP, SCHEME, PRE>(args.items, args.n_items, gc, nullptr);
   const ItemDesc &it = args.items[item];
-  if (it.kind == 0) chunk_body<EST_APPROX, XP_F32, AP, SCHEME, PC, 3, 0, false, false>(args, it, item, gc, smem_tab);
-  else if (it.kind == 1) chunk_body<EST_APPROX, XP_F32, AP, SCHEME, PC, 1, 0, false, false>(args, it, item, gc, smem_tab);
-  else chunk_body<EST_CORR, XP_F32, AP, SCHEME, PC, 1, 0, false, false>(args, it, item, gc, smem_tab);
+  if (it.kind == 0)
+    chunk_body<EST_APPROX, XP_F32, AP, SCHEME, PC, 3, 0, false, false, PRE>(args, it, item, gc, smem_tab);
+  else if (it.kind == 1)
+    chunk_body<EST_APPROX, XP_F32, AP, SCHEME, PC, 1, 0, false, false, PRE>(args, it, item, gc, smem_tab);
+  else
+    chunk_body<EST_CORR, XP_F32, AP, SCHEME, PC, 1, 0, false, false, PRE>(args, it, item, gc, smem_tab);
 }
 
 }  // namespace mlmc

@@ -228,7 +228,8 @@ mlmc_status plan_create_impl(mlmc_plan **out, const mlmc_work *work, int n_work,
     // The nested estimator's 32-bit fixed-point families with Euler-Maruyama and
     // a terminal payoff (15 approximate packed, 8 approximate one sample per
     // thread, 10 correction) share one launch of the merged kernel (family 17)
-    // when more than one of them is present: the same chunk bodies, one grid.
+    // when more than one of them is present: the same chunk bodies, one grid;
+    // family 24 when every item's sum1 fits the pre-scaled product.
     {
       auto kind_of = [&](int i) {
         const BuiltItem &b = built[i];
@@ -236,14 +237,18 @@ mlmc_status plan_create_impl(mlmc_plan **out, const mlmc_work *work, int n_work,
         return b.family == 15 ? 0 : (b.family == 8 ? 1 : (b.family == 10 ? 2 : -1));
       };
       int seen = 0;
+      bool pre = true;   // every merged item takes the pre-scaled product (family 24)
       for (int i = 0; i < n_work; ++i)
-        if (kind_of(i) >= 0 && built[i].it.n_chunks > 0) seen |= 1 << kind_of(i);
+        if (kind_of(i) >= 0 && built[i].it.n_chunks > 0) {
+          seen |= 1 << kind_of(i);
+          pre = pre && built[i].it.ff.pre_ok;
+        }
       if (seen & (seen - 1))
         for (int i = 0; i < n_work; ++i) {
           const int k = kind_of(i);
           if (k < 0) continue;
           built[i].it.kind = k;
-          built[i].family = 17;
+          built[i].family = pre ? 24 : 17;
         }
     }
     // group by kernel configuration; within a launch, most expensive chunks first

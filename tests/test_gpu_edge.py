@@ -152,7 +152,7 @@ def test_plan_launch_items_partition_the_work(m):
             assert len(idx) == n_items > 0
             assert ps == sum(items[i]["N"] << items[i]["level"] for i in idx)
             variants = {items[i]["variant"] for i in idx}
-            if fam == 17:
+            if fam in (17, 24):
                 # the merged nested launch: 32-bit fixed-point approximate and correction chunks
                 assert variants <= {W.FIXED_APPROX, W.CORR_FIXED} and len(variants) == 2
             else:
@@ -189,12 +189,15 @@ def test_worklist_and_raw_results(m):
         assert c[i]["sum"] == x["sum"] and c[i]["n"] == x["n"]
 
 
-def test_merged_nested_launch_equals_separate_items(m):
+@pytest.mark.parametrize("sigma,family", [(0.2, 24), (0.6, 17)])
+def test_merged_nested_launch_equals_separate_items(m, sigma, family):
     # approximate (packed and one sample per thread) and correction items of the
     # 32-bit fixed-point datapath share one launch of the merged kernel (family
-    # 17); each item's sums equal those of the item run alone: integer sums bit
-    # for bit, real sums to FP64 rounding (the chunkings differ)
-    p = W.params(payoff=W.DIGITAL)
+    # 17, or 24 in its pre-scaled form); each item's sums equal those of the item run alone: integer sums bit
+    # for bit, real sums to FP64 rounding (the chunkings differ).  With sigma 0.6
+    # the coarse increments of the low levels are too large for the pre-scaled
+    # product (|sum1| < 2^(rs2 - 1)), so the launch keeps the funnel-shift form.
+    p = W.params(payoff=W.DIGITAL, sigma=sigma)
     P = _P(m, p, pack=1)
     items = [dict(params=P, level=0, variant=W.FIXED_APPROX, N=300_001, first_sample=7),
              dict(params=P, level=3, variant=W.FIXED_APPROX, N=5_000),
@@ -203,7 +206,7 @@ def test_merged_nested_launch_equals_separate_items(m):
              dict(params=P, level=7, variant=W.CORR_FIXED, N=3_000)]
     plan = m.Plan(items, 21)
     try:
-        assert plan.info()["kernels"] == 1 and plan.launch_info(0)[0] == 17
+        assert plan.info()["kernels"] == 1 and plan.launch_info(0)[0] == family
         plan.launch()
         res = plan.results()
     finally:

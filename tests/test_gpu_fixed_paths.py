@@ -45,7 +45,7 @@ def _formats(p, kind, level, rng):
     return fm
 
 
-FAST_FAMILIES = {8, 9, 10, 11, 15, 16, 17}
+FAST_FAMILIES = {8, 9, 10, 11, 15, 16, 17, 24}
 GENERAL_FAMILIES = {2, 5, 12}
 
 
