@@ -57,6 +57,8 @@ struct FastFixed {
   int64_t radd1, radd3, radd2;
   int64_t mfine, mcoarse;    // 1 and 2 in units 2^-2fZ (Milstein)
   int64_t limS;
+  int64_t limT;              // lazy runs: S after an odd fine step (and the coarse S) at most limT
+                             // keeps every fine S within lim_S (fast_fixed)
   int32_t lazy;              // 32-bit S may run unclamped, checked once per pack (fast_fixed)
   int32_t pre_ok;            // |sum1| < 2^(rs2 - 1): sum1 2^(32 - rs2) fits 32 bits, so the rounded
                              // product S sum1 is the high word of one 64-bit multiply-add

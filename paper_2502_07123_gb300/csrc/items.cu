@@ -330,6 +330,12 @@ bool fast_fixed(const int e[7], const int f[7], int64_t con1, int64_t con1c, int
   //    a = max |sum1|, so B_{k+1} = B_k (1 + a) + mulS bounds it from B_0 = 0
   //    (S_0 > 0) and B_n <= lim_S after the path's n steps suffices;
   //  * the first value above +lim_S cannot wrap (snew < 2^31 above).
+  // The lazy run tracks max S only after the odd fine steps (and on the coarse
+  // path), against limT: a fine step takes |S| to at most |S| (1 + A) + mulS,
+  // A = max |sum1| 2^-f_sum1 (mulS = 1 when mul2 is finer than S), so S <= limT
+  // before a step keeps it within lim_S after it; with S_0 <= limT (build_item
+  // checks) every even-index fine S is tracked and every odd-index one follows.
+  ff.limT = (int64_t)(((limS - (I)ff.mulS) << f[F_SUM1]) / (((I)1 << f[F_SUM1]) + sum1_abs));
   ff.lazy = 0;
   if (!s64) {
     const I c1min = std::min(c1, c1c);
@@ -517,6 +523,7 @@ mlmc_status build_item(const mlmc_work &w, int out_index, void *dump, BuiltItem 
       fast = fast_fixed(e, f, con1, con1c, con2, con3, zmax, p->scheme == MLMC_MILSTEIN, (int64_t)1 << lev, it.ff,
                         s64);
       fast64 = s64;
+      if (fast && it.ff.lazy && S0q > it.ff.limT) it.ff.lazy = 0;   // the thinned check needs S_0 <= limT
       // the 32-bit datapath keeps (Z~, fine sum1) pairs in shared memory (2^d x 8
       // bytes: d <= 12) and rounds products by one funnel shift (shifts below 32)
       if (fast && !fast64 &&

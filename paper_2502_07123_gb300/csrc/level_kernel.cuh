@@ -235,7 +235,7 @@ struct LevelSim {
   }
   // LAZY: did some S since hi was reset leave [-lim_S, lim_S]?  (The host
   // proved that it cannot leave below first.)
-  __device__ __forceinline__ bool over() const { return hi > (AS)ff.limS; }
+  __device__ __forceinline__ bool over() const { return hi > (AS)ff.limT; }
 
   // ---- exact path (FP32 / FP64) ----
   __device__ __forceinline__ X exact_inc(X z, X cc1, X mm) const {
@@ -260,7 +260,8 @@ struct LevelSim {
 
   // ---- fast fixed-point Algorithm-1 step (same values as fx_step while S stays in range) ----
   // The S update of a step whose sum1 is known: mul2 = rd(S sum1), S = rd(S + mul2).
-  template <bool EAGER>
+  // TRACK (lazy runs): count this S in the pack's maximum (fast_fixed's limT)
+  template <bool EAGER, bool TRACK = true>
   __device__ __forceinline__ AS ff_apply(AS s, int32_t sum1, SatT &satb) {
     if constexpr (AP == AP_FX32 && PRE) {
       const int64_t p2 = (int64_t)s * sum1 + radd2p;
@@ -275,7 +276,7 @@ struct LevelSim {
       s = (int64_t)((uint64_t)s + (uint64_t)((int64_t)mul2 * ff.mulS));
     }
     if constexpr (LAZY && !EAGER) {
-      hi = max(hi, s);
+      if constexpr (TRACK) hi = max(hi, s);
       return s;
     }
     // saturation of S (the only variable the host could not bound)
@@ -443,7 +444,10 @@ struct LevelSim {
       for (int l = 0; l < KP; ++l) {
         const int2 e = fx32_entry(J, l);
         if constexpr (PC == PC_ASIAN) { if (i > 0) aaccF[l] += aS[l]; }
-        aS[l] = ff_apply<EAGER>(aS[l], e.y, satb[l]);
+        // lazy runs track S after the odd fine steps only (limT); with the parity
+        // unknown at compile time, after every step (more is as exact)
+        constexpr bool TRACK_FINE = PAR == 1 || (PAR == -1 && COARSE);
+        aS[l] = ff_apply<EAGER, TRACK_FINE>(aS[l], e.y, satb[l]);
         if constexpr (PC == PC_LOOKBACK) aminF[l] = aS[l] < aminF[l] ? aS[l] : aminF[l];
         if constexpr (COARSE) {
           if (odd) {
