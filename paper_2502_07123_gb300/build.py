@@ -5,6 +5,7 @@ then linked into paper_2502_07123_gb300/_build/libmlmc_gb300.so.  The
 library is loaded by the ctypes binding in ``mlmc.py``.
 """
 import concurrent.futures
+import fcntl
 import hashlib
 import os
 import subprocess
@@ -48,8 +49,16 @@ def _compile(src):
 
 
 def build(force: bool = False, jobs: int = 0) -> str:
-    """Compile and link the CUDA library if its sources changed; return its path."""
+    """Compile and link the CUDA library if its sources changed; return its path.
+    Concurrent callers (one process per GPU rank) take a file lock, so one of
+    them builds and the others find the library up to date."""
     os.makedirs(OUT_DIR, exist_ok=True)
+    with open(os.path.join(OUT_DIR, "build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        return _build_locked(force, jobs)
+
+
+def _build_locked(force, jobs):
     stamp = os.path.join(OUT_DIR, "stamp")
     fp = _fingerprint()
     if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == fp:
