@@ -8,9 +8,9 @@
 // estimator).  An iteration, captured once as a CUDA graph and replayed, is:
 //   sched_kernel   - reads every slot's pending counts, chunks each pending
 //                    (slot, level, estimator) item exactly as a plan would,
-//                    and lays the items out by launch group (kernel family,
-//                    scheme, payoff class, CTA size, seed) with chunk offsets;
-//   fill_kernel    - writes the iteration's work items from the templates;
+//                    lays the items out by launch group (kernel family,
+//                    scheme, payoff class, CTA size, seed) with chunk offsets,
+//                    and writes the iteration's work items from the templates;
 //   level kernels  - one device-scheduled launch per group, on forked streams,
 //                    each a fixed grid of resident CTAs looping over the
 //                    group's chunks (level_kernel_dyn);
@@ -173,11 +173,14 @@ __device__ uint64_t pending_chunks(const TmplMeta &m, unsigned long long first, 
   return chunk_count(*g1 - *g0, steps_per_group(m.level), m.kp, m.threads, m.spt, num_sms, gpt);
 }
 
-// One block of 1024 threads: the iteration's work list, grouped by launch group.
-__global__ void __launch_bounds__(1024) sched_kernel(const SlotState *slots, const TmplMeta *meta, int n_tmpl, int il,
-                                                     int n_groups, unsigned long long cap_chunks, int num_sms,
-                                                     uint32_t *t_nch, int *run_src, uint32_t *run_nch,
-                                                     uint32_t *run_cb, DynLaunch *dyn, EngStatus *status) {
+// One block of 1024 threads: the iteration's work list, grouped by launch group,
+// and its work items (one warp per item: the lanes copy the template, lane 0
+// sets the samples and chunking; before, a separate kernel node).
+__global__ void __launch_bounds__(1024) sched_kernel(const SlotState *slots, const TmplMeta *meta, const ItemDesc *tmpl,
+                                                     int n_tmpl, int il, int n_groups, unsigned long long cap_chunks,
+                                                     int num_sms, uint32_t *t_nch, int *run_src, uint32_t *run_nch,
+                                                     uint32_t *run_cb, DynLaunch *dyn, EngStatus *status,
+                                                     ItemDesc *run, unsigned long long *run_n) {
   __shared__ uint32_t s_cnt[GMAX], s_fill[GMAX], s_ioff[GMAX];
   __shared__ unsigned long long s_chk[GMAX], s_coff[GMAX];
   __shared__ int s_over;
@@ -251,35 +254,40 @@ __global__ void __launch_bounds__(1024) sched_kernel(const SlotState *slots, con
       base += __shfl_sync(0xffffffffu, inc, 31);
     }
   }
-}
-
-// The iteration's work items, from the templates (one thread per item).
-__global__ void fill_kernel(const SlotState *slots, const TmplMeta *meta, const ItemDesc *tmpl, int il,
-                            int num_sms, const int *run_src, const uint32_t *run_nch, const uint32_t *run_cb,
-                            const EngStatus *status, ItemDesc *run, unsigned long long *run_n) {
-  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (status->overflow || j >= status->n_items) return;
-  const int t = run_src[j];
-  unsigned long long first = 0, N = 0;
-  pending(slots, meta, il, t, first, N);
-  uint32_t gpt;
-  uint64_t g0, g1;
-  pending_chunks(meta[t], first, N, num_sms, &gpt, &g0, &g1);
-  const uint64_t spc = samples_per_group(meta[t].level, meta[t].kp);
-  ItemDesc it = tmpl[t];
-  it.first = first;
-  it.N = N;
-  it.g0 = g0;
-  it.g1 = g1;
-  it.gf0 = (first + spc - 1) / spc;
-  it.gf1 = (first + N) / spc;
-  if (it.gf1 < it.gf0) it.gf1 = it.gf0;
-  it.groups_per_thread = gpt;
-  it.n_chunks = run_nch[j];
-  it.chunk_begin = run_cb[j];
-  it.out_index = j;
-  run[j] = it;
-  run_n[j] = N;
+  __syncthreads();
+  // the iteration's work items from the templates, one warp per item: the
+  // lanes copy the template, lane 0 sets its samples and chunking
+  static_assert(sizeof(ItemDesc) % 8 == 0, "item templates are copied in 8-byte words");
+  const uint32_t n_items = status->n_items;
+  for (uint32_t j = (uint32_t)warp; j < n_items; j += blockDim.x >> 5) {
+    const int t = run_src[j];
+    const unsigned long long *src = (const unsigned long long *)&tmpl[t];
+    unsigned long long *dst = (unsigned long long *)&run[j];
+    for (int w = lane; w < (int)(sizeof(ItemDesc) / 8); w += 32) dst[w] = src[w];
+    __syncwarp();
+    if (lane == 0) {
+      unsigned long long first = 0, N = 0;
+      pending(slots, meta, il, t, first, N);
+      uint32_t gpt;
+      uint64_t g0, g1;
+      pending_chunks(meta[t], first, N, num_sms, &gpt, &g0, &g1);
+      const uint64_t spc = samples_per_group(meta[t].level, meta[t].kp);
+      ItemDesc &it = run[j];
+      it.first = first;
+      it.N = N;
+      it.g0 = g0;
+      it.g1 = g1;
+      it.gf0 = (first + spc - 1) / spc;
+      it.gf1 = (first + N) / spc;
+      if (it.gf1 < it.gf0) it.gf1 = it.gf0;
+      it.groups_per_thread = gpt;
+      it.n_chunks = run_nch[j];
+      it.chunk_begin = run_cb[j];
+      it.out_index = j;
+      run_n[j] = N;
+    }
+    __syncwarp();
+  }
 }
 
 // Sum each item's chunk partials (one warp per item, chunk order) and add the
@@ -549,12 +557,9 @@ void release(mlmc_engine *e) {
 // classes in the graph).
 cudaError_t enqueue_iteration(mlmc_engine *e, const std::vector<int> &live) {
   const int n_tmpl = e->max_slots * e->il;
-  sched_kernel<<<1, 1024, 0, e->cs>>>(e->d_slots, e->d_meta, n_tmpl, e->il, (int)e->groups.size(), e->cap_chunks,
-                                      e->num_sms, e->d_tnch, e->d_run_src, e->d_run_nch, e->d_run_cb, e->d_dyn,
-                                      e->d_status);
-  fill_kernel<<<(n_tmpl + 127) / 128, 128, 0, e->cs>>>(e->d_slots, e->d_meta, e->d_tmpl, e->il, e->num_sms,
-                                                       e->d_run_src, e->d_run_nch, e->d_run_cb, e->d_status,
-                                                       e->d_run, e->d_run_n);
+  sched_kernel<<<1, 1024, 0, e->cs>>>(e->d_slots, e->d_meta, e->d_tmpl, n_tmpl, e->il, (int)e->groups.size(),
+                                      e->cap_chunks, e->num_sms, e->d_tnch, e->d_run_src, e->d_run_nch,
+                                      e->d_run_cb, e->d_dyn, e->d_status, e->d_run, e->d_run_n);
   cudaError_t err = cudaEventRecord(e->fork, e->cs);
   for (size_t i = 0; i < live.size() && err == cudaSuccess; ++i) {
     const Group &G = e->groups[live[i]];
