@@ -183,6 +183,8 @@ void plan_cache_clear();
 // floor: at least four CTAs per SM for this item alone (see chunk_count).
 mlmc_status chunk_built(BuiltItem &b, int threads, int spt, int num_sms, bool floor = true);
 void make_round_keys(uint64_t seed, mlmc::RoundKeys &rk);
+// chunk kind of an item in the merged nested kernel (families 17 / 24), or -1
+int merged_kind(const BuiltItem &b);
 // Launch one level kernel of a family (or, with occ, query the resident CTAs
 // per SM of its device-scheduled kernel).
 cudaError_t launch_by_family(int fam, int scheme, int pc, dim3 grid, dim3 block, size_t smem, cudaStream_t st,

@@ -192,6 +192,15 @@ int family_of(int variant) {
     default: return 21;
   }
 }
+// The chunk kind of an item in the merged nested kernel (families 17 / 24): the
+// 32-bit fixed-point families with Euler-Maruyama and a terminal payoff,
+// 15 approximate packed (0), 8 approximate one sample per thread (1),
+// 10 correction (2); -1 for every other item.
+int merged_kind(const BuiltItem &b) {
+  if (b.scheme != MLMC_EULER || b.pc != PC_TERMINAL || b.it.dump) return -1;
+  return b.family == 15 ? 0 : (b.family == 8 ? 1 : (b.family == 10 ? 2 : -1));
+}
+
 int cost_kind_of(int variant) {
   if (variant == MLMC_FP64_EXACT) return 0;
   if (variant == MLMC_FP32_EXACT) return 1;

@@ -231,11 +231,7 @@ mlmc_status plan_create_impl(mlmc_plan **out, const mlmc_work *work, int n_work,
     // when more than one of them is present: the same chunk bodies, one grid;
     // family 24 when every item's sum1 fits the pre-scaled product.
     {
-      auto kind_of = [&](int i) {
-        const BuiltItem &b = built[i];
-        if (b.scheme != MLMC_EULER || b.pc != PC_TERMINAL || b.it.dump) return -1;
-        return b.family == 15 ? 0 : (b.family == 8 ? 1 : (b.family == 10 ? 2 : -1));
-      };
+      auto kind_of = [&](int i) { return merged_kind(built[i]); };
       int seen = 0;
       bool pre = true;   // every merged item takes the pre-scaled product (family 24)
       for (int i = 0; i < n_work; ++i)
