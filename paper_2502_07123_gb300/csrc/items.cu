@@ -195,9 +195,11 @@ int family_of(int variant) {
 // The chunk kind of an item in the merged nested kernel (families 17 / 24): the
 // 32-bit fixed-point families with Euler-Maruyama and a terminal payoff,
 // 15 approximate packed (0), 8 approximate one sample per thread (1),
-// 10 correction (2); -1 for every other item.
+// 10 correction (2); -1 for every other item (and for enumerated ones).
 int merged_kind(const BuiltItem &b) {
-  if (b.scheme != MLMC_EULER || b.pc != PC_TERMINAL || b.it.dump) return -1;
+  // enumerated items (exact low levels) keep their own launch: the merged
+  // kernel's group code reads Philox words only
+  if (b.scheme != MLMC_EULER || b.pc != PC_TERMINAL || b.it.dump || b.it.enumerate) return -1;
   return b.family == 15 ? 0 : (b.family == 8 ? 1 : (b.family == 10 ? 2 : -1));
 }
 

@@ -102,9 +102,14 @@ __device__ __forceinline__ int32_t ff_sum1(const FastFixed &ff, int32_t z, int32
 // arrives multiplied by 2^(32 - rs2) (the host proved that it fits), so the
 // rounded product rd(S sum1) is the high word of one 64-bit multiply-add: no
 // funnel shift on the ALU pipe, which bounds that kernel.
-template <int EST, int XP, int AP, int SCHEME, int PC, int KP = 1, int MSEL = 0, bool PRE = false>
+// MERGED: the merged nested kernel's instantiation, which takes no enumerated
+// items (the plan keeps those apart), so its group code has no enumeration
+// branch.
+template <int EST, int XP, int AP, int SCHEME, int PC, int KP = 1, int MSEL = 0, bool PRE = false,
+          bool MERGED = false>
 struct LevelSim {
   static_assert(KP == 1 || EST == EST_APPROX, "packed draws feed approximate-only estimators");
+  static constexpr bool ENUMERATE = !MERGED;   // the group code reads enumerated words when asked
   static constexpr bool HAS_EXACT = (EST != EST_APPROX);
   static constexpr bool HAS_APPROX = (EST != EST_EXACT);
   static constexpr bool MIL = (SCHEME == 1);
@@ -837,9 +842,12 @@ __device__ __forceinline__ void run_group(Sim &sim, Acc &acc, const LaunchArgs &
   } else {
     uint64_t gw = g;
     if constexpr (E && Sim::LAZY) opaque(gw);
-    const uint4 w = it.enumerate ? enum_words(gw, LC, it.d)
-                                 : philox4x32_10(make_uint4((uint32_t)gw, (uint32_t)(gw >> 32), it.ctr2, it.ctr3),
-                                                 args.rk);
+    uint4 w;
+    if constexpr (Sim::ENUMERATE)
+      w = it.enumerate ? enum_words(gw, LC, it.d)
+                       : philox4x32_10(make_uint4((uint32_t)gw, (uint32_t)(gw >> 32), it.ctr2, it.ctr3), args.rk);
+    else
+      w = philox4x32_10(make_uint4((uint32_t)gw, (uint32_t)(gw >> 32), it.ctr2, it.ctr3), args.rk);
     constexpr int PPG = LC == 1 ? 2 : 4;  // packs per group
     const uint64_t s0 = (uint64_t)(PPG * KP) * g;
     // samples s0 + k are valid for k in [klo, khi)
@@ -937,10 +945,11 @@ __device__ __forceinline__ void group_loop(Sim &sim, ThreadAcc<EST, XP> &acc, co
 // branch on them.  DYN (device-scheduled kernel) only keeps the
 // instantiations of the static and device-scheduled kernels apart, so that
 // each is compiled inline into its own kernel.
-template <int EST, int XP, int AP, int SCHEME, int PC, int KP, int MSEL, bool DUMP, bool DYN, bool PRE = false>
+template <int EST, int XP, int AP, int SCHEME, int PC, int KP, int MSEL, bool DUMP, bool DYN, bool PRE = false,
+          bool MERGED = false>
 __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDesc &it, int item, uint32_t gc,
                                            const unsigned char *smem_tab) {
-  using Sim = LevelSim<EST, XP, AP, SCHEME, PC, KP, MSEL, PRE>;
+  using Sim = LevelSim<EST, XP, AP, SCHEME, PC, KP, MSEL, PRE, MERGED>;
   Sim sim;
   sim.load(it, smem_tab);
   ThreadAcc<EST, XP> acc;
@@ -1153,11 +1162,11 @@ __global__ void __launch_bounds__(LAUNCH_THREADS, 6) nested_kernel(const __grid_
   const int item = stage_chunk<AP, SCHEME, PRE>(args.items, args.n_items, gc, nullptr);
   const ItemDesc &it = args.items[item];
   if (it.kind == 0)
-    chunk_body<EST_APPROX, XP_F32, AP, SCHEME, PC, 3, 0, false, false, PRE>(args, it, item, gc, smem_tab);
+    chunk_body<EST_APPROX, XP_F32, AP, SCHEME, PC, 3, 0, false, false, PRE, true>(args, it, item, gc, smem_tab);
   else if (it.kind == 1)
-    chunk_body<EST_APPROX, XP_F32, AP, SCHEME, PC, 1, 0, false, false, PRE>(args, it, item, gc, smem_tab);
+    chunk_body<EST_APPROX, XP_F32, AP, SCHEME, PC, 1, 0, false, false, PRE, true>(args, it, item, gc, smem_tab);
   else
-    chunk_body<EST_CORR, XP_F32, AP, SCHEME, PC, 1, 0, false, false, PRE>(args, it, item, gc, smem_tab);
+    chunk_body<EST_CORR, XP_F32, AP, SCHEME, PC, 1, 0, false, false, PRE, true>(args, it, item, gc, smem_tab);
 }
 
 }  // namespace mlmc
