@@ -240,3 +240,28 @@ def test_run_plan_cache_follows_the_work_list(m):
     assert c[0]["isum"] == ref["isum"] and c[0]["isum2"] == ref["isum2"] and c[0]["isum"] != a[0]["isum"]
     P.K = p["K"]
     assert sums(m.mlmc_run(work, 5)) == a
+
+
+def test_item_lookup_over_many_items(m):
+    # a launch of 1500 items (three rounds of the CTAs' warp-ballot item
+    # lookup): every item's exact integer sums equal the item run alone
+    p = W.params()
+    P = _P(m, p, pack=1)
+    rng = np.random.default_rng(5)
+    items = []
+    for i in range(1500):
+        lev = int(rng.integers(0, 4))
+        items.append(dict(params=P, level=lev, variant=W.FIXED_APPROX, N=int(rng.integers(1, 400)),
+                          first_sample=int(rng.integers(0, 10_000))))
+    plan = m.Plan(items, 13)
+    try:
+        assert plan.info()["kernels"] == 1
+        assert plan.launch_info(0)[1] == len(items)
+        plan.launch()
+        res = plan.results()
+    finally:
+        plan.close()
+    for k in rng.choice(len(items), 60, replace=False):
+        it = items[k]
+        one = m.mlmc_level(it["level"], it["N"], P, W.FIXED_APPROX, 13, it["first_sample"])
+        assert res[k]["isum"] == one["isum"] and res[k]["isum2"] == one["isum2"], k
