@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <memory>
 #include <cmath>
 #include <cstdint>
 #include <cstddef>
@@ -141,6 +142,23 @@ bool arena_events(Arena &A, size_t launches) {
   return true;
 }
 
+// A cached single-launch plan's synchronous pass as one CUDA graph (the
+// work-list copy from pinned staging, the timing events and the kernel),
+// replayed while the buffers and round keys it was captured with stay the same.
+struct ReplayGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const void *bufs[6] = {};   // d_items, d_partials, d_out, d_counters, h_items, and t0 (events)
+  const void *t1 = nullptr;
+  RoundKeys rk{};
+  int device = -1;
+  bool failed = false;        // a capture failed: this plan keeps the direct path
+  ~ReplayGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+  }
+};
+
 // Host part of a plan, as mlmc_run's plan cache keeps it.
 struct PlanHost {
   std::vector<ItemDesc> items;
@@ -151,9 +169,11 @@ struct PlanHost {
   uint64_t path_steps;
   uint32_t total_chunks;
   std::vector<uint32_t> empty_out;
+  std::shared_ptr<ReplayGraph> replay;
 };
 std::unordered_map<std::string, PlanHost> g_plan_cache;
 void plan_cache_clear() { g_plan_cache.clear(); }
+cudaStream_t g_capture_st = nullptr;   // stream the replay graphs are captured on
 
 // The bytes a plan's host part depends on: the device, the explicit shape, the
 // shape table's generation and the cost model, and every work item with its
@@ -187,7 +207,8 @@ std::string plan_key(const mlmc_work *work, int n, const mlmc_tuning *tuning) {
 // mlmc_estimate, whose results then equal the engine's, which chunks per item).
 mlmc_status plan_create_impl(mlmc_plan **out, const mlmc_work *work, int n_work, uint64_t seed,
                              const mlmc_tuning *tuning, void *const *dumps, bool launch_chunking,
-                             Arena *arena = nullptr, bool defer_copy = false) {
+                             Arena *arena = nullptr, bool defer_copy = false, PlanHost **entry = nullptr) {
+  if (entry) *entry = nullptr;
   if (!out || !work || n_work <= 0) return MLMC_EINVAL;
   mlmc_status s = ensure_ctx();
   if (s != MLMC_OK) return s;
@@ -320,6 +341,7 @@ mlmc_status plan_create_impl(mlmc_plan **out, const mlmc_work *work, int n_work,
   auto hit = key.empty() ? g_plan_cache.end() : g_plan_cache.find(key);
   if (hit != g_plan_cache.end()) {
     const PlanHost &h = hit->second;
+    if (entry) *entry = &hit->second;
     pl->n_work = n_work;
     pl->items = h.items; pl->launches = h.launches; pl->disc = h.disc; pl->unit = h.unit;
     pl->exact_int = h.exact_int; pl->N = h.N; pl->path_steps = h.path_steps; pl->total_chunks = h.total_chunks;
@@ -328,8 +350,10 @@ mlmc_status plan_create_impl(mlmc_plan **out, const mlmc_work *work, int n_work,
     if ((s = build()) != MLMC_OK) { delete pl; return s; }
     if (!key.empty()) {
       if (g_plan_cache.size() >= 64) g_plan_cache.clear();
-      g_plan_cache.emplace(std::move(key), PlanHost{pl->items, pl->launches, pl->disc, pl->unit, pl->exact_int,
-                                                   pl->N, pl->path_steps, pl->total_chunks, pl->empty_out});
+      auto ins = g_plan_cache.emplace(std::move(key), PlanHost{pl->items, pl->launches, pl->disc, pl->unit,
+                                                              pl->exact_int, pl->N, pl->path_steps,
+                                                              pl->total_chunks, pl->empty_out, nullptr});
+      if (entry) *entry = &ins.first->second;
     }
   }
   const uint32_t chunk = pl->total_chunks;
@@ -406,8 +430,11 @@ mlmc_status plan_create_impl(mlmc_plan **out, const mlmc_work *work, int n_work,
   return MLMC_OK;
 }
 
-mlmc_status plan_launch_impl(mlmc_plan *pl, cudaStream_t st) {
-  MLMC_CK(cudaEventRecord(pl->t0, st));
+// capture: the stream is being captured into a graph, so the timing events
+// are recorded as event nodes of their own (external records)
+mlmc_status plan_launch_impl(mlmc_plan *pl, cudaStream_t st, bool capture = false) {
+  if (capture) MLMC_CK(cudaEventRecordWithFlags(pl->t0, st, cudaEventRecordExternal));
+  else MLMC_CK(cudaEventRecord(pl->t0, st));
   const bool fork = pl->launches.size() > 1;
   if (fork) MLMC_CK(cudaEventRecord(pl->fork, st));
   for (size_t i = 0; i < pl->launches.size(); ++i) {
@@ -440,7 +467,8 @@ mlmc_status plan_launch_impl(mlmc_plan *pl, cudaStream_t st) {
   // are zeroed by the host before the launch)
   if (!pl->out_on_host)
     for (uint32_t o : pl->empty_out) MLMC_CK(cudaMemsetAsync(pl->d_out + o, 0, sizeof(DevSums), st));
-  MLMC_CK(cudaEventRecord(pl->t1, st));
+  if (capture) MLMC_CK(cudaEventRecordWithFlags(pl->t1, st, cudaEventRecordExternal));
+  else MLMC_CK(cudaEventRecord(pl->t1, st));
   pl->last_stream = st;
   pl->launched = true;
   return MLMC_OK;
@@ -505,6 +533,47 @@ bool grow_pinned(T *&p, size_t &cap, size_t need, T **dev = nullptr) {
   return true;
 }
 
+// Launch a cached plan's pass (work-list copy, timing events, kernel) as its
+// replay graph on st, capturing the graph first when it is missing or was
+// captured with other buffers, events, round keys or device.
+mlmc_status replay(PlanHost *entry, mlmc_plan *pl, Arena &A, size_t ni, cudaStream_t st) {
+  if (!entry->replay) entry->replay = std::make_shared<ReplayGraph>();
+  ReplayGraph &R = *entry->replay;
+  const void *bufs[6] = {pl->d_items, pl->d_partials, pl->d_out, pl->d_counters, A.h_items, pl->t0};
+  bool same = R.exec && R.device == g.device && R.t1 == (const void *)pl->t1 &&
+              std::memcmp(R.bufs, bufs, sizeof bufs) == 0 && std::memcmp(&R.rk, &pl->rk, sizeof(RoundKeys)) == 0;
+  if (!same) {
+    if (R.exec) { cudaGraphExecDestroy(R.exec); R.exec = nullptr; }
+    if (R.graph) { cudaGraphDestroy(R.graph); R.graph = nullptr; }
+    if (!g_capture_st) MLMC_CK(cudaStreamCreateWithFlags(&g_capture_st, cudaStreamNonBlocking));
+    MLMC_CK(cudaStreamBeginCapture(g_capture_st, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaMemcpyAsync(pl->d_items, A.h_items, sizeof(ItemDesc) * ni, cudaMemcpyHostToDevice,
+                                    g_capture_st);
+    mlmc_status ls = e == cudaSuccess ? plan_launch_impl(pl, g_capture_st, true) : MLMC_ECUDA;
+    cudaGraph_t gr = nullptr;
+    const cudaError_t end = cudaStreamEndCapture(g_capture_st, &gr);
+    if (ls != MLMC_OK || end != cudaSuccess || !gr) {
+      if (gr) cudaGraphDestroy(gr);
+      R.failed = true;
+      (void)cudaGetLastError();
+      return MLMC_ENOTREADY;
+    }
+    R.graph = gr;
+    if (cudaGraphInstantiate(&R.exec, R.graph, 0) != cudaSuccess) {
+      R.exec = nullptr;
+      R.failed = true;
+      (void)cudaGetLastError();
+      return MLMC_ENOTREADY;
+    }
+    std::memcpy(R.bufs, bufs, sizeof bufs);
+    R.t1 = pl->t1;
+    R.rk = pl->rk;
+    R.device = g.device;
+  }
+  MLMC_CK(cudaGraphLaunch(R.exec, st));
+  return MLMC_OK;
+}
+
 // One synchronous pass on stream st: work list to the device through pinned
 // staging, the launch, one stream sync.  The CTA that completes an item writes
 // its sums straight into mapped pinned host memory, so no copy back is queued
@@ -512,7 +581,8 @@ bool grow_pinned(T *&p, size_t &cap, size_t need, T **dev = nullptr) {
 mlmc_status run_sync(const mlmc_work *work, int n_work, uint64_t seed, const mlmc_tuning *tuning,
                      void *const *dumps, mlmc_sums *out, cudaStream_t st, bool launch_chunking) {
   mlmc_plan *pl = nullptr;
-  mlmc_status s = plan_create_impl(&pl, work, n_work, seed, tuning, dumps, launch_chunking, &g.arena, true);
+  PlanHost *entry = nullptr;
+  mlmc_status s = plan_create_impl(&pl, work, n_work, seed, tuning, dumps, launch_chunking, &g.arena, true, &entry);
   if (s != MLMC_OK) return s;
   Arena &A = g.arena;
   const size_t ni = pl->items.size();
@@ -523,16 +593,26 @@ mlmc_status run_sync(const mlmc_work *work, int n_work, uint64_t seed, const mlm
       break;
     }
     std::memcpy(A.h_items, pl->items.data(), sizeof(ItemDesc) * ni);
-    if (cudaMemcpyAsync(pl->d_items, A.h_items, sizeof(ItemDesc) * ni, cudaMemcpyHostToDevice, st) != cudaSuccess) {
-      s = MLMC_ECUDA;
-      break;
-    }
     // results in host memory: items without samples are zeroed here (no CTA
     // writes them), the others by their last CTA
     pl->d_out = A.d_hout;
     pl->out_on_host = true;
     for (uint32_t o : pl->empty_out) std::memset(&A.h_out[o], 0, sizeof(DevSums));
-    if ((s = plan_launch_impl(pl, st)) != MLMC_OK) break;
+    s = MLMC_ENOTREADY;
+    if (entry && pl->launches.size() == 1 && !(entry->replay && entry->replay->failed)) {
+      // a cached single-launch plan: its pass as one graph launch (a plan whose
+      // capture failed keeps the direct path below)
+      s = replay(entry, pl, A, ni, st);
+      if (s != MLMC_OK && s != MLMC_ENOTREADY) break;
+    }
+    if (s == MLMC_ENOTREADY) {
+      s = MLMC_OK;
+      if (cudaMemcpyAsync(pl->d_items, A.h_items, sizeof(ItemDesc) * ni, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        s = MLMC_ECUDA;
+        break;
+      }
+      if ((s = plan_launch_impl(pl, st)) != MLMC_OK) break;
+    }
     float ms = 0.0f;
     if (cudaStreamSynchronize(st) != cudaSuccess || cudaEventElapsedTime(&ms, pl->t0, pl->t1) != cudaSuccess) {
       s = MLMC_ECUDA;
