@@ -265,3 +265,18 @@ def test_item_lookup_over_many_items(m):
         it = items[k]
         one = m.mlmc_level(it["level"], it["N"], P, W.FIXED_APPROX, 13, it["first_sample"])
         assert res[k]["isum"] == one["isum"] and res[k]["isum2"] == one["isum2"], k
+
+
+def test_run_replay_follows_the_seed(m):
+    # mlmc_run replays a cached single-launch plan as a CUDA graph; a new seed
+    # (new round keys in the kernel's parameters) is captured again, so each
+    # seed's sums equal those computed item by item
+    p = W.params()
+    P = _P(m, p, pack=1)
+    items = [dict(params=P, level=1, variant=W.FIXED_APPROX, N=30_000),
+             dict(params=P, level=3, variant=W.FIXED_APPROX, N=7_000, first_sample=11)]
+    for seed in (5, 6, 5, 6):
+        res = m.mlmc_run(items, seed)
+        for it, r in zip(items, res):
+            one = m.mlmc_level(it["level"], it["N"], P, W.FIXED_APPROX, seed, it.get("first_sample", 0))
+            assert r["isum"] == one["isum"] and r["isum2"] == one["isum2"], seed
