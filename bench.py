@@ -267,6 +267,8 @@ def main():
     ap.add_argument("--no-tte", action="store_true")
     ap.add_argument("--no-serving-sample", action="store_true")
     ap.add_argument("--no-optimiser", action="store_true")
+    ap.add_argument("--no-sweep-levels", action="store_true",
+                    help="skip the brief level-kernel sweep (levels 0-10, every variant, 2^22 paths)")
     ap.add_argument("--sweep", action="store_true",
                     help="also run the level-kernel throughput sweep (Milstein; payoffs x variants x levels)")
     ap.add_argument("--autotune", action="store_true",
@@ -420,6 +422,10 @@ def main():
         out["time_to_eps"] = time_to_eps(m, torch, formats_opt=formats_opt)
     if rank == 0 and world == 1 and args.sweep:
         out["sweep"] = sweep_run(m, torch)
+    elif rank == 0 and world == 1 and not args.no_sweep_levels:
+        # the level-kernel workload in brief: every level 0-10 and every variant
+        # at 2^22 paths (Milstein, European call, sigma 0.2)
+        out["sweep_levels"] = sweep_run(m, torch, levels=range(11), sizes=(1 << 22,), grid=False)
     if rank == 0 and world == 1 and not args.no_serving_sample:
         # bounded serving samples: 200 requests drawn as the serving workload at
         # 100, 1000 and 10000 req/s, accuracies in the coarser half [1e-3, 1e-2] of
@@ -584,7 +590,7 @@ def serving_run(m, rate, n=400, seed=11, mode=5, max_level=16, eps_range=(1e-4, 
 
 
 def sweep_run(m, torch, levels=(0, 2, 4, 6, 8, 10), sizes=(1 << 20, 1 << 24, 1 << 28), grid_n=1 << 22,
-              sigmas=(0.1, 0.2, 0.4)):
+              sigmas=(0.1, 0.2, 0.4), grid=True):
     """Level-kernel throughput sweep (Milstein): path-steps/s of one level-kernel
     launch by CUDA events (median of 5 after 2 warm-up launches, L2 flushed).
     (a) sizes: European call, sigma = 0.2, every variant, N in `sizes` paths at
@@ -630,7 +636,7 @@ def sweep_run(m, torch, levels=(0, 2, 4, 6, 8, 10), sizes=(1 << 20, 1 << 24, 1 <
                 ms, rate = point(P_of(W.EURO, 0.2), lev, v, n)
                 rows.append({"part": "sizes", "payoff": "euro", "sigma": 0.2, "level": lev, "variant": vname,
                              "paths": n, "ms": ms, "path_steps_per_s": rate})
-    for pay_name, pay in (("euro", W.EURO), ("asian", W.ASIAN), ("lookback", W.LOOKBACK)):
+    for pay_name, pay in ((("euro", W.EURO), ("asian", W.ASIAN), ("lookback", W.LOOKBACK)) if grid else ()):
         for sig in sigmas:
             for lev in levels:
                 for vname, v in variants:
