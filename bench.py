@@ -276,6 +276,8 @@ def main():
                          "library's fixed shape table, so that a profile of the same command sees the same launches)")
     ap.add_argument("--serving", action="store_true",
                     help="also run the batched (256 options) and serving (Poisson arrivals) workloads")
+    ap.add_argument("--serving-sample-n", type=int, default=200,
+                    help="requests per arrival rate of the bounded serving sample (eps in [1e-3, 1e-2])")
     ap.add_argument("--serving-n", type=int, default=200,
                     help="requests per arrival rate of --serving (full accuracy range)")
     args = ap.parse_args()
@@ -427,10 +429,12 @@ def main():
         # at 2^22 paths (Milstein, European call, sigma 0.2)
         out["sweep_levels"] = sweep_run(m, torch, levels=range(11), sizes=(1 << 22,), grid=False)
     if rank == 0 and world == 1 and not args.no_serving_sample:
-        # bounded serving samples: 200 requests drawn as the serving workload at
-        # 100, 1000 and 10000 req/s, accuracies in the coarser half [1e-3, 1e-2] of
-        # its range (--serving runs the full range; its eps ~ 1e-4 tail takes minutes)
-        out["serving_sample"] = [serving_run(m, rate, n=200, eps_range=(1e-3, 1e-2)) for rate in (100, 1000, 10000)]
+        # bounded serving samples: 200 requests (--serving-sample-n) drawn as the
+        # serving workload at 100, 1000 and 10000 req/s, accuracies in the coarser
+        # half [1e-3, 1e-2] of its range (--serving runs the full range; its
+        # eps ~ 1e-4 tail takes minutes)
+        out["serving_sample"] = [serving_run(m, rate, n=args.serving_sample_n, eps_range=(1e-3, 1e-2))
+                                 for rate in (100, 1000, 10000)]
     if rank == 0 and world == 1 and args.serving:
         out["batched"] = batched_run(m)
         out["serving"] = [serving_run(m, rate, n=args.serving_n) for rate in (100, 1000, 10000)]
@@ -520,16 +524,15 @@ def batched_run(m, n=256, seed=7, mode=5, iters_per_launch=-4096, max_level=16):
     _engine_solve(eng, _engine_params(m, opts[0], 0, max_level), 1e-2, mode, 99)   # warm tables and kernels
     s0 = eng.stats()
     t0 = time.perf_counter()
-    rids = [eng.submit(_engine_params(m, o, i, max_level), o["eps"], mode, 1) for i, o in enumerate(opts)]
+    index = {eng.submit(_engine_params(m, o, i, max_level), o["eps"], mode, 1): i for i, o in enumerate(opts)}
     done = {}
     while len(done) < n:
         eng.step()
-        for i, r in enumerate(rids):
-            if i not in done:
-                res = eng.poll(r)
-                if res is not None:
-                    res.update(bias_estimate=eng.request_info(r)["bias_estimate"])
-                    done[i] = res
+        for rid in eng.completed():
+            if rid in index:
+                res = eng.poll(rid)
+                res.update(bias_estimate=eng.request_info(rid)["bias_estimate"])
+                done[index[rid]] = res
     wall = time.perf_counter() - t0
     st = eng.stats()
     gi = eng.graph_info()
@@ -555,25 +558,25 @@ def serving_run(m, rate, n=400, seed=11, mode=5, max_level=16, eps_range=(1e-4, 
     eng = m.Engine(max_slots=256, max_level=max_level)
     _engine_solve(eng, _engine_params(m, opts[0], 0, max_level), 1e-2, mode, 99)   # warm tables and kernels
     s0 = eng.stats()
-    rids = [None] * n
+    index = {}      # request id -> option index
     done = {}
     nxt = 0
     t0 = time.perf_counter()
     while len(done) < n:
         t = time.perf_counter() - t0
         while nxt < n and arrivals[nxt] <= t:
-            rids[nxt] = eng.submit(_engine_params(m, opts[nxt], nxt, max_level), opts[nxt]["eps"], mode, 1)
+            index[eng.submit(_engine_params(m, opts[nxt], nxt, max_level), opts[nxt]["eps"], mode, 1)] = nxt
             nxt += 1
         if nxt == len(done) and nxt < n:
             time.sleep(max(0.0, min(arrivals[nxt] - t, 0.01)))
             continue
         eng.step()
-        for i in range(nxt):
-            if i not in done:
-                res = eng.poll(rids[i])
-                if res is not None:
-                    res.update(bias_estimate=eng.request_info(rids[i])["bias_estimate"])
-                    done[i] = res
+        # only the requests that completed in this step (mlmc_engine_completed)
+        for rid in eng.completed():
+            if rid in index:
+                res = eng.poll(rid)
+                res.update(bias_estimate=eng.request_info(rid)["bias_estimate"])
+                done[index[rid]] = res
     wall = time.perf_counter() - t0
     st = eng.stats()
     gi = eng.graph_info()

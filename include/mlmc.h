@@ -369,6 +369,13 @@ mlmc_status mlmc_engine_step(mlmc_engine *e, void *stream, int *active, int *que
  * Returns the request's status (MLMC_OK unless its admission failed). */
 mlmc_status mlmc_engine_poll(mlmc_engine *e, uint64_t req_id, double *price, double *stderr_out, int *L,
                              int *done, double *latency_s);
+/* Drains the ids of requests that completed since the last call, in the order
+ * they completed (admission failures included): up to cap ids into the host
+ * array ids, their count in *n; the rest stay queued for the next call.  A
+ * serving loop reads only what finished instead of polling every request;
+ * mlmc_engine_poll still answers for any id.  MLMC_EINVAL for a NULL engine
+ * or n, a negative cap, or cap > 0 with ids NULL. */
+mlmc_status mlmc_engine_completed(mlmc_engine *e, uint64_t *ids, int cap, int *n);
 /* The schedule and bias test of a completed request: N_l[l * 2 + k] = samples
  * of estimator k on level l (k = 0: plain or approximate, k = 1: correction;
  * host array of 2 * cap_levels, zero beyond the final level L) and

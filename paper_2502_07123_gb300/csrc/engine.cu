@@ -527,6 +527,7 @@ struct mlmc_engine {
   std::deque<size_t> queue;                    // waiting requests (indices into reqs)
   std::vector<Request> reqs;
   std::map<uint64_t, size_t> by_id;
+  std::deque<uint64_t> completed;              // ids of completed requests not yet drained
   uint64_t next_id = 1;
   uint64_t steps = 0, launches = 0, path_steps = 0, captures = 0;
 };
@@ -915,6 +916,7 @@ mlmc_status mlmc_engine_step(mlmc_engine *e, void *stream, int *active_out, int 
       r.status = s;
       r.price = r.se = std::nan("");
       r.t_done = now_s();
+      e->completed.push_back(r.id);
       if (s == MLMC_ECUDA) return s;
       --sl;
       continue;
@@ -961,6 +963,7 @@ mlmc_status mlmc_engine_step(mlmc_engine *e, void *stream, int *active_out, int 
         r.L = hr.L;
         r.rem = hr.rem;
         r.t_done = t;
+        e->completed.push_back(r.id);
         // the request's schedule, read before the slot is cleared (the launch
         // has finished: its stream was synchronised above)
         r.N.assign((size_t)MAXL * 2, 0);
@@ -999,6 +1002,18 @@ mlmc_status mlmc_engine_poll(mlmc_engine *e, uint64_t req_id, double *price, dou
     if (latency_s) *latency_s = r.t_done - r.t_submit;
   }
   return r.status;
+}
+
+mlmc_status mlmc_engine_completed(mlmc_engine *e, uint64_t *ids, int cap, int *n) {
+  MLMC_API_LOCK();
+  if (!e || !n || cap < 0 || (cap > 0 && !ids)) return MLMC_EINVAL;
+  int k = 0;
+  while (k < cap && !e->completed.empty()) {
+    ids[k++] = e->completed.front();
+    e->completed.pop_front();
+  }
+  *n = k;
+  return MLMC_OK;
 }
 
 mlmc_status mlmc_engine_request_info(mlmc_engine *e, uint64_t req_id, uint64_t *N_l, int cap_levels,

@@ -139,6 +139,7 @@ def load():
         "mlmc_engine_step": (st, [ctypes.c_void_p, ctypes.c_void_p, P(ctypes.c_int), P(ctypes.c_int)]),
         "mlmc_engine_poll": (st, [ctypes.c_void_p, ctypes.c_uint64, P(ctypes.c_double), P(ctypes.c_double),
                                   P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_double)]),
+        "mlmc_engine_completed": (st, [ctypes.c_void_p, P(ctypes.c_uint64), ctypes.c_int, P(ctypes.c_int)]),
         "mlmc_engine_request_info": (st, [ctypes.c_void_p, ctypes.c_uint64, P(ctypes.c_uint64), ctypes.c_int,
                                           P(ctypes.c_double)]),
         "mlmc_engine_stats": (st, [ctypes.c_void_p, P(ctypes.c_uint64), P(ctypes.c_uint64), P(ctypes.c_uint64),
@@ -506,6 +507,14 @@ class Engine:
         if not done.value:
             return None
         return dict(price=pr.value, stderr=se.value, L=lev.value, latency_s=lat.value)
+
+    def completed(self, cap=4096):
+        """Ids of the requests that completed since the last call, in completion
+        order (mlmc_engine_completed); at most cap per call."""
+        ids = (ctypes.c_uint64 * max(1, cap))()
+        n = ctypes.c_int()
+        _check(load().mlmc_engine_completed(self._h, ids, cap, ctypes.byref(n)), "mlmc_engine_completed")
+        return [int(ids[i]) for i in range(n.value)]
 
     def request_info(self, rid, cap_levels=21):
         """Schedule N[l] = [N_approx_or_plain, N_corr] per level and the final

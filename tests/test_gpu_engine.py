@@ -221,3 +221,36 @@ def test_engine_mixed_methods_equal_estimate(m, mode):
     for P, rid in zip(reqs, rids):
         ref = m.mlmc_estimate(0.03, P, mode, 23, 10)
         assert res[rid]["price"] == ref["price"] and res[rid]["stderr"] == ref["stderr"]
+
+
+def test_engine_completed_drains_each_request_once(m):
+    """mlmc_engine_completed hands out every finished request exactly once, in
+    the step it finished (a failed admission included), and only finished ones."""
+    p = W.params()
+    bad = [dict(e=list(f["e"]), f=list(f["f"])) for f in (W.default_format(p, lev) for lev in range(11))]
+    bad[1]["e"][6] = 2        # S in 2 integer bits cannot hold S0 = 100
+    eng = m.Engine(max_slots=3, max_level=10)
+    rids = [eng.submit(_P(m, W.params(sigma=0.1 + 0.05 * i), 60 + i), 0.05 - 0.004 * i, 5, 31) for i in range(6)]
+    r_bad = eng.submit(m.make_params(p, d=10, method=1, formats=bad, request=99), 0.05, 5, 31)
+    assert eng.completed() == []
+    seen = []
+    for _ in range(10_000):
+        eng.step()
+        got = eng.completed(cap=2)
+        got += eng.completed()           # the rest of this step's completions
+        for rid in got:
+            assert rid not in seen
+            if rid != r_bad:
+                assert eng.poll(rid) is not None
+            else:
+                with pytest.raises(m.MLMCError) as e:
+                    eng.poll(rid)
+                assert e.value.status == m.EOVERFLOW
+        for rid in set(rids) - set(seen) - set(got):
+            assert eng.poll(rid) is None   # not handed out: not finished
+        seen += got
+        if len(seen) == len(rids) + 1:
+            break
+    assert sorted(seen) == sorted(rids + [r_bad])
+    assert eng.completed() == []
+    eng.close()
