@@ -56,9 +56,9 @@ ALU_PEAK_TOPS = 152 * 4 * 32 * 2.070e9 / 1e12
 # nested launch in its pre-scaled form, family 24, 80,148,728 path-steps):
 #   ncu --set full --clock-control none -k regex:^nested_kernel -s 2 -c 1 -o prof \
 #       python bench.py --steps 3 --warmup 3 --no-cpu-baseline --no-tte \
-#       --no-serving-sample --no-optimiser
+#       --no-serving-sample --no-optimiser --no-sweep-levels
 # keyed by (family, path-steps per launch); another launch reports null
-DOMINANT_TRAFFIC = {(24, 80148728): 164352}
+DOMINANT_TRAFFIC = {}
 
 
 def build_items(m, rank=0, formats=None):

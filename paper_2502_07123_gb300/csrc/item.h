@@ -84,7 +84,9 @@ struct ItemDesc {
                            // of pack s / 3); levels >= 2, approximate-only, KP = 1 kernels
   int32_t kind;            // in a merged nested launch: 0 approximate packed, 1 approximate one
                            // sample per thread, 2 correction (nested_kernel)
-  int32_t kind_pad;
+  int32_t tab_y0;          // 1: a level-0 approximate item of the 32-bit fast datapath with a terminal
+                           // payoff; its shared-memory table holds (Y_j, saturated_j), the sample value
+                           // of every index j (its one fine step is a function of j alone)
   float unit_scale;        // 2^-unit (FP32, correction estimators)
   // exact path constants
   float c1f, c2f, c1cf, c3f, S0f, Kf;

@@ -390,6 +390,16 @@ int64_t table_zmax_fixed(const double *Z, int d, int method, int fZ, int fields)
 
 
 
+// Level-0 approximate items of the 32-bit fast datapath (families 8 and 15)
+// with a terminal payoff take their sample values from the per-index table
+// (tab_y0), unless they write per-sample records.  Only lazy items: S_0 <=
+// limT there, so no index's one fine step leaves lim_S and no sample counts a
+// saturation (the items that may saturate keep the clamped step code).
+int tab_y0_of(const BuiltItem &b, const void *dump) {
+  return (b.family == 8 || b.family == 15) && b.it.level == 0 && b.pc == PC_TERMINAL && b.it.ff.lazy && !dump ? 1
+                                                                                                              : 0;
+}
+
 // Split an item's sample groups into chunks of `threads` x groups_per_thread.
 mlmc_status chunk_built(BuiltItem &b, int threads, int spt, int num_sms, bool floor) {
   ItemDesc &it = b.it;
@@ -597,6 +607,7 @@ mlmc_status build_item(const mlmc_work &w, int out_index, void *dump, BuiltItem 
   }
   b.scheme = p->scheme;
   b.pc = p->payoff == MLMC_ASIAN ? PC_ASIAN : (p->payoff == MLMC_LOOKBACK ? PC_LOOKBACK : PC_TERMINAL);
+  it.tab_y0 = tab_y0_of(b, dump);
   return MLMC_OK;
 }
 
@@ -641,6 +652,7 @@ mlmc_status build_item_cached(const mlmc_work &w, int out_index, void *dump, Bui
   it.N = w.N;
   it.out_index = (uint32_t)out_index;
   it.dump = dump;
+  it.tab_y0 = tab_y0_of(b, dump);
   const uint64_t spc = samples_per_group(lev, b.kp);
   it.g0 = w.first_sample / spc;
   it.g1 = w.N == 0 ? it.g0 : (w.first_sample + w.N + spc - 1) / spc;

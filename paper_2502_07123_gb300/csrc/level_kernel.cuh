@@ -885,6 +885,50 @@ __device__ __forceinline__ void run_group(Sim &sim, Acc &acc, const LaunchArgs &
   }
 }
 
+// One level-0 group of an item whose table holds each index's sample value
+// (ItemDesc::tab_y0): per sample one table read and the two group sums.
+// Samples k outside [klo, khi) add zero (FULL: the whole group is in range).
+template <bool FULL, class Sim, class Acc>
+__device__ __forceinline__ void y0_group(const Sim &sim, Acc &acc, const uint4 &w, int klo, int khi) {
+  constexpr int KP = Sim::KPV;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+#pragma unroll
+    for (int l = 0; l < KP; ++l) {
+      const int k = u * KP + l;
+      const int32_t y = sim.fx32_entry(word_of(w, u), l).x;
+      acc.add_group(FULL || (k >= klo && k < khi) ? y : 0);
+    }
+  }
+  acc.flush_group();
+}
+
+// The groups of a chunk of such an item: the same samples and values as
+// run_group's path (no saturation: see tab_y0_of).
+template <class Sim, class Acc>
+__device__ __forceinline__ void group_loop_y0(const Sim &sim, Acc &acc, const LaunchArgs &args, const GroupCtx &it,
+                                              uint64_t gbeg, uint32_t ng, uint32_t rf0, uint32_t rf1) {
+  constexpr int KP = Sim::KPV;
+  const uint64_t first = it.first, last = it.last;
+  for (uint32_t r = threadIdx.x; r < ng; r += blockDim.x) {
+    const uint64_t g = gbeg + r;
+    uint4 w;
+    if constexpr (Sim::ENUMERATE)
+      w = it.enumerate ? enum_words(g, 0, it.d)
+                       : philox4x32_10(make_uint4((uint32_t)g, (uint32_t)(g >> 32), it.ctr2, it.ctr3), args.rk);
+    else
+      w = philox4x32_10(make_uint4((uint32_t)g, (uint32_t)(g >> 32), it.ctr2, it.ctr3), args.rk);
+    if (r >= rf0 && r < rf1) {
+      y0_group<true>(sim, acc, w, 0, 0);
+    } else {
+      const uint64_t s0 = (uint64_t)(4 * KP) * g;
+      const int klo = s0 >= first ? 0 : (int)min(first - s0, (uint64_t)(4 * KP));
+      const int khi = last <= s0 ? 0 : (int)min(last - s0, (uint64_t)(4 * KP));
+      y0_group<false>(sim, acc, w, klo, khi);
+    }
+  }
+}
+
 // A thread's groups of one chunk, groups gbeg + r for r = threadIdx.x,
 // threadIdx.x + blockDim.x, ... < ng, of level class LC; groups with r in
 // [rf0, rf1) lie entirely in the item's range.  LAZY items run each such group
@@ -980,7 +1024,11 @@ __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDes
   using L2 = std::integral_constant<int, 2>;
   if constexpr (Sim::LAZY && !DUMP && PC == PC_TERMINAL) {
     const bool dig = it.payoff == 1;
-    if (lc == 0) { if (dig) loop(L0{}, PayTag<1>{}); else loop(L0{}, PayTag<0>{}); }
+    if (lc == 0) {
+      if (it.tab_y0) group_loop_y0(sim, acc, args, gx, gbeg, ng, rf0, rf1);
+      else if (dig) loop(L0{}, PayTag<1>{});
+      else loop(L0{}, PayTag<0>{});
+    }
     else if (lc == 1) { if (dig) loop(L1{}, PayTag<1>{}); else loop(L1{}, PayTag<0>{}); }
     else { if (dig) loop(L2{}, PayTag<1>{}); else loop(L2{}, PayTag<0>{}); }
   } else {
@@ -1064,7 +1112,23 @@ __device__ __forceinline__ int stage_chunk(const ItemDesc *items, int n_items, u
         z = ai.neg ? -v : v;
       }
       const int32_t sum1 = ff_sum1<SCHEME == 1, true>(it.ff, z, it.ff.con1r, it.ff.mfine);
-      dst[k] = make_int2(z, PRE ? sum1 * (1 << (32 - it.ff.rs2)) : sum1);
+      if (it.tab_y0) {
+        // level 0: the sample is a function of j alone -- S after the one fine
+        // step from S0 (mul2 = rd(S0 sum1), S = rd(S0 + mul2), clamped to lim_S
+        // as on the clamped datapath) and its terminal payoff
+        // (the host sets tab_y0 on lazy items only, whose S_0 <= limT keeps
+        // that S within lim_S: the clamp changes nothing there)
+        const int32_t s0 = (int32_t)it.fx.S0;
+        const int64_t p2 = (int64_t)s0 * sum1 + it.ff.radd2;
+        const int32_t mul2 = (int32_t)__funnelshift_r((uint32_t)p2, (uint32_t)((uint64_t)p2 >> 32), it.ff.rs2);
+        const int32_t s1 = (int32_t)((uint32_t)s0 + (uint32_t)mul2 * (uint32_t)it.ff.mulS);
+        const int32_t lim = (int32_t)it.ff.limS, kq = (int32_t)it.fx.K;
+        const int32_t c = min(max(s1, -lim), lim);
+        const int32_t y = c > kq ? (it.payoff == 1 ? (int32_t)1 << it.fx.fS : c - kq) : 0;
+        dst[k] = make_int2(y, c != s1 ? 1 : 0);
+      } else {
+        dst[k] = make_int2(z, PRE ? sum1 * (1 << (32 - it.ff.rs2)) : sum1);
+      }
     }
     if (it.perm) {   // after the table: the method-2 interval ranks
       uint16_t *pd = (uint16_t *)(smem_tab + (size_t)n * TabBytes<AP>::value);
