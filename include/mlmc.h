@@ -248,6 +248,12 @@ mlmc_status mlmc_plan_info(const mlmc_plan *plan, int *kernels, uint64_t *ctas,
  * approximate with packed draws 22 / 23).  Waits for that kernel.  MLMC_ENOTREADY before
  * the first launch, MLMC_EINVAL for k out of range. */
 mlmc_status mlmc_plan_kernel_time(const mlmc_plan *plan, int k, int *family, double *ms);
+/* Device time (ms) of the whole last launch of the plan: CUDA events recorded
+ * on the launch stream right before its first kernel and after its last one
+ * (joined streams included); for a one-kernel plan, the same events as
+ * mlmc_plan_kernel_time(plan, 0).  Waits for the launch.  MLMC_ENOTREADY
+ * before the first launch, MLMC_EINVAL for a NULL plan or ms. */
+mlmc_status mlmc_plan_elapsed(const mlmc_plan *plan, double *ms);
 /* Level-kernel launch k of the plan (0 <= k < kernels of mlmc_plan_info):
  * its kernel family, work items, CTAs and fine path-steps (sum of N 2^l over
  * its items); any output may be NULL.  MLMC_EINVAL for k out of range. */

@@ -433,9 +433,17 @@ mlmc_status plan_create_impl(mlmc_plan **out, const mlmc_work *work, int n_work,
 // capture: the stream is being captured into a graph, so the timing events
 // are recorded as event nodes of their own (external records)
 mlmc_status plan_launch_impl(mlmc_plan *pl, cudaStream_t st, bool capture = false) {
+  // items without samples: zero sums (no CTA writes them; host-side results
+  // are zeroed by the host before the launch)
+  if (!pl->out_on_host)
+    for (uint32_t o : pl->empty_out) MLMC_CK(cudaMemsetAsync(pl->d_out + o, 0, sizeof(DevSums), st));
   if (capture) MLMC_CK(cudaEventRecordWithFlags(pl->t0, st, cudaEventRecordExternal));
   else MLMC_CK(cudaEventRecord(pl->t0, st));
   const bool fork = pl->launches.size() > 1;
+  // per-kernel events only for plans a caller owns (mlmc_plan_kernel_time) with
+  // more than one launch: a single launch is timed by the plan's own events,
+  // which then bracket that kernel alone
+  const bool kev = !pl->borrowed && fork;
   if (fork) MLMC_CK(cudaEventRecord(pl->fork, st));
   for (size_t i = 0; i < pl->launches.size(); ++i) {
     const LaunchRec &L = pl->launches[i];
@@ -454,19 +462,14 @@ mlmc_status plan_launch_impl(mlmc_plan *pl, cudaStream_t st, bool capture = fals
     a.counters = pl->d_counters + L.item_off;
     a.out = pl->d_out;
     a.dump = L.dump ? 1 : 0;
-    // per-kernel events only for plans a caller owns (mlmc_plan_kernel_time)
-    if (!pl->borrowed) MLMC_CK(cudaEventRecord(pl->kstart[i], ls));
+    if (kev) MLMC_CK(cudaEventRecord(pl->kstart[i], ls));
     MLMC_CK(launch_by_family(L.family, L.scheme, L.pc, dim3(L.n_chunks), dim3(L.threads), L.smem, ls, a, nullptr));
-    if (!pl->borrowed) MLMC_CK(cudaEventRecord(pl->kstop[i], ls));
+    if (kev) MLMC_CK(cudaEventRecord(pl->kstop[i], ls));
     if (fork) {
       MLMC_CK(cudaEventRecord(pl->join[i], ls));
       MLMC_CK(cudaStreamWaitEvent(st, pl->join[i], 0));
     }
   }
-  // items without samples: zero sums (no CTA writes them; host-side results
-  // are zeroed by the host before the launch)
-  if (!pl->out_on_host)
-    for (uint32_t o : pl->empty_out) MLMC_CK(cudaMemsetAsync(pl->d_out + o, 0, sizeof(DevSums), st));
   if (capture) MLMC_CK(cudaEventRecordWithFlags(pl->t1, st, cudaEventRecordExternal));
   else MLMC_CK(cudaEventRecord(pl->t1, st));
   pl->last_stream = st;
@@ -743,11 +746,24 @@ mlmc_status mlmc_plan_kernel_time(const mlmc_plan *plan, int k, int *family, dou
   if (!plan->launched) return MLMC_ENOTREADY;
   if (family) *family = plan->launches[k].family;
   if (ms) {
-    MLMC_CK(cudaEventSynchronize(plan->kstop[k]));
+    // a single launch: the plan's events bracket the kernel alone
+    const bool one = plan->launches.size() == 1;
+    const cudaEvent_t a = one ? plan->t0 : plan->kstart[k], b = one ? plan->t1 : plan->kstop[k];
+    MLMC_CK(cudaEventSynchronize(b));
     float t = 0.0f;
-    MLMC_CK(cudaEventElapsedTime(&t, plan->kstart[k], plan->kstop[k]));
+    MLMC_CK(cudaEventElapsedTime(&t, a, b));
     *ms = t;
   }
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_plan_elapsed(const mlmc_plan *plan, double *ms) {
+  if (!plan || !ms) return MLMC_EINVAL;
+  if (!plan->launched) return MLMC_ENOTREADY;
+  MLMC_CK(cudaEventSynchronize(plan->t1));
+  float t = 0.0f;
+  MLMC_CK(cudaEventElapsedTime(&t, plan->t0, plan->t1));
+  *ms = t;
   return MLMC_OK;
 }
 

@@ -123,6 +123,7 @@ def load():
         "mlmc_plan_info": (st, [ctypes.c_void_p, P(ctypes.c_int), P(ctypes.c_uint64), P(ctypes.c_uint64),
                                 P(ctypes.c_uint64), P(ctypes.c_uint64)]),
         "mlmc_plan_kernel_time": (st, [ctypes.c_void_p, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_double)]),
+        "mlmc_plan_elapsed": (st, [ctypes.c_void_p, P(ctypes.c_double)]),
         "mlmc_plan_launch_info": (st, [ctypes.c_void_p, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int),
                                        P(ctypes.c_uint64), P(ctypes.c_uint64)]),
         "mlmc_plan_launch_items": (st, [ctypes.c_void_p, ctypes.c_int, P(ctypes.c_int32), ctypes.c_int,
@@ -367,6 +368,12 @@ class Plan:
         _check(load().mlmc_plan_kernel_time(self._h, k, ctypes.byref(fam), ctypes.byref(ms)),
                "mlmc_plan_kernel_time")
         return fam.value, ms.value
+
+    def elapsed_ms(self):
+        """Device time (ms) of the whole last launch (mlmc_plan_elapsed)."""
+        ms = ctypes.c_double()
+        _check(load().mlmc_plan_elapsed(self._h, ctypes.byref(ms)), "mlmc_plan_elapsed")
+        return ms.value
 
     def close(self):
         if self._h:

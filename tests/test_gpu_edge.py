@@ -165,6 +165,35 @@ def test_plan_launch_items_partition_the_work(m):
         plan.close()
 
 
+def test_plan_elapsed_brackets_the_launch(m):
+    # mlmc_plan_elapsed: the whole launch's device time; a one-kernel plan is
+    # timed by the same events as its kernel, a plan of several launches by
+    # events around all of them (and its items with no samples read zero)
+    p = W.params()
+    P = _P(m, p, pack=1)
+    one = m.Plan([dict(params=P, level=3, variant=W.FIXED_APPROX, N=300_000)], 5)
+    several = m.Plan([dict(params=P, level=lev, variant=v, N=n)
+                      for lev, n in ((0, 400_000), (4, 20_000), (6, 0))
+                      for v in (W.FIXED_APPROX, W.FP32_EXACT)], 5)
+    try:
+        with pytest.raises(m.MLMCError) as e:
+            one.elapsed_ms()
+        assert e.value.status == m.ENOTREADY
+        one.launch()
+        assert one.info()["kernels"] == 1
+        assert one.elapsed_ms() == one.kernel_time(0)[1] > 0.0
+        several.launch()
+        k = several.info()["kernels"]
+        assert k >= 2
+        total = several.elapsed_ms()
+        assert all(0.0 < several.kernel_time(j)[1] <= total for j in range(k))
+        res = several.results()
+        assert all(r["n"] == 0 and r["sum"] == 0.0 and r["sum2"] == 0.0 for r in res[4:])
+    finally:
+        one.close()
+        several.close()
+
+
 def test_worklist_and_raw_results(m):
     # a marshalled-once work list and the structured-array results give the
     # same sums as the list-of-dicts call
