@@ -1117,7 +1117,9 @@ __device__ __forceinline__ int stage_chunk(const ItemDesc *items, int n_items, u
         // step from S0 (mul2 = rd(S0 sum1), S = rd(S0 + mul2), clamped to lim_S
         // as on the clamped datapath) and its terminal payoff
         // (the host sets tab_y0 on lazy items only, whose S_0 <= limT keeps
-        // that S within lim_S: the clamp changes nothing there)
+        // that S within lim_S: the clamp changes nothing there).  The same
+        // arithmetic as LevelSim::ff_apply's 32-bit step and fixed_payoff's
+        // 32-bit terminal payoff; the level-0 parity tests hold the two equal.
         const int32_t s0 = (int32_t)it.fx.S0;
         const int64_t p2 = (int64_t)s0 * sum1 + it.ff.radd2;
         const int32_t mul2 = (int32_t)__funnelshift_r((uint32_t)p2, (uint32_t)((uint64_t)p2 >> 32), it.ff.rs2);
