@@ -41,6 +41,8 @@ WORKLOAD = ("nested MLMC step: euro+digital call GBM, EM, levels 0-8, N~ 1e7..1e
 #   fixed-point Algorithm-1 fine step (2 products, 2 sums, 4 roundings): 10
 #   coarse step every other fine step: (1 + 10) / 2 = 5.5
 OPS_APPROX_FIXED_EM = 30.5
+# level 0 has no coarse path (P_-1 = 0): 30.5 - 5.5
+OPS_APPROX_FIXED_EM_L0 = 25.0
 # Correction estimator (FP32 exact minus fixed point on the same J), Euler-Maruyama:
 #   Philox4x32-10, one word per path-step: 10
 #   exact Normal: U = 2^-32 (J + 1/2) with the symmetric fold 3, Phi^-1 in single
@@ -49,6 +51,8 @@ OPS_APPROX_FIXED_EM = 30.5
 #   exact fine step 2 (increment, S update); coarse every other step (3) / 2 = 1.5
 #   approximate part: index, lookup and sign 5, fine Algorithm-1 step 10, coarse 5.5
 OPS_CORR_FIXED_EM = 54.0
+# level 0: no coarse path, exact or approximate: 54 - 1.5 - 5.5
+OPS_CORR_FIXED_EM_L0 = 47.0
 # SM issue peak: 152 SMs x 4 schedulers x 32 lanes x 2070 MHz (one warp instruction per scheduler per clock)
 ALU_PEAK_TOPS = 152 * 4 * 32 * 2.070e9 / 1e12
 # DRAM bytes (read + write) of the dominant launch, from one ncu capture of this
@@ -385,7 +389,11 @@ def main():
         idx = plan.launch_items(j)
         ps_a = sum(items[i]["N"] << items[i]["level"] for i in idx if items[i]["variant"] != W.CORR_FIXED)
         ps_c = sum(items[i]["N"] << items[i]["level"] for i in idx if items[i]["variant"] == W.CORR_FIXED)
-        ops = OPS_APPROX_FIXED_EM * ps_a + OPS_CORR_FIXED_EM * ps_c
+        # level-0 path-steps have no coarse step
+        ps_a0 = sum(items[i]["N"] for i in idx if items[i]["variant"] != W.CORR_FIXED and items[i]["level"] == 0)
+        ps_c0 = sum(items[i]["N"] for i in idx if items[i]["variant"] == W.CORR_FIXED and items[i]["level"] == 0)
+        ops = (OPS_APPROX_FIXED_EM * (ps_a - ps_a0) + OPS_APPROX_FIXED_EM_L0 * ps_a0
+               + OPS_CORR_FIXED_EM * (ps_c - ps_c0) + OPS_CORR_FIXED_EM_L0 * ps_c0)
         dom_ms = sum(launch_ms[j]) / len(launch_ms[j])
         achieved = ops / (dom_ms * 1e-3) / 1e12
         fam_, _, ctas_, _ = launches[j]
@@ -393,8 +401,12 @@ def main():
                     "frac": achieved / ALU_PEAK_TOPS, "traffic": DOMINANT_TRAFFIC.get((dom, ps)),
                     "kernel": fam_names[dom], "ctas": ctas_,
                     "ms_per_launch": dom_ms,
-                    "ops_per_path_step": {"approximate": OPS_APPROX_FIXED_EM, "correction": OPS_CORR_FIXED_EM},
-                    "path_steps_per_launch": ps, "approximate_path_steps": ps_a, "correction_path_steps": ps_c}
+                    "ops_per_path_step": {"approximate": OPS_APPROX_FIXED_EM, "correction": OPS_CORR_FIXED_EM,
+                                          "approximate_level0": OPS_APPROX_FIXED_EM_L0,
+                                          "correction_level0": OPS_CORR_FIXED_EM_L0},
+                    "ops_per_launch": ops,
+                    "path_steps_per_launch": ps, "approximate_path_steps": ps_a, "correction_path_steps": ps_c,
+                    "level0_path_steps": {"approximate": ps_a0, "correction": ps_c0}}
         alone_ms = dominant_alone(m, torch, items, cfg["seed"], tuning, plan, j, flush, stream)
         if alone_ms:
             # the same launch with the GPU to itself (in the step it may share the
