@@ -150,7 +150,8 @@ extern "C" mlmc_status mlmc_estimate(double eps, const mlmc_params *p, int mode,
         }
     if (!work.empty()) {
       res.resize(work.size());
-      s = run_sync(work.data(), (int)work.size(), seed, nullptr, nullptr, res.data(), g.st, false);
+      // (the rounds' device times are not used: no timing events)
+      s = run_sync(work.data(), (int)work.size(), seed, nullptr, nullptr, res.data(), g.st, false, false);
       if (s != MLMC_OK) return s;
       for (size_t j = 0; j < work.size(); ++j) {
         const int l = idx[j].first, k = idx[j].second;

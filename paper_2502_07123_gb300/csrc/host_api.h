@@ -198,7 +198,9 @@ __global__ void finalize_kernel(const mlmc::ItemDesc *items, int n_items, const 
                                 mlmc::DevSums *out);
 double u128_to_double(uint64_t lo, uint64_t hi);
 // Plan, launch, read and release in one synchronous call on stream st.
+// timed = false: no timing events around the launch, out[i].seconds = 0.
 mlmc_status run_sync(const mlmc_work *work, int n_work, uint64_t seed, const mlmc_tuning *tuning,
-                     void *const *dumps, mlmc_sums *out, cudaStream_t st, bool launch_chunking);
+                     void *const *dumps, mlmc_sums *out, cudaStream_t st, bool launch_chunking,
+                     bool timed = true);
 
 }  // namespace mlmc_host

@@ -432,18 +432,18 @@ mlmc_status plan_create_impl(mlmc_plan **out, const mlmc_work *work, int n_work,
 
 // capture: the stream is being captured into a graph, so the timing events
 // are recorded as event nodes of their own (external records)
-mlmc_status plan_launch_impl(mlmc_plan *pl, cudaStream_t st, bool capture = false) {
+mlmc_status plan_launch_impl(mlmc_plan *pl, cudaStream_t st, bool capture = false, bool timed = true) {
   // items without samples: zero sums (no CTA writes them; host-side results
   // are zeroed by the host before the launch)
   if (!pl->out_on_host)
     for (uint32_t o : pl->empty_out) MLMC_CK(cudaMemsetAsync(pl->d_out + o, 0, sizeof(DevSums), st));
   if (capture) MLMC_CK(cudaEventRecordWithFlags(pl->t0, st, cudaEventRecordExternal));
-  else MLMC_CK(cudaEventRecord(pl->t0, st));
+  else if (timed) MLMC_CK(cudaEventRecord(pl->t0, st));
   const bool fork = pl->launches.size() > 1;
   // per-kernel events only for plans a caller owns (mlmc_plan_kernel_time) with
   // more than one launch: a single launch is timed by the plan's own events,
   // which then bracket that kernel alone
-  const bool kev = !pl->borrowed && fork;
+  const bool kev = !pl->borrowed && fork && timed;
   if (fork) MLMC_CK(cudaEventRecord(pl->fork, st));
   for (size_t i = 0; i < pl->launches.size(); ++i) {
     const LaunchRec &L = pl->launches[i];
@@ -471,7 +471,7 @@ mlmc_status plan_launch_impl(mlmc_plan *pl, cudaStream_t st, bool capture = fals
     }
   }
   if (capture) MLMC_CK(cudaEventRecordWithFlags(pl->t1, st, cudaEventRecordExternal));
-  else MLMC_CK(cudaEventRecord(pl->t1, st));
+  else if (timed) MLMC_CK(cudaEventRecord(pl->t1, st));
   pl->last_stream = st;
   pl->launched = true;
   return MLMC_OK;
@@ -582,7 +582,7 @@ mlmc_status replay(PlanHost *entry, mlmc_plan *pl, Arena &A, size_t ni, cudaStre
 // its sums straight into mapped pinned host memory, so no copy back is queued
 // (a small device-to-host copy costs about as much as the launch itself).
 mlmc_status run_sync(const mlmc_work *work, int n_work, uint64_t seed, const mlmc_tuning *tuning,
-                     void *const *dumps, mlmc_sums *out, cudaStream_t st, bool launch_chunking) {
+                     void *const *dumps, mlmc_sums *out, cudaStream_t st, bool launch_chunking, bool timed) {
   mlmc_plan *pl = nullptr;
   PlanHost *entry = nullptr;
   mlmc_status s = plan_create_impl(&pl, work, n_work, seed, tuning, dumps, launch_chunking, &g.arena, true, &entry);
@@ -602,7 +602,7 @@ mlmc_status run_sync(const mlmc_work *work, int n_work, uint64_t seed, const mlm
     pl->out_on_host = true;
     for (uint32_t o : pl->empty_out) std::memset(&A.h_out[o], 0, sizeof(DevSums));
     s = MLMC_ENOTREADY;
-    if (entry && pl->launches.size() == 1 && !(entry->replay && entry->replay->failed)) {
+    if (timed && entry && pl->launches.size() == 1 && !(entry->replay && entry->replay->failed)) {
       // a cached single-launch plan: its pass as one graph launch (a plan whose
       // capture failed keeps the direct path below)
       s = replay(entry, pl, A, ni, st);
@@ -614,10 +614,11 @@ mlmc_status run_sync(const mlmc_work *work, int n_work, uint64_t seed, const mlm
         s = MLMC_ECUDA;
         break;
       }
-      if ((s = plan_launch_impl(pl, st)) != MLMC_OK) break;
+      if ((s = plan_launch_impl(pl, st, false, timed)) != MLMC_OK) break;
     }
     float ms = 0.0f;
-    if (cudaStreamSynchronize(st) != cudaSuccess || cudaEventElapsedTime(&ms, pl->t0, pl->t1) != cudaSuccess) {
+    if (cudaStreamSynchronize(st) != cudaSuccess ||
+        (timed && cudaEventElapsedTime(&ms, pl->t0, pl->t1) != cudaSuccess)) {
       s = MLMC_ECUDA;
       break;
     }
