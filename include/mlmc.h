@@ -522,6 +522,16 @@ mlmc_status mlmc_icdf_method2(int d, int n, double *x, uint32_t *perm, int *iter
  * with method 2 is this with n = 2. */
 mlmc_status mlmc_icdf_method2_table(int d, int n, int rep, int fZ, double *out);
 
+/* The FP32 exact Normal of the level kernels (Sec. 3.1): z[i] = Phi^{-1}(u_i),
+ * u_i = 2^-32 (J[i] + 1/2), as every FP32 exact path and correction estimator
+ * computes it -- the upper half folded by Phi^{-1}(1 - u) = -Phi^{-1}(u), then
+ * a cubic in each of 512 parts of (0, 1/2) (the float's exponent and top four
+ * significand bits; coefficients fitted in FP64).  Error about 1e-7 (1 + |z|).
+ * J and z are device arrays of n elements (caller-owned); the call enqueues on
+ * `stream` (NULL = legacy default stream) and returns after synchronising it.
+ * MLMC_EINVAL for a NULL array with n > 0; MLMC_ECUDA on a CUDA error. */
+mlmc_status mlmc_exact_normal_f32(const uint32_t *J, float *z, uint64_t n, void *stream);
+
 /* Mean square error E[(Z - Z~)^2] of the approximate Normal with d table bits
  * (Sec. 3.4, eq. mse_dyadic), from the library's FP64 Method-1 table Z_k (the
  * mean of Phi^{-1} over interval k, built on the GPU):

@@ -2,6 +2,7 @@
 // approximate Normal maps of Sec. 3, fixed-point re-quantisation (Sec. 4.1)
 // and 128-bit integer accumulation.
 #pragma once
+#include "phi_inv_table.h"
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
@@ -33,12 +34,21 @@ __device__ __forceinline__ uint32_t word_of(const uint4 &w, int k) {
   return k == 0 ? w.x : k == 1 ? w.y : k == 2 ? w.z : w.w;
 }
 
-// Exact Normal Z = Phi^{-1}(2^-32 (J + 1/2)) (Sec. 3.1).  The upper half uses
-// Phi^{-1}(1 - u) = -Phi^{-1}(u) so that the FP32 argument never rounds to 1.
-__device__ __forceinline__ float exact_normal_f32(uint32_t J) {
+// Exact Normal Z = Phi^{-1}(2^-32 (J + 1/2)) in single precision (Sec. 3.1).
+// The upper half uses Phi^{-1}(1 - u) = -Phi^{-1}(u): with J' = J or ~J below
+// 2^31, u = 2^-32 (J' + 1/2) (J' rounded to nearest as a float) lies in
+// [2^-33, 1/2].  Phi^{-1}(u) is the cubic of u's part (phi_inv_table.h; tab:
+// that table in shared memory): u's exponent and the top four bits of its
+// significand pick one of 512 parts of [2^-33, 1/2) (the 513th is u = 1/2),
+// the other 19 bits are the position t in [0, 1) within it.  Error: about
+// 1e-7 (1 + |Z|), unbiased (round to nearest).
+__device__ __forceinline__ float exact_normal_f32(uint32_t J, const float4 *tab) {
   const uint32_t m = (uint32_t)((int32_t)J >> 31);
   const float u = fmaf(__uint2float_rn(J ^ m), 0x1p-32f, 0x1p-33f);
-  const float z = normcdfinvf(u);
+  const uint32_t b = __float_as_uint(u);
+  const float4 c = tab[(b >> 19) - (94u << 4)];   // exponent field of 2^-33 is 94
+  const float t = __uint_as_float(((b << 4) & 0x7FFFF0u) | 0x3F800000u) - 1.0f;
+  const float z = fmaf(fmaf(fmaf(c.w, t, c.z), t, c.y), t, c.x);
   return __int_as_float(__float_as_int(z) ^ (int)(m & 0x80000000u));
 }
 

@@ -9,7 +9,9 @@ cudaError_t launch_nested_fx32(int scheme, int pc, dim3 grid, dim3 block, size_t
                                const LaunchArgs &a, int *occ, bool pre) {
   if (scheme != 0 || pc != PC_TERMINAL || occ || a.dyn || a.dump) return cudaErrorInvalidValue;
   auto k = pre ? nested_kernel<AP_FX32, 0, PC_TERMINAL, true> : nested_kernel<AP_FX32, 0, PC_TERMINAL, false>;
-  if (smem > 48 * 1024) {
+  // above 48 KB of dynamic plus static shared memory (the static part holds
+  // up to about 8.6 KB: the inverse-Normal cubics) the kernel must opt in
+  if (smem > 32 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }

@@ -60,6 +60,23 @@ template <int EST, int AP, int SCHEME, int PC, bool DYN = false> struct MinCtas 
       : ((EST == EST_APPROX && AP == AP_FX32 && PC == PC_ASIAN) ? 4 : 1);
 };
 
+// The inverse-Normal cubics of the FP32 exact path (phi_inv_table.h) in
+// shared memory: 8 KB, the same for every item.  Kernels whose chunks run an
+// FP32 exact path stage them once per CTA, before their first chunk's table
+// (whose barrier makes them visible).
+__device__ __forceinline__ float4 *phi_inv_smem() {
+  __shared__ float4 s_phi_inv[PHI_INV_PARTS];
+  return s_phi_inv;
+}
+__device__ __forceinline__ void stage_phi_inv() {
+  float4 *d = phi_inv_smem();
+  for (int k = threadIdx.x; k < PHI_INV_PARTS; k += blockDim.x) d[k] = k_phi_inv[k];
+}
+template <int EST, int XP>
+struct NeedsPhi {
+  static constexpr bool value = EST != EST_APPROX && XP == XP_F32;
+};
+
 // Bytes per entry of the shared-memory approximate-Normal table of a datapath:
 // the 32-bit fast fixed-point datapath keeps (Z~_j, sum1 of a fine step) pairs.
 template <int AP>
@@ -147,6 +164,7 @@ struct LevelSim {
   int64_t radd2p;
   uint32_t rot[KP], off_mask;
   const uint16_t *perm_s;  // method 2 coupling of the exact path (shared memory), or nullptr
+  const float4 *phi;       // FP32 exact path: the inverse-Normal cubics in shared memory
   uint32_t low_mask;
   X c1, c2, c1c, c3, S0, K;
   // fixed point
@@ -210,6 +228,7 @@ struct LevelSim {
       off_mask = ((1u << it.d) - 1u) << 3;
     }
     perm_s = nullptr;
+    if constexpr (HAS_EXACT && XP == XP_F32) phi = phi_inv_smem();
     low_mask = (1u << dshift) - 1u;
     if constexpr (EST == EST_CORR) {
       if (it.perm) perm_s = (const uint16_t *)((const unsigned char *)tab + ((size_t)1 << it.d) * TabBytes<AP>::value);
@@ -390,7 +409,7 @@ struct LevelSim {
       const uint32_t Je = perm_s ? (((uint32_t)perm_s[J >> dshift] << dshift) | (J & low_mask)) : J;
       X z;
       if constexpr (XP == XP_F64) z = exact_normal_f64(Je);
-      else z = exact_normal_f32(Je);
+      else z = exact_normal_f32(Je, phi);
       if constexpr (PC == PC_ASIAN) { if (i > 0) accF = accF + S; }
       S = fma(S, exact_inc(z, c1, X(1)), S);
       if constexpr (PC == PC_LOOKBACK) minF = fmin(minF, S);
@@ -1063,7 +1082,7 @@ __device__ __forceinline__ void chunk_body(const LaunchArgs &args, const ItemDes
 // approximate-Normal table in shared memory (unless *staged, when given, says
 // that it is there already).  Every thread has finished the previous chunk
 // before the table is overwritten (block_reduce_write ends with a barrier).
-template <int AP, int SCHEME, bool PRE = false>
+template <int AP, int SCHEME, bool PRE = false, bool PHI_BY_KIND = false>
 __device__ __forceinline__ int stage_chunk(const ItemDesc *items, int n_items, uint32_t gc, const void **staged) {
   extern __shared__ __align__(16) unsigned char smem_tab[];
   __shared__ int s_item;
@@ -1136,6 +1155,8 @@ __device__ __forceinline__ int stage_chunk(const ItemDesc *items, int n_items, u
       uint16_t *pd = (uint16_t *)(smem_tab + (size_t)n * TabBytes<AP>::value);
       for (int k = threadIdx.x; k < n; k += blockDim.x) pd[k] = it.perm[k];
     }
+    // merged launch: only the correction chunks (kind 2) run the FP32 exact path
+    if (PHI_BY_KIND && it.kind == 2) stage_phi_inv();
     __syncthreads();
   } else if constexpr (AP != AP_NONE) {
     if (!staged || it.ztab != *staged) {
@@ -1187,6 +1208,7 @@ __device__ __forceinline__ void run_chunk(const LaunchArgs &args, const ItemDesc
 template <int EST, int XP, int AP, int SCHEME, int PC, int KP>
 __global__ void __launch_bounds__(LAUNCH_THREADS, MinCtas<EST, AP, SCHEME, PC>::value)
 level_kernel(const __grid_constant__ LaunchArgs args) {
+  if constexpr (NeedsPhi<EST, XP>::value) stage_phi_inv();
   run_chunk<EST, XP, AP, SCHEME, PC, KP, false, false>(args, args.items, args.n_items, args.chunk0 + blockIdx.x,
                                                       nullptr);
 }
@@ -1197,6 +1219,7 @@ level_kernel(const __grid_constant__ LaunchArgs args) {
 template <int EST, int XP, int AP, int SCHEME, int PC, int KP>
 __global__ void __launch_bounds__(LAUNCH_THREADS, MinCtas<EST, AP, SCHEME, PC>::value)
 level_kernel_dump(const __grid_constant__ LaunchArgs args) {
+  if constexpr (NeedsPhi<EST, XP>::value) stage_phi_inv();
   run_chunk<EST, XP, AP, SCHEME, PC, KP, true, false>(args, args.items, args.n_items, args.chunk0 + blockIdx.x,
                                                      nullptr);
 }
@@ -1209,6 +1232,7 @@ __global__ void __launch_bounds__(LAUNCH_THREADS, MinCtas<EST, AP, SCHEME, PC, t
 level_kernel_dyn(const __grid_constant__ LaunchArgs args) {
   const DynLaunch d = *args.dyn;
   const void *staged = nullptr;
+  if constexpr (NeedsPhi<EST, XP>::value) stage_phi_inv();
   for (uint32_t rel = blockIdx.x; rel < d.n_chunks; rel += gridDim.x)
     run_chunk<EST, XP, AP, SCHEME, PC, KP, false, true>(args, args.items + d.item_off, (int)d.n_items,
                                                         d.chunk0 + rel, &staged);
@@ -1225,7 +1249,7 @@ template <int AP, int SCHEME, int PC, bool PRE>
 __global__ void __launch_bounds__(LAUNCH_THREADS, 6) nested_kernel(const __grid_constant__ LaunchArgs args) {
   extern __shared__ __align__(16) unsigned char smem_tab[];
   const uint32_t gc = args.chunk0 + blockIdx.x;
-  const int item = stage_chunk<AP, SCHEME, PRE>(args.items, args.n_items, gc, nullptr);
+  const int item = stage_chunk<AP, SCHEME, PRE, true>(args.items, args.n_items, gc, nullptr);
   const ItemDesc &it = args.items[item];
   if (it.kind == 0)
     chunk_body<EST_APPROX, XP_F32, AP, SCHEME, PC, 3, 0, false, false, PRE, true>(args, it, item, gc, smem_tab);
@@ -1244,7 +1268,9 @@ cudaError_t launch_one(dim3 grid, dim3 block, size_t smem, cudaStream_t st, cons
   auto k = (a.dyn || occ) ? level_kernel_dyn<EST, XP, AP, SCHEME, PC, KP>
             : a.dump       ? level_kernel_dump<EST, XP, AP, SCHEME, PC, KP>
                            : level_kernel<EST, XP, AP, SCHEME, PC, KP>;
-  if (smem > 48 * 1024) {
+  // above 48 KB of dynamic plus static shared memory (the static part holds
+  // up to about 8.6 KB: the inverse-Normal cubics) the kernel must opt in
+  if (smem > 32 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }

@@ -161,6 +161,7 @@ def load():
         "mlmc_default_format": (st, [P(Params), ctypes.c_int, P(Format)]),
         "mlmc_icdf_table": (st, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_double)]),
         "mlmc_icdf_mse": (st, [ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_double)]),
+        "mlmc_exact_normal_f32": (st, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]),
         "mlmc_philox": (st, [P(ctypes.c_uint32), ctypes.c_uint64, ctypes.c_uint64, P(ctypes.c_uint32)]),
         "mlmc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "mlmc_version": (ctypes.c_char_p, []),
@@ -592,6 +593,17 @@ def mlmc_icdf_method2_table(d, n, rep, fZ=0):
     out = (ctypes.c_double * (1 << (d - 1)))()
     _check(load().mlmc_icdf_method2_table(d, n, rep, fZ, out), "mlmc_icdf_method2_table")
     return np.frombuffer(out, dtype=np.float64).copy()
+
+
+def exact_normal_f32(J, z, stream=None):
+    """z = the FP32 exact Normal of the uint32 words J (device tensors of equal
+    length, z float32), as the level kernels compute it (mlmc_exact_normal_f32)."""
+    if J.numel() != z.numel():
+        raise ValueError("J and z differ in length")
+    h = ctypes.c_void_p(None) if stream is None else _stream_handle(stream)
+    _check(load().mlmc_exact_normal_f32(ctypes.c_void_p(J.data_ptr()), ctypes.c_void_p(z.data_ptr()),
+                                        J.numel(), h), "mlmc_exact_normal_f32")
+    return z
 
 
 def icdf_mse(d, method=1, fields=0):
