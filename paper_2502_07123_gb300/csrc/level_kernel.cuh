@@ -316,9 +316,13 @@ struct LevelSim {
     else return ff_apply<EAGER>(s, ff_sum1<MIL, AP == AP_FX32>(ff, z, c1r, m), satb);
   }
   // FX32: (Z~, sum1 of a fine step) of lane l of word w, from the shared-memory pairs
+  // (the table sits at the start of the dynamic shared memory: addressing it
+  // there, rather than through smem_tab, leaves the base to the load's
+  // immediate offset, one add fewer per lookup)
   __device__ __forceinline__ int2 fx32_entry(uint32_t w, int l) const {
+    extern __shared__ __align__(16) unsigned char smem_dyn[];
     const uint32_t off = __funnelshift_r(w, w, rot[l]) & off_mask;
-    return *(const int2 *)((const unsigned char *)smem_tab + off);
+    return *(const int2 *)(smem_dyn + off);
   }
 
   // ---- half-precision step (one rounding per operation) ----
@@ -1115,23 +1119,31 @@ __device__ __forceinline__ int stage_chunk(const ItemDesc *items, int n_items, u
     // (staged != nullptr) keeps it while its chunks stay in the same item.
     if (staged && *staged == (const void *)&it) return item;
     if (staged) *staged = (const void *)&it;
-    const int n = 1 << it.d;
+    // the item's constants in registers first: the table stores below go
+    // through a pointer the compiler cannot tell apart from the item, so
+    // fields read inside the loop would be loaded again after every store
+    const FastFixed ff = it.ff;
+    const int d = it.d, method = it.method, tab_y0 = it.tab_y0, payoff = it.payoff;
+    const int fZh = it.fx.fZ2 / 2, fS = it.fx.fS;
+    const int32_t S0q = (int32_t)it.fx.S0, Kq = (int32_t)it.fx.K;
+    const void *ztab = it.ztab;
+    const int n = 1 << d;
     int2 *dst = (int2 *)smem_tab;
-    const M3Coef *m3 = (const M3Coef *)it.ztab;
+    const M3Coef *m3 = (const M3Coef *)ztab;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
       int32_t z;
-      if (it.method != 3) {
-        z = ((const int32_t *)it.ztab)[k];
+      if (method != 3) {
+        z = ((const int32_t *)ztab)[k];
       } else {
-        const ApproxIndex ai = approx_index((uint32_t)k << (32 - it.d), it.d);
+        const ApproxIndex ai = approx_index((uint32_t)k << (32 - d), d);
         const int c = m3_class(ai.idx);
         const int64_t t = m3->A[c] + m3->B[c] * (int64_t)ai.idx;
-        const int sh = M3_FRAC - it.fx.fZ2 / 2;
+        const int sh = M3_FRAC - fZh;
         const int32_t v = (int32_t)((t + ((int64_t)1 << (sh - 1))) >> sh);
         z = ai.neg ? -v : v;
       }
-      const int32_t sum1 = ff_sum1<SCHEME == 1, true>(it.ff, z, it.ff.con1r, it.ff.mfine);
-      if (it.tab_y0) {
+      const int32_t sum1 = ff_sum1<SCHEME == 1, true>(ff, z, ff.con1r, ff.mfine);
+      if (tab_y0) {
         // level 0: the sample is a function of j alone -- S after the one fine
         // step from S0 (mul2 = rd(S0 sum1), S = rd(S0 + mul2), clamped to lim_S
         // as on the clamped datapath) and its terminal payoff
@@ -1139,16 +1151,15 @@ __device__ __forceinline__ int stage_chunk(const ItemDesc *items, int n_items, u
         // that S within lim_S: the clamp changes nothing there).  The same
         // arithmetic as LevelSim::ff_apply's 32-bit step and fixed_payoff's
         // 32-bit terminal payoff; the level-0 parity tests hold the two equal.
-        const int32_t s0 = (int32_t)it.fx.S0;
-        const int64_t p2 = (int64_t)s0 * sum1 + it.ff.radd2;
-        const int32_t mul2 = (int32_t)__funnelshift_r((uint32_t)p2, (uint32_t)((uint64_t)p2 >> 32), it.ff.rs2);
-        const int32_t s1 = (int32_t)((uint32_t)s0 + (uint32_t)mul2 * (uint32_t)it.ff.mulS);
-        const int32_t lim = (int32_t)it.ff.limS, kq = (int32_t)it.fx.K;
+        const int64_t p2 = (int64_t)S0q * sum1 + ff.radd2;
+        const int32_t mul2 = (int32_t)__funnelshift_r((uint32_t)p2, (uint32_t)((uint64_t)p2 >> 32), ff.rs2);
+        const int32_t s1 = (int32_t)((uint32_t)S0q + (uint32_t)mul2 * (uint32_t)ff.mulS);
+        const int32_t lim = (int32_t)ff.limS;
         const int32_t c = min(max(s1, -lim), lim);
-        const int32_t y = c > kq ? (it.payoff == 1 ? (int32_t)1 << it.fx.fS : c - kq) : 0;
+        const int32_t y = c > Kq ? (payoff == 1 ? (int32_t)1 << fS : c - Kq) : 0;
         dst[k] = make_int2(y, c != s1 ? 1 : 0);
       } else {
-        dst[k] = make_int2(z, PRE ? sum1 * (1 << (32 - it.ff.rs2)) : sum1);
+        dst[k] = make_int2(z, PRE ? sum1 * (1 << (32 - ff.rs2)) : sum1);
       }
     }
     if (it.perm) {   // after the table: the method-2 interval ranks
