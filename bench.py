@@ -62,7 +62,7 @@ ALU_PEAK_TOPS = 152 * 4 * 32 * 2.070e9 / 1e12
 #       python bench.py --steps 3 --warmup 3 --no-cpu-baseline --no-tte \
 #       --no-serving-sample --no-optimiser --no-sweep-levels
 # keyed by (family, path-steps per launch); another launch reports null
-DOMINANT_TRAFFIC = {}
+DOMINANT_TRAFFIC = {(24, 80148728): 175872}
 
 
 def build_items(m, rank=0, formats=None):
