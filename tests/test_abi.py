@@ -91,3 +91,22 @@ def test_no_cpu_fallback(lib):
     with pytest.raises(lib.MLMCError) as e:
         lib.mlmc_level(2, 100, P, lib.FP32_EXACT, 1)
     assert e.value.status == lib.ECUDA
+
+
+def test_null_handle_and_pointer_checks(lib):
+    # argument checks that come before any CUDA call (no GPU needed)
+    import ctypes
+    L = ctypes.CDLL(lib.LIB_PATH)
+    L.mlmc_engine_completed.restype = ctypes.c_int
+    L.mlmc_engine_completed.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    n = ctypes.c_int(-1)
+    ids = (ctypes.c_uint64 * 4)()
+    assert L.mlmc_engine_completed(None, ids, 4, ctypes.byref(n)) == lib.EINVAL
+    L.mlmc_plan_elapsed.restype = ctypes.c_int
+    L.mlmc_plan_elapsed.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    ms = ctypes.c_double()
+    assert L.mlmc_plan_elapsed(None, ctypes.byref(ms)) == lib.EINVAL
+    L.mlmc_exact_normal_f32.restype = ctypes.c_int
+    L.mlmc_exact_normal_f32.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]
+    assert L.mlmc_exact_normal_f32(None, None, 0, None) == lib.OK          # nothing to do
+    assert L.mlmc_exact_normal_f32(None, None, 16, None) == lib.EINVAL
